@@ -1,0 +1,150 @@
+"""Restriction, prolongation and the STFAS V-cycle, fp64.  Oracle -- test infrastructure only.
+
+Sec. 4.2 / Alg. 2: a FAS V(2,2) cycle on a hierarchy coarsened in space only
+(every timestep kept on every level), 10 smoothing sweeps on the coarsest
+level, coarse right-hand side res^{2h} = f^{2h}(R x^h) + R(res^h - f^h(x^h)).
+
+Readings:
+* levels halve nx, ny while both are even and the halves are >= coarsest_n.
+* R (Sec. 4.3, "simple trilinear interpolation"): a coarse cell is the mean of
+  its 4 children; a coarse face the mean of the 2 fine faces lying on it.
+* P: bilinear interpolation at the fine point -- cell fields (3/4, 1/4) per
+  axis; face fields linear along the face normal (weights 1 or 1/2, 1/2) and
+  (3/4, 1/4) across; indices beyond a wall clamp to the last coarse row.
+* Alg. 2 subtracts P(R x^h) before evaluating f(x^h); here the fine residual
+  is evaluated on the smoothed x^h and the correction is the usual
+  x^h += P(x^{2h}_new - x^{2h}_old), which is what the subtract/add pair
+  amounts to.
+* the coarse target is z^{2h} = R z^h; the fine-level res is 0.
+"""
+import numpy as np
+
+from . import kkt, mac, scgs
+
+
+def hierarchy(P):
+    grids = [P.grid]
+    g = P.grid
+    while g.nx % 2 == 0 and g.ny % 2 == 0 and g.nx // 2 >= P.coarsest_n \
+            and g.ny // 2 >= P.coarsest_n:
+        g = g.coarse()
+        grids.append(g)
+    return grids
+
+
+def restrict_cells(fine, x):
+    X = x.reshape(fine.ny, fine.nx)
+    return (0.25 * (X[0::2, 0::2] + X[0::2, 1::2] + X[1::2, 0::2] + X[1::2, 1::2])).ravel()
+
+
+def restrict_faces(fine, v):
+    vx, vy = fine.split(v)
+    cx = 0.5 * (vx[0::2, 0::2] + vx[1::2, 0::2])      # (nyc, nxc+1)
+    cy = 0.5 * (vy[0::2, 0::2] + vy[0::2, 1::2])      # (nyc+1, nxc)
+    return np.concatenate([cx.ravel(), cy.ravel()])
+
+
+def _interp_weights_cell(nf, nc):
+    """Rows: fine index -> (coarse idx a, weight wa, coarse idx b, weight wb)."""
+    k = np.arange(nf)
+    a = k // 2
+    b = np.where(k % 2 == 0, a - 1, a + 1)
+    b = np.clip(b, 0, nc - 1)
+    return a, b
+
+
+def prolong_cells(fine, coarse, xc):
+    Xc = xc.reshape(coarse.ny, coarse.nx)
+    ay, by = _interp_weights_cell(fine.ny, coarse.ny)
+    ax, bx = _interp_weights_cell(fine.nx, coarse.nx)
+    rows = 0.75 * Xc[ay, :] + 0.25 * Xc[by, :]
+    return (0.75 * rows[:, ax] + 0.25 * rows[:, bx]).ravel()
+
+
+def _interp_weights_normal(nf_faces, nc_faces):
+    """Fine face index k (0..nf) on the normal axis -> coarse faces (a, b), weights."""
+    k = np.arange(nf_faces)
+    a = k // 2
+    b = np.minimum(a + 1, nc_faces - 1)
+    wb = np.where(k % 2 == 1, 0.5, 0.0)
+    return a, b, 1.0 - wb, wb
+
+
+def prolong_faces(fine, coarse, vc):
+    cx, cy = coarse.split(vc)
+    # x-faces: normal axis x (faces 0..nx), transverse axis y (cells)
+    a, b, wa, wb = _interp_weights_normal(fine.nx + 1, coarse.nx + 1)
+    ay, by = _interp_weights_cell(fine.ny, coarse.ny)
+    t = 0.75 * cx[ay, :] + 0.25 * cx[by, :]
+    fx = t[:, a] * wa + t[:, b] * wb
+    # y-faces: normal axis y, transverse x
+    a, b, wa, wb = _interp_weights_normal(fine.ny + 1, coarse.ny + 1)
+    ax, bx = _interp_weights_cell(fine.nx, coarse.nx)
+    t = 0.75 * cy[:, ax] + 0.25 * cy[:, bx]
+    fy = t[a, :] * wa[:, None] + t[b, :] * wb[:, None]
+    return np.concatenate([fx.ravel(), fy.ravel()])
+
+
+def restrict_state(fine, x):
+    return dict(v=np.array([restrict_faces(fine, a) for a in x["v"]]),
+                pbar=np.array([restrict_cells(fine, a) for a in x["pbar"]]),
+                u=np.array([restrict_faces(fine, a) for a in x["u"]]),
+                p=np.array([restrict_cells(fine, a) for a in x["p"]]))
+
+
+def prolong_state(fine, coarse, xc):
+    return dict(v=np.array([prolong_faces(fine, coarse, a) for a in xc["v"]]),
+                pbar=np.array([prolong_cells(fine, coarse, a) for a in xc["pbar"]]),
+                u=np.array([prolong_faces(fine, coarse, a) for a in xc["u"]]),
+                p=np.array([prolong_cells(fine, coarse, a) for a in xc["p"]]))
+
+
+def restrict_faces_batch(fine, z):
+    return np.array([restrict_faces(fine, a) for a in z])
+
+
+def vcycle(P, grids, level, x, z, res):
+    """One FAS V(pre, post) cycle on level ``level`` (in place on x)."""
+    g = grids[level]
+    if level == len(grids) - 1:
+        for _ in range(P.coarse_sweeps):
+            scgs.sweep(P, g, x, z, res)
+        return
+    for _ in range(P.pre):
+        scgs.sweep(P, g, x, z, res)
+    f = kkt.nso_residual(P, g, x, z)
+    rf = {k: res[k] - f[k] for k in f}
+    gc = grids[level + 1]
+    xc = restrict_state(g, x)
+    xc_old = kkt.copy_state(xc)
+    zc = restrict_faces_batch(g, z)
+    fc = kkt.nso_residual(P, gc, xc, zc)
+    rc = restrict_state(g, rf)
+    resc = {k: fc[k] + rc[k] for k in fc}
+    # rows dropped by the fixed v_0 stay zero
+    resc["v"][0] = 0.0
+    resc["pbar"][0] = 0.0
+    vcycle(P, grids, level + 1, xc, zc, resc)
+    corr = prolong_state(g, gc, kkt.state_sub(xc, xc_old))
+    corr["v"][0] = 0.0      # v_0 is data, not an unknown
+    corr["pbar"][0] = 0.0
+    for k in x:
+        x[k] += corr[k]
+    for _ in range(P.post):
+        scgs.sweep(P, g, x, z, res)
+
+
+def normalise_pressures(x):
+    """Remove each timestep's mean from pbar and p (their null space)."""
+    x["pbar"] -= x["pbar"].mean(axis=1, keepdims=True)
+    x["p"] -= x["p"].mean(axis=1, keepdims=True)
+
+
+def stfas_cycle(P, x, z):
+    """One top-level V-cycle for f(x) = 0 followed by pressure normalisation."""
+    grids = hierarchy(P)
+    res = {k: np.zeros_like(a) for k, a in x.items()}
+    vcycle(P, grids, 0, x, z, res)
+    normalise_pressures(x)
+    f = kkt.nso_residual(P, P.grid, x, z)
+    return kkt.state_inf(f)

@@ -1,0 +1,122 @@
+"""Seeded synthetic inputs for the smoke-control workloads.
+
+This module only draws and shapes input data (initial densities, keyframe
+targets, random states for tests); it holds none of the method's arithmetic
+and is shared by the CUDA path's tests/bench and the fp64 oracle's callers.
+
+Recipes (the paper's keyframe shapes -- letters, bunny, armadillo, mocap --
+are not available, so these stand in for them):
+
+* ``gaussian_ball``: exp(-|x - c|^2 / (2 sigma^2)) at cell centres of the unit
+  square.
+* ``disc_bar_union``: the max of 3-5 shapes, each with probability 1/2 a disc
+  (centre U[0.2, 0.8]^2, radius U[0.05, 0.12]) or an axis-aligned bar (width
+  U[0.04, 0.08], length U[0.2, 0.5], orientation a coin flip); the indicator is
+  Gaussian-blurred (sigma in cells, clamped edges) and scaled to a given mass.
+"""
+import math
+
+import numpy as np
+
+
+def cell_centres(nx, ny):
+    h = 1.0 / nx
+    x = (np.arange(nx) + 0.5) * h
+    y = (np.arange(ny) + 0.5) * h
+    return np.meshgrid(x, y)          # arrays (ny, nx)
+
+
+def gaussian_ball(nx, ny, centre, sigma):
+    X, Y = cell_centres(nx, ny)
+    return np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / (2.0 * sigma * sigma)).ravel()
+
+
+def _blur_axis(a, sigma, axis):
+    R = int(math.ceil(3.0 * sigma))
+    t = np.arange(-R, R + 1)
+    w = np.exp(-t * t / (2.0 * sigma * sigma))
+    w /= w.sum()
+    n = a.shape[axis]
+    out = np.zeros_like(a)
+    for k, wk in zip(t, w):
+        idx = np.clip(np.arange(n) + k, 0, n - 1)
+        out += wk * np.take(a, idx, axis=axis)
+    return out
+
+
+def disc_bar_union(nx, ny, seed, mass, blur_cells=1.5, count=None):
+    rng = np.random.default_rng(seed)
+    X, Y = cell_centres(nx, ny)
+    m = np.zeros((ny, nx))
+    k = int(rng.integers(3, 6)) if count is None else count
+    for _ in range(k):
+        if rng.random() < 0.5:
+            c = rng.uniform(0.2, 0.8, 2)
+            r = rng.uniform(0.05, 0.12)
+            m = np.maximum(m, ((X - c[0]) ** 2 + (Y - c[1]) ** 2 <= r * r).astype(float))
+        else:
+            c = rng.uniform(0.2, 0.8, 2)
+            w = rng.uniform(0.04, 0.08)
+            L = rng.uniform(0.2, 0.5)
+            if rng.random() < 0.5:
+                hw, hh = L / 2, w / 2
+            else:
+                hw, hh = w / 2, L / 2
+            m = np.maximum(m, ((np.abs(X - c[0]) <= hw) & (np.abs(Y - c[1]) <= hh)).astype(float))
+    m = _blur_axis(_blur_axis(m, blur_cells, 0), blur_cells, 1)
+    s = m.sum()
+    return (m * (mass / s)).ravel() if s > 0 else m.ravel()
+
+
+def face_count(nx, ny):
+    return ny * (nx + 1) + (ny + 1) * nx
+
+
+def interior_face_mask(nx, ny):
+    mx = np.zeros((ny, nx + 1))
+    mx[:, 1:nx] = 1.0
+    my = np.zeros((ny + 1, nx))
+    my[1:ny, :] = 1.0
+    return np.concatenate([mx.ravel(), my.ravel()])
+
+
+def random_faces(rng, nx, ny, count, scale=1.0):
+    """Random face fields, zero on wall faces: (count, F)."""
+    m = interior_face_mask(nx, ny)
+    return rng.standard_normal((count, face_count(nx, ny))) * m * scale
+
+
+def swirl_velocity(nx, ny, amplitude, centre=(0.5, 0.5), width=0.25):
+    """A smooth vortex-like face field (zero on walls), for non-trivial states."""
+    h = 1.0 / nx
+    xs = np.arange(nx + 1) * h
+    ys = (np.arange(ny) + 0.5) * h
+    X, Y = np.meshgrid(xs, ys)
+    g = np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / (2 * width ** 2))
+    vx = -(Y - centre[1]) * g * amplitude
+    vx[:, 0] = 0.0
+    vx[:, nx] = 0.0
+    xs = (np.arange(nx) + 0.5) * h
+    ys = np.arange(ny + 1) * h
+    X, Y = np.meshgrid(xs, ys)
+    g = np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / (2 * width ** 2))
+    vy = (X - centre[0]) * g * amplitude
+    vy[0, :] = 0.0
+    vy[ny, :] = 0.0
+    return np.concatenate([vx.ravel(), vy.ravel()])
+
+
+def config_small(n=32, N=16):
+    """2D, n^2 cells, N steps, dt = 1/N: ball (sigma 0.08) at (0.5, 0.3) to the
+    same ball at (0.5, 0.7) at t = T, zero initial velocity, r = 1e-3."""
+    rho0 = gaussian_ball(n, n, (0.5, 0.3), 0.08)
+    star = gaussian_ball(n, n, (0.5, 0.7), 0.08)
+    return dict(nx=n, ny=n, N=N, dt=1.0 / N, rho0=rho0, keyframes={N: (star, 1.0)}, r=1e-3)
+
+
+def config_letters(n=128, N=40, seed=2002):
+    """2D, 128^2 cells, 40 steps: ball (sigma 0.08) at (0.5, 0.25) to a seeded,
+    blurred (1.5 cells), mass-matched disc/bar union at t = T, r = 1e-3."""
+    rho0 = gaussian_ball(n, n, (0.5, 0.25), 0.08)
+    star = disc_bar_union(n, n, seed, rho0.sum(), 1.5)
+    return dict(nx=n, ny=n, N=N, dt=1.0 / N, rho0=rho0, keyframes={N: (star, 1.0)}, r=1e-3)
