@@ -1,0 +1,239 @@
+/*
+ * stc.h -- C ABI of libstc: keyframe smoke control by spacetime multigrid on one
+ * GPU (Pan & Manocha, "Efficient Optimal Control of Smoke using Spacetime
+ * Multigrid", arXiv 1608.01102).
+ *
+ * The library solves the control problem of Eq. opt: find forces u_0..u_{N-1}
+ * on a 2D staggered grid so that the density rho_i advected by the implicit
+ * Navier-Stokes velocity v_i (Eq. NSA, NSB, Conv) matches keyframes rho*_i,
+ * with force regularisation r.  It runs the paper's ADMM loop (Alg. 3): the
+ * advection-optimisation fixed point (Alg. 1) and the Navier-Stokes
+ * optimisation solved by STFAS V-cycles (Alg. 2) with the temporally augmented
+ * SCGS smoother (Eq. HESS).
+ *
+ * Conventions (all entry points):
+ *  - Grid: nx x ny cells on [0, nx h] x [0, ny h], h = 1/nx, closed box (all
+ *    wall-normal velocities are zero).  Centre fields are [ny][nx], i fastest.
+ *    Face fields are all x-faces [ny][nx+1] then all y-faces [ny+1][nx], i
+ *    fastest; wall faces are stored and are zero.  A time-dependent field is
+ *    a contiguous sequence of such slabs (v: N+1 slabs, u: N slabs, ...).
+ *  - Host arrays are double precision and owned by the caller; the library
+ *    copies every input and never keeps a host pointer.  A length argument
+ *    that does not match the field returns STC_ERR_INVALID_ARG and writes
+ *    nothing.
+ *  - Device precision follows stc_params.precision: 0 = fp32 state with fp64
+ *    reductions and an fp64 coarsest STFAS level; 1 = fp64 everywhere.
+ *  - All work is enqueued on the CUDA stream given at creation (NULL = the
+ *    legacy default stream); calls that return numbers synchronise it.
+ *  - No exception crosses the ABI.  A CUDA error returns STC_ERR_CUDA and
+ *    leaves the problem unusable.  stc_last_error() gives a thread-local
+ *    message for the last failing call.
+ *  - A problem must not be used from two host threads at once.
+ */
+#ifndef STC_H
+#define STC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  STC_OK = 0,
+  STC_ERR_INVALID_ARG = 1,
+  STC_ERR_OOM = 2,
+  STC_ERR_CUDA = 3,
+  STC_ERR_NOT_CONVERGED = 4,
+  STC_ERR_DIVERGED = 5, /* Taylor order above taylor_kmax, or a non-finite norm */
+  STC_ERR_UNSUPPORTED = 6
+} stc_status;
+
+typedef struct stc_problem stc_problem; /* opaque; owns all of its device memory */
+
+/* Parameters.  Defaults (stc_default_params) follow the paper's Table 2 where it
+ * gives a value and the readings stated beside each field otherwise. */
+typedef struct {
+  int nx, ny;           /* cells per axis (2D); h = 1/nx                          */
+  int num_steps;        /* N timesteps (Sec. 3)                                    */
+  double dt;            /* timestep                                                */
+  double r;             /* force regularisation (Eq. opt)                          */
+  double K;             /* ADMM penalty (Eq. optAdmm); changes the rate, not the solution; default 1 */
+  double beta;          /* multiplier step lambda += K beta (v - v*) (Alg. 3), default 1 */
+  int precision;        /* 0 = fp32 state + fp64 reductions/coarsest, 1 = fp64 */
+  int ao_iters;         /* Alg. 1 forward/backward pairs per ADMM iteration (Table 2: 2) */
+  int pre, post;        /* V-cycle smoothing sweeps (Alg. 2: 2, 2)                 */
+  int coarse_sweeps;    /* smoothing sweeps on the coarsest level (Alg. 2: 10)     */
+  int coarsest_n;       /* stop coarsening below this many cells per axis (4)      */
+  double taylor_tol;    /* Taylor truncation, relative to max|rho_0| (Sec. 3.1: 1e-5) */
+  int taylor_kmax;      /* Taylor order limit; exceeding it is STC_ERR_DIVERGED (64) */
+  double eps_stfas;     /* NSO stop: ||f||_inf <= eps_stfas * ||f||_inf at the first NSO (1e-5) */
+  double eps_admm;      /* ADMM stop on max_i ||rho_i - rho_i^last||_inf (Alg. 3); <0: max|rho_0|/100 */
+  int max_vcycles;      /* V-cycle cap per NSO solve (20)                          */
+  int metric_levels;    /* Gaussian filters in C_i (Sec. 4.1); 0 gives C_i = c_i I  */
+  double metric_sigma0; /* std-dev of the first filter in cells (1)                */
+  double scgs_omega;    /* SCGS under-relaxation (0.8)                             */
+  double lm_shift;      /* Levenberg-Marquardt shift of the smoother's v blocks; <0: 1/dt^2 */
+  int poisson_vcycles;  /* multigrid cycles per projection Q (8)                   */
+  int self_advection;   /* 1 (default); 0 drops Adv (linear saddle problem, tests only) */
+} stc_params;
+
+typedef struct {
+  int admm_iters;      /* ADMM iterations run                                  */
+  int vcycles;         /* V-cycles run in total                                */
+  double kkt_rel;      /* ||g(v)|| / ||g(v_start)|| at exit                    */
+  double kkt_abs;      /* ||g(v)||                                             */
+  double f_inf;        /* NSO residual ||f||_inf at exit                       */
+  double drho;         /* last max_i ||rho_i - rho_i^last||_inf                */
+  double seconds;      /* wall time of the solve                               */
+  double seconds_to_1e4; /* time at which kkt_rel first reached 1e-4 (<0: never) */
+} stc_report;
+
+/* Field identifiers for stc_get_field / stc_set_field (level 0 = finest grid). */
+typedef enum {
+  STC_FIELD_V = 0,      /* velocity v_i, i = 0..N           (N+1) x faces  (level l) */
+  STC_FIELD_PBAR = 1,   /* multiplier pbar_i, i = 0..N      (N+1) x cells  (level l) */
+  STC_FIELD_U = 2,      /* force u_i, i = 0..N-1            N x faces      (level l) */
+  STC_FIELD_P = 3,      /* pressure p_{i+1}, i = 0..N-1     N x cells      (level l) */
+  STC_FIELD_RES_V = 4,  /* residual buffer, rows 1..4 of f  same shapes as V, PBAR, U, P */
+  STC_FIELD_RES_PBAR = 5,
+  STC_FIELD_RES_U = 6,
+  STC_FIELD_RES_P = 7,
+  STC_FIELD_Z = 8,      /* NSO target z_i = v*_i - lambda_i/K  N x faces (level l) */
+  STC_FIELD_VSTAR = 9,  /* slack velocity v*_i, i = 0..N-1  N x faces      */
+  STC_FIELD_LAMBDA = 10,/* ADMM multiplier lambda_i          N x faces      */
+  STC_FIELD_RHO = 11,   /* density rho_i, i = 0..N           (N+1) x cells  */
+  STC_FIELD_MU = 12,    /* adjoint mu_i, i = 0..N-1          N x cells      */
+  STC_FIELD_W = 13,     /* AO target w_i = v_i + lambda_i/K  N x faces      */
+  STC_FIELD_Y = 14,     /* adjoint-sweep output, see stc_adjoint  N x faces  */
+  STC_FIELD_KKT_U = 15, /* u_i(v) of the KKT metric          N x faces      */
+  STC_FIELD_KKT_G = 16, /* reduced gradient g_i(v)           (N+1) x faces  */
+  STC_FIELD_MTERM = 17, /* C_i (rho_i - rho*_i)              (N+1) x cells  */
+  STC_FIELD_RES_IN_V = 18, /* FAS right-hand side res^h of level l (V, PBAR, U, P shapes) */
+  STC_FIELD_RES_IN_PBAR = 19,
+  STC_FIELD_RES_IN_U = 20,
+  STC_FIELD_RES_IN_P = 21,
+  STC_FIELD_XOLD_V = 22,   /* copy of R x^h kept for the FAS correction (level l >= 1) */
+  STC_FIELD_XOLD_PBAR = 23,
+  STC_FIELD_XOLD_U = 24,
+  STC_FIELD_XOLD_P = 25
+} stc_field;
+
+/* Fill *p with the defaults for an nx x ny grid with N steps, dt = 1/N. */
+void stc_default_params(stc_params* p, int nx, int ny, int num_steps);
+
+/* Create a problem (Sec. 3: initial density rho_0 and initial velocity v_0,
+ * which is fixed).  rho0: nx*ny doubles; v0: face array or NULL for zero.
+ * cuda_stream: a cudaStream_t, or NULL.  Allocates all device memory of the
+ * problem (state of every level, AO/KKT buffers, scratch).  Errors:
+ * INVALID_ARG (bad sizes/params), UNSUPPORTED (grid beyond the kernels'
+ * on-chip limits: 2D, nx*ceil(ny/8) <= 4096, projection levels fit in shared
+ * memory), OOM, CUDA. */
+stc_status stc_create_problem(const stc_params* params, const double* rho0, const double* v0,
+                              void* cuda_stream, stc_problem** out);
+
+/* Keyframes (Eq. opt: c_i ||rho_i - rho*_i||^2 with c_i replaced by the metric
+ * C_i of Sec. 4.1).  steps: count step indices in 1..N; rho_star: count x
+ * cells; c: count weights or NULL for 1.  Replaces earlier keyframes. */
+stc_status stc_set_keyframes(stc_problem* p, int count, const int* steps, const double* rho_star,
+                             const double* c);
+
+/* ncycles STFAS V-cycles (Alg. 2) on the NSO system f = 0 with the current
+ * state and target z, each followed by removal of the pressures' means.
+ * nso_res_inf (may be NULL) receives ||f||_inf after the last cycle. */
+stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf);
+
+/* The ADMM outer loop (Alg. 3) from v_i = 0 (i >= 1), lambda = 0: stop when the
+ * relative KKT residual ||g(v)||/||g(v_start)|| <= kkt_rel_tol, or on the
+ * paper's density-change test, or after max_admm iterations (then
+ * STC_ERR_NOT_CONVERGED, with the state kept).  report may be NULL. */
+stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_report* report);
+
+/* Results.  len must equal the field size: u N x faces, rho (N+1) x cells,
+ * v (N+1) x faces. */
+stc_status stc_get_forces(const stc_problem* p, double* u, size_t len);
+stc_status stc_get_density(const stc_problem* p, double* rho, size_t len);
+stc_status stc_get_velocity(const stc_problem* p, double* v, size_t len);
+
+stc_status stc_destroy_problem(stc_problem* p);
+const char* stc_last_error(void);
+
+/* ---- step-level entry points: each runs one row of the hot path ---------- */
+
+/* Copy a field of level `level` to / from the host (sizes as listed in
+ * stc_field; level must be 0 for fields that exist on the finest grid only). */
+stc_status stc_get_field(const stc_problem* p, int field, int level, double* out, size_t len);
+stc_status stc_set_field(stc_problem* p, int field, int level, const double* in, size_t len);
+/* Number of levels, and the cells per axis of one level. */
+stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx, int* ny);
+
+/* Forward density sweep (Eq. Conv, Eq. Adv): rho_{i+1} = A[rho_i, w_i] with
+ * w = v* (source STC_FIELD_VSTAR) or w = v (STC_FIELD_V); writes STC_FIELD_RHO
+ * and the Taylor orders (read with stc_get_taylor_orders). */
+stc_status stc_advect(stc_problem* p, int source_field);
+stc_status stc_get_taylor_orders(const stc_problem* p, int* K, size_t len);
+
+/* Keyframe metric terms C_i (rho_i - rho*_i) of the current STC_FIELD_RHO into
+ * STC_FIELD_MTERM (zero at steps without a keyframe). */
+stc_status stc_metric_terms(stc_problem* p);
+
+/* Backward adjoint sweep of Alg. 1 / Eq. KKTPO for the velocity of the last
+ * stc_advect (source_field as there), using STC_FIELD_RHO, the Taylor orders
+ * and STC_FIELD_MTERM: mu_{i-1} = (dA_i/drho)^T mu_i - C_i(rho_i - rho*_i) into
+ * STC_FIELD_MU, and Y_i = alpha W_i + beta (dA[rho_i, w_i]/dw_i)^T mu_i,
+ * i = 1..N-1, into STC_FIELD_Y. */
+stc_status stc_adjoint(stc_problem* p, int source_field, double alpha, double beta);
+
+/* Solenoidal projection Q (Eq. KKTPO) in place on slabs [first, first+count)
+ * of a face field of the finest level (V, U, VSTAR, Y, W, KKT_U, KKT_G, Z). */
+stc_status stc_project(stc_problem* p, int field, int first, int count);
+
+/* One AO solve (Alg. 1): w = v + lambda/K, v* = w, then `iters` forward /
+ * backward / projection passes; then z = v* - lambda/K on every level. */
+stc_status stc_ao(stc_problem* p, int iters);
+/* z = v* - lambda/K on the finest level, restricted to every coarser level. */
+stc_status stc_prepare_targets(stc_problem* p);
+
+/* NSO residual (Eq. KKTAO) of level `level`: RES fields = f(x) - res^h
+ * (res^h = 0 on the finest level); *inf (may be NULL) = its max-norm. */
+stc_status stc_nso_residual(stc_problem* p, int level, double* inf);
+
+/* `sweeps` SCGS sweeps (Sec. 4.3, Eq. HESS) on level `level` for f = res^h. */
+stc_status stc_smooth(stc_problem* p, int level, int sweeps);
+
+/* FAS transfers of Alg. 2 between level l and l+1: x^{2h} = R x^h (also kept
+ * as XOLD), and x^h += P(x^{2h} - XOLD^{2h}). */
+stc_status stc_restrict(stc_problem* p, int level);
+stc_status stc_prolong_correct(stc_problem* p, int level);
+
+/* Reduced gradient of the KKT metric at the current v: g_i = Q[r(-u_i/dt +
+ * (I/dt + dAdv(v_i))^T u_{i-1}) - (dA[rho_i, v_i]/dv_i)^T mu_i] (Appendix A)
+ * into STC_FIELD_KKT_G; *norm = ||g||_2 (fp64). */
+stc_status stc_kkt_residual(stc_problem* p, double* norm);
+
+/* lambda_i += K beta (v_i - v*_i) (Alg. 3) and *drho = max_i ||rho_i - rho_i^last||_inf,
+ * then rho^last = rho. */
+stc_status stc_admm_update(stc_problem* p, double* drho);
+
+/* ---- instrumentation ------------------------------------------------------ */
+
+/* Number of kernel launches this problem has enqueued since creation (a V-cycle
+ * graph replay counts each kernel node it runs). */
+stc_status stc_launch_count(const stc_problem* p, long long* launches);
+
+/* enable != 0: the V-cycle graph is rebuilt with a CUDA event pair around every
+ * finest-level SCGS colour launch (the dominant kernel), recorded on the
+ * stream that runs it; stc_kernel_timing then returns the summed device time
+ * (ms) and the number of timed launches since the last enable.  enable = 0
+ * rebuilds the graph without events. */
+stc_status stc_set_kernel_timing(stc_problem* p, int enable);
+stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* launches);
+
+/* Device memory held by the problem, in bytes. */
+stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STC_H */

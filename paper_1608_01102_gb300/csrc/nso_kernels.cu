@@ -1,0 +1,693 @@
+// NSO subproblem kernels: residual f of Eq. KKTAO, the temporally augmented
+// SCGS smoother of Sec. 4.3 / Eq. HESS, the STFAS transfer operators R and P
+// (Sec. 4.3, Alg. 2) and reductions.
+#include "stc_internal.cuh"
+#include "stc_kernels.h"
+
+namespace stc {
+
+// ---------------------------------------------------------------------------
+// f(v, pbar, u, p)  (Eq. KKTAO with v_0 fixed, z = v* - lambda/K):
+//   row 1, faces, t = 1..N : a(v_t - z_t)[t<N] - u_t/dt [t<N] + u_{t-1}/dt
+//                            + (dAdv(v_t))^T u_{t-1} + grad pbar_t
+//   row 2, cells, t = 1..N : -div v_t
+//   row 3, faces, t = 0..N-1: (v_{t+1} - v_t)/dt + Adv(v_{t+1}) - u_t + grad p_{t+1}
+//   row 4, cells, t = 0..N-1: -div u_t
+// out = sf * f + sr * res (res may be null).  Rows dropped by the fixed v_0
+// (row 1/2 at t = 0) and wall-face rows are written as 0.
+// Thread x: element index e (a face if e < F, and a cell if e < C);
+// blockIdx.y: time t in [0, N].
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z,
+                                   CState<T> res, State<T> out, T sf, T sr) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (t > g.N) return;
+  const int N = g.N;
+  const T idt = T(g.idt);
+  const T sa = T(g.self_adv);
+  if (e < g.F) {
+    int j, i;
+    bool isx = e < g.Fx;
+    if (isx) {
+      j = e / (g.nx + 1);
+      i = e - j * (g.nx + 1);
+    } else {
+      int q = e - g.Fx;
+      j = q / g.nx;
+      i = q - j * g.nx;
+    }
+    bool interior = isx ? xf_interior(g, j, i) : yf_interior(g, j, i);
+    // row 1 at time t (t >= 1)
+    if (t >= 1) {
+      T val = T(0);
+      if (interior) {
+        const T* vt = x.v + (size_t)t * g.F;
+        const T* um = x.u + (size_t)(t - 1) * g.F;
+        const T* pb = x.pbar + (size_t)t * g.C;
+        val = ld(um + e) * idt;
+        if (g.self_adv) val += sa * (isx ? jtu_x(g, vt, um, j, i) : jtu_y(g, vt, um, j, i));
+        val += isx ? grad_x(g, pb, j, i) : grad_y(g, pb, j, i);
+        if (t < N) {
+          const T* ut = x.u + (size_t)t * g.F;
+          val += T(g.a) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * idt;
+        }
+        val *= sf;
+        if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
+      }
+      out.v[(size_t)t * g.F + e] = val;
+    } else {
+      out.v[e] = T(0);
+    }
+    // row 3 at time t (t < N)
+    if (t < N) {
+      T val = T(0);
+      if (interior) {
+        const T* vn = x.v + (size_t)(t + 1) * g.F;
+        const T* vt = x.v + (size_t)t * g.F;
+        const T* pp = x.p + (size_t)t * g.C;
+        val = (ld(vn + e) - ld(vt + e)) * idt - ld(x.u + (size_t)t * g.F + e);
+        if (g.self_adv) val += sa * (isx ? adv_x(g, vn, j, i) : adv_y(g, vn, j, i));
+        val += isx ? grad_x(g, pp, j, i) : grad_y(g, pp, j, i);
+        val *= sf;
+        if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
+      }
+      out.u[(size_t)t * g.F + e] = val;
+    }
+  }
+  if (e < g.C) {
+    const int j = e / g.nx, i = e - (e / g.nx) * g.nx;
+    if (t >= 1) {
+      T val = -divergence(g, x.v + (size_t)t * g.F, j, i) * sf;
+      if (res.pbar) val += sr * ld(res.pbar + (size_t)t * g.C + e);
+      out.pbar[(size_t)t * g.C + e] = val;
+    } else {
+      out.pbar[e] = T(0);
+    }
+    if (t < N) {
+      T val = -divergence(g, x.u + (size_t)t * g.F, j, i) * sf;
+      if (res.p) val += sr * ld(res.p + (size_t)t * g.C + e);
+      out.p[(size_t)t * g.C + e] = val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SCGS: one colour.  For a cell (j,i) the local unknowns per time block are
+// B_u(t) = {u_t on the 4 faces, p_{t+1}} and B_v(t) = {v_t on the faces,
+// pbar_t}, ordered B_u(0), B_v(1), B_u(1), ..., B_u(N-1), B_v(N).  The local
+// Jacobian is the Eq. HESS restriction: diagonal blocks [[aI, g],[g^T, 0]] and
+// [[-I, g],[g^T, 0]]; couplings -I/dt (v_t with u_t) and I/dt + dAdv_loc(v_{t+1})
+// (u_t with v_{t+1}) and its transpose; the v diagonal carries the
+// Levenberg-Marquardt shift.  It is solved by block Thomas elimination.  Every
+// modified diagonal block keeps the saddle form [[A4, g],[g^T, 0]] with A4
+// symmetric definite, which is solved by LDL^T plus a Schur step on g.
+// rhs = -(f - res), read from a residual buffer computed for this colour.
+// ---------------------------------------------------------------------------
+
+// d Adv_f / d v_g for f, g in (L, R, B, T) faces of cell (j,i), at field v.
+template <class T>
+__device__ void local_adv_jac(const Geom& g, const T* v, int j, int i, T J[4][4]) {
+  const T ih = T(g.ih);
+  // node interior flags at the four corners
+  auto an = [&](int jj, int ii) -> T {
+    return (ii > 0 && ii < g.nx && jj > 0 && jj < g.ny) ? T(1) : T(0);
+  };
+  const T a00 = an(j, i), a10 = an(j + 1, i), a01 = an(j, i + 1), a11 = an(j + 1, i + 1);
+  const T w00 = node_omega(g, v, j, i), w10 = node_omega(g, v, j + 1, i);
+  const T w01 = node_omega(g, v, j, i + 1), w11 = node_omega(g, v, j + 1, i + 1);
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) J[r][c] = T(0);
+  // f = L (x-face (j,i)), s = -1
+  if (xf_interior(g, j, i)) {
+    T wb = T(0.5) * (w00 + w10), tv = tv_x(g, v, j, i);
+    // d wbar / d(L,R,B,T)
+    T dL = T(0.5) * (-a00 + a10) * ih, dB = T(0.5) * a00 * ih, dT = T(0.5) * a10 * ih;
+    J[0][0] = -(dL * tv);
+    J[0][2] = -(dB * tv + wb * T(0.25));
+    J[0][3] = -(dT * tv + wb * T(0.25));
+  }
+  // f = R (x-face (j,i+1)), s = -1
+  if (xf_interior(g, j, i + 1)) {
+    T wb = T(0.5) * (w01 + w11), tv = tv_x(g, v, j, i + 1);
+    T dR = T(0.5) * (-a01 + a11) * ih, dB = -T(0.5) * a01 * ih, dT = -T(0.5) * a11 * ih;
+    J[1][1] = -(dR * tv);
+    J[1][2] = -(dB * tv + wb * T(0.25));
+    J[1][3] = -(dT * tv + wb * T(0.25));
+  }
+  // f = B (y-face (j,i)), s = +1
+  if (yf_interior(g, j, i)) {
+    T wb = T(0.5) * (w00 + w01), tv = tv_y(g, v, j, i);
+    T dB = T(0.5) * (a00 - a01) * ih, dL = -T(0.5) * a00 * ih, dR = -T(0.5) * a01 * ih;
+    J[2][2] = dB * tv;
+    J[2][0] = dL * tv + wb * T(0.25);
+    J[2][1] = dR * tv + wb * T(0.25);
+  }
+  // f = T (y-face (j+1,i)), s = +1
+  if (yf_interior(g, j + 1, i)) {
+    T wb = T(0.5) * (w10 + w11), tv = tv_y(g, v, j + 1, i);
+    T dT = T(0.5) * (a10 - a11) * ih, dL = T(0.5) * a10 * ih, dR = T(0.5) * a11 * ih;
+    J[3][3] = dT * tv;
+    J[3][0] = dL * tv + wb * T(0.25);
+    J[3][1] = dR * tv + wb * T(0.25);
+  }
+}
+
+// Solve [[A, gv],[gv^T, 0]] [X; y] = [Bm; q] for 5 right-hand sides
+// (columns 0..3 of Bm with q = 0, column 4 with q = q4).  A is 4x4 symmetric
+// definite (either sign): LDL^T without pivoting.
+template <class T>
+__device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5], T q4, T Y[5]) {
+  // LDL^T in place: A = L D L^T, L unit lower (stored below the diagonal), D on diagonal
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T d = A[k][k];
+#pragma unroll
+    for (int s = 0; s < k; ++s) d -= A[k][s] * A[k][s] * A[s][s];
+    A[k][k] = d;
+    T id = T(1) / d;
+#pragma unroll
+    for (int r = k + 1; r < 4; ++r) {
+      T l = A[r][k];
+#pragma unroll
+      for (int s = 0; s < k; ++s) l -= A[r][s] * A[k][s] * A[s][s];
+      A[r][k] = l * id;
+    }
+  }
+  // solve A X = [B | gv] (6 columns: 5 rhs + g)
+  T X[4][6];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) X[r][c] = B[r][c];
+    X[r][5] = gv[r];
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      T s = X[r][c];
+#pragma unroll
+      for (int k = 0; k < r; ++k) s -= A[r][k] * X[k][c];
+      X[r][c] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) X[r][c] /= A[r][r];
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+      T s = X[r][c];
+#pragma unroll
+      for (int k = r + 1; k < 4; ++k) s -= A[k][r] * X[k][c];
+      X[r][c] = s;
+    }
+  }
+  // Schur step: y = (g^T A^{-1} b - q) / (g^T A^{-1} g); x = A^{-1} b - A^{-1} g y
+  T sgg = T(0);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) sgg += gv[r] * X[r][5];
+  T isgg = T(1) / sgg;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T sgb = T(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sgb += gv[r] * X[r][c];
+    T y = (sgb - (c == 4 ? q4 : T(0))) * isgg;
+    Y[c] = y;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) B[r][c] = X[r][c] - X[r][5] * y;
+  }
+}
+
+// Scratch layout per colour launch: for block k of the cell with colour-local
+// index q: Cp[k][20][ncell] then dp[k][5][ncell].
+template <class T>
+__global__ void scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
+                                   T* __restrict__ scratch) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncell = ncx * ncy;
+  if (q >= ncell) return;
+  const int i = 2 * (q % ncx) + (colour & 1);
+  const int j = 2 * (q / ncx) + (colour >> 1);
+  if (i >= g.nx || j >= g.ny) return;
+  const int N = g.N;
+  const int nb = 2 * N;
+  const T idt = T(g.idt);
+  const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+  const T act[4] = {T(i > 0), T(i < g.nx - 1), T(j > 0), T(j < g.ny - 1)};
+  const T gv[4] = {act[0] * T(g.ih), -act[1] * T(g.ih), act[2] * T(g.ih), -act[3] * T(g.ih)};
+  const int cc = cidx(g, j, i);
+  const size_t blk = (size_t)25 * ncell;
+
+  // forward elimination
+  T Cprev[4][4];      // face part of C'_{k-1} (its pressure row is not needed by L)
+  T dprev[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    dprev[a] = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Cprev[a][b] = T(0);
+  }
+  for (int k = 0; k < nb; ++k) {
+    const bool ublk = (k % 2) == 0;
+    const int t = ublk ? k / 2 : (k + 1) / 2;
+    // diagonal face block and right-hand side
+    T A[4][4];
+    T diag;
+    if (ublk) diag = T(-1);
+    else diag = (t < N ? T(g.a) : T(0)) + T(g.lm);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) A[a][b] = (a == b) ? (act[a] > T(0) ? diag : T(1)) : T(0);
+    T B[4][5];
+    T q4;
+    if (ublk) {
+      const T* ru = r.u + (size_t)t * g.F;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) B[a][4] = -ld(ru + fidx[a]) * act[a];
+      q4 = -ld(r.p + (size_t)t * g.C + cc);
+    } else {
+      const T* rv = r.v + (size_t)t * g.F;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) B[a][4] = -ld(rv + fidx[a]) * act[a];
+      q4 = -ld(r.pbar + (size_t)t * g.C + cc);
+    }
+    // lower coupling L (face block) to block k-1
+    if (k >= 1) {
+      T L[4][4];
+      if (ublk) {
+        // J[B_u(t), B_v(t)] = -I/dt
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) L[a][b] = (a == b) ? -idt * act[a] : T(0);
+      } else {
+        // J[B_v(t), B_u(t-1)] = (I/dt + dAdv_loc(v_t))^T
+        T Jl[4][4];
+        local_adv_jac(g, x.v + (size_t)t * g.F, j, i, Jl);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            L[a][b] = ((a == b ? idt : T(0)) + T(g.self_adv) * Jl[b][a]) * act[a] * act[b];
+      }
+      // A -= L Cprev ; rhs -= L dprev
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          s += L[a][b] * dprev[b];
+          T acc = T(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc += L[a][c] * Cprev[c][b];
+          A[a][b] -= acc;
+        }
+        B[a][4] -= s;
+      }
+    }
+    // upper coupling U (face block) to block k+1
+    if (k < nb - 1) {
+      if (ublk) {
+        // J[B_u(t), B_v(t+1)] = I/dt + dAdv_loc(v_{t+1})
+        T Jl[4][4];
+        local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            B[a][b] = ((a == b ? idt : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b];
+      } else {
+        // J[B_v(t), B_u(t)] = -I/dt
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) B[a][b] = (a == b) ? -idt * act[a] : T(0);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) B[a][b] = T(0);
+    }
+    // symmetrise the face block (it is symmetric in exact arithmetic)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a + 1; b < 4; ++b) {
+        T m = T(0.5) * (A[a][b] + A[b][a]);
+        A[a][b] = m;
+        A[b][a] = m;
+      }
+    T Y[5];
+    saddle_solve(A, gv, B, q4, Y);
+    // store C'_k (5 x 4) and d'_k (5)
+    T* sk = scratch + (size_t)k * blk;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        sk[(size_t)(a * 4 + b) * ncell + q] = B[a][b];
+        Cprev[a][b] = B[a][b];
+      }
+      sk[(size_t)(20 + a) * ncell + q] = B[a][4];
+      dprev[a] = B[a][4];
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) sk[(size_t)(16 + b) * ncell + q] = Y[b];
+    sk[(size_t)24 * ncell + q] = Y[4];
+  }
+  // back substitution and update x += omega * delta
+  const T om = T(g.omega);
+  T xn[4] = {T(0), T(0), T(0), T(0)};
+  for (int k = nb - 1; k >= 0; --k) {
+    const T* sk = scratch + (size_t)k * blk;
+    T d[5];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) d[a] = sk[(size_t)(20 + a) * ncell + q];
+    d[4] = sk[(size_t)24 * ncell + q];
+    if (k < nb - 1) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s += sk[(size_t)(a * 4 + b) * ncell + q] * xn[b];
+        d[a] -= s;
+      }
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) s += sk[(size_t)(16 + b) * ncell + q] * xn[b];
+      d[4] -= s;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) xn[a] = d[a];
+    const bool ublk = (k % 2) == 0;
+    const int t = ublk ? k / 2 : (k + 1) / 2;
+    if (ublk) {
+      T* ut = x.u + (size_t)t * g.F;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (act[a] > T(0)) ut[fidx[a]] += om * d[a];
+      x.p[(size_t)t * g.C + cc] += om * d[4];
+    } else {
+      T* vt = x.v + (size_t)t * g.F;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (act[a] > T(0)) vt[fidx[a]] += om * d[a];
+      x.pbar[(size_t)t * g.C + cc] += om * d[4];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// transfers (Sec. 4.3): R = mean of the 4 children (cells) / the 2 coincident
+// fine faces (faces); P = bilinear interpolation, faces linear along the
+// normal and (3/4, 1/4) across, clamped at walls.
+// ---------------------------------------------------------------------------
+template <class Tf, class Tc>
+__global__ void restrict_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, const Tf* __restrict__ sf,
+                                const Tf* __restrict__ sc_cells, Tc* df, Tc* dc_cells, Tc* df2,
+                                Tc* dc2) {
+  // faces: nt_face timesteps of gc.F entries; cells: nt_cell timesteps of gc.C
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nfaces = (size_t)nt_face * gc.F;
+  const size_t ncells = (size_t)nt_cell * gc.C;
+  if (e < nfaces) {
+    const int t = (int)(e / gc.F);
+    const int f = (int)(e - (size_t)t * gc.F);
+    const Tf* s = sf + (size_t)t * gf.F;
+    Tc val;
+    if (f < gc.Fx) {
+      int J = f / (gc.nx + 1), I = f - J * (gc.nx + 1);
+      val = Tc(0.5) * (Tc(s[xf(gf, 2 * J, 2 * I)]) + Tc(s[xf(gf, 2 * J + 1, 2 * I)]));
+    } else {
+      int q = f - gc.Fx;
+      int J = q / gc.nx, I = q - J * gc.nx;
+      val = Tc(0.5) * (Tc(s[yf(gf, 2 * J, 2 * I)]) + Tc(s[yf(gf, 2 * J, 2 * I + 1)]));
+    }
+    df[e] = val;
+    if (df2) df2[e] = val;
+  } else if (e < nfaces + ncells) {
+    const size_t ec = e - nfaces;
+    const int t = (int)(ec / gc.C);
+    const int c = (int)(ec - (size_t)t * gc.C);
+    const Tf* s = sc_cells + (size_t)t * gf.C;
+    int J = c / gc.nx, I = c - J * gc.nx;
+    Tc val = Tc(0.25) * (Tc(s[cidx(gf, 2 * J, 2 * I)]) + Tc(s[cidx(gf, 2 * J, 2 * I + 1)]) +
+                         Tc(s[cidx(gf, 2 * J + 1, 2 * I)]) + Tc(s[cidx(gf, 2 * J + 1, 2 * I + 1)]));
+    dc_cells[ec] = val;
+    if (dc2) dc2[ec] = val;
+  }
+}
+
+__device__ __forceinline__ void cell_interp(int k, int nc, int& a, int& b) {
+  a = k >> 1;
+  b = (k & 1) ? a + 1 : a - 1;
+  b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
+}
+
+// fine += P(coarse_new - coarse_old) for faces (t in [t0, t0+nt)) and cells
+template <class Tf, class Tc>
+__global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, int t0_face,
+                                       int t0_cell, Tf* ff, Tf* fc, const Tc* __restrict__ cnf,
+                                       const Tc* __restrict__ cof, const Tc* __restrict__ cnc,
+                                       const Tc* __restrict__ coc) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nfaces = (size_t)nt_face * gf.F;
+  const size_t ncells = (size_t)nt_cell * gf.C;
+  if (e < nfaces) {
+    const int t = (int)(e / gf.F) + t0_face;
+    const int f = (int)(e - (size_t)(t - t0_face) * gf.F);
+    const Tc* n = cnf + (size_t)t * gc.F;
+    const Tc* o = cof + (size_t)t * gc.F;
+    double val;
+    if (f < gf.Fx) {
+      int j = f / (gf.nx + 1), i = f - j * (gf.nx + 1);
+      int ja, jb;
+      cell_interp(j, gc.ny, ja, jb);
+      int ia = i >> 1, ib = (i & 1) ? ia + 1 : ia;
+      double wb = (i & 1) ? 0.5 : 0.0, wa = 1.0 - wb;
+      auto d = [&](int J, int I) { return double(n[xf(gc, J, I)]) - double(o[xf(gc, J, I)]); };
+      double ta = 0.75 * d(ja, ia) + 0.25 * d(jb, ia);
+      double tb = 0.75 * d(ja, ib) + 0.25 * d(jb, ib);
+      val = wa * ta + wb * tb;
+    } else {
+      int qq = f - gf.Fx;
+      int j = qq / gf.nx, i = qq - j * gf.nx;
+      int ia, ib;
+      cell_interp(i, gc.nx, ia, ib);
+      int ja = j >> 1, jb = (j & 1) ? ja + 1 : ja;
+      double wb = (j & 1) ? 0.5 : 0.0, wa = 1.0 - wb;
+      auto d = [&](int J, int I) { return double(n[yf(gc, J, I)]) - double(o[yf(gc, J, I)]); };
+      double ta = 0.75 * d(ja, ia) + 0.25 * d(ja, ib);
+      double tb = 0.75 * d(jb, ia) + 0.25 * d(jb, ib);
+      val = wa * ta + wb * tb;
+    }
+    ff[(size_t)t * gf.F + f] += Tf(val);
+  } else if (e < nfaces + ncells) {
+    const size_t ec = e - nfaces;
+    const int t = (int)(ec / gf.C) + t0_cell;
+    const int c = (int)(ec - (size_t)(t - t0_cell) * gf.C);
+    const Tc* n = cnc + (size_t)t * gc.C;
+    const Tc* o = coc + (size_t)t * gc.C;
+    int j = c / gf.nx, i = c - j * gf.nx;
+    int ja, jb, ia, ib;
+    cell_interp(j, gc.ny, ja, jb);
+    cell_interp(i, gc.nx, ia, ib);
+    auto d = [&](int J, int I) { return double(n[cidx(gc, J, I)]) - double(o[cidx(gc, J, I)]); };
+    double val = 0.5625 * d(ja, ia) + 0.1875 * d(ja, ib) + 0.1875 * d(jb, ia) + 0.0625 * d(jb, ib);
+    fc[(size_t)t * gf.C + c] += Tf(val);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reductions (fp64) and small elementwise kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <class T>
+__global__ void absmax_kernel(const T* __restrict__ a, size_t n, double* out, int* err) {
+  double m = 0.0;
+  bool bad = false;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = fabs((double)a[e]);
+    if (!(v <= 1e300)) bad = true;
+    else m = fmax(m, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x + 31) / 32) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+  }
+  if (bad && err) atomicOr(err, DEV_NONFINITE);
+}
+
+template <class T>
+__global__ void sumsq_kernel(const T* __restrict__ a, size_t n, double* out) {
+  double s = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = (double)a[e];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x + 31) / 32) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+// subtract the mean of each of `count` slabs of length C (one block per slab)
+template <class T>
+__global__ void remove_mean_kernel(T* a, int C) {
+  T* s = a + (size_t)blockIdx.x * C;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < C; e += blockDim.x) acc += (double)s[e];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double sm[32];
+  __shared__ double mean;
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) tot += sm[w];
+    mean = tot / C;
+  }
+  __syncthreads();
+  const T m = T(mean);
+  for (int e = threadIdx.x; e < C; e += blockDim.x) s[e] -= m;
+}
+
+template <class Ts, class Td>
+__global__ void convert_kernel(const Ts* __restrict__ s, Td* d, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    d[e] = Td(s[e]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+template <class T>
+void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                         cudaStream_t st) {
+  const int tpb = 128;
+  const int n = g.F > g.C ? g.F : g.C;
+  dim3 grid(blocks_for(n, tpb), g.N + 1);
+  nso_residual_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, sf, sr);
+}
+
+int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
+
+template <class T>
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, T* scratch, cudaStream_t st) {
+  const int ncx = colour_extent(g.nx, colour & 1);
+  const int ncy = colour_extent(g.ny, colour >> 1);
+  const int ncell = ncx * ncy;
+  if (ncell <= 0) return;
+  const int tpb = 64;
+  scgs_colour_kernel<T><<<blocks_for(ncell, tpb), tpb, 0, st>>>(g, x, r, colour, ncx, ncy, scratch);
+}
+
+template <class Tf, class Tc>
+void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st) {
+  const int tpb = 256;
+  const int N = gf.N;
+  // v (N+1 slabs) with pbar (N+1), then u (N) with p (N)
+  size_t n1 = (size_t)(N + 1) * gc.F + (size_t)(N + 1) * gc.C;
+  restrict_kernel<Tf, Tc><<<blocks_for(n1, tpb), tpb, 0, st>>>(gf, gc, N + 1, N + 1, s.v, s.pbar, d.v, d.pbar,
+                                                                d2.v, d2.pbar);
+  size_t n2 = (size_t)N * gc.F + (size_t)N * gc.C;
+  restrict_kernel<Tf, Tc><<<blocks_for(n2, tpb), tpb, 0, st>>>(gf, gc, N, N, s.u, s.p, d.u, d.p, d2.u, d2.p);
+}
+
+template <class Tf, class Tc>
+void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st) {
+  const int tpb = 256;
+  size_t n = (size_t)nt * gc.F;
+  restrict_kernel<Tf, Tc><<<blocks_for(n, tpb), tpb, 0, st>>>(gf, gc, nt, 0, s, nullptr, d, nullptr, nullptr,
+                                                              nullptr);
+}
+
+template <class Tf, class Tc>
+void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
+                            cudaStream_t st) {
+  const int tpb = 256;
+  const int N = gf.N;
+  // v and pbar for t = 1..N (v_0 is data), u and p for t = 0..N-1
+  size_t n1 = (size_t)N * gf.F + (size_t)N * gf.C;
+  prolong_correct_kernel<Tf, Tc><<<blocks_for(n1, tpb), tpb, 0, st>>>(gf, gc, N, N, 1, 1, f.v, f.pbar, cn.v, co.v,
+                                                                      cn.pbar, co.pbar);
+  size_t n2 = (size_t)N * gf.F + (size_t)N * gf.C;
+  prolong_correct_kernel<Tf, Tc><<<blocks_for(n2, tpb), tpb, 0, st>>>(gf, gc, N, N, 0, 0, f.u, f.p, cn.u, co.u,
+                                                                      cn.p, co.p);
+}
+
+template <class T>
+void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st) {
+  const int tpb = 256;
+  unsigned nb = blocks_for(n, tpb);
+  if (nb > 1216) nb = 1216;
+  if (nb == 0) nb = 1;
+  absmax_kernel<T><<<nb, tpb, 0, st>>>(a, n, out, err);
+}
+
+template <class T>
+void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st) {
+  const int tpb = 256;
+  unsigned nb = blocks_for(n, tpb);
+  if (nb > 1216) nb = 1216;
+  if (nb == 0) nb = 1;
+  sumsq_kernel<T><<<nb, tpb, 0, st>>>(a, n, out);
+}
+
+template <class T>
+void launch_remove_mean(T* a, int count, int C, cudaStream_t st) {
+  if (count <= 0) return;
+  remove_mean_kernel<T><<<count, 256, 0, st>>>(a, C);
+}
+
+template <class Ts, class Td>
+void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
+  const int tpb = 256;
+  unsigned nb = blocks_for(n, tpb);
+  if (nb > 4096) nb = 4096;
+  if (nb == 0) return;
+  convert_kernel<Ts, Td><<<nb, tpb, 0, st>>>(s, d, n);
+}
+
+#define STC_INST_T(T)                                                                                     \
+  template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
+                                       cudaStream_t);                                                      \
+  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, T*, cudaStream_t);            \
+  template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
+  template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
+  template void launch_remove_mean<T>(T*, int, int, cudaStream_t);
+STC_INST_T(float)
+STC_INST_T(double)
+
+#define STC_INST_TT(Tf, Tc)                                                                                 \
+  template void launch_restrict<Tf, Tc>(const Geom&, const Geom&, CState<Tf>, State<Tc>, State<Tc>,        \
+                                        cudaStream_t);                                                     \
+  template void launch_restrict_faces<Tf, Tc>(const Geom&, const Geom&, int, const Tf*, Tc*, cudaStream_t); \
+  template void launch_prolong_correct<Tf, Tc>(const Geom&, const Geom&, State<Tf>, CState<Tc>, CState<Tc>, \
+                                               cudaStream_t);                                              \
+  template void launch_convert<Tf, Tc>(const Tf*, Tc*, size_t, cudaStream_t);
+STC_INST_TT(float, float)
+STC_INST_TT(float, double)
+STC_INST_TT(double, float)
+STC_INST_TT(double, double)
+
+}  // namespace stc

@@ -1,0 +1,356 @@
+// Solenoidal projection Q (Eq. KKTPO: the multiplier of div v* = 0 replaced by
+// Q, computed with a multigrid Poisson solver, Sec. 4.1) and the elementwise
+// kernels of the AO / KKT / ADMM steps.
+//
+// Q v = v - G phi with (D G) phi = D v on the closed box.  One CTA projects one
+// face field: b = D v, phi and every coarse level live in shared memory (a
+// 128^2 fp32 field needs ~171 KB), red-black Gauss-Seidel V(2,2) cycles with
+// average restriction and bilinear prolongation, the coarsest level (<= 3x3)
+// solved by Gauss-Seidel in fp64, then v - G phi written back.
+#include "stc_internal.cuh"
+#include "stc_kernels.h"
+
+namespace stc {
+
+constexpr int kPoissonThreads = 1024;
+constexpr int kMaxPoissonLevels = 12;
+
+struct PLevels {
+  int n;
+  int nx[kMaxPoissonLevels], ny[kMaxPoissonLevels];
+  size_t off[kMaxPoissonLevels];  // element offsets of phi_l; b_l follows phi_l
+};
+
+__host__ __device__ inline PLevels poisson_levels(int nx, int ny) {
+  PLevels L;
+  L.n = 0;
+  size_t off = 0;
+  int a = nx, b = ny;
+  while (true) {
+    L.nx[L.n] = a;
+    L.ny[L.n] = b;
+    L.off[L.n] = off;
+    off += 2 * (size_t)a * b;
+    L.n++;
+    if (L.n == kMaxPoissonLevels || a % 2 || b % 2 || a / 2 < 2 || b / 2 < 2) break;
+    a /= 2;
+    b /= 2;
+  }
+  return L;
+}
+
+__device__ __forceinline__ int ci(int n, int j, int i) { return j * n + i; }
+
+// red-black Gauss-Seidel half sweep on level (nx, ny, h2 = h^2): phi_c = (sum phi_nb - h2 b_c)/n_nb
+template <class T>
+__device__ void rb_half(T* phi, const T* b, int nx, int ny, T h2, int colour) {
+  const int n = nx * ny;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int j = e / nx, i = e - (e / nx) * nx;
+    if (((i + j) & 1) != colour) continue;
+    T s = T(0);
+    int k = 0;
+    if (i > 0) { s += phi[e - 1]; ++k; }
+    if (i < nx - 1) { s += phi[e + 1]; ++k; }
+    if (j > 0) { s += phi[e - nx]; ++k; }
+    if (j < ny - 1) { s += phi[e + nx]; ++k; }
+    phi[e] = (s - h2 * b[e]) / T(k);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T lap(const T* phi, int nx, int ny, int j, int i, T ih2) {
+  const int e = j * nx + i;
+  T s = T(0);
+  int k = 0;
+  if (i > 0) { s += phi[e - 1]; ++k; }
+  if (i < nx - 1) { s += phi[e + 1]; ++k; }
+  if (j > 0) { s += phi[e - nx]; ++k; }
+  if (j < ny - 1) { s += phi[e + nx]; ++k; }
+  return (s - T(k) * phi[e]) * ih2;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPoissonThreads, 1)
+project_kernel(Geom g, T* fields, int vcycles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  __shared__ double red[32];
+  const PLevels L = poisson_levels(g.nx, g.ny);
+  T* v = fields + (size_t)blockIdx.x * g.F;
+  const int nx = g.nx, ny = g.ny;
+  T* phi0 = sm + L.off[0];
+  T* b0 = phi0 + (size_t)nx * ny;
+  // b = D v, phi = 0
+  for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) {
+    const int j = e / nx, i = e - (e / nx) * nx;
+    b0[e] = divergence(g, v, j, i);
+    phi0[e] = T(0);
+  }
+  __syncthreads();
+  const int nl = L.n;
+  for (int cyc = 0; cyc < vcycles; ++cyc) {
+    // descend
+    for (int l = 0; l < nl - 1; ++l) {
+      const int lx = L.nx[l], ly = L.ny[l];
+      const double h = g.h * (double)(1 << l);
+      const T h2 = T(h * h), ih2 = T(1.0 / (h * h));
+      T* phi = sm + L.off[l];
+      T* b = phi + (size_t)lx * ly;
+      if (l > 0) {
+        for (int e = threadIdx.x; e < lx * ly; e += blockDim.x) phi[e] = T(0);
+        __syncthreads();
+      }
+      for (int s = 0; s < 2; ++s) {
+        rb_half(phi, b, lx, ly, h2, 0);
+        __syncthreads();
+        rb_half(phi, b, lx, ly, h2, 1);
+        __syncthreads();
+      }
+      // restricted residual: b_{l+1} = mean over the 4 children of (b - L phi)
+      const int cx = L.nx[l + 1], cy = L.ny[l + 1];
+      T* bc = sm + L.off[l + 1] + (size_t)cx * cy;
+      for (int e = threadIdx.x; e < cx * cy; e += blockDim.x) {
+        const int J = e / cx, I = e - (e / cx) * cx;
+        T acc = T(0);
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+          for (int di = 0; di < 2; ++di) {
+            const int jj = 2 * J + dj, ii = 2 * I + di;
+            acc += b[jj * lx + ii] - lap(phi, lx, ly, jj, ii, ih2);
+          }
+        bc[e] = T(0.25) * acc;
+      }
+      __syncthreads();
+    }
+    // coarsest: Gauss-Seidel in fp64 on the compatible (mean-free) right-hand side
+    {
+      const int l = nl - 1;
+      const int lx = L.nx[l], ly = L.ny[l];
+      const double h = g.h * (double)(1 << l);
+      T* phi = sm + L.off[l];
+      T* b = phi + (size_t)lx * ly;
+      if (threadIdx.x == 0) {
+        double bb[64], pp[64];
+        const int n = lx * ly;
+        double mean = 0.0;
+        for (int e = 0; e < n; ++e) mean += (double)b[e];
+        mean /= n;
+        for (int e = 0; e < n; ++e) {
+          bb[e] = (double)b[e] - mean;
+          pp[e] = 0.0;
+        }
+        for (int it = 0; it < 200; ++it)
+          for (int e = 0; e < n; ++e) {
+            const int j = e / lx, i = e % lx;
+            double s = 0.0;
+            int k = 0;
+            if (i > 0) { s += pp[e - 1]; ++k; }
+            if (i < lx - 1) { s += pp[e + 1]; ++k; }
+            if (j > 0) { s += pp[e - lx]; ++k; }
+            if (j < ly - 1) { s += pp[e + lx]; ++k; }
+            pp[e] = (s - h * h * bb[e]) / k;
+          }
+        for (int e = 0; e < n; ++e) phi[e] = T(pp[e]);
+      }
+      __syncthreads();
+    }
+    // ascend: phi_l += P phi_{l+1}, post-smooth
+    for (int l = nl - 2; l >= 0; --l) {
+      const int lx = L.nx[l], ly = L.ny[l];
+      const int cx = L.nx[l + 1], cy = L.ny[l + 1];
+      const double h = g.h * (double)(1 << l);
+      const T h2 = T(h * h);
+      T* phi = sm + L.off[l];
+      T* b = phi + (size_t)lx * ly;
+      const T* pc = sm + L.off[l + 1];
+      for (int e = threadIdx.x; e < lx * ly; e += blockDim.x) {
+        const int j = e / lx, i = e - (e / lx) * lx;
+        const int ja = j >> 1, ia = i >> 1;
+        int jb = (j & 1) ? ja + 1 : ja - 1;
+        int ib = (i & 1) ? ia + 1 : ia - 1;
+        jb = jb < 0 ? 0 : (jb > cy - 1 ? cy - 1 : jb);
+        ib = ib < 0 ? 0 : (ib > cx - 1 ? cx - 1 : ib);
+        phi[e] += T(0.5625) * pc[ja * cx + ia] + T(0.1875) * pc[ja * cx + ib] + T(0.1875) * pc[jb * cx + ia] +
+                  T(0.0625) * pc[jb * cx + ib];
+      }
+      __syncthreads();
+      for (int s = 0; s < 2; ++s) {
+        rb_half(phi, b, lx, ly, h2, 0);
+        __syncthreads();
+        rb_half(phi, b, lx, ly, h2, 1);
+        __syncthreads();
+      }
+    }
+  }
+  (void)red;
+  // v -= G phi on interior faces
+  for (int e = threadIdx.x; e < g.F; e += blockDim.x) {
+    if (e < g.Fx) {
+      const int j = e / (nx + 1), i = e - j * (nx + 1);
+      if (i >= 1 && i <= nx - 1) v[e] -= (phi0[j * nx + i] - phi0[j * nx + i - 1]) * T(g.ih);
+      else v[e] = T(0);
+    } else {
+      const int q = e - g.Fx;
+      const int j = q / nx, i = q - j * nx;
+      if (j >= 1 && j <= ny - 1) v[e] -= (phi0[j * nx + i] - phi0[(j - 1) * nx + i]) * T(g.ih);
+      else v[e] = T(0);
+    }
+  }
+}
+
+size_t project_smem(const Geom& g, size_t tsize) {
+  const PLevels L = poisson_levels(g.nx, g.ny);
+  const int l = L.n - 1;
+  return (L.off[l] + 2 * (size_t)L.nx[l] * L.ny[l]) * tsize;
+}
+
+bool project_supported(const Geom& g, size_t tsize) {
+  const PLevels L = poisson_levels(g.nx, g.ny);
+  const int l = L.n - 1;
+  return project_smem(g, tsize) <= 227 * 1024 && L.nx[l] * L.ny[l] <= 64;
+}
+
+template <class T>
+cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t sm = project_smem(g, sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute((const void*)project_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  project_kernel<T><<<count, kPoissonThreads, sm, st>>>(g, fields, vcycles);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+// w_s = v_s + lambda_s / K (s >= 1), w_0 = v_0; v*_s = w_s   (Alg. 1 initialisation)
+template <class T>
+__global__ void ao_init_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ lam, double invK, T* w,
+                               T* vstar) {
+  const size_t n = (size_t)g.N * g.F;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    T val = v[e];
+    if (e >= (size_t)g.F) val += T(invK) * lam[e];
+    w[e] = val;
+    vstar[e] = val;
+  }
+}
+
+template <class T>
+__global__ void axpby_kernel(size_t n, const T* __restrict__ a, double alpha, const T* __restrict__ b, double beta,
+                             T* out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = T(alpha) * a[e] + T(beta) * b[e];
+}
+
+// u_raw_t = (v_{t+1} - v_t)/dt + Adv(v_{t+1}), t = 0..N-1   (Appendix A)
+template <class T>
+__global__ void kkt_force_rhs_kernel(Geom g, const T* __restrict__ v, T* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (e >= g.F || t >= g.N) return;
+  const T* vn = v + (size_t)(t + 1) * g.F;
+  const T* vt = v + (size_t)t * g.F;
+  T val = T(0);
+  if (e < g.Fx) {
+    const int j = e / (g.nx + 1), i = e - j * (g.nx + 1);
+    if (xf_interior(g, j, i)) val = (vn[e] - vt[e]) * T(g.idt) + T(g.self_adv) * adv_x(g, vn, j, i);
+  } else {
+    const int q = e - g.Fx;
+    const int j = q / g.nx, i = q - j * g.nx;
+    if (yf_interior(g, j, i)) val = (vn[e] - vt[e]) * T(g.idt) + T(g.self_adv) * adv_y(g, vn, j, i);
+  }
+  out[(size_t)t * g.F + e] = val;
+}
+
+// g_raw_t = r(u_{t-1}/dt + dAdv(v_t)^T u_{t-1} - u_t/dt [t<N]) + dens_t, t = 1..N
+template <class T>
+__global__ void kkt_grad_rhs_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ u,
+                                    const T* __restrict__ dens, double r, T* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y + 1;
+  if (e >= g.F || t > g.N) return;
+  const T* vt = v + (size_t)t * g.F;
+  const T* um = u + (size_t)(t - 1) * g.F;
+  T val = T(0);
+  bool inter;
+  T jt = T(0);
+  if (e < g.Fx) {
+    const int j = e / (g.nx + 1), i = e - j * (g.nx + 1);
+    inter = xf_interior(g, j, i);
+    if (inter && g.self_adv) jt = jtu_x(g, vt, um, j, i);
+  } else {
+    const int q = e - g.Fx;
+    const int j = q / g.nx, i = q - j * g.nx;
+    inter = yf_interior(g, j, i);
+    if (inter && g.self_adv) jt = jtu_y(g, vt, um, j, i);
+  }
+  if (inter) {
+    T s = um[e] * T(g.idt) + jt;
+    if (t < g.N) s -= u[(size_t)t * g.F + e] * T(g.idt);
+    val = T(r) * s + dens[(size_t)t * g.F + e];
+  }
+  out[(size_t)t * g.F + e] = val;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg2(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <class T>
+__global__ void absdiff_max_copy_kernel(const T* __restrict__ a, T* b, size_t n, double* out) {
+  double m = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    m = fmax(m, fabs((double)a[e] - (double)b[e]));
+    b[e] = a[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg2(out, m);
+}
+
+static inline unsigned nblk(size_t n, int tpb, unsigned cap = 4096) {
+  size_t b = (n + tpb - 1) / tpb;
+  if (b > cap) b = cap;
+  return b == 0 ? 1u : (unsigned)b;
+}
+
+template <class T>
+void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, cudaStream_t st) {
+  ao_init_kernel<T><<<nblk((size_t)g.N * g.F, 256), 256, 0, st>>>(g, v, lam, invK, w, vstar);
+}
+template <class T>
+void launch_axpby_faces(const Geom& g, int count, const T* a, double alpha, const T* b, double beta, T* out,
+                        cudaStream_t st) {
+  const size_t n = (size_t)count * g.F;
+  if (n == 0) return;
+  axpby_kernel<T><<<nblk(n, 256), 256, 0, st>>>(n, a, alpha, b, beta, out);
+}
+template <class T>
+void launch_kkt_force_rhs(const Geom& g, const T* v, T* out, cudaStream_t st) {
+  dim3 grid((g.F + 127) / 128, g.N);
+  kkt_force_rhs_kernel<T><<<grid, 128, 0, st>>>(g, v, out);
+}
+template <class T>
+void launch_kkt_grad_rhs(const Geom& g, const T* v, const T* u, const T* dens, double r, T* out, cudaStream_t st) {
+  dim3 grid((g.F + 127) / 128, g.N);
+  kkt_grad_rhs_kernel<T><<<grid, 128, 0, st>>>(g, v, u, dens, r, out);
+}
+template <class T>
+void launch_absdiff_max_copy(const T* a, T* b, size_t n, double* out, cudaStream_t st) {
+  absdiff_max_copy_kernel<T><<<nblk(n, 256, 1216), 256, 0, st>>>(a, b, n, out);
+}
+
+#define STC_POI_INST(T)                                                                                        \
+  template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t);                            \
+  template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, cudaStream_t);             \
+  template void launch_axpby_faces<T>(const Geom&, int, const T*, double, const T*, double, T*, cudaStream_t); \
+  template void launch_kkt_force_rhs<T>(const Geom&, const T*, T*, cudaStream_t);                             \
+  template void launch_kkt_grad_rhs<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);  \
+  template void launch_absdiff_max_copy<T>(const T*, T*, size_t, double*, cudaStream_t);
+STC_POI_INST(float)
+STC_POI_INST(double)
+
+}  // namespace stc

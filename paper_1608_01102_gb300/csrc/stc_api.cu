@@ -1,0 +1,1147 @@
+// Host orchestration and C ABI of libstc (see include/stc.h).
+//
+// The STFAS V-cycle (Alg. 2) is enqueued as a fixed sequence of kernels and
+// captured once into a CUDA graph, then replayed; the AO fixed point (Alg. 1),
+// the KKT metric and the ADMM loop (Alg. 3) are enqueued on the problem's
+// stream.  Host code only marshals arguments, sequences launches and reads
+// back fp64 scalars for the stopping tests.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/stc.h"
+#include "stc_internal.cuh"
+#include "stc_kernels.h"
+
+using namespace stc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct FieldSet {
+  void* v = nullptr;
+  void* pbar = nullptr;
+  void* u = nullptr;
+  void* p = nullptr;
+};
+
+struct Level {
+  Geom g;
+  bool dbl = false;
+  FieldSet x, res, tmp, old;
+  void* z = nullptr;
+  void* scratch = nullptr;
+};
+
+template <class T>
+State<T> st_of(const FieldSet& f) {
+  return State<T>{(T*)f.v, (T*)f.pbar, (T*)f.u, (T*)f.p};
+}
+template <class T>
+CState<T> cst_of(const FieldSet& f) {
+  return CState<T>{(const T*)f.v, (const T*)f.pbar, (const T*)f.u, (const T*)f.p};
+}
+
+template <class F>
+void dispatch(bool dbl, F&& f) {
+  if (dbl) f(double());
+  else f(float());
+}
+
+struct StcError {
+  stc_status code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(stc_status code, const std::string& msg) { throw StcError{code, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(STC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct stc_problem {
+  stc_params prm;
+  cudaStream_t st = nullptr;      // user stream (may be the legacy default)
+  cudaStream_t cap = nullptr;     // private stream used only to capture graphs
+  bool dbl = false;               // finest-level type is double
+  size_t ts = 4;
+  std::vector<Level> lv;
+  std::vector<void*> allocs;
+  void *rho = nullptr, *rho_k = nullptr, *rho_last = nullptr, *mu = nullptr, *vstar = nullptr, *lam = nullptr,
+       *w = nullptr, *y = nullptr, *uk = nullptr, *gk = nullptr, *dens = nullptr, *powers = nullptr,
+       *v0 = nullptr;
+  int *K = nullptr, *Kk = nullptr;
+  double *mterm = nullptr, *mtmp0 = nullptr, *mtmp1 = nullptr, *star = nullptr;
+  std::vector<int> key_steps;
+  std::vector<double> key_c;
+  double* dscal = nullptr;  // device fp64 scalars
+  double* hscal = nullptr;  // pinned host mirror
+  int* derr = nullptr;
+  int* herr = nullptr;
+  double rho_scale = 0.0;
+  double fscale = -1.0;
+  cudaGraphExec_t vgraph = nullptr;
+  bool broken = false;
+  // instrumentation
+  long long launches = 0;       // kernels enqueued (graph replays add graph_launches)
+  long long graph_launches = 0; // kernel nodes of the V-cycle graph
+  long long* counter = nullptr; // where enqueue sites count: &launches, or &graph_launches while capturing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  int ev_used = 0;              // event pairs recorded by the current graph
+  double timed_ms = 0.0;
+  long long timed_launches = 0;
+  size_t bytes = 0;
+};
+
+namespace {
+
+void count(stc_problem* P, long long k) { *(P->counter ? P->counter : &P->launches) += k; }
+
+void* dalloc(stc_problem* P, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  P->bytes += bytes;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? STC_ERR_OOM : STC_ERR_CUDA,
+         std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  P->allocs.push_back(p);
+  ck(cudaMemsetAsync(p, 0, bytes, P->st), "memset");
+  return p;
+}
+
+Geom make_geom(const stc_params& prm, int nx, int ny, double h) {
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.N = prm.num_steps;
+  g.Fx = ny * (nx + 1);
+  g.F = g.Fx + (ny + 1) * nx;
+  g.C = nx * ny;
+  g.h = h;
+  g.ih = 1.0 / h;
+  g.dt = prm.dt;
+  g.idt = 1.0 / prm.dt;
+  g.a = prm.K / prm.r;
+  g.lm = prm.lm_shift < 0 ? 1.0 / (prm.dt * prm.dt) : prm.lm_shift;
+  g.omega = prm.scgs_omega;
+  g.self_adv = prm.self_advection ? 1 : 0;
+  return g;
+}
+
+size_t esz(bool dbl) { return dbl ? 8 : 4; }
+
+void alloc_fieldset(stc_problem* P, FieldSet& f, const Geom& g, bool dbl) {
+  const size_t s = esz(dbl);
+  const int N = g.N;
+  f.v = dalloc(P, (size_t)(N + 1) * g.F * s);
+  f.pbar = dalloc(P, (size_t)(N + 1) * g.C * s);
+  f.u = dalloc(P, (size_t)N * g.F * s);
+  f.p = dalloc(P, (size_t)N * g.C * s);
+}
+
+void check_launch(const char* what) { ck(cudaGetLastError(), what); }
+
+// ---------------------------------------------------------------------------
+// NSO building blocks
+// ---------------------------------------------------------------------------
+// out = sf * f(x) + sr * res  on level l
+void nso_residual(stc_problem* P, int l, double sf, double sr, const FieldSet& res, const FieldSet& out,
+                  cudaStream_t st) {
+  Level& L = P->lv[l];
+  dispatch(L.dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st);
+  });
+  count(P, 1);
+}
+
+void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = false) {
+  Level& L = P->lv[l];
+  for (int s = 0; s < sweeps; ++s)
+    for (int c = 0; c < 4; ++c) {
+      nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st);
+      const bool ev = timed && P->ev_used < (int)P->ev_start.size();
+      if (ev) ck(cudaEventRecordWithFlags(P->ev_start[P->ev_used], st, cudaEventRecordExternal), "event");
+      dispatch(L.dbl, [&](auto tag) {
+        using T = decltype(tag);
+        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, (T*)L.scratch, st);
+      });
+      if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
+      count(P, 1);
+    }
+}
+
+void restrict_level(stc_problem* P, int l, cudaStream_t st) {
+  Level& F = P->lv[l];
+  Level& Cc = P->lv[l + 1];
+  dispatch(F.dbl, [&](auto tf) {
+    using Tf = decltype(tf);
+    dispatch(Cc.dbl, [&](auto tc) {
+      using Tc = decltype(tc);
+      launch_restrict<Tf, Tc>(F.g, Cc.g, cst_of<Tf>(F.x), st_of<Tc>(Cc.x), st_of<Tc>(Cc.old), st);
+    });
+  });
+  count(P, 2);
+}
+
+void restrict_residual(stc_problem* P, int l, cudaStream_t st) {
+  Level& F = P->lv[l];
+  Level& Cc = P->lv[l + 1];
+  dispatch(F.dbl, [&](auto tf) {
+    using Tf = decltype(tf);
+    dispatch(Cc.dbl, [&](auto tc) {
+      using Tc = decltype(tc);
+      launch_restrict<Tf, Tc>(F.g, Cc.g, cst_of<Tf>(F.tmp), st_of<Tc>(Cc.res), State<Tc>{nullptr, nullptr, nullptr, nullptr},
+                              st);
+    });
+  });
+  count(P, 2);
+}
+
+void prolong_level(stc_problem* P, int l, cudaStream_t st) {
+  Level& F = P->lv[l];
+  Level& Cc = P->lv[l + 1];
+  dispatch(F.dbl, [&](auto tf) {
+    using Tf = decltype(tf);
+    dispatch(Cc.dbl, [&](auto tc) {
+      using Tc = decltype(tc);
+      launch_prolong_correct<Tf, Tc>(F.g, Cc.g, st_of<Tf>(F.x), cst_of<Tc>(Cc.x), cst_of<Tc>(Cc.old), st);
+    });
+  });
+  count(P, 2);
+}
+
+void vcycle_level(stc_problem* P, int l, cudaStream_t st) {
+  const int nl = (int)P->lv.size();
+  if (l == nl - 1) {
+    smooth(P, l, P->prm.coarse_sweeps, st);
+    return;
+  }
+  Level& L = P->lv[l];
+  Level& Cc = P->lv[l + 1];
+  const bool timed = P->timing && l == 0 && P->counter == &P->graph_launches;
+  smooth(P, l, P->prm.pre, st, timed);
+  nso_residual(P, l, -1.0, 1.0, L.res, L.tmp, st);         // r^h = res^h - f^h(x^h)
+  restrict_level(P, l, st);                                 // x^{2h} = R x^h, kept as XOLD
+  restrict_residual(P, l, st);                              // res^{2h} = R r^h
+  nso_residual(P, l + 1, 1.0, 1.0, Cc.res, Cc.res, st);     // res^{2h} += f^{2h}(R x^h)
+  vcycle_level(P, l + 1, st);
+  prolong_level(P, l, st);                                  // x^h += P(x^{2h} - R x^h)
+  smooth(P, l, P->prm.post, st, timed);
+}
+
+void remove_pressure_means(stc_problem* P, cudaStream_t st) {
+  Level& L = P->lv[0];
+  dispatch(L.dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_remove_mean<T>((T*)L.x.pbar + L.g.C, L.g.N, L.g.C, st);
+    launch_remove_mean<T>((T*)L.x.p, L.g.N, L.g.C, st);
+  });
+  count(P, 2);
+}
+
+// ||f(x) - res||_inf of level l into dscal[slot]
+void residual_norm(stc_problem* P, int l, int slot, cudaStream_t st) {
+  Level& L = P->lv[l];
+  nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st);
+  ck(cudaMemsetAsync(P->dscal + slot, 0, sizeof(double), st), "memset");
+  const Geom& g = L.g;
+  dispatch(L.dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_absmax<T>((const T*)L.tmp.v, (size_t)(g.N + 1) * g.F, P->dscal + slot, P->derr, st);
+    launch_absmax<T>((const T*)L.tmp.pbar, (size_t)(g.N + 1) * g.C, P->dscal + slot, P->derr, st);
+    launch_absmax<T>((const T*)L.tmp.u, (size_t)g.N * g.F, P->dscal + slot, P->derr, st);
+    launch_absmax<T>((const T*)L.tmp.p, (size_t)g.N * g.C, P->dscal + slot, P->derr, st);
+  });
+  count(P, 4);
+}
+
+void enqueue_top_vcycle(stc_problem* P, cudaStream_t st) {
+  vcycle_level(P, 0, st);
+  remove_pressure_means(P, st);
+  residual_norm(P, 0, 0, st);
+}
+
+double read_scalar(stc_problem* P, int slot) {
+  ck(cudaMemcpyAsync(P->hscal + slot, P->dscal + slot, sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
+  ck(cudaMemcpyAsync(P->herr, P->derr, sizeof(int), cudaMemcpyDeviceToHost, P->st), "d2h");
+  ck(cudaStreamSynchronize(P->st), "sync");
+  if (*P->herr & DEV_TAYLOR_KMAX) fail(STC_ERR_DIVERGED, "Taylor series exceeded taylor_kmax");
+  if (*P->herr & DEV_NONFINITE) fail(STC_ERR_DIVERGED, "non-finite value in a residual norm");
+  return P->hscal[slot];
+}
+
+double run_vcycle(stc_problem* P) {
+  if (!P->vgraph) {
+    cudaGraph_t graph = nullptr;
+    P->graph_launches = 0;
+    P->ev_used = 0;
+    P->counter = &P->graph_launches;
+    ck(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed), "begin capture");
+    try {
+      enqueue_top_vcycle(P, P->cap);
+    } catch (...) {
+      P->counter = nullptr;
+      cudaStreamEndCapture(P->cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    P->counter = nullptr;
+    ck(cudaStreamEndCapture(P->cap, &graph), "end capture");
+    cudaError_t e = cudaGraphInstantiate(&P->vgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    ck(e, "graph instantiate");
+  }
+  ck(cudaGraphLaunch(P->vgraph, P->st), "graph launch");
+  P->launches += P->graph_launches;
+  const double f = read_scalar(P, 0);
+  for (int k = 0; k < P->ev_used; ++k) {
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, P->ev_start[k], P->ev_stop[k]), "event time");
+    P->timed_ms += ms;
+    P->timed_launches += 1;
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// AO / KKT building blocks (finest level)
+// ---------------------------------------------------------------------------
+void metric_terms(stc_problem* P, const void* rho, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  ck(cudaMemsetAsync(P->mterm, 0, sizeof(double) * (size_t)(g.N + 1) * g.C, st), "memset");
+  for (size_t k = 0; k < P->key_steps.size(); ++k) {
+    const int s = P->key_steps[k];
+    dispatch(P->dbl, [&](auto tag) {
+      using T = decltype(tag);
+      launch_metric<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, P->key_c[k], P->prm.metric_levels,
+                       P->prm.metric_sigma0, P->mterm + (size_t)s * g.C, P->mtmp0, P->mtmp1, st);
+    });
+  }
+  count(P, (long long)P->key_steps.size() * (P->prm.metric_levels > 0 ? 1 + 4 * P->prm.metric_levels : 2));
+  check_launch("metric");
+}
+
+void forward(stc_problem* P, const void* vel, void* rho, int* K, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  const double thresh = P->prm.taylor_tol * P->rho_scale;
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    ck(launch_taylor_forward<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, st),
+       "taylor forward");
+  });
+  count(P, 1);
+}
+
+void adjoint(stc_problem* P, const void* vel, const void* rho, const int* K, const void* base, double alpha,
+             double beta, void* out, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    ck(launch_taylor_adjoint<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
+                                T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st),
+       "taylor adjoint");
+  });
+  count(P, 1);
+}
+
+void project(stc_problem* P, void* fields, int count, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st), "project");
+  });
+  if (count > 0) ::count(P, 1);
+}
+
+void prepare_targets(stc_problem* P, cudaStream_t st) {
+  Level& L0 = P->lv[0];
+  const Geom& g = L0.g;
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_axpby_faces<T>(g, g.N, (const T*)P->vstar, 1.0, (const T*)P->lam, -1.0 / P->prm.K, (T*)L0.z, st);
+  });
+  for (size_t l = 0; l + 1 < P->lv.size(); ++l) {
+    Level& F = P->lv[l];
+    Level& Cc = P->lv[l + 1];
+    dispatch(F.dbl, [&](auto tf) {
+      using Tf = decltype(tf);
+      dispatch(Cc.dbl, [&](auto tc) {
+        using Tc = decltype(tc);
+        launch_restrict_faces<Tf, Tc>(F.g, Cc.g, F.g.N, (const Tf*)F.z, (Tc*)Cc.z, st);
+      });
+    });
+    count(P, 1);
+  }
+  count(P, 1);
+  check_launch("targets");
+}
+
+void ao(stc_problem* P, int iters, cudaStream_t st) {
+  Level& L0 = P->lv[0];
+  const Geom& g = L0.g;
+  const size_t fb = (size_t)g.F * P->ts;
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_ao_init<T>(g, (const T*)L0.x.v, (const T*)P->lam, 1.0 / P->prm.K, (T*)P->w, (T*)P->vstar, st);
+  });
+  count(P, 1);
+  for (int it = 0; it < iters; ++it) {
+    forward(P, P->vstar, P->rho, P->K, st);
+    metric_terms(P, P->rho, st);
+    adjoint(P, P->vstar, P->rho, P->K, P->w, 1.0, 1.0 / P->prm.K, P->y, st);
+    if (g.N > 1) {
+      project(P, (char*)P->y + fb, g.N - 1, st);
+      ck(cudaMemcpyAsync((char*)P->vstar + fb, (char*)P->y + fb, fb * (g.N - 1), cudaMemcpyDeviceToDevice, st),
+         "copy v*");
+    }
+  }
+  prepare_targets(P, st);
+}
+
+// ||g(v)||^2 into dscal[1]
+void kkt(stc_problem* P, cudaStream_t st) {
+  Level& L0 = P->lv[0];
+  const Geom& g = L0.g;
+  forward(P, L0.x.v, P->rho_k, P->Kk, st);
+  metric_terms(P, P->rho_k, st);
+  adjoint(P, L0.x.v, P->rho_k, P->Kk, nullptr, 0.0, -1.0, P->dens, st);
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_kkt_force_rhs<T>(g, (const T*)L0.x.v, (T*)P->uk, st);
+  });
+  project(P, P->uk, g.N, st);
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_kkt_grad_rhs<T>(g, (const T*)L0.x.v, (const T*)P->uk, (const T*)P->dens, P->prm.r, (T*)P->gk, st);
+  });
+  project(P, (char*)P->gk + (size_t)g.F * P->ts, g.N, st);
+  ck(cudaMemsetAsync(P->dscal + 1, 0, sizeof(double), st), "memset");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_sumsq<T>((const T*)P->gk, (size_t)(g.N + 1) * g.F, P->dscal + 1, st);
+  });
+  count(P, 3);
+  check_launch("kkt");
+}
+
+template <class T>
+__global__ void lambda_update_kernel(size_t n, size_t skip, T* lam, const T* __restrict__ v, const T* __restrict__ vs,
+                                     double kb) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    if (e >= skip) lam[e] += T(kb) * (v[e] - vs[e]);
+}
+
+void admm_update(stc_problem* P, cudaStream_t st) {
+  Level& L0 = P->lv[0];
+  const Geom& g = L0.g;
+  ck(cudaMemsetAsync(P->dscal + 2, 0, sizeof(double), st), "memset");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_absdiff_max_copy<T>((const T*)P->rho, (T*)P->rho_last, (size_t)(g.N + 1) * g.C, P->dscal + 2, st);
+    const size_t n = (size_t)g.N * g.F;
+    unsigned nb = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    lambda_update_kernel<T><<<nb, 256, 0, st>>>(n, (size_t)g.F, (T*)P->lam, (const T*)L0.x.v, (const T*)P->vstar,
+                                                 P->prm.K * P->prm.beta);
+  });
+  count(P, 2);
+  check_launch("admm update");
+}
+
+void reset_state(stc_problem* P) {
+  for (Level& L : P->lv) {
+    const Geom& g = L.g;
+    const size_t s = esz(L.dbl);
+    FieldSet* sets[3] = {&L.x, &L.res, &L.tmp};
+    for (FieldSet* f : sets) {
+      ck(cudaMemsetAsync(f->v, 0, (size_t)(g.N + 1) * g.F * s, P->st), "memset");
+      ck(cudaMemsetAsync(f->pbar, 0, (size_t)(g.N + 1) * g.C * s, P->st), "memset");
+      ck(cudaMemsetAsync(f->u, 0, (size_t)g.N * g.F * s, P->st), "memset");
+      ck(cudaMemsetAsync(f->p, 0, (size_t)g.N * g.C * s, P->st), "memset");
+    }
+  }
+  const Geom& g = P->lv[0].g;
+  ck(cudaMemcpyAsync(P->lv[0].x.v, P->v0, (size_t)g.F * P->ts, cudaMemcpyDeviceToDevice, P->st), "v0");
+  ck(cudaMemsetAsync(P->lam, 0, (size_t)g.N * g.F * P->ts, P->st), "memset");
+}
+
+// ---------------------------------------------------------------------------
+// field access
+// ---------------------------------------------------------------------------
+struct FieldRef {
+  void* ptr = nullptr;
+  size_t count = 0;
+  int kind = 0;  // 0: level type, 1: fp64
+  bool dbl = false;
+};
+
+FieldRef field_ref(stc_problem* P, int field, int level) {
+  const int nl = (int)P->lv.size();
+  if (level < 0 || level >= nl) fail(STC_ERR_INVALID_ARG, "level out of range");
+  Level& L = P->lv[level];
+  const Geom& g = L.g;
+  const size_t N = g.N;
+  FieldRef r;
+  r.dbl = L.dbl;
+  auto set4 = [&](const FieldSet& f, int which) {
+    switch (which) {
+      case 0: r.ptr = f.v; r.count = (N + 1) * g.F; break;
+      case 1: r.ptr = f.pbar; r.count = (N + 1) * g.C; break;
+      case 2: r.ptr = f.u; r.count = N * g.F; break;
+      default: r.ptr = f.p; r.count = N * g.C; break;
+    }
+  };
+  if (field >= STC_FIELD_V && field <= STC_FIELD_P) {
+    set4(L.x, field - STC_FIELD_V);
+    return r;
+  }
+  if (field >= STC_FIELD_RES_V && field <= STC_FIELD_RES_P) {
+    set4(L.tmp, field - STC_FIELD_RES_V);
+    return r;
+  }
+  if (field >= STC_FIELD_RES_IN_V && field <= STC_FIELD_RES_IN_P) {
+    set4(L.res, field - STC_FIELD_RES_IN_V);
+    return r;
+  }
+  if (field >= STC_FIELD_XOLD_V && field <= STC_FIELD_XOLD_P) {
+    if (level == 0) fail(STC_ERR_INVALID_ARG, "XOLD exists on coarse levels only");
+    set4(L.old, field - STC_FIELD_XOLD_V);
+    return r;
+  }
+  if (field == STC_FIELD_Z) {
+    r.ptr = L.z;
+    r.count = N * g.F;
+    return r;
+  }
+  if (level != 0) fail(STC_ERR_INVALID_ARG, "field exists on the finest level only");
+  r.dbl = P->dbl;
+  switch (field) {
+    case STC_FIELD_VSTAR: r.ptr = P->vstar; r.count = N * g.F; break;
+    case STC_FIELD_LAMBDA: r.ptr = P->lam; r.count = N * g.F; break;
+    case STC_FIELD_RHO: r.ptr = P->rho; r.count = (N + 1) * g.C; break;
+    case STC_FIELD_MU: r.ptr = P->mu; r.count = N * g.C; break;
+    case STC_FIELD_W: r.ptr = P->w; r.count = N * g.F; break;
+    case STC_FIELD_Y: r.ptr = P->y; r.count = N * g.F; break;
+    case STC_FIELD_KKT_U: r.ptr = P->uk; r.count = N * g.F; break;
+    case STC_FIELD_KKT_G: r.ptr = P->gk; r.count = (N + 1) * g.F; break;
+    case STC_FIELD_MTERM: r.ptr = P->mterm; r.count = (N + 1) * g.C; r.kind = 1; break;
+    default: fail(STC_ERR_INVALID_ARG, "unknown field id");
+  }
+  return r;
+}
+
+void copy_out(stc_problem* P, const FieldRef& r, double* out) {
+  if (r.kind == 1 || r.dbl) {
+    ck(cudaMemcpyAsync(out, r.ptr, r.count * sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
+    ck(cudaStreamSynchronize(P->st), "sync");
+    return;
+  }
+  std::vector<float> tmp(r.count);
+  ck(cudaMemcpyAsync(tmp.data(), r.ptr, r.count * sizeof(float), cudaMemcpyDeviceToHost, P->st), "d2h");
+  ck(cudaStreamSynchronize(P->st), "sync");
+  for (size_t e = 0; e < r.count; ++e) out[e] = (double)tmp[e];
+}
+
+void copy_in(stc_problem* P, const FieldRef& r, const double* in) {
+  if (r.kind == 1 || r.dbl) {
+    ck(cudaMemcpyAsync(r.ptr, in, r.count * sizeof(double), cudaMemcpyHostToDevice, P->st), "h2d");
+    ck(cudaStreamSynchronize(P->st), "sync");
+    return;
+  }
+  std::vector<float> tmp(r.count);
+  for (size_t e = 0; e < r.count; ++e) tmp[e] = (float)in[e];
+  ck(cudaMemcpyAsync(r.ptr, tmp.data(), r.count * sizeof(float), cudaMemcpyHostToDevice, P->st), "h2d");
+  ck(cudaStreamSynchronize(P->st), "sync");
+}
+
+template <class F>
+stc_status guarded(stc_problem* P, F&& f) {
+  if (P && P->broken) {
+    g_last_error = "problem is unusable after an earlier CUDA error";
+    return STC_ERR_CUDA;
+  }
+  try {
+    f();
+    return STC_OK;
+  } catch (const StcError& e) {
+    g_last_error = e.msg;
+    if (P && e.code == STC_ERR_CUDA) P->broken = true;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return STC_ERR_OOM;
+  } catch (...) {
+    g_last_error = "unexpected error";
+    return STC_ERR_CUDA;
+  }
+}
+
+void free_problem(stc_problem* P) {
+  if (!P) return;
+  if (P->vgraph) cudaGraphExecDestroy(P->vgraph);
+  for (cudaEvent_t e : P->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->ev_stop) cudaEventDestroy(e);
+  for (void* p : P->allocs) cudaFree(p);
+  if (P->hscal) cudaFreeHost(P->hscal);
+  if (P->herr) cudaFreeHost(P->herr);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  delete P;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx;
+  p->ny = ny;
+  p->num_steps = num_steps;
+  p->dt = num_steps > 0 ? 1.0 / num_steps : 0.0;
+  p->r = 1e-3;
+  p->K = 1.0;
+  p->beta = 1.0;
+  p->precision = 0;
+  p->ao_iters = 2;
+  p->pre = 2;
+  p->post = 2;
+  p->coarse_sweeps = 10;
+  p->coarsest_n = 4;
+  p->taylor_tol = 1e-5;
+  p->taylor_kmax = 64;
+  p->eps_stfas = 1e-5;
+  p->eps_admm = -1.0;
+  p->max_vcycles = 20;
+  p->metric_levels = 0;
+  p->metric_sigma0 = 1.0;
+  p->scgs_omega = 0.8;
+  p->lm_shift = -1.0;
+  p->poisson_vcycles = 8;
+  p->self_advection = 1;
+}
+
+const char* stc_last_error(void) { return g_last_error.c_str(); }
+
+stc_status stc_create_problem(const stc_params* params, const double* rho0, const double* v0, void* cuda_stream,
+                              stc_problem** out) {
+  if (!params || !rho0 || !out) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const stc_params& prm = *params;
+  if (prm.nx < 2 || prm.ny < 2 || prm.num_steps < 1 || !(prm.dt > 0) || !(prm.r > 0) || !(prm.K > 0) ||
+      prm.precision < 0 || prm.precision > 1 || prm.ao_iters < 0 || prm.pre < 0 || prm.post < 0 ||
+      prm.coarse_sweeps < 0 || prm.coarsest_n < 2 || !(prm.taylor_tol > 0) || prm.taylor_kmax < 1 ||
+      prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
+      !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1) {
+    g_last_error = "invalid parameters";
+    return STC_ERR_INVALID_ARG;
+  }
+  stc_problem* P = new (std::nothrow) stc_problem();
+  if (!P) {
+    g_last_error = "host allocation failed";
+    return STC_ERR_OOM;
+  }
+  P->prm = prm;
+  P->st = (cudaStream_t)cuda_stream;
+  P->dbl = prm.precision == 1;
+  P->ts = P->dbl ? 8 : 4;
+  stc_status s = guarded(nullptr, [&]() {
+    // hierarchy: halve while both even and the halves stay >= coarsest_n (space only, Sec. 4.2)
+    int nx = prm.nx, ny = prm.ny;
+    double h = 1.0 / prm.nx;
+    std::vector<Geom> geoms;
+    geoms.push_back(make_geom(prm, nx, ny, h));
+    while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
+      nx /= 2;
+      ny /= 2;
+      h *= 2.0;
+      geoms.push_back(make_geom(prm, nx, ny, h));
+    }
+    const Geom& g0 = geoms[0];
+    if (!advect_supported(g0)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip advection sweep");
+    if (!project_supported(g0, P->ts)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip projection");
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "get device");
+    int smem_optin = 0;
+    ck(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
+    if ((int)advect_smem_adjoint(g0, P->ts) > smem_optin || (int)project_smem(g0, P->ts) > smem_optin)
+      fail(STC_ERR_UNSUPPORTED, "shared memory of this device too small for the grid");
+    ck(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "stream");
+    const int N = prm.num_steps;
+    for (size_t l = 0; l < geoms.size(); ++l) {
+      Level L;
+      L.g = geoms[l];
+      L.dbl = P->dbl || (l > 0 && l == geoms.size() - 1);   // fp64 coarsest level (precision policy)
+      alloc_fieldset(P, L.x, L.g, L.dbl);
+      alloc_fieldset(P, L.res, L.g, L.dbl);
+      alloc_fieldset(P, L.tmp, L.g, L.dbl);
+      if (l > 0) alloc_fieldset(P, L.old, L.g, L.dbl);
+      L.z = dalloc(P, (size_t)N * L.g.F * esz(L.dbl));
+      int maxcell = 0;
+      for (int c = 0; c < 4; ++c)
+        maxcell = std::max(maxcell, colour_extent(L.g.nx, c & 1) * colour_extent(L.g.ny, c >> 1));
+      L.scratch = dalloc(P, (size_t)maxcell * 2 * N * 25 * esz(L.dbl));
+      P->lv.push_back(L);
+    }
+    const size_t F = g0.F, C = g0.C, ts = P->ts;
+    P->rho = dalloc(P, (N + 1) * C * ts);
+    P->rho_k = dalloc(P, (N + 1) * C * ts);
+    P->rho_last = dalloc(P, (N + 1) * C * ts);
+    P->mu = dalloc(P, N * C * ts);
+    P->vstar = dalloc(P, N * F * ts);
+    P->lam = dalloc(P, N * F * ts);
+    P->w = dalloc(P, N * F * ts);
+    P->y = dalloc(P, N * F * ts);
+    P->uk = dalloc(P, N * F * ts);
+    P->gk = dalloc(P, (N + 1) * F * ts);
+    P->dens = dalloc(P, (N + 1) * F * ts);
+    P->powers = dalloc(P, (size_t)prm.taylor_kmax * C * ts);
+    P->v0 = dalloc(P, F * ts);
+    P->K = (int*)dalloc(P, N * sizeof(int));
+    P->Kk = (int*)dalloc(P, N * sizeof(int));
+    P->mterm = (double*)dalloc(P, (N + 1) * C * sizeof(double));
+    P->mtmp0 = (double*)dalloc(P, C * sizeof(double));
+    P->mtmp1 = (double*)dalloc(P, 2 * C * sizeof(double));
+    P->dscal = (double*)dalloc(P, 16 * sizeof(double));
+    P->derr = (int*)dalloc(P, sizeof(int));
+    ck(cudaMallocHost(&P->hscal, 16 * sizeof(double)), "pinned");
+    ck(cudaMallocHost(&P->herr, sizeof(int)), "pinned");
+    // inputs: rho_0 into rho[0] of every density buffer, v_0
+    double mx = 0.0;
+    for (size_t e = 0; e < C; ++e) mx = std::max(mx, std::fabs(rho0[e]));
+    if (!(mx > 0.0)) fail(STC_ERR_INVALID_ARG, "rho0 must have a nonzero entry");
+    P->rho_scale = mx;
+    FieldRef r;
+    r.count = C;
+    r.dbl = P->dbl;
+    r.ptr = P->rho;
+    copy_in(P, r, rho0);
+    r.ptr = P->rho_k;
+    copy_in(P, r, rho0);
+    r.ptr = P->rho_last;
+    copy_in(P, r, rho0);
+    if (v0) {
+      std::vector<double> vv(v0, v0 + F);
+      // wall faces are not unknowns: keep them zero
+      for (int j = 0; j < g0.ny; ++j) {
+        vv[(size_t)j * (g0.nx + 1)] = 0.0;
+        vv[(size_t)j * (g0.nx + 1) + g0.nx] = 0.0;
+      }
+      for (int i = 0; i < g0.nx; ++i) {
+        vv[g0.Fx + i] = 0.0;
+        vv[g0.Fx + (size_t)g0.ny * g0.nx + i] = 0.0;
+      }
+      FieldRef rv;
+      rv.count = F;
+      rv.dbl = P->dbl;
+      rv.ptr = P->v0;
+      copy_in(P, rv, vv.data());
+    }
+    reset_state(P);
+    ck(cudaStreamSynchronize(P->st), "sync");
+  });
+  if (s != STC_OK) {
+    free_problem(P);
+    return s;
+  }
+  *out = P;
+  return STC_OK;
+}
+
+stc_status stc_destroy_problem(stc_problem* p) {
+  if (!p) return STC_OK;
+  if (p->st) cudaStreamSynchronize(p->st);
+  else cudaDeviceSynchronize();
+  free_problem(p);
+  return STC_OK;
+}
+
+stc_status stc_set_keyframes(stc_problem* p, int count, const int* steps, const double* rho_star, const double* c) {
+  if (!p || count < 0 || (count > 0 && (!steps || !rho_star))) {
+    g_last_error = "invalid keyframe arguments";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    const Geom& g = p->lv[0].g;
+    for (int k = 0; k < count; ++k)
+      if (steps[k] < 1 || steps[k] > g.N) fail(STC_ERR_INVALID_ARG, "keyframe step outside 1..N");
+    for (int a = 0; a < count; ++a)
+      for (int b = a + 1; b < count; ++b)
+        if (steps[a] == steps[b]) fail(STC_ERR_INVALID_ARG, "duplicate keyframe step");
+    if (p->star) {
+      cudaFree(p->star);
+      for (auto& q : p->allocs)
+        if (q == p->star) q = nullptr;
+      p->star = nullptr;
+    }
+    p->key_steps.assign(steps, steps + count);
+    p->key_c.assign(count, 1.0);
+    if (c)
+      for (int k = 0; k < count; ++k) p->key_c[k] = c[k];
+    if (count > 0) {
+      p->star = (double*)dalloc(p, (size_t)count * g.C * sizeof(double));
+      ck(cudaMemcpyAsync(p->star, rho_star, (size_t)count * g.C * sizeof(double), cudaMemcpyHostToDevice, p->st),
+         "h2d");
+      ck(cudaStreamSynchronize(p->st), "sync");
+    }
+  });
+}
+
+stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf) {
+  if (!p || ncycles < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    double f = 0.0;
+    for (int c = 0; c < ncycles; ++c) f = run_vcycle(p);
+    if (ncycles == 0) {
+      residual_norm(p, 0, 0, p->st);
+      f = read_scalar(p, 0);
+    }
+    if (nso_res_inf) *nso_res_inf = f;
+  });
+}
+
+stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_report* report) {
+  if (!p || max_admm < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  stc_report rep;
+  std::memset(&rep, 0, sizeof(rep));
+  rep.seconds_to_1e4 = -1.0;
+  bool converged = false;
+  stc_status s = guarded(p, [&]() {
+    auto t0 = std::chrono::steady_clock::now();
+    const stc_params& prm = p->prm;
+    reset_state(p);
+    const Geom& g = p->lv[0].g;
+    const double eps_admm = prm.eps_admm < 0 ? p->rho_scale / 100.0 : prm.eps_admm;
+    // rho^last = uncontrolled densities; KKT denominator at the start
+    kkt(p, p->st);
+    const double g0 = std::sqrt(read_scalar(p, 1));
+    ck(cudaMemcpyAsync(p->rho_last, p->rho_k, (size_t)(g.N + 1) * g.C * p->ts, cudaMemcpyDeviceToDevice, p->st),
+       "copy");
+    p->fscale = -1.0;
+    for (int it = 0; it < max_admm; ++it) {
+      ao(p, prm.ao_iters, p->st);
+      residual_norm(p, 0, 0, p->st);
+      double f = read_scalar(p, 0);
+      if (p->fscale < 0) p->fscale = f;
+      int cycles = 0;
+      while (f > prm.eps_stfas * p->fscale && cycles < prm.max_vcycles) {
+        f = run_vcycle(p);
+        ++cycles;
+      }
+      kkt(p, p->st);
+      const double gn = std::sqrt(read_scalar(p, 1));
+      admm_update(p, p->st);   // drho test + lambda update (lambda unused if we stop)
+      const double drho = read_scalar(p, 2);
+      rep.admm_iters = it + 1;
+      rep.vcycles += cycles;
+      rep.kkt_abs = gn;
+      rep.kkt_rel = g0 > 0 ? gn / g0 : 0.0;
+      rep.f_inf = f;
+      rep.drho = drho;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (rep.kkt_rel <= 1e-4 && rep.seconds_to_1e4 < 0) rep.seconds_to_1e4 = el;
+      if (rep.kkt_rel <= kkt_rel_tol || drho < eps_admm) {
+        converged = rep.kkt_rel <= kkt_rel_tol || drho < eps_admm;
+        break;
+      }
+    }
+    ck(cudaStreamSynchronize(p->st), "sync");
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (report) *report = rep;
+  if (s != STC_OK) return s;
+  if (!converged) {
+    g_last_error = "ADMM iteration cap reached";
+    return STC_ERR_NOT_CONVERGED;
+  }
+  return STC_OK;
+}
+
+stc_status stc_get_forces(const stc_problem* p, double* u, size_t len) {
+  return stc_get_field(p, STC_FIELD_U, 0, u, len);
+}
+stc_status stc_get_density(const stc_problem* p, double* rho, size_t len) {
+  return stc_get_field(p, STC_FIELD_RHO, 0, rho, len);
+}
+stc_status stc_get_velocity(const stc_problem* p, double* v, size_t len) {
+  return stc_get_field(p, STC_FIELD_V, 0, v, len);
+}
+
+stc_status stc_get_field(const stc_problem* cp, int field, int level, double* out, size_t len) {
+  stc_problem* p = const_cast<stc_problem*>(cp);
+  if (!p || !out) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    FieldRef r = field_ref(p, field, level);
+    if (len != r.count) fail(STC_ERR_INVALID_ARG, "length does not match the field size");
+    copy_out(p, r, out);
+  });
+}
+
+stc_status stc_set_field(stc_problem* p, int field, int level, const double* in, size_t len) {
+  if (!p || !in) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    FieldRef r = field_ref(p, field, level);
+    if (len != r.count) fail(STC_ERR_INVALID_ARG, "length does not match the field size");
+    copy_in(p, r, in);
+  });
+}
+
+stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx, int* ny) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (nlevels) *nlevels = (int)p->lv.size();
+  if (level < 0 || level >= (int)p->lv.size()) {
+    g_last_error = "level out of range";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (nx) *nx = p->lv[level].g.nx;
+  if (ny) *ny = p->lv[level].g.ny;
+  return STC_OK;
+}
+
+stc_status stc_advect(stc_problem* p, int source_field) {
+  if (!p || (source_field != STC_FIELD_VSTAR && source_field != STC_FIELD_V)) {
+    g_last_error = "source must be STC_FIELD_VSTAR or STC_FIELD_V";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    const void* vel = source_field == STC_FIELD_V ? p->lv[0].x.v : p->vstar;
+    forward(p, vel, p->rho, p->K, p->st);
+    read_scalar(p, 0);   // synchronise and surface device errors
+  });
+}
+
+stc_status stc_get_taylor_orders(const stc_problem* p, int* K, size_t len) {
+  if (!p || !K || len != (size_t)p->lv[0].g.N) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  stc_problem* q = const_cast<stc_problem*>(p);
+  return guarded(q, [&]() {
+    ck(cudaMemcpyAsync(K, q->K, len * sizeof(int), cudaMemcpyDeviceToHost, q->st), "d2h");
+    ck(cudaStreamSynchronize(q->st), "sync");
+  });
+}
+
+stc_status stc_metric_terms(stc_problem* p) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    metric_terms(p, p->rho, p->st);
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_adjoint(stc_problem* p, int source_field, double alpha, double beta) {
+  if (!p || (source_field != STC_FIELD_VSTAR && source_field != STC_FIELD_V)) {
+    g_last_error = "source must be STC_FIELD_VSTAR or STC_FIELD_V";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    const void* vel = source_field == STC_FIELD_V ? p->lv[0].x.v : p->vstar;
+    adjoint(p, vel, p->rho, p->K, p->w, alpha, beta, p->y, p->st);
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_project(stc_problem* p, int field, int first, int count) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    if (field != STC_FIELD_V && field != STC_FIELD_U && field != STC_FIELD_VSTAR && field != STC_FIELD_Y &&
+        field != STC_FIELD_W && field != STC_FIELD_KKT_U && field != STC_FIELD_KKT_G && field != STC_FIELD_Z)
+      fail(STC_ERR_INVALID_ARG, "not a face field");
+    FieldRef r = field_ref(p, field, 0);
+    const Geom& g = p->lv[0].g;
+    const size_t slabs = r.count / g.F;
+    if (first < 0 || count < 0 || (size_t)first + (size_t)count > slabs)
+      fail(STC_ERR_INVALID_ARG, "slab range outside the field");
+    project(p, (char*)r.ptr + (size_t)first * g.F * p->ts, count, p->st);
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_ao(stc_problem* p, int iters) {
+  if (!p || iters < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    ao(p, iters, p->st);
+    read_scalar(p, 0);
+  });
+}
+
+stc_status stc_prepare_targets(stc_problem* p) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    prepare_targets(p, p->st);
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_nso_residual(stc_problem* p, int level, double* inf) {
+  if (!p || level < 0 || level >= (int)p->lv.size()) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    residual_norm(p, level, 3, p->st);
+    const double v = read_scalar(p, 3);
+    if (inf) *inf = v;
+  });
+}
+
+stc_status stc_smooth(stc_problem* p, int level, int sweeps) {
+  if (!p || level < 0 || level >= (int)p->lv.size() || sweeps < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    smooth(p, level, sweeps, p->st);
+    check_launch("smooth");
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_restrict(stc_problem* p, int level) {
+  if (!p || level < 0 || level + 1 >= (int)p->lv.size()) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    restrict_level(p, level, p->st);
+    check_launch("restrict");
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_prolong_correct(stc_problem* p, int level) {
+  if (!p || level < 0 || level + 1 >= (int)p->lv.size()) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    prolong_level(p, level, p->st);
+    check_launch("prolong");
+    ck(cudaStreamSynchronize(p->st), "sync");
+  });
+}
+
+stc_status stc_kkt_residual(stc_problem* p, double* norm) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    kkt(p, p->st);
+    const double v = read_scalar(p, 1);
+    if (norm) *norm = std::sqrt(v);
+  });
+}
+
+stc_status stc_admm_update(stc_problem* p, double* drho) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    admm_update(p, p->st);
+    const double v = read_scalar(p, 2);
+    if (drho) *drho = v;
+  });
+}
+
+stc_status stc_launch_count(const stc_problem* p, long long* launches) {
+  if (!p || !launches) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  *launches = p->launches;
+  return STC_OK;
+}
+
+stc_status stc_set_kernel_timing(stc_problem* p, int enable) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    if (p->vgraph) {
+      ck(cudaGraphExecDestroy(p->vgraph), "graph destroy");
+      p->vgraph = nullptr;
+    }
+    p->timing = enable != 0;
+    p->timed_ms = 0.0;
+    p->timed_launches = 0;
+    const size_t need = p->lv.size() > 1 ? (size_t)4 * (p->prm.pre + p->prm.post) : (size_t)4 * p->prm.coarse_sweeps;
+    while (p->timing && p->ev_start.size() < need) {
+      cudaEvent_t a, b;
+      ck(cudaEventCreate(&a), "event");
+      ck(cudaEventCreate(&b), "event");
+      p->ev_start.push_back(a);
+      p->ev_stop.push_back(b);
+    }
+  });
+}
+
+stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* launches) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (total_ms) *total_ms = p->timed_ms;
+  if (launches) *launches = p->timed_launches;
+  return STC_OK;
+}
+
+stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes) {
+  if (!p || !bytes) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  *bytes = p->bytes;
+  return STC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Internal definitions shared by the CUDA translation units of libstc.
+//
+// Discretisation (Sec. 3.1 of Pan & Manocha, "Efficient Optimal Control of
+// Smoke using Spacetime Multigrid"): 2D staggered MAC grid, nx x ny cells of
+// size h.  Centre fields (rho, p, pbar, mu) are [ny][nx] (i fastest).  A face
+// field stores all x-faces [ny][nx+1] then all y-faces [ny+1][nx]; wall faces
+// are stored and always hold 0 (closed box).  Time-dependent fields are slabs
+// of one such array per timestep.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stc {
+
+// Geometry and scalar parameters of one level, passed to kernels by value.
+struct Geom {
+  int nx, ny;        // cells
+  int N;             // timesteps
+  int Fx, F, C;      // x-face count, face count, cell count
+  double h, ih;      // cell size and 1/h
+  double dt, idt;    // timestep and 1/dt
+  double a;          // K / r   (Eq. KKTAO row 1)
+  double lm;         // Levenberg-Marquardt shift of the smoother's v blocks
+  double omega;      // SCGS under-relaxation
+  int self_adv;      // 1: Adv on (0 only for linear saddle tests)
+};
+
+// NSO unknowns of one level: v (N+1)F, pbar (N+1)C, u N F, p N C  (p[i] = p_{i+1}).
+template <class T>
+struct State {
+  T* v;
+  T* pbar;
+  T* u;
+  T* p;
+};
+
+template <class T>
+struct CState {
+  const T* v;
+  const T* pbar;
+  const T* u;
+  const T* p;
+};
+
+template <class T>
+__host__ __device__ inline CState<T> cs(const State<T>& s) {
+  return CState<T>{s.v, s.pbar, s.u, s.p};
+}
+
+// ---------------------------------------------------------------------------
+// index helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int xf(const Geom& g, int j, int i) { return j * (g.nx + 1) + i; }
+__host__ __device__ inline int yf(const Geom& g, int j, int i) { return g.Fx + j * g.nx + i; }
+__host__ __device__ inline int cidx(const Geom& g, int j, int i) { return j * g.nx + i; }
+
+template <class T>
+__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// Self-advection Adv[v] = (curl v) x v  (Eq. NSA) and its Jacobian transpose.
+// omega at node (j,i) = (vy(j,i)-vy(j,i-1))/h - (vx(j,i)-vx(j-1,i))/h, zero on
+// wall nodes; Adv_x = -omega_bar * vbar_y, Adv_y = +omega_bar * vbar_x with
+// omega_bar the mean of a face's two nodes and vbar the mean of the four
+// surrounding transverse faces; Adv = 0 on wall faces.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T node_omega(const Geom& g, const T* v, int j, int i) {
+  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return T(0);
+  T a = ld(v + yf(g, j, i)) - ld(v + yf(g, j, i - 1));
+  T b = ld(v + xf(g, j, i)) - ld(v + xf(g, j - 1, i));
+  return (a - b) * T(g.ih);
+}
+
+// transverse mean at an interior x-face (j,i)
+template <class T>
+__device__ __forceinline__ T tv_x(const Geom& g, const T* v, int j, int i) {
+  return T(0.25) * (ld(v + yf(g, j, i - 1)) + ld(v + yf(g, j, i)) + ld(v + yf(g, j + 1, i - 1)) +
+                    ld(v + yf(g, j + 1, i)));
+}
+
+// transverse mean at an interior y-face (j,i)
+template <class T>
+__device__ __forceinline__ T tv_y(const Geom& g, const T* v, int j, int i) {
+  return T(0.25) * (ld(v + xf(g, j - 1, i)) + ld(v + xf(g, j - 1, i + 1)) + ld(v + xf(g, j, i)) +
+                    ld(v + xf(g, j, i + 1)));
+}
+
+template <class T>
+__device__ __forceinline__ T wbar_x(const Geom& g, const T* v, int j, int i) {
+  return T(0.5) * (node_omega(g, v, j, i) + node_omega(g, v, j + 1, i));
+}
+
+template <class T>
+__device__ __forceinline__ T wbar_y(const Geom& g, const T* v, int j, int i) {
+  return T(0.5) * (node_omega(g, v, j, i) + node_omega(g, v, j, i + 1));
+}
+
+__device__ __forceinline__ bool xf_interior(const Geom& g, int j, int i) {
+  return i >= 1 && i <= g.nx - 1 && j >= 0 && j < g.ny;
+}
+__device__ __forceinline__ bool yf_interior(const Geom& g, int j, int i) {
+  return j >= 1 && j <= g.ny - 1 && i >= 0 && i < g.nx;
+}
+
+template <class T>
+__device__ __forceinline__ T adv_x(const Geom& g, const T* v, int j, int i) {
+  if (!xf_interior(g, j, i)) return T(0);
+  return -wbar_x(g, v, j, i) * tv_x(g, v, j, i);
+}
+
+template <class T>
+__device__ __forceinline__ T adv_y(const Geom& g, const T* v, int j, int i) {
+  if (!yf_interior(g, j, i)) return T(0);
+  return wbar_y(g, v, j, i) * tv_y(g, v, j, i);
+}
+
+// P_e = s_e * vbar_e * u_e on interior faces (s = -1 on x-faces, +1 on y-faces)
+template <class T>
+__device__ __forceinline__ T pe_x(const Geom& g, const T* v, const T* u, int j, int i) {
+  if (!xf_interior(g, j, i)) return T(0);
+  return -tv_x(g, v, j, i) * ld(u + xf(g, j, i));
+}
+template <class T>
+__device__ __forceinline__ T pe_y(const Geom& g, const T* v, const T* u, int j, int i) {
+  if (!yf_interior(g, j, i)) return T(0);
+  return tv_y(g, v, j, i) * ld(u + yf(g, j, i));
+}
+
+// Q_n = 1/2 sum of P_e over the interior faces meeting at interior node n
+template <class T>
+__device__ __forceinline__ T node_q(const Geom& g, const T* v, const T* u, int j, int i) {
+  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return T(0);
+  return T(0.5) * (pe_x(g, v, u, j - 1, i) + pe_x(g, v, u, j, i) + pe_y(g, v, u, j, i - 1) +
+                   pe_y(g, v, u, j, i));
+}
+
+// (dAdv/dv)^T u at interior x-face (j,i): the node terms through omega plus the
+// transverse-mean terms through vbar of the four y-faces averaging this face.
+template <class T>
+__device__ T jtu_x(const Geom& g, const T* v, const T* u, int j, int i) {
+  T r = (node_q(g, v, u, j + 1, i) - node_q(g, v, u, j, i)) * T(g.ih);
+  T s = T(0);
+  if (yf_interior(g, j, i - 1)) s += wbar_y(g, v, j, i - 1) * ld(u + yf(g, j, i - 1));
+  if (yf_interior(g, j, i)) s += wbar_y(g, v, j, i) * ld(u + yf(g, j, i));
+  if (yf_interior(g, j + 1, i - 1)) s += wbar_y(g, v, j + 1, i - 1) * ld(u + yf(g, j + 1, i - 1));
+  if (yf_interior(g, j + 1, i)) s += wbar_y(g, v, j + 1, i) * ld(u + yf(g, j + 1, i));
+  return r + T(0.25) * s;
+}
+
+template <class T>
+__device__ T jtu_y(const Geom& g, const T* v, const T* u, int j, int i) {
+  T r = (node_q(g, v, u, j, i) - node_q(g, v, u, j, i + 1)) * T(g.ih);
+  T s = T(0);
+  if (xf_interior(g, j - 1, i)) s -= wbar_x(g, v, j - 1, i) * ld(u + xf(g, j - 1, i));
+  if (xf_interior(g, j - 1, i + 1)) s -= wbar_x(g, v, j - 1, i + 1) * ld(u + xf(g, j - 1, i + 1));
+  if (xf_interior(g, j, i)) s -= wbar_x(g, v, j, i) * ld(u + xf(g, j, i));
+  if (xf_interior(g, j, i + 1)) s -= wbar_x(g, v, j, i + 1) * ld(u + xf(g, j, i + 1));
+  return r + T(0.25) * s;
+}
+
+// gradient of a centre field at a face (zero on walls)
+template <class T>
+__device__ __forceinline__ T grad_x(const Geom& g, const T* p, int j, int i) {
+  if (!xf_interior(g, j, i)) return T(0);
+  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j, i - 1))) * T(g.ih);
+}
+template <class T>
+__device__ __forceinline__ T grad_y(const Geom& g, const T* p, int j, int i) {
+  if (!yf_interior(g, j, i)) return T(0);
+  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j - 1, i))) * T(g.ih);
+}
+
+template <class T>
+__device__ __forceinline__ T divergence(const Geom& g, const T* v, int j, int i) {
+  return (ld(v + xf(g, j, i + 1)) - ld(v + xf(g, j, i)) + ld(v + yf(g, j + 1, i)) -
+          ld(v + yf(g, j, i))) * T(g.ih);
+}
+
+// ---------------------------------------------------------------------------
+// error flags written by kernels (host maps them to stc_status)
+// ---------------------------------------------------------------------------
+enum DevError : int {
+  DEV_OK = 0,
+  DEV_TAYLOR_KMAX = 1,   // Taylor series did not reach tolerance within kmax
+  DEV_NONFINITE = 2,     // a non-finite value reached a norm
+  DEV_BAD_LAUNCH = 4,    // launch shape inconsistent with the data (bounds guard)
+};
+
+}  // namespace stc

@@ -1,0 +1,75 @@
+// Launchers of the CUDA kernels of libstc (host-callable, internal).
+#pragma once
+
+#include "stc_internal.cuh"
+
+namespace stc {
+
+// --- NSO (nso_kernels.cu) ---------------------------------------------------
+template <class T>
+void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                         cudaStream_t st);
+template <class T>
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, T* scratch, cudaStream_t st);
+int colour_extent(int n, int parity);
+template <class Tf, class Tc>
+void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
+template <class Tf, class Tc>
+void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st);
+template <class Tf, class Tc>
+void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
+                            cudaStream_t st);
+template <class T>
+void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st);
+template <class T>
+void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st);
+template <class T>
+void launch_remove_mean(T* a, int count, int C, cudaStream_t st);
+template <class Ts, class Td>
+void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st);
+
+// --- advection (advect_kernels.cu) ------------------------------------------
+constexpr int kClusterCTAs = 8;
+constexpr int kAdvThreads = 512;
+constexpr int kAdvMaxCellsPerThread = 8;
+
+// rho[0] given; writes rho[1..N] and K[0..N-1] (Taylor orders).  vel: N face slabs.
+template <class T>
+cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, double thresh, int kmax, int* err,
+                                  cudaStream_t st);
+// Backward adjoint sweep (Eq. KKTPO): mu_{s-1} = T_s^T mu_s - m_s, mu_{N-1} = -m_N;
+// out_s = alpha * base_s + beta * (dA[rho_s, v_s]/dv)^T mu_s for s = 1..N-1.
+template <class T>
+cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
+                                  T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
+                                  cudaStream_t st);
+// m_s = c * sum_l G_l^T G_l (rho_s - rho*_s) (fp64) into mterm slab s.
+template <class T>
+void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
+                   double* out, double* tmp0, double* tmp1, cudaStream_t st);
+size_t advect_smem_forward(const Geom& g, size_t tsize);
+size_t advect_smem_adjoint(const Geom& g, size_t tsize);
+bool advect_supported(const Geom& g);
+
+// --- projection and elementwise helpers (poisson_kernels.cu) ---------------
+// In-place solenoidal projection of `count` face fields (stride F): Q v = v - G phi
+// with (D G) phi = D v solved by an on-chip multigrid V(2,2) cycle.
+template <class T>
+cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st);
+size_t project_smem(const Geom& g, size_t tsize);
+bool project_supported(const Geom& g, size_t tsize);
+
+template <class T>
+void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, cudaStream_t st);
+template <class T>
+void launch_axpby_faces(const Geom& g, int count, const T* a, double alpha, const T* b, double beta, T* out,
+                        cudaStream_t st);
+template <class T>
+void launch_kkt_force_rhs(const Geom& g, const T* v, T* out, cudaStream_t st);
+template <class T>
+void launch_kkt_grad_rhs(const Geom& g, const T* v, const T* u, const T* dens, double r, T* out,
+                         cudaStream_t st);
+template <class T>
+void launch_absdiff_max_copy(const T* a, T* b, size_t n, double* out, cudaStream_t st);
+
+}  // namespace stc

@@ -1,0 +1,294 @@
+"""Thin Python binding of libstc (include/stc.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays to the C ABI's fp64 host buffers and back.  It raises if libstc.so is
+missing -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstc.so")
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+P_double = ctypes.POINTER(ctypes.c_double)
+P_int = ctypes.POINTER(ctypes.c_int)
+
+FIELDS = dict(V=0, PBAR=1, U=2, P=3, RES_V=4, RES_PBAR=5, RES_U=6, RES_P=7, Z=8, VSTAR=9, LAMBDA=10,
+              RHO=11, MU=12, W=13, Y=14, KKT_U=15, KKT_G=16, MTERM=17, RES_IN_V=18, RES_IN_PBAR=19,
+              RES_IN_U=20, RES_IN_P=21, XOLD_V=22, XOLD_PBAR=23, XOLD_U=24, XOLD_P=25)
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
+          6: "UNSUPPORTED"}
+
+
+class StcParams(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("num_steps", c_int), ("dt", c_double), ("r", c_double),
+                ("K", c_double), ("beta", c_double), ("precision", c_int), ("ao_iters", c_int),
+                ("pre", c_int), ("post", c_int), ("coarse_sweeps", c_int), ("coarsest_n", c_int),
+                ("taylor_tol", c_double), ("taylor_kmax", c_int), ("eps_stfas", c_double),
+                ("eps_admm", c_double), ("max_vcycles", c_int), ("metric_levels", c_int),
+                ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
+                ("poisson_vcycles", c_int), ("self_advection", c_int)]
+
+
+class StcReport(ctypes.Structure):
+    _fields_ = [("admm_iters", c_int), ("vcycles", c_int), ("kkt_rel", c_double), ("kkt_abs", c_double),
+                ("f_inf", c_double), ("drho", c_double), ("seconds", c_double),
+                ("seconds_to_1e4", c_double)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "stc_default_params": (None, [ctypes.POINTER(StcParams), c_int, c_int, c_int]),
+    "stc_create_problem": (c_int, [ctypes.POINTER(StcParams), P_double, P_double, c_void_p,
+                                   ctypes.POINTER(c_void_p)]),
+    "stc_set_keyframes": (c_int, [c_void_p, c_int, P_int, P_double, P_double]),
+    "stc_vcycle": (c_int, [c_void_p, c_int, P_double]),
+    "stc_solve": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(StcReport)]),
+    "stc_get_forces": (c_int, [c_void_p, P_double, c_size_t]),
+    "stc_get_density": (c_int, [c_void_p, P_double, c_size_t]),
+    "stc_get_velocity": (c_int, [c_void_p, P_double, c_size_t]),
+    "stc_destroy_problem": (c_int, [c_void_p]),
+    "stc_last_error": (ctypes.c_char_p, []),
+    "stc_get_field": (c_int, [c_void_p, c_int, c_int, P_double, c_size_t]),
+    "stc_set_field": (c_int, [c_void_p, c_int, c_int, P_double, c_size_t]),
+    "stc_level_info": (c_int, [c_void_p, P_int, c_int, P_int, P_int]),
+    "stc_advect": (c_int, [c_void_p, c_int]),
+    "stc_get_taylor_orders": (c_int, [c_void_p, P_int, c_size_t]),
+    "stc_metric_terms": (c_int, [c_void_p]),
+    "stc_adjoint": (c_int, [c_void_p, c_int, c_double, c_double]),
+    "stc_project": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "stc_ao": (c_int, [c_void_p, c_int]),
+    "stc_prepare_targets": (c_int, [c_void_p]),
+    "stc_nso_residual": (c_int, [c_void_p, c_int, P_double]),
+    "stc_smooth": (c_int, [c_void_p, c_int, c_int]),
+    "stc_restrict": (c_int, [c_void_p, c_int]),
+    "stc_prolong_correct": (c_int, [c_void_p, c_int]),
+    "stc_kkt_residual": (c_int, [c_void_p, P_double]),
+    "stc_admm_update": (c_int, [c_void_p, P_double]),
+    "stc_launch_count": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "stc_set_kernel_timing": (c_int, [c_void_p, c_int]),
+    "stc_kernel_timing": (c_int, [c_void_p, P_double, ctypes.POINTER(ctypes.c_longlong)]),
+    "stc_memory_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+}
+
+_lib = None
+
+
+def load(path=None):
+    """Load libstc.so (built by ``paper_1608_01102_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libstc.so not built (%s): run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class StcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _check(code):
+    if code != 0:
+        raise StcError(code, load().stc_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(P_double)
+
+
+def default_params(nx, ny, N, **overrides):
+    p = StcParams()
+    load().stc_default_params(ctypes.byref(p), nx, ny, N)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Problem:
+    """One control problem resident on the current CUDA device."""
+
+    def __init__(self, params, rho0, v0=None, stream=None):
+        self.lib = load()
+        self.params = params
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64).ravel()
+        v0p = None
+        if v0 is not None:
+            self._v0 = np.ascontiguousarray(v0, dtype=np.float64).ravel()
+            v0p = _dptr(self._v0)
+        h = c_void_p()
+        st = c_void_p(int(stream)) if stream is not None else None
+        _check(self.lib.stc_create_problem(ctypes.byref(params), _dptr(rho0), v0p, st, ctypes.byref(h)))
+        self.h = h
+        self.nx, self.ny, self.N = params.nx, params.ny, params.num_steps
+
+    # sizes --------------------------------------------------------------
+    def level_shape(self, level):
+        nl, nx, ny = c_int(), c_int(), c_int()
+        _check(self.lib.stc_level_info(self.h, ctypes.byref(nl), level, ctypes.byref(nx), ctypes.byref(ny)))
+        return nx.value, ny.value
+
+    def num_levels(self):
+        nl = c_int()
+        _check(self.lib.stc_level_info(self.h, ctypes.byref(nl), 0, None, None))
+        return nl.value
+
+    def field_shape(self, name, level=0):
+        nx, ny = self.level_shape(level)
+        F = ny * (nx + 1) + (ny + 1) * nx
+        C = nx * ny
+        N = self.N
+        face_np1 = ("V", "RES_V", "RES_IN_V", "XOLD_V", "KKT_G")
+        cell_np1 = ("PBAR", "RES_PBAR", "RES_IN_PBAR", "XOLD_PBAR", "RHO", "MTERM")
+        face_n = ("U", "RES_U", "RES_IN_U", "XOLD_U", "Z", "VSTAR", "LAMBDA", "W", "Y", "KKT_U")
+        cell_n = ("P", "RES_P", "RES_IN_P", "XOLD_P", "MU")
+        if name in face_np1:
+            return (N + 1, F)
+        if name in cell_np1:
+            return (N + 1, C)
+        if name in face_n:
+            return (N, F)
+        if name in cell_n:
+            return (N, C)
+        raise KeyError(name)
+
+    # field access -----------------------------------------------------------
+    def get(self, name, level=0):
+        shape = self.field_shape(name, level)
+        out = np.empty(shape, dtype=np.float64)
+        _check(self.lib.stc_get_field(self.h, FIELDS[name], level, _dptr(out), out.size))
+        return out
+
+    def set(self, name, arr, level=0):
+        shape = self.field_shape(name, level)
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(shape)
+        _check(self.lib.stc_set_field(self.h, FIELDS[name], level, _dptr(a), a.size))
+
+    def set_state(self, x, level=0):
+        for k, name in (("v", "V"), ("pbar", "PBAR"), ("u", "U"), ("p", "P")):
+            self.set(name, x[k], level)
+
+    def get_state(self, level=0, prefix=""):
+        return {k: self.get(prefix + name, level)
+                for k, name in (("v", "V"), ("pbar", "PBAR"), ("u", "U"), ("p", "P"))}
+
+    # method steps -------------------------------------------------------------
+    def set_keyframes(self, keyframes):
+        """keyframes: dict step -> (rho_star (C,), c)."""
+        steps = sorted(keyframes)
+        st = (c_int * len(steps))(*steps)
+        stars = np.ascontiguousarray(np.array([keyframes[s][0] for s in steps]).reshape(len(steps), -1),
+                                     dtype=np.float64)
+        cs = np.array([keyframes[s][1] for s in steps], dtype=np.float64)
+        _check(self.lib.stc_set_keyframes(self.h, len(steps), st, _dptr(stars), _dptr(cs)))
+
+    def vcycle(self, n=1):
+        f = c_double()
+        _check(self.lib.stc_vcycle(self.h, n, ctypes.byref(f)))
+        return f.value
+
+    def solve(self, tol=1e-4, max_admm=50, allow_not_converged=True):
+        rep = StcReport()
+        code = self.lib.stc_solve(self.h, tol, max_admm, ctypes.byref(rep))
+        if code != 0 and not (allow_not_converged and code == 4):
+            _check(code)
+        return {k: getattr(rep, k) for k, _ in StcReport._fields_}
+
+    def advect(self, source="VSTAR"):
+        _check(self.lib.stc_advect(self.h, FIELDS[source]))
+
+    def taylor_orders(self):
+        K = (c_int * self.N)()
+        _check(self.lib.stc_get_taylor_orders(self.h, K, self.N))
+        return np.array(list(K))
+
+    def metric_terms(self):
+        _check(self.lib.stc_metric_terms(self.h))
+
+    def adjoint(self, source="VSTAR", alpha=1.0, beta=1.0):
+        _check(self.lib.stc_adjoint(self.h, FIELDS[source], alpha, beta))
+
+    def project(self, name, first, count):
+        _check(self.lib.stc_project(self.h, FIELDS[name], first, count))
+
+    def ao(self, iters=2):
+        _check(self.lib.stc_ao(self.h, iters))
+
+    def prepare_targets(self):
+        _check(self.lib.stc_prepare_targets(self.h))
+
+    def nso_residual(self, level=0):
+        f = c_double()
+        _check(self.lib.stc_nso_residual(self.h, level, ctypes.byref(f)))
+        return f.value
+
+    def smooth(self, level=0, sweeps=1):
+        _check(self.lib.stc_smooth(self.h, level, sweeps))
+
+    def restrict(self, level=0):
+        _check(self.lib.stc_restrict(self.h, level))
+
+    def prolong_correct(self, level=0):
+        _check(self.lib.stc_prolong_correct(self.h, level))
+
+    def kkt_residual(self):
+        f = c_double()
+        _check(self.lib.stc_kkt_residual(self.h, ctypes.byref(f)))
+        return f.value
+
+    def admm_update(self):
+        f = c_double()
+        _check(self.lib.stc_admm_update(self.h, ctypes.byref(f)))
+        return f.value
+
+    def forces(self):
+        return self.get("U")
+
+    def launch_count(self):
+        n = ctypes.c_longlong()
+        _check(self.lib.stc_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def set_kernel_timing(self, on=True):
+        _check(self.lib.stc_set_kernel_timing(self.h, 1 if on else 0))
+
+    def kernel_timing(self):
+        ms, n = c_double(), ctypes.c_longlong()
+        _check(self.lib.stc_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def memory_bytes(self):
+        b = c_size_t()
+        _check(self.lib.stc_memory_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stc_destroy_problem(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,319 @@
+"""GPU parity: every step of the hot path, called through the C ABI of libstc,
+against the fp64 oracle on the same seeded inputs.
+
+fp64 mode (precision=1) must agree to rounding (plus the projection's multigrid
+truncation); fp32 mode (precision=0) within the precision policy's bounds (see
+gpu_common.TOL).  Grids span several colour tiles and ragged shapes.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm, kkt, mac, projection, scgs, stfas
+from paper_1608_01102_gb300 import workloads
+
+from gpu_common import TOL, make_pair, random_state, rel, velocity_trajectory
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::DeprecationWarning")]
+
+PREC = [1, 0]
+
+
+# ---------------------------------------------------------------------------
+# a2: projection Q
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape", [(16, 16), (24, 12), (32, 32)])
+def test_projection(prec, shape):
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=4, precision=prec)
+    rng = np.random.default_rng(1)
+    w = workloads.random_faces(rng, nx, ny, 4)
+    w[1] += workloads.swirl_velocity(nx, ny, 3.0)
+    G.set("W", w)
+    G.project("W", 0, 4)
+    out = G.get("W")
+    for i in range(4):
+        ref = projection.project(P.grid, w[i])
+        assert rel(out[i], ref) < TOL[prec]["project"], (i, rel(out[i], ref))
+        d = mac.div(P.grid, out[i])
+        assert np.max(np.abs(d)) < TOL[prec]["project"] * np.max(np.abs(mac.div(P.grid, w[i]))) * 10
+
+
+# ---------------------------------------------------------------------------
+# a3: forward advection (Taylor exponential, adaptive order)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape,N", [((16, 16), 6), ((24, 12), 5), ((32, 32), 8)])
+def test_forward_advection(prec, shape, N):
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=N, precision=prec)
+    v = velocity_trajectory(nx, ny, N, amp=0.8)
+    G.set("VSTAR", v[:N])
+    G.advect("VSTAR")
+    rho = G.get("RHO")
+    K = G.taylor_orders()
+    ref, Kref = kkt.forward_density(P, v[:N])
+    np.testing.assert_array_equal(K, Kref)
+    assert max(Kref) > 3
+    for i in range(N + 1):
+        assert rel(rho[i], ref[i]) < (1e-12 if prec == 1 else 1e-5), (i, rel(rho[i], ref[i]))
+    # mass is conserved exactly up to rounding
+    assert abs(rho[N].sum() - P.rho0.sum()) < (1e-10 if prec == 1 else 1e-4) * P.rho0.sum()
+
+
+# ---------------------------------------------------------------------------
+# a5 / a6 / a7: keyframe metric, backward adjoint sweep, v*-gradient
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape,N,levels", [((16, 16), 6, 2), ((24, 12), 5, 1), ((32, 32), 6, 3)])
+def test_adjoint_sweep(prec, shape, N, levels):
+    nx, ny = shape
+    star_mid = workloads.gaussian_ball(nx, ny, (0.4, 0.5 * ny / nx), 0.1)
+    star_end = workloads.gaussian_ball(nx, ny, (0.6, 0.6 * ny / nx), 0.1)
+    kf = {N // 2: (star_mid, 0.5), N: (star_end, 1.0)}
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=levels, keyframes=kf, K=2.0)
+    v = velocity_trajectory(nx, ny, N, amp=0.7, seed=3)
+    rng = np.random.default_rng(4)
+    w = workloads.random_faces(rng, nx, ny, N, 0.2)
+    G.set("VSTAR", v[:N])
+    G.set("W", w)
+    G.advect("VSTAR")
+    G.metric_terms()
+    G.adjoint("VSTAR", 1.0, 1.0 / P.K)
+    rhos, Ks = kkt.forward_density(P, v[:N])
+    mt = G.get("MTERM")
+    for s in range(N + 1):
+        ref = P.misfit_grad(s, rhos[s])
+        if s in kf:
+            assert rel(mt[s], ref) < (1e-11 if prec == 1 else 2e-5)
+        else:
+            assert np.all(mt[s] == 0)
+    mu = G.get("MU")
+    mu_ref = kkt.adjoint_density(P, v[:N], rhos, Ks)
+    for s in range(N):
+        assert rel(mu[s], mu_ref[s]) < (1e-11 if prec == 1 else 2e-5), (s, rel(mu[s], mu_ref[s]))
+    dens = kkt.density_gradient(P, v[:N], rhos, Ks, mu_ref)
+    y = G.get("Y")
+    for s in range(1, N):
+        ref = w[s] - dens[s] / P.K
+        assert rel(y[s], ref) < (1e-11 if prec == 1 else 2e-5), (s, rel(y[s], ref))
+
+
+# ---------------------------------------------------------------------------
+# a4: NSO residual f on every level
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape,N", [((16, 16), 4), ((24, 16), 3)])
+def test_nso_residual_all_levels(prec, shape, N):
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=N, precision=prec)
+    grids = stfas.hierarchy(P)
+    assert G.num_levels() == len(grids)
+    for l, g in enumerate(grids):
+        x = random_state(P, 10 + l, grid=g)
+        z = np.random.default_rng(20 + l).standard_normal((N, g.F)) * g.interior_faces()
+        G.set_state(x, level=l)
+        G.set("Z", z, level=l)
+        inf = G.nso_residual(level=l)
+        f = kkt.nso_residual(P, g, x, z)
+        got = G.get_state(level=l, prefix="RES_")
+        dbl = prec == 1 or (l == len(grids) - 1 and l > 0)
+        for k in f:
+            assert rel(got[k], f[k]) < (1e-12 if dbl else 2e-6), (l, k, rel(got[k], f[k]))
+        assert abs(inf - kkt.state_inf(f)) <= (1e-12 if dbl else 1e-5) * kkt.state_inf(f)
+
+
+# ---------------------------------------------------------------------------
+# a8: SCGS sweep (all colours) with the temporal block-tridiagonal solve
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape,N", [((16, 16), 5), ((12, 8), 3), ((8, 8), 1)])
+def test_scgs_sweep(prec, shape, N):
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=N, precision=prec)
+    grids = stfas.hierarchy(P)
+    for l, g in enumerate(grids):
+        x = random_state(P, 30 + l, grid=g, scale=0.3)
+        x["u"] *= 0.3
+        z = np.random.default_rng(40 + l).standard_normal((N, g.F)) * g.interior_faces() * 0.3
+        res = random_state(P, 50 + l, grid=g, scale=0.1) if l > 0 else kkt.zero_state(P, g)
+        if l > 0:
+            res["v"][0] = 0.0
+            res["pbar"][0] = 0.0
+        G.set_state(x, level=l)
+        G.set("Z", z, level=l)
+        for k, name in (("v", "RES_IN_V"), ("pbar", "RES_IN_PBAR"), ("u", "RES_IN_U"), ("p", "RES_IN_P")):
+            G.set(name, res[k], level=l)
+        G.smooth(level=l, sweeps=1)
+        got = G.get_state(level=l)
+        ref = kkt.copy_state(x)
+        scgs.sweep(P, g, ref, z, res)
+        dbl = prec == 1 or (l == len(grids) - 1 and l > 0)
+        for k in ref:
+            d = {kk: ref[kk] - x[kk] for kk in ref}[k]    # compare the update itself
+            assert rel(got[k] - x[k], d) < (TOL[1]["smooth"] if dbl else TOL[0]["smooth"]), \
+                (l, k, rel(got[k] - x[k], d))
+
+
+# ---------------------------------------------------------------------------
+# a9: restriction and prolongation-correction
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_transfers(prec):
+    nx, ny, N = 16, 12, 3
+    P, G = make_pair(nx, ny, N=N, precision=prec)
+    grids = stfas.hierarchy(P)
+    x0 = random_state(P, 60)
+    G.set_state(x0, 0)
+    G.restrict(0)
+    xc = stfas.restrict_state(grids[0], x0)
+    got = G.get_state(1)
+    old = G.get_state(1, prefix="XOLD_")
+    tol = 1e-14 if prec == 1 else 1e-6
+    for k in xc:
+        assert rel(got[k], xc[k]) < tol and rel(old[k], xc[k]) < tol
+    xn = random_state(P, 61, grid=grids[1])
+    G.set_state(xn, 1)
+    G.prolong_correct(0)
+    corr = stfas.prolong_state(grids[0], grids[1], kkt.state_sub(xn, xc))
+    corr["v"][0] = 0.0
+    corr["pbar"][0] = 0.0
+    got = G.get_state(0)
+    for k in x0:
+        assert rel(got[k], x0[k] + corr[k]) < tol, k
+
+
+# ---------------------------------------------------------------------------
+# a10: full V-cycle (Alg. 2) from the AO target
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape,N", [((16, 16), 6), ((32, 32), 8), ((24, 16), 4)])
+def test_vcycle(prec, shape, N):
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=N, precision=prec, r=1e-3)
+    v = velocity_trajectory(nx, ny, N, amp=0.5, seed=5)
+    lam = workloads.random_faces(np.random.default_rng(6), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("VSTAR", v[:N])
+    G.set("LAMBDA", lam)
+    G.prepare_targets()
+    z = v[:N] - lam / P.K
+    np.testing.assert_allclose(G.get("Z"), z, rtol=1e-6 if prec == 0 else 1e-14, atol=1e-7)
+    x = kkt.zero_state(P)
+    for c in range(2):
+        f_gpu = G.vcycle(1)
+        f_ref = stfas.stfas_cycle(P, x, z)
+        got = G.get_state(0)
+        for k in x:
+            assert rel(got[k], x[k]) < TOL[prec]["vcycle"], (c, k, rel(got[k], x[k]))
+        assert abs(f_gpu - f_ref) <= 1e-3 * f_ref + TOL[prec]["vcycle"] * 1e3
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1: AO fixed point (forward, adjoint, projection) and targets
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_ao(prec):
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, K=2.0)
+    v = velocity_trajectory(nx, ny, N, amp=0.4, seed=7)
+    lam = workloads.random_faces(np.random.default_rng(8), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("V", v)
+    G.set("LAMBDA", lam)
+    G.ao(2)
+    vs_ref, rhos_ref, _ = admm.ao(P, v, lam, iters=2)
+    vs = G.get("VSTAR")
+    for s in range(N):
+        assert rel(vs[s], vs_ref[s]) < TOL[prec]["ao"], (s, rel(vs[s], vs_ref[s]))
+    rho = G.get("RHO")
+    for s in range(N + 1):
+        assert rel(rho[s], rhos_ref[s]) < TOL[prec]["ao"]
+    z = G.get("Z")
+    assert rel(z, vs_ref - lam / P.K) < TOL[prec]["ao"]
+
+
+# ---------------------------------------------------------------------------
+# KKT metric: reduced gradient g(v)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_kkt_residual(prec):
+    nx, ny, N = 16, 16, 5
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, r=1e-2)
+    v = velocity_trajectory(nx, ny, N, amp=0.4, seed=9)
+    v = np.array([projection.project(P.grid, a) for a in v])
+    G.set("V", v)
+    norm = G.kkt_residual()
+    g_ref = kkt.reduced_gradient(P, v)
+    u_ref = kkt.forces(P, v)
+    tol = 2e-7 if prec == 1 else 2e-4
+    assert rel(G.get("KKT_U"), u_ref) < tol
+    g = G.get("KKT_G")
+    assert rel(g[1:], g_ref[1:]) < tol, rel(g[1:], g_ref[1:])
+    assert abs(norm - np.linalg.norm(g_ref)) <= tol * np.linalg.norm(g_ref)
+
+
+# ---------------------------------------------------------------------------
+# Alg. 3: a few ADMM iterations end to end
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_admm_iterations(prec):
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, r=1e-3, sigma=0.12)
+    rep = G.solve(tol=1e-12, max_admm=3)
+    x, vs, lam, hist = admm.solve(P, tol=1e-12, max_admm=3, eps_admm=P.rho_scale / 100)
+    assert rep["admm_iters"] == len(hist)
+    tol = 1e-5 if prec == 1 else 1e-3
+    assert abs(rep["kkt_rel"] - hist[-1]["kkt_rel"]) <= tol * hist[-1]["kkt_rel"]
+    v = G.get("V")
+    assert rel(v, x["v"]) < tol, rel(v, x["v"])
+    u = G.get("U")
+    assert rel(u, x["u"]) < (tol if prec == 1 else 1e-3)
+    J_gpu = kkt.objective(P, v)
+    J_ref = kkt.objective(P, x["v"])
+    assert abs(J_gpu - J_ref) <= (1e-8 if prec == 1 else 1e-4) * J_ref
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_single_level_grid_and_single_step():
+    P, G = make_pair(4, 4, N=1, precision=1)
+    assert G.num_levels() == 1
+    x = random_state(P, 70)
+    z = np.random.default_rng(71).standard_normal((1, P.grid.F)) * P.grid.interior_faces()
+    G.set_state(x)
+    G.set("Z", z)
+    G.smooth(0, 2)
+    ref = kkt.copy_state(x)
+    res = kkt.zero_state(P)
+    for _ in range(2):
+        scgs.sweep(P, P.grid, ref, z, res)
+    got = G.get_state()
+    for k in ref:
+        assert rel(got[k], ref[k]) < 1e-10
+
+
+def test_no_keyframes_gives_zero_adjoint():
+    P, G = make_pair(16, 16, N=4, precision=0, keyframes=None)
+    v = velocity_trajectory(16, 16, 4)
+    G.set("VSTAR", v[:4])
+    G.advect("VSTAR")
+    G.metric_terms()
+    G.adjoint("VSTAR", 0.0, 1.0)
+    assert np.all(G.get("MU") == 0)
+    assert np.all(G.get("Y")[1:] == 0)
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_1608_01102_gb300 import stc
+    P, G = make_pair(16, 16, N=4, precision=0)
+    with pytest.raises(stc.StcError):
+        G.lib.stc_get_field(G.h, 0, 0, np.zeros(3).ctypes.data_as(stc.P_double), 3) == 0 or \
+            stc._check(G.lib.stc_get_field(G.h, 0, 0, np.zeros(3).ctypes.data_as(stc.P_double), 3))
+    with pytest.raises(stc.StcError):
+        G.set_keyframes({0: (np.zeros(256), 1.0)})
+    with pytest.raises(stc.StcError):
+        G.project("RHO", 0, 1)
+    with pytest.raises(stc.StcError):
+        G.restrict(G.num_levels() - 1)
