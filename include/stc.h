@@ -143,9 +143,13 @@ stc_status stc_set_keyframes(stc_problem* p, int count, const int* steps, const 
  * nso_res_inf (may be NULL) receives ||f||_inf after the last cycle. */
 stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf);
 
-/* The ADMM outer loop (Alg. 3) from v_i = 0 (i >= 1), lambda = 0: stop when the
- * relative KKT residual ||g(v)||/||g(v_start)|| <= kkt_rel_tol, or on the
- * paper's density-change test, or after max_admm iterations (then
+/* The ADMM outer loop (Alg. 3) from v_i = 0 (i >= 1), lambda = 0: each
+ * iteration runs the AO fixed point (cold on the first iteration, warm-started
+ * from the previous v* afterwards), at least one V-cycle and then V-cycles
+ * until ||f||_inf <= eps_stfas * ||f||_inf of the first NSO (or max_vcycles),
+ * the KKT metric and the multiplier update.  Stops when the relative KKT
+ * residual ||g(v)||/||g(v_start)|| <= kkt_rel_tol, or on the paper's
+ * density-change test, or after max_admm iterations (then
  * STC_ERR_NOT_CONVERGED, with the state kept).  report may be NULL. */
 stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_report* report);
 
@@ -188,9 +192,11 @@ stc_status stc_adjoint(stc_problem* p, int source_field, double alpha, double be
  * of a face field of the finest level (V, U, VSTAR, Y, W, KKT_U, KKT_G, Z). */
 stc_status stc_project(stc_problem* p, int field, int first, int count);
 
-/* One AO solve (Alg. 1): w = v + lambda/K, v* = w, then `iters` forward /
- * backward / projection passes; then z = v* - lambda/K on every level. */
-stc_status stc_ao(stc_problem* p, int iters);
+/* One AO solve (Alg. 1): w = v + lambda/K; v* = w (warm_start = 0) or the
+ * current v* is kept (warm_start != 0, how stc_solve continues the fixed-point
+ * iteration after its first ADMM iteration); then `iters` forward / backward /
+ * projection passes; then z = v* - lambda/K on every level. */
+stc_status stc_ao(stc_problem* p, int iters, int warm_start);
 /* z = v* - lambda/K on the finest level, restricted to every coarser level. */
 stc_status stc_prepare_targets(stc_problem* p);
 

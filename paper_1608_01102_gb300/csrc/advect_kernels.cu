@@ -387,8 +387,8 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
           gys[e] += xf * (buf_at(g, s, cur, j, i) - buf_at(g, s, cur, j - 1, i)) * T(g.ih);
         }
       }
-      // w_{m-1} = c_m mu + A^T w_m   (c_0 = 1: T^T mu)
-      const double cprev = (mm == 0) ? 1.0 : cm * mm / g.dt;
+      // w_{m-1} = c_m mu + A^T w_m with c_m = c_{m+1} (m+1) / dt  (c_0 = 1: T^T mu)
+      const double cprev = (mm == 0) ? 1.0 : cm * (mm + 1) / g.dt;
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;

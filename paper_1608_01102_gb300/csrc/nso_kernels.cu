@@ -219,184 +219,219 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
   }
 }
 
-// Scratch layout per colour launch: for block k of the cell with colour-local
-// index q: Cp[k][20][ncell] then dp[k][5][ncell].
-template <class T>
-__global__ void scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
-                                   T* __restrict__ scratch) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ncell = ncx * ncy;
-  if (q >= ncell) return;
-  const int i = 2 * (q % ncx) + (colour & 1);
-  const int j = 2 * (q / ncx) + (colour >> 1);
-  if (i >= g.nx || j >= g.ny) return;
+// One CTA smooths `cpb` cells of one colour in three phases:
+//  A (parallel over cells x timesteps): the coupling U_t = I/dt + dAdv_loc(v_{t+1})
+//    and the right-hand sides of both blocks of timestep t are assembled into
+//    shared memory -- all global loads happen here, off the sequential path;
+//  B (one thread per cell): block Thomas over the 2N blocks from shared memory,
+//    then back substitution (solution overwrites the right-hand sides);
+//  C (parallel over cells x blocks): x += omega * delta written back.
+// Shared memory per cell: U[N][16], R[2N][5] (rhs -> d' -> delta), Cp[2N][20].
+// State type T (the level's storage) and solve type S: the coarsest level of
+// the fp32 mode keeps its state and residuals in fp64 (T = double) and solves
+// the per-cell correction in fp32 (S = float); elsewhere S = T.
+__host__ __device__ inline size_t scgs_cell_floats(int N) {
+  return (size_t)16 * N + (size_t)5 * 2 * N + (size_t)20 * 2 * N;
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(128)
+scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
   const int nb = 2 * N;
-  const T idt = T(g.idt);
-  const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
-  const T act[4] = {T(i > 0), T(i < g.nx - 1), T(j > 0), T(j < g.ny - 1)};
-  const T gv[4] = {act[0] * T(g.ih), -act[1] * T(g.ih), act[2] * T(g.ih), -act[3] * T(g.ih)};
-  const int cc = cidx(g, j, i);
-  const size_t blk = (size_t)25 * ncell;
+  const int ncell = ncx * ncy;
+  const int q0 = blockIdx.x * cpb;
+  S* Us = reinterpret_cast<S*>(smem_raw);            // [cpb][N][16]
+  S* Rs = Us + (size_t)cpb * N * 16;                  // [cpb][2N][5]
+  S* Cs = Rs + (size_t)cpb * nb * 5;                  // [cpb][2N][20]
 
-  // forward elimination
-  T Cprev[4][4];      // face part of C'_{k-1} (its pressure row is not needed by L)
-  T dprev[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    dprev[a] = T(0);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) Cprev[a][b] = T(0);
-  }
-  for (int k = 0; k < nb; ++k) {
-    const bool ublk = (k % 2) == 0;
-    const int t = ublk ? k / 2 : (k + 1) / 2;
-    // diagonal face block and right-hand side
-    T A[4][4];
-    T diag;
-    if (ublk) diag = T(-1);
-    else diag = (t < N ? T(g.a) : T(0)) + T(g.lm);
+  // ---- phase A: couplings and right-hand sides ----------------------------
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item / N, t = item - (item / N) * N;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const int i = 2 * (q % ncx) + (colour & 1);
+    const int j = 2 * (q / ncx) + (colour >> 1);
+    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+    const T act[4] = {T(i > 0), T(i < g.nx - 1), T(j > 0), T(j < g.ny - 1)};
+    const int cc = cidx(g, j, i);
+    T Jl[4][4];
+    local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
+    S* U = Us + ((size_t)c * N + t) * 16;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) A[a][b] = (a == b) ? (act[a] > T(0) ? diag : T(1)) : T(0);
-    T B[4][5];
-    T q4;
-    if (ublk) {
-      const T* ru = r.u + (size_t)t * g.F;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) B[a][4] = -ld(ru + fidx[a]) * act[a];
-      q4 = -ld(r.p + (size_t)t * g.C + cc);
-    } else {
-      const T* rv = r.v + (size_t)t * g.F;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) B[a][4] = -ld(rv + fidx[a]) * act[a];
-      q4 = -ld(r.pbar + (size_t)t * g.C + cc);
-    }
-    // lower coupling L (face block) to block k-1
-    if (k >= 1) {
-      T L[4][4];
-      if (ublk) {
-        // J[B_u(t), B_v(t)] = -I/dt
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) L[a][b] = (a == b) ? -idt * act[a] : T(0);
-      } else {
-        // J[B_v(t), B_u(t-1)] = (I/dt + dAdv_loc(v_t))^T
-        T Jl[4][4];
-        local_adv_jac(g, x.v + (size_t)t * g.F, j, i, Jl);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            L[a][b] = ((a == b ? idt : T(0)) + T(g.self_adv) * Jl[b][a]) * act[a] * act[b];
-      }
-      // A -= L Cprev ; rhs -= L dprev
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          s += L[a][b] * dprev[b];
-          T acc = T(0);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc += L[a][c] * Cprev[c][b];
-          A[a][b] -= acc;
-        }
-        B[a][4] -= s;
-      }
-    }
-    // upper coupling U (face block) to block k+1
-    if (k < nb - 1) {
-      if (ublk) {
-        // J[B_u(t), B_v(t+1)] = I/dt + dAdv_loc(v_{t+1})
-        T Jl[4][4];
-        local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            B[a][b] = ((a == b ? idt : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b];
-      } else {
-        // J[B_v(t), B_u(t)] = -I/dt
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) B[a][b] = (a == b) ? -idt * act[a] : T(0);
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) B[a][b] = T(0);
-    }
-    // symmetrise the face block (it is symmetric in exact arithmetic)
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a + 1; b < 4; ++b) {
-        T m = T(0.5) * (A[a][b] + A[b][a]);
-        A[a][b] = m;
-        A[b][a] = m;
-      }
-    T Y[5];
-    saddle_solve(A, gv, B, q4, Y);
-    // store C'_k (5 x 4) and d'_k (5)
-    T* sk = scratch + (size_t)k * blk;
+      for (int b = 0; b < 4; ++b)
+        U[a * 4 + b] = S(((a == b ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b]);
+    S* Ru = Rs + ((size_t)c * nb + 2 * t) * 5;        // B_u(t)
+    S* Rv = Ru + 5;                                   // B_v(t+1)
+    const T* ru = r.u + (size_t)t * g.F;
+    const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        sk[(size_t)(a * 4 + b) * ncell + q] = B[a][b];
-        Cprev[a][b] = B[a][b];
-      }
-      sk[(size_t)(20 + a) * ncell + q] = B[a][4];
-      dprev[a] = B[a][4];
+      Ru[a] = S(-ld(ru + fidx[a]) * act[a]);
+      Rv[a] = S(-ld(rv + fidx[a]) * act[a]);
     }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) sk[(size_t)(16 + b) * ncell + q] = Y[b];
-    sk[(size_t)24 * ncell + q] = Y[4];
+    Ru[4] = S(-ld(r.p + (size_t)t * g.C + cc));
+    Rv[4] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
   }
-  // back substitution and update x += omega * delta
-  const T om = T(g.omega);
-  T xn[4] = {T(0), T(0), T(0), T(0)};
-  for (int k = nb - 1; k >= 0; --k) {
-    const T* sk = scratch + (size_t)k * blk;
-    T d[5];
+  __syncthreads();
+
+  // ---- phase B: block Thomas in time, one thread per cell ------------------
+  if ((int)threadIdx.x < cpb && q0 + (int)threadIdx.x < ncell) {
+    const int c = threadIdx.x;
+    const int q = q0 + c;
+    const int i = 2 * (q % ncx) + (colour & 1);
+    const int j = 2 * (q / ncx) + (colour >> 1);
+    const S idt = S(g.idt);
+    const S act[4] = {S(i > 0), S(i < g.nx - 1), S(j > 0), S(j < g.ny - 1)};
+    const S gv[4] = {act[0] * S(g.ih), -act[1] * S(g.ih), act[2] * S(g.ih), -act[3] * S(g.ih)};
+    const S* Uc = Us + (size_t)c * N * 16;
+    S* Rc = Rs + (size_t)c * nb * 5;
+    S* Cc = Cs + (size_t)c * nb * 20;
+    S Cprev[4][4];
+    S dprev[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) d[a] = sk[(size_t)(20 + a) * ncell + q];
-    d[4] = sk[(size_t)24 * ncell + q];
-    if (k < nb - 1) {
+    for (int a = 0; a < 4; ++a) {
+      dprev[a] = S(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Cprev[a][b] = S(0);
+    }
+    for (int k = 0; k < nb; ++k) {
+      const bool ublk = (k % 2) == 0;
+      const int t = ublk ? k / 2 : (k + 1) / 2;
+      S diag = ublk ? S(-1) : ((t < N ? S(g.a) : S(0)) + S(g.lm));
+      S A[4][4];
+      S B[4][5];
+      S* Rk = Rc + (size_t)k * 5;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        T s = T(0);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) s += sk[(size_t)(a * 4 + b) * ncell + q] * xn[b];
-        d[a] -= s;
+        for (int b = 0; b < 4; ++b) A[a][b] = (a == b) ? (act[a] > S(0) ? diag : S(1)) : S(0);
+        B[a][4] = Rk[a];
       }
-      T s = T(0);
+      const S q4 = Rk[4];
+      if (k >= 1) {
+        // lower coupling: J[B_u(t), B_v(t)] = -I/dt, or J[B_v(t), B_u(t-1)] = U_{t-1}^S
+        if (ublk) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) s += sk[(size_t)(16 + b) * ncell + q] * xn[b];
-      d[4] -= s;
+          for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) A[a][b] += idt * act[a] * Cprev[a][b];
+            B[a][4] += idt * act[a] * dprev[a];
+          }
+        } else {
+          const S* Up = Uc + (size_t)(t - 1) * 16;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            S s = S(0);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              s += Up[b * 4 + a] * dprev[b];
+              S acc = S(0);
+#pragma unroll
+              for (int c2 = 0; c2 < 4; ++c2) acc += Up[c2 * 4 + a] * Cprev[c2][b];
+              A[a][b] -= acc;
+            }
+            B[a][4] -= s;
+          }
+        }
+      }
+      // upper coupling: J[B_u(t), B_v(t+1)] = U_t, or J[B_v(t), B_u(t)] = -I/dt
+      if (k < nb - 1) {
+        if (ublk) {
+          const S* Ut = Uc + (size_t)t * 16;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) B[a][b] = Ut[a * 4 + b];
+        } else {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) B[a][b] = (a == b) ? -idt * act[a] : S(0);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) B[a][b] = S(0);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b) {
+          S m = S(0.5) * (A[a][b] + A[b][a]);
+          A[a][b] = m;
+          A[b][a] = m;
+        }
+      S Y[5];
+      saddle_solve(A, gv, B, q4, Y);
+      S* Ck = Cc + (size_t)k * 20;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          Ck[a * 4 + b] = B[a][b];
+          Cprev[a][b] = B[a][b];
+        }
+        Rk[a] = B[a][4];
+        dprev[a] = B[a][4];
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Ck[16 + b] = Y[b];
+      Rk[4] = Y[4];
     }
+    // back substitution: x_k = d'_k - C'_k x_{k+1} (faces of x_{k+1})
+    S xn[4] = {S(0), S(0), S(0), S(0)};
+    for (int k = nb - 1; k >= 0; --k) {
+      S* Rk = Rc + (size_t)k * 5;
+      const S* Ck = Cc + (size_t)k * 20;
+      S d[5];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) xn[a] = d[a];
+      for (int a = 0; a < 5; ++a) d[a] = Rk[a];
+      if (k < nb - 1) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          S s = S(0);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) s += Ck[a * 4 + b] * xn[b];
+          d[a] -= s;
+        }
+        S s = S(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s += Ck[16 + b] * xn[b];
+        d[4] -= s;
+      }
+#pragma unroll
+      for (int a = 0; a < 5; ++a) Rk[a] = d[a];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xn[a] = d[a];
+    }
+  }
+  __syncthreads();
+
+  // ---- phase C: x += omega * delta -----------------------------------------
+  const T om = T(g.omega);
+  for (int item = threadIdx.x; item < cpb * nb; item += blockDim.x) {
+    const int c = item / nb, k = item - (item / nb) * nb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const int i = 2 * (q % ncx) + (colour & 1);
+    const int j = 2 * (q / ncx) + (colour >> 1);
+    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+    const bool act[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
+    const int cc = cidx(g, j, i);
+    const S* d = Rs + ((size_t)c * nb + k) * 5;
     const bool ublk = (k % 2) == 0;
     const int t = ublk ? k / 2 : (k + 1) / 2;
-    if (ublk) {
-      T* ut = x.u + (size_t)t * g.F;
+    T* fu = ublk ? x.u + (size_t)t * g.F : x.v + (size_t)t * g.F;
+    T* cu = ublk ? x.p + (size_t)t * g.C : x.pbar + (size_t)t * g.C;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-        if (act[a] > T(0)) ut[fidx[a]] += om * d[a];
-      x.p[(size_t)t * g.C + cc] += om * d[4];
-    } else {
-      T* vt = x.v + (size_t)t * g.F;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-        if (act[a] > T(0)) vt[fidx[a]] += om * d[a];
-      x.pbar[(size_t)t * g.C + cc] += om * d[4];
-    }
+    for (int a = 0; a < 4; ++a)
+      if (act[a]) fu[fidx[a]] += om * T(d[a]);
+    cu[cc] += om * T(d[4]);
   }
 }
 
@@ -591,14 +626,41 @@ void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, 
 
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 
-template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, T* scratch, cudaStream_t st) {
+template <class S>
+int scgs_cells_per_cta(int N) {
+  // two CTAs of ~110 KB per SM, at most 16 cells per CTA
+  const size_t per = scgs_cell_floats(N) * sizeof(S);
+  int c = (int)((110 * 1024) / per);
+  if (c > 16) c = 16;
+  return c < 1 ? 1 : c;
+}
+
+template <class T, class S>
+static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, cudaStream_t st) {
   const int ncx = colour_extent(g.nx, colour & 1);
   const int ncy = colour_extent(g.ny, colour >> 1);
   const int ncell = ncx * ncy;
   if (ncell <= 0) return;
-  const int tpb = 64;
-  scgs_colour_kernel<T><<<blocks_for(ncell, tpb), tpb, 0, st>>>(g, x, r, colour, ncx, ncy, scratch);
+  const int cpb = scgs_cells_per_cta<S>(g.N);
+  const size_t sm = (size_t)cpb * scgs_cell_floats(g.N) * sizeof(S);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute((const void*)scgs_colour_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr_set = true;
+  }
+  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 128, sm, st>>>(g, x, r, colour, ncx, ncy, cpb);
+}
+
+template <class T>
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st) {
+  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, st);
+  else launch_scgs_ts<T, T>(g, x, r, colour, st);
+}
+
+size_t scgs_smem_bytes(int N, size_t tsize) {
+  return tsize == 4 ? (size_t)scgs_cells_per_cta<float>(N) * scgs_cell_floats(N) * 4
+                    : (size_t)scgs_cells_per_cta<double>(N) * scgs_cell_floats(N) * 8;
 }
 
 template <class Tf, class Tc>
@@ -671,7 +733,7 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
                                        cudaStream_t);                                                      \
-  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, T*, cudaStream_t);            \
+  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t);           \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
   template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
   template void launch_remove_mean<T>(T*, int, int, cudaStream_t);

@@ -5,8 +5,9 @@
 // Q v = v - G phi with (D G) phi = D v on the closed box.  One CTA projects one
 // face field: b = D v, phi and every coarse level live in shared memory (a
 // 128^2 fp32 field needs ~171 KB), red-black Gauss-Seidel V(2,2) cycles with
-// average restriction and bilinear prolongation, the coarsest level (<= 3x3)
-// solved by Gauss-Seidel in fp64, then v - G phi written back.
+// average restriction and bilinear prolongation, the coarsest level (<= 64
+// cells) by 30 parallel red-black Gauss-Seidel sweeps in fp64, then v - G phi
+// written back.
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
 
@@ -75,7 +76,8 @@ __global__ void __launch_bounds__(kPoissonThreads, 1)
 project_kernel(Geom g, T* fields, int vcycles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  __shared__ double red[32];
+  __shared__ double cb[64], cp[64];
+  __shared__ double cmean;
   const PLevels L = poisson_levels(g.nx, g.ny);
   T* v = fields + (size_t)blockIdx.x * g.F;
   const int nx = g.nx, ny = g.ny;
@@ -124,36 +126,44 @@ project_kernel(Geom g, T* fields, int vcycles) {
       }
       __syncthreads();
     }
-    // coarsest: Gauss-Seidel in fp64 on the compatible (mean-free) right-hand side
+    // coarsest (<= 64 cells): red-black Gauss-Seidel in fp64 on the compatible
+    // (mean-free) right-hand side, one thread per cell
     {
       const int l = nl - 1;
       const int lx = L.nx[l], ly = L.ny[l];
-      const double h = g.h * (double)(1 << l);
+      const int n = lx * ly;
+      const double h2 = (g.h * (double)(1 << l)) * (g.h * (double)(1 << l));
       T* phi = sm + L.off[l];
-      T* b = phi + (size_t)lx * ly;
-      if (threadIdx.x == 0) {
-        double bb[64], pp[64];
-        const int n = lx * ly;
-        double mean = 0.0;
-        for (int e = 0; e < n; ++e) mean += (double)b[e];
-        mean /= n;
-        for (int e = 0; e < n; ++e) {
-          bb[e] = (double)b[e] - mean;
-          pp[e] = 0.0;
-        }
-        for (int it = 0; it < 200; ++it)
-          for (int e = 0; e < n; ++e) {
-            const int j = e / lx, i = e % lx;
-            double s = 0.0;
-            int k = 0;
-            if (i > 0) { s += pp[e - 1]; ++k; }
-            if (i < lx - 1) { s += pp[e + 1]; ++k; }
-            if (j > 0) { s += pp[e - lx]; ++k; }
-            if (j < ly - 1) { s += pp[e + lx]; ++k; }
-            pp[e] = (s - h * h * bb[e]) / k;
-          }
-        for (int e = 0; e < n; ++e) phi[e] = T(pp[e]);
+      T* b = phi + (size_t)n;
+      const int e = threadIdx.x;
+      if (e < n) {
+        cb[e] = (double)b[e];
+        cp[e] = 0.0;
       }
+      __syncthreads();
+      if (e == 0) {
+        double m = 0.0;
+        for (int k = 0; k < n; ++k) m += cb[k];
+        cmean = m / n;
+      }
+      __syncthreads();
+      if (e < n) cb[e] -= cmean;
+      __syncthreads();
+      const int j = e / lx, i = e - (e / lx) * lx;
+      for (int it = 0; it < 30; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+          if (e < n && ((i + j) & 1) == colour) {
+            double sacc = 0.0;
+            int k = 0;
+            if (i > 0) { sacc += cp[e - 1]; ++k; }
+            if (i < lx - 1) { sacc += cp[e + 1]; ++k; }
+            if (j > 0) { sacc += cp[e - lx]; ++k; }
+            if (j < ly - 1) { sacc += cp[e + lx]; ++k; }
+            cp[e] = (sacc - h2 * cb[e]) / k;
+          }
+          __syncthreads();
+        }
+      if (e < n) phi[e] = T(cp[e]);
       __syncthreads();
     }
     // ascend: phi_l += P phi_{l+1}, post-smooth
@@ -184,7 +194,6 @@ project_kernel(Geom g, T* fields, int vcycles) {
       }
     }
   }
-  (void)red;
   // v -= G phi on interior faces
   for (int e = threadIdx.x; e < g.F; e += blockDim.x) {
     if (e < g.Fx) {
@@ -226,16 +235,17 @@ cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cud
 // ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
-// w_s = v_s + lambda_s / K (s >= 1), w_0 = v_0; v*_s = w_s   (Alg. 1 initialisation)
+// w_s = v_s + lambda_s / K (s >= 1), w_0 = v_0; v*_s = w_s unless warm-starting
+// (Alg. 1 initialisation; v*_0 = v_0 always)
 template <class T>
 __global__ void ao_init_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ lam, double invK, T* w,
-                               T* vstar) {
+                               T* vstar, int warm) {
   const size_t n = (size_t)g.N * g.F;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     T val = v[e];
     if (e >= (size_t)g.F) val += T(invK) * lam[e];
     w[e] = val;
-    vstar[e] = val;
+    if (!warm || e < (size_t)g.F) vstar[e] = val;
   }
 }
 
@@ -318,8 +328,9 @@ static inline unsigned nblk(size_t n, int tpb, unsigned cap = 4096) {
 }
 
 template <class T>
-void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, cudaStream_t st) {
-  ao_init_kernel<T><<<nblk((size_t)g.N * g.F, 256), 256, 0, st>>>(g, v, lam, invK, w, vstar);
+void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, int warm,
+                    cudaStream_t st) {
+  ao_init_kernel<T><<<nblk((size_t)g.N * g.F, 256), 256, 0, st>>>(g, v, lam, invK, w, vstar, warm);
 }
 template <class T>
 void launch_axpby_faces(const Geom& g, int count, const T* a, double alpha, const T* b, double beta, T* out,
@@ -345,7 +356,7 @@ void launch_absdiff_max_copy(const T* a, T* b, size_t n, double* out, cudaStream
 
 #define STC_POI_INST(T)                                                                                        \
   template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t);                            \
-  template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, cudaStream_t);             \
+  template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, int, cudaStream_t);             \
   template void launch_axpby_faces<T>(const Geom&, int, const T*, double, const T*, double, T*, cudaStream_t); \
   template void launch_kkt_force_rhs<T>(const Geom&, const T*, T*, cudaStream_t);                             \
   template void launch_kkt_grad_rhs<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);  \

@@ -37,7 +37,6 @@ struct Level {
   bool dbl = false;
   FieldSet x, res, tmp, old;
   void* z = nullptr;
-  void* scratch = nullptr;
 };
 
 template <class T>
@@ -177,7 +176,8 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
       if (ev) ck(cudaEventRecordWithFlags(P->ev_start[P->ev_used], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
-        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, (T*)L.scratch, st);
+        // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
+        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st);
       });
       if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
       count(P, 1);
@@ -390,13 +390,14 @@ void prepare_targets(stc_problem* P, cudaStream_t st) {
   check_launch("targets");
 }
 
-void ao(stc_problem* P, int iters, cudaStream_t st) {
+void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
   Level& L0 = P->lv[0];
   const Geom& g = L0.g;
   const size_t fb = (size_t)g.F * P->ts;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    launch_ao_init<T>(g, (const T*)L0.x.v, (const T*)P->lam, 1.0 / P->prm.K, (T*)P->w, (T*)P->vstar, st);
+    launch_ao_init<T>(g, (const T*)L0.x.v, (const T*)P->lam, 1.0 / P->prm.K, (T*)P->w, (T*)P->vstar, warm ? 1 : 0,
+                      st);
   });
   count(P, 1);
   for (int it = 0; it < iters; ++it) {
@@ -696,10 +697,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       alloc_fieldset(P, L.tmp, L.g, L.dbl);
       if (l > 0) alloc_fieldset(P, L.old, L.g, L.dbl);
       L.z = dalloc(P, (size_t)N * L.g.F * esz(L.dbl));
-      int maxcell = 0;
-      for (int c = 0; c < 4; ++c)
-        maxcell = std::max(maxcell, colour_extent(L.g.nx, c & 1) * colour_extent(L.g.ny, c >> 1));
-      L.scratch = dalloc(P, (size_t)maxcell * 2 * N * 25 * esz(L.dbl));
+      if (scgs_smem_bytes(N, esz(L.dbl)) > (size_t)smem_optin)
+        fail(STC_ERR_UNSUPPORTED, "too many timesteps for the shared-memory SCGS solve");
       P->lv.push_back(L);
     }
     const size_t F = g0.F, C = g0.C, ts = P->ts;
@@ -844,12 +843,15 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
        "copy");
     p->fscale = -1.0;
     for (int it = 0; it < max_admm; ++it) {
-      ao(p, prm.ao_iters, p->st);
+      // Alg. 1 initialises v* = v + lambda/K on the first ADMM iteration and
+      // continues from the previous v* afterwards (warm start)
+      ao(p, prm.ao_iters, it > 0, p->st);
       residual_norm(p, 0, 0, p->st);
       double f = read_scalar(p, 0);
       if (p->fscale < 0) p->fscale = f;
       int cycles = 0;
-      while (f > prm.eps_stfas * p->fscale && cycles < prm.max_vcycles) {
+      // at least one V-cycle per ADMM iteration, then until the NSO tolerance
+      while ((cycles < 1 || f > prm.eps_stfas * p->fscale) && cycles < prm.max_vcycles) {
         f = run_vcycle(p);
         ++cycles;
       }
@@ -998,13 +1000,13 @@ stc_status stc_project(stc_problem* p, int field, int first, int count) {
   });
 }
 
-stc_status stc_ao(stc_problem* p, int iters) {
+stc_status stc_ao(stc_problem* p, int iters, int warm_start) {
   if (!p || iters < 0) {
     g_last_error = "invalid argument";
     return STC_ERR_INVALID_ARG;
   }
   return guarded(p, [&]() {
-    ao(p, iters, p->st);
+    ao(p, iters, warm_start != 0, p->st);
     read_scalar(p, 0);
   });
 }

@@ -10,7 +10,8 @@ template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
                          cudaStream_t st);
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, T* scratch, cudaStream_t st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st);
+size_t scgs_smem_bytes(int N, size_t tsize);
 int colour_extent(int n, int parity);
 template <class Tf, class Tc>
 void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
@@ -60,7 +61,8 @@ size_t project_smem(const Geom& g, size_t tsize);
 bool project_supported(const Geom& g, size_t tsize);
 
 template <class T>
-void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, cudaStream_t st);
+void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, int warm,
+                    cudaStream_t st);
 template <class T>
 void launch_axpby_faces(const Geom& g, int count, const T* a, double alpha, const T* b, double beta, T* out,
                         cudaStream_t st);

@@ -61,7 +61,7 @@ SIGNATURES = {
     "stc_metric_terms": (c_int, [c_void_p]),
     "stc_adjoint": (c_int, [c_void_p, c_int, c_double, c_double]),
     "stc_project": (c_int, [c_void_p, c_int, c_int, c_int]),
-    "stc_ao": (c_int, [c_void_p, c_int]),
+    "stc_ao": (c_int, [c_void_p, c_int, c_int]),
     "stc_prepare_targets": (c_int, [c_void_p]),
     "stc_nso_residual": (c_int, [c_void_p, c_int, P_double]),
     "stc_smooth": (c_int, [c_void_p, c_int, c_int]),
@@ -225,8 +225,8 @@ class Problem:
     def project(self, name, first, count):
         _check(self.lib.stc_project(self.h, FIELDS[name], first, count))
 
-    def ao(self, iters=2):
-        _check(self.lib.stc_ao(self.h, iters))
+    def ao(self, iters=2, warm=False):
+        _check(self.lib.stc_ao(self.h, iters, 1 if warm else 0))
 
     def prepare_targets(self):
         _check(self.lib.stc_prepare_targets(self.h))

@@ -22,7 +22,7 @@ def rel(a, b, floor=1e-30):
 
 
 def make_pair(nx=16, ny=None, N=6, precision=1, levels=2, r=1e-2, K=1.0, keyframes="end", v0=None,
-              sigma=0.12, **over):
+              sigma=0.12, dt=None, **over):
     ny = ny or nx
     rho0 = workloads.gaussian_ball(nx, ny, (0.5, 0.35 * ny / nx), sigma)
     star = workloads.gaussian_ball(nx, ny, (0.5, 0.65 * ny / nx), sigma)
@@ -35,10 +35,11 @@ def make_pair(nx=16, ny=None, N=6, precision=1, levels=2, r=1e-2, K=1.0, keyfram
     o_over = {k: v for k, v in over.items() if k not in ("poisson_vcycles", "scgs_omega")}
     if "scgs_omega" in over:
         o_over["omega"] = over["scgs_omega"]
-    P = kkt.Problem(nx, ny, N, 1.0 / N, rho0, r=r, K=K, keyframes=kf, metric_levels=levels, **o_over)
+    dt = 1.0 / N if dt is None else dt
+    P = kkt.Problem(nx, ny, N, dt, rho0, r=r, K=K, keyframes=kf, metric_levels=levels, **o_over)
     if v0 is not None:
         P.v0 = v0.copy()
-    prm = stc.default_params(nx, ny, N, precision=precision, r=r, K=K, metric_levels=levels)
+    prm = stc.default_params(nx, ny, N, precision=precision, r=r, K=K, metric_levels=levels, dt=dt)
     for k, v in over.items():
         setattr(prm, k, int(v) if isinstance(v, bool) else v)
     G = stc.Problem(prm, rho0, v0)

@@ -130,7 +130,9 @@ def test_nso_residual_all_levels(prec, shape, N):
 @pytest.mark.parametrize("shape,N", [((16, 16), 5), ((12, 8), 3), ((8, 8), 1)])
 def test_scgs_sweep(prec, shape, N):
     nx, ny = shape
-    P, G = make_pair(nx, ny, N=N, precision=prec)
+    # a physical timestep (dt = 1 with a random state makes one Gauss-Seidel
+    # sweep amplify the state 1e4-fold, a test artefact rather than a case)
+    P, G = make_pair(nx, ny, N=N, precision=prec, dt=1.0 / max(N, 16))
     grids = stfas.hierarchy(P)
     for l, g in enumerate(grids):
         x = random_state(P, 30 + l, grid=g, scale=0.3)
@@ -148,11 +150,15 @@ def test_scgs_sweep(prec, shape, N):
         got = G.get_state(level=l)
         ref = kkt.copy_state(x)
         scgs.sweep(P, g, ref, z, res)
-        dbl = prec == 1 or (l == len(grids) - 1 and l > 0)
+        dbl = prec == 1   # the fp32 mode solves even the fp64 coarsest level's corrections in fp32
         for k in ref:
-            d = {kk: ref[kk] - x[kk] for kk in ref}[k]    # compare the update itself
-            assert rel(got[k] - x[k], d) < (TOL[1]["smooth"] if dbl else TOL[0]["smooth"]), \
-                (l, k, rel(got[k] - x[k], d))
+            # compare the update itself; in fp32 the stored state carries its own
+            # rounding (eps * |x|), which bounds how well a small update can agree
+            d = ref[k] - x[k]
+            err = np.linalg.norm(got[k] - ref[k])
+            tol = TOL[1]["smooth"] if dbl else TOL[0]["smooth"]
+            floor = 0.0 if dbl else 2e-7 * np.linalg.norm(x[k])
+            assert err <= tol * np.linalg.norm(d) + floor, (l, k, err / max(np.linalg.norm(d), 1e-300))
 
 
 # ---------------------------------------------------------------------------
@@ -231,6 +237,12 @@ def test_ao(prec):
         assert rel(rho[s], rhos_ref[s]) < TOL[prec]["ao"]
     z = G.get("Z")
     assert rel(z, vs_ref - lam / P.K) < TOL[prec]["ao"]
+    # warm start: continue the fixed-point iteration from the current v*
+    G.ao(2, warm=True)
+    vs2_ref, _, _ = admm.ao(P, v, lam, iters=2, start=vs_ref)
+    vs2 = G.get("VSTAR")
+    for s in range(N):
+        assert rel(vs2[s], vs2_ref[s]) < 2 * TOL[prec]["ao"], (s, rel(vs2[s], vs2_ref[s]))
 
 
 # ---------------------------------------------------------------------------
@@ -309,8 +321,7 @@ def test_invalid_arguments_are_rejected():
     from paper_1608_01102_gb300 import stc
     P, G = make_pair(16, 16, N=4, precision=0)
     with pytest.raises(stc.StcError):
-        G.lib.stc_get_field(G.h, 0, 0, np.zeros(3).ctypes.data_as(stc.P_double), 3) == 0 or \
-            stc._check(G.lib.stc_get_field(G.h, 0, 0, np.zeros(3).ctypes.data_as(stc.P_double), 3))
+        stc._check(G.lib.stc_get_field(G.h, 0, 0, np.zeros(3).ctypes.data_as(stc.P_double), 3))
     with pytest.raises(stc.StcError):
         G.set_keyframes({0: (np.zeros(256), 1.0)})
     with pytest.raises(stc.StcError):
