@@ -120,19 +120,34 @@ __device__ T apply_AT(const Geom& g, const Slab& s, const T* b, const T* vxs, co
   return acc * T(g.ih);
 }
 
-// Copy the 2-row halo of buffer `b` (offset `off` in every CTA's shared
-// memory) from the owning CTAs of the cluster.
+// Push this CTA's rows that other CTAs need as halo (rows within 2 of its slab
+// edges) into their copy of buffer `b` (same shared-memory offset in every CTA)
+// with remote stores; the next cluster barrier publishes them.  No CTA reads
+// remote shared memory on the critical path.
 template <class T>
-__device__ void halo_copy(cg::cluster_group& cl, const Geom& g, const Slab& s, T* b) {
+__device__ void halo_push(cg::cluster_group& cl, const Geom& g, const Slab& s, T* b, int rank) {
   const int nx = g.nx;
-  const int rows[4] = {s.r0 - 2, s.r0 - 1, s.r1, s.r1 + 1};
+  if (s.r1 <= s.r0) return;
   for (int e = threadIdx.x; e < 4 * nx; e += blockDim.x) {
     const int q = e / nx, i = e - q * nx;
-    const int jj = rows[q];
-    if (jj < 0 || jj >= g.ny || s.r1 <= s.r0) continue;
-    const int owner = jj / s.rpc;
-    const T* rb = cl.map_shared_rank(b, owner);
-    b[(jj - s.r0 + 2) * nx + i] = rb[(jj - owner * s.rpc + 2) * nx + i];
+    const int jj = (q < 2) ? s.r0 + q : s.r1 - 4 + q;   // r0, r0+1, r1-2, r1-1
+    if (jj < s.r0 || jj >= s.r1) continue;
+    if (q >= 2 && jj < s.r0 + 2) continue;               // already pushed as r0 / r0+1
+    const T val = b[(jj - s.r0 + 2) * nx + i];
+    int last = -1;
+    for (int d = -2; d <= 2; ++d) {
+      const int row = jj + d;
+      if (d == 0 || row < 0 || row >= g.ny) continue;
+      const int owner = row / s.rpc;
+      if (owner == rank || owner == last) continue;
+      last = owner;
+      const int r0o = owner * s.rpc;
+      const int r1o = min(g.ny, r0o + s.rpc);
+      if ((jj >= r0o - 2 && jj < r0o) || (jj >= r1o && jj < r1o + 2)) {
+        T* rb = cl.map_shared_rank(b, owner);
+        rb[(jj - r0o + 2) * nx + i] = val;
+      }
+    }
   }
 }
 
@@ -164,7 +179,7 @@ __host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) 
   L.vy = (size_t)(rpc + 3) * g.nx;
   L.gx = adjoint ? (size_t)rpc * (g.nx + 1) : 0;
   L.gy = adjoint ? (size_t)(rpc + 1) * g.nx : 0;
-  L.total = (2 * L.buf + L.vx + L.vy + L.gx + L.gy) * sizeof(T) + 4 * sizeof(double);
+  L.total = (2 * L.buf + L.vx + L.vy + L.gx + L.gy) * sizeof(T) + 2 * kClusterCTAs * sizeof(double);
   return L;
 }
 
@@ -217,21 +232,21 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
   }
   int kfail = 0;
   for (int st = 0; st < g.N; ++st) {
-    // t_0 = rho_st into tb0 own rows; faces of v_st
+    // t_0 = rho_st into tb0 own rows, its halo pushed; faces of v_st
 #pragma unroll
     for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < nown) tb0[2 * g.nx + e] = acc[q];
     }
     load_faces(g, s, vel + (size_t)st * g.F, vxs, vys);
+    __syncthreads();
+    halo_push(cl, g, s, tb0, rank);
     cl.sync();
     T* cur = tb0;
     T* nxt = tb1;
     int K = kmax;
     bool done = false;
     for (int k = 1; k <= kmax; ++k) {
-      halo_copy(cl, g, s, cur);
-      __syncthreads();
       const T ck = T(g.dt / k);
       double lmax = 0.0;
 #pragma unroll
@@ -249,11 +264,14 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
           lmax = fmax(lmax, fabs((double)t));
         }
       }
-      const double bm = block_max(lmax, red);
-      if (threadIdx.x == 0) cmax[k & 1] = bm;
+      const double bm = block_max(lmax, red);   // also orders the nxt writes before the push
+      halo_push(cl, g, s, nxt, rank);
+      if (threadIdx.x < kClusterCTAs)
+        *cl.map_shared_rank(cmax + (k & 1) * kClusterCTAs + rank, (int)threadIdx.x) = bm;
       cl.sync();
       double gm = 0.0;
-      for (int r = 0; r < kClusterCTAs; ++r) gm = fmax(gm, *cl.map_shared_rank(cmax + (k & 1), r));
+#pragma unroll
+      for (int r = 0; r < kClusterCTAs; ++r) gm = fmax(gm, cmax[(k & 1) * kClusterCTAs + r]);
       T* tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -332,18 +350,20 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     load_faces(g, s, vs, vxs, vys);
     // powers P_1 .. P_{K-1}
     for (int e = threadIdx.x; e < nown; e += blockDim.x) tb0[2 * nx + e] = rs[(size_t)s.r0 * nx + e];
+    __syncthreads();
+    halo_push(cl, g, s, tb0, rank);
     T* cur = tb0;
     T* nxt = tb1;
     for (int k = 1; k < K; ++k) {
       cl.sync();
-      halo_copy(cl, g, s, cur);
-      __syncthreads();
       for (int e = threadIdx.x; e < nown; e += blockDim.x) {
         const int j = s.r0 + e / nx, i = e % nx;
         const T t = apply_A(g, s, cur, vxs, vys, j, i);
         nxt[2 * nx + e] = t;
         powers[(size_t)k * g.C + (size_t)s.r0 * nx + e] = t;
       }
+      __syncthreads();
+      halo_push(cl, g, s, nxt, rank);
       T* tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -361,11 +381,11 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       const int e = threadIdx.x + q * blockDim.x;
       if (e < nown) cur[2 * nx + e] = T(cK) * m[q];
     }
+    __syncthreads();
+    halo_push(cl, g, s, cur, rank);
     double cm = cK;
     for (int mm = K - 1; mm >= 0; --mm) {
       cl.sync();
-      halo_copy(cl, g, s, cur);
-      __syncthreads();
       const T* P = (mm == 0) ? rs : powers + (size_t)mm * g.C;
       // grad += B(P_m)^T w_m on own faces
       for (int e = threadIdx.x; e < ngx; e += blockDim.x) {
@@ -398,6 +418,8 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
         }
       }
       cm = cprev;
+      __syncthreads();
+      halo_push(cl, g, s, nxt, rank);
       T* tmp = cur;
       cur = nxt;
       nxt = tmp;

@@ -159,14 +159,17 @@ __device__ void local_adv_jac(const Geom& g, const T* v, int j, int i, T J[4][4]
 // definite (either sign): LDL^T without pivoting.
 template <class T>
 __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5], T q4, T Y[5]) {
-  // LDL^T in place: A = L D L^T, L unit lower (stored below the diagonal), D on diagonal
+  // LDL^T in place: A = L D L^T, L unit lower (stored below the diagonal), D on
+  // the diagonal; the reciprocals of D are kept so that the solves multiply
+  T dinv[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     T d = A[k][k];
 #pragma unroll
     for (int s = 0; s < k; ++s) d -= A[k][s] * A[k][s] * A[s][s];
     A[k][k] = d;
-    T id = T(1) / d;
+    const T id = T(1) / d;
+    dinv[k] = id;
 #pragma unroll
     for (int r = k + 1; r < 4; ++r) {
       T l = A[r][k];
@@ -193,7 +196,7 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
       X[r][c] = s;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) X[r][c] /= A[r][r];
+    for (int r = 0; r < 4; ++r) X[r][c] *= dinv[r];
 #pragma unroll
     for (int r = 3; r >= 0; --r) {
       T s = X[r][c];
@@ -223,32 +226,33 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
 //  A (parallel over cells x timesteps): the coupling U_t = I/dt + dAdv_loc(v_{t+1})
 //    and the right-hand sides of both blocks of timestep t are assembled into
 //    shared memory -- all global loads happen here, off the sequential path;
-//  B (one thread per cell): block Thomas over the 2N blocks from shared memory,
-//    then back substitution (solution overwrites the right-hand sides);
+//  B (one thread per cell): block Thomas over the 2N blocks, reading U and the
+//    right-hand sides from shared memory; the elimination factors C'_k go to an
+//    L2-resident global buffer (written on the forward chain, prefetched one
+//    step ahead during back substitution), the solution overwrites the
+//    right-hand sides;
 //  C (parallel over cells x blocks): x += omega * delta written back.
-// Shared memory per cell: U[N][16], R[2N][5] (rhs -> d' -> delta), Cp[2N][20].
-// State type T (the level's storage) and solve type S: the coarsest level of
-// the fp32 mode keeps its state and residuals in fp64 (T = double) and solves
-// the per-cell correction in fp32 (S = float); elsewhere S = T.
-__host__ __device__ inline size_t scgs_cell_floats(int N) {
-  return (size_t)16 * N + (size_t)5 * 2 * N + (size_t)20 * 2 * N;
-}
+// Shared arrays are interleaved with the cell index fastest ([t][comp][cell]),
+// so the chains of one warp read consecutive banks.  State type T (the level's
+// storage) and solve type S: the coarsest level of the fp32 mode keeps its
+// state and residuals in fp64 (T = double) and solves the per-cell correction
+// in fp32 (S = float); elsewhere S = T.
+__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)16 * N + (size_t)5 * 2 * N; }
 
 template <class T, class S>
 __global__ void __launch_bounds__(128)
-scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb) {
+scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb, S* __restrict__ cfac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
   const int nb = 2 * N;
   const int ncell = ncx * ncy;
   const int q0 = blockIdx.x * cpb;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // [cpb][N][16]
-  S* Rs = Us + (size_t)cpb * N * 16;                  // [cpb][2N][5]
-  S* Cs = Rs + (size_t)cpb * nb * 5;                  // [cpb][2N][20]
+  S* Us = reinterpret_cast<S*>(smem_raw);            // [N][16][cpb]
+  S* Rs = Us + (size_t)N * 16 * cpb;                  // [2N][5][cpb]
 
   // ---- phase A: couplings and right-hand sides ----------------------------
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
-    const int c = item / N, t = item - (item / N) * N;
+    const int c = item % cpb, t = item / cpb;
     const int q = q0 + c;
     if (q >= ncell) continue;
     const int i = 2 * (q % ncx) + (colour & 1);
@@ -258,23 +262,23 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     const int cc = cidx(g, j, i);
     T Jl[4][4];
     local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
-    S* U = Us + ((size_t)c * N + t) * 16;
+    S* U = Us + (size_t)t * 16 * cpb + c;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b)
-        U[a * 4 + b] = S(((a == b ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b]);
-    S* Ru = Rs + ((size_t)c * nb + 2 * t) * 5;        // B_u(t)
-    S* Rv = Ru + 5;                                   // B_v(t+1)
+        U[(a * 4 + b) * cpb] = S(((a == b ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b]);
+    S* Ru = Rs + (size_t)(2 * t) * 5 * cpb + c;        // B_u(t)
+    S* Rv = Ru + (size_t)5 * cpb;                      // B_v(t+1)
     const T* ru = r.u + (size_t)t * g.F;
     const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      Ru[a] = S(-ld(ru + fidx[a]) * act[a]);
-      Rv[a] = S(-ld(rv + fidx[a]) * act[a]);
+      Ru[a * cpb] = S(-ld(ru + fidx[a]) * act[a]);
+      Rv[a * cpb] = S(-ld(rv + fidx[a]) * act[a]);
     }
-    Ru[4] = S(-ld(r.p + (size_t)t * g.C + cc));
-    Rv[4] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
+    Ru[4 * cpb] = S(-ld(r.p + (size_t)t * g.C + cc));
+    Rv[4 * cpb] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
   }
   __syncthreads();
 
@@ -287,9 +291,9 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     const S idt = S(g.idt);
     const S act[4] = {S(i > 0), S(i < g.nx - 1), S(j > 0), S(j < g.ny - 1)};
     const S gv[4] = {act[0] * S(g.ih), -act[1] * S(g.ih), act[2] * S(g.ih), -act[3] * S(g.ih)};
-    const S* Uc = Us + (size_t)c * N * 16;
-    S* Rc = Rs + (size_t)c * nb * 5;
-    S* Cc = Cs + (size_t)c * nb * 20;
+    // global factor layout: [k][20][ncell], cell index fastest (coalesced)
+    S* cf = cfac + q;
+    const size_t kstride = (size_t)20 * ncell;
     S Cprev[4][4];
     S dprev[4];
 #pragma unroll
@@ -301,19 +305,19 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     for (int k = 0; k < nb; ++k) {
       const bool ublk = (k % 2) == 0;
       const int t = ublk ? k / 2 : (k + 1) / 2;
-      S diag = ublk ? S(-1) : ((t < N ? S(g.a) : S(0)) + S(g.lm));
+      const S diag = ublk ? S(-1) : ((t < N ? S(g.a) : S(0)) + S(g.lm));
       S A[4][4];
       S B[4][5];
-      S* Rk = Rc + (size_t)k * 5;
+      S* Rk = Rs + (size_t)k * 5 * cpb + c;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) A[a][b] = (a == b) ? (act[a] > S(0) ? diag : S(1)) : S(0);
-        B[a][4] = Rk[a];
+        B[a][4] = Rk[a * cpb];
       }
-      const S q4 = Rk[4];
+      const S q4 = Rk[4 * cpb];
       if (k >= 1) {
-        // lower coupling: J[B_u(t), B_v(t)] = -I/dt, or J[B_v(t), B_u(t-1)] = U_{t-1}^S
+        // lower coupling: J[B_u(t), B_v(t)] = -I/dt, or J[B_v(t), B_u(t-1)] = U_{t-1}^T
         if (ublk) {
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
@@ -322,30 +326,35 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
             B[a][4] += idt * act[a] * dprev[a];
           }
         } else {
-          const S* Up = Uc + (size_t)(t - 1) * 16;
+          const S* Up = Us + (size_t)(t - 1) * 16 * cpb + c;
+          S Ut[4][4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Ut[a][b] = Up[(a * 4 + b) * cpb];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            S s = S(0);
+            S sacc = S(0);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-              s += Up[b * 4 + a] * dprev[b];
+              sacc += Ut[b][a] * dprev[b];
               S acc = S(0);
 #pragma unroll
-              for (int c2 = 0; c2 < 4; ++c2) acc += Up[c2 * 4 + a] * Cprev[c2][b];
+              for (int c2 = 0; c2 < 4; ++c2) acc += Ut[c2][a] * Cprev[c2][b];
               A[a][b] -= acc;
             }
-            B[a][4] -= s;
+            B[a][4] -= sacc;
           }
         }
       }
       // upper coupling: J[B_u(t), B_v(t+1)] = U_t, or J[B_v(t), B_u(t)] = -I/dt
       if (k < nb - 1) {
         if (ublk) {
-          const S* Ut = Uc + (size_t)t * 16;
+          const S* Ut = Us + (size_t)t * 16 * cpb + c;
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) B[a][b] = Ut[a * 4 + b];
+            for (int b = 0; b < 4; ++b) B[a][b] = Ut[(a * 4 + b) * cpb];
         } else {
 #pragma unroll
           for (int a = 0; a < 4; ++a)
@@ -362,50 +371,67 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a + 1; b < 4; ++b) {
-          S m = S(0.5) * (A[a][b] + A[b][a]);
+          const S m = S(0.5) * (A[a][b] + A[b][a]);
           A[a][b] = m;
           A[b][a] = m;
         }
       S Y[5];
       saddle_solve(A, gv, B, q4, Y);
-      S* Ck = Cc + (size_t)k * 20;
+      S* Ck = cf + (size_t)k * kstride;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          Ck[a * 4 + b] = B[a][b];
+          Ck[(size_t)(a * 4 + b) * ncell] = B[a][b];
           Cprev[a][b] = B[a][b];
         }
-        Rk[a] = B[a][4];
+        Rk[a * cpb] = B[a][4];
         dprev[a] = B[a][4];
       }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) Ck[16 + b] = Y[b];
-      Rk[4] = Y[4];
+      for (int b = 0; b < 4; ++b) Ck[(size_t)(16 + b) * ncell] = Y[b];
+      Rk[4 * cpb] = Y[4];
     }
-    // back substitution: x_k = d'_k - C'_k x_{k+1} (faces of x_{k+1})
+    // back substitution: x_k = d'_k - C'_k x_{k+1} (faces of x_{k+1}); the factor
+    // of step k-1 is loaded while step k computes
     S xn[4] = {S(0), S(0), S(0), S(0)};
-    for (int k = nb - 1; k >= 0; --k) {
-      S* Rk = Rc + (size_t)k * 5;
-      const S* Ck = Cc + (size_t)k * 20;
+    S Cn[20];
+    if (nb >= 2) {
+      const S* Ck = cf + (size_t)(nb - 2) * kstride;
+#pragma unroll
+      for (int e = 0; e < 20; ++e) Cn[e] = Ck[(size_t)e * ncell];
+    }
+    {
+      S* Rk = Rs + (size_t)(nb - 1) * 5 * cpb + c;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xn[a] = Rk[a * cpb];
+    }
+    for (int k = nb - 2; k >= 0; --k) {
+      S Cc[20];
+#pragma unroll
+      for (int e = 0; e < 20; ++e) Cc[e] = Cn[e];
+      if (k >= 1) {
+        const S* Ck = cf + (size_t)(k - 1) * kstride;
+#pragma unroll
+        for (int e = 0; e < 20; ++e) Cn[e] = Ck[(size_t)e * ncell];
+      }
+      S* Rk = Rs + (size_t)k * 5 * cpb + c;
       S d[5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) d[a] = Rk[a];
-      if (k < nb - 1) {
+      for (int a = 0; a < 5; ++a) d[a] = Rk[a * cpb];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          S s = S(0);
+      for (int a = 0; a < 4; ++a) {
+        S sacc = S(0);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) s += Ck[a * 4 + b] * xn[b];
-          d[a] -= s;
-        }
-        S s = S(0);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) s += Ck[16 + b] * xn[b];
-        d[4] -= s;
+        for (int b = 0; b < 4; ++b) sacc += Cc[a * 4 + b] * xn[b];
+        d[a] -= sacc;
       }
+      S sacc = S(0);
 #pragma unroll
-      for (int a = 0; a < 5; ++a) Rk[a] = d[a];
+      for (int b = 0; b < 4; ++b) sacc += Cc[16 + b] * xn[b];
+      d[4] -= sacc;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) Rk[a * cpb] = d[a];
 #pragma unroll
       for (int a = 0; a < 4; ++a) xn[a] = d[a];
     }
@@ -415,7 +441,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   // ---- phase C: x += omega * delta -----------------------------------------
   const T om = T(g.omega);
   for (int item = threadIdx.x; item < cpb * nb; item += blockDim.x) {
-    const int c = item / nb, k = item - (item / nb) * nb;
+    const int c = item % cpb, k = item / cpb;
     const int q = q0 + c;
     if (q >= ncell) continue;
     const int i = 2 * (q % ncx) + (colour & 1);
@@ -423,15 +449,15 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
     const bool act[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
     const int cc = cidx(g, j, i);
-    const S* d = Rs + ((size_t)c * nb + k) * 5;
+    const S* d = Rs + (size_t)k * 5 * cpb + c;
     const bool ublk = (k % 2) == 0;
     const int t = ublk ? k / 2 : (k + 1) / 2;
     T* fu = ublk ? x.u + (size_t)t * g.F : x.v + (size_t)t * g.F;
     T* cu = ublk ? x.p + (size_t)t * g.C : x.pbar + (size_t)t * g.C;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-      if (act[a]) fu[fidx[a]] += om * T(d[a]);
-    cu[cc] += om * T(d[4]);
+      if (act[a]) fu[fidx[a]] += om * T(d[a * cpb]);
+    cu[cc] += om * T(d[4 * cpb]);
   }
 }
 
@@ -628,15 +654,15 @@ int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 
 template <class S>
 int scgs_cells_per_cta(int N) {
-  // two CTAs of ~110 KB per SM, at most 16 cells per CTA
+  // ~110 KB of shared memory per CTA (two CTAs per SM), at most 32 cells
   const size_t per = scgs_cell_floats(N) * sizeof(S);
   int c = (int)((110 * 1024) / per);
-  if (c > 16) c = 16;
+  if (c > 32) c = 32;
   return c < 1 ? 1 : c;
 }
 
 template <class T, class S>
-static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, cudaStream_t st) {
+static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, void* factors, cudaStream_t st) {
   const int ncx = colour_extent(g.nx, colour & 1);
   const int ncy = colour_extent(g.ny, colour >> 1);
   const int ncell = ncx * ncy;
@@ -649,18 +675,28 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
                          227 * 1024);
     attr_set = true;
   }
-  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 128, sm, st>>>(g, x, r, colour, ncx, ncy, cpb);
+  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 128, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, (S*)factors);
 }
 
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st) {
-  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, st);
-  else launch_scgs_ts<T, T>(g, x, r, colour, st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, void* factors,
+                        cudaStream_t st) {
+  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, factors, st);
+  else launch_scgs_ts<T, T>(g, x, r, colour, factors, st);
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
   return tsize == 4 ? (size_t)scgs_cells_per_cta<float>(N) * scgs_cell_floats(N) * 4
                     : (size_t)scgs_cells_per_cta<double>(N) * scgs_cell_floats(N) * 8;
+}
+
+size_t scgs_factor_bytes(int nx, int ny, int N, size_t ssize) {
+  int maxcell = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int n = colour_extent(nx, c & 1) * colour_extent(ny, c >> 1);
+    maxcell = n > maxcell ? n : maxcell;
+  }
+  return (size_t)maxcell * 2 * N * 20 * ssize;
 }
 
 template <class Tf, class Tc>
@@ -733,7 +769,7 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
                                        cudaStream_t);                                                      \
-  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t);           \
+  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, void*, cudaStream_t);    \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
   template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
   template void launch_remove_mean<T>(T*, int, int, cudaStream_t);
