@@ -167,7 +167,9 @@ __device__ void load_faces(const Geom& g, const Slab& s, const T* vel, T* vxs, T
 
 template <class T>
 struct AdvLayout {
-  size_t buf, vx, vy, gx, gy, total;
+  size_t buf, vx, vy, gx, gy;  // element counts of the T arrays
+  size_t cm_off;               // byte offset of the fp64 cluster-max slots (16-byte aligned)
+  size_t total;                // bytes
 };
 
 template <class T>
@@ -179,7 +181,8 @@ __host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) 
   L.vy = (size_t)(rpc + 3) * g.nx;
   L.gx = adjoint ? (size_t)rpc * (g.nx + 1) : 0;
   L.gy = adjoint ? (size_t)(rpc + 1) * g.nx : 0;
-  L.total = (2 * L.buf + L.vx + L.vy + L.gx + L.gy) * sizeof(T) + 2 * kClusterCTAs * sizeof(double);
+  L.cm_off = ((2 * L.buf + L.vx + L.vy + L.gx + L.gy) * sizeof(T) + 15) / 16 * 16;
+  L.total = L.cm_off + 2 * kClusterCTAs * sizeof(double);
   return L;
 }
 
@@ -219,7 +222,7 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
   T* tb1 = tb0 + L.buf;
   T* vxs = tb1 + L.buf;
   T* vys = vxs + L.vx;
-  double* cmax = reinterpret_cast<double*>(smem_raw + (2 * L.buf + L.vx + L.vy) * sizeof(T));
+  double* cmax = reinterpret_cast<double*>(smem_raw + L.cm_off);
   __shared__ double red[32];
   const int nown = (s.r1 - s.r0) * g.nx;
 

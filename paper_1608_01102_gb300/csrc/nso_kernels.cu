@@ -222,11 +222,50 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
   }
 }
 
+// Solve A x = b for a symmetric definite 4x4 A (either sign) by LDL^T without
+// pivoting (A is factorised in the caller's copy).
+template <class T>
+__device__ __forceinline__ void ldlt_solve4(T A[4][4], const T b[4], T x[4]) {
+  T dinv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T d = A[k][k];
+#pragma unroll
+    for (int s = 0; s < k; ++s) d -= A[k][s] * A[k][s] * A[s][s];
+    A[k][k] = d;
+    const T id = T(1) / d;
+    dinv[k] = id;
+#pragma unroll
+    for (int r = k + 1; r < 4; ++r) {
+      T l = A[r][k];
+#pragma unroll
+      for (int s = 0; s < k; ++s) l -= A[r][s] * A[k][s] * A[s][s];
+      A[r][k] = l * id;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    T s = b[r];
+#pragma unroll
+    for (int k = 0; k < r; ++k) s -= A[r][k] * x[k];
+    x[r] = s;
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) x[r] *= dinv[r];
+#pragma unroll
+  for (int r = 3; r >= 0; --r) {
+    T s = x[r];
+#pragma unroll
+    for (int k = r + 1; k < 4; ++k) s -= A[k][r] * x[k];
+    x[r] = s;
+  }
+}
+
 // One CTA smooths `cpb` cells of one colour in three phases:
 //  A (parallel over cells x timesteps): the coupling U_t = I/dt + dAdv_loc(v_{t+1})
 //    and the right-hand sides of both blocks of timestep t are assembled into
 //    shared memory -- all global loads happen here, off the sequential path;
-//  B (one thread per cell): block Thomas over the 2N blocks, reading U and the
+//  B (8 lanes per cell): block Thomas over the 2N blocks, reading U and the
 //    right-hand sides from shared memory; the elimination factors C'_k go to an
 //    L2-resident global buffer (written on the forward chain, prefetched one
 //    step ahead during back substitution), the solution overwrites the
@@ -240,7 +279,7 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
 __host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)16 * N + (size_t)5 * 2 * N; }
 
 template <class T, class S>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb, S* __restrict__ cfac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
@@ -282,158 +321,177 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   }
   __syncthreads();
 
-  // ---- phase B: block Thomas in time, one thread per cell ------------------
-  if ((int)threadIdx.x < cpb && q0 + (int)threadIdx.x < ncell) {
-    const int c = threadIdx.x;
+  // ---- phase B: block Thomas in time, 8 lanes per cell ---------------------
+  // Lane `sub` of a cell's group owns column `sub` of [C'_k | d'_k] (sub < 5)
+  // and of the right-hand side block [U_k | r_k | g] (sub < 6); the 4x4 pivot
+  // block is gathered by shuffles and factorised redundantly on every lane.
+  if ((int)(threadIdx.x >> 5) * 4 < cpb) {
+    const unsigned full = 0xffffffffu;
+    const int sub = threadIdx.x & 7;
+    const int c = threadIdx.x >> 3;
     const int q = q0 + c;
-    const int i = 2 * (q % ncx) + (colour & 1);
-    const int j = 2 * (q / ncx) + (colour >> 1);
-    const S idt = S(g.idt);
-    const S act[4] = {S(i > 0), S(i < g.nx - 1), S(j > 0), S(j < g.ny - 1)};
-    const S gv[4] = {act[0] * S(g.ih), -act[1] * S(g.ih), act[2] * S(g.ih), -act[3] * S(g.ih)};
-    // global factor layout: [k][20][ncell], cell index fastest (coalesced)
-    S* cf = cfac + q;
-    const size_t kstride = (size_t)20 * ncell;
-    S Cprev[4][4];
-    S dprev[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      dprev[a] = S(0);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) Cprev[a][b] = S(0);
+    const bool valid = c < cpb && q < ncell;
+    const int cs = valid ? c : 0;   // shared-memory slot read by idle groups (never written)
+    int i = 0, j = 0;
+    if (valid) {
+      i = 2 * (q % ncx) + (colour & 1);
+      j = 2 * (q / ncx) + (colour >> 1);
     }
+    const S idt = S(g.idt);
+    S act[4];
+    if (valid) {
+      act[0] = S(i > 0);
+      act[1] = S(i < g.nx - 1);
+      act[2] = S(j > 0);
+      act[3] = S(j < g.ny - 1);
+    } else {
+      act[0] = act[1] = act[2] = act[3] = S(1);
+    }
+    const S gv[4] = {act[0] * S(g.ih), -act[1] * S(g.ih), act[2] * S(g.ih), -act[3] * S(g.ih)};
+    S* cf = cfac + (valid ? q : 0);
+    const size_t kstride = (size_t)20 * ncell;
+    S prev[4] = {S(0), S(0), S(0), S(0)};   // column `sub` of [C'_{k-1} | d'_{k-1}] (faces)
     for (int k = 0; k < nb; ++k) {
       const bool ublk = (k % 2) == 0;
       const int t = ublk ? k / 2 : (k + 1) / 2;
       const S diag = ublk ? S(-1) : ((t < N ? S(g.a) : S(0)) + S(g.lm));
-      S A[4][4];
-      S B[4][5];
-      S* Rk = Rs + (size_t)k * 5 * cpb + c;
+      const S* Rk = Rs + (size_t)k * 5 * cpb + cs;
+      // this lane's column of [D_k | r_k] (face rows)
+      S col[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) A[a][b] = (a == b) ? (act[a] > S(0) ? diag : S(1)) : S(0);
-        B[a][4] = Rk[a * cpb];
+      for (int a2 = 0; a2 < 4; ++a2) {
+        if (sub < 4) col[a2] = (a2 == sub) ? (act[a2] > S(0) ? diag : S(1)) : S(0);
+        else if (sub == 4) col[a2] = Rk[a2 * cpb];
+        else col[a2] = S(0);
       }
       const S q4 = Rk[4 * cpb];
+      // minus the lower coupling times the previous factor column
       if (k >= 1) {
-        // lower coupling: J[B_u(t), B_v(t)] = -I/dt, or J[B_v(t), B_u(t-1)] = U_{t-1}^T
         if (ublk) {
+          // J[B_u(t), B_v(t)] = -I/dt
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) A[a][b] += idt * act[a] * Cprev[a][b];
-            B[a][4] += idt * act[a] * dprev[a];
-          }
+          for (int a2 = 0; a2 < 4; ++a2) col[a2] += idt * act[a2] * prev[a2];
         } else {
-          const S* Up = Us + (size_t)(t - 1) * 16 * cpb + c;
-          S Ut[4][4];
+          // J[B_v(t), B_u(t-1)] = U_{t-1}^T
+          const S* Up = Us + (size_t)(t - 1) * 16 * cpb + cs;
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+          for (int a2 = 0; a2 < 4; ++a2) {
+            S acc = S(0);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) Ut[a][b] = Up[(a * 4 + b) * cpb];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            S sacc = S(0);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              sacc += Ut[b][a] * dprev[b];
-              S acc = S(0);
-#pragma unroll
-              for (int c2 = 0; c2 < 4; ++c2) acc += Ut[c2][a] * Cprev[c2][b];
-              A[a][b] -= acc;
-            }
-            B[a][4] -= sacc;
+            for (int c2 = 0; c2 < 4; ++c2) acc += Up[(c2 * 4 + a2) * cpb] * prev[c2];
+            col[a2] -= acc;
           }
         }
       }
-      // upper coupling: J[B_u(t), B_v(t+1)] = U_t, or J[B_v(t), B_u(t)] = -I/dt
-      if (k < nb - 1) {
-        if (ublk) {
-          const S* Ut = Us + (size_t)t * 16 * cpb + c;
+      // gather the pivot face block A (column b lives on lane b)
+      S A[4][4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+      for (int bb = 0; bb < 4; ++bb)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) B[a][b] = Ut[(a * 4 + b) * cpb];
+        for (int a2 = 0; a2 < 4; ++a2) A[a2][bb] = __shfl_sync(full, col[a2], bb, 8);
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int bb = a2 + 1; bb < 4; ++bb) {
+          const S m = S(0.5) * (A[a2][bb] + A[bb][a2]);
+          A[a2][bb] = m;
+          A[bb][a2] = m;
+        }
+      // this lane's right-hand side: U_k column (sub < 4), r_k (4), g (5)
+      S bcol[4];
+      S qc = S(0);
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) {
+        if (sub < 4) {
+          if (k < nb - 1) {
+            if (ublk) bcol[a2] = Us[((size_t)t * 16 + a2 * 4 + sub) * cpb + cs];
+            else bcol[a2] = (a2 == sub) ? -idt * act[a2] : S(0);
+          } else {
+            bcol[a2] = S(0);
+          }
+        } else if (sub == 4) {
+          bcol[a2] = col[a2];
         } else {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) B[a][b] = (a == b) ? -idt * act[a] : S(0);
+          bcol[a2] = gv[a2];
         }
-      } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) B[a][b] = S(0);
       }
+      if (sub == 4) qc = q4;
+      S X[4];
+      ldlt_solve4(A, bcol, X);
+      S Xg[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a2 = 0; a2 < 4; ++a2) Xg[a2] = __shfl_sync(full, X[a2], 5, 8);
+      S sgg = S(0), sgb = S(0);
 #pragma unroll
-        for (int b = a + 1; b < 4; ++b) {
-          const S m = S(0.5) * (A[a][b] + A[b][a]);
-          A[a][b] = m;
-          A[b][a] = m;
-        }
-      S Y[5];
-      saddle_solve(A, gv, B, q4, Y);
-      S* Ck = cf + (size_t)k * kstride;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          Ck[(size_t)(a * 4 + b) * ncell] = B[a][b];
-          Cprev[a][b] = B[a][b];
-        }
-        Rk[a * cpb] = B[a][4];
-        dprev[a] = B[a][4];
+      for (int a2 = 0; a2 < 4; ++a2) {
+        sgg += gv[a2] * Xg[a2];
+        sgb += gv[a2] * X[a2];
       }
+      const S y = (sgb - qc) * (S(1) / sgg);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) Ck[(size_t)(16 + b) * ncell] = Y[b];
-      Rk[4 * cpb] = Y[4];
-    }
-    // back substitution: x_k = d'_k - C'_k x_{k+1} (faces of x_{k+1}); the factor
-    // of step k-1 is loaded while step k computes
-    S xn[4] = {S(0), S(0), S(0), S(0)};
-    S Cn[20];
-    if (nb >= 2) {
-      const S* Ck = cf + (size_t)(nb - 2) * kstride;
+      for (int a2 = 0; a2 < 4; ++a2) prev[a2] = X[a2] - Xg[a2] * y;
+      if (valid) {
+        if (sub < 4) {
+          S* Ck = cf + (size_t)k * kstride + (size_t)(sub * 5) * ncell;
 #pragma unroll
-      for (int e = 0; e < 20; ++e) Cn[e] = Ck[(size_t)e * ncell];
+          for (int a2 = 0; a2 < 4; ++a2) Ck[(size_t)a2 * ncell] = prev[a2];
+          Ck[(size_t)4 * ncell] = y;
+        } else if (sub == 4) {
+          S* Rw = Rs + (size_t)k * 5 * cpb + c;
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) Rw[a2 * cpb] = prev[a2];
+          Rw[4 * cpb] = y;
+        }
+      }
     }
+    __syncwarp();
+    // back substitution: x_k = d'_k - C'_k x_{k+1}; lane b (< 4) holds column b
+    // of C'_k, prefetched one step ahead; the sum over b is a shuffle reduction
+    S xn[4];
     {
-      S* Rk = Rs + (size_t)(nb - 1) * 5 * cpb + c;
+      const S* Rl = Rs + (size_t)(nb - 1) * 5 * cpb + cs;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) xn[a] = Rk[a * cpb];
+      for (int a2 = 0; a2 < 4; ++a2) xn[a2] = Rl[a2 * cpb];
+    }
+    S Cn[5] = {S(0), S(0), S(0), S(0), S(0)};
+    if (nb >= 2 && sub < 4) {
+      const S* Ck = cf + (size_t)(nb - 2) * kstride + (size_t)(sub * 5) * ncell;
+#pragma unroll
+      for (int a2 = 0; a2 < 5; ++a2) Cn[a2] = Ck[(size_t)a2 * ncell];
     }
     for (int k = nb - 2; k >= 0; --k) {
-      S Cc[20];
+      S Cc[5];
 #pragma unroll
-      for (int e = 0; e < 20; ++e) Cc[e] = Cn[e];
-      if (k >= 1) {
-        const S* Ck = cf + (size_t)(k - 1) * kstride;
+      for (int a2 = 0; a2 < 5; ++a2) Cc[a2] = Cn[a2];
+      if (k >= 1 && sub < 4) {
+        const S* Ck = cf + (size_t)(k - 1) * kstride + (size_t)(sub * 5) * ncell;
 #pragma unroll
-        for (int e = 0; e < 20; ++e) Cn[e] = Ck[(size_t)e * ncell];
+        for (int a2 = 0; a2 < 5; ++a2) Cn[a2] = Ck[(size_t)a2 * ncell];
       }
-      S* Rk = Rs + (size_t)k * 5 * cpb + c;
+      // lane sub < 4 contributes column sub times x_{k+1}[sub]
+      S xs = xn[0];
+#pragma unroll
+      for (int a2 = 1; a2 < 4; ++a2) xs = (sub == a2) ? xn[a2] : xs;
+      S part[5];
+#pragma unroll
+      for (int a2 = 0; a2 < 5; ++a2) part[a2] = (sub < 4) ? Cc[a2] * xs : S(0);
+#pragma unroll
+      for (int a2 = 0; a2 < 5; ++a2) {
+        part[a2] += __shfl_xor_sync(full, part[a2], 1, 8);
+        part[a2] += __shfl_xor_sync(full, part[a2], 2, 8);
+        part[a2] = __shfl_sync(full, part[a2], 0, 8);
+      }
+      S* Rk = Rs + (size_t)k * 5 * cpb + cs;
       S d[5];
 #pragma unroll
-      for (int a = 0; a < 5; ++a) d[a] = Rk[a * cpb];
+      for (int a2 = 0; a2 < 5; ++a2) d[a2] = Rk[a2 * cpb] - part[a2];
+      __syncwarp();
+      if (valid && sub == 0) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        S sacc = S(0);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) sacc += Cc[a * 4 + b] * xn[b];
-        d[a] -= sacc;
+        for (int a2 = 0; a2 < 5; ++a2) Rk[a2 * cpb] = d[a2];
       }
-      S sacc = S(0);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) sacc += Cc[16 + b] * xn[b];
-      d[4] -= sacc;
-#pragma unroll
-      for (int a = 0; a < 5; ++a) Rk[a * cpb] = d[a];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) xn[a] = d[a];
+      for (int a2 = 0; a2 < 4; ++a2) xn[a2] = d[a2];
     }
   }
   __syncthreads();
@@ -675,7 +733,7 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, v
                          227 * 1024);
     attr_set = true;
   }
-  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 128, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, (S*)factors);
+  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 256, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, (S*)factors);
 }
 
 template <class T>

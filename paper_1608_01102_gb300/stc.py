@@ -271,6 +271,9 @@ class Problem:
         _check(self.lib.stc_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def taylor_kmax(self):
+        return self.params.taylor_kmax
+
     def memory_bytes(self):
         b = c_size_t()
         _check(self.lib.stc_memory_bytes(self.h, ctypes.byref(b)))
@@ -292,3 +295,4 @@ class Problem:
             self.close()
         except Exception:
             pass
+

@@ -43,7 +43,7 @@ def test_projection(prec, shape):
 # a3: forward advection (Taylor exponential, adaptive order)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", PREC)
-@pytest.mark.parametrize("shape,N", [((16, 16), 6), ((24, 12), 5), ((32, 32), 8)])
+@pytest.mark.parametrize("shape,N", [((16, 16), 6), ((24, 12), 5), ((32, 32), 8), ((32, 24), 4), ((12, 8), 3)])
 def test_forward_advection(prec, shape, N):
     nx, ny = shape
     P, G = make_pair(nx, ny, N=N, precision=prec)
@@ -65,7 +65,8 @@ def test_forward_advection(prec, shape, N):
 # a5 / a6 / a7: keyframe metric, backward adjoint sweep, v*-gradient
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", PREC)
-@pytest.mark.parametrize("shape,N,levels", [((16, 16), 6, 2), ((24, 12), 5, 1), ((32, 32), 6, 3)])
+@pytest.mark.parametrize("shape,N,levels", [((16, 16), 6, 2), ((24, 12), 5, 1), ((32, 32), 6, 3),
+                                            ((32, 24), 4, 2), ((12, 8), 3, 1)])
 def test_adjoint_sweep(prec, shape, N, levels):
     nx, ny = shape
     star_mid = workloads.gaussian_ball(nx, ny, (0.4, 0.5 * ny / nx), 0.1)
