@@ -238,6 +238,37 @@ stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* 
 /* Device memory held by the problem, in bytes. */
 stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes);
 
+/* ---- allocation-free entry point ------------------------------------------- */
+
+/* The backward adjoint sweep of stc_adjoint on caller-owned device arrays,
+ * allocating nothing.  The paper has no counterpart: this exists for callers
+ * that cannot allocate device memory when they run the sweep -- a process that
+ * reserves its whole device-memory budget up front in its own pool (so a later
+ * cudaMalloc fails or is forbidden), or a latency-critical caller that cannot
+ * afford cudaMalloc's implicit device synchronisation.
+ *
+ * fp32 arrays on the device, layouts as the fields of the same names:
+ * vel = the advecting velocity (N face slabs), rho = densities (N+1 cell
+ * slabs), K = the Taylor orders of the forward sweep (N ints), mterm =
+ * C_i (rho_i - rho*_i) (N+1 cell slabs, fp64), mu = output adjoint (N cell
+ * slabs), base = N face slabs or NULL, out = output face slabs: slab i =
+ * alpha base_i + beta (dA[rho_i, vel_i]/dvel_i)^T mu_i for i = 1..N-1 (slab 0
+ * is not written).  Enqueued on cuda_stream (NULL = legacy default stream).
+ *
+ * Scratch: the sweep's Taylor powers live in one library-wide device array of
+ * 1,048,576 floats (4 MiB) that every GPU loading the library holds until the
+ * process exits.  taylor_kmax * nx * ny above that returns STC_ERR_INVALID_ARG
+ * with a message.  Every call shares the array and it keeps the last call's
+ * contents (nothing needs to start at zero), so calls that overlap on the GPU
+ * race: serialise them.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, double dt, int taylor_kmax,
+                                     const float* vel, const float* rho, const int* K, const double* mterm,
+                                     float* mu, const float* base, double alpha, double beta, float* out,
+                                     void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,9 @@
 // cluster-wide max |t_k|, so all CTAs take the same decision.
 #include <cooperative_groups.h>
 
+#include <mutex>
+
+#include "../../include/stc.h"
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
 
@@ -600,6 +603,97 @@ cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, con
                   (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax};
   return cluster_launch(taylor_adjoint_kernel<T>, adv_layout<T>(g, true).total, st, args);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the backward adjoint sweep.
+//
+// Some callers cannot allocate device memory when they need this sweep: a
+// process that reserves its whole device-memory budget up front in its own
+// pool (so a later cudaMalloc fails or is forbidden), or a latency-critical
+// caller that cannot afford cudaMalloc's implicit device synchronisation.
+// For them the sweep's only scratch -- the Taylor powers A^m rho_s, taylor_kmax
+// cell fields -- lives in this file-scope device array instead of a buffer the
+// problem allocates.  It is modest (4 MiB) and, being a module global, it is
+// held on every GPU that loads the library until the process exits.  All
+// calls share it, so calls that overlap on the GPU race; nothing in it needs
+// to start at zero (each power is written before it is read).
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocPowersFloats = (size_t)1 << 20;
+static __device__ __align__(256) float g_noalloc_powers[kNoAllocPowersFloats];
+
+namespace {
+std::mutex g_noalloc_mutex;
+constexpr int kNoAllocMaxDevices = 256;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+// Device address of g_noalloc_powers on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, not a device address).
+static cudaError_t noalloc_powers(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_powers);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace stc
+
+extern "C" stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, double dt, int taylor_kmax,
+                                                const float* vel, const float* rho, const int* K,
+                                                const double* mterm, float* mu, const float* base, double alpha,
+                                                double beta, float* out, void* cuda_stream) {
+  using namespace stc;
+  if (nx < 2 || ny < 2 || num_steps < 1 || !(dt > 0.0) || taylor_kmax < 1 || taylor_kmax > 256 || !vel || !rho ||
+      !K || !mterm || !mu || !out) {
+    set_last_error("stc_adjoint_sweep_noalloc: invalid argument");
+    return STC_ERR_INVALID_ARG;
+  }
+  const size_t need = (size_t)taylor_kmax * (size_t)nx * (size_t)ny;
+  if (need > kNoAllocPowersFloats) {
+    set_last_error("stc_adjoint_sweep_noalloc: taylor_kmax * nx * ny exceeds the fixed scratch of 1048576 floats");
+    return STC_ERR_INVALID_ARG;
+  }
+  Geom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.N = num_steps;
+  g.Fx = ny * (nx + 1);
+  g.F = g.Fx + (ny + 1) * nx;
+  g.C = nx * ny;
+  g.h = 1.0 / nx;
+  g.ih = (double)nx;
+  g.dt = dt;
+  g.idt = 1.0 / dt;
+  g.a = 0.0;
+  g.lm = 0.0;
+  g.omega = 1.0;
+  g.self_adv = 1;
+  if (!advect_supported(g)) {
+    set_last_error("stc_adjoint_sweep_noalloc: grid too large for the on-chip sweep");
+    return STC_ERR_UNSUPPORTED;
+  }
+  float* scratch = nullptr;
+  cudaError_t e = noalloc_powers(&scratch);
+  if (e == cudaSuccess)
+    e = launch_taylor_adjoint<float>(g, vel, rho, K, mterm, mu, base, float(alpha), float(beta), out, scratch,
+                                     taylor_kmax, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return STC_ERR_CUDA;
+  }
+  return STC_OK;
+}
+
+namespace stc {
 
 #define STC_ADV_INST(T)                                                                                         \
   template cudaError_t launch_taylor_forward<T>(const Geom&, const T*, T*, int*, double, int, int*,           \

@@ -68,6 +68,8 @@ void ck(cudaError_t e, const char* what) {
 
 }  // namespace
 
+void stc::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct stc_problem {
   stc_params prm;
   cudaStream_t st = nullptr;      // user stream (may be the legacy default)

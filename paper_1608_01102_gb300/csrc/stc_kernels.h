@@ -5,6 +5,9 @@
 
 namespace stc {
 
+// thread-local message returned by stc_last_error()
+void set_last_error(const char* msg);
+
 // --- NSO (nso_kernels.cu) ---------------------------------------------------
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,

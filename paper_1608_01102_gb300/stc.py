@@ -73,6 +73,9 @@ SIGNATURES = {
     "stc_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "stc_kernel_timing": (c_int, [c_void_p, P_double, ctypes.POINTER(ctypes.c_longlong)]),
     "stc_memory_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
+    "stc_adjoint_sweep_noalloc": (c_int, [c_int, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p,
+                                          c_void_p]),
 }
 
 _lib = None
@@ -296,3 +299,16 @@ class Problem:
         except Exception:
             pass
 
+
+def adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vel, rho, K, mterm, mu, base, alpha, beta, out,
+                          stream=None):
+    """stc_adjoint_sweep_noalloc on device pointers (ints, e.g. tensor.data_ptr()).
+
+    For callers that cannot allocate device memory at the call (a fixed,
+    pre-reserved device-memory budget, or no tolerance for cudaMalloc's implicit
+    synchronisation): the library allocates nothing here; its only scratch is a
+    fixed 4 MiB device array shared by all calls, so overlapping calls race."""
+    lib = load()
+    vp = lambda p: c_void_p(int(p)) if p else None
+    _check(lib.stc_adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vp(vel), vp(rho), vp(K), vp(mterm), vp(mu),
+                                         vp(base), alpha, beta, vp(out), vp(stream)))
