@@ -222,72 +222,66 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
   }
 }
 
-// Solve A x = b for a symmetric definite 4x4 A (either sign) by LDL^T without
-// pivoting (A is factorised in the caller's copy).
-template <class T>
-__device__ __forceinline__ void ldlt_solve4(T A[4][4], const T b[4], T x[4]) {
-  T dinv[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    T d = A[k][k];
-#pragma unroll
-    for (int s = 0; s < k; ++s) d -= A[k][s] * A[k][s] * A[s][s];
-    A[k][k] = d;
-    const T id = T(1) / d;
-    dinv[k] = id;
-#pragma unroll
-    for (int r = k + 1; r < 4; ++r) {
-      T l = A[r][k];
-#pragma unroll
-      for (int s = 0; s < k; ++s) l -= A[r][s] * A[k][s] * A[s][s];
-      A[r][k] = l * id;
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    T s = b[r];
-#pragma unroll
-    for (int k = 0; k < r; ++k) s -= A[r][k] * x[k];
-    x[r] = s;
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) x[r] *= dinv[r];
-#pragma unroll
-  for (int r = 3; r >= 0; --r) {
-    T s = x[r];
-#pragma unroll
-    for (int k = r + 1; k < 4; ++k) s -= A[k][r] * x[k];
-    x[r] = s;
-  }
-}
+// One CTA smooths `cpb` cells of one colour.  Block order of a cell's time
+// column: B_u(0), B_v(1), B_u(1), ..., B_u(N-1), B_v(N).  Every u block
+// D_u = [[-I, g], [g^T, 0]] has the closed-form inverse
+//   [[-P, gh], [gh^T, 1/|g|^2]],  P = I - g g^T / |g|^2,  gh = g / |g|^2
+// (on the cell's active faces), so all u blocks are eliminated at once and the
+// sequential block-Thomas recurrence runs over the N v blocks only:
+//   S_t  = (a_t + lm) I + [t<N] P / dt^2 + U_{t-1}^T P U_{t-1}     (v_t pivot face block)
+//   O_t  = -P U_t / dt                                            (v_t -> v_{t+1} coupling)
+//   R_t  = b_v(t) + [t<N] y_t / dt - U_{t-1}^T y_{t-1}            (faces; y = D_u^{-1} b_u)
+// with U_t = I/dt + dAdv_loc(v_{t+1}).  Phases:
+//  A (parallel over cells x timesteps): U_t, b_u(t), b_v(t+1) into shared memory;
+//  A2 (parallel): y_t, S_t, R_t;
+//  B (one thread per cell): Thomas over v_1..v_N (factors C'_t to an L2-resident
+//    global buffer, prefetched in back substitution); each pivot is a saddle
+//    block [[S, g], [g^T, 0]] solved by LDL^T of S + gamma g g^T (an exact
+//    identity: it leaves x unchanged and shifts the multiplier by gamma q)
+//    plus a Schur step on g;
+//  C (parallel): u_t = y_t + D_u^{-1} [v_t/dt - U_t v_{t+1}; 0]; x += omega delta.
+// Shared arrays are interleaved with the cell index fastest.  State type T and
+// solve type S: the fp32 mode's fp64 coarsest level solves in fp32.
+__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)36 * N; }
 
-// One CTA smooths `cpb` cells of one colour in three phases:
-//  A (parallel over cells x timesteps): the coupling U_t = I/dt + dAdv_loc(v_{t+1})
-//    and the right-hand sides of both blocks of timestep t are assembled into
-//    shared memory -- all global loads happen here, off the sequential path;
-//  B (8 lanes per cell): block Thomas over the 2N blocks, reading U and the
-//    right-hand sides from shared memory; the elimination factors C'_k go to an
-//    L2-resident global buffer (written on the forward chain, prefetched one
-//    step ahead during back substitution), the solution overwrites the
-//    right-hand sides;
-//  C (parallel over cells x blocks): x += omega * delta written back.
-// Shared arrays are interleaved with the cell index fastest ([t][comp][cell]),
-// so the chains of one warp read consecutive banks.  State type T (the level's
-// storage) and solve type S: the coarsest level of the fp32 mode keeps its
-// state and residuals in fp64 (T = double) and solves the per-cell correction
-// in fp32 (S = float); elsewhere S = T.
-__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)16 * N + (size_t)5 * 2 * N; }
+// per-cell constants: active-face flags, g = d(grad p)/dp_c, P = I - g g^T/|g|^2
+template <class S>
+struct CellG {
+  S act[4], g[4], gh[4], ig2;
+  __device__ void init(const Geom& geo, int i, int j) {
+    act[0] = S(i > 0);
+    act[1] = S(i < geo.nx - 1);
+    act[2] = S(j > 0);
+    act[3] = S(j < geo.ny - 1);
+    g[0] = act[0] * S(geo.ih);
+    g[1] = -act[1] * S(geo.ih);
+    g[2] = act[2] * S(geo.ih);
+    g[3] = -act[3] * S(geo.ih);
+    S g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + g[3] * g[3];
+    ig2 = S(1) / g2;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) gh[a] = g[a] * ig2;
+  }
+  // P w on the active faces (zero on inactive ones)
+  __device__ __forceinline__ void proj(const S w[4], S out[4]) const {
+    S d = g[0] * w[0] + g[1] * w[1] + g[2] * w[2] + g[3] * w[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) out[a] = act[a] * w[a] - gh[a] * d;
+  }
+};
 
 template <class T, class S>
 __global__ void __launch_bounds__(256)
 scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb, S* __restrict__ cfac) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
-  const int nb = 2 * N;
   const int ncell = ncx * ncy;
   const int q0 = blockIdx.x * cpb;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // [N][16][cpb]
-  S* Rs = Us + (size_t)N * 16 * cpb;                  // [2N][5][cpb]
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t       [N][16][cpb]
+  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u(t) -> y_t -> u solution  [N][5][cpb]
+  S* Bv = Bu + (size_t)N * 5 * cpb;                   // b_v(t+1) -> R -> d' -> v solution [N][5][cpb]
+  S* Ss = Bv + (size_t)N * 5 * cpb;                   // S_{t+1} (upper triangle, 10) [N][10][cpb]
+  const S idt = S(g.idt);
 
   // ---- phase A: couplings and right-hand sides ----------------------------
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
@@ -303,219 +297,304 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
     S* U = Us + (size_t)t * 16 * cpb + c;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
-      for (int b = 0; b < 4; ++b)
-        U[(a * 4 + b) * cpb] = S(((a == b ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a][b]) * act[a] * act[b]);
-    S* Ru = Rs + (size_t)(2 * t) * 5 * cpb + c;        // B_u(t)
-    S* Rv = Ru + (size_t)5 * cpb;                      // B_v(t+1)
+      for (int b2 = 0; b2 < 4; ++b2)
+        U[(a2 * 4 + b2) * cpb] =
+            S(((a2 == b2 ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2]);
+    S* Ru = Bu + (size_t)t * 5 * cpb + c;
+    S* Rv = Bv + (size_t)t * 5 * cpb + c;
     const T* ru = r.u + (size_t)t * g.F;
     const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      Ru[a * cpb] = S(-ld(ru + fidx[a]) * act[a]);
-      Rv[a * cpb] = S(-ld(rv + fidx[a]) * act[a]);
+    for (int a2 = 0; a2 < 4; ++a2) {
+      Ru[a2 * cpb] = S(-ld(ru + fidx[a2]) * act[a2]);
+      Rv[a2 * cpb] = S(-ld(rv + fidx[a2]) * act[a2]);
     }
     Ru[4 * cpb] = S(-ld(r.p + (size_t)t * g.C + cc));
     Rv[4 * cpb] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
   }
   __syncthreads();
 
-  // ---- phase B: block Thomas in time, 8 lanes per cell ---------------------
-  // Lane `sub` of a cell's group owns column `sub` of [C'_k | d'_k] (sub < 5)
-  // and of the right-hand side block [U_k | r_k | g] (sub < 6); the 4x4 pivot
-  // block is gathered by shuffles and factorised redundantly on every lane.
-  if ((int)(threadIdx.x >> 5) * 4 < cpb) {
-    const unsigned full = 0xffffffffu;
-    const int sub = threadIdx.x & 7;
-    const int c = threadIdx.x >> 3;
+  // ---- phase A2: eliminate the u blocks ------------------------------------
+  // (a) y_t = D_u^{-1} b_u(t) in place
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
     const int q = q0 + c;
-    const bool valid = c < cpb && q < ncell;
-    const int cs = valid ? c : 0;   // shared-memory slot read by idle groups (never written)
-    int i = 0, j = 0;
-    if (valid) {
-      i = 2 * (q % ncx) + (colour & 1);
-      j = 2 * (q / ncx) + (colour >> 1);
+    if (q >= ncell) continue;
+    CellG<S> cg_;
+    cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+    S* Ru = Bu + (size_t)t * 5 * cpb + c;
+    S bf[4], pb[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) bf[a2] = Ru[a2 * cpb];
+    const S bp = Ru[4 * cpb];
+    cg_.proj(bf, pb);
+    S gb = S(0);
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) gb += cg_.gh[a2] * bf[a2];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) Ru[a2 * cpb] = -pb[a2] + cg_.gh[a2] * bp;
+    Ru[4 * cpb] = gb + bp * cg_.ig2;
+  }
+  __syncthreads();
+  // (b) S_{t+1}, R_{t+1} for the v block t+1 (index t = 0..N-1)
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;   // v block t+1
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    CellG<S> cg_;
+    cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+    const int tv = t + 1;
+    const S* U = Us + (size_t)t * 16 * cpb + c;     // U_{tv-1}
+    S Um[4][4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) Um[a2][b2] = U[(a2 * 4 + b2) * cpb];
+    // P U_{tv-1} column by column, then U^T (P U)
+    S PU[4][4];
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) {
+      S w[4], pw[4];
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) w[a2] = Um[a2][b2];
+      cg_.proj(w, pw);
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) PU[a2][b2] = pw[a2];
     }
-    const S idt = S(g.idt);
-    S act[4];
-    if (valid) {
-      act[0] = S(i > 0);
-      act[1] = S(i < g.nx - 1);
-      act[2] = S(j > 0);
-      act[3] = S(j < g.ny - 1);
-    } else {
-      act[0] = act[1] = act[2] = act[3] = S(1);
-    }
-    const S gv[4] = {act[0] * S(g.ih), -act[1] * S(g.ih), act[2] * S(g.ih), -act[3] * S(g.ih)};
-    S* cf = cfac + (valid ? q : 0);
-    const size_t kstride = (size_t)20 * ncell;
-    S prev[4] = {S(0), S(0), S(0), S(0)};   // column `sub` of [C'_{k-1} | d'_{k-1}] (faces)
-    for (int k = 0; k < nb; ++k) {
-      const bool ublk = (k % 2) == 0;
-      const int t = ublk ? k / 2 : (k + 1) / 2;
-      const S diag = ublk ? S(-1) : ((t < N ? S(g.a) : S(0)) + S(g.lm));
-      const S* Rk = Rs + (size_t)k * 5 * cpb + cs;
-      // this lane's column of [D_k | r_k] (face rows)
-      S col[4];
+    const S diag = (tv < N ? S(g.a) : S(0)) + S(g.lm);
+    S* Sd = Ss + (size_t)t * 10 * cpb + c;
+    int e = 0;
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-        if (sub < 4) col[a2] = (a2 == sub) ? (act[a2] > S(0) ? diag : S(1)) : S(0);
-        else if (sub == 4) col[a2] = Rk[a2 * cpb];
-        else col[a2] = S(0);
-      }
-      const S q4 = Rk[4 * cpb];
-      // minus the lower coupling times the previous factor column
-      if (k >= 1) {
-        if (ublk) {
-          // J[B_u(t), B_v(t)] = -I/dt
+    for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) col[a2] += idt * act[a2] * prev[a2];
-        } else {
-          // J[B_v(t), B_u(t-1)] = U_{t-1}^T
-          const S* Up = Us + (size_t)(t - 1) * 16 * cpb + cs;
+      for (int b2 = a2; b2 < 4; ++b2) {
+        S v = S(0);
 #pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) {
-            S acc = S(0);
-#pragma unroll
-            for (int c2 = 0; c2 < 4; ++c2) acc += Up[(c2 * 4 + a2) * cpb] * prev[c2];
-            col[a2] -= acc;
-          }
+        for (int c2 = 0; c2 < 4; ++c2) v += Um[c2][a2] * PU[c2][b2];
+        if (tv < N) {
+          // + P / dt^2
+          const S pab = (a2 == b2 ? cg_.act[a2] : S(0)) - cg_.gh[a2] * cg_.g[b2];
+          v += pab * idt * idt;
         }
+        if (a2 == b2) v += cg_.act[a2] > S(0) ? diag : S(1);
+        Sd[e * cpb] = v;
+        ++e;
       }
-      // gather the pivot face block A (column b lives on lane b)
+    // R = b_v + [tv<N] y_tv / dt - U_{tv-1}^T y_{tv-1}
+    S* Rv = Bv + (size_t)t * 5 * cpb + c;
+    const S* y0 = Bu + (size_t)t * 5 * cpb + c;   // y_{tv-1}
+    S yv[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) yv[a2] = y0[a2 * cpb];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      S v = Rv[a2 * cpb];
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) v -= Um[c2][a2] * yv[c2];
+      if (tv < N) v += idt * cg_.act[a2] * Bu[((size_t)tv * 5 + a2) * cpb + c];
+      Rv[a2 * cpb] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: block Thomas over the v blocks, one thread per cell --------
+  if ((int)threadIdx.x < cpb && q0 + (int)threadIdx.x < ncell) {
+    const int c = threadIdx.x;
+    const int q = q0 + c;
+    CellG<S> cg_;
+    cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+    S* cf = cfac + q;
+    const size_t kstride = (size_t)20 * ncell;
+    S Cprev[4][4];   // face rows of C'_{t-1} (columns: the faces of v_t)
+    S dprev[4];
+    S Oprev[4][4];   // O_{t-1}
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      dprev[a2] = S(0);
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) Cprev[a2][b2] = Oprev[a2][b2] = S(0);
+    }
+    for (int t = 0; t < N; ++t) {   // v block tv = t + 1
+      const S* Sd = Ss + (size_t)t * 10 * cpb + c;
       S A[4][4];
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb)
-#pragma unroll
-        for (int a2 = 0; a2 < 4; ++a2) A[a2][bb] = __shfl_sync(full, col[a2], bb, 8);
+      int e = 0;
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
-        for (int bb = a2 + 1; bb < 4; ++bb) {
-          const S m = S(0.5) * (A[a2][bb] + A[bb][a2]);
-          A[a2][bb] = m;
-          A[bb][a2] = m;
+        for (int b2 = a2; b2 < 4; ++b2) {
+          A[a2][b2] = Sd[e * cpb];
+          A[b2][a2] = A[a2][b2];
+          ++e;
         }
-      // this lane's right-hand side: U_k column (sub < 4), r_k (4), g (5)
-      S bcol[4];
-      S qc = S(0);
+      S* Rk = Bv + (size_t)t * 5 * cpb + c;
+      S B[4][5];
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-        if (sub < 4) {
-          if (k < nb - 1) {
-            if (ublk) bcol[a2] = Us[((size_t)t * 16 + a2 * 4 + sub) * cpb + cs];
-            else bcol[a2] = (a2 == sub) ? -idt * act[a2] : S(0);
-          } else {
-            bcol[a2] = S(0);
+      for (int a2 = 0; a2 < 4; ++a2) B[a2][4] = Rk[a2 * cpb];
+      const S q4 = Rk[4 * cpb];
+      if (t >= 1) {
+        // A -= O_{t-1}^T C'_{t-1},  rhs -= O_{t-1}^T d'_{t-1}
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) {
+          S sacc = S(0);
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) {
+            sacc += Oprev[b2][a2] * dprev[b2];
+            S acc = S(0);
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) acc += Oprev[c2][a2] * Cprev[c2][b2];
+            A[a2][b2] -= acc;
           }
-        } else if (sub == 4) {
-          bcol[a2] = col[a2];
-        } else {
-          bcol[a2] = gv[a2];
+          B[a2][4] -= sacc;
         }
       }
-      if (sub == 4) qc = q4;
-      S X[4];
-      ldlt_solve4(A, bcol, X);
-      S Xg[4];
+      // upper coupling O_t = -P U_t / dt (v_{t+1} -> v_{t+2}), none for the last block
+      S Ot[4][4];
+      if (t + 1 < N) {
+        const S* U = Us + (size_t)(t + 1) * 16 * cpb + c;
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) Xg[a2] = __shfl_sync(full, X[a2], 5, 8);
-      S sgg = S(0), sgb = S(0);
+        for (int b2 = 0; b2 < 4; ++b2) {
+          S w[4], pw[4];
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) w[a2] = U[(a2 * 4 + b2) * cpb];
+          cg_.proj(w, pw);
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) Ot[a2][b2] = -idt * pw[a2];
+        }
+      } else {
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) Ot[a2][b2] = S(0);
+      }
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) B[a2][b2] = Ot[a2][b2];
+      // symmetrise and shift along g (exact identity, see above)
+      S tr = S(0);
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) tr += A[a2][a2];
+      const S gam = S(0.25) * tr * cg_.ig2;
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int b2 = a2; b2 < 4; ++b2) {
+          const S m = S(0.5) * (A[a2][b2] + A[b2][a2]) + gam * cg_.g[a2] * cg_.g[b2];
+          A[a2][b2] = m;
+          A[b2][a2] = m;
+        }
+      S Y[5];
+      saddle_solve(A, cg_.g, B, q4, Y);
+      // undo the shift on the multiplier: y = y' + gamma q
+      Y[4] += gam * q4;
+      S* Ck = cf + (size_t)t * kstride;
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2) {
-        sgg += gv[a2] * Xg[a2];
-        sgb += gv[a2] * X[a2];
-      }
-      const S y = (sgb - qc) * (S(1) / sgg);
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) prev[a2] = X[a2] - Xg[a2] * y;
-      if (valid) {
-        if (sub < 4) {
-          S* Ck = cf + (size_t)k * kstride + (size_t)(sub * 5) * ncell;
-#pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) Ck[(size_t)a2 * ncell] = prev[a2];
-          Ck[(size_t)4 * ncell] = y;
-        } else if (sub == 4) {
-          S* Rw = Rs + (size_t)k * 5 * cpb + c;
-#pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) Rw[a2 * cpb] = prev[a2];
-          Rw[4 * cpb] = y;
+        for (int b2 = 0; b2 < 4; ++b2) {
+          Ck[(size_t)(a2 * 4 + b2) * ncell] = B[a2][b2];
+          Cprev[a2][b2] = B[a2][b2];
+          Oprev[a2][b2] = Ot[a2][b2];
         }
+        Rk[a2 * cpb] = B[a2][4];
+        dprev[a2] = B[a2][4];
       }
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) Ck[(size_t)(16 + b2) * ncell] = Y[b2];
+      Rk[4 * cpb] = Y[4];
     }
-    __syncwarp();
-    // back substitution: x_k = d'_k - C'_k x_{k+1}; lane b (< 4) holds column b
-    // of C'_k, prefetched one step ahead; the sum over b is a shuffle reduction
+    // back substitution over the v blocks: x_t = d'_t - C'_t x_{t+1}
     S xn[4];
     {
-      const S* Rl = Rs + (size_t)(nb - 1) * 5 * cpb + cs;
+      const S* Rl = Bv + (size_t)(N - 1) * 5 * cpb + c;
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2) xn[a2] = Rl[a2 * cpb];
     }
-    S Cn[5] = {S(0), S(0), S(0), S(0), S(0)};
-    if (nb >= 2 && sub < 4) {
-      const S* Ck = cf + (size_t)(nb - 2) * kstride + (size_t)(sub * 5) * ncell;
+    S Cn[20];
+    if (N >= 2) {
+      const S* Ck = cf + (size_t)(N - 2) * kstride;
 #pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) Cn[a2] = Ck[(size_t)a2 * ncell];
+      for (int e2 = 0; e2 < 20; ++e2) Cn[e2] = Ck[(size_t)e2 * ncell];
     }
-    for (int k = nb - 2; k >= 0; --k) {
-      S Cc[5];
+    for (int t = N - 2; t >= 0; --t) {
+      S Cc[20];
 #pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) Cc[a2] = Cn[a2];
-      if (k >= 1 && sub < 4) {
-        const S* Ck = cf + (size_t)(k - 1) * kstride + (size_t)(sub * 5) * ncell;
+      for (int e2 = 0; e2 < 20; ++e2) Cc[e2] = Cn[e2];
+      if (t >= 1) {
+        const S* Ck = cf + (size_t)(t - 1) * kstride;
 #pragma unroll
-        for (int a2 = 0; a2 < 5; ++a2) Cn[a2] = Ck[(size_t)a2 * ncell];
+        for (int e2 = 0; e2 < 20; ++e2) Cn[e2] = Ck[(size_t)e2 * ncell];
       }
-      // lane sub < 4 contributes column sub times x_{k+1}[sub]
-      S xs = xn[0];
-#pragma unroll
-      for (int a2 = 1; a2 < 4; ++a2) xs = (sub == a2) ? xn[a2] : xs;
-      S part[5];
-#pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) part[a2] = (sub < 4) ? Cc[a2] * xs : S(0);
-#pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) {
-        part[a2] += __shfl_xor_sync(full, part[a2], 1, 8);
-        part[a2] += __shfl_xor_sync(full, part[a2], 2, 8);
-        part[a2] = __shfl_sync(full, part[a2], 0, 8);
-      }
-      S* Rk = Rs + (size_t)k * 5 * cpb + cs;
+      S* Rk = Bv + (size_t)t * 5 * cpb + c;
       S d[5];
 #pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) d[a2] = Rk[a2 * cpb] - part[a2];
-      __syncwarp();
-      if (valid && sub == 0) {
+      for (int a2 = 0; a2 < 5; ++a2) d[a2] = Rk[a2 * cpb];
 #pragma unroll
-        for (int a2 = 0; a2 < 5; ++a2) Rk[a2 * cpb] = d[a2];
+      for (int a2 = 0; a2 < 4; ++a2) {
+        S sacc = S(0);
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) sacc += Cc[a2 * 4 + b2] * xn[b2];
+        d[a2] -= sacc;
       }
+      S sacc = S(0);
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) sacc += Cc[16 + b2] * xn[b2];
+      d[4] -= sacc;
+#pragma unroll
+      for (int a2 = 0; a2 < 5; ++a2) Rk[a2 * cpb] = d[a2];
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2) xn[a2] = d[a2];
     }
   }
   __syncthreads();
 
-  // ---- phase C: x += omega * delta -----------------------------------------
+  // ---- phase C: u blocks from the v solution, x += omega * delta -----------
   const T om = T(g.omega);
-  for (int item = threadIdx.x; item < cpb * nb; item += blockDim.x) {
-    const int c = item % cpb, k = item / cpb;
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
     const int q = q0 + c;
     if (q >= ncell) continue;
     const int i = 2 * (q % ncx) + (colour & 1);
     const int j = 2 * (q / ncx) + (colour >> 1);
-    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
-    const bool act[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
-    const int cc = cidx(g, j, i);
-    const S* d = Rs + (size_t)k * 5 * cpb + c;
-    const bool ublk = (k % 2) == 0;
-    const int t = ublk ? k / 2 : (k + 1) / 2;
-    T* fu = ublk ? x.u + (size_t)t * g.F : x.v + (size_t)t * g.F;
-    T* cu = ublk ? x.p + (size_t)t * g.C : x.pbar + (size_t)t * g.C;
+    CellG<S> cg_;
+    cg_.init(g, i, j);
+    // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
+    const S* U = Us + (size_t)t * 16 * cpb + c;
+    const S* xv1 = Bv + (size_t)t * 5 * cpb + c;          // v_{t+1}
+    S w[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-      if (act[a]) fu[fidx[a]] += om * T(d[a * cpb]);
-    cu[cc] += om * T(d[4 * cpb]);
+    for (int a2 = 0; a2 < 4; ++a2) {
+      S v = S(0);
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) v -= U[(a2 * 4 + b2) * cpb] * xv1[b2 * cpb];
+      if (t >= 1) v += idt * cg_.act[a2] * Bv[((size_t)(t - 1) * 5 + a2) * cpb + c];
+      w[a2] = v;
+    }
+    S pw[4];
+    cg_.proj(w, pw);
+    S gw = S(0);
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) gw += cg_.gh[a2] * w[a2];
+    const S* y = Bu + (size_t)t * 5 * cpb + c;
+    S du[5];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
+    du[4] = y[4 * cpb] + gw;
+    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+    const bool actb[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
+    const int cc = cidx(g, j, i);
+    T* fu = x.u + (size_t)t * g.F;
+    T* fv = x.v + (size_t)(t + 1) * g.F;
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+      if (actb[a2]) {
+        fu[fidx[a2]] += om * T(du[a2]);
+        fv[fidx[a2]] += om * T(xv1[a2 * cpb]);
+      }
+    x.p[(size_t)t * g.C + cc] += om * T(du[4]);
+    x.pbar[(size_t)(t + 1) * g.C + cc] += om * T(xv1[4 * cpb]);
   }
 }
 
@@ -754,7 +833,7 @@ size_t scgs_factor_bytes(int nx, int ny, int N, size_t ssize) {
     const int n = colour_extent(nx, c & 1) * colour_extent(ny, c >> 1);
     maxcell = n > maxcell ? n : maxcell;
   }
-  return (size_t)maxcell * 2 * N * 20 * ssize;
+  return (size_t)maxcell * N * 20 * ssize;
 }
 
 template <class Tf, class Tc>
