@@ -154,13 +154,12 @@ __device__ void local_adv_jac(const Geom& g, const T* v, int j, int i, T J[4][4]
   }
 }
 
-// Solve [[A, gv],[gv^T, 0]] [X; y] = [Bm; q] for 5 right-hand sides
-// (columns 0..3 of Bm with q = 0, column 4 with q = q4).  A is 4x4 symmetric
-// definite (either sign): LDL^T without pivoting.
-template <class T>
-__device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5], T q4, T Y[5]) {
-  // LDL^T in place: A = L D L^T, L unit lower (stored below the diagonal), D on
-  // the diagonal; the reciprocals of D are kept so that the solves multiply
+// Solve [[A, g], [g^T, 0]] [X; y] = [B; q] for NC right-hand sides.  A is the
+// 4x4 symmetric face block, definite (either sign): LDL^T without pivoting,
+// solves for the NC columns and for g, then the Schur step on g.  On return B
+// holds X and Y holds y.
+template <class T, int NC>
+__device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][NC], const T q[NC], T Y[NC]) {
   T dinv[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -178,16 +177,15 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
       A[r][k] = l * id;
     }
   }
-  // solve A X = [B | gv] (6 columns: 5 rhs + g)
-  T X[4][6];
+  T X[4][NC + 1];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) X[r][c] = B[r][c];
-    X[r][5] = gv[r];
+    for (int c = 0; c < NC; ++c) X[r][c] = B[r][c];
+    X[r][NC] = gv[r];
   }
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
+  for (int c = 0; c <= NC; ++c) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       T s = X[r][c];
@@ -205,20 +203,19 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
       X[r][c] = s;
     }
   }
-  // Schur step: y = (g^T A^{-1} b - q) / (g^T A^{-1} g); x = A^{-1} b - A^{-1} g y
   T sgg = T(0);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) sgg += gv[r] * X[r][5];
-  T isgg = T(1) / sgg;
+  for (int r = 0; r < 4; ++r) sgg += gv[r] * X[r][NC];
+  const T isgg = T(1) / sgg;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < NC; ++c) {
     T sgb = T(0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) sgb += gv[r] * X[r][c];
-    T y = (sgb - (c == 4 ? q4 : T(0))) * isgg;
+    const T y = (sgb - q[c]) * isgg;
     Y[c] = y;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) B[r][c] = X[r][c] - X[r][5] * y;
+    for (int r = 0; r < 4; ++r) B[r][c] = X[r][c] - X[r][NC] * y;
   }
 }
 
@@ -226,23 +223,28 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][5]
 // column: B_u(0), B_v(1), B_u(1), ..., B_u(N-1), B_v(N).  Every u block
 // D_u = [[-I, g], [g^T, 0]] has the closed-form inverse
 //   [[-P, gh], [gh^T, 1/|g|^2]],  P = I - g g^T / |g|^2,  gh = g / |g|^2
-// (on the cell's active faces), so all u blocks are eliminated at once and the
-// sequential block-Thomas recurrence runs over the N v blocks only:
+// (on the cell's active faces), so all u blocks are eliminated at once,
+// leaving a symmetric block-tridiagonal system over the N v blocks:
 //   S_t  = (a_t + lm) I + [t<N] P / dt^2 + U_{t-1}^T P U_{t-1}     (v_t pivot face block)
 //   O_t  = -P U_t / dt                                            (v_t -> v_{t+1} coupling)
 //   R_t  = b_v(t) + [t<N] y_t / dt - U_{t-1}^T y_{t-1}            (faces; y = D_u^{-1} b_u)
-// with U_t = I/dt + dAdv_loc(v_{t+1}).  Phases:
+// with U_t = I/dt + dAdv_loc(v_{t+1}).  That system is solved by cyclic
+// reduction: at stride s the blocks j = s, 3s, 5s, ... are eliminated in
+// parallel (each a saddle solve with 9 right-hand sides: its left and right
+// couplings and its right-hand side), then the blocks j = 0, 2s, 4s, ...
+// gather both neighbours' contributions; after log2(N) levels block 0 is
+// solved and the levels are unwound.  Each saddle pivot is solved after an
+// exact gamma g g^T shift of its face block (x unchanged, multiplier shifted
+// by gamma q) that keeps the block definite.  Phases:
 //  A (parallel over cells x timesteps): U_t, b_u(t), b_v(t+1) into shared memory;
-//  A2 (parallel): y_t, S_t, R_t;
-//  B (one thread per cell): Thomas over v_1..v_N (factors C'_t to an L2-resident
-//    global buffer, prefetched in back substitution); each pivot is a saddle
-//    block [[S, g], [g^T, 0]] solved by LDL^T of S + gamma g g^T (an exact
-//    identity: it leaves x unchanged and shifts the multiplier by gamma q)
-//    plus a Schur step on g;
+//  A2 (parallel): y_t; the v blocks' S, R and couplings;
+//  B (one warp per cell, one lane per block): the cyclic reduction;
 //  C (parallel): u_t = y_t + D_u^{-1} [v_t/dt - U_t v_{t+1}; 0]; x += omega delta.
-// Shared arrays are interleaved with the cell index fastest.  State type T and
-// solve type S: the fp32 mode's fp64 coarsest level solves in fp32.
-__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)36 * N; }
+// State type T and solve type S: the fp32 mode's fp64 coarsest level solves in fp32.
+constexpr int kCrStride = 77;   // per-block record, odd so a warp's lanes hit distinct banks
+enum : int { CR_A = 0, CR_R = 10, CR_C = 15, CR_ZL = 31, CR_ZR = 51, CR_Z = 71 };
+
+__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)(16 + 5 + kCrStride) * N; }
 
 // per-cell constants: active-face flags, g = d(grad p)/dp_c, P = I - g g^T/|g|^2
 template <class S>
@@ -270,17 +272,57 @@ struct CellG {
   }
 };
 
+template <class S>
+__device__ __forceinline__ void load_sym(const S* v, S A[4][4]) {
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      A[a][b] = v[e];
+      A[b][a] = v[e];
+      ++e;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void store_sym(S* v, const S A[4][4]) {
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      v[e] = S(0.5) * (A[a][b] + A[b][a]);
+      ++e;
+    }
+}
+
+// shift A by gamma g g^T (gamma from the trace) and symmetrise; returns gamma
+template <class S>
+__device__ __forceinline__ S shift_sym(S A[4][4], const CellG<S>& cg) {
+  S tr = A[0][0] + A[1][1] + A[2][2] + A[3][3];
+  const S gam = S(0.25) * tr * cg.ig2;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a; b < 4; ++b) {
+      const S m = S(0.5) * (A[a][b] + A[b][a]) + gam * cg.g[a] * cg.g[b];
+      A[a][b] = m;
+      A[b][a] = m;
+    }
+  return gam;
+}
+
 template <class T, class S>
 __global__ void __launch_bounds__(256)
-scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb, S* __restrict__ cfac) {
+scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
   const int ncell = ncx * ncy;
   const int q0 = blockIdx.x * cpb;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t       [N][16][cpb]
-  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u(t) -> y_t -> u solution  [N][5][cpb]
-  S* Bv = Bu + (size_t)N * 5 * cpb;                   // b_v(t+1) -> R -> d' -> v solution [N][5][cpb]
-  S* Ss = Bv + (size_t)N * 5 * cpb;                   // S_{t+1} (upper triangle, 10) [N][10][cpb]
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
+  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u -> y_t [N][5][cpb]
+  S* Vb = Bu + (size_t)N * 5 * cpb;                   // v blocks   [cpb][N][kCrStride]
   const S idt = S(g.idt);
 
   // ---- phase A: couplings and right-hand sides ----------------------------
@@ -303,16 +345,16 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
         U[(a2 * 4 + b2) * cpb] =
             S(((a2 == b2 ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2]);
     S* Ru = Bu + (size_t)t * 5 * cpb + c;
-    S* Rv = Bv + (size_t)t * 5 * cpb + c;
+    S* Rv = Vb + ((size_t)c * N + t) * kCrStride + CR_R;
     const T* ru = r.u + (size_t)t * g.F;
     const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) {
       Ru[a2 * cpb] = S(-ld(ru + fidx[a2]) * act[a2]);
-      Rv[a2 * cpb] = S(-ld(rv + fidx[a2]) * act[a2]);
+      Rv[a2] = S(-ld(rv + fidx[a2]) * act[a2]);
     }
     Ru[4 * cpb] = S(-ld(r.p + (size_t)t * g.C + cc));
-    Rv[4 * cpb] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
+    Rv[4] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
   }
   __syncthreads();
 
@@ -338,21 +380,21 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     Ru[4 * cpb] = gb + bp * cg_.ig2;
   }
   __syncthreads();
-  // (b) S_{t+1}, R_{t+1} for the v block t+1 (index t = 0..N-1)
+  // (b) v block j = t (v_{t+1}): S, R, and its upper coupling O_{t+1} = -P U_{t+1} / dt
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
-    const int c = item % cpb, t = item / cpb;   // v block t+1
+    const int c = item % cpb, t = item / cpb;
     const int q = q0 + c;
     if (q >= ncell) continue;
     CellG<S> cg_;
     cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
     const int tv = t + 1;
+    S* V = Vb + ((size_t)c * N + t) * kCrStride;
     const S* U = Us + (size_t)t * 16 * cpb + c;     // U_{tv-1}
     S Um[4][4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
       for (int b2 = 0; b2 < 4; ++b2) Um[a2][b2] = U[(a2 * 4 + b2) * cpb];
-    // P U_{tv-1} column by column, then U^T (P U)
     S PU[4][4];
 #pragma unroll
     for (int b2 = 0; b2 < 4; ++b2) {
@@ -364,7 +406,6 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
       for (int a2 = 0; a2 < 4; ++a2) PU[a2][b2] = pw[a2];
     }
     const S diag = (tv < N ? S(g.a) : S(0)) + S(g.lm);
-    S* Sd = Ss + (size_t)t * 10 * cpb + c;
     int e = 0;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
@@ -373,179 +414,204 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
         S v = S(0);
 #pragma unroll
         for (int c2 = 0; c2 < 4; ++c2) v += Um[c2][a2] * PU[c2][b2];
-        if (tv < N) {
-          // + P / dt^2
-          const S pab = (a2 == b2 ? cg_.act[a2] : S(0)) - cg_.gh[a2] * cg_.g[b2];
-          v += pab * idt * idt;
-        }
+        if (tv < N) v += ((a2 == b2 ? cg_.act[a2] : S(0)) - cg_.gh[a2] * cg_.g[b2]) * idt * idt;
         if (a2 == b2) v += cg_.act[a2] > S(0) ? diag : S(1);
-        Sd[e * cpb] = v;
+        V[CR_A + e] = v;
         ++e;
       }
     // R = b_v + [tv<N] y_tv / dt - U_{tv-1}^T y_{tv-1}
-    S* Rv = Bv + (size_t)t * 5 * cpb + c;
-    const S* y0 = Bu + (size_t)t * 5 * cpb + c;   // y_{tv-1}
+    const S* y0 = Bu + (size_t)t * 5 * cpb + c;
     S yv[4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) yv[a2] = y0[a2 * cpb];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) {
-      S v = Rv[a2 * cpb];
+      S v = V[CR_R + a2];
 #pragma unroll
       for (int c2 = 0; c2 < 4; ++c2) v -= Um[c2][a2] * yv[c2];
       if (tv < N) v += idt * cg_.act[a2] * Bu[((size_t)tv * 5 + a2) * cpb + c];
-      Rv[a2 * cpb] = v;
+      V[CR_R + a2] = v;
+    }
+    // coupling to v_{tv+1}: O_tv = -P U_tv / dt
+    if (tv < N) {
+      const S* U1 = Us + (size_t)tv * 16 * cpb + c;
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) {
+        S w[4], pw[4];
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) w[a2] = U1[(a2 * 4 + b2) * cpb];
+        cg_.proj(w, pw);
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) V[CR_C + a2 * 4 + b2] = -idt * pw[a2];
+      }
+    } else {
+#pragma unroll
+      for (int e2 = 0; e2 < 16; ++e2) V[CR_C + e2] = S(0);
     }
   }
   __syncthreads();
 
-  // ---- phase B: block Thomas over the v blocks, one thread per cell --------
-  if ((int)threadIdx.x < cpb && q0 + (int)threadIdx.x < ncell) {
-    const int c = threadIdx.x;
-    const int q = q0 + c;
-    CellG<S> cg_;
-    cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
-    S* cf = cfac + q;
-    const size_t kstride = (size_t)20 * ncell;
-    S Cprev[4][4];   // face rows of C'_{t-1} (columns: the faces of v_t)
-    S dprev[4];
-    S Oprev[4][4];   // O_{t-1}
+  // ---- phase B: cyclic reduction over the v blocks, one warp per cell -------
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = q0 + warp;
+    if (warp < cpb && q < ncell) {
+      CellG<S> cg_;
+      cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+      S* V = Vb + (size_t)warp * N * kCrStride;
+      int top = 0;
+      for (int s2 = 1; s2 < N; s2 <<= 1) {
+        top = s2;
+        // eliminate the odd blocks o = s2 (2m + 1)
+        for (int m = lane;; m += 32) {
+          const int o = s2 * (2 * m + 1);
+          if (o >= N) break;
+          const bool hasb = o + s2 < N;
+          S* Vo = V + (size_t)o * kCrStride;
+          const S* Va = V + (size_t)(o - s2) * kCrStride;
+          S A[4][4];
+          load_sym(Vo + CR_A, A);
+          S B[4][9];
+          S qv[9];
 #pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2) {
-      dprev[a2] = S(0);
+          for (int r2 = 0; r2 < 4; ++r2) {
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) Cprev[a2][b2] = Oprev[a2][b2] = S(0);
-    }
-    for (int t = 0; t < N; ++t) {   // v block tv = t + 1
-      const S* Sd = Ss + (size_t)t * 10 * cpb + c;
-      S A[4][4];
-      int e = 0;
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2)
-#pragma unroll
-        for (int b2 = a2; b2 < 4; ++b2) {
-          A[a2][b2] = Sd[e * cpb];
-          A[b2][a2] = A[a2][b2];
-          ++e;
-        }
-      S* Rk = Bv + (size_t)t * 5 * cpb + c;
-      S B[4][5];
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) B[a2][4] = Rk[a2 * cpb];
-      const S q4 = Rk[4 * cpb];
-      if (t >= 1) {
-        // A -= O_{t-1}^T C'_{t-1},  rhs -= O_{t-1}^T d'_{t-1}
-#pragma unroll
-        for (int a2 = 0; a2 < 4; ++a2) {
-          S sacc = S(0);
-#pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) {
-            sacc += Oprev[b2][a2] * dprev[b2];
-            S acc = S(0);
-#pragma unroll
-            for (int c2 = 0; c2 < 4; ++c2) acc += Oprev[c2][a2] * Cprev[c2][b2];
-            A[a2][b2] -= acc;
+            for (int c2 = 0; c2 < 4; ++c2) {
+              B[r2][c2] = Va[CR_C + c2 * 4 + r2];                  // (coupling a -> o)^T
+              B[r2][4 + c2] = hasb ? Vo[CR_C + r2 * 4 + c2] : S(0);  // coupling o -> b
+            }
+            B[r2][8] = Vo[CR_R + r2];
           }
-          B[a2][4] -= sacc;
+#pragma unroll
+          for (int c2 = 0; c2 < 8; ++c2) qv[c2] = S(0);
+          qv[8] = Vo[CR_R + 4];
+          const S gam = shift_sym(A, cg_);
+          S Y[9];
+          saddle_solve<S, 9>(A, cg_.g, B, qv, Y);
+          Y[8] += gam * qv[8];
+#pragma unroll
+          for (int c2 = 0; c2 < 4; ++c2) {
+#pragma unroll
+            for (int r2 = 0; r2 < 4; ++r2) {
+              Vo[CR_ZL + r2 * 4 + c2] = B[r2][c2];
+              Vo[CR_ZR + r2 * 4 + c2] = B[r2][4 + c2];
+            }
+            Vo[CR_ZL + 16 + c2] = Y[c2];
+            Vo[CR_ZR + 16 + c2] = Y[4 + c2];
+          }
+#pragma unroll
+          for (int r2 = 0; r2 < 4; ++r2) Vo[CR_Z + r2] = B[r2][8];
+          Vo[CR_Z + 4] = Y[8];
         }
-      }
-      // upper coupling O_t = -P U_t / dt (v_{t+1} -> v_{t+2}), none for the last block
-      S Ot[4][4];
-      if (t + 1 < N) {
-        const S* U = Us + (size_t)(t + 1) * 16 * cpb + c;
+        __syncwarp();
+        // update the even blocks e = 2 s2 m from both eliminated neighbours
+        for (int m = lane;; m += 32) {
+          const int e = 2 * s2 * m;
+          if (e >= N) break;
+          S* Ve = V + (size_t)e * kCrStride;
+          S A[4][4];
+          load_sym(Ve + CR_A, A);
+          S rf[4], Ce[4][4], Cn[4][4];
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) {
-          S w[4], pw[4];
+          for (int r2 = 0; r2 < 4; ++r2) {
+            rf[r2] = Ve[CR_R + r2];
 #pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) w[a2] = U[(a2 * 4 + b2) * cpb];
-          cg_.proj(w, pw);
+            for (int c2 = 0; c2 < 4; ++c2) {
+              Ce[r2][c2] = Ve[CR_C + r2 * 4 + c2];
+              Cn[r2][c2] = S(0);
+            }
+          }
+          const int o2 = e + s2;
+          if (o2 < N) {
+            const S* V2 = V + (size_t)o2 * kCrStride;
+            const bool hasb2 = o2 + s2 < N;
 #pragma unroll
-          for (int a2 = 0; a2 < 4; ++a2) Ot[a2][b2] = -idt * pw[a2];
+            for (int r2 = 0; r2 < 4; ++r2) {
+#pragma unroll
+              for (int c2 = 0; c2 < 4; ++c2) {
+                S aL = S(0), aR = S(0);
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) {
+                  aL += Ce[r2][k2] * V2[CR_ZL + k2 * 4 + c2];
+                  aR += Ce[r2][k2] * V2[CR_ZR + k2 * 4 + c2];
+                }
+                A[r2][c2] -= aL;
+                Cn[r2][c2] = hasb2 ? -aR : S(0);
+              }
+              S az = S(0);
+#pragma unroll
+              for (int k2 = 0; k2 < 4; ++k2) az += Ce[r2][k2] * V2[CR_Z + k2];
+              rf[r2] -= az;
+            }
+          }
+          const int o1 = e - s2;
+          if (o1 >= 0) {
+            const S* V1 = V + (size_t)o1 * kCrStride;
+#pragma unroll
+            for (int r2 = 0; r2 < 4; ++r2) {
+#pragma unroll
+              for (int c2 = 0; c2 < 4; ++c2) {
+                S aR = S(0);
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) aR += V1[CR_C + k2 * 4 + r2] * V1[CR_ZR + k2 * 4 + c2];
+                A[r2][c2] -= aR;
+              }
+              S az = S(0);
+#pragma unroll
+              for (int k2 = 0; k2 < 4; ++k2) az += V1[CR_C + k2 * 4 + r2] * V1[CR_Z + k2];
+              rf[r2] -= az;
+            }
+          }
+          store_sym(Ve + CR_A, A);
+#pragma unroll
+          for (int r2 = 0; r2 < 4; ++r2) {
+            Ve[CR_R + r2] = rf[r2];
+#pragma unroll
+            for (int c2 = 0; c2 < 4; ++c2) Ve[CR_C + r2 * 4 + c2] = Cn[r2][c2];
+          }
         }
-      } else {
-#pragma unroll
-        for (int a2 = 0; a2 < 4; ++a2)
-#pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) Ot[a2][b2] = S(0);
+        __syncwarp();
       }
+      // the last remaining block
+      if (lane == 0) {
+        S A[4][4];
+        load_sym(V + CR_A, A);
+        S B[4][1];
+        S qv[1] = {V[CR_R + 4]};
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2)
+        for (int r2 = 0; r2 < 4; ++r2) B[r2][0] = V[CR_R + r2];
+        const S gam = shift_sym(A, cg_);
+        S Y[1];
+        saddle_solve<S, 1>(A, cg_.g, B, qv, Y);
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) B[a2][b2] = Ot[a2][b2];
-      // symmetrise and shift along g (exact identity, see above)
-      S tr = S(0);
+        for (int r2 = 0; r2 < 4; ++r2) V[CR_Z + r2] = B[r2][0];
+        V[CR_Z + 4] = Y[0] + gam * qv[0];
+      }
+      __syncwarp();
+      // unwind: x_o = z_o - ZL_o x_a - ZR_o x_b (faces of the neighbours)
+      for (int s2 = top; s2 >= 1; s2 >>= 1) {
+        for (int m = lane;; m += 32) {
+          const int o = s2 * (2 * m + 1);
+          if (o >= N) break;
+          S* Vo = V + (size_t)o * kCrStride;
+          const S* Va = V + (size_t)(o - s2) * kCrStride;
+          const bool hasb = o + s2 < N;
+          S xa[4], xb[4];
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) tr += A[a2][a2];
-      const S gam = S(0.25) * tr * cg_.ig2;
+          for (int k2 = 0; k2 < 4; ++k2) {
+            xa[k2] = Va[CR_Z + k2];
+            xb[k2] = hasb ? V[(size_t)(o + s2) * kCrStride + CR_Z + k2] : S(0);
+          }
 #pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2)
+          for (int r2 = 0; r2 < 5; ++r2) {
+            S v = Vo[CR_Z + r2];
 #pragma unroll
-        for (int b2 = a2; b2 < 4; ++b2) {
-          const S m = S(0.5) * (A[a2][b2] + A[b2][a2]) + gam * cg_.g[a2] * cg_.g[b2];
-          A[a2][b2] = m;
-          A[b2][a2] = m;
+            for (int k2 = 0; k2 < 4; ++k2) v -= Vo[CR_ZL + r2 * 4 + k2] * xa[k2] + Vo[CR_ZR + r2 * 4 + k2] * xb[k2];
+            Vo[CR_Z + r2] = v;
+          }
         }
-      S Y[5];
-      saddle_solve(A, cg_.g, B, q4, Y);
-      // undo the shift on the multiplier: y = y' + gamma q
-      Y[4] += gam * q4;
-      S* Ck = cf + (size_t)t * kstride;
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) {
-          Ck[(size_t)(a2 * 4 + b2) * ncell] = B[a2][b2];
-          Cprev[a2][b2] = B[a2][b2];
-          Oprev[a2][b2] = Ot[a2][b2];
-        }
-        Rk[a2 * cpb] = B[a2][4];
-        dprev[a2] = B[a2][4];
+        __syncwarp();
       }
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) Ck[(size_t)(16 + b2) * ncell] = Y[b2];
-      Rk[4 * cpb] = Y[4];
-    }
-    // back substitution over the v blocks: x_t = d'_t - C'_t x_{t+1}
-    S xn[4];
-    {
-      const S* Rl = Bv + (size_t)(N - 1) * 5 * cpb + c;
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) xn[a2] = Rl[a2 * cpb];
-    }
-    S Cn[20];
-    if (N >= 2) {
-      const S* Ck = cf + (size_t)(N - 2) * kstride;
-#pragma unroll
-      for (int e2 = 0; e2 < 20; ++e2) Cn[e2] = Ck[(size_t)e2 * ncell];
-    }
-    for (int t = N - 2; t >= 0; --t) {
-      S Cc[20];
-#pragma unroll
-      for (int e2 = 0; e2 < 20; ++e2) Cc[e2] = Cn[e2];
-      if (t >= 1) {
-        const S* Ck = cf + (size_t)(t - 1) * kstride;
-#pragma unroll
-        for (int e2 = 0; e2 < 20; ++e2) Cn[e2] = Ck[(size_t)e2 * ncell];
-      }
-      S* Rk = Bv + (size_t)t * 5 * cpb + c;
-      S d[5];
-#pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) d[a2] = Rk[a2 * cpb];
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-        S sacc = S(0);
-#pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) sacc += Cc[a2 * 4 + b2] * xn[b2];
-        d[a2] -= sacc;
-      }
-      S sacc = S(0);
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) sacc += Cc[16 + b2] * xn[b2];
-      d[4] -= sacc;
-#pragma unroll
-      for (int a2 = 0; a2 < 5; ++a2) Rk[a2 * cpb] = d[a2];
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) xn[a2] = d[a2];
     }
   }
   __syncthreads();
@@ -562,14 +628,15 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     cg_.init(g, i, j);
     // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
     const S* U = Us + (size_t)t * 16 * cpb + c;
-    const S* xv1 = Bv + (size_t)t * 5 * cpb + c;          // v_{t+1}
+    const S* xv1 = Vb + ((size_t)c * N + t) * kCrStride + CR_Z;          // v_{t+1}
+    const S* xv0 = Vb + ((size_t)c * N + (t > 0 ? t - 1 : 0)) * kCrStride + CR_Z;   // v_t
     S w[4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) {
       S v = S(0);
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) v -= U[(a2 * 4 + b2) * cpb] * xv1[b2 * cpb];
-      if (t >= 1) v += idt * cg_.act[a2] * Bv[((size_t)(t - 1) * 5 + a2) * cpb + c];
+      for (int b2 = 0; b2 < 4; ++b2) v -= U[(a2 * 4 + b2) * cpb] * xv1[b2];
+      if (t >= 1) v += idt * cg_.act[a2] * xv0[a2];
       w[a2] = v;
     }
     S pw[4];
@@ -591,10 +658,10 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     for (int a2 = 0; a2 < 4; ++a2)
       if (actb[a2]) {
         fu[fidx[a2]] += om * T(du[a2]);
-        fv[fidx[a2]] += om * T(xv1[a2 * cpb]);
+        fv[fidx[a2]] += om * T(xv1[a2]);
       }
     x.p[(size_t)t * g.C + cc] += om * T(du[4]);
-    x.pbar[(size_t)(t + 1) * g.C + cc] += om * T(xv1[4 * cpb]);
+    x.pbar[(size_t)(t + 1) * g.C + cc] += om * T(xv1[4]);
   }
 }
 
@@ -791,15 +858,15 @@ int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 
 template <class S>
 int scgs_cells_per_cta(int N) {
-  // ~110 KB of shared memory per CTA (two CTAs per SM), at most 32 cells
+  // one warp per cell, at most 8 per CTA; ~110 KB of shared memory per CTA
   const size_t per = scgs_cell_floats(N) * sizeof(S);
   int c = (int)((110 * 1024) / per);
-  if (c > 32) c = 32;
+  if (c > 8) c = 8;
   return c < 1 ? 1 : c;
 }
 
 template <class T, class S>
-static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, void* factors, cudaStream_t st) {
+static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, cudaStream_t st) {
   const int ncx = colour_extent(g.nx, colour & 1);
   const int ncy = colour_extent(g.ny, colour >> 1);
   const int ncell = ncx * ncy;
@@ -812,28 +879,18 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, v
                          227 * 1024);
     attr_set = true;
   }
-  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 256, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, (S*)factors);
+  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 32 * cpb, sm, st>>>(g, x, r, colour, ncx, ncy, cpb);
 }
 
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, void* factors,
-                        cudaStream_t st) {
-  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, factors, st);
-  else launch_scgs_ts<T, T>(g, x, r, colour, factors, st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st) {
+  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, st);
+  else launch_scgs_ts<T, T>(g, x, r, colour, st);
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
   return tsize == 4 ? (size_t)scgs_cells_per_cta<float>(N) * scgs_cell_floats(N) * 4
                     : (size_t)scgs_cells_per_cta<double>(N) * scgs_cell_floats(N) * 8;
-}
-
-size_t scgs_factor_bytes(int nx, int ny, int N, size_t ssize) {
-  int maxcell = 0;
-  for (int c = 0; c < 4; ++c) {
-    const int n = colour_extent(nx, c & 1) * colour_extent(ny, c >> 1);
-    maxcell = n > maxcell ? n : maxcell;
-  }
-  return (size_t)maxcell * N * 20 * ssize;
 }
 
 template <class Tf, class Tc>
@@ -906,7 +963,7 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
                                        cudaStream_t);                                                      \
-  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, void*, cudaStream_t);    \
+  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t);           \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
   template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
   template void launch_remove_mean<T>(T*, int, int, cudaStream_t);

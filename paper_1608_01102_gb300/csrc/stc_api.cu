@@ -37,7 +37,6 @@ struct Level {
   bool dbl = false;
   FieldSet x, res, tmp, old;
   void* z = nullptr;
-  void* factors = nullptr;  // block-Thomas factors of the smoother (scratch)
 };
 
 template <class T>
@@ -180,7 +179,7 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
-        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, L.factors, st);
+        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st);
       });
       if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
       count(P, 1);
@@ -703,7 +702,7 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       const size_t solve_size = P->dbl ? 8 : 4;   // fp32 mode solves corrections in fp32 on every level
       if (scgs_smem_bytes(N, solve_size) > (size_t)smem_optin)
         fail(STC_ERR_UNSUPPORTED, "too many timesteps for the shared-memory SCGS solve");
-      L.factors = dalloc(P, scgs_factor_bytes(L.g.nx, L.g.ny, N, solve_size));
+
       P->lv.push_back(L);
     }
     const size_t F = g0.F, C = g0.C, ts = P->ts;

@@ -13,11 +13,8 @@ template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
                          cudaStream_t st);
 template <class T>
-// factors: global buffer of scgs_factor_bytes() for the block-Thomas factors
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, void* factors,
-                        cudaStream_t st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st);
 size_t scgs_smem_bytes(int N, size_t tsize);
-size_t scgs_factor_bytes(int nx, int ny, int N, size_t ssize);
 int colour_extent(int n, int parity);
 template <class Tf, class Tc>
 void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
