@@ -26,101 +26,172 @@ struct Slab {
 
 __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
-// QUICK face value (Leonard): upwind U, downwind D, far-upwind UU; v = 0 gives
-// the mean of both one-sided values (subgradient convention).
+// QUICK (Leonard) coefficients of one face between cells lo and hi: the
+// weights of (lo, hi, lo-1, hi+1) in the face value, the far cells clamped at
+// the walls.  v > 0: upwind lo; v < 0: upwind hi; v = 0: the mean of both
+// one-sided stencils (the subgradient used for d/dv at v = 0).
 template <class T>
-__device__ __forceinline__ T quick(T vel, T tL, T tR, T tLL, T tRR) {
-  const T pos = (T(6) * tL + T(3) * tR - tLL) * T(0.125);
-  const T neg = (T(6) * tR + T(3) * tL - tRR) * T(0.125);
-  if (vel > T(0)) return pos;
-  if (vel < T(0)) return neg;
-  return T(0.5) * (pos + neg);
+__device__ __forceinline__ void quick_coef(T v, T c[4]) {
+  const bool pos = v > T(0), neg = v < T(0);
+  c[0] = pos ? T(0.75) : (neg ? T(0.375) : T(0.5625));
+  c[1] = pos ? T(0.375) : (neg ? T(0.75) : T(0.5625));
+  c[2] = pos ? T(-0.125) : (neg ? T(0) : T(-0.0625));
+  c[3] = pos ? T(0) : (neg ? T(-0.125) : T(-0.0625));
 }
 
-// buffer with halo: row jj (clamped to the grid) of a slab buffer
+// row jj (clamped to the grid) of a slab buffer with a 2-row halo
 template <class T>
-__device__ __forceinline__ T buf_at(const Geom& g, const Slab& s, const T* b, int jj, int ii) {
+__device__ __forceinline__ const T* buf_row(const Geom& g, const Slab& s, const T* b, int jj) {
   jj = clampi(jj, 0, g.ny - 1);
-  ii = clampi(ii, 0, g.nx - 1);
-  return b[(jj - s.r0 + 2) * g.nx + ii];
+  return b + (jj - s.r0 + 2) * g.nx;
 }
 
-// (A(v) t)_c at own cell (j,i); vxs holds x-faces of rows [r0, r1),
-// vys y-faces of rows [r0 - 1, r0 + rpc + 1] (offset 1).
+// Face arrays of a slab: x-faces of the owned rows [r0, r1) (all columns),
+// y-faces of rows [r0 - 1, r0 + rpc + 1] (row index offset by 1).
+__device__ __forceinline__ int nxf(const Geom& g, const Slab& s) { return s.rpc * (g.nx + 1); }
+__device__ __forceinline__ int nyf(const Geom& g, const Slab& s) { return (s.rpc + 3) * g.nx; }
+
 template <class T>
-__device__ T apply_A(const Geom& g, const Slab& s, const T* b, const T* vxs, const T* vys, int j, int i) {
-  T fl = T(0), fr = T(0), fb = T(0), ft = T(0);
-  const int lr = j - s.r0;
-  if (i >= 1) {
-    T v = vxs[lr * (g.nx + 1) + i];
-    if (v != T(0))
-      fl = v * quick(v, buf_at(g, s, b, j, i - 1), buf_at(g, s, b, j, i), buf_at(g, s, b, j, i - 2),
-                     buf_at(g, s, b, j, i + 1));
+__device__ void load_velocity(const Geom& g, const Slab& s, const T* vel, T* vx, T* vy) {
+  const int nx = g.nx;
+  for (int e = threadIdx.x; e < nxf(g, s); e += blockDim.x) {
+    const int j = s.r0 + e / (nx + 1);
+    vx[e] = (j < s.r1) ? vel[(size_t)s.r0 * (nx + 1) + e] : T(0);
   }
-  if (i + 1 <= g.nx - 1) {
-    T v = vxs[lr * (g.nx + 1) + i + 1];
-    if (v != T(0))
-      fr = v * quick(v, buf_at(g, s, b, j, i), buf_at(g, s, b, j, i + 1), buf_at(g, s, b, j, i - 1),
-                     buf_at(g, s, b, j, i + 2));
+  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x) {
+    const int jf = s.r0 - 1 + e / nx, i = e % nx;
+    vy[e] = (jf >= 0 && jf <= g.ny && s.r1 > s.r0) ? vel[g.Fx + (size_t)jf * nx + i] : T(0);
   }
-  if (j >= 1) {
-    T v = vys[(j - s.r0 + 1) * g.nx + i];
-    if (v != T(0))
-      fb = v * quick(v, buf_at(g, s, b, j - 1, i), buf_at(g, s, b, j, i), buf_at(g, s, b, j - 2, i),
-                     buf_at(g, s, b, j + 1, i));
-  }
-  if (j + 1 <= g.ny - 1) {
-    T v = vys[(j + 1 - s.r0 + 1) * g.nx + i];
-    if (v != T(0))
-      ft = v * quick(v, buf_at(g, s, b, j, i), buf_at(g, s, b, j + 1, i), buf_at(g, s, b, j - 1, i),
-                     buf_at(g, s, b, j + 2, i));
-  }
-  return -T(g.ih) * (fr - fl + ft - fb);
 }
 
-// weight of cell c in the QUICK stencil of the face between cells lo = f-1 and
-// hi = f (along one axis of n cells) for velocity sign of v
+// fluxes F_f = v_f * QUICK(t)_f on the faces the owned cells need
 template <class T>
-__device__ __forceinline__ T quick_weight(T v, int f, int c, int n) {
-  const int lo = f - 1, hi = f;
-  T w = T(0);
-  if (v > T(0)) {
-    if (lo == c) w += T(0.75);
-    if (hi == c) w += T(0.375);
-    if (clampi(f - 2, 0, n - 1) == c) w -= T(0.125);
-  } else if (v < T(0)) {
-    if (hi == c) w += T(0.75);
-    if (lo == c) w += T(0.375);
-    if (clampi(f + 1, 0, n - 1) == c) w -= T(0.125);
+__device__ void face_fluxes(const Geom& g, const Slab& s, const T* t, const T* vx, const T* vy, T* Fx, T* Fy) {
+  const int nx = g.nx;
+  const int nown = s.r1 - s.r0;
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
+    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+    T F = T(0);
+    const T v = vx[e];
+    if (i >= 1 && i <= nx - 1 && v != T(0)) {
+      T c[4];
+      quick_coef(v, c);
+      const T* row = buf_row(g, s, t, j);
+      F = v * (c[0] * row[i - 1] + c[1] * row[i] + c[2] * row[max(i - 2, 0)] + c[3] * row[min(i + 1, nx - 1)]);
+    }
+    Fx[e] = F;
   }
-  return w;
+  // y-faces r0 .. r1 (local rows 1 .. nown + 1)
+  for (int e = threadIdx.x; e < (nown + 1) * nx; e += blockDim.x) {
+    const int jf = s.r0 + e / nx, i = e % nx;
+    const int le = e + nx;
+    T F = T(0);
+    const T v = vy[le];
+    if (jf >= 1 && jf <= g.ny - 1 && v != T(0)) {
+      T c[4];
+      quick_coef(v, c);
+      F = v * (c[0] * buf_row(g, s, t, jf - 1)[i] + c[1] * buf_row(g, s, t, jf)[i] +
+               c[2] * buf_row(g, s, t, jf - 2)[i] + c[3] * buf_row(g, s, t, jf + 1)[i]);
+    }
+    Fy[le] = F;
+  }
 }
 
-// (A(v)^T w)_c at own cell (j,i): A^T = -R_up^T diag(v) D^T, so each face f
-// whose upwind stencil contains c contributes weight * v_f * (w_hi - w_lo)/h.
+// (A t)_c = -(1/h) sum_a (F_{c+1/2} - F_{c-1/2}) at owned cell e (slab-local index)
 template <class T>
-__device__ T apply_AT(const Geom& g, const Slab& s, const T* b, const T* vxs, const T* vys, int j, int i) {
-  T acc = T(0);
-  const int lr = j - s.r0;
-#pragma unroll
-  for (int d = -1; d <= 2; ++d) {
-    const int f = i + d;
-    if (f >= 1 && f <= g.nx - 1) {
-      T v = vxs[lr * (g.nx + 1) + f];
-      T w = quick_weight(v, f, i, g.nx);
-      if (w != T(0)) acc += w * v * (buf_at(g, s, b, j, f) - buf_at(g, s, b, j, f - 1));
+__device__ __forceinline__ T flux_divergence(const Geom& g, const T* Fx, const T* Fy, int e) {
+  const int nx = g.nx;
+  const int lj = e / nx, i = e - (e / nx) * nx;
+  const int xr = lj * (nx + 1) + i;
+  const int yr = (lj + 1) * nx + i;
+  return -T(g.ih) * (Fx[xr + 1] - Fx[xr] + Fy[yr + nx] - Fy[yr]);
+}
+
+// E_f = v_f (w_hi - w_lo) / h on the faces within two cells of the owned rows
+template <class T>
+__device__ void face_differences(const Geom& g, const Slab& s, const T* w, const T* vx, const T* vy, T* Ex, T* Ey,
+                                 T* Gx, T* Gy) {
+  const int nx = g.nx;
+  const int nown = s.r1 - s.r0;
+  const T ih = T(g.ih);
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
+    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+    T d = T(0);
+    if (i >= 1 && i <= nx - 1) {
+      const T* row = buf_row(g, s, w, j);
+      d = (row[i] - row[i - 1]) * ih;
+    }
+    Gx[e] = d;
+    Ex[e] = vx[e] * d;
+  }
+  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x) {
+    const int jf = s.r0 - 1 + e / nx, i = e % nx;
+    T d = T(0);
+    if (jf >= 1 && jf <= g.ny - 1 && jf <= s.r1 + 1 && s.r1 > s.r0)
+      d = (buf_row(g, s, w, jf)[i] - buf_row(g, s, w, jf - 1)[i]) * ih;
+    Gy[e] = d;
+    Ey[e] = vy[e] * d;
+  }
+}
+
+// (A^T w)_c = sum over faces f whose QUICK stencil holds c of coef(f, c) E_f;
+// along one axis of n cells, cell i is hi of face i, lo of face i+1, lo-1 of
+// face i+2 and hi+1 of face i-1, plus the wall-clamped extras of faces 1 and n-1.
+template <class T>
+__device__ __forceinline__ T gather_axis(const T* v, const T* E, int stride, int i, int n) {
+  T acc = T(0), c[4];
+  if (i >= 1) { quick_coef(v[i * stride], c); acc += c[1] * E[i * stride]; }
+  if (i + 1 <= n - 1) { quick_coef(v[(i + 1) * stride], c); acc += c[0] * E[(i + 1) * stride]; }
+  if (i + 2 <= n - 1) { quick_coef(v[(i + 2) * stride], c); acc += c[2] * E[(i + 2) * stride]; }
+  if (i - 1 >= 1) { quick_coef(v[(i - 1) * stride], c); acc += c[3] * E[(i - 1) * stride]; }
+  if (i == 0 && n >= 2) { quick_coef(v[stride], c); acc += c[2] * E[stride]; }
+  if (i == n - 1 && n >= 2) { quick_coef(v[(n - 1) * stride], c); acc += c[3] * E[(n - 1) * stride]; }
+  return acc;
+}
+
+template <class T>
+__device__ __forceinline__ T apply_AT_cell(const Geom& g, const Slab& s, const T* vx, const T* vy, const T* Ex,
+                                           const T* Ey, int e) {
+  const int nx = g.nx;
+  const int lj = e / nx, i = e - (e / nx) * nx;
+  const int j = s.r0 + lj;
+  // x: faces of row j, index i' in [0, nx]
+  const T ax = gather_axis(vx + lj * (nx + 1), Ex + lj * (nx + 1), 1, i, nx);
+  // y: faces of column i, face row jf at local row jf - r0 + 1; pass pointers shifted so that
+  // index jf addresses face row jf
+  const T* vyc = vy + (1 - s.r0) * nx + i;
+  const T* Eyc = Ey + (1 - s.r0) * nx + i;
+  const T ay = gather_axis(vyc, Eyc, nx, j, g.ny);
+  return ax + ay;
+}
+
+// B(P)^T at the owned faces: QUICK(P)_f * (w_hi - w_lo)/h, P from global memory
+template <class T>
+__device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const T* vx, const T* vy, const T* Gx,
+                                const T* Gy, T* gxs, T* gys) {
+  const int nx = g.nx;
+  const int nown = s.r1 - s.r0;
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
+    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+    if (i >= 1 && i <= nx - 1) {
+      T c[4];
+      quick_coef(vx[e], c);
+      const T* row = P + (size_t)j * nx;
+      gxs[e] += (c[0] * row[i - 1] + c[1] * row[i] + c[2] * row[max(i - 2, 0)] + c[3] * row[min(i + 1, nx - 1)]) *
+                Gx[e];
     }
   }
-#pragma unroll
-  for (int d = -1; d <= 2; ++d) {
-    const int f = j + d;
-    if (f >= 1 && f <= g.ny - 1) {
-      T v = vys[(f - s.r0 + 1) * g.nx + i];
-      T w = quick_weight(v, f, j, g.ny);
-      if (w != T(0)) acc += w * v * (buf_at(g, s, b, f, i) - buf_at(g, s, b, f - 1, i));
+  for (int e = threadIdx.x; e < nown * nx; e += blockDim.x) {
+    const int jf = s.r0 + e / nx, i = e % nx;
+    if (jf >= 1 && jf <= g.ny - 1) {
+      T c[4];
+      const int le = e + nx;
+      quick_coef(vy[le], c);
+      gys[e] += (c[0] * P[(size_t)(jf - 1) * nx + i] + c[1] * P[(size_t)jf * nx + i] +
+                 c[2] * P[(size_t)max(jf - 2, 0) * nx + i] + c[3] * P[(size_t)min(jf + 1, g.ny - 1) * nx + i]) *
+                Gy[le];
     }
   }
-  return acc * T(g.ih);
 }
 
 // Push this CTA's rows that other CTAs need as halo (rows within 2 of its slab
@@ -154,25 +225,13 @@ __device__ void halo_push(cg::cluster_group& cl, const Geom& g, const Slab& s, T
   }
 }
 
-template <class T>
-__device__ void load_faces(const Geom& g, const Slab& s, const T* vel, T* vxs, T* vys) {
-  const int nx = g.nx;
-  const int nrx = s.r1 - s.r0;
-  for (int e = threadIdx.x; e < nrx * (nx + 1); e += blockDim.x) vxs[e] = vel[(size_t)s.r0 * (nx + 1) + e];
-  // y-face rows [r0 - 1, r1 + 1] clipped to [0, ny]
-  const int nry = s.rpc + 3;
-  for (int e = threadIdx.x; e < nry * nx; e += blockDim.x) {
-    const int q = e / nx, i = e - q * nx;
-    const int jj = s.r0 - 1 + q;
-    vys[e] = (jj >= 0 && jj <= g.ny && s.r1 > s.r0) ? vel[g.Fx + (size_t)jj * nx + i] : T(0);
-  }
-}
-
+// Shared-memory layout of both sweeps (element counts of T arrays, then the
+// fp64 cluster-max slots at a 16-byte-aligned byte offset).
 template <class T>
 struct AdvLayout {
-  size_t buf, vx, vy, gx, gy;  // element counts of the T arrays
-  size_t cm_off;               // byte offset of the fp64 cluster-max slots (16-byte aligned)
-  size_t total;                // bytes
+  size_t buf, fx, fy, gx, gy;
+  size_t cm_off;
+  size_t total;
 };
 
 template <class T>
@@ -180,11 +239,13 @@ __host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) 
   const int rpc = (g.ny + kClusterCTAs - 1) / kClusterCTAs;
   AdvLayout<T> L;
   L.buf = (size_t)(rpc + 4) * g.nx;
-  L.vx = (size_t)rpc * (g.nx + 1);
-  L.vy = (size_t)(rpc + 3) * g.nx;
-  L.gx = adjoint ? (size_t)rpc * (g.nx + 1) : 0;
-  L.gy = adjoint ? (size_t)(rpc + 1) * g.nx : 0;
-  L.cm_off = ((2 * L.buf + L.vx + L.vy + L.gx + L.gy) * sizeof(T) + 15) / 16 * 16;
+  L.fx = (size_t)rpc * (g.nx + 1);
+  L.fy = (size_t)(rpc + 3) * g.nx;
+  L.gx = adjoint ? L.fx : 0;
+  L.gy = adjoint ? L.fy : 0;
+  // tb0, tb1, vx, vy, Fx (E), Fy (E), [Gx, Gy, gxs, gys]
+  const size_t n = 2 * L.buf + 2 * L.fx + 2 * L.fy + (adjoint ? 2 * L.fx + 2 * L.fy : 0);
+  L.cm_off = (n * sizeof(T) + 15) / 16 * 16;
   L.total = L.cm_off + 2 * kClusterCTAs * sizeof(double);
   return L;
 }
@@ -223,8 +284,10 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
   const AdvLayout<T> L = adv_layout<T>(g, false);
   T* tb0 = reinterpret_cast<T*>(smem_raw);
   T* tb1 = tb0 + L.buf;
-  T* vxs = tb1 + L.buf;
-  T* vys = vxs + L.vx;
+  T* vx = tb1 + L.buf;
+  T* vy = vx + L.fx;
+  T* Fx = vy + L.fy;
+  T* Fy = Fx + L.fx;
   double* cmax = reinterpret_cast<double*>(smem_raw + L.cm_off);
   __shared__ double red[32];
   const int nown = (s.r1 - s.r0) * g.nx;
@@ -238,13 +301,13 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
   }
   int kfail = 0;
   for (int st = 0; st < g.N; ++st) {
-    // t_0 = rho_st into tb0 own rows, its halo pushed; faces of v_st
+    // t_0 = rho_st into tb0 own rows, its halo pushed; velocity of step st
 #pragma unroll
     for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
       if (e < nown) tb0[2 * g.nx + e] = acc[q];
     }
-    load_faces(g, s, vel + (size_t)st * g.F, vxs, vys);
+    load_velocity(g, s, vel + (size_t)st * g.F, vx, vy);
     __syncthreads();
     halo_push(cl, g, s, tb0, rank);
     cl.sync();
@@ -253,14 +316,15 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
     int K = kmax;
     bool done = false;
     for (int k = 1; k <= kmax; ++k) {
+      face_fluxes(g, s, cur, vx, vy, Fx, Fy);
+      __syncthreads();
       const T ck = T(g.dt / k);
       double lmax = 0.0;
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
         if (e < nown) {
-          const int j = s.r0 + e / g.nx, i = e % g.nx;
-          const T t = ck * apply_A(g, s, cur, vxs, vys, j, i);
+          const T t = ck * flux_divergence(g, Fx, Fy, e);
           nxt[2 * g.nx + e] = t;
           // two-sum accumulation of the series
           const T sum = acc[q] + t;
@@ -323,10 +387,14 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
   const AdvLayout<T> L = adv_layout<T>(g, true);
   T* tb0 = reinterpret_cast<T*>(smem_raw);
   T* tb1 = tb0 + L.buf;
-  T* vxs = tb1 + L.buf;
-  T* vys = vxs + L.vx;
-  T* gxs = vys + L.vy;
-  T* gys = gxs + L.gx;
+  T* vx = tb1 + L.buf;
+  T* vy = vx + L.fx;
+  T* Ex = vy + L.fy;
+  T* Ey = Ex + L.fx;
+  T* Gx = Ey + L.fy;
+  T* Gy = Gx + L.fx;
+  T* gxs = Gy + L.fy;
+  T* gys = gxs + L.fx;
   const int nx = g.nx;
   const int nown = (s.r1 - s.r0) * nx;
   const int ngx = (s.r1 - s.r0) * (nx + 1);
@@ -351,9 +419,8 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     int K = Ks[st];
     if (K < 1) K = 1;
     if (K > kmax) K = kmax;
-    const T* vs = vel + (size_t)st * g.F;
     const T* rs = rho + (size_t)st * g.C;
-    load_faces(g, s, vs, vxs, vys);
+    load_velocity(g, s, vel + (size_t)st * g.F, vx, vy);
     // powers P_1 .. P_{K-1}
     for (int e = threadIdx.x; e < nown; e += blockDim.x) tb0[2 * nx + e] = rs[(size_t)s.r0 * nx + e];
     __syncthreads();
@@ -362,9 +429,10 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     T* nxt = tb1;
     for (int k = 1; k < K; ++k) {
       cl.sync();
+      face_fluxes(g, s, cur, vx, vy, Ex, Ey);
+      __syncthreads();
       for (int e = threadIdx.x; e < nown; e += blockDim.x) {
-        const int j = s.r0 + e / nx, i = e % nx;
-        const T t = apply_A(g, s, cur, vxs, vys, j, i);
+        const T t = flux_divergence(g, Ex, Ey, e);
         nxt[2 * nx + e] = t;
         powers[(size_t)k * g.C + (size_t)s.r0 * nx + e] = t;
       }
@@ -392,36 +460,16 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     double cm = cK;
     for (int mm = K - 1; mm >= 0; --mm) {
       cl.sync();
-      const T* P = (mm == 0) ? rs : powers + (size_t)mm * g.C;
+      face_differences(g, s, cur, vx, vy, Ex, Ey, Gx, Gy);
+      __syncthreads();
       // grad += B(P_m)^T w_m on own faces
-      for (int e = threadIdx.x; e < ngx; e += blockDim.x) {
-        const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
-        if (i >= 1 && i <= nx - 1) {
-          const T v = vxs[e];
-          const T* Pr = P + (size_t)j * nx;
-          const T xf = quick(v, Pr[i - 1], Pr[i], Pr[clampi(i - 2, 0, nx - 1)], Pr[clampi(i + 1, 0, nx - 1)]);
-          gxs[e] += xf * (buf_at(g, s, cur, j, i) - buf_at(g, s, cur, j, i - 1)) * T(g.ih);
-        }
-      }
-      for (int e = threadIdx.x; e < ngy; e += blockDim.x) {
-        const int j = s.r0 + e / nx, i = e % nx;
-        if (j >= 1 && j <= g.ny - 1) {
-          const T v = vys[(j - s.r0 + 1) * nx + i];
-          const T xf = quick(v, P[(size_t)(j - 1) * nx + i], P[(size_t)j * nx + i],
-                             P[(size_t)clampi(j - 2, 0, g.ny - 1) * nx + i],
-                             P[(size_t)clampi(j + 1, 0, g.ny - 1) * nx + i]);
-          gys[e] += xf * (buf_at(g, s, cur, j, i) - buf_at(g, s, cur, j - 1, i)) * T(g.ih);
-        }
-      }
+      accumulate_grad(g, s, (mm == 0) ? rs : powers + (size_t)mm * g.C, vx, vy, Gx, Gy, gxs, gys);
       // w_{m-1} = c_m mu + A^T w_m with c_m = c_{m+1} (m+1) / dt  (c_0 = 1: T^T mu)
       const double cprev = (mm == 0) ? 1.0 : cm * (mm + 1) / g.dt;
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
-        if (e < nown) {
-          const int j = s.r0 + e / nx, i = e % nx;
-          nxt[2 * nx + e] = T(cprev) * m[q] + apply_AT(g, s, cur, vxs, vys, j, i);
-        }
+        if (e < nown) nxt[2 * nx + e] = T(cprev) * m[q] + apply_AT_cell(g, s, vx, vy, Ex, Ey, e);
       }
       cm = cprev;
       __syncthreads();
