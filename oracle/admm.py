@@ -11,6 +11,21 @@ Readings:
   biases the ADMM fixed point away from the KKT point (the AO gradient is then
   taken at w, not at v*): on an 8^2 x 4 problem the relative KKT residual
   stalled at 0.09 that way, and keeps falling with the warm start.
+* Sec. 5 (convergence analysis) safeguards Alg. 1 by blending: the fixed-point
+  update y = Q(w - dPhi/K) is not taken whole; v* moves to v* + a (y - v*) with
+  a = 1, 1/2, 1/4, ... until the AO objective (Eq. PO) does not increase.  The
+  blend of two solenoidal fields is solenoidal, so no projection follows it.
+  ``P.ao_halvings`` bounds the halvings (default 8); when none of the trials
+  decreases the objective, v* is kept and the remaining AO passes are skipped
+  (they would repeat the same trials).  A trial whose Taylor series does not
+  reach the tolerance within taylor_kmax counts as rejected.  Descent along
+  y - v* is guaranteed only for solenoidal w (as in Alg. 3, where v and lambda
+  are solenoidal); ``ao_halvings = -1`` is the plain Alg. 1
+  (a = 1 always).  Without the blend, K = 1 on 32^2 x 16 sent the AO objective
+  up and down between ADMM iterations and the relative KKT residual climbed to
+  15; with it the same run falls below 1 within 20 iterations.
+* ao() returns the densities and Taylor orders of a forward sweep at the
+  final v* (the blend evaluates them anyway; the plain form runs one more sweep).
 * Alg. 3's inner loop runs at least one V-cycle per ADMM iteration, so that v
   follows every new target; then V-cycles until ||f||_inf <= eps * ||f||_inf
   of the first NSO.
@@ -23,43 +38,101 @@ Readings:
 """
 import numpy as np
 
-from . import kkt, projection, stfas
+from . import advection, kkt, projection, stfas
 
 
-def ao(P, v, lam, iters=None, start=None):
-    """Alg. 1.  Returns (v*, rhos, Ks) -- rhos/Ks from the last forward sweep.
+def ao(P, v, lam, iters=None, start=None, trace=None):
+    """Alg. 1 with Sec. 5's blending safeguard.  Returns (v*, rhos, Ks) with
+    rhos/Ks from a forward sweep at the returned v*.
 
-    ``start``: the v* to continue from (warm start); None initialises v* = w."""
+    ``start``: the v* to continue from (warm start); None initialises v* = w.
+    ``trace``: a list that receives, per AO pass, the number of halvings taken
+    (-1 when every trial was rejected)."""
     iters = P.ao_iters if iters is None else iters
     N = P.N
     w = v[:N] + lam / P.K
     w[0] = P.v0
     vstar = w.copy() if start is None else start.copy()
+    rhos, Ks = kkt.forward_density(P, vstar)
+    J = ao_objective_from(P, w, vstar, rhos)
     for _ in range(iters):
-        rhos, Ks = kkt.forward_density(P, vstar)
         mu = kkt.adjoint_density(P, vstar, rhos, Ks)
         dens = kkt.density_gradient(P, vstar, rhos, Ks, mu)   # -(dA/dv*)^T mu
-        new = vstar.copy()
+        y = vstar.copy()
         for i in range(1, N):
-            new[i] = projection.project(P.grid, w[i] - dens[i] / P.K)
-        vstar = new
+            y[i] = projection.project(P.grid, w[i] - dens[i] / P.K)
+        if P.ao_halvings < 0:                  # plain Alg. 1
+            vstar = y
+            rhos, Ks = kkt.forward_density(P, vstar)
+            J = ao_objective_from(P, w, vstar, rhos)
+            if trace is not None:
+                trace.append(0)
+            continue
+        a, taken = 1.0, -1
+        for h in range(P.ao_halvings + 1):
+            cand = vstar + a * (y - vstar)
+            try:
+                rc, kc = kkt.forward_density(P, cand)
+                Jc = ao_objective_from(P, w, cand, rc)
+            except advection.TaylorOrderError:
+                Jc = np.inf                    # a trial too fast to advect is rejected
+            if Jc <= J:
+                vstar, rhos, Ks, J, taken = cand, rc, kc, Jc, h
+                break
+            a *= 0.5
+        if trace is not None:
+            trace.append(taken)
+        if taken < 0:
+            break
     return vstar, rhos, Ks
 
 
-def ao_objective(P, w, vstar):
-    rhos, _ = kkt.forward_density(P, vstar)
+def ao_objective_from(P, w, vstar, rhos):
+    """Eq. PO's objective: keyframe misfit in the C_i metric plus
+    K/2 sum_{i=1}^{N-1} ||w_i - v*_i||^2 (v*_0 = v_0 is fixed)."""
     d = (w - vstar)[1:]
     return P.misfit(rhos) + 0.5 * P.K * float(np.sum(d * d))
 
 
-def nso(P, x, z, fscale, eps_rel, max_cycles):
+def ao_objective(P, w, vstar):
+    rhos, _ = kkt.forward_density(P, vstar)
+    return ao_objective_from(P, w, vstar, rhos)
+
+
+def nso(P, x, z, fscale, eps_rel, max_cycles, lm=None):
     """Alg. 3 inner loop: at least one V-cycle, then V-cycles until
-    ||f||_inf <= eps_rel * fscale (or the cap)."""
+    ||f||_inf <= eps_rel * fscale (or the cap).
+
+    ``lm`` (a dict with "gamma", "gamma0", "rejected"; used when P.lm_adapt):
+    Sec. 5's Levenberg-Marquardt safeguard -- the FAS cycle acts as the
+    subproblem solver of an LM method whose damping is the shift gamma of the
+    smoother's v blocks.  A cycle that raises ||f||_inf (or fails: a
+    non-finite norm, a singular local solve) is undone and gamma quadrupled;
+    an accepted cycle halves gamma back toward its default.  f itself, and so
+    the fixed point, does not depend on gamma.  Returns (||f||_inf, cycles)."""
     f = kkt.state_inf(kkt.nso_residual(P, P.grid, x, z))
     cycles = 0
     while (cycles < 1 or f > eps_rel * fscale) and cycles < max_cycles:
-        f = stfas.stfas_cycle(P, x, z)
         cycles += 1
+        if lm is None or not P.lm_adapt:
+            f = stfas.stfas_cycle(P, x, z)
+            continue
+        keep = kkt.copy_state(x)
+        P.lm_shift = lm["gamma"]
+        try:
+            fn = stfas.stfas_cycle(P, x, z)
+        except np.linalg.LinAlgError:
+            fn = np.inf
+        if fn <= f:
+            f = fn
+            lm["gamma"] = max(lm["gamma0"], 0.5 * lm["gamma"])
+        else:
+            for k in x:
+                x[k] = keep[k]
+            lm["gamma"] = min(4.0 * lm["gamma"], 1e30)
+            lm["rejected"] += 1
+    if lm is not None:
+        P.lm_shift = lm["gamma"]
     return f, cycles
 
 
@@ -79,20 +152,23 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
     hist = []
     fscale = None
     vstar = None
+    lm = dict(gamma=P.lm_shift, gamma0=P.lm_shift, rejected=0)
     for it in range(max_admm):
         vstar, rhos, _ = ao(P, x["v"], lam, start=vstar)
         z = vstar - lam / P.K
         if fscale is None:
             fscale = kkt.state_inf(kkt.nso_residual(P, P.grid, x, z))
-        fres, cycles = nso(P, x, z, fscale, eps_stfas, max_vcycles)
+        fres, cycles = nso(P, x, z, fscale, eps_stfas, max_vcycles, lm)
         R = kkt.kkt_norm(P, x["v"]) / g0
         dr = float(np.max(np.abs(rho_last - rhos)))
         hist.append(dict(it=it, kkt_rel=R, f_inf=fres, vcycles=cycles, drho=dr,
-                         objective=kkt.objective(P, x["v"])))
+                         objective=kkt.objective(P, x["v"]), rejected=lm["rejected"],
+                         lm_shift=lm["gamma"]))
         if callback:
             callback(hist[-1])
         if R <= tol or dr < eps_admm:
             break
         rho_last = rhos
         lam[1:N] += P.K * P.beta * (x["v"][1:N] - vstar[1:N])
+    P.lm_shift = lm["gamma0"]
     return x, vstar, lam, hist

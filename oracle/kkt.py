@@ -29,11 +29,14 @@ class Problem:
     taylor_tol: float = 1e-5
     taylor_kmax: int = 64
     ao_iters: int = 2
+    ao_halvings: int = 8             # Sec. 5 blending safeguard of Alg. 1 (-1: plain)
     pre: int = 2
     post: int = 2
     coarse_sweeps: int = 10
     coarsest_n: int = 4
     omega: float = 0.8               # SCGS under-relaxation
+    cgc_guard: bool = True           # keep a coarse correction only if it lowers ||res - f||_2
+    lm_adapt: bool = True            # Sec. 5 LM safeguard of the NSO loop (adaptive lm_shift)
     self_advection: bool = True      # False drops Adv (linear saddle problem; pins only)
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
 

@@ -16,6 +16,15 @@ Readings:
   x^h += P(x^{2h}_new - x^{2h}_old), which is what the subtract/add pair
   amounts to.
 * the coarse target is z^{2h} = R z^h; the fine-level res is 0.
+* coarse-grid correction guard (``P.cgc_guard``, default on): the correction
+  is kept only if ||res - f(x + P e)||_2 <= ||res - f(x)||_2 on that level;
+  otherwise x stays as the pre-smoothing left it.  Alg. 2 has no such test.
+  Once the ADMM iterate carries strong flows (CFL of several cells per step),
+  the unguarded cycle stalled at ||f||_inf ~ 1.7e2 on 32^2 x 16 (and
+  diverged on 128^2 x 40) while the smoother alone kept reducing ||f||: the
+  coarse correction undid the smoothing.  In the regime where the cycle
+  contracts, the correction cuts the residual several-fold and is always kept,
+  so the guard does not change the cycle there.
 """
 import numpy as np
 
@@ -128,8 +137,19 @@ def vcycle(P, grids, level, x, z, res):
     corr = prolong_state(g, gc, kkt.state_sub(xc, xc_old))
     corr["v"][0] = 0.0      # v_0 is data, not an unknown
     corr["pbar"][0] = 0.0
-    for k in x:
-        x[k] += corr[k]
+    trial = {k: x[k] + corr[k] for k in x}
+    if P.cgc_guard:
+        # keep the coarse-grid correction only if it does not raise the
+        # level's residual 2-norm; otherwise continue from the smoothed x
+        ft = kkt.nso_residual(P, g, trial, z)
+        before = sum(float(np.sum(a * a)) for a in rf.values())
+        after = sum(float(np.sum((res[k] - ft[k]) ** 2)) for k in ft)
+        if after <= before:
+            for k in x:
+                x[k] = trial[k]
+    else:
+        for k in x:
+            x[k] = trial[k]
     for _ in range(P.post):
         scgs.sweep(P, g, x, z, res)
 

@@ -263,6 +263,37 @@ def test_ao_step_decreases_its_objective_and_is_solenoidal():
         assert np.max(np.abs(mac.div(P.grid, vstar[i]))) < 1e-10
 
 
+def test_ao_blend_never_raises_the_objective_and_reduces_to_plain_steps():
+    """Sec. 5's blend: with solenoidal w (v = 0, lambda = 0) every accepted pass
+    lowers the AO objective; a pass that took no halving is exactly the plain
+    fixed-point step y = Q(w - grad misfit / K); a small K forces halvings;
+    v* stays solenoidal; the returned densities are a forward sweep at v*."""
+    for K, want_halving in ((1.0, False), (0.01, True)):
+        P = _problem(8, 4, sigma=0.15, levels=2, K=K)
+        v = np.zeros((P.N + 1, P.grid.F))
+        lam = np.zeros((P.N, P.grid.F))
+        w = v[:P.N].copy()
+        vs, J, traces = None, admm.ao_objective(P, w, w), []
+        for _ in range(3):
+            tr = []
+            new, rhos, Ks = admm.ao(P, v, lam, iters=1, start=vs, trace=tr)
+            Jn = admm.ao_objective(P, w, new)
+            assert Jn <= J + 1e-15
+            if tr[0] == 0:
+                Pp = _problem(8, 4, sigma=0.15, levels=2, K=K, ao_halvings=-1)
+                ref, _, _ = admm.ao(Pp, v, lam, iters=1, start=vs)
+                np.testing.assert_allclose(new, ref, rtol=0, atol=1e-14)
+            if tr[0] < 0:
+                np.testing.assert_array_equal(new, w if vs is None else vs)
+            r2, _ = kkt.forward_density(P, new)
+            np.testing.assert_allclose(rhos, r2, rtol=0, atol=1e-15)
+            for i in range(1, P.N):
+                assert np.max(np.abs(mac.div(P.grid, new[i]))) < 1e-10
+            traces += tr
+            vs, J = new, Jn
+        assert any(t > 0 for t in traces) == want_halving, traces
+
+
 @pytest.mark.slow
 def test_admm_reaches_the_full_resimulation_objective_on_a_tiny_problem():
     """North-star check: STFAS + ADMM and a full-resimulation quasi-Newton solve
