@@ -46,7 +46,8 @@ typedef enum {
   STC_ERR_CUDA = 3,
   STC_ERR_NOT_CONVERGED = 4,
   STC_ERR_DIVERGED = 5, /* Taylor order above taylor_kmax, or a non-finite norm */
-  STC_ERR_UNSUPPORTED = 6
+  STC_ERR_UNSUPPORTED = 6,
+  STC_ERR_BUSY = 7      /* the object is in use (a running serving request) */
 } stc_status;
 
 typedef struct stc_problem stc_problem; /* opaque; owns all of its device memory */
@@ -76,6 +77,14 @@ typedef struct {
   double lm_shift;      /* Levenberg-Marquardt shift of the smoother's v blocks; <0: 1/dt^2 */
   int poisson_vcycles;  /* multigrid cycles per projection Q (8)                   */
   int self_advection;   /* 1 (default); 0 drops Adv (linear saddle problem, tests only) */
+  int ao_halvings;      /* Sec. 5 safeguard of Alg. 1: v* moves to v* + a (y - v*) with
+                           a = 1, 1/2, ... (at most this many halvings) until the AO
+                           objective of Eq. PO does not increase; -1 = plain Alg. 1 (8) */
+  int cgc_guard;        /* 1 (default): a V-cycle keeps a level's coarse-grid correction
+                           only if it does not raise that level's ||res - f||_2 */
+  int lm_adapt;         /* 1 (default): Sec. 5's Levenberg-Marquardt safeguard in stc_solve's
+                           NSO loop: a V-cycle that raises ||f||_inf is undone and lm_shift
+                           quadrupled; an accepted one halves it back toward its default */
 } stc_params;
 
 typedef struct {
@@ -87,6 +96,12 @@ typedef struct {
   double drho;         /* last max_i ||rho_i - rho_i^last||_inf                */
   double seconds;      /* wall time of the solve                               */
   double seconds_to_1e4; /* time at which kkt_rel first reached 1e-4 (<0: never) */
+  int rejected_vcycles; /* V-cycles undone by the LM safeguard (counted in vcycles) */
+  double lm_shift;      /* the smoother's LM shift at exit                      */
+  int density_stop_iter;      /* first ADMM iteration (1-based) at which Alg. 3's density
+                                 test max_i ||rho_i - rho_i^last||_inf < max|rho_0|/100
+                                 held, whatever eps_admm is (0: never)          */
+  double seconds_to_density_stop; /* wall time at that iteration (<0: never)    */
 } stc_report;
 
 /* Field identifiers for stc_get_field / stc_set_field (level 0 = finest grid). */
@@ -194,9 +209,26 @@ stc_status stc_project(stc_problem* p, int field, int first, int count);
 
 /* One AO solve (Alg. 1): w = v + lambda/K; v* = w (warm_start = 0) or the
  * current v* is kept (warm_start != 0, how stc_solve continues the fixed-point
- * iteration after its first ADMM iteration); then `iters` forward / backward /
- * projection passes; then z = v* - lambda/K on every level. */
+ * iteration after its first ADMM iteration); then `iters` passes, each a
+ * backward sweep and projection y = Q(w + (dA/dv*)^T mu / K) followed, when
+ * ao_halvings >= 0, by Sec. 5's blend v* <- v* + a (y - v*) with the first
+ * a in 1, 1/2, ..., 2^-ao_halvings whose forward sweep does not raise the AO
+ * objective (fp64, read back per trial; if none does, v* stays and the pass
+ * loop ends); then z = v* - lambda/K on every level.  Afterwards
+ * STC_FIELD_RHO and the Taylor orders are those of a forward sweep at the
+ * final v*. */
 stc_status stc_ao(stc_problem* p, int iters, int warm_start);
+/* Halvings taken by each pass of the last stc_ao (-1: every trial rejected;
+ * 0 for every pass of the plain form).  *count = passes run; at most `len`
+ * are written. */
+stc_status stc_ao_trace(const stc_problem* p, int* halvings, size_t len, int* count);
+/* The NSO solve of Alg. 3's inner loop on the current targets: at least one
+ * V-cycle, then V-cycles until ||f||_inf <= f_target or max_cycles, each under
+ * the LM safeguard when stc_params.lm_adapt is set (a cycle that raises
+ * ||f||_inf is undone and the smoother's shift quadrupled; an accepted one
+ * halves it back toward its default).  Outputs (may be NULL): cycles run,
+ * including undone ones, and the final ||f||_inf. */
+stc_status stc_nso_solve(stc_problem* p, double f_target, int max_cycles, int* cycles, double* f_inf);
 /* z = v* - lambda/K on the finest level, restricted to every coarser level. */
 stc_status stc_prepare_targets(stc_problem* p);
 
@@ -237,6 +269,12 @@ stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* 
 
 /* Device memory held by the problem, in bytes. */
 stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes);
+/* Device bytes stc_create_problem(params) followed by stc_set_keyframes with
+ * nkeys keyframes would allocate -- the number stc_memory_bytes reports for
+ * that problem -- computed on the host without a device (the serving
+ * admission size).  STC_ERR_INVALID_ARG for parameters stc_create_problem
+ * rejects. */
+stc_status stc_problem_bytes(const stc_params* params, int nkeys, size_t* bytes);
 
 /* ---- allocation-free entry point ------------------------------------------- */
 

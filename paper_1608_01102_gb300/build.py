@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstc.so")
-SOURCES = ["stc_api.cu", "nso_kernels.cu", "advect_kernels.cu", "poisson_kernels.cu"]
+SOURCES = ["stc_api.cu", "nso_kernels.cu", "advect_kernels.cu", "poisson_kernels.cu", "stc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]
@@ -40,7 +40,7 @@ def _stale(out, deps):
 def build(verbose=False, extra=None, force=False):
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "stc.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in ("stc.h", "stc_server.h")]
     cc = nvcc()
     extra = list(extra or [])
 

@@ -11,6 +11,7 @@
 #include <cooperative_groups.h>
 
 #include <mutex>
+#include <vector>
 
 #include "../../include/stc.h"
 #include "stc_internal.cuh"
@@ -615,9 +616,30 @@ size_t advect_smem_adjoint(const Geom& g, size_t tsize) {
   return tsize == 4 ? adv_layout<float>(g, true).total : adv_layout<double>(g, true).total;
 }
 
+// The dynamic shared-memory cap of a kernel is raised once, to the opt-in
+// maximum, rather than to each launch's size: problems of different sizes
+// launched from several host threads would otherwise race on the attribute.
+static cudaError_t allow_max_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const void* k : done)
+    if (k == kernel) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (err == cudaSuccess) err = cudaFuncGetAttributes(&fa, kernel);
+  // the cap covers dynamic memory only: opt-in total minus the static arrays
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (err == cudaSuccess) done.push_back(kernel);
+  return err;
+}
+
 template <class K>
 static cudaError_t cluster_launch(K kernel, size_t smem, cudaStream_t st, void** args) {
-  cudaError_t e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)kernel);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kClusterCTAs, 1, 1);

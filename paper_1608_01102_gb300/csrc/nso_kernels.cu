@@ -1,6 +1,7 @@
 // NSO subproblem kernels: residual f of Eq. KKTAO, the temporally augmented
 // SCGS smoother of Sec. 4.3 / Eq. HESS, the STFAS transfer operators R and P
 // (Sec. 4.3, Alg. 2) and reductions.
+#include <mutex>
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
 
@@ -20,10 +21,15 @@ namespace stc {
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z,
-                                   CState<T> res, State<T> out, T sf, T sr) {
+                                   CState<T> res, State<T> out, T sf, T sr, double* sq,
+                                   const double* only_if_undone) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (t > g.N) return;
+  // conditional form (after a guarded coarse-grid correction): the residual
+  // already in `out` is current unless the correction was undone
+  if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
+  double acc = 0.0;   // sum of squares of this thread's outputs (when sq != nullptr)
   const int N = g.N;
   const T idt = T(g.idt);
   const T sa = T(g.self_adv);
@@ -57,6 +63,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
         if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
       }
       out.v[(size_t)t * g.F + e] = val;
+      acc += (double)val * (double)val;
     } else {
       out.v[e] = T(0);
     }
@@ -74,6 +81,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
         if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
       }
       out.u[(size_t)t * g.F + e] = val;
+      acc += (double)val * (double)val;
     }
   }
   if (e < g.C) {
@@ -82,6 +90,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       T val = -divergence(g, x.v + (size_t)t * g.F, j, i) * sf;
       if (res.pbar) val += sr * ld(res.pbar + (size_t)t * g.C + e);
       out.pbar[(size_t)t * g.C + e] = val;
+      acc += (double)val * (double)val;
     } else {
       out.pbar[e] = T(0);
     }
@@ -89,6 +98,18 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       T val = -divergence(g, x.u + (size_t)t * g.F, j, i) * sf;
       if (res.p) val += sr * ld(res.p + (size_t)t * g.C + e);
       out.p[(size_t)t * g.C + e] = val;
+      acc += (double)val * (double)val;
+    }
+  }
+  if (sq) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      acc = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (threadIdx.x == 0) atomicAdd(sq, acc);
     }
   }
 }
@@ -315,9 +336,13 @@ __device__ __forceinline__ S shift_sym(S A[4][4], const CellG<S>& cg) {
 
 template <class T, class S>
 __global__ void __launch_bounds__(256)
-scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb) {
+scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb,
+                   const double* __restrict__ lm_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
+  // Levenberg-Marquardt shift of the v blocks: a device scalar when the solve
+  // adapts it between V-cycles (the captured graph stays valid), else g.lm
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
   const int ncell = ncx * ncy;
   const int q0 = blockIdx.x * cpb;
   S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
@@ -405,7 +430,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2) PU[a2][b2] = pw[a2];
     }
-    const S diag = (tv < N ? S(g.a) : S(0)) + S(g.lm);
+    const S diag = (tv < N ? S(g.a) : S(0)) + lm;
     int e = 0;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
@@ -717,7 +742,14 @@ template <class Tf, class Tc>
 __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, int t0_face,
                                        int t0_cell, Tf* ff, Tf* fc, const Tc* __restrict__ cnf,
                                        const Tc* __restrict__ cof, const Tc* __restrict__ cnc,
-                                       const Tc* __restrict__ coc) {
+                                       const Tc* __restrict__ coc, const double* undo_if_rose) {
+  // undo form: subtract the same correction again when the guarded level's
+  // residual norm rose (norms[1] after vs norms[0] before; NaN counts as rose)
+  double sgn = 1.0;
+  if (undo_if_rose) {
+    if (undo_if_rose[1] <= undo_if_rose[0]) return;
+    sgn = -1.0;
+  }
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nfaces = (size_t)nt_face * gf.F;
   const size_t ncells = (size_t)nt_cell * gf.C;
@@ -749,7 +781,7 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
       double tb = 0.75 * d(jb, ia) + 0.25 * d(jb, ib);
       val = wa * ta + wb * tb;
     }
-    ff[(size_t)t * gf.F + f] += Tf(val);
+    ff[(size_t)t * gf.F + f] += Tf(sgn * val);
   } else if (e < nfaces + ncells) {
     const size_t ec = e - nfaces;
     const int t = (int)(ec / gf.C) + t0_cell;
@@ -762,7 +794,7 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
     cell_interp(i, gc.nx, ia, ib);
     auto d = [&](int J, int I) { return double(n[cidx(gc, J, I)]) - double(o[cidx(gc, J, I)]); };
     double val = 0.5625 * d(ja, ia) + 0.1875 * d(ja, ib) + 0.1875 * d(jb, ia) + 0.0625 * d(jb, ib);
-    fc[(size_t)t * gf.C + c] += Tf(val);
+    fc[(size_t)t * gf.C + c] += Tf(sgn * val);
   }
 }
 
@@ -847,11 +879,11 @@ static inline unsigned blocks_for(size_t n, int tpb) { return (unsigned)((n + tp
 
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st) {
+                         cudaStream_t st, double* sq, const double* only_if_undone) {
   const int tpb = 128;
   const int n = g.F > g.C ? g.F : g.C;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
-  nso_residual_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, sf, sr);
+  nso_residual_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, sf, sr, sq, only_if_undone);
 }
 
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
@@ -866,26 +898,29 @@ int scgs_cells_per_cta(int N) {
 }
 
 template <class T, class S>
-static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, cudaStream_t st) {
+static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev,
+                           cudaStream_t st) {
   const int ncx = colour_extent(g.nx, colour & 1);
   const int ncy = colour_extent(g.ny, colour >> 1);
   const int ncell = ncx * ncy;
   if (ncell <= 0) return;
   const int cpb = scgs_cells_per_cta<S>(g.N);
   const size_t sm = (size_t)cpb * scgs_cell_floats(g.N) * sizeof(S);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, (const void*)scgs_colour_kernel<T, S>);
     cudaFuncSetAttribute((const void*)scgs_colour_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_set = true;
-  }
-  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 32 * cpb, sm, st>>>(g, x, r, colour, ncx, ncy, cpb);
+                         227 * 1024 - (int)fa.sharedSizeBytes);
+  });
+  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 32 * cpb, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, lm_dev);
 }
 
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st) {
-  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, st);
-  else launch_scgs_ts<T, T>(g, x, r, colour, st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+                        const double* lm_dev) {
+  if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, lm_dev, st);
+  else launch_scgs_ts<T, T>(g, x, r, colour, lm_dev, st);
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
@@ -915,16 +950,16 @@ void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, 
 
 template <class Tf, class Tc>
 void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
-                            cudaStream_t st) {
+                            cudaStream_t st, const double* undo_if_rose) {
   const int tpb = 256;
   const int N = gf.N;
   // v and pbar for t = 1..N (v_0 is data), u and p for t = 0..N-1
   size_t n1 = (size_t)N * gf.F + (size_t)N * gf.C;
   prolong_correct_kernel<Tf, Tc><<<blocks_for(n1, tpb), tpb, 0, st>>>(gf, gc, N, N, 1, 1, f.v, f.pbar, cn.v, co.v,
-                                                                      cn.pbar, co.pbar);
+                                                                      cn.pbar, co.pbar, undo_if_rose);
   size_t n2 = (size_t)N * gf.F + (size_t)N * gf.C;
   prolong_correct_kernel<Tf, Tc><<<blocks_for(n2, tpb), tpb, 0, st>>>(gf, gc, N, N, 0, 0, f.u, f.p, cn.u, co.u,
-                                                                      cn.p, co.p);
+                                                                      cn.p, co.p, undo_if_rose);
 }
 
 template <class T>
@@ -962,8 +997,9 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
-                                       cudaStream_t);                                                      \
-  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t);           \
+                                       cudaStream_t, double*, const double*);                              \
+  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
+                                      const double*);                                                      \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
   template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
   template void launch_remove_mean<T>(T*, int, int, cudaStream_t);
@@ -975,7 +1011,7 @@ STC_INST_T(double)
                                         cudaStream_t);                                                     \
   template void launch_restrict_faces<Tf, Tc>(const Geom&, const Geom&, int, const Tf*, Tc*, cudaStream_t); \
   template void launch_prolong_correct<Tf, Tc>(const Geom&, const Geom&, State<Tf>, CState<Tc>, CState<Tc>, \
-                                               cudaStream_t);                                              \
+                                               cudaStream_t, const double*);                               \
   template void launch_convert<Tf, Tc>(const Tf*, Tc*, size_t, cudaStream_t);
 STC_INST_TT(float, float)
 STC_INST_TT(float, double)

@@ -8,6 +8,7 @@
 // average restriction and bilinear prolongation, the coarsest level (<= 64
 // cells) by 30 parallel red-black Gauss-Seidel sweeps in fp64, then v - G phi
 // written back.
+#include <mutex>
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
 
@@ -225,9 +226,23 @@ template <class T>
 cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const size_t sm = project_smem(g, sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute((const void*)project_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
-  if (e != cudaSuccess) return e;
+  // raise the cap once to the opt-in maximum (per-size settings would race
+  // between host threads solving problems of different sizes)
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    attr_err = cudaGetDevice(&dev);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, (const void*)project_kernel<T>);
+    // the cap covers dynamic memory only: opt-in total minus the static arrays
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute((const void*)project_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin - (int)fa.sharedSizeBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   project_kernel<T><<<count, kPoissonThreads, sm, st>>>(g, fields, vcycles);
   return cudaGetLastError();
 }
@@ -321,6 +336,46 @@ __global__ void absdiff_max_copy_kernel(const T* __restrict__ a, T* b, size_t n,
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg2(out, m);
 }
 
+// AO blend (Sec. 5): out = x + a (y - x); a blend of solenoidal fields is solenoidal
+template <class T>
+__global__ void blend_kernel(size_t n, const T* __restrict__ x, const T* __restrict__ y, double a, T* out) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = x[e] + T(a) * (y[e] - x[e]);
+}
+
+__device__ __forceinline__ void block_add(double s, double* out) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+// keyframe misfit of Eq. opt in the C_i metric: 0.5 (rho - rho*)^T m with m = C (rho - rho*)
+template <class T>
+__global__ void misfit_dot_kernel(int C, const T* __restrict__ rho, const double* __restrict__ star,
+                                  const double* __restrict__ m, double* out) {
+  double s = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C; e += gridDim.x * blockDim.x)
+    s += ((double)rho[e] - star[e]) * m[e];
+  block_add(0.5 * s, out);
+}
+
+template <class T>
+__global__ void diff_sumsq_kernel(size_t n, const T* __restrict__ a, const T* __restrict__ b, double scale,
+                                  double* out) {
+  double s = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double d = (double)a[e] - (double)b[e];
+    s += d * d;
+  }
+  block_add(scale * s, out);
+}
+
 static inline unsigned nblk(size_t n, int tpb, unsigned cap = 4096) {
   size_t b = (n + tpb - 1) / tpb;
   if (b > cap) b = cap;
@@ -354,13 +409,34 @@ void launch_absdiff_max_copy(const T* a, T* b, size_t n, double* out, cudaStream
   absdiff_max_copy_kernel<T><<<nblk(n, 256, 1216), 256, 0, st>>>(a, b, n, out);
 }
 
+template <class T>
+void launch_blend_faces(const Geom& g, int count, const T* x, const T* y, double a, T* out, cudaStream_t st) {
+  const size_t n = (size_t)count * g.F;
+  if (n == 0) return;
+  blend_kernel<T><<<nblk(n, 256), 256, 0, st>>>(n, x, y, a, out);
+}
+template <class T>
+void launch_misfit_dot(const Geom& g, const T* rho, const double* star, const double* m, double* out,
+                       cudaStream_t st) {
+  misfit_dot_kernel<T><<<nblk(g.C, 256, 304), 256, 0, st>>>(g.C, rho, star, m, out);
+}
+template <class T>
+void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st) {
+  if (n == 0) return;
+  diff_sumsq_kernel<T><<<nblk(n, 256, 1216), 256, 0, st>>>(n, a, b, scale, out);
+}
+
 #define STC_POI_INST(T)                                                                                        \
   template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t);                            \
   template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, int, cudaStream_t);             \
   template void launch_axpby_faces<T>(const Geom&, int, const T*, double, const T*, double, T*, cudaStream_t); \
   template void launch_kkt_force_rhs<T>(const Geom&, const T*, T*, cudaStream_t);                             \
   template void launch_kkt_grad_rhs<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);  \
-  template void launch_absdiff_max_copy<T>(const T*, T*, size_t, double*, cudaStream_t);
+  template void launch_absdiff_max_copy<T>(const T*, T*, size_t, double*, cudaStream_t);                   \
+  template void launch_blend_faces<T>(const Geom&, int, const T*, const T*, double, T*, cudaStream_t);        \
+  template void launch_misfit_dot<T>(const Geom&, const T*, const double*, const double*, double*,            \
+                                     cudaStream_t);                                                           \
+  template void launch_diff_sumsq<T>(const T*, const T*, size_t, double, double*, cudaStream_t);
 STC_POI_INST(float)
 STC_POI_INST(double)
 

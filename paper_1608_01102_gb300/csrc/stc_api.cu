@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <limits>
 #include <vector>
 
 #include "../../include/stc.h"
@@ -80,8 +81,17 @@ struct stc_problem {
   void *rho = nullptr, *rho_k = nullptr, *rho_last = nullptr, *mu = nullptr, *vstar = nullptr, *lam = nullptr,
        *w = nullptr, *y = nullptr, *uk = nullptr, *gk = nullptr, *dens = nullptr, *powers = nullptr,
        *v0 = nullptr;
-  int *K = nullptr, *Kk = nullptr;
+  void *vcand = nullptr, *rho_c = nullptr;   // AO blend trial: v*, its densities and Taylor orders
+  int *K = nullptr, *Kk = nullptr, *K_c = nullptr;
+  bool rho_at_vstar = false;      // rho / K hold the forward sweep of the current v*
+  std::vector<int> ao_trace;      // halvings per pass of the last AO
+  double* dguard = nullptr;       // per level {before, after} ||res - f||_2^2 of the guarded correction
+  double* dlm = nullptr;          // device copy of the smoother's LM shift gamma (read by every SCGS launch)
+  double lm0 = 0.0, lm = 0.0;     // default and current gamma
+  FieldSet xb;                    // finest state before the last V-cycle (undo of a rejected cycle)
+  int rejected = 0;               // V-cycles undone by the LM safeguard
   double *mterm = nullptr, *mtmp0 = nullptr, *mtmp1 = nullptr, *star = nullptr;
+  size_t star_bytes = 0;
   std::vector<int> key_steps;
   std::vector<double> key_c;
   double* dscal = nullptr;  // device fp64 scalars
@@ -160,26 +170,30 @@ void check_launch(const char* what) { ck(cudaGetLastError(), what); }
 // ---------------------------------------------------------------------------
 // out = sf * f(x) + sr * res  on level l
 void nso_residual(stc_problem* P, int l, double sf, double sr, const FieldSet& res, const FieldSet& out,
-                  cudaStream_t st) {
+                  cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr) {
   Level& L = P->lv[l];
   dispatch(L.dbl, [&](auto tag) {
     using T = decltype(tag);
-    launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st);
+    launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st,
+                           sq, only_if_undone);
   });
   count(P, 1);
 }
 
-void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = false) {
+// `first_only_if_undone`: the residual in L.tmp is already current unless the
+// guarded coarse-grid correction recorded there was undone
+void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = false,
+            const double* first_only_if_undone = nullptr) {
   Level& L = P->lv[l];
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 4; ++c) {
-      nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st);
+      nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st, nullptr, s == 0 && c == 0 ? first_only_if_undone : nullptr);
       const bool ev = timed && P->ev_used < (int)P->ev_start.size();
       if (ev) ck(cudaEventRecordWithFlags(P->ev_start[P->ev_used], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
-        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st);
+        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm);
       });
       if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
       count(P, 1);
@@ -213,14 +227,15 @@ void restrict_residual(stc_problem* P, int l, cudaStream_t st) {
   count(P, 2);
 }
 
-void prolong_level(stc_problem* P, int l, cudaStream_t st) {
+void prolong_level(stc_problem* P, int l, cudaStream_t st, const double* undo_if_rose = nullptr) {
   Level& F = P->lv[l];
   Level& Cc = P->lv[l + 1];
   dispatch(F.dbl, [&](auto tf) {
     using Tf = decltype(tf);
     dispatch(Cc.dbl, [&](auto tc) {
       using Tc = decltype(tc);
-      launch_prolong_correct<Tf, Tc>(F.g, Cc.g, st_of<Tf>(F.x), cst_of<Tc>(Cc.x), cst_of<Tc>(Cc.old), st);
+      launch_prolong_correct<Tf, Tc>(F.g, Cc.g, st_of<Tf>(F.x), cst_of<Tc>(Cc.x), cst_of<Tc>(Cc.old), st,
+                                     undo_if_rose);
     });
   });
   count(P, 2);
@@ -235,14 +250,22 @@ void vcycle_level(stc_problem* P, int l, cudaStream_t st) {
   Level& L = P->lv[l];
   Level& Cc = P->lv[l + 1];
   const bool timed = P->timing && l == 0 && P->counter == &P->graph_launches;
+  // guard: norms[0] = ||r^h||_2^2 before the correction, norms[1] after it
+  double* norms = P->prm.cgc_guard ? P->dguard + 2 * l : nullptr;
   smooth(P, l, P->prm.pre, st, timed);
-  nso_residual(P, l, -1.0, 1.0, L.res, L.tmp, st);         // r^h = res^h - f^h(x^h)
+  nso_residual(P, l, -1.0, 1.0, L.res, L.tmp, st, norms);  // r^h = res^h - f^h(x^h)
   restrict_level(P, l, st);                                 // x^{2h} = R x^h, kept as XOLD
   restrict_residual(P, l, st);                              // res^{2h} = R r^h
   nso_residual(P, l + 1, 1.0, 1.0, Cc.res, Cc.res, st);     // res^{2h} += f^{2h}(R x^h)
   vcycle_level(P, l + 1, st);
   prolong_level(P, l, st);                                  // x^h += P(x^{2h} - R x^h)
-  smooth(P, l, P->prm.post, st, timed);
+  if (norms) {
+    nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st, norms + 1);   // f^h(x^h) - res^h after it
+    prolong_level(P, l, st, norms);                                // undo if the norm rose
+    smooth(P, l, P->prm.post, st, timed, norms);
+  } else {
+    smooth(P, l, P->prm.post, st, timed);
+  }
 }
 
 void remove_pressure_means(stc_problem* P, cudaStream_t st) {
@@ -271,22 +294,44 @@ void residual_norm(stc_problem* P, int l, int slot, cudaStream_t st) {
   count(P, 4);
 }
 
+void copy_state(stc_problem* P, const FieldSet& from, const FieldSet& to, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  const size_t s = P->ts;
+  ck(cudaMemcpyAsync(to.v, from.v, (size_t)(g.N + 1) * g.F * s, cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemcpyAsync(to.pbar, from.pbar, (size_t)(g.N + 1) * g.C * s, cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemcpyAsync(to.u, from.u, (size_t)g.N * g.F * s, cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemcpyAsync(to.p, from.p, (size_t)g.N * g.C * s, cudaMemcpyDeviceToDevice, st), "copy");
+}
+
 void enqueue_top_vcycle(stc_problem* P, cudaStream_t st) {
+  if (P->prm.lm_adapt) copy_state(P, P->lv[0].x, P->xb, st);   // kept for an undo
+  if (P->prm.cgc_guard)
+    ck(cudaMemsetAsync(P->dguard, 0, 2 * P->lv.size() * sizeof(double), st), "memset");
   vcycle_level(P, 0, st);
   remove_pressure_means(P, st);
   residual_norm(P, 0, 0, st);
 }
 
-double read_scalar(stc_problem* P, int slot) {
+// Reads a device fp64 scalar (synchronising the stream) and surfaces device
+// error flags.  With kmax_rejects (an AO blend trial) a Taylor-order overflow,
+// with nonfinite_rejects (an NSO V-cycle under the LM safeguard) a non-finite
+// norm, is not an error: the flag is cleared and +inf returned.
+double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool nonfinite_rejects = false) {
   ck(cudaMemcpyAsync(P->hscal + slot, P->dscal + slot, sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
   ck(cudaMemcpyAsync(P->herr, P->derr, sizeof(int), cudaMemcpyDeviceToHost, P->st), "d2h");
   ck(cudaStreamSynchronize(P->st), "sync");
+  const int rejectable = (kmax_rejects ? DEV_TAYLOR_KMAX : 0) | (nonfinite_rejects ? DEV_NONFINITE : 0);
+  if (*P->herr && (*P->herr & ~rejectable) == 0) {
+    ck(cudaMemsetAsync(P->derr, 0, sizeof(int), P->st), "memset");
+    ck(cudaStreamSynchronize(P->st), "sync");
+    return std::numeric_limits<double>::infinity();
+  }
   if (*P->herr & DEV_TAYLOR_KMAX) fail(STC_ERR_DIVERGED, "Taylor series exceeded taylor_kmax");
   if (*P->herr & DEV_NONFINITE) fail(STC_ERR_DIVERGED, "non-finite value in a residual norm");
   return P->hscal[slot];
 }
 
-double run_vcycle(stc_problem* P) {
+double run_vcycle(stc_problem* P, bool nonfinite_rejects = false) {
   if (!P->vgraph) {
     cudaGraph_t graph = nullptr;
     P->graph_launches = 0;
@@ -309,7 +354,7 @@ double run_vcycle(stc_problem* P) {
   }
   ck(cudaGraphLaunch(P->vgraph, P->st), "graph launch");
   P->launches += P->graph_launches;
-  const double f = read_scalar(P, 0);
+  const double f = read_scalar(P, 0, false, nonfinite_rejects);
   for (int k = 0; k < P->ev_used; ++k) {
     float ms = 0.f;
     ck(cudaEventElapsedTime(&ms, P->ev_start[k], P->ev_stop[k]), "event time");
@@ -317,6 +362,32 @@ double run_vcycle(stc_problem* P) {
     P->timed_launches += 1;
   }
   return f;
+}
+
+void set_lm(stc_problem* P, double lm) {
+  P->lm = lm;
+  P->hscal[8] = lm;
+  ck(cudaMemcpyAsync(P->dlm, P->hscal + 8, sizeof(double), cudaMemcpyHostToDevice, P->st), "h2d");
+  ck(cudaStreamSynchronize(P->st), "sync");
+}
+
+// One NSO V-cycle under the Levenberg-Marquardt safeguard of Sec. 5 (the FAS
+// cycle as the subproblem solver of an LM method): a cycle that raises
+// ||f||_inf above f_old, or yields a non-finite norm, is undone and gamma
+// (the shift of the smoother's v blocks) is quadrupled; an accepted cycle
+// halves gamma back toward its default.  The fixed point f = 0 does not
+// depend on gamma.  Returns the residual of the state kept.
+double nso_cycle(stc_problem* P, double f_old) {
+  if (!P->prm.lm_adapt) return run_vcycle(P);
+  const double f = run_vcycle(P, true);
+  if (f <= f_old) {
+    if (P->lm > P->lm0) set_lm(P, std::max(P->lm0, 0.5 * P->lm));
+    return f;
+  }
+  copy_state(P, P->xb, P->lv[0].x, P->st);
+  ++P->rejected;
+  set_lm(P, std::min(4.0 * P->lm, 1e30));
+  return f_old;
 }
 
 // ---------------------------------------------------------------------------
@@ -392,6 +463,26 @@ void prepare_targets(stc_problem* P, cudaStream_t st) {
   check_launch("targets");
 }
 
+// AO objective of Eq. PO at v* = vel with densities rho (metric terms current):
+// 0.5 sum_keys (rho_s - rho*_s)^T C_s (rho_s - rho*_s) + K/2 sum_{i=1}^{N-1} ||w_i - v*_i||^2
+double ao_objective(stc_problem* P, const void* vel, const void* rho, cudaStream_t st, bool trial = false) {
+  const Geom& g = P->lv[0].g;
+  ck(cudaMemsetAsync(P->dscal + 4, 0, sizeof(double), st), "memset");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    for (size_t k = 0; k < P->key_steps.size(); ++k) {
+      const int s = P->key_steps[k];
+      launch_misfit_dot<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, P->mterm + (size_t)s * g.C,
+                           P->dscal + 4, st);
+    }
+    launch_diff_sumsq<T>((const T*)P->w + g.F, (const T*)vel + g.F, (size_t)(g.N - 1) * g.F, 0.5 * P->prm.K,
+                         P->dscal + 4, st);
+  });
+  count(P, (long long)P->key_steps.size() + (g.N > 1 ? 1 : 0));
+  check_launch("ao objective");
+  return read_scalar(P, 4, trial);
+}
+
 void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
   Level& L0 = P->lv[0];
   const Geom& g = L0.g;
@@ -402,14 +493,57 @@ void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
                       st);
   });
   count(P, 1);
-  for (int it = 0; it < iters; ++it) {
-    forward(P, P->vstar, P->rho, P->K, st);
+  P->ao_trace.clear();
+  const bool blend = P->prm.ao_halvings >= 0;
+  // densities at the starting v* (still valid after a warm start that kept v*)
+  if (!(warm && P->rho_at_vstar)) forward(P, P->vstar, P->rho, P->K, st);
+  P->rho_at_vstar = true;
+  double J = 0.0;
+  if (blend && iters > 0) {
     metric_terms(P, P->rho, st);
+    J = ao_objective(P, P->vstar, P->rho, st);
+  }
+  for (int it = 0; it < iters; ++it) {
+    // y = Q(w + (dA/dv*)^T mu / K) on steps 1..N-1.  With the blend, mterm
+    // already holds C(rho - rho*) of the accepted densities.
+    if (!blend) metric_terms(P, P->rho, st);
     adjoint(P, P->vstar, P->rho, P->K, P->w, 1.0, 1.0 / P->prm.K, P->y, st);
-    if (g.N > 1) {
-      project(P, (char*)P->y + fb, g.N - 1, st);
-      ck(cudaMemcpyAsync((char*)P->vstar + fb, (char*)P->y + fb, fb * (g.N - 1), cudaMemcpyDeviceToDevice, st),
-         "copy v*");
+    if (g.N > 1) project(P, (char*)P->y + fb, g.N - 1, st);
+    if (!blend) {   // plain Alg. 1: v* = y
+      if (g.N > 1)
+        ck(cudaMemcpyAsync((char*)P->vstar + fb, (char*)P->y + fb, fb * (g.N - 1), cudaMemcpyDeviceToDevice, st),
+           "copy v*");
+      forward(P, P->vstar, P->rho, P->K, st);
+      P->ao_trace.push_back(0);
+      continue;
+    }
+    // Sec. 5 blend: first a = 2^-h whose forward sweep does not raise the objective
+    ck(cudaMemcpyAsync(P->vcand, P->vstar, fb, cudaMemcpyDeviceToDevice, st), "copy v*_0");
+    int taken = -1;
+    double a = 1.0;
+    for (int h = 0; h <= P->prm.ao_halvings; ++h, a *= 0.5) {
+      dispatch(P->dbl, [&](auto tag) {
+        using T = decltype(tag);
+        launch_blend_faces<T>(g, g.N - 1, (const T*)P->vstar + g.F, (const T*)P->y + g.F, a, (T*)P->vcand + g.F,
+                              st);
+      });
+      count(P, g.N > 1 ? 1 : 0);
+      forward(P, P->vcand, P->rho_c, P->K_c, st);
+      metric_terms(P, P->rho_c, st);
+      const double Jc = ao_objective(P, P->vcand, P->rho_c, st, true);
+      if (Jc <= J) {
+        std::swap(P->vstar, P->vcand);
+        std::swap(P->rho, P->rho_c);
+        std::swap(P->K, P->K_c);
+        J = Jc;
+        taken = h;
+        break;
+      }
+    }
+    P->ao_trace.push_back(taken);
+    if (taken < 0) {
+      metric_terms(P, P->rho, st);   // leave the metric terms of the kept v*
+      break;
     }
   }
   prepare_targets(P, st);
@@ -479,6 +613,10 @@ void reset_state(stc_problem* P) {
   const Geom& g = P->lv[0].g;
   ck(cudaMemcpyAsync(P->lv[0].x.v, P->v0, (size_t)g.F * P->ts, cudaMemcpyDeviceToDevice, P->st), "v0");
   ck(cudaMemsetAsync(P->lam, 0, (size_t)g.N * g.F * P->ts, P->st), "memset");
+  P->rho_at_vstar = false;
+  P->lm0 = g.lm;
+  P->rejected = 0;
+  set_lm(P, P->lm0);
 }
 
 // ---------------------------------------------------------------------------
@@ -592,6 +730,49 @@ stc_status guarded(stc_problem* P, F&& f) {
   }
 }
 
+bool params_valid(const stc_params& prm) {
+  return !(prm.nx < 2 || prm.ny < 2 || prm.num_steps < 1 || !(prm.dt > 0) || !(prm.r > 0) || !(prm.K > 0) ||
+      prm.precision < 0 || prm.precision > 1 || prm.ao_iters < 0 || prm.pre < 0 || prm.post < 0 ||
+      prm.coarse_sweeps < 0 || prm.coarsest_n < 2 || !(prm.taylor_tol > 0) || prm.taylor_kmax < 1 ||
+      prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
+      !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
+      prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1);
+}
+
+// Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
+// the same list of buffers as the allocations below, without allocating
+// (the serving admission test).  Must be kept in step with them.
+size_t plan_bytes(const stc_params& prm, int nkeys) {
+  auto b = [](size_t n) { return n == 0 ? (size_t)16 : n; };
+  const bool dbl = prm.precision == 1;
+  const size_t ts = dbl ? 8 : 4;
+  const size_t N = (size_t)prm.num_steps;
+  std::vector<std::pair<int, int>> dims{{prm.nx, prm.ny}};
+  int nx = prm.nx, ny = prm.ny;
+  while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
+    nx /= 2;
+    ny /= 2;
+    dims.push_back({nx, ny});
+  }
+  auto faces = [](int x, int y) { return (size_t)y * (x + 1) + (size_t)(y + 1) * x; };
+  auto fieldset = [&](size_t F, size_t C, size_t s) {
+    return b((N + 1) * F * s) + b((N + 1) * C * s) + b(N * F * s) + b(N * C * s);
+  };
+  size_t total = 0;
+  for (size_t l = 0; l < dims.size(); ++l) {
+    const size_t F = faces(dims[l].first, dims[l].second), C = (size_t)dims[l].first * dims[l].second;
+    const size_t s = (dbl || (l > 0 && l == dims.size() - 1)) ? 8 : 4;
+    total += 3 * fieldset(F, C, s) + (l > 0 ? fieldset(F, C, s) : 0) + b(N * F * s);
+  }
+  const size_t F = faces(prm.nx, prm.ny), C = (size_t)prm.nx * prm.ny;
+  total += 3 * b((N + 1) * C * ts) + b(N * C * ts) + 2 * b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) +
+           b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts) : 0) + 4 * b(N * F * ts) +
+           2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
+           b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
+  if (nkeys > 0) total += b((size_t)nkeys * C * 8);
+  return total;
+}
+
 void free_problem(stc_problem* P) {
   if (!P) return;
   if (P->vgraph) cudaGraphExecDestroy(P->vgraph);
@@ -638,6 +819,9 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->lm_shift = -1.0;
   p->poisson_vcycles = 8;
   p->self_advection = 1;
+  p->ao_halvings = 8;
+  p->cgc_guard = 1;
+  p->lm_adapt = 1;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -650,11 +834,7 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
   }
   *out = nullptr;
   const stc_params& prm = *params;
-  if (prm.nx < 2 || prm.ny < 2 || prm.num_steps < 1 || !(prm.dt > 0) || !(prm.r > 0) || !(prm.K > 0) ||
-      prm.precision < 0 || prm.precision > 1 || prm.ao_iters < 0 || prm.pre < 0 || prm.post < 0 ||
-      prm.coarse_sweeps < 0 || prm.coarsest_n < 2 || !(prm.taylor_tol > 0) || prm.taylor_kmax < 1 ||
-      prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
-      !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1) {
+  if (!params_valid(prm)) {
     g_last_error = "invalid parameters";
     return STC_ERR_INVALID_ARG;
   }
@@ -711,6 +891,12 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->rho_last = dalloc(P, (N + 1) * C * ts);
     P->mu = dalloc(P, N * C * ts);
     P->vstar = dalloc(P, N * F * ts);
+    P->vcand = dalloc(P, N * F * ts);
+    P->rho_c = dalloc(P, (N + 1) * C * ts);
+    P->K_c = (int*)dalloc(P, N * sizeof(int));
+    P->dguard = (double*)dalloc(P, 2 * P->lv.size() * sizeof(double));
+    P->dlm = (double*)dalloc(P, sizeof(double));
+    if (prm.lm_adapt) alloc_fieldset(P, P->xb, g0, P->dbl);
     P->lam = dalloc(P, N * F * ts);
     P->w = dalloc(P, N * F * ts);
     P->y = dalloc(P, N * F * ts);
@@ -741,6 +927,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     r.ptr = P->rho_k;
     copy_in(P, r, rho0);
     r.ptr = P->rho_last;
+    copy_in(P, r, rho0);
+    r.ptr = P->rho_c;
     copy_in(P, r, rho0);
     if (v0) {
       std::vector<double> vv(v0, v0 + F);
@@ -795,13 +983,16 @@ stc_status stc_set_keyframes(stc_problem* p, int count, const int* steps, const 
       for (auto& q : p->allocs)
         if (q == p->star) q = nullptr;
       p->star = nullptr;
+      p->bytes -= p->star_bytes;
+      p->star_bytes = 0;
     }
     p->key_steps.assign(steps, steps + count);
     p->key_c.assign(count, 1.0);
     if (c)
       for (int k = 0; k < count; ++k) p->key_c[k] = c[k];
     if (count > 0) {
-      p->star = (double*)dalloc(p, (size_t)count * g.C * sizeof(double));
+      p->star_bytes = (size_t)count * g.C * sizeof(double);
+      p->star = (double*)dalloc(p, p->star_bytes);
       ck(cudaMemcpyAsync(p->star, rho_star, (size_t)count * g.C * sizeof(double), cudaMemcpyHostToDevice, p->st),
          "h2d");
       ck(cudaStreamSynchronize(p->st), "sync");
@@ -833,6 +1024,7 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
   stc_report rep;
   std::memset(&rep, 0, sizeof(rep));
   rep.seconds_to_1e4 = -1.0;
+  rep.seconds_to_density_stop = -1.0;
   bool converged = false;
   stc_status s = guarded(p, [&]() {
     auto t0 = std::chrono::steady_clock::now();
@@ -856,7 +1048,7 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       int cycles = 0;
       // at least one V-cycle per ADMM iteration, then until the NSO tolerance
       while ((cycles < 1 || f > prm.eps_stfas * p->fscale) && cycles < prm.max_vcycles) {
-        f = run_vcycle(p);
+        f = nso_cycle(p, f);
         ++cycles;
       }
       kkt(p, p->st);
@@ -865,12 +1057,18 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       const double drho = read_scalar(p, 2);
       rep.admm_iters = it + 1;
       rep.vcycles += cycles;
+      rep.rejected_vcycles = p->rejected;
+      rep.lm_shift = p->lm;
       rep.kkt_abs = gn;
       rep.kkt_rel = g0 > 0 ? gn / g0 : 0.0;
       rep.f_inf = f;
       rep.drho = drho;
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (rep.kkt_rel <= 1e-4 && rep.seconds_to_1e4 < 0) rep.seconds_to_1e4 = el;
+      if (drho < p->rho_scale / 100.0 && rep.density_stop_iter == 0) {
+        rep.density_stop_iter = it + 1;
+        rep.seconds_to_density_stop = el;
+      }
       if (rep.kkt_rel <= kkt_rel_tol || drho < eps_admm) {
         converged = rep.kkt_rel <= kkt_rel_tol || drho < eps_admm;
         break;
@@ -920,6 +1118,7 @@ stc_status stc_set_field(stc_problem* p, int field, int level, const double* in,
     FieldRef r = field_ref(p, field, level);
     if (len != r.count) fail(STC_ERR_INVALID_ARG, "length does not match the field size");
     copy_in(p, r, in);
+    if (field == STC_FIELD_VSTAR || field == STC_FIELD_RHO) p->rho_at_vstar = false;
   });
 }
 
@@ -946,6 +1145,7 @@ stc_status stc_advect(stc_problem* p, int source_field) {
   return guarded(p, [&]() {
     const void* vel = source_field == STC_FIELD_V ? p->lv[0].x.v : p->vstar;
     forward(p, vel, p->rho, p->K, p->st);
+    p->rho_at_vstar = source_field == STC_FIELD_VSTAR;
     read_scalar(p, 0);   // synchronise and surface device errors
   });
 }
@@ -1000,6 +1200,7 @@ stc_status stc_project(stc_problem* p, int field, int first, int count) {
     if (first < 0 || count < 0 || (size_t)first + (size_t)count > slabs)
       fail(STC_ERR_INVALID_ARG, "slab range outside the field");
     project(p, (char*)r.ptr + (size_t)first * g.F * p->ts, count, p->st);
+    if (field == STC_FIELD_VSTAR) p->rho_at_vstar = false;
     ck(cudaStreamSynchronize(p->st), "sync");
   });
 }
@@ -1013,6 +1214,17 @@ stc_status stc_ao(stc_problem* p, int iters, int warm_start) {
     ao(p, iters, warm_start != 0, p->st);
     read_scalar(p, 0);
   });
+}
+
+stc_status stc_ao_trace(const stc_problem* p, int* halvings, size_t len, int* count) {
+  if (!p || (!halvings && len > 0)) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  const size_t n = p->ao_trace.size();
+  for (size_t k = 0; k < n && k < len; ++k) halvings[k] = p->ao_trace[k];
+  if (count) *count = (int)n;
+  return STC_OK;
 }
 
 stc_status stc_prepare_targets(stc_problem* p) {
@@ -1035,6 +1247,24 @@ stc_status stc_nso_residual(stc_problem* p, int level, double* inf) {
     residual_norm(p, level, 3, p->st);
     const double v = read_scalar(p, 3);
     if (inf) *inf = v;
+  });
+}
+
+stc_status stc_nso_solve(stc_problem* p, double f_target, int max_cycles, int* cycles, double* f_inf) {
+  if (!p || max_cycles < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    residual_norm(p, 0, 0, p->st);
+    double f = read_scalar(p, 0);
+    int c = 0;
+    while ((c < 1 || f > f_target) && c < max_cycles) {
+      f = nso_cycle(p, f);
+      ++c;
+    }
+    if (cycles) *cycles = c;
+    if (f_inf) *f_inf = f;
   });
 }
 
@@ -1138,6 +1368,15 @@ stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* 
   }
   if (total_ms) *total_ms = p->timed_ms;
   if (launches) *launches = p->timed_launches;
+  return STC_OK;
+}
+
+stc_status stc_problem_bytes(const stc_params* params, int nkeys, size_t* bytes) {
+  if (!params || !bytes || nkeys < 0 || !params_valid(*params)) {
+    stc::set_last_error("invalid parameters");
+    return STC_ERR_INVALID_ARG;
+  }
+  *bytes = plan_bytes(*params, nkeys);
   return STC_OK;
 }
 

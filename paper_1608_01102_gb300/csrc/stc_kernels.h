@@ -9,20 +9,27 @@ namespace stc {
 void set_last_error(const char* msg);
 
 // --- NSO (nso_kernels.cu) ---------------------------------------------------
+// out = sf * f(x) + sr * res.  sq (optional): += sum of squares of out (fp64).
+// only_if_undone (optional, a guard's {before, after} norms): skip unless the
+// guarded coarse-grid correction was undone (after > before or NaN).
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st);
+                         cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr);
+// lm_dev (optional): device fp64 Levenberg-Marquardt shift of the v blocks, else g.lm
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st);
+void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+                        const double* lm_dev = nullptr);
 size_t scgs_smem_bytes(int N, size_t tsize);
 int colour_extent(int n, int parity);
 template <class Tf, class Tc>
 void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
 template <class Tf, class Tc>
 void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st);
+// f += P(cn - co); with undo_if_rose = a guard's {before, after} norms, instead
+// f -= P(cn - co) when after > before (or NaN), and nothing otherwise.
 template <class Tf, class Tc>
 void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
-                            cudaStream_t st);
+                            cudaStream_t st, const double* undo_if_rose = nullptr);
 template <class T>
 void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st);
 template <class T>
@@ -76,5 +83,15 @@ void launch_kkt_grad_rhs(const Geom& g, const T* v, const T* u, const T* dens, d
                          cudaStream_t st);
 template <class T>
 void launch_absdiff_max_copy(const T* a, T* b, size_t n, double* out, cudaStream_t st);
+// out = x + a (y - x) over count face slabs (the AO blend of Sec. 5)
+template <class T>
+void launch_blend_faces(const Geom& g, int count, const T* x, const T* y, double a, T* out, cudaStream_t st);
+// out += 0.5 * sum_c (rho_c - star_c) * m_c over one cell slab (fp64)
+template <class T>
+void launch_misfit_dot(const Geom& g, const T* rho, const double* star, const double* m, double* out,
+                       cudaStream_t st);
+// out += scale * sum_e (a_e - b_e)^2 over n entries (fp64)
+template <class T>
+void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st);
 
 }  // namespace stc

@@ -1,0 +1,341 @@
+// Serving runtime: admission of control problems against a device-memory
+// budget and concurrent solves on per-problem CUDA streams (host code; the
+// device work is the library's own kernels through stc_solve).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/stc.h"
+#include "../../include/stc_server.h"
+#include "stc_kernels.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long ticket = 0;
+  stc_params prm{};
+  std::vector<double> rho0, v0, stars, cs;
+  std::vector<int> steps;
+  double tol = 1e-4;
+  int max_admm = 50;
+  double sim_seconds = 0.0;
+  int sim_status = 0;
+  size_t bytes = 0;
+  int bypassed = 0;
+  stc_ticket_info info{};
+  std::vector<double> forces;
+};
+
+}  // namespace
+
+struct stc_server {
+  stc_server_params sp{};
+  std::mutex mu;
+  std::condition_variable cv_work;   // workers: a request may be admissible
+  std::condition_variable cv_done;   // waiters: a ticket changed state
+  std::deque<Request*> queue;        // arrival order
+  std::map<long long, std::unique_ptr<Request>> all;
+  size_t in_use = 0, peak = 0;
+  int running = 0;
+  long long next_ticket = 1;
+  bool stopping = false;
+  Clock::time_point t0 = Clock::now();
+  std::vector<std::thread> workers;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+bool finished(int state) {
+  return state == STC_TICKET_DONE || state == STC_TICKET_FAILED || state == STC_TICKET_CANCELLED;
+}
+
+// First fit in arrival order, except that a request passed over max_bypass
+// times must be admitted before anything behind it.  Called with mu held.
+Request* pick(stc_server* s) {
+  const size_t free_bytes = s->sp.budget_bytes - s->in_use;
+  for (size_t k = 0; k < s->queue.size(); ++k) {
+    Request* r = s->queue[k];
+    if (r->bytes <= free_bytes) {
+      for (size_t j = 0; j < k; ++j) s->queue[j]->bypassed++;
+      s->queue.erase(s->queue.begin() + (long)k);
+      return r;
+    }
+    if (r->bypassed >= s->sp.max_bypass) return nullptr;   // holds the line until it fits
+  }
+  return nullptr;
+}
+
+void set_error(Request* r, const char* msg) {
+  std::strncpy(r->info.error, msg ? msg : "", sizeof(r->info.error) - 1);
+  r->info.error[sizeof(r->info.error) - 1] = 0;
+}
+
+// The solve of one admitted request (no lock held).
+void solve(stc_server* s, Request* r) {
+  if (s->sp.backend == 1) {   // simulated: no CUDA call
+    if (r->sim_seconds > 0) std::this_thread::sleep_for(std::chrono::duration<double>(r->sim_seconds));
+    r->info.status = r->sim_status;
+    const size_t F = (size_t)r->prm.ny * (r->prm.nx + 1) + (size_t)(r->prm.ny + 1) * r->prm.nx;
+    if (r->sim_status == STC_OK || r->sim_status == STC_ERR_NOT_CONVERGED)
+      r->forces.assign((size_t)r->prm.num_steps * F, 0.0);
+    else
+      set_error(r, "simulated failure");
+    return;
+  }
+  cudaStream_t st = nullptr;
+  stc_problem* p = nullptr;
+  stc_status status = STC_OK;
+  if (cudaSetDevice(s->sp.device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    r->info.status = STC_ERR_CUDA;
+    set_error(r, "could not create a stream for the request");
+    return;
+  }
+  status = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), st, &p);
+  if (status == STC_OK && !r->steps.empty())
+    status = stc_set_keyframes(p, (int)r->steps.size(), r->steps.data(), r->stars.data(), r->cs.data());
+  if (status == STC_OK) {
+    status = stc_solve(p, r->tol, r->max_admm, &r->info.report);
+    if (status == STC_OK || status == STC_ERR_NOT_CONVERGED) {
+      const size_t F = (size_t)r->prm.ny * (r->prm.nx + 1) + (size_t)(r->prm.ny + 1) * r->prm.nx;
+      r->forces.resize((size_t)r->prm.num_steps * F);
+      const stc_status g = stc_get_forces(p, r->forces.data(), r->forces.size());
+      if (g != STC_OK) status = g;
+    }
+  }
+  r->info.status = status;
+  if (status != STC_OK && status != STC_ERR_NOT_CONVERGED) set_error(r, stc_last_error());
+  if (p) stc_destroy_problem(p);
+  cudaStreamDestroy(st);
+}
+
+void worker(stc_server* s) {
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    Request* r = nullptr;
+    s->cv_work.wait(lock, [&] { return s->stopping || (r = pick(s)) != nullptr; });
+    if (!r) return;   // stopping
+    s->in_use += r->bytes;
+    s->peak = std::max(s->peak, s->in_use);
+    s->running++;
+    r->info.state = STC_TICKET_RUNNING;
+    r->info.t_admit = s->now();
+    s->cv_done.notify_all();
+    lock.unlock();
+    solve(s, r);
+    lock.lock();
+    s->in_use -= r->bytes;
+    s->running--;
+    r->info.t_done = s->now();
+    r->info.state = (r->info.status == STC_OK || r->info.status == STC_ERR_NOT_CONVERGED) ? STC_TICKET_DONE
+                                                                                          : STC_TICKET_FAILED;
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();   // memory came back: another request may fit
+  }
+}
+
+stc_status fail_arg(const char* msg, stc_status code = STC_ERR_INVALID_ARG) {
+  stc::set_last_error(msg);
+  return code;
+}
+
+Request* find(stc_server* s, long long ticket) {
+  auto it = s->all.find(ticket);
+  return it == s->all.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+void stc_server_default_params(stc_server_params* sp, size_t budget_bytes) {
+  if (!sp) return;
+  std::memset(sp, 0, sizeof(*sp));
+  sp->budget_bytes = budget_bytes;
+  sp->workers = 8;
+  sp->backend = 0;
+  sp->device = 0;
+  sp->max_bypass = 8;
+}
+
+stc_status stc_server_create(const stc_server_params* sp, stc_server** out) {
+  if (!sp || !out || sp->workers < 1 || sp->workers > 256 || sp->budget_bytes == 0 || sp->backend < 0 ||
+      sp->backend > 1 || sp->max_bypass < 0)
+    return fail_arg("invalid server parameters");
+  *out = nullptr;
+  stc_server* s = new (std::nothrow) stc_server();
+  if (!s) return fail_arg("host allocation failed", STC_ERR_OOM);
+  s->sp = *sp;
+  try {
+    for (int k = 0; k < sp->workers; ++k) s->workers.emplace_back(worker, s);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
+    return fail_arg("could not start the worker threads", STC_ERR_OOM);
+  }
+  *out = s;
+  return STC_OK;
+}
+
+stc_status stc_server_submit(stc_server* s, const stc_request* rq, long long* ticket) {
+  if (!s || !rq || !rq->params || !rq->rho0 || !ticket || rq->nkeys < 0 ||
+      (rq->nkeys > 0 && (!rq->key_steps || !rq->key_rho)) || rq->max_admm < 0)
+    return fail_arg("invalid request");
+  size_t bytes = 0;
+  if (stc_problem_bytes(rq->params, rq->nkeys, &bytes) != STC_OK) return fail_arg("invalid problem parameters");
+  const stc_params& prm = *rq->params;
+  for (int k = 0; k < rq->nkeys; ++k)
+    if (rq->key_steps[k] < 1 || rq->key_steps[k] > prm.num_steps) return fail_arg("keyframe step outside 1..N");
+  if (bytes > s->sp.budget_bytes) return fail_arg("request exceeds the server's memory budget", STC_ERR_OOM);
+  auto r = std::make_unique<Request>();
+  try {
+    const size_t C = (size_t)prm.nx * prm.ny;
+    const size_t F = (size_t)prm.ny * (prm.nx + 1) + (size_t)(prm.ny + 1) * prm.nx;
+    r->prm = prm;
+    r->rho0.assign(rq->rho0, rq->rho0 + C);
+    if (rq->v0) r->v0.assign(rq->v0, rq->v0 + F);
+    r->steps.assign(rq->key_steps, rq->key_steps + rq->nkeys);
+    if (rq->nkeys > 0) r->stars.assign(rq->key_rho, rq->key_rho + (size_t)rq->nkeys * C);
+    r->cs.assign(rq->nkeys, 1.0);
+    if (rq->key_c)
+      for (int k = 0; k < rq->nkeys; ++k) r->cs[k] = rq->key_c[k];
+  } catch (const std::bad_alloc&) {
+    return fail_arg("host allocation failed", STC_ERR_OOM);
+  }
+  r->tol = rq->kkt_rel_tol;
+  r->max_admm = rq->max_admm;
+  r->sim_seconds = rq->sim_seconds;
+  r->sim_status = rq->sim_status;
+  r->bytes = bytes;
+  r->info.state = STC_TICKET_QUEUED;
+  r->info.bytes = bytes;
+  r->info.t_admit = r->info.t_done = -1.0;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stopping) return fail_arg("server is shutting down", STC_ERR_BUSY);
+    r->ticket = s->next_ticket++;
+    r->info.t_submit = s->now();
+    *ticket = r->ticket;
+    s->queue.push_back(r.get());
+    s->all[r->ticket] = std::move(r);
+  }
+  s->cv_work.notify_all();
+  return STC_OK;
+}
+
+stc_status stc_server_poll(stc_server* s, long long ticket, stc_ticket_info* info) {
+  if (!s || !info) return fail_arg("null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) return fail_arg("unknown ticket");
+  *info = r->info;
+  return STC_OK;
+}
+
+stc_status stc_server_wait(stc_server* s, long long ticket, double timeout_s, stc_ticket_info* info) {
+  if (!s) return fail_arg("null argument");
+  std::unique_lock<std::mutex> lock(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) return fail_arg("unknown ticket");
+  auto done = [&] { return finished(r->info.state); };
+  if (timeout_s < 0)
+    s->cv_done.wait(lock, done);
+  else
+    s->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), done);
+  if (info) *info = r->info;
+  return STC_OK;
+}
+
+stc_status stc_server_cancel(stc_server* s, long long ticket) {
+  if (!s) return fail_arg("null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) return fail_arg("unknown ticket");
+  if (r->info.state == STC_TICKET_RUNNING) return fail_arg("request is running", STC_ERR_BUSY);
+  if (r->info.state != STC_TICKET_QUEUED) return STC_OK;
+  s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+  r->info.state = STC_TICKET_CANCELLED;
+  r->info.t_done = s->now();
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();   // a request held behind this one may now be admissible
+  return STC_OK;
+}
+
+stc_status stc_server_get_forces(stc_server* s, long long ticket, double* u, size_t len) {
+  if (!s || !u) return fail_arg("null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) return fail_arg("unknown ticket");
+  if (r->info.state != STC_TICKET_DONE) return fail_arg("ticket has no result", STC_ERR_BUSY);
+  if (len != r->forces.size()) return fail_arg("length does not match the force field");
+  std::copy(r->forces.begin(), r->forces.end(), u);
+  return STC_OK;
+}
+
+stc_status stc_server_release(stc_server* s, long long ticket) {
+  if (!s) return fail_arg("null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  Request* r = find(s, ticket);
+  if (!r) return fail_arg("unknown ticket");
+  if (!finished(r->info.state)) return fail_arg("ticket is not finished", STC_ERR_BUSY);
+  s->all.erase(ticket);
+  return STC_OK;
+}
+
+stc_status stc_server_stats_get(stc_server* s, stc_server_stats* out) {
+  if (!s || !out) return fail_arg("null argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  for (auto& kv : s->all) {
+    switch (kv.second->info.state) {
+      case STC_TICKET_QUEUED: out->queued++; break;
+      case STC_TICKET_RUNNING: out->running++; break;
+      case STC_TICKET_DONE: out->done++; break;
+      case STC_TICKET_FAILED: out->failed++; break;
+      default: out->cancelled++; break;
+    }
+  }
+  out->bytes_in_use = s->in_use;
+  out->peak_bytes = s->peak;
+  return STC_OK;
+}
+
+stc_status stc_server_destroy(stc_server* s) {
+  if (!s) return STC_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stopping = true;
+    for (Request* r : s->queue) {
+      r->info.state = STC_TICKET_CANCELLED;
+      r->info.t_done = s->now();
+    }
+    s->queue.clear();
+  }
+  s->cv_work.notify_all();
+  s->cv_done.notify_all();
+  for (auto& t : s->workers) t.join();
+  delete s;
+  return STC_OK;
+}
+
+}  // extern "C"

@@ -21,7 +21,7 @@ FIELDS = dict(V=0, PBAR=1, U=2, P=3, RES_V=4, RES_PBAR=5, RES_U=6, RES_P=7, Z=8,
               RES_IN_U=20, RES_IN_P=21, XOLD_V=22, XOLD_PBAR=23, XOLD_U=24, XOLD_P=25)
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
-          6: "UNSUPPORTED"}
+          6: "UNSUPPORTED", 7: "BUSY"}
 
 
 class StcParams(ctypes.Structure):
@@ -31,14 +31,42 @@ class StcParams(ctypes.Structure):
                 ("taylor_tol", c_double), ("taylor_kmax", c_int), ("eps_stfas", c_double),
                 ("eps_admm", c_double), ("max_vcycles", c_int), ("metric_levels", c_int),
                 ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
-                ("poisson_vcycles", c_int), ("self_advection", c_int)]
+                ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
+                ("cgc_guard", c_int), ("lm_adapt", c_int)]
 
 
 class StcReport(ctypes.Structure):
     _fields_ = [("admm_iters", c_int), ("vcycles", c_int), ("kkt_rel", c_double), ("kkt_abs", c_double),
                 ("f_inf", c_double), ("drho", c_double), ("seconds", c_double),
-                ("seconds_to_1e4", c_double)]
+                ("seconds_to_1e4", c_double), ("rejected_vcycles", c_int), ("lm_shift", c_double),
+                ("density_stop_iter", c_int), ("seconds_to_density_stop", c_double)]
 
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("budget_bytes", c_size_t), ("workers", c_int), ("backend", c_int), ("device", c_int),
+                ("max_bypass", c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("params", ctypes.POINTER(StcParams)), ("rho0", P_double), ("v0", P_double),
+                ("nkeys", c_int), ("key_steps", P_int), ("key_rho", P_double), ("key_c", P_double),
+                ("kkt_rel_tol", c_double), ("max_admm", c_int), ("sim_seconds", c_double),
+                ("sim_status", c_int)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("state", c_int), ("status", c_int), ("bytes", c_size_t), ("t_submit", c_double),
+                ("t_admit", c_double), ("t_done", c_double), ("report", StcReport),
+                ("error", ctypes.c_char * 160)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", c_int), ("running", c_int), ("done", c_int), ("failed", c_int),
+                ("cancelled", c_int), ("bytes_in_use", c_size_t), ("peak_bytes", c_size_t)]
+
+
+P_server = c_void_p
+P_ll = ctypes.POINTER(ctypes.c_longlong)
 
 # name -> (restype, argtypes)
 SIGNATURES = {
@@ -62,9 +90,22 @@ SIGNATURES = {
     "stc_adjoint": (c_int, [c_void_p, c_int, c_double, c_double]),
     "stc_project": (c_int, [c_void_p, c_int, c_int, c_int]),
     "stc_ao": (c_int, [c_void_p, c_int, c_int]),
+    "stc_ao_trace": (c_int, [c_void_p, P_int, c_size_t, P_int]),
     "stc_prepare_targets": (c_int, [c_void_p]),
     "stc_nso_residual": (c_int, [c_void_p, c_int, P_double]),
     "stc_smooth": (c_int, [c_void_p, c_int, c_int]),
+    "stc_problem_bytes": (c_int, [ctypes.POINTER(StcParams), c_int, ctypes.POINTER(c_size_t)]),
+    "stc_server_default_params": (None, [ctypes.POINTER(ServerParams), c_size_t]),
+    "stc_server_create": (c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(c_void_p)]),
+    "stc_server_submit": (c_int, [P_server, ctypes.POINTER(Request), P_ll]),
+    "stc_server_poll": (c_int, [P_server, ctypes.c_longlong, ctypes.POINTER(TicketInfo)]),
+    "stc_server_wait": (c_int, [P_server, ctypes.c_longlong, c_double, ctypes.POINTER(TicketInfo)]),
+    "stc_server_cancel": (c_int, [P_server, ctypes.c_longlong]),
+    "stc_server_get_forces": (c_int, [P_server, ctypes.c_longlong, P_double, c_size_t]),
+    "stc_server_release": (c_int, [P_server, ctypes.c_longlong]),
+    "stc_server_stats_get": (c_int, [P_server, ctypes.POINTER(ServerStats)]),
+    "stc_server_destroy": (c_int, [P_server]),
+    "stc_nso_solve": (c_int, [c_void_p, c_double, c_int, P_int, P_double]),
     "stc_restrict": (c_int, [c_void_p, c_int]),
     "stc_prolong_correct": (c_int, [c_void_p, c_int]),
     "stc_kkt_residual": (c_int, [c_void_p, P_double]),
@@ -231,6 +272,12 @@ class Problem:
     def ao(self, iters=2, warm=False):
         _check(self.lib.stc_ao(self.h, iters, 1 if warm else 0))
 
+    def ao_trace(self):
+        buf = np.zeros(256, dtype=np.int32)
+        n = c_int()
+        _check(self.lib.stc_ao_trace(self.h, buf.ctypes.data_as(P_int), buf.size, ctypes.byref(n)))
+        return [int(a) for a in buf[:min(n.value, buf.size)]]
+
     def prepare_targets(self):
         _check(self.lib.stc_prepare_targets(self.h))
 
@@ -238,6 +285,12 @@ class Problem:
         f = c_double()
         _check(self.lib.stc_nso_residual(self.h, level, ctypes.byref(f)))
         return f.value
+
+    def nso_solve(self, f_target, max_cycles=20):
+        c = c_int()
+        f = c_double()
+        _check(self.lib.stc_nso_solve(self.h, f_target, max_cycles, ctypes.byref(c), ctypes.byref(f)))
+        return f.value, c.value
 
     def smooth(self, level=0, sweeps=1):
         _check(self.lib.stc_smooth(self.h, level, sweeps))
@@ -312,3 +365,107 @@ def adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vel, rho, K, mterm, mu, ba
     vp = lambda p: c_void_p(int(p)) if p else None
     _check(lib.stc_adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vp(vel), vp(rho), vp(K), vp(mterm), vp(mu),
                                          vp(base), alpha, beta, vp(out), vp(stream)))
+
+
+def problem_bytes(params, nkeys=1):
+    """Device bytes of a problem with these parameters and nkeys keyframes
+    (stc_problem_bytes: host arithmetic, no device needed)."""
+    b = c_size_t()
+    _check(load().stc_problem_bytes(ctypes.byref(params), nkeys, ctypes.byref(b)))
+    return b.value
+
+
+TICKET_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+def _info_dict(info):
+    d = {k: getattr(info, k) for k, _ in TicketInfo._fields_ if k not in ("report", "error")}
+    d["state"] = TICKET_STATES[info.state]
+    d["report"] = {k: getattr(info.report, k) for k, _ in StcReport._fields_}
+    d["error"] = info.error.decode(errors="replace")
+    return d
+
+
+class Server:
+    """Serving many control problems on one device (include/stc_server.h)."""
+
+    def __init__(self, budget_bytes, workers=8, backend=0, device=0, max_bypass=8):
+        self.lib = load()
+        sp = ServerParams()
+        self.lib.stc_server_default_params(ctypes.byref(sp), int(budget_bytes))
+        sp.workers, sp.backend, sp.device, sp.max_bypass = workers, backend, device, max_bypass
+        h = c_void_p()
+        _check(self.lib.stc_server_create(ctypes.byref(sp), ctypes.byref(h)))
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, params, rho0, keyframes=None, v0=None, tol=1e-4, max_admm=50, sim_seconds=0.0,
+               sim_status=0):
+        """keyframes: dict step -> (rho_star, c).  Returns the ticket."""
+        keyframes = keyframes or {}
+        rho0 = np.ascontiguousarray(rho0, dtype=np.float64).ravel()
+        steps = sorted(keyframes)
+        ks = np.array(steps, dtype=np.int32)
+        kr = np.ascontiguousarray(np.array([keyframes[k][0] for k in steps], dtype=np.float64).reshape(-1))
+        kc = np.array([keyframes[k][1] for k in steps], dtype=np.float64)
+        v0a = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64).ravel()
+        rq = Request()
+        rq.params = ctypes.pointer(params)
+        rq.rho0 = _dptr(rho0)
+        rq.v0 = _dptr(v0a) if v0a is not None else None
+        rq.nkeys = len(steps)
+        rq.key_steps = ks.ctypes.data_as(P_int) if steps else None
+        rq.key_rho = _dptr(kr) if steps else None
+        rq.key_c = _dptr(kc) if steps else None
+        rq.kkt_rel_tol, rq.max_admm = tol, max_admm
+        rq.sim_seconds, rq.sim_status = sim_seconds, sim_status
+        t = ctypes.c_longlong()
+        _check(self.lib.stc_server_submit(self.h, ctypes.byref(rq), ctypes.byref(t)))
+        F = params.ny * (params.nx + 1) + (params.ny + 1) * params.nx
+        self._sizes[t.value] = (params.num_steps, F)
+        return t.value
+
+    def poll(self, ticket):
+        info = TicketInfo()
+        _check(self.lib.stc_server_poll(self.h, ticket, ctypes.byref(info)))
+        return _info_dict(info)
+
+    def wait(self, ticket, timeout=-1.0):
+        info = TicketInfo()
+        _check(self.lib.stc_server_wait(self.h, ticket, float(timeout), ctypes.byref(info)))
+        return _info_dict(info)
+
+    def cancel(self, ticket):
+        _check(self.lib.stc_server_cancel(self.h, ticket))
+
+    def forces(self, ticket):
+        N, F = self._sizes[ticket]
+        out = np.zeros((N, F))
+        _check(self.lib.stc_server_get_forces(self.h, ticket, _dptr(out), out.size))
+        return out
+
+    def release(self, ticket):
+        _check(self.lib.stc_server_release(self.h, ticket))
+        self._sizes.pop(ticket, None)
+
+    def stats(self):
+        st = ServerStats()
+        _check(self.lib.stc_server_stats_get(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stc_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -229,7 +229,10 @@ def test_ao(prec):
     G.set("V", v)
     G.set("LAMBDA", lam)
     G.ao(2)
-    vs_ref, rhos_ref, _ = admm.ao(P, v, lam, iters=2)
+    trace_ref = []
+    vs_ref, rhos_ref, _ = admm.ao(P, v, lam, iters=2, trace=trace_ref)
+    # the blend decisions (halvings per pass) are integers: identical
+    assert G.ao_trace() == trace_ref, (G.ao_trace(), trace_ref)
     vs = G.get("VSTAR")
     for s in range(N):
         assert rel(vs[s], vs_ref[s]) < TOL[prec]["ao"], (s, rel(vs[s], vs_ref[s]))
@@ -240,10 +243,61 @@ def test_ao(prec):
     assert rel(z, vs_ref - lam / P.K) < TOL[prec]["ao"]
     # warm start: continue the fixed-point iteration from the current v*
     G.ao(2, warm=True)
-    vs2_ref, _, _ = admm.ao(P, v, lam, iters=2, start=vs_ref)
+    trace2 = []
+    vs2_ref, _, _ = admm.ao(P, v, lam, iters=2, start=vs_ref, trace=trace2)
+    assert G.ao_trace() == trace2
     vs2 = G.get("VSTAR")
     for s in range(N):
         assert rel(vs2[s], vs2_ref[s]) < 2 * TOL[prec]["ao"], (s, rel(vs2[s], vs2_ref[s]))
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_ao_blend_halvings(prec):
+    """Sec. 5's blend with several halvings per pass (a small K makes the full
+    fixed-point step overshoot; some trials exceed taylor_kmax and count as
+    rejected).  The oracle's decisions have margins >= 3e-5 relative here, far
+    above the fp32 rounding of the objective."""
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, K=0.2)
+    v = velocity_trajectory(nx, ny, N, amp=0.4, seed=7)
+    lam = workloads.random_faces(np.random.default_rng(8), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("V", v)
+    G.set("LAMBDA", lam)
+    G.ao(4)
+    trace_ref = []
+    vs_ref, rhos_ref, ks_ref = admm.ao(P, v, lam, iters=4, trace=trace_ref)
+    assert max(trace_ref) >= 2
+    assert G.ao_trace() == trace_ref, (G.ao_trace(), trace_ref)
+    assert list(G.taylor_orders()) == list(ks_ref)
+    vs = G.get("VSTAR")
+    for s in range(N):
+        assert rel(vs[s], vs_ref[s]) < TOL[prec]["ao"], (s, rel(vs[s], vs_ref[s]))
+    rho = G.get("RHO")
+    for s in range(N + 1):
+        assert rel(rho[s], rhos_ref[s]) < TOL[prec]["ao"]
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_ao_plain(prec):
+    """ao_halvings = -1: the plain Alg. 1 (v* = y every pass)."""
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, K=2.0, ao_halvings=-1)
+    v = velocity_trajectory(nx, ny, N, amp=0.4, seed=7)
+    lam = workloads.random_faces(np.random.default_rng(8), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("V", v)
+    G.set("LAMBDA", lam)
+    G.ao(2)
+    trace_ref = []
+    vs_ref, rhos_ref, _ = admm.ao(P, v, lam, iters=2, trace=trace_ref)
+    assert G.ao_trace() == trace_ref == [0, 0]
+    vs = G.get("VSTAR")
+    for s in range(N):
+        assert rel(vs[s], vs_ref[s]) < TOL[prec]["ao"], (s, rel(vs[s], vs_ref[s]))
+    rho = G.get("RHO")
+    for s in range(N + 1):
+        assert rel(rho[s], rhos_ref[s]) < TOL[prec]["ao"]
 
 
 # ---------------------------------------------------------------------------
