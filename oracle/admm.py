@@ -40,6 +40,8 @@ import numpy as np
 
 from . import advection, kkt, projection, stfas
 
+LM_MAX_RATIO = 4.0 ** 6   # largest LM shift relative to its default
+
 
 def ao(P, v, lam, iters=None, start=None, trace=None):
     """Alg. 1 with Sec. 5's blending safeguard.  Returns (v*, rhos, Ks) with
@@ -108,8 +110,15 @@ def nso(P, x, z, fscale, eps_rel, max_cycles, lm=None):
     subproblem solver of an LM method whose damping is the shift gamma of the
     smoother's v blocks.  A cycle that raises ||f||_inf (or fails: a
     non-finite norm, a singular local solve) is undone and gamma quadrupled;
-    an accepted cycle halves gamma back toward its default.  f itself, and so
-    the fixed point, does not depend on gamma.  Returns (||f||_inf, cycles)."""
+    gamma does not fall during one NSO solve and is halved back toward its
+    default when the next one starts (halving after each accepted cycle made
+    gamma oscillate: every third cycle was undone on rough targets).  gamma
+    stays below LM_MAX_RATIO times its default; a cycle undone at that bound
+    ends the solve (unbounded growth left every later cycle undone).  f
+    itself, and so the fixed point, does not depend on gamma.  Returns
+    (||f||_inf, cycles)."""
+    if lm is not None and P.lm_adapt:
+        lm["gamma"] = max(lm["gamma0"], 0.5 * lm["gamma"])
     f = kkt.state_inf(kkt.nso_residual(P, P.grid, x, z))
     cycles = 0
     while (cycles < 1 or f > eps_rel * fscale) and cycles < max_cycles:
@@ -125,12 +134,13 @@ def nso(P, x, z, fscale, eps_rel, max_cycles, lm=None):
             fn = np.inf
         if fn <= f:
             f = fn
-            lm["gamma"] = max(lm["gamma0"], 0.5 * lm["gamma"])
         else:
             for k in x:
                 x[k] = keep[k]
-            lm["gamma"] = min(4.0 * lm["gamma"], 1e30)
             lm["rejected"] += 1
+            if lm["gamma"] >= LM_MAX_RATIO * lm["gamma0"]:
+                break                          # undone even at the largest shift: give up this solve
+            lm["gamma"] = min(4.0 * lm["gamma"], LM_MAX_RATIO * lm["gamma0"])
     if lm is not None:
         P.lm_shift = lm["gamma"]
     return f, cycles
