@@ -2,11 +2,20 @@
 
 A step is one ADMM iteration of Alg. 3 on the 2D letters workload (128^2 cells,
 40 steps, fp32 state, one blurred disc/bar keyframe at t = T, metric with 6
-Gaussian levels, r = 1e-3): the AO fixed point (2 forward/backward/projection
-passes), a fixed number of STFAS V-cycles, the KKT metric and the multiplier
-update -- every row of the hot path.  The metric is STFAS spacetime cells/s:
-fine cells x timesteps x V-cycles per step / step time (the AO and KKT time
-counts against it).
+Gaussian levels, r = 1e-3): the AO fixed point (2 warm-started
+backward/projection/blend/forward passes), a fixed number of STFAS V-cycles,
+the KKT metric and the multiplier update -- every row of the hot path.  The
+metric is STFAS spacetime cells/s: fine cells x timesteps x V-cycles per step /
+step time (the AO and KKT time counts against it).
+
+Two more legs follow on rank 0 at N = 1 (skip with --no-solve / --serve 0):
+* time to solution: stc_solve on the same workload from scratch, with the
+  seconds until the relative KKT residual first reached 1e-4 (if it did within
+  the iteration cap) and the paper's own stop (Alg. 3's density test);
+* serving: the first --serve requests of the seeded Poisson stream
+  (workloads.config_serving: n in {32..128}, N in [16, 48], 1-3 keyframes,
+  4 requests/s) replayed in real time into stc_server with a 64 GB budget;
+  p50/p99 time to solution (submit to result) and problems/hour.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference];
 N > 1 under torchrun runs one independent replica per GPU (the method has no
@@ -20,6 +29,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -183,8 +194,11 @@ def run_native(args, rank, world, local_rank):
     G.set_keyframes({N_STEPS: (star, 1.0)})
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
+    warm = [False]
+
     def step():
-        G.ao(2)
+        G.ao(2, warm=warm[0])      # Alg. 3 continues the AO fixed point after its first iteration
+        warm[0] = True
         G.vcycle(VCYCLES)
         G.kkt_residual()
         G.admm_update()
@@ -217,13 +231,8 @@ def run_native(args, rank, world, local_rank):
     launches = G.launch_count() - n0
     k_ms, k_n = G.kernel_timing()
     G.set_kernel_timing(False)
-    ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     cells = N_CELLS * N_CELLS * N_STEPS * VCYCLES
-    value = world * cells / (ms * 1e-3)
+    ms, value = aggregate(sum(times) / len(times), cells, world, dev)
 
     # end to end through the public API with host buffers: keyframe up, forces down
     h2d = star.nbytes
@@ -261,8 +270,77 @@ def run_native(args, rank, world, local_rank):
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches * world), "clocks": clocks}
     if cpu is not None:
         line["cpu_baseline"] = cpu_baseline_obj(cpu)
-    print(json.dumps(line), flush=True)
     G.close()
+    if world == 1 and not args.no_solve:
+        line["time_to_solution"] = solve_leg(stc, cfg, star, args.solve_max_admm)
+    if world == 1 and args.serve > 0:
+        line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm)
+    print(json.dumps(line), flush=True)
+
+
+def aggregate(ms, cells, world, device):
+    """Whole-job figures over `world` independent replicas: the step time is the
+    slowest rank's (max over ranks), the throughput all ranks' cells per step
+    over it.  Returns (ms, cells/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * cells / (ms * 1e-3)
+
+
+def solve_leg(stc, cfg, star, max_admm):
+    """stc_solve from scratch on the bench workload (fp32 policy)."""
+    # eps_admm = 0 switches Alg. 3's density test off: the solve runs to the KKT tolerance or the cap
+    prm = stc.default_params(N_CELLS, N_CELLS, N_STEPS, precision=0, r=1e-3, K=1.0, metric_levels=6,
+                             eps_admm=0.0)
+    with stc.Problem(prm, cfg["rho0"]) as G:
+        G.set_keyframes({N_STEPS: (star, 1.0)})
+        t0 = time.perf_counter()
+        rep = G.solve(tol=1e-4, max_admm=max_admm)
+        wall = time.perf_counter() - t0
+    return {"workload": "same as config.workload, solved from v = 0", "tol_kkt_rel": 1e-4,
+            "max_admm": max_admm, "seconds": wall, "admm_iters": rep["admm_iters"],
+            "vcycles": rep["vcycles"], "rejected_vcycles": rep["rejected_vcycles"],
+            "kkt_rel": rep["kkt_rel"], "seconds_to_1e-4": rep["seconds_to_1e4"] if rep["seconds_to_1e4"] >= 0
+            else None, "drho_last": rep["drho"],
+            "paper_stop": {"rule": "Alg. 3: max_i ||rho_i - rho_i^last||_inf < max|rho_0|/100",
+                           "admm_iters": rep["density_stop_iter"] or None,
+                           "seconds": rep["seconds_to_density_stop"] if rep["seconds_to_density_stop"] >= 0
+                           else None},
+            "stopped_by": "kkt" if rep["kkt_rel"] <= 1e-4 else "iteration cap"}
+
+
+def serve_leg(stc, workloads, count, max_admm, budget=64 << 30, workers=8):
+    """Replay the first `count` requests of the seeded stream in real time."""
+    reqs = workloads.config_serving(count)
+    with stc.Server(budget, workers=workers) as S:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            delay = r["arrival"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            n, N = r["nx"], r["N"]
+            prm = stc.default_params(n, n, N, precision=0, r=r["r"], K=1.0,
+                                     metric_levels=max(0, int(np.floor(np.log2(n / 2)))))
+            tickets.append(S.submit(prm, r["rho0"], r["keyframes"], tol=1e-4, max_admm=max_admm))
+        infos = [S.wait(t) for t in tickets]
+        peak = S.stats()["peak_bytes"]
+    lat = [i["t_done"] - i["t_submit"] for i in infos if i["state"] == "done"]
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    kk = [i["report"]["kkt_rel"] for i in infos if i["state"] == "done"]
+    return {"requests": count, "completed": len(lat), "failed": sum(i["state"] == "failed" for i in infos),
+            "p50_s": float(np.percentile(lat, 50)) if lat else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat else None,
+            "problems_per_hour": 3600.0 * len(lat) / span if span > 0 else None,
+            "reached_kkt_1e-4": sum(k <= 1e-4 for k in kk), "kkt_rel_median": float(np.median(kk)) if kk else None,
+            "admm_iters_median": float(np.median([i["report"]["admm_iters"] for i in infos])),
+            "budget_bytes": budget, "peak_bytes": peak, "workers": workers, "max_admm": max_admm,
+            "stream": "workloads.config_serving(seed 4004): Poisson 4/s, n in {32,48,64,96,128}, N in [16,48], "
+                      "1-3 disc/bar keyframes, fp32 policy, stop at KKT 1e-4 or Alg. 3's density test"}
 
 
 def main():
@@ -272,6 +350,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-max-admm", type=int, default=100)
+    ap.add_argument("--serve", type=int, default=24, help="serving requests to replay (0: skip)")
+    ap.add_argument("--serve-max-admm", type=int, default=50)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -84,7 +84,9 @@ typedef struct {
                            only if it does not raise that level's ||res - f||_2 */
   int lm_adapt;         /* 1 (default): Sec. 5's Levenberg-Marquardt safeguard in stc_solve's
                            NSO loop: a V-cycle that raises ||f||_inf is undone and lm_shift
-                           quadrupled; an accepted one halves it back toward its default */
+                           quadrupled (at most 4096x its default; a cycle undone there ends
+                           the NSO solve); each NSO solve starts by halving it back toward
+                           its default */
 } stc_params;
 
 typedef struct {
@@ -224,11 +226,14 @@ stc_status stc_ao(stc_problem* p, int iters, int warm_start);
 stc_status stc_ao_trace(const stc_problem* p, int* halvings, size_t len, int* count);
 /* The NSO solve of Alg. 3's inner loop on the current targets: at least one
  * V-cycle, then V-cycles until ||f||_inf <= f_target or max_cycles, each under
- * the LM safeguard when stc_params.lm_adapt is set (a cycle that raises
- * ||f||_inf is undone and the smoother's shift quadrupled; an accepted one
- * halves it back toward its default).  Outputs (may be NULL): cycles run,
+ * the LM safeguard when stc_params.lm_adapt is set (the smoother's shift is
+ * first halved back toward its default; a cycle that raises ||f||_inf is
+ * undone and the shift quadrupled).  Outputs (may be NULL): cycles run,
  * including undone ones, and the final ||f||_inf. */
 stc_status stc_nso_solve(stc_problem* p, double f_target, int max_cycles, int* cycles, double* f_inf);
+/* The smoother's current LM shift and the V-cycles undone by the safeguard
+ * since the problem was created or stc_solve last started. */
+stc_status stc_lm_info(const stc_problem* p, double* lm_shift, int* rejected);
 /* z = v* - lambda/K on the finest level, restricted to every coarser level. */
 stc_status stc_prepare_targets(stc_problem* p);
 

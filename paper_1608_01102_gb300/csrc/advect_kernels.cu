@@ -516,89 +516,113 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
 // ---------------------------------------------------------------------------
 // keyframe metric: m = c * sum_l G_l^T G_l (rho - rho*), separable Gaussian
 // filters (sigma_l = sigma0 2^l cells, taps to ceil(3 sigma), normalised,
-// clamp-to-edge).  G^T is evaluated as a gather of the clamped-tap matrix.
+// clamp-to-edge).  G^T is evaluated as a gather of the clamped-tap matrix;
+// its first and last columns collect whole tails of the taps, read from a
+// prefix sum of the weights.  Arithmetic in the state type Tc (fp32 in the
+// fp32 policy: the metric term feeds the fp32 adjoint sweep); the weights are
+// formed in fp64 and the result is accumulated into the fp64 metric slab.
 // ---------------------------------------------------------------------------
-__global__ void blur_kernel(int nx, int ny, int axis, int transpose, double sigma, const double* __restrict__ in,
-                            double* out, double scale, int accumulate) {
-  extern __shared__ double w[];
+template <class Tc, class To>
+__global__ void blur_kernel(int nx, int ny, int axis, int transpose, double sigma, const Tc* __restrict__ in,
+                            To* out, double scale, int accumulate) {
+  extern __shared__ double wsm[];
   const int R = (int)ceil(3.0 * sigma);
   const int nt = 2 * R + 1;
-  __shared__ double wsum;
+  double* wd = wsm;              // raw weights, then their prefix sums (fp64)
+  Tc* w = reinterpret_cast<Tc*>(wsm + nt);        // normalised weights
+  Tc* cw = w + nt;                                 // cw[k] = w[0] + ... + w[k]
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     const double d = t - R;
-    w[t] = exp(-d * d / (2.0 * sigma * sigma));
+    wd[t] = exp(-d * d / (2.0 * sigma * sigma));
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int t = 0; t < nt; ++t) s += w[t];
-    wsum = s;
+  // inclusive prefix sums of the raw weights: a parallel scan when the taps
+  // fit the block, else one thread
+  const double raw = threadIdx.x < nt ? wd[threadIdx.x] : 0.0;
+  if (nt <= (int)blockDim.x) {
+    for (int off = 1; off < nt; off <<= 1) {
+      const double add = (threadIdx.x < nt && (int)threadIdx.x >= off) ? wd[threadIdx.x - off] : 0.0;
+      __syncthreads();
+      if (threadIdx.x < nt) wd[threadIdx.x] += add;
+      __syncthreads();
+    }
+  } else {
+    if (threadIdx.x == 0)
+      for (int t = 1; t < nt; ++t) wd[t] += wd[t - 1];
+    __syncthreads();
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nt; t += blockDim.x) w[t] /= wsum;
+  const double inv = 1.0 / wd[nt - 1];
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const double rt = nt <= (int)blockDim.x ? raw : (t > 0 ? wd[t] - wd[t - 1] : wd[0]);
+    w[t] = Tc(rt * inv);
+    cw[t] = Tc(wd[t] * inv);
+  }
   __syncthreads();
   const int n = axis == 0 ? nx : ny;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nx * ny; e += gridDim.x * blockDim.x) {
     const int j = e / nx, i = e % nx;
     const int a = axis == 0 ? i : j;
     auto at = [&](int b) { return axis == 0 ? in[j * nx + b] : in[b * nx + i]; };
-    double acc = 0.0;
+    Tc acc = Tc(0);
     if (!transpose) {
       for (int t = -R; t <= R; ++t) acc += w[t + R] * at(clampi(a + t, 0, n - 1));
     } else {
       // (G^T y)_a = sum_b G[b,a] y_b, G[b,a] = sum_t w_t [clamp(b+t) == a]
       const int lo = a - R < 0 ? 0 : a - R, hi = a + R > n - 1 ? n - 1 : a + R;
-      for (int b = lo; b <= hi; ++b) {
-        double gba = 0.0;
-        if (a == 0 && a == n - 1) {
-          gba = 1.0;
-        } else if (a == 0) {
-          for (int t = -R; t <= -b; ++t) gba += w[t + R];
-        } else if (a == n - 1) {
-          for (int t = n - 1 - b; t <= R; ++t) gba += w[t + R];
-        } else {
-          gba = w[a - b + R];
+      if (n == 1) {
+        acc = at(0);
+      } else if (a == 0) {            // taps t <= -b clamp onto column 0
+        for (int b = lo; b <= hi; ++b) acc += cw[R - b] * at(b);
+      } else if (a == n - 1) {        // taps t >= n-1-b clamp onto column n-1
+        for (int b = lo; b <= hi; ++b) {
+          const int k0 = n - 2 - b + R;      // prefix index just below the tail
+          acc += (cw[2 * R] - (k0 >= 0 ? cw[k0] : Tc(0))) * at(b);
         }
-        acc += gba * at(b);
+      } else {
+        for (int b = lo; b <= hi; ++b) acc += w[a - b + R] * at(b);
       }
     }
-    acc *= scale;
-    if (accumulate) out[e] += acc;
-    else out[e] = acc;
+    const Tc val = acc * Tc(scale);
+    if (accumulate) out[e] += To(val);
+    else out[e] = To(val);
   }
 }
 
-template <class T>
-__global__ void metric_diff_kernel(const T* __restrict__ rho, const double* __restrict__ star, double* d, int C) {
+template <class T, class Tc>
+__global__ void metric_diff_kernel(const T* __restrict__ rho, const double* __restrict__ star, Tc* d, int C) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C; e += gridDim.x * blockDim.x)
-    d[e] = (double)rho[e] - star[e];
+    d[e] = Tc((double)rho[e] - star[e]);
 }
 
-__global__ void scale_kernel(const double* __restrict__ in, double* out, double c, int n) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) out[e] = c * in[e];
+template <class Tc>
+__global__ void scale_kernel(const Tc* __restrict__ in, double* out, double c, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) out[e] = c * (double)in[e];
 }
 
-// tmp0: C doubles, tmp1: 2C doubles
+// tmp0: C doubles, tmp1: 2C doubles (used as arrays of the state type)
 template <class T>
 void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
                    double* out, double* tmp0, double* tmp1, cudaStream_t st) {
   const int C = g.C;
   const int tpb = 256;
   const unsigned nb = (unsigned)((C + tpb - 1) / tpb);
-  metric_diff_kernel<T><<<nb, tpb, 0, st>>>(rho_s, star, tmp0, C);
+  T* d0 = reinterpret_cast<T*>(tmp0);
+  T* d1 = reinterpret_cast<T*>(tmp1);
+  T* d2 = d1 + C;
+  metric_diff_kernel<T, T><<<nb, tpb, 0, st>>>(rho_s, star, d0, C);
   if (levels <= 0) {
-    scale_kernel<<<nb, tpb, 0, st>>>(tmp0, out, c, C);   // C_i = c_i I
+    scale_kernel<T><<<nb, tpb, 0, st>>>(d0, out, c, C);   // C_i = c_i I
     return;
   }
   cudaMemsetAsync(out, 0, sizeof(double) * C, st);
   for (int l = 0; l < levels; ++l) {
     const double sig = sigma0 * (double)(1 << l);
     const int R = (int)ceil(3.0 * sig);
-    const size_t sm = sizeof(double) * (2 * R + 1);
-    blur_kernel<<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 0, sig, tmp0, tmp1, 1.0, 0);        // G_x
-    blur_kernel<<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 0, sig, tmp1, tmp1 + C, 1.0, 0);    // G_y
-    blur_kernel<<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 1, sig, tmp1 + C, tmp1, 1.0, 0);    // G_y^T
-    blur_kernel<<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 1, sig, tmp1, out, c, 1);           // += c G_x^T
+    const size_t sm = sizeof(double) * 3 * (2 * R + 1);
+    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 0, sig, d0, d1, 1.0, 0);          // G_x
+    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 0, sig, d1, d2, 1.0, 0);          // G_y
+    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 1, sig, d2, d1, 1.0, 0);          // G_y^T
+    blur_kernel<T, double><<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 1, sig, d1, out, c, 1);      // += c G_x^T
   }
 }
 

@@ -17,8 +17,37 @@ namespace stc {
 // out = sf * f + sr * res (res may be null).  Rows dropped by the fixed v_0
 // (row 1/2 at t = 0) and wall-face rows are written as 0.
 // Thread x: element index e (a face if e < F, and a cell if e < C);
-// blockIdx.y: time t in [0, N].
+// blockIdx.y: time t in [0, N].  The rows are evaluated by the helpers below,
+// which the SCGS kernel also calls for its own cells (same arithmetic).
 // ---------------------------------------------------------------------------
+// row 1 at interior face e = (j, i) of direction isx, time t >= 1
+template <class T>
+__device__ __forceinline__ T nso_row1(const Geom& g, const CState<T>& x, const T* __restrict__ z, int t, int e,
+                                      bool isx, int j, int i) {
+  const T* vt = x.v + (size_t)t * g.F;
+  const T* um = x.u + (size_t)(t - 1) * g.F;
+  const T* pb = x.pbar + (size_t)t * g.C;
+  T val = ld(um + e) * T(g.idt);
+  if (g.self_adv) val += T(g.self_adv) * (isx ? jtu_x(g, vt, um, j, i) : jtu_y(g, vt, um, j, i));
+  val += isx ? grad_x(g, pb, j, i) : grad_y(g, pb, j, i);
+  if (t < g.N) {
+    const T* ut = x.u + (size_t)t * g.F;
+    val += T(g.a) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * T(g.idt);
+  }
+  return val;
+}
+// row 3 at interior face e = (j, i), time t <= N - 1
+template <class T>
+__device__ __forceinline__ T nso_row3(const Geom& g, const CState<T>& x, int t, int e, bool isx, int j, int i) {
+  const T* vn = x.v + (size_t)(t + 1) * g.F;
+  const T* vt = x.v + (size_t)t * g.F;
+  const T* pp = x.p + (size_t)t * g.C;
+  T val = (ld(vn + e) - ld(vt + e)) * T(g.idt) - ld(x.u + (size_t)t * g.F + e);
+  if (g.self_adv) val += T(g.self_adv) * (isx ? adv_x(g, vn, j, i) : adv_y(g, vn, j, i));
+  val += isx ? grad_x(g, pp, j, i) : grad_y(g, pp, j, i);
+  return val;
+}
+
 template <class T>
 __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z,
                                    CState<T> res, State<T> out, T sf, T sr, double* sq,
@@ -49,17 +78,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
     if (t >= 1) {
       T val = T(0);
       if (interior) {
-        const T* vt = x.v + (size_t)t * g.F;
-        const T* um = x.u + (size_t)(t - 1) * g.F;
-        const T* pb = x.pbar + (size_t)t * g.C;
-        val = ld(um + e) * idt;
-        if (g.self_adv) val += sa * (isx ? jtu_x(g, vt, um, j, i) : jtu_y(g, vt, um, j, i));
-        val += isx ? grad_x(g, pb, j, i) : grad_y(g, pb, j, i);
-        if (t < N) {
-          const T* ut = x.u + (size_t)t * g.F;
-          val += T(g.a) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * idt;
-        }
-        val *= sf;
+        val = nso_row1(g, x, z, t, e, isx, j, i) * sf;
         if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
       }
       out.v[(size_t)t * g.F + e] = val;
@@ -71,13 +90,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
     if (t < N) {
       T val = T(0);
       if (interior) {
-        const T* vn = x.v + (size_t)(t + 1) * g.F;
-        const T* vt = x.v + (size_t)t * g.F;
-        const T* pp = x.p + (size_t)t * g.C;
-        val = (ld(vn + e) - ld(vt + e)) * idt - ld(x.u + (size_t)t * g.F + e);
-        if (g.self_adv) val += sa * (isx ? adv_x(g, vn, j, i) : adv_y(g, vn, j, i));
-        val += isx ? grad_x(g, pp, j, i) : grad_y(g, pp, j, i);
-        val *= sf;
+        val = nso_row3(g, x, t, e, isx, j, i) * sf;
         if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
       }
       out.u[(size_t)t * g.F + e] = val;
@@ -110,6 +123,78 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       acc = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (threadIdx.x == 0) atomicAdd(sq, acc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// f - res restricted to what the SCGS sweep of one colour reads: the rows at
+// the faces of that colour's cells (x-faces of rows j = py mod 2, y-faces of
+// columns i = px mod 2) and at its cells; other entries of `out` are left as
+// they are.  Same rows and arithmetic as nso_residual_kernel with sf = 1,
+// sr = -1.  Thread x: index over (x-faces, y-faces, cells) of the colour;
+// blockIdx.y: time t in [0, N].
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void nso_residual_colour_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res,
+                                           State<T> out, int px, int py, const double* only_if_undone) {
+  const int t = blockIdx.y;
+  if (t > g.N) return;
+  if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
+  const int N = g.N;
+  const int nrx = (g.ny - py + 1) / 2;          // x-face rows j = py, py + 2, ...
+  const int ncy = (g.nx - px + 1) / 2;          // y-face columns i = px, px + 2, ...
+  const int nxf = nrx * (g.nx + 1), nyf = (g.ny + 1) * ncy;
+  const int ncells = ((g.nx - px + 1) / 2) * nrx;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nxf + nyf) {
+    int j, i, f;
+    bool isx = e < nxf;
+    if (isx) {
+      const int r = e / (g.nx + 1);
+      i = e - r * (g.nx + 1);
+      j = py + 2 * r;
+      f = xf(g, j, i);
+    } else {
+      const int q = e - nxf;
+      const int r = q / ncy;
+      j = r;
+      i = px + 2 * (q - r * ncy);
+      f = yf(g, j, i);
+    }
+    const bool interior = isx ? xf_interior(g, j, i) : yf_interior(g, j, i);
+    if (t >= 1) {
+      T val = T(0);
+      if (interior) {
+        val = nso_row1(g, x, z, t, f, isx, j, i);
+        if (res.v) val -= ld(res.v + (size_t)t * g.F + f);
+      }
+      out.v[(size_t)t * g.F + f] = val;
+    }
+    if (t < N) {
+      T val = T(0);
+      if (interior) {
+        val = nso_row3(g, x, t, f, isx, j, i);
+        if (res.u) val -= ld(res.u + (size_t)t * g.F + f);
+      }
+      out.u[(size_t)t * g.F + f] = val;
+    }
+    return;
+  }
+  e -= nxf + nyf;
+  if (e < ncells) {
+    const int ncx = (g.nx - px + 1) / 2;
+    const int j = py + 2 * (e / ncx), i = px + 2 * (e % ncx);
+    const int c = cidx(g, j, i);
+    if (t >= 1) {
+      T val = -divergence(g, x.v + (size_t)t * g.F, j, i);
+      if (res.pbar) val -= ld(res.pbar + (size_t)t * g.C + c);
+      out.pbar[(size_t)t * g.C + c] = val;
+    }
+    if (t < N) {
+      T val = -divergence(g, x.u + (size_t)t * g.F, j, i);
+      if (res.p) val -= ld(res.p + (size_t)t * g.C + c);
+      out.p[(size_t)t * g.C + c] = val;
     }
   }
 }
@@ -888,6 +973,17 @@ void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, 
 
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 
+template <class T>
+void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                cudaStream_t st, const double* only_if_undone) {
+  const int px = colour & 1, py = colour >> 1;
+  const int nrx = colour_extent(g.ny, py), ncy = colour_extent(g.nx, px);
+  const int n = nrx * (g.nx + 1) + (g.ny + 1) * ncy + colour_extent(g.nx, px) * nrx;
+  const int tpb = 128;
+  dim3 grid(blocks_for(n, tpb), g.N + 1);
+  nso_residual_colour_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, px, py, only_if_undone);
+}
+
 template <class S>
 int scgs_cells_per_cta(int N) {
   // one warp per cell, at most 8 per CTA; ~110 KB of shared memory per CTA
@@ -998,6 +1094,8 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
                                        cudaStream_t, double*, const double*);                              \
+  template void launch_nso_residual_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,     \
+                                              cudaStream_t, const double*);                                \
   template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
                                       const double*);                                                      \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \

@@ -187,7 +187,13 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
   Level& L = P->lv[l];
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 4; ++c) {
-      nso_residual(P, l, 1.0, -1.0, L.res, L.tmp, st, nullptr, s == 0 && c == 0 ? first_only_if_undone : nullptr);
+      // f - res where this colour's cells read it, all from the pre-colour state
+      dispatch(L.dbl, [&](auto tag) {
+        using T = decltype(tag);
+        launch_nso_residual_colour<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(L.res), st_of<T>(L.tmp), c, st,
+                                      s == 0 && c == 0 ? first_only_if_undone : nullptr);
+      });
+      count(P, 1);
       const bool ev = timed && P->ev_used < (int)P->ev_start.size();
       if (ev) ck(cudaEventRecordWithFlags(P->ev_start[P->ev_used], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
@@ -374,20 +380,29 @@ void set_lm(stc_problem* P, double lm) {
 // One NSO V-cycle under the Levenberg-Marquardt safeguard of Sec. 5 (the FAS
 // cycle as the subproblem solver of an LM method): a cycle that raises
 // ||f||_inf above f_old, or yields a non-finite norm, is undone and gamma
-// (the shift of the smoother's v blocks) is quadrupled; an accepted cycle
-// halves gamma back toward its default.  The fixed point f = 0 does not
-// depend on gamma.  Returns the residual of the state kept.
-double nso_cycle(stc_problem* P, double f_old) {
+// (the shift of the smoother's v blocks) is quadrupled.  gamma does not fall
+// during one NSO solve (nso_begin halves it back toward its default when the
+// next one starts).  The fixed point f = 0 does not depend on gamma.
+// Returns the residual of the state kept.
+constexpr double kLmMaxRatio = 4096.0;   // largest LM shift relative to its default (4^6)
+
+// *give_up is set when a cycle was undone at the largest shift: the NSO solve
+// ends there (unbounded growth left every later cycle undone).
+double nso_cycle(stc_problem* P, double f_old, bool* give_up) {
+  *give_up = false;
   if (!P->prm.lm_adapt) return run_vcycle(P);
   const double f = run_vcycle(P, true);
-  if (f <= f_old) {
-    if (P->lm > P->lm0) set_lm(P, std::max(P->lm0, 0.5 * P->lm));
-    return f;
-  }
+  if (f <= f_old) return f;
   copy_state(P, P->xb, P->lv[0].x, P->st);
   ++P->rejected;
-  set_lm(P, std::min(4.0 * P->lm, 1e30));
+  if (P->lm >= kLmMaxRatio * P->lm0) *give_up = true;
+  else set_lm(P, std::min(4.0 * P->lm, kLmMaxRatio * P->lm0));
   return f_old;
+}
+
+// start of an NSO solve: the LM shift halves back toward its default
+void nso_begin(stc_problem* P) {
+  if (P->prm.lm_adapt && P->lm > P->lm0) set_lm(P, std::max(P->lm0, 0.5 * P->lm));
 }
 
 // ---------------------------------------------------------------------------
@@ -1046,9 +1061,11 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       double f = read_scalar(p, 0);
       if (p->fscale < 0) p->fscale = f;
       int cycles = 0;
+      nso_begin(p);
       // at least one V-cycle per ADMM iteration, then until the NSO tolerance
-      while ((cycles < 1 || f > prm.eps_stfas * p->fscale) && cycles < prm.max_vcycles) {
-        f = nso_cycle(p, f);
+      bool give_up = false;
+      while ((cycles < 1 || f > prm.eps_stfas * p->fscale) && cycles < prm.max_vcycles && !give_up) {
+        f = nso_cycle(p, f, &give_up);
         ++cycles;
       }
       kkt(p, p->st);
@@ -1256,16 +1273,28 @@ stc_status stc_nso_solve(stc_problem* p, double f_target, int max_cycles, int* c
     return STC_ERR_INVALID_ARG;
   }
   return guarded(p, [&]() {
+    nso_begin(p);
     residual_norm(p, 0, 0, p->st);
     double f = read_scalar(p, 0);
     int c = 0;
-    while ((c < 1 || f > f_target) && c < max_cycles) {
-      f = nso_cycle(p, f);
+    bool give_up = false;
+    while ((c < 1 || f > f_target) && c < max_cycles && !give_up) {
+      f = nso_cycle(p, f, &give_up);
       ++c;
     }
     if (cycles) *cycles = c;
     if (f_inf) *f_inf = f;
   });
+}
+
+stc_status stc_lm_info(const stc_problem* p, double* lm_shift, int* rejected) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (lm_shift) *lm_shift = p->lm;
+  if (rejected) *rejected = p->rejected;
+  return STC_OK;
 }
 
 stc_status stc_smooth(stc_problem* p, int level, int sweeps) {

@@ -15,6 +15,11 @@ void set_last_error(const char* msg);
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
                          cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr);
+// out = f - res at the faces and cells one SCGS colour reads (other entries untouched);
+// only_if_undone as in launch_nso_residual
+template <class T>
+void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                cudaStream_t st, const double* only_if_undone = nullptr);
 // lm_dev (optional): device fp64 Levenberg-Marquardt shift of the v blocks, else g.lm
 template <class T>
 void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,

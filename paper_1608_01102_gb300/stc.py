@@ -106,6 +106,7 @@ SIGNATURES = {
     "stc_server_stats_get": (c_int, [P_server, ctypes.POINTER(ServerStats)]),
     "stc_server_destroy": (c_int, [P_server]),
     "stc_nso_solve": (c_int, [c_void_p, c_double, c_int, P_int, P_double]),
+    "stc_lm_info": (c_int, [c_void_p, P_double, P_int]),
     "stc_restrict": (c_int, [c_void_p, c_int]),
     "stc_prolong_correct": (c_int, [c_void_p, c_int]),
     "stc_kkt_residual": (c_int, [c_void_p, P_double]),
@@ -291,6 +292,11 @@ class Problem:
         f = c_double()
         _check(self.lib.stc_nso_solve(self.h, f_target, max_cycles, ctypes.byref(c), ctypes.byref(f)))
         return f.value, c.value
+
+    def lm_info(self):
+        lm, rej = c_double(), c_int()
+        _check(self.lib.stc_lm_info(self.h, ctypes.byref(lm), ctypes.byref(rej)))
+        return lm.value, rej.value
 
     def smooth(self, level=0, sweeps=1):
         _check(self.lib.stc_smooth(self.h, level, sweeps))

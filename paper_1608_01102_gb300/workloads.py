@@ -120,3 +120,27 @@ def config_letters(n=128, N=40, seed=2002):
     rho0 = gaussian_ball(n, n, (0.5, 0.25), 0.08)
     star = disc_bar_union(n, n, seed, rho0.sum(), 1.5)
     return dict(nx=n, ny=n, N=N, dt=1.0 / N, rho0=rho0, keyframes={N: (star, 1.0)}, r=1e-3)
+
+
+def config_serving(count=256, seed=4004, rate=4.0):
+    """A stream of 2D control requests: Poisson arrivals at ``rate`` per second
+    (exponential gaps), n uniform over {32, 48, 64, 96, 128}, N uniform in
+    [16, 48] (dt = 1/N), m uniform over {1, 2, 3} keyframes at steps
+    round(j N / m), each a seeded blurred (1.5 cells) disc/bar union with the
+    initial mass; the initial density is the ball of config_letters; r = 1e-3.
+    Returns a list of dicts (the config_letters keys plus ``arrival`` in s)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = int(rng.choice([32, 48, 64, 96, 128]))
+        N = int(rng.integers(16, 49))
+        m = int(rng.integers(1, 4))
+        rho0 = gaussian_ball(n, n, (0.5, 0.25), 0.08)
+        kf = {}
+        for j in range(1, m + 1):
+            step = int(round(j * N / m))
+            kf[step] = (disc_bar_union(n, n, int(rng.integers(0, 2**31 - 1)), rho0.sum(), 1.5), 1.0)
+        out.append(dict(nx=n, ny=n, N=N, dt=1.0 / N, rho0=rho0, keyframes=kf, r=1e-3, arrival=t))
+    return out

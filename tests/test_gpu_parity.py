@@ -66,7 +66,7 @@ def test_forward_advection(prec, shape, N):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", PREC)
 @pytest.mark.parametrize("shape,N,levels", [((16, 16), 6, 2), ((24, 12), 5, 1), ((32, 32), 6, 3),
-                                            ((32, 24), 4, 2), ((12, 8), 3, 1)])
+                                            ((32, 24), 4, 2), ((12, 8), 3, 1), ((16, 12), 3, 5)])
 def test_adjoint_sweep(prec, shape, N, levels):
     nx, ny = shape
     star_mid = workloads.gaussian_ball(nx, ny, (0.4, 0.5 * ny / nx), 0.1)
@@ -339,6 +339,33 @@ def test_admm_iterations(prec):
     J_gpu = kkt.objective(P, v)
     J_ref = kkt.objective(P, x["v"])
     assert abs(J_gpu - J_ref) <= (1e-8 if prec == 1 else 1e-4) * J_ref
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5 LM safeguard of the NSO loop on a rough target: the first cycle at the
+# default shift blows up on both sides and is undone, the raised shift converges
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_nso_solve_lm_safeguard(prec):
+    nx, ny, N = 16, 16, 4
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, r=1e-3, K=1.0)
+    z = workloads.random_faces(np.random.default_rng(0), nx, ny, N, 1.0)
+    z[0] = 0.0
+    G.set("VSTAR", z)
+    G.set("LAMBDA", np.zeros_like(z))
+    G.prepare_targets()
+    x = kkt.zero_state(P)
+    lm = dict(gamma=P.lm_shift, gamma0=P.lm_shift, rejected=0)
+    f_ref, c_ref = admm.nso(P, x, z, 1.0, 0.0, 6, lm)
+    f_gpu, c_gpu = G.nso_solve(0.0, 6)
+    gamma, rejected = G.lm_info()
+    assert lm["rejected"] >= 1 and c_gpu == c_ref == 6
+    assert rejected == lm["rejected"] and gamma == lm["gamma"], (rejected, gamma, lm)
+    got = G.get_state()
+    tol = 1e-8 if prec == 1 else 2e-3
+    for k in x:
+        assert rel(got[k], x[k]) < tol, (k, rel(got[k], x[k]))
+    assert abs(f_gpu - f_ref) <= tol * f_ref * 10
 
 
 # ---------------------------------------------------------------------------
