@@ -369,11 +369,16 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
 }
 
 // ---------------------------------------------------------------------------
-// backward sweep.  For s = N-1 .. 1 with mu_s known:
-//   powers P_m = A^m rho_s (m < K_s) -> global scratch
-//   Horner  w_{K-1} = c_K mu, w_{m-1} = c_m mu + A^T w_m  (c_m = dt^m / m!)
-//   grad    = sum_m B(P_m)^T w_m  = (dA[rho_s, v_s]/dv_s)^T mu_s
+// backward sweep.  For s = N-1 .. 1 with mu_s known, with c_m = dt^m / m!:
+//   Taylor terms t_m = c_m A^m rho_s (m < K_s) -> global scratch
+//   Horner  w_{K-1} = c_K mu, w_{m-1} = c_m mu + A^T w_m
+//   grad    = sum_m B(A^m rho_s)^T w_m  = (dA[rho_s, v_s]/dv_s)^T mu_s
 //   T^T mu  = w_{-1};  mu_{s-1} = T^T mu_s - m_s
+// evaluated in the scaled variables w'_m = w_m / c_m, so that every stored
+// quantity stays bounded like the series terms (the raw powers A^m rho grow
+// like ||A||^m and overflowed fp32 at m ~ 17 on strong flows):
+//   w'_{K-1} = (dt/K) mu,  w'_{m-1} = (dt/m)(mu + A^T w'_m),
+//   grad = sum_m B(t_m)^T w'_m,  T^T mu = mu + A^T w'_0.
 // B(x)^T w at a face = QUICK(x)_face * (w_hi - w_lo) / h.
 // ---------------------------------------------------------------------------
 template <class T>
@@ -432,8 +437,9 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       cl.sync();
       face_fluxes(g, s, cur, vx, vy, Ex, Ey);
       __syncthreads();
+      const T ck = T(g.dt / k);
       for (int e = threadIdx.x; e < nown; e += blockDim.x) {
-        const T t = flux_divergence(g, Ex, Ey, e);
+        const T t = ck * flux_divergence(g, Ex, Ey, e);
         nxt[2 * nx + e] = t;
         powers[(size_t)k * g.C + (size_t)s.r0 * nx + e] = t;
       }
@@ -445,34 +451,29 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     }
     for (int e = threadIdx.x; e < ngx; e += blockDim.x) gxs[e] = T(0);
     for (int e = threadIdx.x; e < ngy; e += blockDim.x) gys[e] = T(0);
-    // c_K = dt^K / K!
-    double cK = 1.0;
-    for (int k = 1; k <= K; ++k) cK *= g.dt / k;
-    cl.sync();  // powers visible to the cluster; everyone done with tb buffers
+    cl.sync();  // terms visible to the cluster; everyone done with tb buffers
     cur = tb0;
     nxt = tb1;
 #pragma unroll
     for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
-      if (e < nown) cur[2 * nx + e] = T(cK) * m[q];
+      if (e < nown) cur[2 * nx + e] = T(g.dt / K) * m[q];   // w'_{K-1}
     }
     __syncthreads();
     halo_push(cl, g, s, cur, rank);
-    double cm = cK;
     for (int mm = K - 1; mm >= 0; --mm) {
       cl.sync();
       face_differences(g, s, cur, vx, vy, Ex, Ey, Gx, Gy);
       __syncthreads();
-      // grad += B(P_m)^T w_m on own faces
+      // grad += B(t_m)^T w'_m on own faces
       accumulate_grad(g, s, (mm == 0) ? rs : powers + (size_t)mm * g.C, vx, vy, Gx, Gy, gxs, gys);
-      // w_{m-1} = c_m mu + A^T w_m with c_m = c_{m+1} (m+1) / dt  (c_0 = 1: T^T mu)
-      const double cprev = (mm == 0) ? 1.0 : cm * (mm + 1) / g.dt;
+      // w'_{m-1} = (dt/m)(mu + A^T w'_m); for m = 0 the factor is 1 (T^T mu)
+      const T fac = (mm == 0) ? T(1) : T(g.dt / mm);
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
-        if (e < nown) nxt[2 * nx + e] = T(cprev) * m[q] + apply_AT_cell(g, s, vx, vy, Ex, Ey, e);
+        if (e < nown) nxt[2 * nx + e] = fac * (m[q] + apply_AT_cell(g, s, vx, vy, Ex, Ey, e));
       }
-      cm = cprev;
       __syncthreads();
       halo_push(cl, g, s, nxt, rank);
       T* tmp = cur;

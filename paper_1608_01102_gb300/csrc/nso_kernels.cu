@@ -727,6 +727,9 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   __syncthreads();
 
   // ---- phase C: u blocks from the v solution, x += omega * delta -----------
+  // The old values of the 10 unknowns are all loaded before any store: the
+  // state arrays may alias as far as the compiler knows, so interleaved
+  // read-modify-writes would serialise ten global-memory latencies.
   const T om = T(g.omega);
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
     const int c = item % cpb, t = item / cpb;
@@ -734,6 +737,20 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     if (q >= ncell) continue;
     const int i = 2 * (q % ncx) + (colour & 1);
     const int j = 2 * (q / ncx) + (colour >> 1);
+    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+    const bool actb[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
+    const int cc = cidx(g, j, i);
+    T* fu = x.u + (size_t)t * g.F;
+    T* fv = x.v + (size_t)(t + 1) * g.F;
+    T* fp = x.p + (size_t)t * g.C + cc;
+    T* fpb = x.pbar + (size_t)(t + 1) * g.C + cc;
+    T old_u[4], old_v[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      old_u[a2] = actb[a2] ? fu[fidx[a2]] : T(0);
+      old_v[a2] = actb[a2] ? fv[fidx[a2]] : T(0);
+    }
+    const T old_p = *fp, old_pb = *fpb;
     CellG<S> cg_;
     cg_.init(g, i, j);
     // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
@@ -759,19 +776,14 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
     du[4] = y[4 * cpb] + gw;
-    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
-    const bool actb[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
-    const int cc = cidx(g, j, i);
-    T* fu = x.u + (size_t)t * g.F;
-    T* fv = x.v + (size_t)(t + 1) * g.F;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
       if (actb[a2]) {
-        fu[fidx[a2]] += om * T(du[a2]);
-        fv[fidx[a2]] += om * T(xv1[a2]);
+        fu[fidx[a2]] = old_u[a2] + om * T(du[a2]);
+        fv[fidx[a2]] = old_v[a2] + om * T(xv1[a2]);
       }
-    x.p[(size_t)t * g.C + cc] += om * T(du[4]);
-    x.pbar[(size_t)(t + 1) * g.C + cc] += om * T(xv1[4]);
+    *fp = old_p + om * T(du[4]);
+    *fpb = old_pb + om * T(xv1[4]);
   }
 }
 
