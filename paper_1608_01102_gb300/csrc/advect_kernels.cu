@@ -47,6 +47,26 @@ __device__ __forceinline__ const T* buf_row(const Geom& g, const Slab& s, const 
   return b + (jj - s.r0 + 2) * g.nx;
 }
 
+// Row/column of e = threadIdx.x, threadIdx.x + blockDim.x, ... in a row-major
+// range of rows of length P, advanced without a division per element.
+struct RowWalk {
+  int q, r, dq, dr, P;
+  __device__ __forceinline__ RowWalk(int P_) : P(P_) {
+    q = (int)threadIdx.x / P;
+    r = (int)threadIdx.x - q * P;
+    dq = (int)blockDim.x / P;
+    dr = (int)blockDim.x - dq * P;
+  }
+  __device__ __forceinline__ void next() {
+    q += dq;
+    r += dr;
+    if (r >= P) {
+      r -= P;
+      ++q;
+    }
+  }
+};
+
 // Face arrays of a slab: x-faces of the owned rows [r0, r1) (all columns),
 // y-faces of rows [r0 - 1, r0 + rpc + 1] (row index offset by 1).
 __device__ __forceinline__ int nxf(const Geom& g, const Slab& s) { return s.rpc * (g.nx + 1); }
@@ -55,12 +75,14 @@ __device__ __forceinline__ int nyf(const Geom& g, const Slab& s) { return (s.rpc
 template <class T>
 __device__ void load_velocity(const Geom& g, const Slab& s, const T* vel, T* vx, T* vy) {
   const int nx = g.nx;
-  for (int e = threadIdx.x; e < nxf(g, s); e += blockDim.x) {
-    const int j = s.r0 + e / (nx + 1);
+  RowWalk wx(nx + 1);
+  for (int e = threadIdx.x; e < nxf(g, s); e += blockDim.x, wx.next()) {
+    const int j = s.r0 + wx.q;
     vx[e] = (j < s.r1) ? vel[(size_t)s.r0 * (nx + 1) + e] : T(0);
   }
-  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x) {
-    const int jf = s.r0 - 1 + e / nx, i = e % nx;
+  RowWalk wy(nx);
+  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x, wy.next()) {
+    const int jf = s.r0 - 1 + wy.q, i = wy.r;
     vy[e] = (jf >= 0 && jf <= g.ny && s.r1 > s.r0) ? vel[g.Fx + (size_t)jf * nx + i] : T(0);
   }
 }
@@ -70,8 +92,9 @@ template <class T>
 __device__ void face_fluxes(const Geom& g, const Slab& s, const T* t, const T* vx, const T* vy, T* Fx, T* Fy) {
   const int nx = g.nx;
   const int nown = s.r1 - s.r0;
-  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
-    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+  RowWalk wx(nx + 1);
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x, wx.next()) {
+    const int j = s.r0 + wx.q, i = wx.r;
     T F = T(0);
     const T v = vx[e];
     if (i >= 1 && i <= nx - 1 && v != T(0)) {
@@ -83,8 +106,9 @@ __device__ void face_fluxes(const Geom& g, const Slab& s, const T* t, const T* v
     Fx[e] = F;
   }
   // y-faces r0 .. r1 (local rows 1 .. nown + 1)
-  for (int e = threadIdx.x; e < (nown + 1) * nx; e += blockDim.x) {
-    const int jf = s.r0 + e / nx, i = e % nx;
+  RowWalk wy(nx);
+  for (int e = threadIdx.x; e < (nown + 1) * nx; e += blockDim.x, wy.next()) {
+    const int jf = s.r0 + wy.q, i = wy.r;
     const int le = e + nx;
     T F = T(0);
     const T v = vy[le];
@@ -100,12 +124,11 @@ __device__ void face_fluxes(const Geom& g, const Slab& s, const T* t, const T* v
 
 // (A t)_c = -(1/h) sum_a (F_{c+1/2} - F_{c-1/2}) at owned cell e (slab-local index)
 template <class T>
-__device__ __forceinline__ T flux_divergence(const Geom& g, const T* Fx, const T* Fy, int e) {
+__device__ __forceinline__ T flux_divergence(const Geom& g, const T* Fx, const T* Fy, int lj, int i) {
   const int nx = g.nx;
-  const int lj = e / nx, i = e - (e / nx) * nx;
   const int xr = lj * (nx + 1) + i;
   const int yr = (lj + 1) * nx + i;
-  return -T(g.ih) * (Fx[xr + 1] - Fx[xr] + Fy[yr + nx] - Fy[yr]);
+  return -pick<T>(g.ih, g.ihf) * (Fx[xr + 1] - Fx[xr] + Fy[yr + nx] - Fy[yr]);
 }
 
 // E_f = v_f (w_hi - w_lo) / h on the faces within two cells of the owned rows
@@ -114,9 +137,10 @@ __device__ void face_differences(const Geom& g, const Slab& s, const T* w, const
                                  T* Gx, T* Gy) {
   const int nx = g.nx;
   const int nown = s.r1 - s.r0;
-  const T ih = T(g.ih);
-  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
-    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+  const T ih = pick<T>(g.ih, g.ihf);
+  RowWalk wx(nx + 1);
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x, wx.next()) {
+    const int j = s.r0 + wx.q, i = wx.r;
     T d = T(0);
     if (i >= 1 && i <= nx - 1) {
       const T* row = buf_row(g, s, w, j);
@@ -125,8 +149,9 @@ __device__ void face_differences(const Geom& g, const Slab& s, const T* w, const
     Gx[e] = d;
     Ex[e] = vx[e] * d;
   }
-  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x) {
-    const int jf = s.r0 - 1 + e / nx, i = e % nx;
+  RowWalk wy(nx);
+  for (int e = threadIdx.x; e < nyf(g, s); e += blockDim.x, wy.next()) {
+    const int jf = s.r0 - 1 + wy.q, i = wy.r;
     T d = T(0);
     if (jf >= 1 && jf <= g.ny - 1 && jf <= s.r1 + 1 && s.r1 > s.r0)
       d = (buf_row(g, s, w, jf)[i] - buf_row(g, s, w, jf - 1)[i]) * ih;
@@ -152,9 +177,8 @@ __device__ __forceinline__ T gather_axis(const T* v, const T* E, int stride, int
 
 template <class T>
 __device__ __forceinline__ T apply_AT_cell(const Geom& g, const Slab& s, const T* vx, const T* vy, const T* Ex,
-                                           const T* Ey, int e) {
+                                           const T* Ey, int lj, int i) {
   const int nx = g.nx;
-  const int lj = e / nx, i = e - (e / nx) * nx;
   const int j = s.r0 + lj;
   // x: faces of row j, index i' in [0, nx]
   const T ax = gather_axis(vx + lj * (nx + 1), Ex + lj * (nx + 1), 1, i, nx);
@@ -172,8 +196,9 @@ __device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const 
                                 const T* Gy, T* gxs, T* gys) {
   const int nx = g.nx;
   const int nown = s.r1 - s.r0;
-  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x) {
-    const int j = s.r0 + e / (nx + 1), i = e % (nx + 1);
+  RowWalk wx(nx + 1);
+  for (int e = threadIdx.x; e < nown * (nx + 1); e += blockDim.x, wx.next()) {
+    const int j = s.r0 + wx.q, i = wx.r;
     if (i >= 1 && i <= nx - 1) {
       T c[4];
       quick_coef(vx[e], c);
@@ -182,8 +207,9 @@ __device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const 
                 Gx[e];
     }
   }
-  for (int e = threadIdx.x; e < nown * nx; e += blockDim.x) {
-    const int jf = s.r0 + e / nx, i = e % nx;
+  RowWalk wy(nx);
+  for (int e = threadIdx.x; e < nown * nx; e += blockDim.x, wy.next()) {
+    const int jf = s.r0 + wy.q, i = wy.r;
     if (jf >= 1 && jf <= g.ny - 1) {
       T c[4];
       const int le = e + nx;
@@ -261,14 +287,28 @@ __device__ __forceinline__ Slab make_slab(const Geom& g, int rank) {
   return s;
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
+// Block-wide max of non-negative values.  A max is exact in any precision, so
+// the series' stopping test reduces in the state type (fp64 arithmetic runs at
+// a small fraction of the fp32 rate) and compares with its fp64 threshold
+// only at the end: the decision is the same as reducing in fp64.
+template <class T>
+__device__ __forceinline__ T block_max(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double m = 0.0;
+  T m = T(0);
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
   return m;
+}
+
+// dt / k for k = 1..kmax, formed once per launch in fp64 and rounded to T
+// (the per-term quotient would otherwise be an fp64 division in every thread)
+constexpr int kTaylorKmaxLimit = 256;
+template <class T>
+__device__ __forceinline__ void fill_dt_over_k(const Geom& g, int kmax, T* tab) {
+  for (int k = (int)threadIdx.x + 1; k <= kmax; k += blockDim.x) tab[k] = T(g.dt / k);
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -289,16 +329,21 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
   T* vy = vx + L.fx;
   T* Fx = vy + L.fy;
   T* Fy = Fx + L.fx;
-  double* cmax = reinterpret_cast<double*>(smem_raw + L.cm_off);
-  __shared__ double red[32];
+  T* cmax = reinterpret_cast<T*>(smem_raw + L.cm_off);
+  __shared__ T red[32];
+  __shared__ T dtk[kTaylorKmaxLimit + 1];
+  fill_dt_over_k(g, kmax, dtk);
   const int nown = (s.r1 - s.r0) * g.nx;
 
   T acc[kAdvMaxCellsPerThread], cmp[kAdvMaxCellsPerThread];
+  int clj[kAdvMaxCellsPerThread], cii[kAdvMaxCellsPerThread];   // slab row / column of each owned cell
 #pragma unroll
   for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
     const int e = threadIdx.x + q * blockDim.x;
     acc[q] = (e < nown) ? rho[(size_t)s.r0 * g.nx + e] : T(0);
     cmp[q] = T(0);
+    clj[q] = e / g.nx;
+    cii[q] = e - clj[q] * g.nx;
   }
   int kfail = 0;
   for (int st = 0; st < g.N; ++st) {
@@ -319,34 +364,34 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
     for (int k = 1; k <= kmax; ++k) {
       face_fluxes(g, s, cur, vx, vy, Fx, Fy);
       __syncthreads();
-      const T ck = T(g.dt / k);
-      double lmax = 0.0;
+      const T ck = dtk[k];
+      T lmax = T(0);
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
         if (e < nown) {
-          const T t = ck * flux_divergence(g, Fx, Fy, e);
+          const T t = ck * flux_divergence(g, Fx, Fy, clj[q], cii[q]);
           nxt[2 * g.nx + e] = t;
           // two-sum accumulation of the series
           const T sum = acc[q] + t;
           const T bb = sum - acc[q];
           cmp[q] += (acc[q] - (sum - bb)) + (t - bb);
           acc[q] = sum;
-          lmax = fmax(lmax, fabs((double)t));
+          lmax = fmax(lmax, fabs(t));
         }
       }
-      const double bm = block_max(lmax, red);   // also orders the nxt writes before the push
+      const T bm = block_max(lmax, red);   // also orders the nxt writes before the push
       halo_push(cl, g, s, nxt, rank);
       if (threadIdx.x < kClusterCTAs)
         *cl.map_shared_rank(cmax + (k & 1) * kClusterCTAs + rank, (int)threadIdx.x) = bm;
       cl.sync();
-      double gm = 0.0;
+      T gm = T(0);
 #pragma unroll
       for (int r = 0; r < kClusterCTAs; ++r) gm = fmax(gm, cmax[(k & 1) * kClusterCTAs + r]);
       T* tmp = cur;
       cur = nxt;
       nxt = tmp;
-      if (gm < thresh) {
+      if ((double)gm < thresh) {
         K = k;
         done = true;
         break;
@@ -386,6 +431,8 @@ __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                       const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
                       T* out, T* powers, int kmax) {
+  __shared__ T dtk[kTaylorKmaxLimit + 1];
+  fill_dt_over_k(g, kmax, dtk);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const Slab s = make_slab(g, rank);
@@ -407,10 +454,13 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
   const int ngy = (s.r1 - s.r0) * nx;
 
   T m[kAdvMaxCellsPerThread];
+  int clj[kAdvMaxCellsPerThread], cii[kAdvMaxCellsPerThread];   // slab row / column of each owned cell
 #pragma unroll
   for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
     const int e = threadIdx.x + q * blockDim.x;
     m[q] = (e < nown) ? T(-mterm[(size_t)g.N * g.C + (size_t)s.r0 * nx + e]) : T(0);
+    clj[q] = e / nx;
+    cii[q] = e - clj[q] * nx;
   }
   for (int st = g.N - 1; st >= 1; --st) {
     // every CTA has finished the previous step (halo reads of the term
@@ -437,9 +487,10 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       cl.sync();
       face_fluxes(g, s, cur, vx, vy, Ex, Ey);
       __syncthreads();
-      const T ck = T(g.dt / k);
-      for (int e = threadIdx.x; e < nown; e += blockDim.x) {
-        const T t = ck * flux_divergence(g, Ex, Ey, e);
+      const T ck = dtk[k];
+      RowWalk wc(nx);
+      for (int e = threadIdx.x; e < nown; e += blockDim.x, wc.next()) {
+        const T t = ck * flux_divergence(g, Ex, Ey, wc.q, wc.r);
         nxt[2 * nx + e] = t;
         powers[(size_t)k * g.C + (size_t)s.r0 * nx + e] = t;
       }
@@ -457,7 +508,7 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
 #pragma unroll
     for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
       const int e = threadIdx.x + q * blockDim.x;
-      if (e < nown) cur[2 * nx + e] = T(g.dt / K) * m[q];   // w'_{K-1}
+      if (e < nown) cur[2 * nx + e] = dtk[K] * m[q];   // w'_{K-1}
     }
     __syncthreads();
     halo_push(cl, g, s, cur, rank);
@@ -468,11 +519,11 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       // grad += B(t_m)^T w'_m on own faces
       accumulate_grad(g, s, (mm == 0) ? rs : powers + (size_t)mm * g.C, vx, vy, Gx, Gy, gxs, gys);
       // w'_{m-1} = (dt/m)(mu + A^T w'_m); for m = 0 the factor is 1 (T^T mu)
-      const T fac = (mm == 0) ? T(1) : T(g.dt / mm);
+      const T fac = (mm == 0) ? T(1) : dtk[mm];
 #pragma unroll
       for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
         const int e = threadIdx.x + q * blockDim.x;
-        if (e < nown) nxt[2 * nx + e] = fac * (m[q] + apply_AT_cell(g, s, vx, vy, Ex, Ey, e));
+        if (e < nown) nxt[2 * nx + e] = fac * (m[q] + apply_AT_cell(g, s, vx, vy, Ex, Ey, clj[q], cii[q]));
       }
       __syncthreads();
       halo_push(cl, g, s, nxt, rank);
@@ -684,6 +735,7 @@ static cudaError_t cluster_launch(K kernel, size_t smem, cudaStream_t st, void**
 template <class T>
 cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, double thresh, int kmax, int* err,
                                   cudaStream_t st) {
+  if (kmax < 1 || kmax > kTaylorKmaxLimit) return cudaErrorInvalidValue;   // size of the dt/k table
   Geom gg = g;
   void* args[] = {&gg, (void*)&vel, (void*)&rho, (void*)&K, (void*)&thresh, (void*)&kmax, (void*)&err};
   return cluster_launch(taylor_forward_kernel<T>, adv_layout<T>(g, false).total, st, args);
@@ -693,6 +745,7 @@ template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
                                   cudaStream_t st) {
+  if (kmax < 1 || kmax > kTaylorKmaxLimit) return cudaErrorInvalidValue;   // size of the dt/k table
   Geom gg = g;
   void* args[] = {&gg,          (void*)&vel,  (void*)&rho,   (void*)&K,   (void*)&mterm,  (void*)&mu,
                   (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax};
@@ -772,6 +825,7 @@ extern "C" stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, d
   g.lm = 0.0;
   g.omega = 1.0;
   g.self_adv = 1;
+  set_fp32_copies(g);
   if (!advect_supported(g)) {
     set_last_error("stc_adjoint_sweep_noalloc: grid too large for the on-chip sweep");
     return STC_ERR_UNSUPPORTED;

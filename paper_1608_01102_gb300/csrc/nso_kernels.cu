@@ -2,6 +2,7 @@
 // SCGS smoother of Sec. 4.3 / Eq. HESS, the STFAS transfer operators R and P
 // (Sec. 4.3, Alg. 2) and reductions.
 #include <mutex>
+#include <type_traits>
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
 
@@ -27,12 +28,12 @@ __device__ __forceinline__ T nso_row1(const Geom& g, const CState<T>& x, const T
   const T* vt = x.v + (size_t)t * g.F;
   const T* um = x.u + (size_t)(t - 1) * g.F;
   const T* pb = x.pbar + (size_t)t * g.C;
-  T val = ld(um + e) * T(g.idt);
+  T val = ld(um + e) * pick<T>(g.idt, g.idtf);
   if (g.self_adv) val += T(g.self_adv) * (isx ? jtu_x(g, vt, um, j, i) : jtu_y(g, vt, um, j, i));
   val += isx ? grad_x(g, pb, j, i) : grad_y(g, pb, j, i);
   if (t < g.N) {
     const T* ut = x.u + (size_t)t * g.F;
-    val += T(g.a) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * T(g.idt);
+    val += pick<T>(g.a, g.af) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * pick<T>(g.idt, g.idtf);
   }
   return val;
 }
@@ -42,7 +43,7 @@ __device__ __forceinline__ T nso_row3(const Geom& g, const CState<T>& x, int t, 
   const T* vn = x.v + (size_t)(t + 1) * g.F;
   const T* vt = x.v + (size_t)t * g.F;
   const T* pp = x.p + (size_t)t * g.C;
-  T val = (ld(vn + e) - ld(vt + e)) * T(g.idt) - ld(x.u + (size_t)t * g.F + e);
+  T val = (ld(vn + e) - ld(vt + e)) * pick<T>(g.idt, g.idtf) - ld(x.u + (size_t)t * g.F + e);
   if (g.self_adv) val += T(g.self_adv) * (isx ? adv_x(g, vn, j, i) : adv_y(g, vn, j, i));
   val += isx ? grad_x(g, pp, j, i) : grad_y(g, pp, j, i);
   return val;
@@ -58,9 +59,9 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
   // conditional form (after a guarded coarse-grid correction): the residual
   // already in `out` is current unless the correction was undone
   if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
-  double acc = 0.0;   // sum of squares of this thread's outputs (when sq != nullptr)
+  T acc = T(0);   // sum of squares of this thread's (at most 4) outputs; fp64 across threads
   const int N = g.N;
-  const T idt = T(g.idt);
+  const T idt = pick<T>(g.idt, g.idtf);
   const T sa = T(g.self_adv);
   if (e < g.F) {
     int j, i;
@@ -82,7 +83,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
         if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
       }
       out.v[(size_t)t * g.F + e] = val;
-      acc += (double)val * (double)val;
+      acc += val * val;
     } else {
       out.v[e] = T(0);
     }
@@ -94,7 +95,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
         if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
       }
       out.u[(size_t)t * g.F + e] = val;
-      acc += (double)val * (double)val;
+      acc += val * val;
     }
   }
   if (e < g.C) {
@@ -103,7 +104,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       T val = -divergence(g, x.v + (size_t)t * g.F, j, i) * sf;
       if (res.pbar) val += sr * ld(res.pbar + (size_t)t * g.C + e);
       out.pbar[(size_t)t * g.C + e] = val;
-      acc += (double)val * (double)val;
+      acc += val * val;
     } else {
       out.pbar[e] = T(0);
     }
@@ -111,18 +112,19 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       T val = -divergence(g, x.u + (size_t)t * g.F, j, i) * sf;
       if (res.p) val += sr * ld(res.p + (size_t)t * g.C + e);
       out.p[(size_t)t * g.C + e] = val;
-      acc += (double)val * (double)val;
+      acc += val * val;
     }
   }
   if (sq) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    double w = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     __shared__ double part[32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
     __syncthreads();
     if (threadIdx.x < 32) {
-      acc = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (threadIdx.x == 0) atomicAdd(sq, acc);
+      w = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (threadIdx.x == 0) atomicAdd(sq, w);
     }
   }
 }
@@ -213,50 +215,51 @@ __global__ void nso_residual_colour_kernel(Geom g, CState<T> x, const T* __restr
 // ---------------------------------------------------------------------------
 
 // d Adv_f / d v_g for f, g in (L, R, B, T) faces of cell (j,i), at field v.
-template <class T>
-__device__ void local_adv_jac(const Geom& g, const T* v, int j, int i, T J[4][4]) {
-  const T ih = T(g.ih);
+// (T: element type of v; R: arithmetic type of J)
+template <class T, class R = T>
+__device__ void local_adv_jac(const Geom& g, const T* v, int j, int i, R J[4][4]) {
+  const R ih = pick<R>(g.ih, g.ihf);
   // node interior flags at the four corners
-  auto an = [&](int jj, int ii) -> T {
-    return (ii > 0 && ii < g.nx && jj > 0 && jj < g.ny) ? T(1) : T(0);
+  auto an = [&](int jj, int ii) -> R {
+    return (ii > 0 && ii < g.nx && jj > 0 && jj < g.ny) ? R(1) : R(0);
   };
-  const T a00 = an(j, i), a10 = an(j + 1, i), a01 = an(j, i + 1), a11 = an(j + 1, i + 1);
-  const T w00 = node_omega(g, v, j, i), w10 = node_omega(g, v, j + 1, i);
-  const T w01 = node_omega(g, v, j, i + 1), w11 = node_omega(g, v, j + 1, i + 1);
+  const R a00 = an(j, i), a10 = an(j + 1, i), a01 = an(j, i + 1), a11 = an(j + 1, i + 1);
+  const R w00 = node_omega<T, R>(g, v, j, i), w10 = node_omega<T, R>(g, v, j + 1, i);
+  const R w01 = node_omega<T, R>(g, v, j, i + 1), w11 = node_omega<T, R>(g, v, j + 1, i + 1);
   for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 4; ++c) J[r][c] = T(0);
+    for (int c = 0; c < 4; ++c) J[r][c] = R(0);
   // f = L (x-face (j,i)), s = -1
   if (xf_interior(g, j, i)) {
-    T wb = T(0.5) * (w00 + w10), tv = tv_x(g, v, j, i);
+    R wb = R(0.5) * (w00 + w10), tv = tv_x<T, R>(g, v, j, i);
     // d wbar / d(L,R,B,T)
-    T dL = T(0.5) * (-a00 + a10) * ih, dB = T(0.5) * a00 * ih, dT = T(0.5) * a10 * ih;
+    R dL = R(0.5) * (-a00 + a10) * ih, dB = R(0.5) * a00 * ih, dT = R(0.5) * a10 * ih;
     J[0][0] = -(dL * tv);
-    J[0][2] = -(dB * tv + wb * T(0.25));
-    J[0][3] = -(dT * tv + wb * T(0.25));
+    J[0][2] = -(dB * tv + wb * R(0.25));
+    J[0][3] = -(dT * tv + wb * R(0.25));
   }
   // f = R (x-face (j,i+1)), s = -1
   if (xf_interior(g, j, i + 1)) {
-    T wb = T(0.5) * (w01 + w11), tv = tv_x(g, v, j, i + 1);
-    T dR = T(0.5) * (-a01 + a11) * ih, dB = -T(0.5) * a01 * ih, dT = -T(0.5) * a11 * ih;
+    R wb = R(0.5) * (w01 + w11), tv = tv_x<T, R>(g, v, j, i + 1);
+    R dR = R(0.5) * (-a01 + a11) * ih, dB = -R(0.5) * a01 * ih, dT = -R(0.5) * a11 * ih;
     J[1][1] = -(dR * tv);
-    J[1][2] = -(dB * tv + wb * T(0.25));
-    J[1][3] = -(dT * tv + wb * T(0.25));
+    J[1][2] = -(dB * tv + wb * R(0.25));
+    J[1][3] = -(dT * tv + wb * R(0.25));
   }
   // f = B (y-face (j,i)), s = +1
   if (yf_interior(g, j, i)) {
-    T wb = T(0.5) * (w00 + w01), tv = tv_y(g, v, j, i);
-    T dB = T(0.5) * (a00 - a01) * ih, dL = -T(0.5) * a00 * ih, dR = -T(0.5) * a01 * ih;
+    R wb = R(0.5) * (w00 + w01), tv = tv_y<T, R>(g, v, j, i);
+    R dB = R(0.5) * (a00 - a01) * ih, dL = -R(0.5) * a00 * ih, dR = -R(0.5) * a01 * ih;
     J[2][2] = dB * tv;
-    J[2][0] = dL * tv + wb * T(0.25);
-    J[2][1] = dR * tv + wb * T(0.25);
+    J[2][0] = dL * tv + wb * R(0.25);
+    J[2][1] = dR * tv + wb * R(0.25);
   }
   // f = T (y-face (j+1,i)), s = +1
   if (yf_interior(g, j + 1, i)) {
-    T wb = T(0.5) * (w10 + w11), tv = tv_y(g, v, j + 1, i);
-    T dT = T(0.5) * (a10 - a11) * ih, dL = T(0.5) * a10 * ih, dR = T(0.5) * a11 * ih;
+    R wb = R(0.5) * (w10 + w11), tv = tv_y<T, R>(g, v, j + 1, i);
+    R dT = R(0.5) * (a10 - a11) * ih, dL = R(0.5) * a10 * ih, dR = R(0.5) * a11 * ih;
     J[3][3] = dT * tv;
-    J[3][0] = dL * tv + wb * T(0.25);
-    J[3][1] = dR * tv + wb * T(0.25);
+    J[3][0] = dL * tv + wb * R(0.25);
+    J[3][1] = dR * tv + wb * R(0.25);
   }
 }
 
@@ -433,7 +436,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
   S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u -> y_t [N][5][cpb]
   S* Vb = Bu + (size_t)N * 5 * cpb;                   // v blocks   [cpb][N][kCrStride]
-  const S idt = S(g.idt);
+  const S idt = pick<S>(g.idt, g.idtf);
 
   // ---- phase A: couplings and right-hand sides ----------------------------
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
@@ -445,15 +448,15 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
     const T act[4] = {T(i > 0), T(i < g.nx - 1), T(j > 0), T(j < g.ny - 1)};
     const int cc = cidx(g, j, i);
-    T Jl[4][4];
-    local_adv_jac(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
+    S Jl[4][4];   // in the solve type: the blocks are stored as S
+    local_adv_jac<T, S>(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
     S* U = Us + (size_t)t * 16 * cpb + c;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
       for (int b2 = 0; b2 < 4; ++b2)
         U[(a2 * 4 + b2) * cpb] =
-            S(((a2 == b2 ? T(g.idt) : T(0)) + T(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2]);
+            ((a2 == b2 ? pick<S>(g.idt, g.idtf) : S(0)) + S(g.self_adv) * Jl[a2][b2]) * S(act[a2] * act[b2]);
     S* Ru = Bu + (size_t)t * 5 * cpb + c;
     S* Rv = Vb + ((size_t)c * N + t) * kCrStride + CR_R;
     const T* ru = r.u + (size_t)t * g.F;
@@ -515,7 +518,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
 #pragma unroll
       for (int a2 = 0; a2 < 4; ++a2) PU[a2][b2] = pw[a2];
     }
-    const S diag = (tv < N ? S(g.a) : S(0)) + lm;
+    const S diag = (tv < N ? pick<S>(g.a, g.af) : S(0)) + lm;
     int e = 0;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
@@ -730,7 +733,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   // The old values of the 10 unknowns are all loaded before any store: the
   // state arrays may alias as far as the compiler knows, so interleaved
   // read-modify-writes would serialise ten global-memory latencies.
-  const T om = T(g.omega);
+  const T om = pick<T>(g.omega, g.omegaf);
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
     const int c = item % cpb, t = item / cpb;
     const int q = q0 + c;
@@ -842,10 +845,12 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
                                        const Tc* __restrict__ coc, const double* undo_if_rose) {
   // undo form: subtract the same correction again when the guarded level's
   // residual norm rose (norms[1] after vs norms[0] before; NaN counts as rose)
-  double sgn = 1.0;
+  // interpolation arithmetic: fp64 when either level is fp64, else fp32
+  using W = typename std::conditional<(sizeof(Tf) == 8 || sizeof(Tc) == 8), double, float>::type;
+  W sgn = W(1);
   if (undo_if_rose) {
     if (undo_if_rose[1] <= undo_if_rose[0]) return;
-    sgn = -1.0;
+    sgn = W(-1);
   }
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nfaces = (size_t)nt_face * gf.F;
@@ -855,16 +860,16 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
     const int f = (int)(e - (size_t)(t - t0_face) * gf.F);
     const Tc* n = cnf + (size_t)t * gc.F;
     const Tc* o = cof + (size_t)t * gc.F;
-    double val;
+    W val;
     if (f < gf.Fx) {
       int j = f / (gf.nx + 1), i = f - j * (gf.nx + 1);
       int ja, jb;
       cell_interp(j, gc.ny, ja, jb);
       int ia = i >> 1, ib = (i & 1) ? ia + 1 : ia;
-      double wb = (i & 1) ? 0.5 : 0.0, wa = 1.0 - wb;
-      auto d = [&](int J, int I) { return double(n[xf(gc, J, I)]) - double(o[xf(gc, J, I)]); };
-      double ta = 0.75 * d(ja, ia) + 0.25 * d(jb, ia);
-      double tb = 0.75 * d(ja, ib) + 0.25 * d(jb, ib);
+      W wb = (i & 1) ? W(0.5) : W(0), wa = W(1) - wb;
+      auto d = [&](int J, int I) { return W(n[xf(gc, J, I)]) - W(o[xf(gc, J, I)]); };
+      W ta = W(0.75) * d(ja, ia) + W(0.25) * d(jb, ia);
+      W tb = W(0.75) * d(ja, ib) + W(0.25) * d(jb, ib);
       val = wa * ta + wb * tb;
     } else {
       int qq = f - gf.Fx;
@@ -872,10 +877,10 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
       int ia, ib;
       cell_interp(i, gc.nx, ia, ib);
       int ja = j >> 1, jb = (j & 1) ? ja + 1 : ja;
-      double wb = (j & 1) ? 0.5 : 0.0, wa = 1.0 - wb;
-      auto d = [&](int J, int I) { return double(n[yf(gc, J, I)]) - double(o[yf(gc, J, I)]); };
-      double ta = 0.75 * d(ja, ia) + 0.25 * d(ja, ib);
-      double tb = 0.75 * d(jb, ia) + 0.25 * d(jb, ib);
+      W wb = (j & 1) ? W(0.5) : W(0), wa = W(1) - wb;
+      auto d = [&](int J, int I) { return W(n[yf(gc, J, I)]) - W(o[yf(gc, J, I)]); };
+      W ta = W(0.75) * d(ja, ia) + W(0.25) * d(ja, ib);
+      W tb = W(0.75) * d(jb, ia) + W(0.25) * d(jb, ib);
       val = wa * ta + wb * tb;
     }
     ff[(size_t)t * gf.F + f] += Tf(sgn * val);
@@ -889,8 +894,8 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
     int ja, jb, ia, ib;
     cell_interp(j, gc.ny, ja, jb);
     cell_interp(i, gc.nx, ia, ib);
-    auto d = [&](int J, int I) { return double(n[cidx(gc, J, I)]) - double(o[cidx(gc, J, I)]); };
-    double val = 0.5625 * d(ja, ia) + 0.1875 * d(ja, ib) + 0.1875 * d(jb, ia) + 0.0625 * d(jb, ib);
+    auto d = [&](int J, int I) { return W(n[cidx(gc, J, I)]) - W(o[cidx(gc, J, I)]); };
+    W val = W(0.5625) * d(ja, ia) + W(0.1875) * d(ja, ib) + W(0.1875) * d(jb, ia) + W(0.0625) * d(jb, ib);
     fc[(size_t)t * gf.C + c] += Tf(sgn * val);
   }
 }
@@ -903,23 +908,25 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// max |a| into *out (fp64) and a flag for non-finite entries.  A max is exact
+// in the element type: the reduction runs in T and converts once per block.
 template <class T>
 __global__ void absmax_kernel(const T* __restrict__ a, size_t n, double* out, int* err) {
-  double m = 0.0;
+  T m = T(0);
   bool bad = false;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    double v = fabs((double)a[e]);
-    if (!(v <= 1e300)) bad = true;
+    const T v = fabs(a[e]);
+    if (!isfinite(v)) bad = true;
     else m = fmax(m, v);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ double sm[32];
+  __shared__ T sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x < 32) {
-    m = (threadIdx.x < (blockDim.x + 31) / 32) ? sm[threadIdx.x] : 0.0;
+    m = (threadIdx.x < (blockDim.x + 31) / 32) ? sm[threadIdx.x] : T(0);
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) atomic_max_nonneg(out, m);
+    if (threadIdx.x == 0) atomic_max_nonneg(out, (double)m);
   }
   if (bad && err) atomicOr(err, DEV_NONFINITE);
 }

@@ -4,7 +4,8 @@
 //
 // Q v = v - G phi with (D G) phi = D v on the closed box.  One CTA projects one
 // face field: b = D v, phi and every coarse level live in shared memory (a
-// 128^2 fp32 field needs ~171 KB), red-black Gauss-Seidel V(2,2) cycles with
+// 128^2 fp32 field needs ~171 KB; larger layouts, e.g. 128^2 in fp64, use a
+// per-field scratch in global memory instead), red-black Gauss-Seidel V(2,2) cycles with
 // average restriction and bilinear prolongation, the coarsest level (<= 64
 // cells) by 30 parallel red-black Gauss-Seidel sweeps in fp64, then v - G phi
 // written back.
@@ -74,12 +75,25 @@ __device__ __forceinline__ T lap(const T* phi, int nx, int ny, int j, int i, T i
 
 template <class T>
 __global__ void __launch_bounds__(kPoissonThreads, 1)
-project_kernel(Geom g, T* fields, int vcycles) {
+project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+  // all levels' phi and b: shared memory, or this field's slice of the scratch
+  T* sm = scratch ? scratch + (size_t)blockIdx.x * per_field : reinterpret_cast<T*>(smem_raw);
   __shared__ double cb[64], cp[64];
   __shared__ double cmean;
+  // h_l^2 and 1/h_l^2 per level, h_l = h 2^l: formed once (scaling by 4^l is
+  // exact, so these equal the per-level fp64 expressions rounded to T)
+  __shared__ T h2tab[16], ih2tab[16];
   const PLevels L = poisson_levels(g.nx, g.ny);
+  if (threadIdx.x == 0) {
+    const T h2 = T(g.h * g.h), ih2 = T(1.0 / (g.h * g.h));
+    T s4 = T(1);
+    for (int l = 0; l < L.n && l < 16; ++l, s4 *= T(4)) {
+      h2tab[l] = h2 * s4;
+      ih2tab[l] = ih2 / s4;
+    }
+  }
+  __syncthreads();
   T* v = fields + (size_t)blockIdx.x * g.F;
   const int nx = g.nx, ny = g.ny;
   T* phi0 = sm + L.off[0];
@@ -96,8 +110,7 @@ project_kernel(Geom g, T* fields, int vcycles) {
     // descend
     for (int l = 0; l < nl - 1; ++l) {
       const int lx = L.nx[l], ly = L.ny[l];
-      const double h = g.h * (double)(1 << l);
-      const T h2 = T(h * h), ih2 = T(1.0 / (h * h));
+      const T h2 = h2tab[l], ih2 = ih2tab[l];
       T* phi = sm + L.off[l];
       T* b = phi + (size_t)lx * ly;
       if (l > 0) {
@@ -151,16 +164,18 @@ project_kernel(Geom g, T* fields, int vcycles) {
       if (e < n) cb[e] -= cmean;
       __syncthreads();
       const int j = e / lx, i = e - (e / lx) * lx;
+      // neighbour count of this cell, and its reciprocal formed once
+      const int kn = (i > 0) + (i < lx - 1) + (j > 0) + (j < ly - 1);
+      const double ikn = kn > 0 ? 1.0 / kn : 0.0;
       for (int it = 0; it < 30; ++it)
         for (int colour = 0; colour < 2; ++colour) {
           if (e < n && ((i + j) & 1) == colour) {
             double sacc = 0.0;
-            int k = 0;
-            if (i > 0) { sacc += cp[e - 1]; ++k; }
-            if (i < lx - 1) { sacc += cp[e + 1]; ++k; }
-            if (j > 0) { sacc += cp[e - lx]; ++k; }
-            if (j < ly - 1) { sacc += cp[e + lx]; ++k; }
-            cp[e] = (sacc - h2 * cb[e]) / k;
+            if (i > 0) sacc += cp[e - 1];
+            if (i < lx - 1) sacc += cp[e + 1];
+            if (j > 0) sacc += cp[e - lx];
+            if (j < ly - 1) sacc += cp[e + lx];
+            cp[e] = (sacc - h2 * cb[e]) * ikn;
           }
           __syncthreads();
         }
@@ -171,8 +186,7 @@ project_kernel(Geom g, T* fields, int vcycles) {
     for (int l = nl - 2; l >= 0; --l) {
       const int lx = L.nx[l], ly = L.ny[l];
       const int cx = L.nx[l + 1], cy = L.ny[l + 1];
-      const double h = g.h * (double)(1 << l);
-      const T h2 = T(h * h);
+      const T h2 = h2tab[l];
       T* phi = sm + L.off[l];
       T* b = phi + (size_t)lx * ly;
       const T* pc = sm + L.off[l + 1];
@@ -199,12 +213,12 @@ project_kernel(Geom g, T* fields, int vcycles) {
   for (int e = threadIdx.x; e < g.F; e += blockDim.x) {
     if (e < g.Fx) {
       const int j = e / (nx + 1), i = e - j * (nx + 1);
-      if (i >= 1 && i <= nx - 1) v[e] -= (phi0[j * nx + i] - phi0[j * nx + i - 1]) * T(g.ih);
+      if (i >= 1 && i <= nx - 1) v[e] -= (phi0[j * nx + i] - phi0[j * nx + i - 1]) * pick<T>(g.ih, g.ihf);
       else v[e] = T(0);
     } else {
       const int q = e - g.Fx;
       const int j = q / nx, i = q - j * nx;
-      if (j >= 1 && j <= ny - 1) v[e] -= (phi0[j * nx + i] - phi0[(j - 1) * nx + i]) * T(g.ih);
+      if (j >= 1 && j <= ny - 1) v[e] -= (phi0[j * nx + i] - phi0[(j - 1) * nx + i]) * pick<T>(g.ih, g.ihf);
       else v[e] = T(0);
     }
   }
@@ -216,16 +230,20 @@ size_t project_smem(const Geom& g, size_t tsize) {
   return (L.off[l] + 2 * (size_t)L.nx[l] * L.ny[l]) * tsize;
 }
 
-bool project_supported(const Geom& g, size_t tsize) {
+bool project_supported(const Geom& g, size_t) {
   const PLevels L = poisson_levels(g.nx, g.ny);
   const int l = L.n - 1;
-  return project_smem(g, tsize) <= 227 * 1024 && L.nx[l] * L.ny[l] <= 64;
+  return L.nx[l] * L.ny[l] <= 64;   // the coarsest solve's fp64 arrays
 }
 
+bool project_needs_scratch(const Geom& g, size_t tsize) { return project_smem(g, tsize) > kProjectSmemLimit; }
+
 template <class T>
-cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st) {
+cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch) {
   if (count <= 0) return cudaSuccess;
-  const size_t sm = project_smem(g, sizeof(T));
+  const size_t layout = project_smem(g, sizeof(T));
+  if (project_needs_scratch(g, sizeof(T)) && !scratch) return cudaErrorInvalidValue;
+  const size_t sm = scratch ? 0 : layout;
   // raise the cap once to the opt-in maximum (per-size settings would race
   // between host threads solving problems of different sizes)
   static std::once_flag once;
@@ -243,7 +261,7 @@ cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cud
                                       optin - (int)fa.sharedSizeBytes);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  project_kernel<T><<<count, kPoissonThreads, sm, st>>>(g, fields, vcycles);
+  project_kernel<T><<<count, kPoissonThreads, sm, st>>>(g, fields, vcycles, scratch, layout / sizeof(T));
   return cudaGetLastError();
 }
 
@@ -282,11 +300,11 @@ __global__ void kkt_force_rhs_kernel(Geom g, const T* __restrict__ v, T* out) {
   T val = T(0);
   if (e < g.Fx) {
     const int j = e / (g.nx + 1), i = e - j * (g.nx + 1);
-    if (xf_interior(g, j, i)) val = (vn[e] - vt[e]) * T(g.idt) + T(g.self_adv) * adv_x(g, vn, j, i);
+    if (xf_interior(g, j, i)) val = (vn[e] - vt[e]) * pick<T>(g.idt, g.idtf) + T(g.self_adv) * adv_x(g, vn, j, i);
   } else {
     const int q = e - g.Fx;
     const int j = q / g.nx, i = q - j * g.nx;
-    if (yf_interior(g, j, i)) val = (vn[e] - vt[e]) * T(g.idt) + T(g.self_adv) * adv_y(g, vn, j, i);
+    if (yf_interior(g, j, i)) val = (vn[e] - vt[e]) * pick<T>(g.idt, g.idtf) + T(g.self_adv) * adv_y(g, vn, j, i);
   }
   out[(size_t)t * g.F + e] = val;
 }
@@ -314,8 +332,8 @@ __global__ void kkt_grad_rhs_kernel(Geom g, const T* __restrict__ v, const T* __
     if (inter && g.self_adv) jt = jtu_y(g, vt, um, j, i);
   }
   if (inter) {
-    T s = um[e] * T(g.idt) + jt;
-    if (t < g.N) s -= u[(size_t)t * g.F + e] * T(g.idt);
+    T s = um[e] * pick<T>(g.idt, g.idtf) + jt;
+    if (t < g.N) s -= u[(size_t)t * g.F + e] * pick<T>(g.idt, g.idtf);
     val = T(r) * s + dens[(size_t)t * g.F + e];
   }
   out[(size_t)t * g.F + e] = val;
@@ -427,7 +445,7 @@ void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* o
 }
 
 #define STC_POI_INST(T)                                                                                        \
-  template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t);                            \
+  template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t, T*);                        \
   template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, int, cudaStream_t);             \
   template void launch_axpby_faces<T>(const Geom&, int, const T*, double, const T*, double, T*, cudaStream_t); \
   template void launch_kkt_force_rhs<T>(const Geom&, const T*, T*, cudaStream_t);                             \

@@ -92,6 +92,7 @@ struct stc_problem {
   int rejected = 0;               // V-cycles undone by the LM safeguard
   double *mterm = nullptr, *mtmp0 = nullptr, *mtmp1 = nullptr, *star = nullptr;
   size_t star_bytes = 0;
+  void* pscratch = nullptr;       // projection level arrays when they do not fit on chip
   std::vector<int> key_steps;
   std::vector<double> key_c;
   double* dscal = nullptr;  // device fp64 scalars
@@ -149,6 +150,7 @@ Geom make_geom(const stc_params& prm, int nx, int ny, double h) {
   g.lm = prm.lm_shift < 0 ? 1.0 / (prm.dt * prm.dt) : prm.lm_shift;
   g.omega = prm.scgs_omega;
   g.self_adv = prm.self_advection ? 1 : 0;
+  set_fp32_copies(g);
   return g;
 }
 
@@ -450,7 +452,7 @@ void project(stc_problem* P, void* fields, int count, cudaStream_t st) {
   const Geom& g = P->lv[0].g;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st), "project");
+    ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st, (T*)P->pscratch), "project");
   });
   if (count > 0) ::count(P, 1);
 }
@@ -785,6 +787,8 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
            b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
+  Geom g0 = make_geom(prm, prm.nx, prm.ny, 1.0 / prm.nx);
+  if (project_needs_scratch(g0, ts)) total += b((N + 1) * project_smem(g0, ts));
   return total;
 }
 
@@ -881,7 +885,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     ck(cudaGetDevice(&dev), "get device");
     int smem_optin = 0;
     ck(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if ((int)advect_smem_adjoint(g0, P->ts) > smem_optin || (int)project_smem(g0, P->ts) > smem_optin)
+    if ((int)advect_smem_adjoint(g0, P->ts) > smem_optin ||
+        (!project_needs_scratch(g0, P->ts) && (int)project_smem(g0, P->ts) > smem_optin))
       fail(STC_ERR_UNSUPPORTED, "shared memory of this device too small for the grid");
     ck(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "stream");
     const int N = prm.num_steps;
@@ -927,6 +932,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->mtmp1 = (double*)dalloc(P, 2 * C * sizeof(double));
     P->dscal = (double*)dalloc(P, 16 * sizeof(double));
     P->derr = (int*)dalloc(P, sizeof(int));
+    // projections run on at most N + 1 fields at once (stc_project on V or KKT_G)
+    if (project_needs_scratch(g0, ts)) P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
     ck(cudaMallocHost(&P->hscal, 16 * sizeof(double)), "pinned");
     ck(cudaMallocHost(&P->herr, sizeof(int)), "pinned");
     // inputs: rho_0 into rho[0] of every density buffer, v_0

@@ -24,7 +24,23 @@ struct Geom {
   double lm;         // Levenberg-Marquardt shift of the smoother's v blocks
   double omega;      // SCGS under-relaxation
   int self_adv;      // 1: Adv on (0 only for linear saddle tests)
+  // the same scalars rounded to fp32 on the host (set_fp32_copies): fp32
+  // kernels read these instead of converting fp64 scalars in every thread
+  // (conversions from fp64 run at the much lower fp64 rate)
+  float ihf, idtf, af, omegaf;
 };
+
+inline void set_fp32_copies(Geom& g) {
+  g.ihf = (float)g.ih;
+  g.idtf = (float)g.idt;
+  g.af = (float)g.a;
+  g.omegaf = (float)g.omega;
+}
+
+// geometry scalar in the arithmetic type: the fp32 copy or the fp64 value
+template <class T> __host__ __device__ __forceinline__ T pick(double d, float f);
+template <> __host__ __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __host__ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 // NSO unknowns of one level: v (N+1)F, pbar (N+1)C, u N F, p N C  (p[i] = p_{i+1}).
 template <class T>
@@ -65,26 +81,27 @@ __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 // omega_bar the mean of a face's two nodes and vbar the mean of the four
 // surrounding transverse faces; Adv = 0 on wall faces.
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ T node_omega(const Geom& g, const T* v, int j, int i) {
-  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return T(0);
-  T a = ld(v + yf(g, j, i)) - ld(v + yf(g, j, i - 1));
-  T b = ld(v + xf(g, j, i)) - ld(v + xf(g, j - 1, i));
-  return (a - b) * T(g.ih);
+// (T: element type of v; R: arithmetic type, T unless a caller asks otherwise)
+template <class T, class R = T>
+__device__ __forceinline__ R node_omega(const Geom& g, const T* v, int j, int i) {
+  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return R(0);
+  R a = R(ld(v + yf(g, j, i))) - R(ld(v + yf(g, j, i - 1)));
+  R b = R(ld(v + xf(g, j, i))) - R(ld(v + xf(g, j - 1, i)));
+  return (a - b) * pick<R>(g.ih, g.ihf);
 }
 
 // transverse mean at an interior x-face (j,i)
-template <class T>
-__device__ __forceinline__ T tv_x(const Geom& g, const T* v, int j, int i) {
-  return T(0.25) * (ld(v + yf(g, j, i - 1)) + ld(v + yf(g, j, i)) + ld(v + yf(g, j + 1, i - 1)) +
-                    ld(v + yf(g, j + 1, i)));
+template <class T, class R = T>
+__device__ __forceinline__ R tv_x(const Geom& g, const T* v, int j, int i) {
+  return R(0.25) * (R(ld(v + yf(g, j, i - 1))) + R(ld(v + yf(g, j, i))) + R(ld(v + yf(g, j + 1, i - 1))) +
+                    R(ld(v + yf(g, j + 1, i))));
 }
 
 // transverse mean at an interior y-face (j,i)
-template <class T>
-__device__ __forceinline__ T tv_y(const Geom& g, const T* v, int j, int i) {
-  return T(0.25) * (ld(v + xf(g, j - 1, i)) + ld(v + xf(g, j - 1, i + 1)) + ld(v + xf(g, j, i)) +
-                    ld(v + xf(g, j, i + 1)));
+template <class T, class R = T>
+__device__ __forceinline__ R tv_y(const Geom& g, const T* v, int j, int i) {
+  return R(0.25) * (R(ld(v + xf(g, j - 1, i))) + R(ld(v + xf(g, j - 1, i + 1))) + R(ld(v + xf(g, j, i))) +
+                    R(ld(v + xf(g, j, i + 1))));
 }
 
 template <class T>
@@ -140,7 +157,7 @@ __device__ __forceinline__ T node_q(const Geom& g, const T* v, const T* u, int j
 // transverse-mean terms through vbar of the four y-faces averaging this face.
 template <class T>
 __device__ T jtu_x(const Geom& g, const T* v, const T* u, int j, int i) {
-  T r = (node_q(g, v, u, j + 1, i) - node_q(g, v, u, j, i)) * T(g.ih);
+  T r = (node_q(g, v, u, j + 1, i) - node_q(g, v, u, j, i)) * pick<T>(g.ih, g.ihf);
   T s = T(0);
   if (yf_interior(g, j, i - 1)) s += wbar_y(g, v, j, i - 1) * ld(u + yf(g, j, i - 1));
   if (yf_interior(g, j, i)) s += wbar_y(g, v, j, i) * ld(u + yf(g, j, i));
@@ -151,7 +168,7 @@ __device__ T jtu_x(const Geom& g, const T* v, const T* u, int j, int i) {
 
 template <class T>
 __device__ T jtu_y(const Geom& g, const T* v, const T* u, int j, int i) {
-  T r = (node_q(g, v, u, j, i) - node_q(g, v, u, j, i + 1)) * T(g.ih);
+  T r = (node_q(g, v, u, j, i) - node_q(g, v, u, j, i + 1)) * pick<T>(g.ih, g.ihf);
   T s = T(0);
   if (xf_interior(g, j - 1, i)) s -= wbar_x(g, v, j - 1, i) * ld(u + xf(g, j - 1, i));
   if (xf_interior(g, j - 1, i + 1)) s -= wbar_x(g, v, j - 1, i + 1) * ld(u + xf(g, j - 1, i + 1));
@@ -164,18 +181,18 @@ __device__ T jtu_y(const Geom& g, const T* v, const T* u, int j, int i) {
 template <class T>
 __device__ __forceinline__ T grad_x(const Geom& g, const T* p, int j, int i) {
   if (!xf_interior(g, j, i)) return T(0);
-  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j, i - 1))) * T(g.ih);
+  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j, i - 1))) * pick<T>(g.ih, g.ihf);
 }
 template <class T>
 __device__ __forceinline__ T grad_y(const Geom& g, const T* p, int j, int i) {
   if (!yf_interior(g, j, i)) return T(0);
-  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j - 1, i))) * T(g.ih);
+  return (ld(p + cidx(g, j, i)) - ld(p + cidx(g, j - 1, i))) * pick<T>(g.ih, g.ihf);
 }
 
 template <class T>
 __device__ __forceinline__ T divergence(const Geom& g, const T* v, int j, int i) {
   return (ld(v + xf(g, j, i + 1)) - ld(v + xf(g, j, i)) + ld(v + yf(g, j + 1, i)) -
-          ld(v + yf(g, j, i))) * T(g.ih);
+          ld(v + yf(g, j, i))) * pick<T>(g.ih, g.ihf);
 }
 
 // ---------------------------------------------------------------------------

@@ -70,10 +70,15 @@ bool advect_supported(const Geom& g);
 // --- projection and elementwise helpers (poisson_kernels.cu) ---------------
 // In-place solenoidal projection of `count` face fields (stride F): Q v = v - G phi
 // with (D G) phi = D v solved by an on-chip multigrid V(2,2) cycle.
+// scratch: (count x project_smem / tsize) elements of global memory, required
+// when project_needs_scratch (the level arrays then live there, not on chip)
 template <class T>
-cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st);
+cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st,
+                           T* scratch = nullptr);
 size_t project_smem(const Geom& g, size_t tsize);
 bool project_supported(const Geom& g, size_t tsize);
+constexpr size_t kProjectSmemLimit = 200 * 1024;   // on-chip layout limit (opt-in 227 KB less static use)
+bool project_needs_scratch(const Geom& g, size_t tsize);
 
 template <class T>
 void launch_ao_init(const Geom& g, const T* v, const T* lam, double invK, T* w, T* vstar, int warm,

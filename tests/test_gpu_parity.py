@@ -39,6 +39,22 @@ def test_projection(prec, shape):
         assert np.max(np.abs(d)) < TOL[prec]["project"] * np.max(np.abs(mac.div(P.grid, w[i]))) * 10
 
 
+def test_projection_with_global_scratch_fp64_128():
+    """128^2 in fp64 does not fit the on-chip multigrid layout: the level
+    arrays move to a per-field global scratch (same arithmetic)."""
+    nx = ny = 128
+    P, G = make_pair(nx, ny, N=2, precision=1, levels=0)
+    rng = np.random.default_rng(2)
+    w = workloads.random_faces(rng, nx, ny, 2)
+    w[1] += workloads.swirl_velocity(nx, ny, 3.0)
+    G.set("W", w)
+    G.project("W", 0, 2)
+    out = G.get("W")
+    for i in range(2):
+        ref = projection.project(P.grid, w[i])
+        assert rel(out[i], ref) < TOL[1]["project"] * 10, (i, rel(out[i], ref))
+
+
 # ---------------------------------------------------------------------------
 # a3: forward advection (Taylor exponential, adaptive order)
 # ---------------------------------------------------------------------------
