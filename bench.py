@@ -42,6 +42,10 @@ WORKLOAD = ("2D smoke control, 128^2 cells, 40 timesteps, dt=1/40, fp32 state wi
             "levels; one ADMM iteration per step = AO(2) + %d V(2,2)-cycles + KKT metric + lambda update"
             % VCYCLES)
 ORACLE_STEPS = 2  # timesteps of the bounded oracle sample (same grid, same per-step work)
+# dram__bytes_read.sum + dram__bytes_write.sum of one finest-level SCGS colour launch
+# of this workload (ncu --set full, profiles/scgs_colour_finest_letters_128x40.md);
+# to be re-measured whenever scgs_colour_kernel changes
+SCGS_FINEST_DRAM_BYTES = 23261184 + 512
 
 
 def _peaks():
@@ -255,7 +259,7 @@ def run_native(args, rank, world, local_rank):
     peak, kind = _peaks()
     achieved = bytes_per_launch / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
+            "frac": achieved / peak if achieved else None, "traffic": SCGS_FINEST_DRAM_BYTES,
             "kernel": "scgs_colour_kernel<float> (finest level)", "peak_kind": kind,
             "launches_timed": k_n, "avg_launch_us": 1e3 * k_ms / k_n if k_n else None,
             "algorithmic_bytes_per_launch": bytes_per_launch}
