@@ -35,6 +35,11 @@ Readings:
 * NSO target z_i = v*_i - lambda_i / K (scaled ADMM form of Eq. optAdmm).
 * stopping: the relative KKT residual R(v) = ||g(v)|| / ||g(v_start)|| <= tol,
   or Alg. 3's max_i ||rho_i^last - rho_i||_inf < eps_admm.
+* Sec. 5's augmented-Lagrangian fallback (``P.al_threshold`` >= 0; default -1
+  = the plain Alg. 3): the multiplier update is applied only once the
+  objective J(v) of Eq. opt stops decreasing by more than al_threshold * |J|
+  between ADMM iterations (the first iteration compares with J(v_start));
+  otherwise the AO/NSO alternation continues with the same lambda.
 """
 import numpy as np
 
@@ -159,6 +164,8 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
     x["v"] = v
     rho_last, _ = kkt.forward_density(P, v)
     g0 = kkt.kkt_norm(P, v)
+    J_prev = kkt.objective(P, v)
+    updates = 0
     hist = []
     fscale = None
     vstar = None
@@ -171,14 +178,19 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
         fres, cycles = nso(P, x, z, fscale, eps_stfas, max_vcycles, lm)
         R = kkt.kkt_norm(P, x["v"]) / g0
         dr = float(np.max(np.abs(rho_last - rhos)))
+        J = kkt.objective(P, x["v"])
+        apply = P.al_threshold < 0 or (J_prev - J) <= P.al_threshold * abs(J_prev)
         hist.append(dict(it=it, kkt_rel=R, f_inf=fres, vcycles=cycles, drho=dr,
-                         objective=kkt.objective(P, x["v"]), rejected=lm["rejected"],
-                         lm_shift=lm["gamma"]))
+                         objective=J, rejected=lm["rejected"], lm_shift=lm["gamma"],
+                         lambda_updates=updates + (1 if apply else 0)))
+        J_prev = J
         if callback:
             callback(hist[-1])
         if R <= tol or dr < eps_admm:
             break
         rho_last = rhos
-        lam[1:N] += P.K * P.beta * (x["v"][1:N] - vstar[1:N])
+        if apply:
+            lam[1:N] += P.K * P.beta * (x["v"][1:N] - vstar[1:N])
+            updates += 1
     P.lm_shift = lm["gamma0"]
     return x, vstar, lam, hist

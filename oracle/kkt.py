@@ -37,6 +37,7 @@ class Problem:
     omega: float = 0.8               # SCGS under-relaxation
     cgc_guard: bool = True           # keep a coarse correction only if it lowers ||res - f||_2
     lm_adapt: bool = True            # Sec. 5 LM safeguard of the NSO loop (adaptive lm_shift)
+    al_threshold: float = -1.0       # Sec. 5 AL fallback: lambda update only when J stalls (<0: off)
     self_advection: bool = True      # False drops Adv (linear saddle problem; pins only)
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
 

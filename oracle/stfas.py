@@ -6,7 +6,7 @@ level, coarse right-hand side res^{2h} = f^{2h}(R x^h) + R(res^h - f^h(x^h)).
 
 Readings:
 * levels halve nx, ny while both are even and the halves are >= coarsest_n.
-* R (Sec. 4.3, "simple trilinear interpolation"): a coarse cell is the mean of
+* R (Sec. 4.3 names trilinear interpolation): a coarse cell is the mean of
   its 4 children; a coarse face the mean of the 2 fine faces lying on it.
 * P: bilinear interpolation at the fine point -- cell fields (3/4, 1/4) per
   axis; face fields linear along the face normal (weights 1 or 1/2, 1/2) and

@@ -294,6 +294,26 @@ def test_ao_blend_never_raises_the_objective_and_reduces_to_plain_steps():
         assert any(t > 0 for t in traces) == want_halving, traces
 
 
+def test_al_fallback_holds_lambda_while_the_objective_falls():
+    """Sec. 5's augmented-Lagrangian fallback: the multiplier moves only at the
+    ADMM iterations where the objective fell by at most al_threshold * |J|; a
+    threshold no decrease can exceed gives back the plain Alg. 3 exactly."""
+    P = _problem(8, 4, sigma=0.15, levels=2, al_threshold=0.15)
+    x, vs, lam, hist = admm.solve(P, tol=1e-12, max_admm=8, eps_admm=0.0)
+    v0 = np.zeros((P.N + 1, P.grid.F))
+    J = [kkt.objective(P, v0)] + [h["objective"] for h in hist]
+    expected = 0
+    for k, h in enumerate(hist):
+        if J[k] - J[k + 1] <= 0.15 * abs(J[k]):
+            expected += 1
+        assert h["lambda_updates"] == expected
+    assert 0 < expected < len(hist)                      # both branches taken
+    plain = admm.solve(_problem(8, 4, sigma=0.15, levels=2), tol=1e-12, max_admm=4, eps_admm=0.0)[3]
+    always = admm.solve(_problem(8, 4, sigma=0.15, levels=2, al_threshold=1e30), tol=1e-12, max_admm=4,
+                        eps_admm=0.0)[3]
+    assert [h["objective"] for h in always] == [h["objective"] for h in plain]
+
+
 @pytest.mark.slow
 def test_admm_reaches_the_full_resimulation_objective_on_a_tiny_problem():
     """North-star check: STFAS + ADMM and a full-resimulation quasi-Newton solve
