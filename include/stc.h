@@ -87,6 +87,10 @@ typedef struct {
                            quadrupled (at most 4096x its default; a cycle undone there ends
                            the NSO solve); each NSO solve starts by halving it back toward
                            its default */
+  double al_threshold;  /* Sec. 5 augmented-Lagrangian fallback in stc_solve: the multiplier
+                           update is applied only when the objective of Eq. opt fell by at
+                           most al_threshold * |J| since the previous ADMM iteration; < 0
+                           (default) applies it every iteration (the plain Alg. 3) */
 } stc_params;
 
 typedef struct {
@@ -104,6 +108,9 @@ typedef struct {
                                  test max_i ||rho_i - rho_i^last||_inf < max|rho_0|/100
                                  held, whatever eps_admm is (0: never)          */
   double seconds_to_density_stop; /* wall time at that iteration (<0: never)    */
+  double objective;     /* J(v) of Eq. opt at exit (misfit + r/2 ||u||^2)        */
+  int lambda_updates;   /* multiplier updates applied (fewer than admm_iters under
+                           the AL fallback)                                       */
 } stc_report;
 
 /* Field identifiers for stc_get_field / stc_set_field (level 0 = finest grid). */

@@ -325,7 +325,8 @@ void enqueue_top_vcycle(stc_problem* P, cudaStream_t st) {
 // with nonfinite_rejects (an NSO V-cycle under the LM safeguard) a non-finite
 // norm, is not an error: the flag is cleared and +inf returned.
 double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool nonfinite_rejects = false) {
-  ck(cudaMemcpyAsync(P->hscal + slot, P->dscal + slot, sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
+  // all scalar slots 0..7 come back together (the others stay readable in hscal)
+  ck(cudaMemcpyAsync(P->hscal, P->dscal, 8 * sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
   ck(cudaMemcpyAsync(P->herr, P->derr, sizeof(int), cudaMemcpyDeviceToHost, P->st), "d2h");
   ck(cudaStreamSynchronize(P->st), "sync");
   const int rejectable = (kmax_rejects ? DEV_TAYLOR_KMAX : 0) | (nonfinite_rejects ? DEV_NONFINITE : 0);
@@ -578,6 +579,18 @@ void kkt(stc_problem* P, cudaStream_t st) {
     launch_kkt_force_rhs<T>(g, (const T*)L0.x.v, (T*)P->uk, st);
   });
   project(P, P->uk, g.N, st);
+  // objective of Eq. opt at v: misfit of rho(v) (dscal[5]) and ||u(v)||^2 (dscal[6])
+  ck(cudaMemsetAsync(P->dscal + 5, 0, 2 * sizeof(double), st), "memset");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    for (size_t k = 0; k < P->key_steps.size(); ++k) {
+      const int s = P->key_steps[k];
+      launch_misfit_dot<T>(g, (const T*)P->rho_k + (size_t)s * g.C, P->star + k * g.C, P->mterm + (size_t)s * g.C,
+                           P->dscal + 5, st);
+    }
+    launch_sumsq<T>((const T*)P->uk, (size_t)g.N * g.F, P->dscal + 6, st);
+  });
+  count(P, (long long)P->key_steps.size() + 1);
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     launch_kkt_grad_rhs<T>(g, (const T*)L0.x.v, (const T*)P->uk, (const T*)P->dens, P->prm.r, (T*)P->gk, st);
@@ -599,19 +612,23 @@ __global__ void lambda_update_kernel(size_t n, size_t skip, T* lam, const T* __r
     if (e >= skip) lam[e] += T(kb) * (v[e] - vs[e]);
 }
 
-void admm_update(stc_problem* P, cudaStream_t st) {
+// Alg. 3's density test (max |rho - rho^last| into dscal[2], rho^last <- rho)
+// and, unless the AL fallback holds it back, the multiplier update.
+void admm_update(stc_problem* P, cudaStream_t st, bool update_lambda = true) {
   Level& L0 = P->lv[0];
   const Geom& g = L0.g;
   ck(cudaMemsetAsync(P->dscal + 2, 0, sizeof(double), st), "memset");
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     launch_absdiff_max_copy<T>((const T*)P->rho, (T*)P->rho_last, (size_t)(g.N + 1) * g.C, P->dscal + 2, st);
-    const size_t n = (size_t)g.N * g.F;
-    unsigned nb = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
-    lambda_update_kernel<T><<<nb, 256, 0, st>>>(n, (size_t)g.F, (T*)P->lam, (const T*)L0.x.v, (const T*)P->vstar,
-                                                 P->prm.K * P->prm.beta);
+    if (update_lambda) {
+      const size_t n = (size_t)g.N * g.F;
+      unsigned nb = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+      lambda_update_kernel<T><<<nb, 256, 0, st>>>(n, (size_t)g.F, (T*)P->lam, (const T*)L0.x.v,
+                                                   (const T*)P->vstar, P->prm.K * P->prm.beta);
+    }
   });
-  count(P, 2);
+  count(P, update_lambda ? 2 : 1);
   check_launch("admm update");
 }
 
@@ -753,7 +770,8 @@ bool params_valid(const stc_params& prm) {
       prm.coarse_sweeps < 0 || prm.coarsest_n < 2 || !(prm.taylor_tol > 0) || prm.taylor_kmax < 1 ||
       prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
-      prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1);
+      prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
+      prm.al_threshold != prm.al_threshold);
 }
 
 // Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
@@ -841,6 +859,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->ao_halvings = 8;
   p->cgc_guard = 1;
   p->lm_adapt = 1;
+  p->al_threshold = -1.0;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -1057,6 +1076,7 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
     // rho^last = uncontrolled densities; KKT denominator at the start
     kkt(p, p->st);
     const double g0 = std::sqrt(read_scalar(p, 1));
+    double J_prev = p->hscal[5] + 0.5 * prm.r * p->hscal[6];   // objective at v_start
     ck(cudaMemcpyAsync(p->rho_last, p->rho_k, (size_t)(g.N + 1) * g.C * p->ts, cudaMemcpyDeviceToDevice, p->st),
        "copy");
     p->fscale = -1.0;
@@ -1077,8 +1097,15 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       }
       kkt(p, p->st);
       const double gn = std::sqrt(read_scalar(p, 1));
-      admm_update(p, p->st);   // drho test + lambda update (lambda unused if we stop)
+      const double J = p->hscal[5] + 0.5 * prm.r * p->hscal[6];
+      // Sec. 5 AL fallback: hold lambda while the objective still falls by more
+      // than al_threshold * |J| per iteration (al_threshold < 0: plain Alg. 3)
+      const bool update = prm.al_threshold < 0 || (J_prev - J) <= prm.al_threshold * std::fabs(J_prev);
+      J_prev = J;
+      admm_update(p, p->st, update);   // drho test + lambda update (lambda unused if we stop)
       const double drho = read_scalar(p, 2);
+      rep.objective = J;
+      if (update) ++rep.lambda_updates;
       rep.admm_iters = it + 1;
       rep.vcycles += cycles;
       rep.rejected_vcycles = p->rejected;

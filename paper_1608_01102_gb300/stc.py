@@ -32,14 +32,15 @@ class StcParams(ctypes.Structure):
                 ("eps_admm", c_double), ("max_vcycles", c_int), ("metric_levels", c_int),
                 ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
                 ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
-                ("cgc_guard", c_int), ("lm_adapt", c_int)]
+                ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double)]
 
 
 class StcReport(ctypes.Structure):
     _fields_ = [("admm_iters", c_int), ("vcycles", c_int), ("kkt_rel", c_double), ("kkt_abs", c_double),
                 ("f_inf", c_double), ("drho", c_double), ("seconds", c_double),
                 ("seconds_to_1e4", c_double), ("rejected_vcycles", c_int), ("lm_shift", c_double),
-                ("density_stop_iter", c_int), ("seconds_to_density_stop", c_double)]
+                ("density_stop_iter", c_int), ("seconds_to_density_stop", c_double), ("objective", c_double),
+                ("lambda_updates", c_int)]
 
 
 class ServerParams(ctypes.Structure):

@@ -357,6 +357,22 @@ def test_admm_iterations(prec):
     assert abs(J_gpu - J_ref) <= (1e-8 if prec == 1 else 1e-4) * J_ref
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_admm_al_fallback(prec):
+    """Sec. 5's AL fallback: the same multiplier-update decisions and the same
+    iterate as the oracle (decisions with a clear margin on this case)."""
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, r=1e-3, sigma=0.12, al_threshold=0.15)
+    rep = G.solve(tol=1e-12, max_admm=5)
+    x, vs, lam, hist = admm.solve(P, tol=1e-12, max_admm=5, eps_admm=P.rho_scale / 100)
+    assert rep["admm_iters"] == len(hist)
+    assert rep["lambda_updates"] == hist[-1]["lambda_updates"]
+    tol = 1e-5 if prec == 1 else 1e-3
+    assert abs(rep["objective"] - hist[-1]["objective"]) <= tol * hist[-1]["objective"]
+    assert rel(G.get("V"), x["v"]) < tol
+    assert rel(G.get("LAMBDA")[1:], lam[1:]) < (tol if prec == 1 else 1e-2) or np.all(lam == 0)
+
+
 # ---------------------------------------------------------------------------
 # Sec. 5 LM safeguard of the NSO loop on a rough target: the first cycle at the
 # default shift blows up on both sides and is undone, the raised shift converges
