@@ -190,10 +190,36 @@ __device__ __forceinline__ T apply_AT_cell(const Geom& g, const Slab& s, const T
   return ax + ay;
 }
 
-// B(P)^T at the owned faces: QUICK(P)_f * (w_hi - w_lo)/h, P from global memory
+// Asynchronous global -> shared copies of single elements (cp.async, sm_80+);
+// the issuing thread waits for its own copies with cp_async_wait_all, a block
+// barrier after that makes them visible to the block.
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (B == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start copying rows [max(r0-2, 0), min(r1+1, ny-1)] of a cell field P (global)
+// into Ps; returns the first staged row.  These are all the rows the QUICK
+// stencils of the owned faces read (accumulate_grad).
 template <class T>
-__device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const T* vx, const T* vy, const T* Gx,
-                                const T* Gy, T* gxs, T* gys) {
+__device__ int stage_term_rows(const Geom& g, const Slab& s, const T* P, T* Ps) {
+  const int rlo = max(s.r0 - 2, 0), rhi = min(s.r1 + 1, g.ny - 1);
+  const int n = s.r1 > s.r0 ? (rhi - rlo + 1) * g.nx : 0;
+  const T* src = P + (size_t)rlo * g.nx;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async_elem<sizeof(T)>(Ps + e, src + e);
+  cp_async_commit();
+  return rlo;
+}
+
+// B(P)^T at the owned faces: QUICK(P)_f * (w_hi - w_lo)/h, P staged in shared
+// memory (rows from rlo, see stage_term_rows)
+template <class T>
+__device__ void accumulate_grad(const Geom& g, const Slab& s, const T* Ps, int rlo, const T* vx, const T* vy,
+                                const T* Gx, const T* Gy, T* gxs, T* gys) {
   const int nx = g.nx;
   const int nown = s.r1 - s.r0;
   RowWalk wx(nx + 1);
@@ -202,7 +228,7 @@ __device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const 
     if (i >= 1 && i <= nx - 1) {
       T c[4];
       quick_coef(vx[e], c);
-      const T* row = P + (size_t)j * nx;
+      const T* row = Ps + (size_t)(j - rlo) * nx;
       gxs[e] += (c[0] * row[i - 1] + c[1] * row[i] + c[2] * row[max(i - 2, 0)] + c[3] * row[min(i + 1, nx - 1)]) *
                 Gx[e];
     }
@@ -214,8 +240,9 @@ __device__ void accumulate_grad(const Geom& g, const Slab& s, const T* P, const 
       T c[4];
       const int le = e + nx;
       quick_coef(vy[le], c);
-      gys[e] += (c[0] * P[(size_t)(jf - 1) * nx + i] + c[1] * P[(size_t)jf * nx + i] +
-                 c[2] * P[(size_t)max(jf - 2, 0) * nx + i] + c[3] * P[(size_t)min(jf + 1, g.ny - 1) * nx + i]) *
+      gys[e] += (c[0] * Ps[(size_t)(jf - 1 - rlo) * nx + i] + c[1] * Ps[(size_t)(jf - rlo) * nx + i] +
+                 c[2] * Ps[(size_t)(max(jf - 2, 0) - rlo) * nx + i] +
+                 c[3] * Ps[(size_t)(min(jf + 1, g.ny - 1) - rlo) * nx + i]) *
                 Gy[le];
     }
   }
@@ -256,7 +283,7 @@ __device__ void halo_push(cg::cluster_group& cl, const Geom& g, const Slab& s, T
 // fp64 cluster-max slots at a 16-byte-aligned byte offset).
 template <class T>
 struct AdvLayout {
-  size_t buf, fx, fy, gx, gy;
+  size_t buf, fx, fy, gx, gy, ps;
   size_t cm_off;
   size_t total;
 };
@@ -270,8 +297,9 @@ __host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) 
   L.fy = (size_t)(rpc + 3) * g.nx;
   L.gx = adjoint ? L.fx : 0;
   L.gy = adjoint ? L.fy : 0;
-  // tb0, tb1, vx, vy, Fx (E), Fy (E), [Gx, Gy, gxs, gys]
-  const size_t n = 2 * L.buf + 2 * L.fx + 2 * L.fy + (adjoint ? 2 * L.fx + 2 * L.fy : 0);
+  L.ps = adjoint ? (size_t)(rpc + 4) * g.nx : 0;   // staged rows of a series term
+  // tb0, tb1, vx, vy, Fx (E), Fy (E), [Gx, Gy, gxs, gys, Ps]
+  const size_t n = 2 * L.buf + 2 * L.fx + 2 * L.fy + (adjoint ? 2 * L.fx + 2 * L.fy + L.ps : 0);
   L.cm_off = (n * sizeof(T) + 15) / 16 * 16;
   L.total = L.cm_off + 2 * kClusterCTAs * sizeof(double);
   return L;
@@ -448,6 +476,7 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
   T* Gy = Gx + L.fx;
   T* gxs = Gy + L.fy;
   T* gys = gxs + L.fx;
+  T* Ps = gys + L.fy;
   const int nx = g.nx;
   const int nown = (s.r1 - s.r0) * nx;
   const int ngx = (s.r1 - s.r0) * (nx + 1);
@@ -514,10 +543,13 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     halo_push(cl, g, s, cur, rank);
     for (int mm = K - 1; mm >= 0; --mm) {
       cl.sync();
+      // the rows of t_m this CTA's stencils read, copied while E and G are formed
+      const int rlo = stage_term_rows(g, s, (mm == 0) ? rs : powers + (size_t)mm * g.C, Ps);
       face_differences(g, s, cur, vx, vy, Ex, Ey, Gx, Gy);
+      cp_async_wait_all();
       __syncthreads();
       // grad += B(t_m)^T w'_m on own faces
-      accumulate_grad(g, s, (mm == 0) ? rs : powers + (size_t)mm * g.C, vx, vy, Gx, Gy, gxs, gys);
+      accumulate_grad(g, s, Ps, rlo, vx, vy, Gx, Gy, gxs, gys);
       // w'_{m-1} = (dt/m)(mu + A^T w'_m); for m = 0 the factor is 1 (T^T mu)
       const T fac = (mm == 0) ? T(1) : dtk[mm];
 #pragma unroll
