@@ -289,8 +289,8 @@ struct AdvLayout {
 };
 
 template <class T>
-__host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) {
-  const int rpc = (g.ny + kClusterCTAs - 1) / kClusterCTAs;
+__host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint, int ncta) {
+  const int rpc = (g.ny + ncta - 1) / ncta;
   AdvLayout<T> L;
   L.buf = (size_t)(rpc + 4) * g.nx;
   L.fx = (size_t)rpc * (g.nx + 1);
@@ -301,13 +301,13 @@ __host__ __device__ inline AdvLayout<T> adv_layout(const Geom& g, bool adjoint) 
   // tb0, tb1, vx, vy, Fx (E), Fy (E), [Gx, Gy, gxs, gys, Ps]
   const size_t n = 2 * L.buf + 2 * L.fx + 2 * L.fy + (adjoint ? 2 * L.fx + 2 * L.fy + L.ps : 0);
   L.cm_off = (n * sizeof(T) + 15) / 16 * 16;
-  L.total = L.cm_off + 2 * kClusterCTAs * sizeof(double);
+  L.total = L.cm_off + 2 * kMaxClusterCTAs * sizeof(double);
   return L;
 }
 
-__device__ __forceinline__ Slab make_slab(const Geom& g, int rank) {
+__device__ __forceinline__ Slab make_slab(const Geom& g, int rank, int ncta) {
   Slab s;
-  s.rpc = (g.ny + kClusterCTAs - 1) / kClusterCTAs;
+  s.rpc = (g.ny + ncta - 1) / ncta;
   s.r0 = rank * s.rpc;
   if (s.r0 > g.ny) s.r0 = g.ny;
   s.r1 = s.r0 + s.rpc;
@@ -348,9 +348,10 @@ __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double thresh, int kmax, int* err) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const Slab s = make_slab(g, rank);
+  const int ncta = (int)cl.num_blocks();
+  const Slab s = make_slab(g, rank, ncta);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const AdvLayout<T> L = adv_layout<T>(g, false);
+  const AdvLayout<T> L = adv_layout<T>(g, false, ncta);
   T* tb0 = reinterpret_cast<T*>(smem_raw);
   T* tb1 = tb0 + L.buf;
   T* vx = tb1 + L.buf;
@@ -410,12 +411,12 @@ taylor_forward_kernel(Geom g, const T* __restrict__ vel, T* rho, int* Ks, double
       }
       const T bm = block_max(lmax, red);   // also orders the nxt writes before the push
       halo_push(cl, g, s, nxt, rank);
-      if (threadIdx.x < kClusterCTAs)
-        *cl.map_shared_rank(cmax + (k & 1) * kClusterCTAs + rank, (int)threadIdx.x) = bm;
+      if ((int)threadIdx.x < ncta)
+        *cl.map_shared_rank(cmax + (k & 1) * kMaxClusterCTAs + rank, (int)threadIdx.x) = bm;
       cl.sync();
       T gm = T(0);
 #pragma unroll
-      for (int r = 0; r < kClusterCTAs; ++r) gm = fmax(gm, cmax[(k & 1) * kClusterCTAs + r]);
+      for (int r = 0; r < ncta; ++r) gm = fmax(gm, cmax[(k & 1) * kMaxClusterCTAs + r]);
       T* tmp = cur;
       cur = nxt;
       nxt = tmp;
@@ -463,9 +464,10 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
   fill_dt_over_k(g, kmax, dtk);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const Slab s = make_slab(g, rank);
+  const int ncta = (int)cl.num_blocks();
+  const Slab s = make_slab(g, rank, ncta);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const AdvLayout<T> L = adv_layout<T>(g, true);
+  const AdvLayout<T> L = adv_layout<T>(g, true, ncta);
   T* tb0 = reinterpret_cast<T*>(smem_raw);
   T* tb1 = tb0 + L.buf;
   T* vx = tb1 + L.buf;
@@ -714,14 +716,17 @@ void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, 
 // host launchers
 // ---------------------------------------------------------------------------
 bool advect_supported(const Geom& g) {
-  const int rpc = (g.ny + kClusterCTAs - 1) / kClusterCTAs;
+  const int ncta = advect_cluster_ctas();
+  const int rpc = (g.ny + ncta - 1) / ncta;
   return g.nx >= 2 && g.ny >= 2 && rpc * g.nx <= kAdvThreads * kAdvMaxCellsPerThread;
 }
 size_t advect_smem_forward(const Geom& g, size_t tsize) {
-  return tsize == 4 ? adv_layout<float>(g, false).total : adv_layout<double>(g, false).total;
+  const int n = advect_cluster_ctas();
+  return tsize == 4 ? adv_layout<float>(g, false, n).total : adv_layout<double>(g, false, n).total;
 }
 size_t advect_smem_adjoint(const Geom& g, size_t tsize) {
-  return tsize == 4 ? adv_layout<float>(g, true).total : adv_layout<double>(g, true).total;
+  const int n = advect_cluster_ctas();
+  return tsize == 4 ? adv_layout<float>(g, true, n).total : adv_layout<double>(g, true, n).total;
 }
 
 // The dynamic shared-memory cap of a kernel is raised once, to the opt-in
@@ -741,22 +746,63 @@ static cudaError_t allow_max_smem(const void* kernel) {
   // the cap covers dynamic memory only: opt-in total minus the static arrays
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (err == cudaSuccess) err = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (err == cudaSuccess) done.push_back(kernel);
   return err;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kAdvThreads, 1)
+taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
+                      const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
+                      T* out, T* powers, int kmax);
+
+// A 16-CTA cluster halves each CTA's rows (the per-term latency of the sweeps
+// scales with them); it needs 16 SMs of one GPC free at once.  The device is
+// asked once whether such a cluster of the backward sweep (the larger shared
+// memory) for a 128^2 fp32 grid can be resident; otherwise 8 CTAs are used.
+int advect_cluster_ctas() {
+  static std::once_flag once;
+  static int n = 8;
+  std::call_once(once, [] {
+    const void* k = (const void*)taylor_adjoint_kernel<float>;
+    if (allow_max_smem(k) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    Geom g{};
+    g.nx = g.ny = 128;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kMaxClusterCTAs, 1, 1);
+    cfg.blockDim = dim3(kAdvThreads, 1, 1);
+    cfg.dynamicSmemBytes = adv_layout<float>(g, true, kMaxClusterCTAs).total;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kMaxClusterCTAs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) == cudaSuccess && clusters >= 1) n = kMaxClusterCTAs;
+    cudaGetLastError();
+  });
+  return n;
 }
 
 template <class K>
 static cudaError_t cluster_launch(K kernel, size_t smem, cudaStream_t st, void** args) {
   cudaError_t e = allow_max_smem((const void*)kernel);
   if (e != cudaSuccess) return e;
+  const int ncta = advect_cluster_ctas();
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterCTAs, 1, 1);
+  cfg.gridDim = dim3(ncta, 1, 1);
   cfg.blockDim = dim3(kAdvThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kClusterCTAs;
+  attr[0].val.clusterDim.x = ncta;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -770,7 +816,7 @@ cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, d
   if (kmax < 1 || kmax > kTaylorKmaxLimit) return cudaErrorInvalidValue;   // size of the dt/k table
   Geom gg = g;
   void* args[] = {&gg, (void*)&vel, (void*)&rho, (void*)&K, (void*)&thresh, (void*)&kmax, (void*)&err};
-  return cluster_launch(taylor_forward_kernel<T>, adv_layout<T>(g, false).total, st, args);
+  return cluster_launch(taylor_forward_kernel<T>, adv_layout<T>(g, false, advect_cluster_ctas()).total, st, args);
 }
 
 template <class T>
@@ -781,7 +827,7 @@ cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, con
   Geom gg = g;
   void* args[] = {&gg,          (void*)&vel,  (void*)&rho,   (void*)&K,   (void*)&mterm,  (void*)&mu,
                   (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax};
-  return cluster_launch(taylor_adjoint_kernel<T>, adv_layout<T>(g, true).total, st, args);
+  return cluster_launch(taylor_adjoint_kernel<T>, adv_layout<T>(g, true, advect_cluster_ctas()).total, st, args);
 }
 
 // ---------------------------------------------------------------------------

@@ -45,7 +45,10 @@ template <class Ts, class Td>
 void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st);
 
 // --- advection (advect_kernels.cu) ------------------------------------------
-constexpr int kClusterCTAs = 8;
+constexpr int kMaxClusterCTAs = 16;   // the sweeps run on one cluster of 16 (non-portable) or 8 CTAs
+// cluster size of the advection sweeps on this device: 16 when a 16-CTA cluster
+// of the sweep kernels can be scheduled, else 8 (decided once per process)
+int advect_cluster_ctas();
 constexpr int kAdvThreads = 512;
 constexpr int kAdvMaxCellsPerThread = 8;
 
