@@ -47,25 +47,6 @@ __device__ __forceinline__ const T* buf_row(const Geom& g, const Slab& s, const 
   return b + (jj - s.r0 + 2) * g.nx;
 }
 
-// Row/column of e = threadIdx.x, threadIdx.x + blockDim.x, ... in a row-major
-// range of rows of length P, advanced without a division per element.
-struct RowWalk {
-  int q, r, dq, dr, P;
-  __device__ __forceinline__ RowWalk(int P_) : P(P_) {
-    q = (int)threadIdx.x / P;
-    r = (int)threadIdx.x - q * P;
-    dq = (int)blockDim.x / P;
-    dr = (int)blockDim.x - dq * P;
-  }
-  __device__ __forceinline__ void next() {
-    q += dq;
-    r += dr;
-    if (r >= P) {
-      r -= P;
-      ++q;
-    }
-  }
-};
 
 // Face arrays of a slab: x-faces of the owned rows [r0, r1) (all columns),
 // y-faces of rows [r0 - 1, r0 + rpc + 1] (row index offset by 1).

@@ -44,20 +44,27 @@ __host__ __device__ inline PLevels poisson_levels(int nx, int ny) {
 
 __device__ __forceinline__ int ci(int n, int j, int i) { return j * n + i; }
 
-// red-black Gauss-Seidel half sweep on level (nx, ny, h2 = h^2): phi_c = (sum phi_nb - h2 b_c)/n_nb
+// red-black Gauss-Seidel half sweep on level (nx, ny, h2 = h^2): phi_c = (sum phi_nb - h2 b_c)/n_nb,
+// visiting only the cells of one colour (the cell of slot r in row j is
+// i = 2r + ((j + colour) & 1)); dividing by 2 or 4 neighbours is a multiply
+// by 1/2 or 1/4, which is exact
 template <class T>
 __device__ void rb_half(T* phi, const T* b, int nx, int ny, T h2, int colour) {
-  const int n = nx * ny;
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int j = e / nx, i = e - (e / nx) * nx;
-    if (((i + j) & 1) != colour) continue;
+  const int half = (nx + 1) / 2;
+  const int n = half * ny;
+  RowWalk w(half);
+  for (int t = threadIdx.x; t < n; t += blockDim.x, w.next()) {
+    const int j = w.q, i = 2 * w.r + ((j + colour) & 1);
+    if (i >= nx) continue;
+    const int e = j * nx + i;
     T s = T(0);
     int k = 0;
     if (i > 0) { s += phi[e - 1]; ++k; }
     if (i < nx - 1) { s += phi[e + 1]; ++k; }
     if (j > 0) { s += phi[e - nx]; ++k; }
     if (j < ny - 1) { s += phi[e + nx]; ++k; }
-    phi[e] = (s - h2 * b[e]) / T(k);
+    const T v = s - h2 * b[e];
+    phi[e] = k == 4 ? v * T(0.25) : (k == 2 ? v * T(0.5) : v / T(k));
   }
 }
 
@@ -99,10 +106,12 @@ project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
   T* phi0 = sm + L.off[0];
   T* b0 = phi0 + (size_t)nx * ny;
   // b = D v, phi = 0
-  for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) {
-    const int j = e / nx, i = e - (e / nx) * nx;
-    b0[e] = divergence(g, v, j, i);
-    phi0[e] = T(0);
+  {
+    RowWalk w(nx);
+    for (int e = threadIdx.x; e < nx * ny; e += blockDim.x, w.next()) {
+      b0[e] = divergence(g, v, w.q, w.r);
+      phi0[e] = T(0);
+    }
   }
   __syncthreads();
   const int nl = L.n;
@@ -126,8 +135,9 @@ project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
       // restricted residual: b_{l+1} = mean over the 4 children of (b - L phi)
       const int cx = L.nx[l + 1], cy = L.ny[l + 1];
       T* bc = sm + L.off[l + 1] + (size_t)cx * cy;
-      for (int e = threadIdx.x; e < cx * cy; e += blockDim.x) {
-        const int J = e / cx, I = e - (e / cx) * cx;
+      RowWalk wc(cx);
+      for (int e = threadIdx.x; e < cx * cy; e += blockDim.x, wc.next()) {
+        const int J = wc.q, I = wc.r;
         T acc = T(0);
 #pragma unroll
         for (int dj = 0; dj < 2; ++dj)
@@ -141,7 +151,8 @@ project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
       __syncthreads();
     }
     // coarsest (<= 64 cells): red-black Gauss-Seidel in fp64 on the compatible
-    // (mean-free) right-hand side, one thread per cell
+    // (mean-free) right-hand side, by warp 0 alone (two cells per lane, warp
+    // synchronisation between the half-sweeps)
     {
       const int l = nl - 1;
       const int lx = L.nx[l], ly = L.ny[l];
@@ -149,37 +160,50 @@ project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
       const double h2 = (g.h * (double)(1 << l)) * (g.h * (double)(1 << l));
       T* phi = sm + L.off[l];
       T* b = phi + (size_t)n;
-      const int e = threadIdx.x;
-      if (e < n) {
-        cb[e] = (double)b[e];
-        cp[e] = 0.0;
-      }
-      __syncthreads();
-      if (e == 0) {
-        double m = 0.0;
-        for (int k = 0; k < n; ++k) m += cb[k];
-        cmean = m / n;
-      }
-      __syncthreads();
-      if (e < n) cb[e] -= cmean;
-      __syncthreads();
-      const int j = e / lx, i = e - (e / lx) * lx;
-      // neighbour count of this cell, and its reciprocal formed once
-      const int kn = (i > 0) + (i < lx - 1) + (j > 0) + (j < ly - 1);
-      const double ikn = kn > 0 ? 1.0 / kn : 0.0;
-      for (int it = 0; it < 30; ++it)
-        for (int colour = 0; colour < 2; ++colour) {
-          if (e < n && ((i + j) & 1) == colour) {
-            double sacc = 0.0;
-            if (i > 0) sacc += cp[e - 1];
-            if (i < lx - 1) sacc += cp[e + 1];
-            if (j > 0) sacc += cp[e - lx];
-            if (j < ly - 1) sacc += cp[e + lx];
-            cp[e] = (sacc - h2 * cb[e]) * ikn;
-          }
-          __syncthreads();
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int e = lane; e < n; e += 32) {
+          cb[e] = (double)b[e];
+          cp[e] = 0.0;
         }
-      if (e < n) phi[e] = T(cp[e]);
+        __syncwarp();
+        if (lane == 0) {
+          double m = 0.0;
+          for (int k = 0; k < n; ++k) m += cb[k];
+          cmean = m / n;
+        }
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) cb[e] -= cmean;
+        __syncwarp();
+        // a lane's (up to) two cells, their neighbour counts and reciprocals
+        int ce[2], cc[2];
+        double ikn[2];
+        for (int q = 0; q < 2; ++q) {
+          const int e = lane + 32 * q;
+          ce[q] = e;
+          const int j = e / lx, i = e - (e / lx) * lx;
+          cc[q] = (i + j) & 1;
+          const int kn = (i > 0) + (i < lx - 1) + (j > 0) + (j < ly - 1);
+          ikn[q] = kn > 0 ? 1.0 / kn : 0.0;
+        }
+        for (int it = 0; it < 30; ++it)
+          for (int colour = 0; colour < 2; ++colour) {
+            for (int q = 0; q < 2; ++q) {
+              const int e = ce[q];
+              if (e < n && cc[q] == colour) {
+                const int j = e / lx, i = e - (e / lx) * lx;
+                double sacc = 0.0;
+                if (i > 0) sacc += cp[e - 1];
+                if (i < lx - 1) sacc += cp[e + 1];
+                if (j > 0) sacc += cp[e - lx];
+                if (j < ly - 1) sacc += cp[e + lx];
+                cp[e] = (sacc - h2 * cb[e]) * ikn[q];
+              }
+            }
+            __syncwarp();
+          }
+        for (int e = lane; e < n; e += 32) phi[e] = T(cp[e]);
+      }
       __syncthreads();
     }
     // ascend: phi_l += P phi_{l+1}, post-smooth
@@ -190,8 +214,9 @@ project_kernel(Geom g, T* fields, int vcycles, T* scratch, size_t per_field) {
       T* phi = sm + L.off[l];
       T* b = phi + (size_t)lx * ly;
       const T* pc = sm + L.off[l + 1];
-      for (int e = threadIdx.x; e < lx * ly; e += blockDim.x) {
-        const int j = e / lx, i = e - (e / lx) * lx;
+      RowWalk wf(lx);
+      for (int e = threadIdx.x; e < lx * ly; e += blockDim.x, wf.next()) {
+        const int j = wf.q, i = wf.r;
         const int ja = j >> 1, ia = i >> 1;
         int jb = (j & 1) ? ja + 1 : ja - 1;
         int ib = (i & 1) ? ia + 1 : ia - 1;

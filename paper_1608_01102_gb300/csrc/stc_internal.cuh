@@ -74,6 +74,26 @@ __host__ __device__ inline int cidx(const Geom& g, int j, int i) { return j * g.
 template <class T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Row/column of e = threadIdx.x, threadIdx.x + blockDim.x, ... in a row-major
+// range of rows of length P, advanced without a division per element.
+struct RowWalk {
+  int q, r, dq, dr, P;
+  __device__ __forceinline__ RowWalk(int P_) : P(P_) {
+    q = (int)threadIdx.x / P;
+    r = (int)threadIdx.x - q * P;
+    dq = (int)blockDim.x / P;
+    dr = (int)blockDim.x - dq * P;
+  }
+  __device__ __forceinline__ void next() {
+    q += dq;
+    r += dr;
+    if (r >= P) {
+      r -= P;
+      ++q;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Self-advection Adv[v] = (curl v) x v  (Eq. NSA) and its Jacobian transpose.
 // omega at node (j,i) = (vy(j,i)-vy(j,i-1))/h - (vx(j,i)-vx(j-1,i))/h, zero on
