@@ -38,6 +38,7 @@ class Problem:
     cgc_guard: bool = True           # keep a coarse correction only if it lowers ||res - f||_2
     lm_adapt: bool = True            # Sec. 5 LM safeguard of the NSO loop (adaptive lm_shift)
     al_threshold: float = -1.0       # Sec. 5 AL fallback: lambda update only when J stalls (<0: off)
+    time_coarsen: bool = False       # STFAS coarse levels halve N too (the paper: space only)
     self_advection: bool = True      # False drops Adv (linear saddle problem; pins only)
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
 

@@ -25,7 +25,17 @@ Readings:
   coarse correction undid the smoothing.  In the regime where the cycle
   contracts, the correction cuts the residual several-fold and is always kept,
   so the guard does not change the cycle there.
+* time coarsening (``P.time_coarsen``, off by default: the paper coarsens in
+  space only): while a level's N is even, the next level also halves N and
+  doubles dt.  In time, point fields (v, pbar and their rows; the targets z)
+  restrict by injection at the two ends and full weighting (1/4, 1/2, 1/4)
+  inside, and prolong linearly; interval fields (u, p and their rows)
+  restrict by the mean of the two sub-intervals and prolong piecewise
+  constant.  Space and time transfers are applied one after the other.  The
+  fine-level fixed point f = 0 does not depend on any of this.
 """
+import dataclasses
+
 import numpy as np
 
 from . import kkt, mac, scgs
@@ -112,36 +122,109 @@ def restrict_faces_batch(fine, z):
     return np.array([restrict_faces(fine, a) for a in z])
 
 
+def levels(P):
+    """[(grid_l, P_l)] of the hierarchy: the grids of hierarchy(P); P_l = P with
+    the level's N and dt (halved / doubled at every level while N is even when
+    P.time_coarsen is set; the smoother's shift stays the finest level's)."""
+    out = []
+    Pl = P
+    for l, g in enumerate(hierarchy(P)):
+        if l > 0 and P.time_coarsen and Pl.N % 2 == 0:
+            Pl = dataclasses.replace(Pl, N=Pl.N // 2, dt=2.0 * Pl.dt, lm_shift=P.lm_shift)
+        out.append((g, Pl))
+    return out
+
+
+def restrict_time_points(a):
+    """(N+1) point slabs -> (N/2+1): injection at 0 and N, full weighting inside.
+    Also used for the N target slabs z_0..z_{N-1} (-> N/2), which have no end
+    point to inject."""
+    n = a.shape[0]
+    if n % 2 == 1:                      # points 0..N
+        nc = (n - 1) // 2 + 1
+        out = np.empty((nc,) + a.shape[1:])
+        out[0] = a[0]
+        out[nc - 1] = a[n - 1]
+    else:                               # targets 0..N-1
+        nc = n // 2
+        out = np.empty((nc,) + a.shape[1:])
+        out[0] = a[0]
+    for i in range(1, nc if n % 2 == 0 else nc - 1):
+        out[i] = 0.25 * a[2 * i - 1] + 0.5 * a[2 * i] + 0.25 * a[2 * i + 1]
+    return out
+
+
+def restrict_time_intervals(a):
+    """N interval slabs -> N/2: the mean of the two sub-intervals."""
+    return 0.5 * (a[0::2] + a[1::2])
+
+
+def prolong_time_points(ac):
+    """(N/2+1) point slabs -> (N+1): linear interpolation."""
+    nc = ac.shape[0]
+    out = np.empty((2 * (nc - 1) + 1,) + ac.shape[1:])
+    out[0::2] = ac
+    out[1::2] = 0.5 * (ac[:-1] + ac[1:])
+    return out
+
+
+def prolong_time_intervals(ac):
+    """N/2 interval slabs -> N: piecewise constant."""
+    return np.repeat(ac, 2, axis=0)
+
+
+def restrict_state_st(fine, x, in_time):
+    xc = restrict_state(fine, x)
+    if in_time:
+        xc = dict(v=restrict_time_points(xc["v"]), pbar=restrict_time_points(xc["pbar"]),
+                  u=restrict_time_intervals(xc["u"]), p=restrict_time_intervals(xc["p"]))
+    return xc
+
+
+def prolong_state_st(fine, coarse, xc, in_time):
+    if in_time:
+        xc = dict(v=prolong_time_points(xc["v"]), pbar=prolong_time_points(xc["pbar"]),
+                  u=prolong_time_intervals(xc["u"]), p=prolong_time_intervals(xc["p"]))
+    return prolong_state(fine, coarse, xc)
+
+
+def restrict_targets(fine, z, in_time):
+    zc = restrict_faces_batch(fine, z)
+    return restrict_time_points(zc) if in_time else zc
+
+
 def vcycle(P, grids, level, x, z, res):
-    """One FAS V(pre, post) cycle on level ``level`` (in place on x)."""
-    g = grids[level]
+    """One FAS V(pre, post) cycle on level ``level`` (in place on x).  ``grids``
+    is hierarchy(P) (space only) or levels(P) (grid and per-level problem)."""
+    g, Pl = grids[level] if isinstance(grids[level], tuple) else (grids[level], P)
     if level == len(grids) - 1:
         for _ in range(P.coarse_sweeps):
-            scgs.sweep(P, g, x, z, res)
+            scgs.sweep(Pl, g, x, z, res)
         return
     for _ in range(P.pre):
-        scgs.sweep(P, g, x, z, res)
-    f = kkt.nso_residual(P, g, x, z)
+        scgs.sweep(Pl, g, x, z, res)
+    f = kkt.nso_residual(Pl, g, x, z)
     rf = {k: res[k] - f[k] for k in f}
-    gc = grids[level + 1]
-    xc = restrict_state(g, x)
+    gc, Pc = grids[level + 1] if isinstance(grids[level + 1], tuple) else (grids[level + 1], P)
+    in_time = Pc.N != Pl.N
+    xc = restrict_state_st(g, x, in_time)
     xc_old = kkt.copy_state(xc)
-    zc = restrict_faces_batch(g, z)
-    fc = kkt.nso_residual(P, gc, xc, zc)
-    rc = restrict_state(g, rf)
+    zc = restrict_targets(g, z, in_time)
+    fc = kkt.nso_residual(Pc, gc, xc, zc)
+    rc = restrict_state_st(g, rf, in_time)
     resc = {k: fc[k] + rc[k] for k in fc}
     # rows dropped by the fixed v_0 stay zero
     resc["v"][0] = 0.0
     resc["pbar"][0] = 0.0
     vcycle(P, grids, level + 1, xc, zc, resc)
-    corr = prolong_state(g, gc, kkt.state_sub(xc, xc_old))
+    corr = prolong_state_st(g, gc, kkt.state_sub(xc, xc_old), in_time)
     corr["v"][0] = 0.0      # v_0 is data, not an unknown
     corr["pbar"][0] = 0.0
     trial = {k: x[k] + corr[k] for k in x}
     if P.cgc_guard:
         # keep the coarse-grid correction only if it does not raise the
         # level's residual 2-norm; otherwise continue from the smoothed x
-        ft = kkt.nso_residual(P, g, trial, z)
+        ft = kkt.nso_residual(Pl, g, trial, z)
         before = sum(float(np.sum(a * a)) for a in rf.values())
         after = sum(float(np.sum((res[k] - ft[k]) ** 2)) for k in ft)
         if after <= before:
@@ -151,7 +234,7 @@ def vcycle(P, grids, level, x, z, res):
         for k in x:
             x[k] = trial[k]
     for _ in range(P.post):
-        scgs.sweep(P, g, x, z, res)
+        scgs.sweep(Pl, g, x, z, res)
 
 
 def normalise_pressures(x):
@@ -162,7 +245,7 @@ def normalise_pressures(x):
 
 def stfas_cycle(P, x, z):
     """One top-level V-cycle for f(x) = 0 followed by pressure normalisation."""
-    grids = hierarchy(P)
+    grids = levels(P)
     res = {k: np.zeros_like(a) for k, a in x.items()}
     vcycle(P, grids, 0, x, z, res)
     normalise_pressures(x)

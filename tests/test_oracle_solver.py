@@ -232,6 +232,49 @@ def test_vcycles_converge_to_direct_solution_of_linear_saddle_problem(n, N):
         np.testing.assert_allclose(x[k], ref[k], atol=1e-7 * scale)
 
 
+def test_time_transfers_are_exact_on_affine_and_pairwise_constant_fields():
+    """Time coarsening (off by default): linear interpolation reproduces a field
+    affine in time after restriction; intervals restrict by pair means and
+    prolong piecewise constant."""
+    t = np.arange(9.0)[:, None] * np.array([[0.5, -1.0, 2.0]]) + np.array([[1.0, 0.0, -3.0]])
+    rc = stfas.restrict_time_points(t)
+    np.testing.assert_allclose(rc, t[0::2], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(stfas.prolong_time_points(rc), t, rtol=0, atol=1e-14)
+    z = t[:8]                                  # targets 0..N-1 restrict to 0..N/2-1
+    np.testing.assert_allclose(stfas.restrict_time_points(z), z[0::2], rtol=0, atol=1e-14)
+    u = np.repeat(np.arange(4.0)[:, None] * np.ones((1, 3)), 2, axis=0)
+    np.testing.assert_allclose(stfas.prolong_time_intervals(stfas.restrict_time_intervals(u)), u, atol=0)
+    P = _problem(8, 8, time_coarsen=True)
+    Ns = [Pl.N for _, Pl in stfas.levels(P)]
+    dts = [Pl.dt for _, Pl in stfas.levels(P)]
+    assert Ns == [8, 4] and dts == [P.dt, 2 * P.dt]
+
+
+def test_time_coarsened_vcycles_reach_the_same_linear_solution():
+    """The coarse levels change the rate only: with time coarsening the V-cycles
+    converge to the direct solution of the linear saddle problem (more slowly:
+    the SCGS smoother already solves each cell's time line exactly, so halving N
+    on the coarse levels adds little; measured rate ~0.66 against ~0.05 in
+    space only), and a converged state is a fixed point of the cycle."""
+    n, N = 8, 4
+    rng = np.random.default_rng(17)
+    P = _problem(n, N, self_advection=False, time_coarsen=True)
+    assert [Pl.N for _, Pl in stfas.levels(P)] == [4, 2]
+    z = np.array([projection.project(P.grid, w) for w in workloads.random_faces(rng, n, n, N)])
+    ref = _linear_solution(P, z)
+    x = kkt.zero_state(P)
+    hist = [stfas.stfas_cycle(P, x, z) for _ in range(60)]
+    for k in ("v", "u", "pbar", "p"):
+        scale = max(np.max(np.abs(ref[k])), 1e-3 * np.max(np.abs(ref["u"])))
+        np.testing.assert_allclose(x[k], ref[k], atol=1e-7 * scale)
+    assert max(hist[k + 1] / hist[k] for k in range(2, 20)) < 0.8   # contracts every cycle
+    x2 = kkt.copy_state(ref)
+    f = stfas.stfas_cycle(P, x2, z)
+    assert f < 1e-9 * max(1.0, hist[0])
+    for k in x2:
+        np.testing.assert_allclose(x2[k], ref[k], atol=1e-9 * max(1.0, np.max(np.abs(ref[k]))))
+
+
 def test_vcycle_rate_roughly_independent_of_n_and_N():
     """Sec. 4.3 / Fig. Convergence: the rate does not depend on n or N."""
     rng = np.random.default_rng(16)
