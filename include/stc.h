@@ -91,6 +91,10 @@ typedef struct {
                            update is applied only when the objective of Eq. opt fell by at
                            most al_threshold * |J| since the previous ADMM iteration; < 0
                            (default) applies it every iteration (the plain Alg. 3) */
+  int time_coarsen;     /* 0 (default, the paper: STFAS coarsens in space only); 1: every
+                           level whose N is even hands the next one N/2 steps of 2 dt
+                           (point fields: full weighting / linear interpolation in time,
+                           interval fields: pair means / piecewise constant) */
 } stc_params;
 
 typedef struct {
@@ -194,6 +198,9 @@ stc_status stc_get_field(const stc_problem* p, int field, int level, double* out
 stc_status stc_set_field(stc_problem* p, int field, int level, const double* in, size_t len);
 /* Number of levels, and the cells per axis of one level. */
 stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx, int* ny);
+/* Timesteps N_l and timestep dt_l of level `level` (they differ from the
+ * finest level's only with stc_params.time_coarsen).  Either output may be NULL. */
+stc_status stc_level_steps(const stc_problem* p, int level, int* num_steps, double* dt);
 
 /* Forward density sweep (Eq. Conv, Eq. Adv): rho_{i+1} = A[rho_i, w_i] with
  * w = v* (source STC_FIELD_VSTAR) or w = v (STC_FIELD_V); writes STC_FIELD_RHO

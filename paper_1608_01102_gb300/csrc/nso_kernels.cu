@@ -53,6 +53,7 @@ template <class T>
 __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z,
                                    CState<T> res, State<T> out, T sf, T sr, double* sq,
                                    const double* only_if_undone) {
+  pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (t > g.N) return;
@@ -140,6 +141,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
 template <class T>
 __global__ void nso_residual_colour_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res,
                                            State<T> out, int px, int py, const double* only_if_undone) {
+  pdl_wait();
   const int t = blockIdx.y;
   if (t > g.N) return;
   if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
@@ -426,6 +428,7 @@ template <class T, class S>
 __global__ void __launch_bounds__(256)
 scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb,
                    const double* __restrict__ lm_dev) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
   // Levenberg-Marquardt shift of the v blocks: a device scalar when the solve
@@ -795,37 +798,62 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
 // fine faces (faces); P = bilinear interpolation, faces linear along the
 // normal and (3/4, 1/4) across, clamped at walls.
 // ---------------------------------------------------------------------------
+// Time modes of the transfers (levels that also halve N, an opt-in):
+//   0  slab t <-> slab t (space-only hierarchy)
+//   1  point fields (v, pbar, their rows): injection at the first and last
+//      point, full weighting (1/4, 1/2, 1/4) inside; prolongation linear
+//   2  interval fields (u, p, their rows): mean of the two sub-intervals;
+//      prolongation piecewise constant
+//   3  the targets z_0..z_{N-1}: injection at 0, full weighting after
+// The spatial transfer is applied per slab, then the time weights.
 template <class Tf, class Tc>
 __global__ void restrict_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, const Tf* __restrict__ sf,
                                 const Tf* __restrict__ sc_cells, Tc* df, Tc* dc_cells, Tc* df2,
-                                Tc* dc2) {
-  // faces: nt_face timesteps of gc.F entries; cells: nt_cell timesteps of gc.C
+                                Tc* dc2, int tmode) {
+  pdl_wait();
+  // faces: nt_face coarse slabs of gc.F entries; cells: nt_cell coarse slabs of gc.C
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nfaces = (size_t)nt_face * gc.F;
   const size_t ncells = (size_t)nt_cell * gc.C;
+  auto in_time = [&](auto rs, int t, int nt) -> Tc {
+    switch (tmode) {
+      case 0: return rs(t);
+      case 1:
+        if (t == 0 || t == nt - 1) return rs(2 * t);
+        return Tc(0.25) * rs(2 * t - 1) + Tc(0.5) * rs(2 * t) + Tc(0.25) * rs(2 * t + 1);
+      case 2: return Tc(0.5) * (rs(2 * t) + rs(2 * t + 1));
+      default:
+        if (t == 0) return rs(0);
+        return Tc(0.25) * rs(2 * t - 1) + Tc(0.5) * rs(2 * t) + Tc(0.25) * rs(2 * t + 1);
+    }
+  };
   if (e < nfaces) {
     const int t = (int)(e / gc.F);
     const int f = (int)(e - (size_t)t * gc.F);
-    const Tf* s = sf + (size_t)t * gf.F;
-    Tc val;
-    if (f < gc.Fx) {
-      int J = f / (gc.nx + 1), I = f - J * (gc.nx + 1);
-      val = Tc(0.5) * (Tc(s[xf(gf, 2 * J, 2 * I)]) + Tc(s[xf(gf, 2 * J + 1, 2 * I)]));
-    } else {
+    auto rs = [&](int tf) -> Tc {
+      const Tf* s = sf + (size_t)tf * gf.F;
+      if (f < gc.Fx) {
+        int J = f / (gc.nx + 1), I = f - J * (gc.nx + 1);
+        return Tc(0.5) * (Tc(s[xf(gf, 2 * J, 2 * I)]) + Tc(s[xf(gf, 2 * J + 1, 2 * I)]));
+      }
       int q = f - gc.Fx;
       int J = q / gc.nx, I = q - J * gc.nx;
-      val = Tc(0.5) * (Tc(s[yf(gf, 2 * J, 2 * I)]) + Tc(s[yf(gf, 2 * J, 2 * I + 1)]));
-    }
+      return Tc(0.5) * (Tc(s[yf(gf, 2 * J, 2 * I)]) + Tc(s[yf(gf, 2 * J, 2 * I + 1)]));
+    };
+    const Tc val = in_time(rs, t, nt_face);
     df[e] = val;
     if (df2) df2[e] = val;
   } else if (e < nfaces + ncells) {
     const size_t ec = e - nfaces;
     const int t = (int)(ec / gc.C);
     const int c = (int)(ec - (size_t)t * gc.C);
-    const Tf* s = sc_cells + (size_t)t * gf.C;
-    int J = c / gc.nx, I = c - J * gc.nx;
-    Tc val = Tc(0.25) * (Tc(s[cidx(gf, 2 * J, 2 * I)]) + Tc(s[cidx(gf, 2 * J, 2 * I + 1)]) +
+    const int J = c / gc.nx, I = c - J * gc.nx;
+    auto rs = [&](int tf) -> Tc {
+      const Tf* s = sc_cells + (size_t)tf * gf.C;
+      return Tc(0.25) * (Tc(s[cidx(gf, 2 * J, 2 * I)]) + Tc(s[cidx(gf, 2 * J, 2 * I + 1)]) +
                          Tc(s[cidx(gf, 2 * J + 1, 2 * I)]) + Tc(s[cidx(gf, 2 * J + 1, 2 * I + 1)]));
+    };
+    const Tc val = in_time(rs, t, nt_cell);
     dc_cells[ec] = val;
     if (dc2) dc2[ec] = val;
   }
@@ -842,7 +870,8 @@ template <class Tf, class Tc>
 __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, int t0_face,
                                        int t0_cell, Tf* ff, Tf* fc, const Tc* __restrict__ cnf,
                                        const Tc* __restrict__ cof, const Tc* __restrict__ cnc,
-                                       const Tc* __restrict__ coc, const double* undo_if_rose) {
+                                       const Tc* __restrict__ coc, const double* undo_if_rose, int tmode) {
+  pdl_wait();
   // undo form: subtract the same correction again when the guarded level's
   // residual norm rose (norms[1] after vs norms[0] before; NaN counts as rose)
   // interpolation arithmetic: fp64 when either level is fp64, else fp32
@@ -855,11 +884,20 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t nfaces = (size_t)nt_face * gf.F;
   const size_t ncells = (size_t)nt_cell * gf.C;
+  // fine slab t of the correction from the coarse slab(s) it sits on (time modes
+  // as in restrict_kernel: 1 linear between points, 2 piecewise constant)
+  auto in_time = [&](auto ps, int t) -> W {
+    if (tmode == 0) return ps(t);
+    if (tmode == 2) return ps(t >> 1);
+    if ((t & 1) == 0) return ps(t >> 1);
+    return W(0.5) * (ps(t >> 1) + ps((t >> 1) + 1));
+  };
   if (e < nfaces) {
     const int t = (int)(e / gf.F) + t0_face;
     const int f = (int)(e - (size_t)(t - t0_face) * gf.F);
-    const Tc* n = cnf + (size_t)t * gc.F;
-    const Tc* o = cof + (size_t)t * gc.F;
+    auto ps = [&](int tc) -> W {
+    const Tc* n = cnf + (size_t)tc * gc.F;
+    const Tc* o = cof + (size_t)tc * gc.F;
     W val;
     if (f < gf.Fx) {
       int j = f / (gf.nx + 1), i = f - j * (gf.nx + 1);
@@ -883,20 +921,24 @@ __global__ void prolong_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cel
       W tb = W(0.75) * d(jb, ia) + W(0.25) * d(jb, ib);
       val = wa * ta + wb * tb;
     }
-    ff[(size_t)t * gf.F + f] += Tf(sgn * val);
+    return val;
+    };
+    ff[(size_t)t * gf.F + f] += Tf(sgn * in_time(ps, t));
   } else if (e < nfaces + ncells) {
     const size_t ec = e - nfaces;
     const int t = (int)(ec / gf.C) + t0_cell;
     const int c = (int)(ec - (size_t)(t - t0_cell) * gf.C);
-    const Tc* n = cnc + (size_t)t * gc.C;
-    const Tc* o = coc + (size_t)t * gc.C;
     int j = c / gf.nx, i = c - j * gf.nx;
     int ja, jb, ia, ib;
     cell_interp(j, gc.ny, ja, jb);
     cell_interp(i, gc.nx, ia, ib);
-    auto d = [&](int J, int I) { return W(n[cidx(gc, J, I)]) - W(o[cidx(gc, J, I)]); };
-    W val = W(0.5625) * d(ja, ia) + W(0.1875) * d(ja, ib) + W(0.1875) * d(jb, ia) + W(0.0625) * d(jb, ib);
-    fc[(size_t)t * gf.C + c] += Tf(sgn * val);
+    auto ps = [&](int tc) -> W {
+      const Tc* n = cnc + (size_t)tc * gc.C;
+      const Tc* o = coc + (size_t)tc * gc.C;
+      auto d = [&](int J, int I) { return W(n[cidx(gc, J, I)]) - W(o[cidx(gc, J, I)]); };
+      return W(0.5625) * d(ja, ia) + W(0.1875) * d(ja, ib) + W(0.1875) * d(jb, ia) + W(0.0625) * d(jb, ib);
+    };
+    fc[(size_t)t * gf.C + c] += Tf(sgn * in_time(ps, t));
   }
 }
 
@@ -912,6 +954,7 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // in the element type: the reduction runs in T and converts once per block.
 template <class T>
 __global__ void absmax_kernel(const T* __restrict__ a, size_t n, double* out, int* err) {
+  pdl_wait();
   T m = T(0);
   bool bad = false;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
@@ -933,6 +976,7 @@ __global__ void absmax_kernel(const T* __restrict__ a, size_t n, double* out, in
 
 template <class T>
 __global__ void sumsq_kernel(const T* __restrict__ a, size_t n, double* out) {
+  pdl_wait();
   double s = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     double v = (double)a[e];
@@ -952,6 +996,7 @@ __global__ void sumsq_kernel(const T* __restrict__ a, size_t n, double* out) {
 // subtract the mean of each of `count` slabs of length C (one block per slab)
 template <class T>
 __global__ void remove_mean_kernel(T* a, int C) {
+  pdl_wait();
   T* s = a + (size_t)blockIdx.x * C;
   double acc = 0.0;
   for (int e = threadIdx.x; e < C; e += blockDim.x) acc += (double)s[e];
@@ -972,6 +1017,7 @@ __global__ void remove_mean_kernel(T* a, int C) {
 
 template <class Ts, class Td>
 __global__ void convert_kernel(const Ts* __restrict__ s, Td* d, size_t n) {
+  pdl_wait();
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
     d[e] = Td(s[e]);
 }
@@ -981,13 +1027,32 @@ __global__ void convert_kernel(const Ts* __restrict__ s, Td* d, size_t n) {
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
 
+// Launch with the programmatic-stream-serialization attribute (see pdl_wait):
+// inside the captured V-cycle graph consecutive kernels get programmatic
+// edges, so a kernel's launch overlaps the end of its predecessor.
+template <class... KArgs, class... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
                          cudaStream_t st, double* sq, const double* only_if_undone) {
   const int tpb = 128;
   const int n = g.F > g.C ? g.F : g.C;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
-  nso_residual_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, sf, sr, sq, only_if_undone);
+  launch_pdl(nso_residual_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, sf, sr, sq, only_if_undone);
 }
 
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
@@ -1000,7 +1065,7 @@ void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T
   const int n = nrx * (g.nx + 1) + (g.ny + 1) * ncy + colour_extent(g.nx, px) * nrx;
   const int tpb = 128;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
-  nso_residual_colour_kernel<T><<<grid, tpb, 0, st>>>(g, x, z, res, out, px, py, only_if_undone);
+  launch_pdl(nso_residual_colour_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, px, py, only_if_undone);
 }
 
 template <class S>
@@ -1028,7 +1093,8 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
     cudaFuncSetAttribute((const void*)scgs_colour_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          227 * 1024 - (int)fa.sharedSizeBytes);
   });
-  scgs_colour_kernel<T, S><<<blocks_for(ncell, cpb), 32 * cpb, sm, st>>>(g, x, r, colour, ncx, ncy, cpb, lm_dev);
+  launch_pdl(scgs_colour_kernel<T, S>, dim3(blocks_for(ncell, cpb)), dim3(32 * cpb), sm, st, g, x, r, colour, ncx, ncy,
+             cpb, lm_dev);
 }
 
 template <class T>
@@ -1046,21 +1112,26 @@ size_t scgs_smem_bytes(int N, size_t tsize) {
 template <class Tf, class Tc>
 void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st) {
   const int tpb = 256;
-  const int N = gf.N;
+  const int N = gc.N;                       // coarse slab counts
+  const bool in_time = gc.N != gf.N;
   // v (N+1 slabs) with pbar (N+1), then u (N) with p (N)
   size_t n1 = (size_t)(N + 1) * gc.F + (size_t)(N + 1) * gc.C;
-  restrict_kernel<Tf, Tc><<<blocks_for(n1, tpb), tpb, 0, st>>>(gf, gc, N + 1, N + 1, s.v, s.pbar, d.v, d.pbar,
-                                                                d2.v, d2.pbar);
+  launch_pdl(restrict_kernel<Tf, Tc>, dim3(blocks_for(n1, tpb)), dim3(tpb), 0, st, gf, gc, N + 1, N + 1, s.v, s.pbar,
+             d.v, d.pbar, d2.v, d2.pbar, in_time ? 1 : 0);
   size_t n2 = (size_t)N * gc.F + (size_t)N * gc.C;
-  restrict_kernel<Tf, Tc><<<blocks_for(n2, tpb), tpb, 0, st>>>(gf, gc, N, N, s.u, s.p, d.u, d.p, d2.u, d2.p);
+  launch_pdl(restrict_kernel<Tf, Tc>, dim3(blocks_for(n2, tpb)), dim3(tpb), 0, st, gf, gc, N, N, s.u, s.p, d.u, d.p,
+             d2.u, d2.p, in_time ? 2 : 0);
 }
 
 template <class Tf, class Tc>
 void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st) {
   const int tpb = 256;
-  size_t n = (size_t)nt * gc.F;
-  restrict_kernel<Tf, Tc><<<blocks_for(n, tpb), tpb, 0, st>>>(gf, gc, nt, 0, s, nullptr, d, nullptr, nullptr,
-                                                              nullptr);
+  // nt fine target slabs; the coarse level holds nt / 2 of them when it halves N
+  const bool in_time = gc.N != gf.N;
+  const int ntc = in_time ? nt / 2 : nt;
+  size_t n = (size_t)ntc * gc.F;
+  launch_pdl(restrict_kernel<Tf, Tc>, dim3(blocks_for(n, tpb)), dim3(tpb), 0, st, gf, gc, ntc, 0, s,
+             (const Tf*)nullptr, d, (Tc*)nullptr, (Tc*)nullptr, (Tc*)nullptr, in_time ? 3 : 0);
 }
 
 template <class Tf, class Tc>
@@ -1068,13 +1139,14 @@ void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<
                             cudaStream_t st, const double* undo_if_rose) {
   const int tpb = 256;
   const int N = gf.N;
+  const bool in_time = gc.N != gf.N;
   // v and pbar for t = 1..N (v_0 is data), u and p for t = 0..N-1
   size_t n1 = (size_t)N * gf.F + (size_t)N * gf.C;
-  prolong_correct_kernel<Tf, Tc><<<blocks_for(n1, tpb), tpb, 0, st>>>(gf, gc, N, N, 1, 1, f.v, f.pbar, cn.v, co.v,
-                                                                      cn.pbar, co.pbar, undo_if_rose);
+  launch_pdl(prolong_correct_kernel<Tf, Tc>, dim3(blocks_for(n1, tpb)), dim3(tpb), 0, st, gf, gc, N, N, 1, 1, f.v,
+             f.pbar, cn.v, co.v, cn.pbar, co.pbar, undo_if_rose, in_time ? 1 : 0);
   size_t n2 = (size_t)N * gf.F + (size_t)N * gf.C;
-  prolong_correct_kernel<Tf, Tc><<<blocks_for(n2, tpb), tpb, 0, st>>>(gf, gc, N, N, 0, 0, f.u, f.p, cn.u, co.u,
-                                                                      cn.p, co.p, undo_if_rose);
+  launch_pdl(prolong_correct_kernel<Tf, Tc>, dim3(blocks_for(n2, tpb)), dim3(tpb), 0, st, gf, gc, N, N, 0, 0, f.u,
+             f.p, cn.u, co.u, cn.p, co.p, undo_if_rose, in_time ? 2 : 0);
 }
 
 template <class T>
@@ -1083,7 +1155,7 @@ void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st)
   unsigned nb = blocks_for(n, tpb);
   if (nb > 1216) nb = 1216;
   if (nb == 0) nb = 1;
-  absmax_kernel<T><<<nb, tpb, 0, st>>>(a, n, out, err);
+  launch_pdl(absmax_kernel<T>, dim3(nb), dim3(tpb), 0, st, a, n, out, err);
 }
 
 template <class T>
@@ -1092,13 +1164,13 @@ void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st) {
   unsigned nb = blocks_for(n, tpb);
   if (nb > 1216) nb = 1216;
   if (nb == 0) nb = 1;
-  sumsq_kernel<T><<<nb, tpb, 0, st>>>(a, n, out);
+  launch_pdl(sumsq_kernel<T>, dim3(nb), dim3(tpb), 0, st, a, n, out);
 }
 
 template <class T>
 void launch_remove_mean(T* a, int count, int C, cudaStream_t st) {
   if (count <= 0) return;
-  remove_mean_kernel<T><<<count, 256, 0, st>>>(a, C);
+  launch_pdl(remove_mean_kernel<T>, dim3(count), dim3(256), 0, st, a, C);
 }
 
 template <class Ts, class Td>

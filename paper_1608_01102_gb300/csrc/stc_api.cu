@@ -134,18 +134,19 @@ void* dalloc(stc_problem* P, size_t bytes) {
   return p;
 }
 
-Geom make_geom(const stc_params& prm, int nx, int ny, double h) {
+// (N, dt: the level's; the smoother's LM shift stays the finest level's)
+Geom make_geom(const stc_params& prm, int nx, int ny, double h, int N, double dt) {
   Geom g;
   g.nx = nx;
   g.ny = ny;
-  g.N = prm.num_steps;
+  g.N = N;
   g.Fx = ny * (nx + 1);
   g.F = g.Fx + (ny + 1) * nx;
   g.C = nx * ny;
   g.h = h;
   g.ih = 1.0 / h;
-  g.dt = prm.dt;
-  g.idt = 1.0 / prm.dt;
+  g.dt = dt;
+  g.idt = 1.0 / dt;
   g.a = prm.K / prm.r;
   g.lm = prm.lm_shift < 0 ? 1.0 / (prm.dt * prm.dt) : prm.lm_shift;
   g.omega = prm.scgs_omega;
@@ -771,7 +772,7 @@ bool params_valid(const stc_params& prm) {
       prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
-      prm.al_threshold != prm.al_threshold);
+      prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1);
 }
 
 // Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
@@ -782,30 +783,33 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   const bool dbl = prm.precision == 1;
   const size_t ts = dbl ? 8 : 4;
   const size_t N = (size_t)prm.num_steps;
-  std::vector<std::pair<int, int>> dims{{prm.nx, prm.ny}};
-  int nx = prm.nx, ny = prm.ny;
+  struct Dim { int nx, ny, N; };
+  std::vector<Dim> dims{{prm.nx, prm.ny, prm.num_steps}};
+  int nx = prm.nx, ny = prm.ny, Nl = prm.num_steps;
   while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
     nx /= 2;
     ny /= 2;
-    dims.push_back({nx, ny});
+    if (prm.time_coarsen && Nl % 2 == 0) Nl /= 2;
+    dims.push_back({nx, ny, Nl});
   }
   auto faces = [](int x, int y) { return (size_t)y * (x + 1) + (size_t)(y + 1) * x; };
-  auto fieldset = [&](size_t F, size_t C, size_t s) {
-    return b((N + 1) * F * s) + b((N + 1) * C * s) + b(N * F * s) + b(N * C * s);
+  auto fieldset = [&](size_t F, size_t C, size_t s, size_t Nl_) {
+    return b((Nl_ + 1) * F * s) + b((Nl_ + 1) * C * s) + b(Nl_ * F * s) + b(Nl_ * C * s);
   };
   size_t total = 0;
   for (size_t l = 0; l < dims.size(); ++l) {
-    const size_t F = faces(dims[l].first, dims[l].second), C = (size_t)dims[l].first * dims[l].second;
+    const size_t F = faces(dims[l].nx, dims[l].ny), C = (size_t)dims[l].nx * dims[l].ny;
+    const size_t Nl_ = (size_t)dims[l].N;
     const size_t s = (dbl || (l > 0 && l == dims.size() - 1)) ? 8 : 4;
-    total += 3 * fieldset(F, C, s) + (l > 0 ? fieldset(F, C, s) : 0) + b(N * F * s);
+    total += 3 * fieldset(F, C, s, Nl_) + (l > 0 ? fieldset(F, C, s, Nl_) : 0) + b(Nl_ * F * s);
   }
   const size_t F = faces(prm.nx, prm.ny), C = (size_t)prm.nx * prm.ny;
   total += 3 * b((N + 1) * C * ts) + b(N * C * ts) + 2 * b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) +
-           b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts) : 0) + 4 * b(N * F * ts) +
+           b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts, N) : 0) + 4 * b(N * F * ts) +
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
            b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
-  Geom g0 = make_geom(prm, prm.nx, prm.ny, 1.0 / prm.nx);
+  Geom g0 = make_geom(prm, prm.nx, prm.ny, 1.0 / prm.nx, prm.num_steps, prm.dt);
   if (project_needs_scratch(g0, ts)) total += b((N + 1) * project_smem(g0, ts));
   return total;
 }
@@ -860,6 +864,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->cgc_guard = 1;
   p->lm_adapt = 1;
   p->al_threshold = -1.0;
+  p->time_coarsen = 0;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -886,16 +891,22 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
   P->dbl = prm.precision == 1;
   P->ts = P->dbl ? 8 : 4;
   stc_status s = guarded(nullptr, [&]() {
-    // hierarchy: halve while both even and the halves stay >= coarsest_n (space only, Sec. 4.2)
-    int nx = prm.nx, ny = prm.ny;
-    double h = 1.0 / prm.nx;
+    // hierarchy: halve while both even and the halves stay >= coarsest_n (in
+    // space, Sec. 4.2); with time_coarsen each level whose N is even also
+    // hands the next one N/2 steps of 2 dt
+    int nx = prm.nx, ny = prm.ny, Nl = prm.num_steps;
+    double h = 1.0 / prm.nx, dtl = prm.dt;
     std::vector<Geom> geoms;
-    geoms.push_back(make_geom(prm, nx, ny, h));
+    geoms.push_back(make_geom(prm, nx, ny, h, Nl, dtl));
     while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
       nx /= 2;
       ny /= 2;
       h *= 2.0;
-      geoms.push_back(make_geom(prm, nx, ny, h));
+      if (prm.time_coarsen && Nl % 2 == 0) {
+        Nl /= 2;
+        dtl *= 2.0;
+      }
+      geoms.push_back(make_geom(prm, nx, ny, h, Nl, dtl));
     }
     const Geom& g0 = geoms[0];
     if (!advect_supported(g0)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip advection sweep");
@@ -1185,6 +1196,16 @@ stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx
   }
   if (nx) *nx = p->lv[level].g.nx;
   if (ny) *ny = p->lv[level].g.ny;
+  return STC_OK;
+}
+
+stc_status stc_level_steps(const stc_problem* p, int level, int* num_steps, double* dt) {
+  if (!p || level < 0 || level >= (int)p->lv.size()) {
+    g_last_error = "level out of range";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (num_steps) *num_steps = p->lv[level].g.N;
+  if (dt) *dt = p->lv[level].g.dt;
   return STC_OK;
 }
 

@@ -74,6 +74,12 @@ __host__ __device__ inline int cidx(const Geom& g, int j, int i) { return j * g.
 template <class T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Programmatic dependent launch: a kernel of the V-cycle chain may be launched
+// while its predecessor is still finishing; it waits here, before touching any
+// data, until the predecessor has completed and its writes are visible.  A
+// no-op when the kernel was launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // Row/column of e = threadIdx.x, threadIdx.x + blockDim.x, ... in a row-major
 // range of rows of length P, advanced without a division per element.
 struct RowWalk {

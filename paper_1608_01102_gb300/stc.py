@@ -32,7 +32,7 @@ class StcParams(ctypes.Structure):
                 ("eps_admm", c_double), ("max_vcycles", c_int), ("metric_levels", c_int),
                 ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
                 ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
-                ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double)]
+                ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double), ("time_coarsen", c_int)]
 
 
 class StcReport(ctypes.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = {
     "stc_get_field": (c_int, [c_void_p, c_int, c_int, P_double, c_size_t]),
     "stc_set_field": (c_int, [c_void_p, c_int, c_int, P_double, c_size_t]),
     "stc_level_info": (c_int, [c_void_p, P_int, c_int, P_int, P_int]),
+    "stc_level_steps": (c_int, [c_void_p, c_int, P_int, P_double]),
     "stc_advect": (c_int, [c_void_p, c_int]),
     "stc_get_taylor_orders": (c_int, [c_void_p, P_int, c_size_t]),
     "stc_metric_terms": (c_int, [c_void_p]),
@@ -193,11 +194,16 @@ class Problem:
         _check(self.lib.stc_level_info(self.h, ctypes.byref(nl), 0, None, None))
         return nl.value
 
+    def level_steps(self, level=0):
+        n, dt = c_int(), c_double()
+        _check(self.lib.stc_level_steps(self.h, level, ctypes.byref(n), ctypes.byref(dt)))
+        return n.value, dt.value
+
     def field_shape(self, name, level=0):
         nx, ny = self.level_shape(level)
         F = ny * (nx + 1) + (ny + 1) * nx
         C = nx * ny
-        N = self.N
+        N = self.level_steps(level)[0] if level > 0 else self.N
         face_np1 = ("V", "RES_V", "RES_IN_V", "XOLD_V", "KKT_G")
         cell_np1 = ("PBAR", "RES_PBAR", "RES_IN_PBAR", "XOLD_PBAR", "RHO", "MTERM")
         face_n = ("U", "RES_U", "RES_IN_U", "XOLD_U", "Z", "VSTAR", "LAMBDA", "W", "Y", "KKT_U")

@@ -207,6 +207,78 @@ def test_transfers(prec):
 
 
 # ---------------------------------------------------------------------------
+# a14: time coarsening (opt-in): hierarchy, transfers in space and time, V-cycle
+# ---------------------------------------------------------------------------
+def _tc_random_state(P, seed, g, N):
+    rng = np.random.default_rng(seed)
+    m = g.interior_faces()
+    x = dict(v=rng.standard_normal((N + 1, g.F)) * m, pbar=rng.standard_normal((N + 1, g.C)),
+             u=rng.standard_normal((N, g.F)) * m, p=rng.standard_normal((N, g.C)))
+    x["v"][0] = 0.0
+    x["pbar"][0] = 0.0
+    return x
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_time_coarsened_hierarchy_and_transfers(prec):
+    nx, ny, N = 16, 12, 8
+    P, G = make_pair(nx, ny, N=N, precision=prec, time_coarsen=True)
+    lv = stfas.levels(P)
+    assert G.num_levels() == len(lv)
+    for l, (g, Pl) in enumerate(lv):
+        n, dt = G.level_steps(l)
+        assert n == Pl.N and dt == pytest.approx(Pl.dt, rel=1e-15)
+    (g0, P0), (g1, P1) = lv[0], lv[1]
+    assert P1.N == N // 2
+    x0 = _tc_random_state(P, 62, g0, N)
+    G.set_state(x0, 0)
+    G.restrict(0)
+    xc = stfas.restrict_state_st(g0, x0, True)
+    got = G.get_state(1)
+    tol = 1e-14 if prec == 1 else 1e-6
+    for k in xc:
+        assert got[k].shape == xc[k].shape and rel(got[k], xc[k]) < tol, k
+    xn = _tc_random_state(P, 63, g1, P1.N)
+    G.set_state(xn, 1)
+    G.prolong_correct(0)
+    corr = stfas.prolong_state_st(g0, g1, kkt.state_sub(xn, xc), True)
+    corr["v"][0] = 0.0
+    corr["pbar"][0] = 0.0
+    got = G.get_state(0)
+    for k in x0:
+        assert rel(got[k], x0[k] + corr[k]) < tol * 10, k
+    # the targets restrict as point fields without an end point
+    z = workloads.random_faces(np.random.default_rng(64), nx, ny, N)
+    G.set("VSTAR", z)
+    G.set("LAMBDA", np.zeros_like(z))
+    G.prepare_targets()
+    zc = stfas.restrict_targets(g0, z, True)
+    assert rel(G.get("Z", 1), zc) < tol
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_time_coarsened_vcycle(prec):
+    nx, ny, N = 16, 16, 8
+    P, G = make_pair(nx, ny, N=N, precision=prec, r=1e-3, time_coarsen=True)
+    assert [G.level_steps(l)[0] for l in range(G.num_levels())] == [Pl.N for _, Pl in stfas.levels(P)]
+    v = velocity_trajectory(nx, ny, N, amp=0.5, seed=5)
+    lam = workloads.random_faces(np.random.default_rng(6), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("VSTAR", v[:N])
+    G.set("LAMBDA", lam)
+    G.prepare_targets()
+    z = v[:N] - lam / P.K
+    x = kkt.zero_state(P)
+    for c in range(2):
+        f_gpu = G.vcycle(1)
+        f_ref = stfas.stfas_cycle(P, x, z)
+        got = G.get_state(0)
+        for k in x:
+            assert rel(got[k], x[k]) < TOL[prec]["vcycle"], (c, k, rel(got[k], x[k]))
+        assert abs(f_gpu - f_ref) <= 1e-3 * f_ref + TOL[prec]["vcycle"] * 1e3
+
+
+# ---------------------------------------------------------------------------
 # a10: full V-cycle (Alg. 2) from the AO target
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", PREC)
