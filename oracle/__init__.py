@@ -8,7 +8,8 @@ the product package.
 
 Every function is a plain, slow, fp64 restatement of the paper
 (Pan & Manocha, "Efficient Optimal Control of Smoke using Spacetime
-Multigrid"), citing the section / equation / algorithm it follows:
+Multigrid"), citing the section / equation / algorithm it follows, on the
+2D grid (``mac.Grid``) and the 3D grid (``mac.Grid3``; ``kkt.Problem(nz=..)``):
 
 * ``mac``        -- staggered (MAC) grid operators: div, grad, vorticity form
                     self-advection Adv (Sec. 3.1, Eq. NSA), QUICK upwind
@@ -26,7 +27,8 @@ Multigrid"), citing the section / equation / algorithm it follows:
                     (the gradient-based comparison of Sec. 5) for tiny grids.
 
 Parity status: every function listed above is pinned by ``tests/`` against
-closed forms, library routines, finite differences or invariants, except the
+closed forms, library routines, finite differences or invariants (the 3D
+operators also against the pinned 2D ones on each coordinate plane), except the
 full ADMM solve, whose agreement with the paper's own runs is unpinned (the
 paper's workloads are not available); only its self-consistency is pinned.
 """

@@ -41,10 +41,12 @@ class Problem:
     time_coarsen: bool = False       # STFAS coarse levels halve N too (the paper: space only)
     self_advection: bool = True      # False drops Adv (linear saddle problem; pins only)
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
+    nz: int = 0                      # 0: the 2D grid nx x ny; > 0: the 3D grid nx x ny x nz
 
     def __post_init__(self):
         self.h = 1.0 / self.nx
-        self.grid = mac.Grid(self.nx, self.ny, self.h)
+        self.grid = (mac.Grid3(self.nx, self.ny, self.nz, self.h) if self.nz
+                     else mac.Grid(self.nx, self.ny, self.h))
         self.rho0 = np.asarray(self.rho0, float).ravel()
         if self.v0 is None:
             self.v0 = np.zeros(self.grid.F)
@@ -59,7 +61,7 @@ class Problem:
             return np.zeros(self.grid.C)
         star, c = self.keyframes[i]
         return metric.apply_metric(self.nx, self.ny, rho_i - star, self.metric_levels,
-                                   self.metric_sigma0, c)
+                                   self.metric_sigma0, c, self.nz)
 
     def misfit(self, rhos):
         e = 0.0

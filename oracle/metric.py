@@ -4,7 +4,8 @@ Sec. 4.1: C_i is a sum of Gaussian filters whose standard deviation doubles
 from one to the next.  Readings (the paper gives no sigma_0, truncation or
 count): sigma_l = sigma_0 * 2^l cells, l = 0..L-1, taps truncated at
 ceil(3 sigma_l), weights normalised to sum 1, clamp-to-edge boundary, separable
-in x and y.  L = 0 gives C_i = c_i I (the plain objective of Eq. opt).
+in x and y (and z on a 3D grid).  L = 0 gives C_i = c_i I (the plain
+objective of Eq. opt).
 """
 import math
 
@@ -35,27 +36,32 @@ def blur_matrix_1d(n, sigma):
     return M
 
 
-def apply_metric(nx, ny, x, levels, sigma0=1.0, c=1.0):
-    """C x = c sum_l G_l^T G_l x for a centre field x (flattened, i fastest)."""
-    X = x.reshape(ny, nx)
+def apply_metric(nx, ny, x, levels, sigma0=1.0, c=1.0, nz=0):
+    """C x = c sum_l G_l^T G_l x for a centre field x (flattened, i fastest);
+    nz > 0 makes it a 3D field of shape (nz, ny, nx)."""
+    shape = (nz, ny, nx) if nz else (ny, nx)
+    X = x.reshape(shape)
     if levels == 0:
         return c * x.copy()
     out = np.zeros_like(X)
     for l in range(levels):
         s = sigma0 * 2.0 ** l
-        Mx = blur_matrix_1d(nx, s)
-        My = blur_matrix_1d(ny, s)
-        GX = My @ X @ Mx.T          # G_l x
-        out += My.T @ GX @ Mx       # G_l^T (G_l x)
+        mats = [blur_matrix_1d(n, s) for n in shape]     # one per axis
+        GX = X
+        for ax, M in enumerate(mats):                    # G_l x
+            GX = np.moveaxis(np.tensordot(M, GX, axes=([1], [ax])), 0, ax)
+        for ax, M in enumerate(mats):                    # G_l^T (G_l x)
+            GX = np.moveaxis(np.tensordot(M.T, GX, axes=([1], [ax])), 0, ax)
+        out += GX
     return c * out.ravel()
 
 
-def metric_matrix(nx, ny, levels, sigma0=1.0, c=1.0):
+def metric_matrix(nx, ny, levels, sigma0=1.0, c=1.0, nz=0):
     """Dense C (for small-grid pins only)."""
-    n = nx * ny
+    n = nx * ny * max(nz, 1)
     M = np.zeros((n, n))
     for k in range(n):
         e = np.zeros(n)
         e[k] = 1.0
-        M[:, k] = apply_metric(nx, ny, e, levels, sigma0, c)
+        M[:, k] = apply_metric(nx, ny, e, levels, sigma0, c, nz)
     return M

@@ -6,7 +6,6 @@ definition itself: Q v = v - G phi with (D G) phi = D v on the closed box
 (Neumann Laplacian), solved exactly by a sparse factorisation with one cell
 grounded (the constant is the Laplacian's null space and G removes it).
 """
-from functools import lru_cache
 
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -14,16 +13,21 @@ import scipy.sparse.linalg as spla
 from . import mac
 
 
-@lru_cache(maxsize=32)
-def _factor(nx, ny, h):
-    o = mac._ops(nx, ny, h)
-    L = (o["D"] @ o["G"]).tocsc()
-    return spla.factorized(L[1:, 1:].tocsc())
+_FACTORS = {}
+
+
+def _factor(grid):
+    key = grid.key()
+    if key not in _FACTORS:
+        o = mac.ops(grid)
+        L = (o["D"] @ o["G"]).tocsc()
+        _FACTORS[key] = spla.factorized(L[1:, 1:].tocsc())
+    return _FACTORS[key]
 
 
 def poisson_neumann(grid, b):
     """Solve (D G) phi = b (b must have zero mean); returns the mean-zero phi."""
-    solve = _factor(grid.nx, grid.ny, grid.h)
+    solve = _factor(grid)
     phi = np.zeros(grid.C)
     phi[1:] = solve(b[1:])
     return phi - phi.mean()

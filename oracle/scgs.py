@@ -17,9 +17,10 @@ Readings:
   the fixed point f = 0) and [[-I, g], [g^T, 0]]; couplings -I/dt
   between v_i and u_i, and I/dt + dAdv_loc(v_{i+1}) between u_i and v_{i+1}
   (and its transpose); g = d(grad p)/dp_c = (+1, -1, +1, -1)/h on the
-  (left, right, bottom, top) faces.  The second-order term of Adv is dropped
+  (left, right, bottom, top) faces, and (+1, -1)/h on the (back, front)
+  z-faces in 3D.  The second-order term of Adv is dropped
   (Eq. HESS keeps only (K/r) I on the v diagonal).
-* colours c = (i mod 2) + 2 (j mod 2) in increasing order; every cell of one
+* colours c = (i mod 2) + 2 (j mod 2) [+ 4 (k mod 2)] in increasing order; every cell of one
   colour is updated from the same state; under-relaxation x += omega * delta
   with omega = 0.8 by default (undamped sweeps diverge once the flow's CFL
   number passes 1; Vanka smoothers for Navier-Stokes are customarily damped).
@@ -30,11 +31,22 @@ import numpy as np
 
 from . import kkt, mac
 
-NB = 5  # 2d + 1 unknowns per block in 2D
+def nfaces(grid):
+    """2d faces per cell; a time block holds them and one pressure (2d + 1)."""
+    return 2 * grid.dim
 
 
-def cell_faces(grid, J, I):
-    """Local faces (left, right, bottom, top) of cells (J, I) and their activity."""
+def cell_faces(grid, idx):
+    """Local faces (left, right, bottom, top[, back, front]) of the cells with
+    index arrays idx = (J, I) or (K, J, I), and their activity (1 = not a wall)."""
+    if grid.dim == 3:
+        K, J, I = idx
+        faces = np.stack([grid.xf(K, J, I), grid.xf(K, J, I + 1), grid.yf(K, J, I),
+                          grid.yf(K, J + 1, I), grid.zf(K, J, I), grid.zf(K + 1, J, I)], -1)
+        active = np.stack([I > 0, I < grid.nx - 1, J > 0, J < grid.ny - 1,
+                           K > 0, K < grid.nz - 1], -1).astype(float)
+        return faces, active
+    J, I = idx
     faces = np.stack([grid.xf(J, I), grid.xf(J, I + 1), grid.yf(J, I), grid.yf(J + 1, I)], -1)
     active = np.stack([I > 0, I < grid.nx - 1, J > 0, J < grid.ny - 1], -1).astype(float)
     return faces, active
@@ -44,69 +56,76 @@ _STATIC = {}
 
 
 def _static_entries(grid, faces):
-    """OmW[f, g] and T[f, g] for f, g among each cell's faces (fixed stencils)."""
+    """M[f, g] and T[f, g] of every bilinear term of Adv, for f, g among each
+    cell's faces (fixed stencils)."""
     key = (grid.key(), faces.tobytes())
     if key not in _STATIC:
-        o = mac.ops(grid)
-        rows = np.repeat(faces[:, :, None], 4, axis=2).ravel()
-        cols = np.repeat(faces[:, None, :], 4, axis=1).ravel()
-        om = np.asarray(o["OmW"][rows, cols]).reshape(faces.shape[0], 4, 4)
-        tt = np.asarray(o["T"][rows, cols]).reshape(faces.shape[0], 4, 4)
-        _STATIC[key] = (om, tt)
+        nf = faces.shape[1]
+        rows = np.repeat(faces[:, :, None], nf, axis=2).ravel()
+        cols = np.repeat(faces[:, None, :], nf, axis=1).ravel()
+        ent = []
+        for M, T in mac.ops(grid)["terms"]:
+            ent.append((np.asarray(M[rows, cols]).reshape(faces.shape[0], nf, nf),
+                        np.asarray(T[rows, cols]).reshape(faces.shape[0], nf, nf)))
+        _STATIC[key] = ent
     return _STATIC[key]
 
 
 def local_adv_jacobian(grid, v, faces):
-    """dAdv_f / dv_g for f, g among each cell's four faces: (ncell, 4, 4).
+    """dAdv_f / dv_g for f, g among each cell's faces: (ncell, 2d, 2d).
 
-    Entries of d Adv / d v = diag(a) OmW + diag(b) T at the local rows/columns."""
-    om, tt = _static_entries(grid, faces)
-    a, b = mac.adv_jacobian_factors(grid, v)
-    return a[faces][:, :, None] * om + b[faces][:, :, None] * tt
+    Entries of d Adv / d v = sum over terms of diag(T v) M + diag(M v) T at the
+    local rows/columns."""
+    out = 0.0
+    for (M, T), (m, t) in zip(mac.ops(grid)["terms"], _static_entries(grid, faces)):
+        out = out + (T @ v)[faces][:, :, None] * m + (M @ v)[faces][:, :, None] * t
+    return out
 
 
 def assemble(P, grid, x, faces, active):
-    """Block-tridiagonal local Jacobians (Dg, Lo, Up), each (ncell, 2N, 5, 5)."""
+    """Block-tridiagonal local Jacobians (Dg, Lo, Up), each (ncell, 2N, 2d+1, 2d+1)."""
     N, dt, h = P.N, P.dt, grid.h
-    nc = faces.shape[0]
+    nc, nf = faces.shape
+    NB = nf + 1
     nb = 2 * N
     Dg = np.zeros((nc, nb, NB, NB))
     Lo = np.zeros((nc, nb, NB, NB))
     Up = np.zeros((nc, nb, NB, NB))
-    gl = active * np.array([1.0, -1.0, 1.0, -1.0]) / h          # (nc, 4)
+    gl = active * np.tile([1.0, -1.0], nf // 2) / h             # (nc, 2d)
     Am = active[:, :, None] * active[:, None, :]                # active-pair mask
-    eye = np.eye(4)[None] * Am
-    ina = np.eye(4)[None] * (1.0 - active)[:, :, None]          # identity on walls
+    eye = np.eye(nf)[None] * Am
+    ina = np.eye(nf)[None] * (1.0 - active)[:, :, None]         # identity on walls
     for k in range(nb):
         if k % 2 == 0:      # B_u(i), i = k/2
-            Dg[:, k, :4, :4] = -eye + ina
+            Dg[:, k, :nf, :nf] = -eye + ina
         else:               # B_v(i), i = (k+1)/2
             i = (k + 1) // 2
             a = (P.K / P.r if i < N else 0.0) + P.lm_shift
-            Dg[:, k, :4, :4] = a * eye + ina
-        Dg[:, k, :4, 4] = gl
-        Dg[:, k, 4, :4] = gl
+            Dg[:, k, :nf, :nf] = a * eye + ina
+        Dg[:, k, :nf, nf] = gl
+        Dg[:, k, nf, :nf] = gl
     for i in range(N):
         k = 2 * i
         sa = 1.0 if P.self_advection else 0.0
         M = (eye / dt + sa * local_adv_jacobian(grid, x["v"][i + 1], faces) * Am)
-        Up[:, k, :4, :4] = M                          # J[B_u(i), B_v(i+1)]
-        Lo[:, k + 1, :4, :4] = np.transpose(M, (0, 2, 1))   # J[B_v(i+1), B_u(i)]
+        Up[:, k, :nf, :nf] = M                        # J[B_u(i), B_v(i+1)]
+        Lo[:, k + 1, :nf, :nf] = np.transpose(M, (0, 2, 1))   # J[B_v(i+1), B_u(i)]
         if i >= 1:
-            Lo[:, k, :4, :4] = -eye / dt              # J[B_u(i), B_v(i)]
-            Up[:, k - 1, :4, :4] = -eye / dt          # J[B_v(i), B_u(i)]
+            Lo[:, k, :nf, :nf] = -eye / dt            # J[B_u(i), B_v(i)]
+            Up[:, k - 1, :nf, :nf] = -eye / dt        # J[B_v(i), B_u(i)]
     return Dg, Lo, Up
 
 
 def local_rhs(P, grid, r, faces, cells, active):
-    """b = -(f - res) restricted to the local unknowns: (ncell, 2N, 5)."""
+    """b = -(f - res) restricted to the local unknowns: (ncell, 2N, 2d+1)."""
     N = P.N
-    b = np.zeros((faces.shape[0], 2 * N, NB))
+    nf = faces.shape[1]
+    b = np.zeros((faces.shape[0], 2 * N, nf + 1))
     for i in range(N):
-        b[:, 2 * i, :4] = -r["u"][i][faces] * active
-        b[:, 2 * i, 4] = -r["p"][i][cells]
-        b[:, 2 * i + 1, :4] = -r["v"][i + 1][faces] * active
-        b[:, 2 * i + 1, 4] = -r["pbar"][i + 1][cells]
+        b[:, 2 * i, :nf] = -r["u"][i][faces] * active
+        b[:, 2 * i, nf] = -r["p"][i][cells]
+        b[:, 2 * i + 1, :nf] = -r["v"][i + 1][faces] * active
+        b[:, 2 * i + 1, nf] = -r["pbar"][i + 1][cells]
     return b
 
 
@@ -132,8 +151,9 @@ def block_thomas(Dg, Lo, Up, b):
 
 
 def dense_from_blocks(Dg, Lo, Up):
-    """Assemble the dense (2N*5)^2 matrix of one cell's block-tridiagonal system."""
+    """Assemble the dense (2N*(2d+1))^2 matrix of one cell's block-tridiagonal system."""
     nb = Dg.shape[0]
+    NB = Dg.shape[1]
     A = np.zeros((nb * NB, nb * NB))
     for k in range(nb):
         A[k * NB:(k + 1) * NB, k * NB:(k + 1) * NB] = Dg[k]
@@ -145,6 +165,12 @@ def dense_from_blocks(Dg, Lo, Up):
 
 
 def colour_cells(grid, colour):
+    """Index arrays (J, I) or (K, J, I) of the cells of one parity colour."""
+    if grid.dim == 3:
+        K, J, I = np.meshgrid(np.arange(grid.nz), np.arange(grid.ny), np.arange(grid.nx),
+                              indexing="ij")
+        sel = ((I % 2) + 2 * (J % 2) + 4 * (K % 2)) == colour
+        return K[sel], J[sel], I[sel]
     J, I = np.meshgrid(np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
     sel = ((I % 2) + 2 * (J % 2)) == colour
     return J[sel], I[sel]
@@ -152,11 +178,12 @@ def colour_cells(grid, colour):
 
 def smooth_colour(P, grid, x, z, res, colour):
     """Update every cell of one colour from the same state (in place)."""
-    J, I = colour_cells(grid, colour)
-    if J.size == 0:
+    idx = colour_cells(grid, colour)
+    if idx[0].size == 0:
         return
-    faces, active = cell_faces(grid, J, I)
-    cells = grid.cell(J, I)
+    faces, active = cell_faces(grid, idx)
+    nf = faces.shape[1]
+    cells = grid.cell(*idx)
     f = kkt.nso_residual(P, grid, x, z)
     r = {k: f[k] - res[k] for k in f}
     Dg, Lo, Up = assemble(P, grid, x, faces, active)
@@ -164,13 +191,13 @@ def smooth_colour(P, grid, x, z, res, colour):
     d = P.omega * block_thomas(Dg, Lo, Up, b)
     N = P.N
     for i in range(N):
-        x["u"][i][faces] += d[:, 2 * i, :4] * active
-        x["p"][i][cells] += d[:, 2 * i, 4]
-        x["v"][i + 1][faces] += d[:, 2 * i + 1, :4] * active
-        x["pbar"][i + 1][cells] += d[:, 2 * i + 1, 4]
+        x["u"][i][faces] += d[:, 2 * i, :nf] * active
+        x["p"][i][cells] += d[:, 2 * i, nf]
+        x["v"][i + 1][faces] += d[:, 2 * i + 1, :nf] * active
+        x["pbar"][i + 1][cells] += d[:, 2 * i + 1, nf]
 
 
 def sweep(P, grid, x, z, res):
     """One SCGS sweep: the 2^d colours in increasing order."""
-    for colour in range(4):
+    for colour in range(2 ** grid.dim):
         smooth_colour(P, grid, x, z, res, colour)

@@ -5,12 +5,13 @@ Sec. 4.2 / Alg. 2: a FAS V(2,2) cycle on a hierarchy coarsened in space only
 level, coarse right-hand side res^{2h} = f^{2h}(R x^h) + R(res^h - f^h(x^h)).
 
 Readings:
-* levels halve nx, ny while both are even and the halves are >= coarsest_n.
+* levels halve every axis while all are even and the halves are >= coarsest_n.
 * R (Sec. 4.3 names trilinear interpolation): a coarse cell is the mean of
-  its 4 children; a coarse face the mean of the 2 fine faces lying on it.
-* P: bilinear interpolation at the fine point -- cell fields (3/4, 1/4) per
-  axis; face fields linear along the face normal (weights 1 or 1/2, 1/2) and
-  (3/4, 1/4) across; indices beyond a wall clamp to the last coarse row.
+  its 2^d children; a coarse face the mean of the 2^(d-1) fine faces lying
+  on it.
+* P: (bi/tri)linear interpolation at the fine point -- cell fields (3/4, 1/4)
+  per axis; face fields linear along the face normal (weights 1 or 1/2, 1/2)
+  and (3/4, 1/4) across; indices beyond a wall clamp to the last coarse row.
 * Alg. 2 subtracts P(R x^h) before evaluating f(x^h); here the fine residual
   is evaluated on the smoothed x^h and the correction is the usual
   x^h += P(x^{2h}_new - x^{2h}_old), which is what the subtract/add pair
@@ -41,22 +42,47 @@ import numpy as np
 from . import kkt, mac, scgs
 
 
+def _axes(g):
+    return (g.nx, g.ny, g.nz) if g.dim == 3 else (g.nx, g.ny)
+
+
 def hierarchy(P):
     grids = [P.grid]
     g = P.grid
-    while g.nx % 2 == 0 and g.ny % 2 == 0 and g.nx // 2 >= P.coarsest_n \
-            and g.ny // 2 >= P.coarsest_n:
+    while all(n % 2 == 0 and n // 2 >= P.coarsest_n for n in _axes(g)):
         g = g.coarse()
         grids.append(g)
     return grids
 
 
+def _pair_mean(X, axis):
+    """Mean of the element pairs (2m, 2m+1) along ``axis``."""
+    a = np.take(X, np.arange(0, X.shape[axis] - 1, 2), axis=axis)
+    b = np.take(X, np.arange(1, X.shape[axis], 2), axis=axis)
+    return 0.5 * (a + b)
+
+
+def _even(X, axis):
+    """Elements 0, 2, 4, ... along ``axis`` (fine faces on coarse faces)."""
+    return np.take(X, np.arange(0, X.shape[axis], 2), axis=axis)
+
+
 def restrict_cells(fine, x):
+    if fine.dim == 3:
+        X = x.reshape(fine.cell_shape())
+        return _pair_mean(_pair_mean(_pair_mean(X, 0), 1), 2).ravel()
     X = x.reshape(fine.ny, fine.nx)
     return (0.25 * (X[0::2, 0::2] + X[0::2, 1::2] + X[1::2, 0::2] + X[1::2, 1::2])).ravel()
 
 
 def restrict_faces(fine, v):
+    if fine.dim == 3:
+        # a coarse a-face: even fine a-faces along a, pair means across (axes k, j, i)
+        vx, vy, vz = fine.split(v)
+        cx = _even(_pair_mean(_pair_mean(vx, 0), 1), 2)
+        cy = _even(_pair_mean(_pair_mean(vy, 0), 2), 1)
+        cz = _even(_pair_mean(_pair_mean(vz, 1), 2), 0)
+        return np.concatenate([cx.ravel(), cy.ravel(), cz.ravel()])
     vx, vy = fine.split(v)
     cx = 0.5 * (vx[0::2, 0::2] + vx[1::2, 0::2])      # (nyc, nxc+1)
     cy = 0.5 * (vy[0::2, 0::2] + vy[0::2, 1::2])      # (nyc+1, nxc)
@@ -72,7 +98,26 @@ def _interp_weights_cell(nf, nc):
     return a, b
 
 
+def _interp_cells_axis(Xc, axis, nf):
+    """(3/4, 1/4) interpolation of cell-centred data to nf fine cells along ``axis``."""
+    a, b = _interp_weights_cell(nf, Xc.shape[axis])
+    return 0.75 * np.take(Xc, a, axis=axis) + 0.25 * np.take(Xc, b, axis=axis)
+
+
+def _interp_normal_axis(Xc, axis, nf_faces):
+    """Linear interpolation of face data along the face normal (weights 1 or 1/2, 1/2)."""
+    a, b, wa, wb = _interp_weights_normal(nf_faces, Xc.shape[axis])
+    shape = [1] * Xc.ndim
+    shape[axis] = -1
+    return np.take(Xc, a, axis=axis) * wa.reshape(shape) + np.take(Xc, b, axis=axis) * wb.reshape(shape)
+
+
 def prolong_cells(fine, coarse, xc):
+    if fine.dim == 3:
+        X = xc.reshape(coarse.cell_shape())
+        for axis, nf in enumerate(fine.cell_shape()):
+            X = _interp_cells_axis(X, axis, nf)
+        return X.ravel()
     Xc = xc.reshape(coarse.ny, coarse.nx)
     ay, by = _interp_weights_cell(fine.ny, coarse.ny)
     ax, bx = _interp_weights_cell(fine.nx, coarse.nx)
@@ -90,6 +135,17 @@ def _interp_weights_normal(nf_faces, nc_faces):
 
 
 def prolong_faces(fine, coarse, vc):
+    if fine.dim == 3:
+        out = []
+        for normal, X in zip((2, 1, 0), coarse.split(vc)):     # x-, y-, z-faces; axes (k, j, i)
+            nfs = fine.face_shapes()[2 - normal]
+            for axis in range(3):
+                if axis == normal:
+                    X = _interp_normal_axis(X, axis, nfs[axis])
+                else:
+                    X = _interp_cells_axis(X, axis, nfs[axis])
+            out.append(X.ravel())
+        return np.concatenate(out)
     cx, cy = coarse.split(vc)
     # x-faces: normal axis x (faces 0..nx), transverse axis y (cells)
     a, b, wa, wb = _interp_weights_normal(fine.nx + 1, coarse.nx + 1)

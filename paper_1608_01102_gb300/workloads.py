@@ -13,6 +13,11 @@ are not available, so these stand in for them):
   (centre U[0.2, 0.8]^2, radius U[0.05, 0.12]) or an axis-aligned bar (width
   U[0.04, 0.08], length U[0.2, 0.5], orientation a coin flip); the indicator is
   Gaussian-blurred (sigma in cells, clamped edges) and scaled to a given mass.
+* ``ellipsoid_union`` (3D): the max of 2-4 axis-aligned ellipsoids (centre
+  U[0.25, 0.75]^3, semi-axes U[0.05, 0.2]), blurred (sigma in cells) and
+  scaled to a given mass.
+* 3D arrays are (nz, ny, nx) with i fastest; face vectors hold the x-, y- and
+  z-faces in that order, each (k, j, i) with i fastest.
 """
 import math
 
@@ -106,6 +111,75 @@ def swirl_velocity(nx, ny, amplitude, centre=(0.5, 0.5), width=0.25):
     return np.concatenate([vx.ravel(), vy.ravel()])
 
 
+def cell_centres3(nx, ny, nz):
+    h = 1.0 / nx
+    z, y, x = ((np.arange(n) + 0.5) * h for n in (nz, ny, nx))
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z                    # arrays (nz, ny, nx)
+
+
+def gaussian_ball3(nx, ny, nz, centre, sigma):
+    X, Y, Z = cell_centres3(nx, ny, nz)
+    d2 = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2
+    return np.exp(-d2 / (2.0 * sigma * sigma)).ravel()
+
+
+def ellipsoid_union(nx, ny, nz, seed, mass, blur_cells=1.0, count=None):
+    rng = np.random.default_rng(seed)
+    X, Y, Z = cell_centres3(nx, ny, nz)
+    m = np.zeros((nz, ny, nx))
+    k = int(rng.integers(2, 5)) if count is None else count
+    for _ in range(k):
+        c = rng.uniform(0.25, 0.75, 3)
+        a = rng.uniform(0.05, 0.2, 3)
+        q = ((X - c[0]) / a[0]) ** 2 + ((Y - c[1]) / a[1]) ** 2 + ((Z - c[2]) / a[2]) ** 2
+        m = np.maximum(m, (q <= 1.0).astype(float))
+    for axis in range(3):
+        m = _blur_axis(m, blur_cells, axis)
+    s = m.sum()
+    return (m * (mass / s)).ravel() if s > 0 else m.ravel()
+
+
+def face_count3(nx, ny, nz):
+    return nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx
+
+
+def interior_face_mask3(nx, ny, nz):
+    mx = np.zeros((nz, ny, nx + 1))
+    mx[:, :, 1:nx] = 1.0
+    my = np.zeros((nz, ny + 1, nx))
+    my[:, 1:ny, :] = 1.0
+    mz = np.zeros((nz + 1, ny, nx))
+    mz[1:nz] = 1.0
+    return np.concatenate([mx.ravel(), my.ravel(), mz.ravel()])
+
+
+def random_faces3(rng, nx, ny, nz, count, scale=1.0):
+    """Random 3D face fields, zero on wall faces: (count, F)."""
+    m = interior_face_mask3(nx, ny, nz)
+    return rng.standard_normal((count, face_count3(nx, ny, nz))) * m * scale
+
+
+def swirl_velocity3(nx, ny, nz, amplitude, centre=(0.5, 0.5, 0.5), width=0.25):
+    """A smooth face field rotating about the z axis with a Gaussian envelope
+    and a weak vertical component (zero on walls), for non-trivial 3D states."""
+    h = 1.0 / nx
+    def pos(axis):
+        shp = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)][axis]
+        ax = [np.arange(n) * h if a == 2 - axis else (np.arange(n) + 0.5) * h
+              for a, n in enumerate(shp)]
+        Z, Y, X = np.meshgrid(*ax, indexing="ij")
+        return X, Y, Z
+    out = []
+    for axis in range(3):
+        X, Y, Z = pos(axis)
+        g = np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2)
+                   / (2 * width ** 2)) * amplitude
+        f = [-(Y - centre[1]) * g, (X - centre[0]) * g, 0.25 * (X - centre[0]) * g][axis]
+        out.append(f.ravel())
+    return np.concatenate(out) * interior_face_mask3(nx, ny, nz)
+
+
 def config_small(n=32, N=16):
     """2D, n^2 cells, N steps, dt = 1/N: ball (sigma 0.08) at (0.5, 0.3) to the
     same ball at (0.5, 0.7) at t = T, zero initial velocity, r = 1e-3."""
@@ -120,6 +194,18 @@ def config_letters(n=128, N=40, seed=2002):
     rho0 = gaussian_ball(n, n, (0.5, 0.25), 0.08)
     star = disc_bar_union(n, n, seed, rho0.sum(), 1.5)
     return dict(nx=n, ny=n, N=N, dt=1.0 / N, rho0=rho0, keyframes={N: (star, 1.0)}, r=1e-3)
+
+
+def config_3d(n=64, N=60, seed=3003):
+    """3D, n^3 cells, N steps, dt = 1/N: ball (sigma 0.1) at (0.5, 0.2, 0.5);
+    keyframes at steps N/2 and N (30 and 60 for N = 60), each a seeded union of
+    2-4 ellipsoids blurred by 1 cell and scaled to the initial mass; r = 1e-3."""
+    rho0 = gaussian_ball3(n, n, n, (0.5, 0.2, 0.5), 0.1)
+    rng = np.random.default_rng(seed)
+    kf = {}
+    for step in (N // 2, N):
+        kf[step] = (ellipsoid_union(n, n, n, int(rng.integers(0, 2**31 - 1)), rho0.sum(), 1.0), 1.0)
+    return dict(nx=n, ny=n, nz=n, N=N, dt=1.0 / N, rho0=rho0, keyframes=kf, r=1e-3)
 
 
 def config_serving(count=256, seed=4004, rate=4.0):

@@ -108,8 +108,7 @@ def test_block_thomas_equals_dense_solve():
     rng = np.random.default_rng(13)
     P = _problem(8, 5)
     x = _random_state(P, rng)
-    J, I = scgs.colour_cells(P.grid, 3)
-    faces, active = scgs.cell_faces(P.grid, J, I)
+    faces, active = scgs.cell_faces(P.grid, scgs.colour_cells(P.grid, 3))
     Dg, Lo, Up = scgs.assemble(P, P.grid, x, faces, active)
     b = rng.standard_normal((faces.shape[0], 2 * P.N, 5))
     sol = scgs.block_thomas(Dg, Lo, Up, b)
@@ -129,7 +128,7 @@ def test_local_blocks_are_the_jacobian_of_f():
     z = np.zeros((P.N, P.grid.F))
     g = P.grid
     J, I = np.array([2]), np.array([3])          # an interior cell
-    faces, active = scgs.cell_faces(g, J, I)
+    faces, active = scgs.cell_faces(g, (J, I))
     cell = g.cell(J, I)[0]
     Dg, Lo, Up = scgs.assemble(P, g, x, faces, active)
     A = scgs.dense_from_blocks(Dg[0], Lo[0], Up[0])
