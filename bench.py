@@ -17,6 +17,10 @@ Two more legs follow on rank 0 at N = 1 (skip with --no-solve / --serve 0):
   4 requests/s) replayed in real time into stc_server with a 64 GB budget;
   p50/p99 time to solution (submit to result) and problems/hour.
 
+--workload 3d runs the same step on the 3D workload instead (64^3 cells, 60
+steps, two seeded ellipsoid-union keyframes at t = 30 and 60, metric with 5
+levels); its time-to-solution leg solves that problem, and it has no serving leg.
+
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference];
 N > 1 under torchrun runs one independent replica per GPU (the method has no
 data-path collective) and reports the summed throughput over the max time.
@@ -41,6 +45,11 @@ WORKLOAD = ("2D smoke control, 128^2 cells, 40 timesteps, dt=1/40, fp32 state wi
             "(1.5 cells) mass-matched union of 3-5 discs/bars at t=T; r=1e-3, K=1, C_i with 6 Gaussian "
             "levels; one ADMM iteration per step = AO(2) + %d V(2,2)-cycles + KKT metric + lambda update"
             % VCYCLES)
+WORKLOAD_3D = ("3D smoke control, 64^3 cells, 60 timesteps, dt=1/60, fp32 state with fp64 reductions and "
+               "fp64 coarsest level; Gaussian ball (sigma 0.1) at (0.5,0.2,0.5); keyframes at t=30 and t=60, "
+               "each a seeded (3003) union of 2-4 ellipsoids (semi-axes 0.05-0.2) blurred by 1 cell and "
+               "mass-matched; r=1e-3, K=1, C_i with 5 Gaussian levels; one ADMM iteration per step = AO(2) + "
+               "%d V(2,2)-cycles + KKT metric + lambda update" % VCYCLES)
 ORACLE_STEPS = 2  # timesteps of the bounded oracle sample (same grid, same per-step work)
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level SCGS colour launch
 # of this workload (ncu --set full, profiles/scgs_colour_finest_letters_128x40.md);
@@ -176,6 +185,13 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def workload_spec(name, workloads):
+    """(cfg, n, nz, N, metric levels, description) of a bench workload."""
+    if name == "3d":
+        return workloads.config_3d(64, 60), 64, 64, 60, 5, WORKLOAD_3D
+    return workloads.config_letters(N_CELLS, N_STEPS), N_CELLS, 0, N_STEPS, 6, WORKLOAD
+
+
 def run_native(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -187,15 +203,16 @@ def run_native(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     # oracle baseline first, in a separate process, before heavy GPU work
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    d3 = args.workload == "3d"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not d3:
         cpu = oracle_sample()[0]
 
-    cfg = workloads.config_letters(N_CELLS, N_STEPS)
-    star = cfg["keyframes"][N_STEPS][0]
-    prm = stc.default_params(N_CELLS, N_CELLS, N_STEPS, precision=0, r=1e-3, K=1.0, metric_levels=6)
+    cfg, n, nz, N, levels, desc = workload_spec(args.workload, workloads)
+    keys = cfg["keyframes"]
+    prm = stc.default_params(n, n, N, precision=0, r=1e-3, K=1.0, metric_levels=levels, nz=nz)
     stream = torch.cuda.Stream(device=dev)
     G = stc.Problem(prm, cfg["rho0"], stream=stream.cuda_stream)
-    G.set_keyframes({N_STEPS: (star, 1.0)})
+    G.set_keyframes(keys)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     warm = [False]
@@ -235,32 +252,40 @@ def run_native(args, rank, world, local_rank):
     launches = G.launch_count() - n0
     k_ms, k_n = G.kernel_timing()
     G.set_kernel_timing(False)
-    cells = N_CELLS * N_CELLS * N_STEPS * VCYCLES
+    cells = n * n * (nz or 1) * N * VCYCLES
     ms, value = aggregate(sum(times) / len(times), cells, world, dev)
 
-    # end to end through the public API with host buffers: keyframe up, forces down
-    h2d = star.nbytes
-    d2h = N_STEPS * G.field_shape("U")[1] * 8
+    # end to end through the public API with host buffers: keyframes up, forces down
+    h2d = sum(a.nbytes for a, _ in keys.values())
+    d2h = N * G.field_shape("U")[1] * 8
     e2e_times = []
     for _ in range(max(2, args.steps // 2)):
         t0 = time.perf_counter()
-        G.set_keyframes({N_STEPS: (star, 1.0)})
+        G.set_keyframes(keys)
         step()
         u = G.forces()
         e2e_times.append(time.perf_counter() - t0)
-    assert u.shape[0] == N_STEPS
+    assert u.shape[0] == N
     e2e = {"value": world * cells / (sum(e2e_times) / len(e2e_times)), "unit": "cells/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel: the finest-level SCGS colour sweep
+    # roofline of the dominant kernel: the finest-level SCGS colour sweep.  Per
+    # timestep it reads v (F) and the residual rows at the colour's faces and
+    # cells, and reads and writes the colour's unknowns: a colour holds 1/2^d of
+    # the cells and (in 2D) half, (in 3D) a quarter of the faces of each direction
     F = G.field_shape("V")[1]
     C = G.field_shape("RHO")[1]
-    bytes_per_launch = 4.0 * N_STEPS * (4 * F + 1.5 * C)
+    if d3:
+        bytes_per_launch = 4.0 * N * (2.5 * F + 0.75 * C)
+    else:
+        bytes_per_launch = 4.0 * N * (4 * F + 1.5 * C)
     peak, kind = _peaks()
     achieved = bytes_per_launch / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": SCGS_FINEST_DRAM_BYTES,
-            "kernel": "scgs_colour_kernel<float> (finest level)", "peak_kind": kind,
+            "frac": achieved / peak if achieved else None,
+            "traffic": None if d3 else SCGS_FINEST_DRAM_BYTES,
+            "kernel": ("scgs3_colour_kernel<float> (finest level)" if d3
+                       else "scgs_colour_kernel<float> (finest level)"), "peak_kind": kind,
             "launches_timed": k_n, "avg_launch_us": 1e3 * k_ms / k_n if k_n else None,
             "algorithmic_bytes_per_launch": bytes_per_launch}
     if rank != 0:
@@ -268,7 +293,7 @@ def run_native(args, rank, world, local_rank):
     line = {"metric": "STFAS spacetime cells/s", "value": value, "unit": "cells/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "vcycles_per_step": VCYCLES,
+            "config": {"workload": desc, "vcycles_per_step": VCYCLES,
                        "l2": "256 MiB buffer written between timed steps (outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches * world), "clocks": clocks}
@@ -276,8 +301,8 @@ def run_native(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu_baseline_obj(cpu)
     G.close()
     if world == 1 and not args.no_solve:
-        line["time_to_solution"] = solve_leg(stc, cfg, star, args.solve_max_admm)
-    if world == 1 and args.serve > 0:
+        line["time_to_solution"] = solve_leg(stc, cfg, n, nz, N, levels, args.solve_max_admm)
+    if world == 1 and args.serve > 0 and not d3:
         line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm)
     print(json.dumps(line), flush=True)
 
@@ -295,13 +320,12 @@ def aggregate(ms, cells, world, device):
     return ms, world * cells / (ms * 1e-3)
 
 
-def solve_leg(stc, cfg, star, max_admm):
+def solve_leg(stc, cfg, n, nz, N, levels, max_admm):
     """stc_solve from scratch on the bench workload (fp32 policy)."""
     # eps_admm = 0 switches Alg. 3's density test off: the solve runs to the KKT tolerance or the cap
-    prm = stc.default_params(N_CELLS, N_CELLS, N_STEPS, precision=0, r=1e-3, K=1.0, metric_levels=6,
-                             eps_admm=0.0)
+    prm = stc.default_params(n, n, N, precision=0, r=1e-3, K=1.0, metric_levels=levels, eps_admm=0.0, nz=nz)
     with stc.Problem(prm, cfg["rho0"]) as G:
-        G.set_keyframes({N_STEPS: (star, 1.0)})
+        G.set_keyframes(cfg["keyframes"])
         t0 = time.perf_counter()
         rep = G.solve(tol=1e-4, max_admm=max_admm)
         wall = time.perf_counter() - t0
@@ -358,6 +382,8 @@ def main():
     ap.add_argument("--solve-max-admm", type=int, default=100)
     ap.add_argument("--serve", type=int, default=24, help="serving requests to replay (0: skip)")
     ap.add_argument("--serve-max-admm", type=int, default=50)
+    ap.add_argument("--workload", default="letters", choices=["letters", "3d"],
+                    help="letters: the 2D 128^2 x 40 workload (default); 3d: 64^3 x 60")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

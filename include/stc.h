@@ -4,7 +4,7 @@
  * Multigrid", arXiv 1608.01102).
  *
  * The library solves the control problem of Eq. opt: find forces u_0..u_{N-1}
- * on a 2D staggered grid so that the density rho_i advected by the implicit
+ * on a 2D or 3D staggered grid so that the density rho_i advected by the implicit
  * Navier-Stokes velocity v_i (Eq. NSA, NSB, Conv) matches keyframes rho*_i,
  * with force regularisation r.  It runs the paper's ADMM loop (Alg. 3): the
  * advection-optimisation fixed point (Alg. 1) and the Navier-Stokes
@@ -17,6 +17,8 @@
  *    Face fields are all x-faces [ny][nx+1] then all y-faces [ny+1][nx], i
  *    fastest; wall faces are stored and are zero.  A time-dependent field is
  *    a contiguous sequence of such slabs (v: N+1 slabs, u: N slabs, ...).
+ *    A 3D grid (stc_params.nz >= 2) adds a third axis: cells [nz][ny][nx],
+ *    faces x [nz][ny][nx+1], y [nz][ny+1][nx], z [nz+1][ny][nx].
  *  - Host arrays are double precision and owned by the caller; the library
  *    copies every input and never keeps a host pointer.  A length argument
  *    that does not match the field returns STC_ERR_INVALID_ARG and writes
@@ -95,6 +97,12 @@ typedef struct {
                            level whose N is even hands the next one N/2 steps of 2 dt
                            (point fields: full weighting / linear interpolation in time,
                            interval fields: pair means / piecewise constant) */
+  int nz;               /* 0 (default): the 2D grid nx x ny.  >= 2: the 3D grid nx x ny x nz
+                           (Sec. 3.1 with a third axis; h = 1/nx).  3D layouts: cells
+                           [nz][ny][nx]; faces = x-faces [nz][ny][nx+1], then y-faces
+                           [nz][ny+1][nx], then z-faces [nz+1][ny][nx]; the hierarchy
+                           halves all three axes; SCGS blocks are 7x7 (6 faces + pressure)
+                           with 8 parity colours.  1 is invalid. */
 } stc_params;
 
 typedef struct {
@@ -198,6 +206,8 @@ stc_status stc_get_field(const stc_problem* p, int field, int level, double* out
 stc_status stc_set_field(stc_problem* p, int field, int level, const double* in, size_t len);
 /* Number of levels, and the cells per axis of one level. */
 stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx, int* ny);
+/* Cells per axis of one level, nz = 0 on a 2D grid.  Outputs may be NULL. */
+stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int* nz);
 /* Timesteps N_l and timestep dt_l of level `level` (they differ from the
  * finest level's only with stc_params.time_coarsen).  Either output may be NULL. */
 stc_status stc_level_steps(const stc_problem* p, int level, int* num_steps, double* dt);

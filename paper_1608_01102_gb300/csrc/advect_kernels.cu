@@ -313,7 +313,6 @@ __device__ __forceinline__ T block_max(T v, T* red) {
 
 // dt / k for k = 1..kmax, formed once per launch in fp64 and rounded to T
 // (the per-term quotient would otherwise be an fp64 division in every thread)
-constexpr int kTaylorKmaxLimit = 256;
 template <class T>
 __device__ __forceinline__ void fill_dt_over_k(const Geom& g, int kmax, T* tab) {
   for (int k = (int)threadIdx.x + 1; k <= kmax; k += blockDim.x) tab[k] = T(g.dt / k);
@@ -670,6 +669,7 @@ __global__ void scale_kernel(const Tc* __restrict__ in, double* out, double c, i
 template <class T>
 void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
                    double* out, double* tmp0, double* tmp1, cudaStream_t st) {
+  if (g.dim == 3) return launch_metric3<T>(g, rho_s, star, c, levels, sigma0, out, tmp0, tmp1, st);
   const int C = g.C;
   const int tpb = 256;
   const unsigned nb = (unsigned)((C + tpb - 1) / tpb);
@@ -876,6 +876,10 @@ extern "C" stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, d
   g.Fx = ny * (nx + 1);
   g.F = g.Fx + (ny + 1) * nx;
   g.C = nx * ny;
+  g.dim = 2;
+  g.nz = 1;
+  g.Fy = (ny + 1) * nx;
+  g.Fxy = g.F;
   g.h = 1.0 / nx;
   g.ih = (double)nx;
   g.dt = dt;

@@ -1,0 +1,1121 @@
+// NSO residual, SCGS smoother and transfers on the 3D grid (Sec. 4.2-4.3 with
+// a third axis).  Same rows, block structure and transfers as the 2D kernels
+// of nso_kernels.cu; a cell has 6 faces, so a time block holds 7 unknowns and
+// the cells are 8-coloured by the parities of (i, j, k).
+#include <mutex>
+#include <type_traits>
+
+#include "grid3d.cuh"
+#include "stc_kernels.h"
+
+namespace stc {
+namespace {
+
+using namespace g3;
+
+// ---------------------------------------------------------------------------
+// rows of f (Eq. KKTAO) at an interior face (axis, k, j, i), flat index e
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T row1(const Geom& g, const CState<T>& x, const T* __restrict__ z, int t, int e, int axis,
+                                  int k, int j, int i) {
+  const T* vt = x.v + (size_t)t * g.F;
+  const T* um = x.u + (size_t)(t - 1) * g.F;
+  const T* pb = x.pbar + (size_t)t * g.C;
+  T val = ld(um + e) * pick<T>(g.idt, g.idtf);
+  if (g.self_adv) val += jtu(g, vt, um, axis, k, j, i);
+  val += grad(g, pb, axis, k, j, i);
+  if (t < g.N) {
+    const T* ut = x.u + (size_t)t * g.F;
+    val += pick<T>(g.a, g.af) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * pick<T>(g.idt, g.idtf);
+  }
+  return val;
+}
+
+template <class T>
+__device__ __forceinline__ T row3(const Geom& g, const CState<T>& x, int t, int e, int axis, int k, int j, int i) {
+  const T* vn = x.v + (size_t)(t + 1) * g.F;
+  const T* vt = x.v + (size_t)t * g.F;
+  T val = (ld(vn + e) - ld(vt + e)) * pick<T>(g.idt, g.idtf) - ld(x.u + (size_t)t * g.F + e);
+  if (g.self_adv) val += adv(g, vn, axis, k, j, i);
+  val += grad(g, x.p + (size_t)t * g.C, axis, k, j, i);
+  return val;
+}
+
+__device__ __forceinline__ void block_sumsq(double w, double* sq) {
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    w = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) atomicAdd(sq, w);
+  }
+}
+
+// out = sf * f(x) + sr * res; thread x: face e (< F) and cell e (< C); blockIdx.y: t
+template <class T>
+__global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res, State<T> out,
+                                     T sf, T sr, double* sq, const double* only_if_undone) {
+  pdl_wait();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (t > g.N) return;
+  if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
+  T acc = T(0);
+  if (e < g.F) {
+    int k, j, i;
+    const int axis = face_coords(g, e, k, j, i);
+    const bool in = interior(g, axis, k, j, i);
+    if (t >= 1) {
+      T val = T(0);
+      if (in) {
+        val = row1(g, x, z, t, e, axis, k, j, i) * sf;
+        if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
+      }
+      out.v[(size_t)t * g.F + e] = val;
+      acc += val * val;
+    } else {
+      out.v[e] = T(0);
+    }
+    if (t < g.N) {
+      T val = T(0);
+      if (in) {
+        val = row3(g, x, t, e, axis, k, j, i) * sf;
+        if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
+      }
+      out.u[(size_t)t * g.F + e] = val;
+      acc += val * val;
+    }
+  }
+  if (e < g.C) {
+    const int i = e % g.nx, r = e / g.nx, j = r % g.ny, k = r / g.ny;
+    if (t >= 1) {
+      T val = -divergence(g, x.v + (size_t)t * g.F, k, j, i) * sf;
+      if (res.pbar) val += sr * ld(res.pbar + (size_t)t * g.C + e);
+      out.pbar[(size_t)t * g.C + e] = val;
+      acc += val * val;
+    } else {
+      out.pbar[e] = T(0);
+    }
+    if (t < g.N) {
+      T val = -divergence(g, x.u + (size_t)t * g.F, k, j, i) * sf;
+      if (res.p) val += sr * ld(res.p + (size_t)t * g.C + e);
+      out.p[(size_t)t * g.C + e] = val;
+      acc += val * val;
+    }
+  }
+  if (sq) block_sumsq((double)acc, sq);
+}
+
+// f - res at what one colour's SCGS reads: the faces of its cells (x-faces of
+// rows j = py, k = pz (mod 2); y-faces of i = px, k = pz; z-faces of i = px,
+// j = py) and its cells.  Thread x: index over those; blockIdx.y: t.
+template <class T>
+__global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res,
+                                            State<T> out, int px, int py, int pz, const double* only_if_undone) {
+  pdl_wait();
+  const int t = blockIdx.y;
+  if (t > g.N) return;
+  if (only_if_undone && only_if_undone[1] <= only_if_undone[0]) return;
+  const int ncx = (g.nx - px + 1) / 2, ncy = (g.ny - py + 1) / 2, ncz = (g.nz - pz + 1) / 2;
+  const int nxf = ncz * ncy * (g.nx + 1), nyf = ncz * (g.ny + 1) * ncx, nzf = (g.nz + 1) * ncy * ncx;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nxf + nyf + nzf) {
+    int axis, k, j, i;
+    if (e < nxf) {
+      axis = 0;
+      i = e % (g.nx + 1);
+      const int r = e / (g.nx + 1);
+      j = py + 2 * (r % ncy);
+      k = pz + 2 * (r / ncy);
+    } else if (e < nxf + nyf) {
+      axis = 1;
+      const int q = e - nxf;
+      i = px + 2 * (q % ncx);
+      const int r = q / ncx;
+      j = r % (g.ny + 1);
+      k = pz + 2 * (r / (g.ny + 1));
+    } else {
+      axis = 2;
+      const int q = e - nxf - nyf;
+      i = px + 2 * (q % ncx);
+      const int r = q / ncx;
+      j = py + 2 * (r % ncy);
+      k = r / ncy;
+    }
+    const int f = axis == 0 ? xf(g, k, j, i) : (axis == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
+    const bool in = interior(g, axis, k, j, i);
+    if (t >= 1) {
+      T val = T(0);
+      if (in) {
+        val = row1(g, x, z, t, f, axis, k, j, i);
+        if (res.v) val -= ld(res.v + (size_t)t * g.F + f);
+      }
+      out.v[(size_t)t * g.F + f] = val;
+    }
+    if (t < g.N) {
+      T val = T(0);
+      if (in) {
+        val = row3(g, x, t, f, axis, k, j, i);
+        if (res.u) val -= ld(res.u + (size_t)t * g.F + f);
+      }
+      out.u[(size_t)t * g.F + f] = val;
+    }
+    return;
+  }
+  e -= nxf + nyf + nzf;
+  if (e < ncx * ncy * ncz) {
+    const int i = px + 2 * (e % ncx), r = e / ncx, j = py + 2 * (r % ncy), k = pz + 2 * (r / ncy);
+    const int c = cid(g, k, j, i);
+    if (t >= 1) {
+      T val = -divergence(g, x.v + (size_t)t * g.F, k, j, i);
+      if (res.pbar) val -= ld(res.pbar + (size_t)t * g.C + c);
+      out.pbar[(size_t)t * g.C + c] = val;
+    }
+    if (t < g.N) {
+      T val = -divergence(g, x.u + (size_t)t * g.F, k, j, i);
+      if (res.p) val -= ld(res.p + (size_t)t * g.C + c);
+      out.p[(size_t)t * g.C + c] = val;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SCGS on the 3D grid.  Local faces a = 0..5: (x-, x+, y-, y+, z-, z+) of the
+// cell, axis a / 2, side a % 2.  Block structure and phases as in the 2D
+// kernel (nso_kernels.cu): all u blocks eliminated in closed form, cyclic
+// reduction over the N v blocks (one warp per cell), u blocks recovered.
+// ---------------------------------------------------------------------------
+constexpr int NF = 6;                 // faces per cell
+constexpr int NB = NF + 1;            // unknowns per time block
+constexpr int NSYM = NF * (NF + 1) / 2;
+constexpr int NRHS = 2 * NF + 1;      // saddle solves in the reduction: two couplings + rhs
+enum : int {
+  C3_A = 0,                       // symmetric face block (NSYM)
+  C3_R = C3_A + NSYM,             // right-hand side (NB)
+  C3_C = C3_R + NB,               // coupling to the next block (NF x NF)
+  C3_ZL = C3_C + NF * NF,         // solved left coupling (NF x NF) + its multipliers (NF)
+  C3_ZR = C3_ZL + NF * NF + NF,   // solved right coupling + multipliers
+  C3_Z = C3_ZR + NF * NF + NF,    // solved right-hand side (NB)
+  kCr3Stride = C3_Z + NB          // 155: odd, so a warp's lanes hit distinct banks
+};
+static_assert(kCr3Stride % 2 == 1, "record stride must be odd");
+
+__host__ __device__ inline size_t scgs3_cell_floats(int N) { return (size_t)(NF * NF + NB + kCr3Stride) * N; }
+
+template <class S>
+struct CellG3 {
+  S act[NF], g[NF], gh[NF], ig2;
+  __device__ void init(const Geom& geo, int i, int j, int k) {
+    act[0] = S(i > 0);
+    act[1] = S(i < geo.nx - 1);
+    act[2] = S(j > 0);
+    act[3] = S(j < geo.ny - 1);
+    act[4] = S(k > 0);
+    act[5] = S(k < geo.nz - 1);
+    S g2 = S(0);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+      g[a] = ((a & 1) ? -act[a] : act[a]) * S(geo.ih);
+      g2 += g[a] * g[a];
+    }
+    ig2 = S(1) / g2;
+#pragma unroll
+    for (int a = 0; a < NF; ++a) gh[a] = g[a] * ig2;
+  }
+  __device__ __forceinline__ void proj(const S w[NF], S out[NF]) const {
+    S d = S(0);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) d += g[a] * w[a];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) out[a] = act[a] * w[a] - gh[a] * d;
+  }
+};
+
+// d Adv_f / d v_g for f, g among the 6 faces of cell (k, j, i) at field v.
+// Face f = (A, s) carries two terms: +O1 V1 with omega component C = A+1 and
+// face mean of component B = A+2, and -O2 V2 with C = A+2, B = A+1 (cyclic).
+// The C-edges on f lie at its two ends along B, at the corners with the
+// cell's faces (B, d); such an edge is interior iff neither face plane is a
+// wall.  Its curl stencil holds two of the cell's faces: (A, s) with weight
+// c(C, A, d) and (B, d) with weight c(C, B, s), where
+//   c(C, X, side) = (X == C+2 ? +1 : -1) * (side == 0 ? +1 : -1) / h.
+// The face mean of component B holds the cell's two B-faces with weight 1/4.
+template <class T, class R>
+__device__ void local_adv_jac3(const Geom& g, const T* v, int k, int j, int i, const R act[NF], R J[NF][NF]) {
+  const R ih = pick<R>(g.ih, g.ihf);
+#pragma unroll
+  for (int r = 0; r < NF; ++r)
+#pragma unroll
+    for (int c = 0; c < NF; ++c) J[r][c] = R(0);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int A = f >> 1, s = f & 1;
+    const int fk = k + (A == 2 ? s : 0), fj = j + (A == 1 ? s : 0), fi = i + (A == 0 ? s : 0);
+    if (!interior(g, A, fk, fj, fi)) continue;
+    const Terms<R> tm = terms<T, R>(g, v, A, fk, fj, fi);
+#pragma unroll
+    for (int term = 0; term < 2; ++term) {
+      const int C = term == 0 ? (A + 1) % 3 : (A + 2) % 3;
+      const int B = term == 0 ? (A + 2) % 3 : (A + 1) % 3;
+      const R sgn = term == 0 ? R(1) : R(-1);
+      const R O = term == 0 ? tm.o1 : tm.o2;
+      const R V = term == 0 ? tm.v1 : tm.v2;
+      const R sA = (A == (C + 2) % 3) ? R(1) : R(-1);
+      const R sB = (B == (C + 2) % 3) ? R(1) : R(-1);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const R ae = act[f] * act[2 * B + d];
+        const R dside = d == 0 ? R(1) : R(-1);
+        const R sside = s == 0 ? R(1) : R(-1);
+        // d O / d v_(A,s) and d O / d v_(B,d)
+        J[f][f] += sgn * V * R(0.5) * ae * sA * dside * ih;
+        J[f][2 * B + d] += sgn * (V * R(0.5) * ae * sB * sside * ih + O * R(0.25));
+      }
+    }
+  }
+}
+
+// Solve [[A, g], [g^T, 0]] [X; y] = [B; q] for NC right-hand sides (A the
+// symmetric definite NF x NF face block): LDL^T, the NC columns and g, then
+// the Schur step on g.  On return B holds X and Y holds y.
+template <class S, int NC>
+__device__ __forceinline__ void saddle_solve6(S A[NF][NF], const S gv[NF], S B[NF][NC], const S q[NC], S Y[NC]) {
+  S dinv[NF];
+#pragma unroll
+  for (int kk = 0; kk < NF; ++kk) {
+    S d = A[kk][kk];
+#pragma unroll
+    for (int s = 0; s < kk; ++s) d -= A[kk][s] * A[kk][s] * A[s][s];
+    A[kk][kk] = d;
+    const S id = S(1) / d;
+    dinv[kk] = id;
+#pragma unroll
+    for (int r = kk + 1; r < NF; ++r) {
+      S l = A[r][kk];
+#pragma unroll
+      for (int s = 0; s < kk; ++s) l -= A[r][s] * A[kk][s] * A[s][s];
+      A[r][kk] = l * id;
+    }
+  }
+  S X[NF][NC + 1];
+#pragma unroll
+  for (int r = 0; r < NF; ++r) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) X[r][c] = B[r][c];
+    X[r][NC] = gv[r];
+  }
+#pragma unroll
+  for (int c = 0; c <= NC; ++c) {
+#pragma unroll
+    for (int r = 0; r < NF; ++r) {
+      S s = X[r][c];
+#pragma unroll
+      for (int kk = 0; kk < r; ++kk) s -= A[r][kk] * X[kk][c];
+      X[r][c] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < NF; ++r) X[r][c] *= dinv[r];
+#pragma unroll
+    for (int r = NF - 1; r >= 0; --r) {
+      S s = X[r][c];
+#pragma unroll
+      for (int kk = r + 1; kk < NF; ++kk) s -= A[kk][r] * X[kk][c];
+      X[r][c] = s;
+    }
+  }
+  S sgg = S(0);
+#pragma unroll
+  for (int r = 0; r < NF; ++r) sgg += gv[r] * X[r][NC];
+  const S isgg = S(1) / sgg;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    S sgb = S(0);
+#pragma unroll
+    for (int r = 0; r < NF; ++r) sgb += gv[r] * X[r][c];
+    const S y = (sgb - q[c]) * isgg;
+    Y[c] = y;
+#pragma unroll
+    for (int r = 0; r < NF; ++r) B[r][c] = X[r][c] - X[r][NC] * y;
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void load_sym6(const S* v, S A[NF][NF]) {
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int b = a; b < NF; ++b) {
+      A[a][b] = v[e];
+      A[b][a] = v[e];
+      ++e;
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void store_sym6(S* v, const S A[NF][NF]) {
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int b = a; b < NF; ++b) {
+      v[e] = S(0.5) * (A[a][b] + A[b][a]);
+      ++e;
+    }
+}
+
+// shift A by gamma g g^T (gamma from the trace; x unchanged, the multiplier
+// shifted by gamma q) and symmetrise; returns gamma
+template <class S>
+__device__ __forceinline__ S shift_sym6(S A[NF][NF], const CellG3<S>& cg) {
+  S tr = S(0);
+#pragma unroll
+  for (int a = 0; a < NF; ++a) tr += A[a][a];
+  const S gam = tr * cg.ig2 / S(NF);
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int b = a; b < NF; ++b) {
+      const S m = S(0.5) * (A[a][b] + A[b][a]) + gam * cg.g[a] * cg.g[b];
+      A[a][b] = m;
+      A[b][a] = m;
+    }
+  return gam;
+}
+
+struct Cell3 {
+  int i, j, k;
+};
+
+__device__ __forceinline__ Cell3 colour_cell(const Geom& g, int colour, int q) {
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+  const int ncx = (g.nx - px + 1) / 2, ncy = (g.ny - py + 1) / 2;
+  Cell3 c;
+  c.i = px + 2 * (q % ncx);
+  const int r = q / ncx;
+  c.j = py + 2 * (r % ncy);
+  c.k = pz + 2 * (r / ncy);
+  return c;
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(256)
+scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int cpb, const double* __restrict__ lm_dev) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = g.N;
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
+  const int q0 = blockIdx.x * cpb;
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][36][cpb]
+  S* Bu = Us + (size_t)N * NF * NF * cpb;            // b_u -> y_t [N][7][cpb]
+  S* Vb = Bu + (size_t)N * NB * cpb;                 // v blocks   [cpb][N][kCr3Stride]
+  const S idt = pick<S>(g.idt, g.idtf);
+
+  // ---- phase A: couplings and right-hand sides ----------------------------
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const Cell3 cl = colour_cell(g, colour, q);
+    const int fidx[NF] = {xf(g, cl.k, cl.j, cl.i), xf(g, cl.k, cl.j, cl.i + 1), yf(g, cl.k, cl.j, cl.i),
+                          yf(g, cl.k, cl.j + 1, cl.i), zf(g, cl.k, cl.j, cl.i), zf(g, cl.k + 1, cl.j, cl.i)};
+    S act[NF] = {S(cl.i > 0), S(cl.i < g.nx - 1), S(cl.j > 0), S(cl.j < g.ny - 1), S(cl.k > 0), S(cl.k < g.nz - 1)};
+    const int cc = cid(g, cl.k, cl.j, cl.i);
+    S Jl[NF][NF];
+    local_adv_jac3<T, S>(g, x.v + (size_t)(t + 1) * g.F, cl.k, cl.j, cl.i, act, Jl);
+    S* U = Us + (size_t)t * NF * NF * cpb + c;
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < NF; ++b2)
+        U[(a2 * NF + b2) * cpb] = ((a2 == b2 ? idt : S(0)) + S(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2];
+    S* Ru = Bu + (size_t)t * NB * cpb + c;
+    S* Rv = Vb + ((size_t)c * N + t) * kCr3Stride + C3_R;
+    const T* ru = r.u + (size_t)t * g.F;
+    const T* rv = r.v + (size_t)(t + 1) * g.F;
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) {
+      Ru[a2 * cpb] = S(-ld(ru + fidx[a2])) * act[a2];
+      Rv[a2] = S(-ld(rv + fidx[a2])) * act[a2];
+    }
+    Ru[NF * cpb] = S(-ld(r.p + (size_t)t * g.C + cc));
+    Rv[NF] = S(-ld(r.pbar + (size_t)(t + 1) * g.C + cc));
+  }
+  __syncthreads();
+
+  // ---- phase A2: eliminate the u blocks ------------------------------------
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const Cell3 cl = colour_cell(g, colour, q);
+    CellG3<S> cg_;
+    cg_.init(g, cl.i, cl.j, cl.k);
+    S* Ru = Bu + (size_t)t * NB * cpb + c;
+    S bf[NF], pb[NF];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) bf[a2] = Ru[a2 * cpb];
+    const S bp = Ru[NF * cpb];
+    cg_.proj(bf, pb);
+    S gb = S(0);
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) gb += cg_.gh[a2] * bf[a2];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) Ru[a2 * cpb] = -pb[a2] + cg_.gh[a2] * bp;
+    Ru[NF * cpb] = gb + bp * cg_.ig2;
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const Cell3 cl = colour_cell(g, colour, q);
+    CellG3<S> cg_;
+    cg_.init(g, cl.i, cl.j, cl.k);
+    const int tv = t + 1;
+    S* V = Vb + ((size_t)c * N + t) * kCr3Stride;
+    const S* U = Us + (size_t)t * NF * NF * cpb + c;
+    S Um[NF][NF];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 < NF; ++b2) Um[a2][b2] = U[(a2 * NF + b2) * cpb];
+    S PU[NF][NF];
+#pragma unroll
+    for (int b2 = 0; b2 < NF; ++b2) {
+      S w[NF], pw[NF];
+#pragma unroll
+      for (int a2 = 0; a2 < NF; ++a2) w[a2] = Um[a2][b2];
+      cg_.proj(w, pw);
+#pragma unroll
+      for (int a2 = 0; a2 < NF; ++a2) PU[a2][b2] = pw[a2];
+    }
+    const S diag = (tv < N ? pick<S>(g.a, g.af) : S(0)) + lm;
+    int e = 0;
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2)
+#pragma unroll
+      for (int b2 = a2; b2 < NF; ++b2) {
+        S v = S(0);
+#pragma unroll
+        for (int c2 = 0; c2 < NF; ++c2) v += Um[c2][a2] * PU[c2][b2];
+        if (tv < N) v += ((a2 == b2 ? cg_.act[a2] : S(0)) - cg_.gh[a2] * cg_.g[b2]) * idt * idt;
+        if (a2 == b2) v += cg_.act[a2] > S(0) ? diag : S(1);
+        V[C3_A + e] = v;
+        ++e;
+      }
+    const S* y0 = Bu + (size_t)t * NB * cpb + c;
+    S yv[NF];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) yv[a2] = y0[a2 * cpb];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) {
+      S v = V[C3_R + a2];
+#pragma unroll
+      for (int c2 = 0; c2 < NF; ++c2) v -= Um[c2][a2] * yv[c2];
+      if (tv < N) v += idt * cg_.act[a2] * Bu[((size_t)tv * NB + a2) * cpb + c];
+      V[C3_R + a2] = v;
+    }
+    if (tv < N) {
+      const S* U1 = Us + (size_t)tv * NF * NF * cpb + c;
+#pragma unroll
+      for (int b2 = 0; b2 < NF; ++b2) {
+        S w[NF], pw[NF];
+#pragma unroll
+        for (int a2 = 0; a2 < NF; ++a2) w[a2] = U1[(a2 * NF + b2) * cpb];
+        cg_.proj(w, pw);
+#pragma unroll
+        for (int a2 = 0; a2 < NF; ++a2) V[C3_C + a2 * NF + b2] = -idt * pw[a2];
+      }
+    } else {
+#pragma unroll
+      for (int e2 = 0; e2 < NF * NF; ++e2) V[C3_C + e2] = S(0);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: cyclic reduction over the v blocks, one warp per cell -------
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = q0 + warp;
+    if (warp < cpb && q < ncell) {
+      const Cell3 cl = colour_cell(g, colour, q);
+      CellG3<S> cg_;
+      cg_.init(g, cl.i, cl.j, cl.k);
+      S* V = Vb + (size_t)warp * N * kCr3Stride;
+      int top = 0;
+      for (int s2 = 1; s2 < N; s2 <<= 1) {
+        top = s2;
+        for (int m = lane;; m += 32) {
+          const int o = s2 * (2 * m + 1);
+          if (o >= N) break;
+          const bool hasb = o + s2 < N;
+          S* Vo = V + (size_t)o * kCr3Stride;
+          const S* Va = V + (size_t)(o - s2) * kCr3Stride;
+          S A[NF][NF];
+          load_sym6(Vo + C3_A, A);
+          S B[NF][NRHS];
+          S qv[NRHS];
+#pragma unroll
+          for (int r2 = 0; r2 < NF; ++r2) {
+#pragma unroll
+            for (int c2 = 0; c2 < NF; ++c2) {
+              B[r2][c2] = Va[C3_C + c2 * NF + r2];
+              B[r2][NF + c2] = hasb ? Vo[C3_C + r2 * NF + c2] : S(0);
+            }
+            B[r2][2 * NF] = Vo[C3_R + r2];
+          }
+#pragma unroll
+          for (int c2 = 0; c2 < 2 * NF; ++c2) qv[c2] = S(0);
+          qv[2 * NF] = Vo[C3_R + NF];
+          const S gam = shift_sym6(A, cg_);
+          S Y[NRHS];
+          saddle_solve6<S, NRHS>(A, cg_.g, B, qv, Y);
+          Y[2 * NF] += gam * qv[2 * NF];
+#pragma unroll
+          for (int c2 = 0; c2 < NF; ++c2) {
+#pragma unroll
+            for (int r2 = 0; r2 < NF; ++r2) {
+              Vo[C3_ZL + r2 * NF + c2] = B[r2][c2];
+              Vo[C3_ZR + r2 * NF + c2] = B[r2][NF + c2];
+            }
+            Vo[C3_ZL + NF * NF + c2] = Y[c2];
+            Vo[C3_ZR + NF * NF + c2] = Y[NF + c2];
+          }
+#pragma unroll
+          for (int r2 = 0; r2 < NF; ++r2) Vo[C3_Z + r2] = B[r2][2 * NF];
+          Vo[C3_Z + NF] = Y[2 * NF];
+        }
+        __syncwarp();
+        for (int m = lane;; m += 32) {
+          const int e = 2 * s2 * m;
+          if (e >= N) break;
+          S* Ve = V + (size_t)e * kCr3Stride;
+          S A[NF][NF];
+          load_sym6(Ve + C3_A, A);
+          S rf[NF], Ce[NF][NF], Cn[NF][NF];
+#pragma unroll
+          for (int r2 = 0; r2 < NF; ++r2) {
+            rf[r2] = Ve[C3_R + r2];
+#pragma unroll
+            for (int c2 = 0; c2 < NF; ++c2) {
+              Ce[r2][c2] = Ve[C3_C + r2 * NF + c2];
+              Cn[r2][c2] = S(0);
+            }
+          }
+          const int o2 = e + s2;
+          if (o2 < N) {
+            const S* V2 = V + (size_t)o2 * kCr3Stride;
+            const bool hasb2 = o2 + s2 < N;
+#pragma unroll
+            for (int r2 = 0; r2 < NF; ++r2) {
+#pragma unroll
+              for (int c2 = 0; c2 < NF; ++c2) {
+                S aL = S(0), aR = S(0);
+#pragma unroll
+                for (int k2 = 0; k2 < NF; ++k2) {
+                  aL += Ce[r2][k2] * V2[C3_ZL + k2 * NF + c2];
+                  aR += Ce[r2][k2] * V2[C3_ZR + k2 * NF + c2];
+                }
+                A[r2][c2] -= aL;
+                Cn[r2][c2] = hasb2 ? -aR : S(0);
+              }
+              S az = S(0);
+#pragma unroll
+              for (int k2 = 0; k2 < NF; ++k2) az += Ce[r2][k2] * V2[C3_Z + k2];
+              rf[r2] -= az;
+            }
+          }
+          const int o1 = e - s2;
+          if (o1 >= 0) {
+            const S* V1 = V + (size_t)o1 * kCr3Stride;
+#pragma unroll
+            for (int r2 = 0; r2 < NF; ++r2) {
+#pragma unroll
+              for (int c2 = 0; c2 < NF; ++c2) {
+                S aR = S(0);
+#pragma unroll
+                for (int k2 = 0; k2 < NF; ++k2) aR += V1[C3_C + k2 * NF + r2] * V1[C3_ZR + k2 * NF + c2];
+                A[r2][c2] -= aR;
+              }
+              S az = S(0);
+#pragma unroll
+              for (int k2 = 0; k2 < NF; ++k2) az += V1[C3_C + k2 * NF + r2] * V1[C3_Z + k2];
+              rf[r2] -= az;
+            }
+          }
+          store_sym6(Ve + C3_A, A);
+#pragma unroll
+          for (int r2 = 0; r2 < NF; ++r2) {
+            Ve[C3_R + r2] = rf[r2];
+#pragma unroll
+            for (int c2 = 0; c2 < NF; ++c2) Ve[C3_C + r2 * NF + c2] = Cn[r2][c2];
+          }
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        S A[NF][NF];
+        load_sym6(V + C3_A, A);
+        S B[NF][1];
+        S qv[1] = {V[C3_R + NF]};
+#pragma unroll
+        for (int r2 = 0; r2 < NF; ++r2) B[r2][0] = V[C3_R + r2];
+        const S gam = shift_sym6(A, cg_);
+        S Y[1];
+        saddle_solve6<S, 1>(A, cg_.g, B, qv, Y);
+#pragma unroll
+        for (int r2 = 0; r2 < NF; ++r2) V[C3_Z + r2] = B[r2][0];
+        V[C3_Z + NF] = Y[0] + gam * qv[0];
+      }
+      __syncwarp();
+      for (int s2 = top; s2 >= 1; s2 >>= 1) {
+        for (int m = lane;; m += 32) {
+          const int o = s2 * (2 * m + 1);
+          if (o >= N) break;
+          S* Vo = V + (size_t)o * kCr3Stride;
+          const S* Va = V + (size_t)(o - s2) * kCr3Stride;
+          const bool hasb = o + s2 < N;
+          S xa[NF], xb[NF];
+#pragma unroll
+          for (int k2 = 0; k2 < NF; ++k2) {
+            xa[k2] = Va[C3_Z + k2];
+            xb[k2] = hasb ? V[(size_t)(o + s2) * kCr3Stride + C3_Z + k2] : S(0);
+          }
+#pragma unroll
+          for (int r2 = 0; r2 < NB; ++r2) {
+            S v = Vo[C3_Z + r2];
+#pragma unroll
+            for (int k2 = 0; k2 < NF; ++k2) v -= Vo[C3_ZL + r2 * NF + k2] * xa[k2] + Vo[C3_ZR + r2 * NF + k2] * xb[k2];
+            Vo[C3_Z + r2] = v;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- phase C: u blocks from the v solution, x += omega * delta -----------
+  const T om = pick<T>(g.omega, g.omegaf);
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const Cell3 cl = colour_cell(g, colour, q);
+    const int fidx[NF] = {xf(g, cl.k, cl.j, cl.i), xf(g, cl.k, cl.j, cl.i + 1), yf(g, cl.k, cl.j, cl.i),
+                          yf(g, cl.k, cl.j + 1, cl.i), zf(g, cl.k, cl.j, cl.i), zf(g, cl.k + 1, cl.j, cl.i)};
+    const bool actb[NF] = {cl.i > 0, cl.i < g.nx - 1, cl.j > 0, cl.j < g.ny - 1, cl.k > 0, cl.k < g.nz - 1};
+    const int cc = cid(g, cl.k, cl.j, cl.i);
+    T* fu = x.u + (size_t)t * g.F;
+    T* fv = x.v + (size_t)(t + 1) * g.F;
+    T* fp = x.p + (size_t)t * g.C + cc;
+    T* fpb = x.pbar + (size_t)(t + 1) * g.C + cc;
+    T old_u[NF], old_v[NF];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) {
+      old_u[a2] = actb[a2] ? fu[fidx[a2]] : T(0);
+      old_v[a2] = actb[a2] ? fv[fidx[a2]] : T(0);
+    }
+    const T old_p = *fp, old_pb = *fpb;
+    CellG3<S> cg_;
+    cg_.init(g, cl.i, cl.j, cl.k);
+    const S* U = Us + (size_t)t * NF * NF * cpb + c;
+    const S* xv1 = Vb + ((size_t)c * N + t) * kCr3Stride + C3_Z;
+    const S* xv0 = Vb + ((size_t)c * N + (t > 0 ? t - 1 : 0)) * kCr3Stride + C3_Z;
+    S w[NF];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) {
+      S v = S(0);
+#pragma unroll
+      for (int b2 = 0; b2 < NF; ++b2) v -= U[(a2 * NF + b2) * cpb] * xv1[b2];
+      if (t >= 1) v += idt * cg_.act[a2] * xv0[a2];
+      w[a2] = v;
+    }
+    S pw[NF];
+    cg_.proj(w, pw);
+    S gw = S(0);
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) gw += cg_.gh[a2] * w[a2];
+    const S* y = Bu + (size_t)t * NB * cpb + c;
+    S du[NB];
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
+    du[NF] = y[NF * cpb] + gw;
+#pragma unroll
+    for (int a2 = 0; a2 < NF; ++a2)
+      if (actb[a2]) {
+        fu[fidx[a2]] = old_u[a2] + om * T(du[a2]);
+        fv[fidx[a2]] = old_v[a2] + om * T(xv1[a2]);
+      }
+    *fp = old_p + om * T(du[NF]);
+    *fpb = old_pb + om * T(xv1[NF]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// transfers (Sec. 4.3 with a third axis): R = mean of the 8 children (cells) /
+// the 4 coincident fine faces (faces); P = trilinear, faces linear along the
+// normal and (3/4, 1/4) across, clamped at walls.  Time modes as the 2D
+// kernels (0 same slabs, 1 points, 2 intervals, 3 targets).
+// ---------------------------------------------------------------------------
+template <class Tc, class RS>
+__device__ __forceinline__ Tc in_time_r(RS rs, int tmode, int t, int nt) {
+  switch (tmode) {
+    case 0: return rs(t);
+    case 1:
+      if (t == 0 || t == nt - 1) return rs(2 * t);
+      return Tc(0.25) * rs(2 * t - 1) + Tc(0.5) * rs(2 * t) + Tc(0.25) * rs(2 * t + 1);
+    case 2: return Tc(0.5) * (rs(2 * t) + rs(2 * t + 1));
+    default:
+      if (t == 0) return rs(0);
+      return Tc(0.25) * rs(2 * t - 1) + Tc(0.5) * rs(2 * t) + Tc(0.25) * rs(2 * t + 1);
+  }
+}
+
+template <class Tf, class Tc>
+__global__ void restrict3_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, const Tf* __restrict__ sf,
+                                 const Tf* __restrict__ sc_cells, Tc* df, Tc* dc_cells, Tc* df2, Tc* dc2, int tmode) {
+  pdl_wait();
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nfaces = (size_t)nt_face * gc.F;
+  const size_t ncells = (size_t)nt_cell * gc.C;
+  if (e < nfaces) {
+    const int t = (int)(e / gc.F);
+    const int f = (int)(e - (size_t)t * gc.F);
+    int K, J, I;
+    const int axis = face_coords(gc, f, K, J, I);
+    auto rs = [&](int tf) -> Tc {
+      const Tf* s = sf + (size_t)tf * gf.F;
+      Tc acc = Tc(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          int idx;
+          if (axis == 0) idx = xf(gf, 2 * K + a, 2 * J + b, 2 * I);
+          else if (axis == 1) idx = yf(gf, 2 * K + a, 2 * J, 2 * I + b);
+          else idx = zf(gf, 2 * K, 2 * J + a, 2 * I + b);
+          acc += Tc(s[idx]);
+        }
+      return Tc(0.25) * acc;
+    };
+    const Tc val = in_time_r<Tc>(rs, tmode, t, nt_face);
+    df[e] = val;
+    if (df2) df2[e] = val;
+  } else if (e < nfaces + ncells) {
+    const size_t ec = e - nfaces;
+    const int t = (int)(ec / gc.C);
+    const int c = (int)(ec - (size_t)t * gc.C);
+    const int I = c % gc.nx, r = c / gc.nx, J = r % gc.ny, K = r / gc.ny;
+    auto rs = [&](int tf) -> Tc {
+      const Tf* s = sc_cells + (size_t)tf * gf.C;
+      Tc acc = Tc(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int d = 0; d < 2; ++d) acc += Tc(s[cid(gf, 2 * K + a, 2 * J + b, 2 * I + d)]);
+      return Tc(0.125) * acc;
+    };
+    const Tc val = in_time_r<Tc>(rs, tmode, t, nt_cell);
+    dc_cells[ec] = val;
+    if (dc2) dc2[ec] = val;
+  }
+}
+
+__device__ __forceinline__ void cell_interp3(int k, int nc, int& a, int& b) {
+  a = k >> 1;
+  b = (k & 1) ? a + 1 : a - 1;
+  b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
+}
+
+template <class Tf, class Tc>
+__global__ void prolong3_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, int t0_face, int t0_cell, Tf* ff,
+                                        Tf* fc, const Tc* __restrict__ cnf, const Tc* __restrict__ cof,
+                                        const Tc* __restrict__ cnc, const Tc* __restrict__ coc,
+                                        const double* undo_if_rose, int tmode) {
+  pdl_wait();
+  using W = typename std::conditional<(sizeof(Tf) == 8 || sizeof(Tc) == 8), double, float>::type;
+  W sgn = W(1);
+  if (undo_if_rose) {
+    if (undo_if_rose[1] <= undo_if_rose[0]) return;
+    sgn = W(-1);
+  }
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t nfaces = (size_t)nt_face * gf.F;
+  const size_t ncells = (size_t)nt_cell * gf.C;
+  auto in_time = [&](auto ps, int t) -> W {
+    if (tmode == 0) return ps(t);
+    if (tmode == 2) return ps(t >> 1);
+    if ((t & 1) == 0) return ps(t >> 1);
+    return W(0.5) * (ps(t >> 1) + ps((t >> 1) + 1));
+  };
+  if (e < nfaces) {
+    const int t = (int)(e / gf.F) + t0_face;
+    const int f = (int)(e - (size_t)(t - t0_face) * gf.F);
+    int k, j, i;
+    const int axis = face_coords(gf, f, k, j, i);
+    // per axis (k, j, i): two coarse indices and weights
+    int ca[3], cb[3];
+    W wa[3], wb[3];
+    const int fine[3] = {k, j, i};
+    const int nce[3] = {gc.nz, gc.ny, gc.nx};
+    const int normal = 2 - axis;   // array axis of the face normal (x -> i)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d == normal) {
+        ca[d] = fine[d] >> 1;
+        cb[d] = (fine[d] & 1) ? ca[d] + 1 : ca[d];
+        wb[d] = (fine[d] & 1) ? W(0.5) : W(0);
+        wa[d] = W(1) - wb[d];
+      } else {
+        cell_interp3(fine[d], nce[d], ca[d], cb[d]);
+        wa[d] = W(0.75);
+        wb[d] = W(0.25);
+      }
+    }
+    auto ps = [&](int tc) -> W {
+      const Tc* n = cnf + (size_t)tc * gc.F;
+      const Tc* o = cof + (size_t)tc * gc.F;
+      W val = W(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int K = a ? cb[0] : ca[0], J = b ? cb[1] : ca[1], I = c ? cb[2] : ca[2];
+            const W w = (a ? wb[0] : wa[0]) * (b ? wb[1] : wa[1]) * (c ? wb[2] : wa[2]);
+            if (w == W(0)) continue;
+            const int idx = axis == 0 ? xf(gc, K, J, I) : (axis == 1 ? yf(gc, K, J, I) : zf(gc, K, J, I));
+            val += w * (W(n[idx]) - W(o[idx]));
+          }
+      return val;
+    };
+    ff[(size_t)t * gf.F + f] += Tf(sgn * in_time(ps, t));
+  } else if (e < nfaces + ncells) {
+    const size_t ec = e - nfaces;
+    const int t = (int)(ec / gf.C) + t0_cell;
+    const int c = (int)(ec - (size_t)(t - t0_cell) * gf.C);
+    const int i = c % gf.nx, r = c / gf.nx, j = r % gf.ny, k = r / gf.ny;
+    int ka, kb, ja, jb, ia, ib;
+    cell_interp3(k, gc.nz, ka, kb);
+    cell_interp3(j, gc.ny, ja, jb);
+    cell_interp3(i, gc.nx, ia, ib);
+    auto ps = [&](int tc) -> W {
+      const Tc* n = cnc + (size_t)tc * gc.C;
+      const Tc* o = coc + (size_t)tc * gc.C;
+      W val = W(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int d = 0; d < 2; ++d) {
+            const int idx = cid(gc, a ? kb : ka, b ? jb : ja, d ? ib : ia);
+            const W w = (a ? W(0.25) : W(0.75)) * (b ? W(0.25) : W(0.75)) * (d ? W(0.25) : W(0.75));
+            val += w * (W(n[idx]) - W(o[idx]));
+          }
+      return val;
+    };
+    fc[(size_t)t * gf.C + c] += Tf(sgn * in_time(ps, t));
+  }
+}
+
+// u_raw_t = (v_{t+1} - v_t)/dt + Adv(v_{t+1}), t = 0..N-1   (Appendix A)
+template <class T>
+__global__ void kkt_force_rhs3_kernel(Geom g, const T* __restrict__ v, T* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (e >= g.F || t >= g.N) return;
+  const T* vn = v + (size_t)(t + 1) * g.F;
+  const T* vt = v + (size_t)t * g.F;
+  int k, j, i;
+  const int axis = face_coords(g, e, k, j, i);
+  T val = T(0);
+  if (interior(g, axis, k, j, i))
+    val = (vn[e] - vt[e]) * pick<T>(g.idt, g.idtf) + T(g.self_adv) * adv(g, vn, axis, k, j, i);
+  out[(size_t)t * g.F + e] = val;
+}
+
+// g_raw_t = r(u_{t-1}/dt + dAdv(v_t)^T u_{t-1} - u_t/dt [t<N]) + dens_t, t = 1..N
+template <class T>
+__global__ void kkt_grad_rhs3_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ u,
+                                     const T* __restrict__ dens, double r, T* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y + 1;
+  if (e >= g.F || t > g.N) return;
+  const T* vt = v + (size_t)t * g.F;
+  const T* um = u + (size_t)(t - 1) * g.F;
+  int k, j, i;
+  const int axis = face_coords(g, e, k, j, i);
+  T val = T(0);
+  if (interior(g, axis, k, j, i)) {
+    T s = um[e] * pick<T>(g.idt, g.idtf);
+    if (g.self_adv) s += jtu(g, vt, um, axis, k, j, i);
+    if (t < g.N) s -= u[(size_t)t * g.F + e] * pick<T>(g.idt, g.idtf);
+    val = T(r) * s + dens[(size_t)t * g.F + e];
+  }
+  out[(size_t)t * g.F + e] = val;
+}
+
+template <class... KArgs, class... Args>
+void launch_pdl3(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+inline unsigned blocks3(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers (called by the dimension-generic launchers when g.dim == 3)
+// ---------------------------------------------------------------------------
+template <class T>
+void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                          cudaStream_t st, double* sq, const double* only_if_undone) {
+  const int n = g.F > g.C ? g.F : g.C;
+  launch_pdl3(nso_residual3_kernel<T>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out, sf, sr,
+              sq, only_if_undone);
+}
+
+template <class T>
+void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                 cudaStream_t st, const double* only_if_undone) {
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+  const int ncx = (g.nx - px + 1) / 2, ncy = (g.ny - py + 1) / 2, ncz = (g.nz - pz + 1) / 2;
+  const int n = ncz * ncy * (g.nx + 1) + ncz * (g.ny + 1) * ncx + (g.nz + 1) * ncy * ncx + ncx * ncy * ncz;
+  launch_pdl3(nso_residual3_colour_kernel<T>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
+              px, py, pz, only_if_undone);
+}
+
+size_t scgs3_smem_bytes(int N, size_t tsize) { return scgs3_cell_floats(N) * tsize; }
+
+// cells per CTA: as many as fit the opt-in shared memory, at most 8 (one warp each)
+static int scgs3_cells_per_block(int N, size_t ssize) {
+  static std::once_flag once;
+  static int optin = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    optin -= 1024;   // the kernel's static shared memory
+  });
+  int cpb = (int)((size_t)optin / scgs3_smem_bytes(N, ssize));
+  return cpb > 8 ? 8 : cpb;
+}
+
+template <class T, class S>
+static void launch_scgs3_ts(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev,
+                            cudaStream_t st) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncGetAttributes(&fa, (const void*)scgs3_colour_kernel<T, S>);
+    cudaFuncSetAttribute((const void*)scgs3_colour_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         optin - (int)fa.sharedSizeBytes);
+  });
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+  const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
+  if (ncell == 0) return;
+  const int cpb = scgs3_cells_per_block(g.N, sizeof(S));
+  if (cpb < 1) return;   // refused at problem creation (scgs_smem_bytes)
+  const size_t smem = (size_t)cpb * scgs3_smem_bytes(g.N, sizeof(S));
+  const int threads = 32 * cpb < 64 ? 64 : 32 * cpb;
+  launch_pdl3(scgs3_colour_kernel<T, S>, dim3((ncell + cpb - 1) / cpb), dim3(threads), smem, st, g, x, r, colour,
+              ncell, cpb, lm_dev);
+}
+
+template <class T>
+void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+                         const double* lm_dev) {
+  if (solve_fp32) launch_scgs3_ts<T, float>(g, x, r, colour, lm_dev, st);
+  else launch_scgs3_ts<T, T>(g, x, r, colour, lm_dev, st);
+}
+
+template <class Tf, class Tc>
+void launch_restrict3(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st) {
+  const bool in_time = gc.N != gf.N;
+  const size_t nv = (size_t)(gc.N + 1) * gc.F + (size_t)(gc.N + 1) * gc.C;
+  launch_pdl3(restrict3_kernel<Tf, Tc>, dim3(blocks3(nv, 256)), dim3(256), 0, st, gf, gc, gc.N + 1, gc.N + 1, s.v,
+              s.pbar, d.v, d.pbar, d2.v, d2.pbar, in_time ? 1 : 0);
+  const size_t nu = (size_t)gc.N * gc.F + (size_t)gc.N * gc.C;
+  launch_pdl3(restrict3_kernel<Tf, Tc>, dim3(blocks3(nu, 256)), dim3(256), 0, st, gf, gc, gc.N, gc.N, s.u, s.p, d.u,
+              d.p, d2.u, d2.p, in_time ? 2 : 0);
+}
+
+template <class Tf, class Tc>
+void launch_restrict3_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st) {
+  const bool in_time = gc.N != gf.N;
+  const int ntc = in_time ? nt / 2 : nt;
+  const size_t n = (size_t)ntc * gc.F;
+  if (n == 0) return;
+  launch_pdl3(restrict3_kernel<Tf, Tc>, dim3(blocks3(n, 256)), dim3(256), 0, st, gf, gc, ntc, 0, s, (const Tf*)nullptr,
+              d, (Tc*)nullptr, (Tc*)nullptr, (Tc*)nullptr, in_time ? 3 : 0);
+}
+
+template <class Tf, class Tc>
+void launch_prolong3_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
+                             cudaStream_t st, const double* undo_if_rose) {
+  const bool in_time = gc.N != gf.N;
+  // v and pbar from slab 1 (v_0 fixed, pbar_0 unused)
+  const size_t nv = (size_t)gf.N * gf.F + (size_t)gf.N * gf.C;
+  launch_pdl3(prolong3_correct_kernel<Tf, Tc>, dim3(blocks3(nv, 256)), dim3(256), 0, st, gf, gc, gf.N, gf.N, 1, 1,
+              f.v, f.pbar, cn.v, co.v, cn.pbar, co.pbar, undo_if_rose, in_time ? 1 : 0);
+  const size_t nu = (size_t)gf.N * gf.F + (size_t)gf.N * gf.C;
+  launch_pdl3(prolong3_correct_kernel<Tf, Tc>, dim3(blocks3(nu, 256)), dim3(256), 0, st, gf, gc, gf.N, gf.N, 0, 0,
+              f.u, f.p, cn.u, co.u, cn.p, co.p, undo_if_rose, in_time ? 2 : 0);
+}
+
+template <class T>
+void launch_kkt_force_rhs3(const Geom& g, const T* v, T* out, cudaStream_t st) {
+  kkt_force_rhs3_kernel<T><<<dim3(blocks3(g.F, 128), g.N), 128, 0, st>>>(g, v, out);
+}
+
+template <class T>
+void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, double r, T* out, cudaStream_t st) {
+  kkt_grad_rhs3_kernel<T><<<dim3(blocks3(g.F, 128), g.N), 128, 0, st>>>(g, v, u, dens, r, out);
+}
+
+#define STC3_INST_T(T)                                                                                         \
+  template void launch_nso_residual3<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
+                                        cudaStream_t, double*, const double*);                                \
+  template void launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,    \
+                                               cudaStream_t, const double*);                                  \
+  template void launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \
+                                       const double*);                                                        \
+  template void launch_kkt_force_rhs3<T>(const Geom&, const T*, T*, cudaStream_t);                            \
+  template void launch_kkt_grad_rhs3<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);
+STC3_INST_T(float)
+STC3_INST_T(double)
+
+#define STC3_INST_TT(Tf, Tc)                                                                                   \
+  template void launch_restrict3<Tf, Tc>(const Geom&, const Geom&, CState<Tf>, State<Tc>, State<Tc>,          \
+                                         cudaStream_t);                                                       \
+  template void launch_restrict3_faces<Tf, Tc>(const Geom&, const Geom&, int, const Tf*, Tc*, cudaStream_t);  \
+  template void launch_prolong3_correct<Tf, Tc>(const Geom&, const Geom&, State<Tf>, CState<Tc>, CState<Tc>, \
+                                                cudaStream_t, const double*);
+STC3_INST_TT(float, float)
+STC3_INST_TT(double, double)
+STC3_INST_TT(float, double)
+STC3_INST_TT(double, float)
+
+}  // namespace stc

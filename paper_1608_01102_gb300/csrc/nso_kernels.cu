@@ -1049,6 +1049,7 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
                          cudaStream_t st, double* sq, const double* only_if_undone) {
+  if (g.dim == 3) return launch_nso_residual3<T>(g, x, z, res, out, sf, sr, st, sq, only_if_undone);
   const int tpb = 128;
   const int n = g.F > g.C ? g.F : g.C;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
@@ -1060,6 +1061,7 @@ int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 template <class T>
 void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
                                 cudaStream_t st, const double* only_if_undone) {
+  if (g.dim == 3) return launch_nso_residual3_colour<T>(g, x, z, res, out, colour, st, only_if_undone);
   const int px = colour & 1, py = colour >> 1;
   const int nrx = colour_extent(g.ny, py), ncy = colour_extent(g.nx, px);
   const int n = nrx * (g.nx + 1) + (g.ny + 1) * ncy + colour_extent(g.nx, px) * nrx;
@@ -1100,6 +1102,7 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
 template <class T>
 void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                         const double* lm_dev) {
+  if (g.dim == 3) return launch_scgs3_colour<T>(g, x, r, colour, solve_fp32, st, lm_dev);
   if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, lm_dev, st);
   else launch_scgs_ts<T, T>(g, x, r, colour, lm_dev, st);
 }
@@ -1111,6 +1114,7 @@ size_t scgs_smem_bytes(int N, size_t tsize) {
 
 template <class Tf, class Tc>
 void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st) {
+  if (gf.dim == 3) return launch_restrict3<Tf, Tc>(gf, gc, s, d, d2, st);
   const int tpb = 256;
   const int N = gc.N;                       // coarse slab counts
   const bool in_time = gc.N != gf.N;
@@ -1125,6 +1129,7 @@ void launch_restrict(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, 
 
 template <class Tf, class Tc>
 void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st) {
+  if (gf.dim == 3) return launch_restrict3_faces<Tf, Tc>(gf, gc, nt, s, d, st);
   const int tpb = 256;
   // nt fine target slabs; the coarse level holds nt / 2 of them when it halves N
   const bool in_time = gc.N != gf.N;
@@ -1137,6 +1142,7 @@ void launch_restrict_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, 
 template <class Tf, class Tc>
 void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
                             cudaStream_t st, const double* undo_if_rose) {
+  if (gf.dim == 3) return launch_prolong3_correct<Tf, Tc>(gf, gc, f, cn, co, st, undo_if_rose);
   const int tpb = 256;
   const int N = gf.N;
   const bool in_time = gc.N != gf.N;

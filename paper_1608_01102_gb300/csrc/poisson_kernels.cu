@@ -265,6 +265,7 @@ bool project_needs_scratch(const Geom& g, size_t tsize) { return project_smem(g,
 
 template <class T>
 cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch) {
+  if (g.dim == 3) return launch_project3<T>(g, fields, count, vcycles, st, scratch);
   if (count <= 0) return cudaSuccess;
   const size_t layout = project_smem(g, sizeof(T));
   if (project_needs_scratch(g, sizeof(T)) && !scratch) return cudaErrorInvalidValue;
@@ -439,11 +440,13 @@ void launch_axpby_faces(const Geom& g, int count, const T* a, double alpha, cons
 }
 template <class T>
 void launch_kkt_force_rhs(const Geom& g, const T* v, T* out, cudaStream_t st) {
+  if (g.dim == 3) return launch_kkt_force_rhs3<T>(g, v, out, st);
   dim3 grid((g.F + 127) / 128, g.N);
   kkt_force_rhs_kernel<T><<<grid, 128, 0, st>>>(g, v, out);
 }
 template <class T>
 void launch_kkt_grad_rhs(const Geom& g, const T* v, const T* u, const T* dens, double r, T* out, cudaStream_t st) {
+  if (g.dim == 3) return launch_kkt_grad_rhs3<T>(g, v, u, dens, r, out, st);
   dim3 grid((g.F + 127) / 128, g.N);
   kkt_grad_rhs_kernel<T><<<grid, 128, 0, st>>>(g, v, u, dens, r, out);
 }

@@ -93,6 +93,7 @@ struct stc_problem {
   double *mterm = nullptr, *mtmp0 = nullptr, *mtmp1 = nullptr, *star = nullptr;
   size_t star_bytes = 0;
   void* pscratch = nullptr;       // projection level arrays when they do not fit on chip
+  void* adv3 = nullptr;           // 3D sweeps: term buffers and grid-barrier words
   std::vector<int> key_steps;
   std::vector<double> key_c;
   double* dscal = nullptr;  // device fp64 scalars
@@ -134,15 +135,30 @@ void* dalloc(stc_problem* P, size_t bytes) {
   return p;
 }
 
-// (N, dt: the level's; the smoother's LM shift stays the finest level's)
-Geom make_geom(const stc_params& prm, int nx, int ny, double h, int N, double dt) {
+// (N, dt: the level's; the smoother's LM shift stays the finest level's;
+// nz = 0: the 2D grid, else the 3D grid with nz cells along z)
+Geom make_geom(const stc_params& prm, int nx, int ny, int nz, double h, int N, double dt) {
   Geom g;
   g.nx = nx;
   g.ny = ny;
   g.N = N;
-  g.Fx = ny * (nx + 1);
-  g.F = g.Fx + (ny + 1) * nx;
-  g.C = nx * ny;
+  if (nz > 0) {
+    g.dim = 3;
+    g.nz = nz;
+    g.Fx = nz * ny * (nx + 1);
+    g.Fy = nz * (ny + 1) * nx;
+    g.Fxy = g.Fx + g.Fy;
+    g.F = g.Fxy + (nz + 1) * ny * nx;
+    g.C = nx * ny * nz;
+  } else {
+    g.dim = 2;
+    g.nz = 1;
+    g.Fx = ny * (nx + 1);
+    g.Fy = (ny + 1) * nx;
+    g.F = g.Fx + g.Fy;
+    g.Fxy = g.F;
+    g.C = nx * ny;
+  }
   g.h = h;
   g.ih = 1.0 / h;
   g.dt = dt;
@@ -153,6 +169,12 @@ Geom make_geom(const stc_params& prm, int nx, int ny, double h, int N, double dt
   g.self_adv = prm.self_advection ? 1 : 0;
   set_fp32_copies(g);
   return g;
+}
+
+// the STFAS hierarchy coarsens while every axis is even and its half stays >= coarsest_n
+bool can_halve(const stc_params& prm, int nx, int ny, int nz) {
+  const bool xy = nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n;
+  return xy && (nz == 0 || (nz % 2 == 0 && nz / 2 >= prm.coarsest_n));
 }
 
 size_t esz(bool dbl) { return dbl ? 8 : 4; }
@@ -188,8 +210,9 @@ void nso_residual(stc_problem* P, int l, double sf, double sr, const FieldSet& r
 void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = false,
             const double* first_only_if_undone = nullptr) {
   Level& L = P->lv[l];
+  const int ncol = 1 << L.g.dim;   // parity colours of (i, j[, k])
   for (int s = 0; s < sweeps; ++s)
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < ncol; ++c) {
       // f - res where this colour's cells read it, all from the pre-colour state
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
@@ -336,6 +359,7 @@ double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool non
     ck(cudaStreamSynchronize(P->st), "sync");
     return std::numeric_limits<double>::infinity();
   }
+  if (*P->herr & DEV_BARRIER_TIMEOUT) fail(STC_ERR_CUDA, "a grid-wide barrier of a 3D sweep timed out");
   if (*P->herr & DEV_TAYLOR_KMAX) fail(STC_ERR_DIVERGED, "Taylor series exceeded taylor_kmax");
   if (*P->herr & DEV_NONFINITE) fail(STC_ERR_DIVERGED, "non-finite value in a residual norm");
   return P->hscal[slot];
@@ -432,8 +456,12 @@ void forward(stc_problem* P, const void* vel, void* rho, int* K, cudaStream_t st
   const double thresh = P->prm.taylor_tol * P->rho_scale;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    ck(launch_taylor_forward<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, st),
-       "taylor forward");
+    if (g.dim == 3)
+      ck(launch_taylor_forward3<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, P->adv3, st),
+         "taylor forward");
+    else
+      ck(launch_taylor_forward<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, st),
+         "taylor forward");
   });
   count(P, 1);
 }
@@ -443,9 +471,14 @@ void adjoint(stc_problem* P, const void* vel, const void* rho, const int* K, con
   const Geom& g = P->lv[0].g;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    ck(launch_taylor_adjoint<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
-                                T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st),
-       "taylor adjoint");
+    if (g.dim == 3)
+      ck(launch_taylor_adjoint3<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
+                                   T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, P->derr, P->adv3, st),
+         "taylor adjoint");
+    else
+      ck(launch_taylor_adjoint<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
+                                  T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st),
+         "taylor adjoint");
   });
   count(P, 1);
 }
@@ -456,7 +489,7 @@ void project(stc_problem* P, void* fields, int count, cudaStream_t st) {
     using T = decltype(tag);
     ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st, (T*)P->pscratch), "project");
   });
-  if (count > 0) ::count(P, 1);
+  if (count > 0) ::count(P, g.dim == 3 ? project3_launches(g, P->prm.poisson_vcycles) : 1);
 }
 
 void prepare_targets(stc_problem* P, cudaStream_t st) {
@@ -772,7 +805,8 @@ bool params_valid(const stc_params& prm) {
       prm.taylor_kmax > 256 || prm.max_vcycles < 0 || prm.metric_levels < 0 || prm.metric_levels > 12 ||
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
-      prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1);
+      prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1 || prm.nz < 0 ||
+      prm.nz == 1);
 }
 
 // Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
@@ -783,34 +817,43 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   const bool dbl = prm.precision == 1;
   const size_t ts = dbl ? 8 : 4;
   const size_t N = (size_t)prm.num_steps;
-  struct Dim { int nx, ny, N; };
-  std::vector<Dim> dims{{prm.nx, prm.ny, prm.num_steps}};
-  int nx = prm.nx, ny = prm.ny, Nl = prm.num_steps;
-  while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
+  struct Dim { int nx, ny, nz, N; };
+  std::vector<Dim> dims{{prm.nx, prm.ny, prm.nz, prm.num_steps}};
+  int nx = prm.nx, ny = prm.ny, nz = prm.nz, Nl = prm.num_steps;
+  while (can_halve(prm, nx, ny, nz)) {
     nx /= 2;
     ny /= 2;
+    nz /= 2;
     if (prm.time_coarsen && Nl % 2 == 0) Nl /= 2;
-    dims.push_back({nx, ny, Nl});
+    dims.push_back({nx, ny, nz, Nl});
   }
-  auto faces = [](int x, int y) { return (size_t)y * (x + 1) + (size_t)(y + 1) * x; };
+  auto faces = [](int x, int y, int z) {
+    return z > 0 ? (size_t)z * y * (x + 1) + (size_t)z * (y + 1) * x + (size_t)(z + 1) * y * x
+                 : (size_t)y * (x + 1) + (size_t)(y + 1) * x;
+  };
+  auto cells = [](int x, int y, int z) { return (size_t)x * y * (z > 0 ? z : 1); };
   auto fieldset = [&](size_t F, size_t C, size_t s, size_t Nl_) {
     return b((Nl_ + 1) * F * s) + b((Nl_ + 1) * C * s) + b(Nl_ * F * s) + b(Nl_ * C * s);
   };
   size_t total = 0;
   for (size_t l = 0; l < dims.size(); ++l) {
-    const size_t F = faces(dims[l].nx, dims[l].ny), C = (size_t)dims[l].nx * dims[l].ny;
+    const size_t F = faces(dims[l].nx, dims[l].ny, dims[l].nz), C = cells(dims[l].nx, dims[l].ny, dims[l].nz);
     const size_t Nl_ = (size_t)dims[l].N;
     const size_t s = (dbl || (l > 0 && l == dims.size() - 1)) ? 8 : 4;
     total += 3 * fieldset(F, C, s, Nl_) + (l > 0 ? fieldset(F, C, s, Nl_) : 0) + b(Nl_ * F * s);
   }
-  const size_t F = faces(prm.nx, prm.ny), C = (size_t)prm.nx * prm.ny;
+  const size_t F = faces(prm.nx, prm.ny, prm.nz), C = cells(prm.nx, prm.ny, prm.nz);
   total += 3 * b((N + 1) * C * ts) + b(N * C * ts) + 2 * b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) +
            b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts, N) : 0) + 4 * b(N * F * ts) +
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
            b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
-  Geom g0 = make_geom(prm, prm.nx, prm.ny, 1.0 / prm.nx, prm.num_steps, prm.dt);
-  if (project_needs_scratch(g0, ts)) total += b((N + 1) * project_smem(g0, ts));
+  Geom g0 = make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt);
+  if (g0.dim == 3) {
+    total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts);
+  } else if (project_needs_scratch(g0, ts)) {
+    total += b((N + 1) * project_smem(g0, ts));
+  }
   return total;
 }
 
@@ -865,6 +908,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->lm_adapt = 1;
   p->al_threshold = -1.0;
   p->time_coarsen = 0;
+  p->nz = 0;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -894,29 +938,32 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     // hierarchy: halve while both even and the halves stay >= coarsest_n (in
     // space, Sec. 4.2); with time_coarsen each level whose N is even also
     // hands the next one N/2 steps of 2 dt
-    int nx = prm.nx, ny = prm.ny, Nl = prm.num_steps;
+    int nx = prm.nx, ny = prm.ny, nz = prm.nz, Nl = prm.num_steps;
     double h = 1.0 / prm.nx, dtl = prm.dt;
     std::vector<Geom> geoms;
-    geoms.push_back(make_geom(prm, nx, ny, h, Nl, dtl));
-    while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= prm.coarsest_n && ny / 2 >= prm.coarsest_n) {
+    geoms.push_back(make_geom(prm, nx, ny, nz, h, Nl, dtl));
+    while (can_halve(prm, nx, ny, nz)) {
       nx /= 2;
       ny /= 2;
+      nz /= 2;
       h *= 2.0;
       if (prm.time_coarsen && Nl % 2 == 0) {
         Nl /= 2;
         dtl *= 2.0;
       }
-      geoms.push_back(make_geom(prm, nx, ny, h, Nl, dtl));
+      geoms.push_back(make_geom(prm, nx, ny, nz, h, Nl, dtl));
     }
     const Geom& g0 = geoms[0];
-    if (!advect_supported(g0)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip advection sweep");
-    if (!project_supported(g0, P->ts)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip projection");
+    const bool d3 = g0.dim == 3;
+    if (!d3 && !advect_supported(g0)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip advection sweep");
+    if (!d3 && !project_supported(g0, P->ts)) fail(STC_ERR_UNSUPPORTED, "grid too large for the on-chip projection");
+    if (d3 && !project3_supported(g0)) fail(STC_ERR_UNSUPPORTED, "coarsest projection level above 512 cells");
     int dev = 0;
     ck(cudaGetDevice(&dev), "get device");
     int smem_optin = 0;
     ck(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "attr");
-    if ((int)advect_smem_adjoint(g0, P->ts) > smem_optin ||
-        (!project_needs_scratch(g0, P->ts) && (int)project_smem(g0, P->ts) > smem_optin))
+    if (!d3 && ((int)advect_smem_adjoint(g0, P->ts) > smem_optin ||
+                (!project_needs_scratch(g0, P->ts) && (int)project_smem(g0, P->ts) > smem_optin)))
       fail(STC_ERR_UNSUPPORTED, "shared memory of this device too small for the grid");
     ck(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "stream");
     const int N = prm.num_steps;
@@ -930,7 +977,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       if (l > 0) alloc_fieldset(P, L.old, L.g, L.dbl);
       L.z = dalloc(P, (size_t)N * L.g.F * esz(L.dbl));
       const size_t solve_size = P->dbl ? 8 : 4;   // fp32 mode solves corrections in fp32 on every level
-      if (scgs_smem_bytes(N, solve_size) > (size_t)smem_optin)
+      const size_t scgs_bytes = d3 ? scgs3_smem_bytes(L.g.N, solve_size) : scgs_smem_bytes(N, solve_size);
+      if (scgs_bytes + (d3 ? 1024 : 0) > (size_t)smem_optin)
         fail(STC_ERR_UNSUPPORTED, "too many timesteps for the shared-memory SCGS solve");
 
       P->lv.push_back(L);
@@ -963,7 +1011,12 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->dscal = (double*)dalloc(P, 16 * sizeof(double));
     P->derr = (int*)dalloc(P, sizeof(int));
     // projections run on at most N + 1 fields at once (stc_project on V or KKT_G)
-    if (project_needs_scratch(g0, ts)) P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
+    if (d3) {
+      P->pscratch = dalloc(P, project3_scratch_elems(g0, N + 1) * ts);
+      P->adv3 = dalloc(P, advect3_scratch_bytes(g0, ts));
+    } else if (project_needs_scratch(g0, ts)) {
+      P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
+    }
     ck(cudaMallocHost(&P->hscal, 16 * sizeof(double)), "pinned");
     ck(cudaMallocHost(&P->herr, sizeof(int)), "pinned");
     // inputs: rho_0 into rho[0] of every density buffer, v_0
@@ -985,13 +1038,40 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     if (v0) {
       std::vector<double> vv(v0, v0 + F);
       // wall faces are not unknowns: keep them zero
-      for (int j = 0; j < g0.ny; ++j) {
-        vv[(size_t)j * (g0.nx + 1)] = 0.0;
-        vv[(size_t)j * (g0.nx + 1) + g0.nx] = 0.0;
-      }
-      for (int i = 0; i < g0.nx; ++i) {
-        vv[g0.Fx + i] = 0.0;
-        vv[g0.Fx + (size_t)g0.ny * g0.nx + i] = 0.0;
+      if (d3) {
+        for (size_t f = 0; f < F; ++f) {
+          int axis, k, j, i;
+          if (f < (size_t)g0.Fx) {
+            axis = 0;
+            i = (int)(f % (g0.nx + 1));
+            j = (int)((f / (g0.nx + 1)) % g0.ny);
+            k = (int)(f / ((size_t)(g0.nx + 1) * g0.ny));
+          } else if (f < (size_t)g0.Fxy) {
+            axis = 1;
+            const size_t q = f - g0.Fx;
+            i = (int)(q % g0.nx);
+            j = (int)((q / g0.nx) % (g0.ny + 1));
+            k = (int)(q / ((size_t)g0.nx * (g0.ny + 1)));
+          } else {
+            axis = 2;
+            const size_t q = f - g0.Fxy;
+            i = (int)(q % g0.nx);
+            j = (int)((q / g0.nx) % g0.ny);
+            k = (int)(q / ((size_t)g0.nx * g0.ny));
+          }
+          const int p = axis == 0 ? i : (axis == 1 ? j : k);
+          const int n = axis == 0 ? g0.nx : (axis == 1 ? g0.ny : g0.nz);
+          if (p == 0 || p == n) vv[f] = 0.0;
+        }
+      } else {
+        for (int j = 0; j < g0.ny; ++j) {
+          vv[(size_t)j * (g0.nx + 1)] = 0.0;
+          vv[(size_t)j * (g0.nx + 1) + g0.nx] = 0.0;
+        }
+        for (int i = 0; i < g0.nx; ++i) {
+          vv[g0.Fx + i] = 0.0;
+          vv[g0.Fx + (size_t)g0.ny * g0.nx + i] = 0.0;
+        }
       }
       FieldRef rv;
       rv.count = F;
@@ -1196,6 +1276,22 @@ stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx
   }
   if (nx) *nx = p->lv[level].g.nx;
   if (ny) *ny = p->lv[level].g.ny;
+  return STC_OK;
+}
+
+stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int* nz) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (level < 0 || level >= (int)p->lv.size()) {
+    g_last_error = "level out of range";
+    return STC_ERR_INVALID_ARG;
+  }
+  const Geom& g = p->lv[level].g;
+  if (nx) *nx = g.nx;
+  if (ny) *ny = g.ny;
+  if (nz) *nz = g.dim == 3 ? g.nz : 0;
   return STC_OK;
 }
 

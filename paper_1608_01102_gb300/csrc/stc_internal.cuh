@@ -14,10 +14,15 @@
 namespace stc {
 
 // Geometry and scalar parameters of one level, passed to kernels by value.
+// dim = 2: the nx x ny grid above (nz = 1, Fxy = F).  dim = 3: the
+// nx x ny x nz grid of grid3d.cuh (x-, y-, then z-faces; Fxy = Fx + Fy is the
+// offset of the z-faces).
 struct Geom {
   int nx, ny;        // cells
   int N;             // timesteps
   int Fx, F, C;      // x-face count, face count, cell count
+  int dim, nz;       // 2 or 3; cells along z (1 in 2D)
+  int Fy, Fxy;       // y-face count; x- plus y-face count
   double h, ih;      // cell size and 1/h
   double dt, idt;    // timestep and 1/dt
   double a;          // K / r   (Eq. KKTAO row 1)
@@ -229,6 +234,7 @@ enum DevError : int {
   DEV_TAYLOR_KMAX = 1,   // Taylor series did not reach tolerance within kmax
   DEV_NONFINITE = 2,     // a non-finite value reached a norm
   DEV_BAD_LAUNCH = 4,    // launch shape inconsistent with the data (bounds guard)
+  DEV_BARRIER_TIMEOUT = 8,   // a grid-wide barrier waited past its iteration limit
 };
 
 }  // namespace stc

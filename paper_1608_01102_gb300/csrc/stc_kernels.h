@@ -50,6 +50,7 @@ constexpr int kMaxClusterCTAs = 16;   // the sweeps run on one cluster of 16 (no
 // of the sweep kernels can be scheduled, else 8 (decided once per process)
 int advect_cluster_ctas();
 constexpr int kAdvThreads = 512;
+constexpr int kTaylorKmaxLimit = 256;   // largest taylor_kmax (size of the sweeps' dt/k tables)
 constexpr int kAdvMaxCellsPerThread = 8;
 
 // rho[0] given; writes rho[1..N] and K[0..N-1] (Taylor orders).  vel: N face slabs.
@@ -106,5 +107,49 @@ void launch_misfit_dot(const Geom& g, const T* rho, const double* star, const do
 // out += scale * sum_e (a_e - b_e)^2 over n entries (fp64)
 template <class T>
 void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st);
+
+// --- 3D grid (nso3d_kernels.cu, advect3d_kernels.cu, poisson3d_kernels.cu) ---
+// Same contracts as the 2D launchers above; the generic launchers forward to
+// these when g.dim == 3.
+template <class T>
+void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                          cudaStream_t st, double* sq, const double* only_if_undone);
+template <class T>
+void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                 cudaStream_t st, const double* only_if_undone);
+template <class T>
+void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+                         const double* lm_dev);
+size_t scgs3_smem_bytes(int N, size_t tsize);   // shared memory of one cell's SCGS solve
+template <class Tf, class Tc>
+void launch_restrict3(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
+template <class Tf, class Tc>
+void launch_restrict3_faces(const Geom& gf, const Geom& gc, int nt, const Tf* s, Tc* d, cudaStream_t st);
+template <class Tf, class Tc>
+void launch_prolong3_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<Tc> cn, CState<Tc> co,
+                             cudaStream_t st, const double* undo_if_rose);
+template <class T>
+void launch_kkt_force_rhs3(const Geom& g, const T* v, T* out, cudaStream_t st);
+template <class T>
+void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, double r, T* out, cudaStream_t st);
+// The 3D sweeps are single cooperative launches over the whole GPU; scratch:
+// advect3_scratch_bytes (term buffers and the grid barrier's words).
+size_t advect3_scratch_bytes(const Geom& g, size_t tsize);
+template <class T>
+cudaError_t launch_taylor_forward3(const Geom& g, const T* vel, T* rho, int* K, double thresh, int kmax, int* err,
+                                   void* scratch, cudaStream_t st);
+template <class T>
+cudaError_t launch_taylor_adjoint3(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
+                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax, int* err,
+                                   void* scratch, cudaStream_t st);
+template <class T>
+void launch_metric3(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
+                    double* out, double* tmp0, double* tmp1, cudaStream_t st);
+// batched multigrid projection of `count` fields; scratch: project3_scratch_elems(g, count) elements
+size_t project3_scratch_elems(const Geom& g, int count);
+bool project3_supported(const Geom& g);
+template <class T>
+cudaError_t launch_project3(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch);
+int project3_launches(const Geom& g, int vcycles);
 
 }  // namespace stc

@@ -32,7 +32,8 @@ class StcParams(ctypes.Structure):
                 ("eps_admm", c_double), ("max_vcycles", c_int), ("metric_levels", c_int),
                 ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
                 ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
-                ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double), ("time_coarsen", c_int)]
+                ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double), ("time_coarsen", c_int),
+                ("nz", c_int)]
 
 
 class StcReport(ctypes.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "stc_set_field": (c_int, [c_void_p, c_int, c_int, P_double, c_size_t]),
     "stc_level_info": (c_int, [c_void_p, P_int, c_int, P_int, P_int]),
     "stc_level_steps": (c_int, [c_void_p, c_int, P_int, P_double]),
+    "stc_level_dims": (c_int, [c_void_p, c_int, P_int, P_int, P_int]),
     "stc_advect": (c_int, [c_void_p, c_int]),
     "stc_get_taylor_orders": (c_int, [c_void_p, P_int, c_size_t]),
     "stc_metric_terms": (c_int, [c_void_p]),
@@ -158,6 +160,13 @@ def _dptr(a):
     return a.ctypes.data_as(P_double)
 
 
+def grid_sizes(nx, ny, nz=0):
+    """(faces, cells) of the 2D grid nx x ny (nz = 0) or the 3D grid nx x ny x nz."""
+    if nz:
+        return nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx, nx * ny * nz
+    return ny * (nx + 1) + (ny + 1) * nx, nx * ny
+
+
 def default_params(nx, ny, N, **overrides):
     p = StcParams()
     load().stc_default_params(ctypes.byref(p), nx, ny, N)
@@ -182,12 +191,14 @@ class Problem:
         _check(self.lib.stc_create_problem(ctypes.byref(params), _dptr(rho0), v0p, st, ctypes.byref(h)))
         self.h = h
         self.nx, self.ny, self.N = params.nx, params.ny, params.num_steps
+        self.nz = params.nz
 
     # sizes --------------------------------------------------------------
     def level_shape(self, level):
-        nl, nx, ny = c_int(), c_int(), c_int()
-        _check(self.lib.stc_level_info(self.h, ctypes.byref(nl), level, ctypes.byref(nx), ctypes.byref(ny)))
-        return nx.value, ny.value
+        """(nx, ny) of a 2D level, (nx, ny, nz) of a 3D one."""
+        nx, ny, nz = c_int(), c_int(), c_int()
+        _check(self.lib.stc_level_dims(self.h, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz)))
+        return (nx.value, ny.value, nz.value) if nz.value else (nx.value, ny.value)
 
     def num_levels(self):
         nl = c_int()
@@ -200,9 +211,7 @@ class Problem:
         return n.value, dt.value
 
     def field_shape(self, name, level=0):
-        nx, ny = self.level_shape(level)
-        F = ny * (nx + 1) + (ny + 1) * nx
-        C = nx * ny
+        F, C = grid_sizes(*self.level_shape(level))
         N = self.level_steps(level)[0] if level > 0 else self.N
         face_np1 = ("V", "RES_V", "RES_IN_V", "XOLD_V", "KKT_G")
         cell_np1 = ("PBAR", "RES_PBAR", "RES_IN_PBAR", "XOLD_PBAR", "RHO", "MTERM")
@@ -434,7 +443,7 @@ class Server:
         rq.sim_seconds, rq.sim_status = sim_seconds, sim_status
         t = ctypes.c_longlong()
         _check(self.lib.stc_server_submit(self.h, ctypes.byref(rq), ctypes.byref(t)))
-        F = params.ny * (params.nx + 1) + (params.ny + 1) * params.nx
+        F = grid_sizes(params.nx, params.ny, params.nz)[0]
         self._sizes[t.value] = (params.num_steps, F)
         return t.value
 
