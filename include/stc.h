@@ -152,7 +152,13 @@ typedef enum {
   STC_FIELD_XOLD_V = 22,   /* copy of R x^h kept for the FAS correction (level l >= 1) */
   STC_FIELD_XOLD_PBAR = 23,
   STC_FIELD_XOLD_U = 24,
-  STC_FIELD_XOLD_P = 25
+  STC_FIELD_XOLD_P = 25,
+  /* forward simulation and its adjoint (stc_simulate, stc_simulate_adjoint) */
+  STC_FIELD_SIM_GRAD_RHO = 26, /* input dL/d rho_i, i = 0..N (fp64)  (N+1) x cells */
+  STC_FIELD_SIM_GRAD_U = 27,   /* output dL/d u_i, i = 0..N-1      N x faces      */
+  STC_FIELD_SIM_ADJ_V0 = 28,   /* output dL/d v_0                  1 x faces      */
+  STC_FIELD_SIM_ADJ_RHO0 = 29, /* output dL/d rho_0 (with_step0)   1 x cells      */
+  STC_FIELD_SIM_ADJ_VN = 30    /* input dL/d v_N (zero unless set) 1 x faces      */
 } stc_field;
 
 /* Fill *p with the defaults for an nx x ny grid with N steps, dt = 1/N. */
@@ -208,6 +214,37 @@ stc_status stc_set_field(stc_problem* p, int field, int level, const double* in,
 stc_status stc_level_info(const stc_problem* p, int* nlevels, int level, int* nx, int* ny);
 /* Cells per axis of one level, nz = 0 on a 2D grid.  Outputs may be NULL. */
 stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int* nz);
+
+/* ---- forward simulation with a given control, and its adjoint -------------
+ * The full-resimulation path of Sec. 5 and Appendix A: from v_0 (STC_FIELD_V
+ * slab 0) and rho_0 (STC_FIELD_RHO slab 0) under the forces u_i (STC_FIELD_U),
+ * stc_simulate solves each implicit step of Eq. NSA/NSB,
+ *   (v_{i+1} - v_i)/dt + Adv(v_{i+1}) - u_i + grad p = 0,  div v_{i+1} = 0,
+ * by the Picard iteration v <- Q[v_i + dt (u_i - Adv(v))] until the change is
+ * at most picard_tol * max|v| (STC_ERR_NOT_CONVERGED after max_iter), writes
+ * v_1..v_N, then advects rho_1..rho_N with v_0..v_{N-1} (Eq. Conv; Taylor
+ * orders as stc_advect).  iters (may be NULL): Picard iterations in total.
+ * The buffers of both calls are allocated at the first call (not counted by
+ * stc_problem_bytes).  The multigrid projection makes Q exact to its
+ * truncation (~1e-7 relative in fp32, ~1e-9 in fp64 after 8 cycles). */
+stc_status stc_simulate(stc_problem* p, double picard_tol, int max_iter, int* iters);
+/* Adjoint of stc_simulate's map (u, v_0, rho_0) -> (rho_0..rho_N, v_N) at its last
+ * trajectory: given dL/d rho_i in STC_FIELD_SIM_GRAD_RHO and dL/d v_N in
+ * STC_FIELD_SIM_ADJ_VN, writes dL/d u_i to STC_FIELD_SIM_GRAD_U and dL/d v_0 to
+ * STC_FIELD_SIM_ADJ_V0 (through the velocity chain and, with with_step0, the
+ * density of step 0); with with_step0 also the total dL/d rho_0 (its direct
+ * term SIM_GRAD_RHO slab 0 included) to STC_FIELD_SIM_ADJ_RHO0, else zero there.  The density part is the
+ * backward sweep of stc_adjoint (it overwrites STC_FIELD_MTERM and MU); the
+ * velocity part the transposed step z <- Q[a - dt dAdv(v_{i+1})^T z],
+ * dL/d u_i = dt z, a <- dL/d v_i|density + z, until the change is at most
+ * picard_tol * max|z|.  iters: iterations in total. */
+stc_status stc_simulate_adjoint(stc_problem* p, double picard_tol, int max_iter, int with_step0, int* iters);
+/* Device-to-device copy between a field and a caller's device buffer of len
+ * elements (fp64 if buffer_is_double, else fp32), converting to the field's
+ * type and multiplying by scale; to_field = 1 writes the field, 0 reads it.
+ * Enqueued on the problem's stream (no synchronisation). */
+stc_status stc_copy_field_device(stc_problem* p, int field, int level, void* buffer, size_t len,
+                                 int buffer_is_double, int to_field, double scale);
 /* Timesteps N_l and timestep dt_l of level `level` (they differ from the
  * finest level's only with stc_params.time_coarsen).  Either output may be NULL. */
 stc_status stc_level_steps(const stc_problem* p, int level, int* num_steps, double* dt);

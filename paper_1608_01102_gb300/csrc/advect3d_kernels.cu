@@ -275,7 +275,7 @@ template <class T>
 __global__ void __launch_bounds__(kAdv3Threads)
 taylor_adjoint3_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                        const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta, T* out,
-                       T* powers, int kmax, int* err, unsigned char* scratch) {
+                       T* powers, int kmax, int* err, unsigned char* scratch, int s_end, T* mu_m1) {
   __shared__ T dtk[kTaylorKmaxLimit + 1];
   for (int k = threadIdx.x; k <= kmax; k += blockDim.x) dtk[k] = k == 0 ? T(1) : T(g.dt / (double)k);
   const int C = g.C, F = g.F;
@@ -288,7 +288,7 @@ taylor_adjoint3_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ 
   // m = mu_{N-1} = -m_N, kept in mu's slab of the current step
   T* m = mu + (size_t)(g.N - 1) * C;
   for (int e = tid; e < C; e += nth) m[e] = T(-mterm[(size_t)g.N * C + e]);
-  for (int st = g.N - 1; st >= 1; --st) {
+  for (int st = g.N - 1; st >= s_end; --st) {
     m = mu + (size_t)st * C;
     int K = Ks[st];
     K = K < 1 ? 1 : (K > kmax ? kmax : K);
@@ -338,9 +338,10 @@ taylor_adjoint3_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ 
       cur = nxt;
       nxt = tmp;
     }
-    // mu_{st-1} = T^T mu_st - m_st
-    T* mprev = mu + (size_t)(st - 1) * C;
-    for (int e = tid; e < C; e += nth) mprev[e] = cur[e] - T(mterm[(size_t)st * C + e]);
+    // mu_{st-1} = T^T mu_st - m_st (for st = 0: the adjoint density of step 0, into mu_m1)
+    T* mprev = st > 0 ? mu + (size_t)(st - 1) * C : mu_m1;
+    if (mprev)
+      for (int e = tid; e < C; e += nth) mprev[e] = cur[e] - T(mterm[(size_t)st * C + e]);
     if (!grid_barrier(bar, err)) return;
   }
 }
@@ -486,8 +487,8 @@ cudaError_t launch_taylor_forward3(const Geom& g, const T* vel, T* rho, int* K, 
 template <class T>
 cudaError_t launch_taylor_adjoint3(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                    T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax, int* err,
-                                   void* scratch, cudaStream_t st) {
-  if (kmax < 1 || kmax > kTaylorKmaxLimit || !scratch) return cudaErrorInvalidValue;
+                                   void* scratch, cudaStream_t st, int s_end, T* mu_m1) {
+  if (kmax < 1 || kmax > kTaylorKmaxLimit || !scratch || (s_end != 0 && s_end != 1)) return cudaErrorInvalidValue;
   static std::once_flag once;
   static CoopShape shape;
   std::call_once(once, [] { shape = coop_shape(taylor_adjoint3_kernel<T>); });
@@ -498,7 +499,7 @@ cudaError_t launch_taylor_adjoint3(const Geom& g, const T* vel, const T* rho, co
   Geom gg = g;
   void* args[] = {&gg,         (void*)&vel,   (void*)&rho,  (void*)&K,   (void*)&mterm,
                   (void*)&mu,  (void*)&base,  (void*)&alpha, (void*)&beta, (void*)&out,
-                  (void*)&powers, (void*)&kmax, (void*)&err, (void*)&sc};
+                  (void*)&powers, (void*)&kmax, (void*)&err, (void*)&sc, (void*)&s_end, (void*)&mu_m1};
   return coop_launch(taylor_adjoint3_kernel<T>, shape.blocks, st, args);
 }
 
@@ -535,7 +536,8 @@ void launch_metric3(const Geom& g, const T* rho_s, const double* star, double c,
   template cudaError_t launch_taylor_forward3<T>(const Geom&, const T*, T*, int*, double, int, int*, void*,    \
                                                  cudaStream_t);                                                \
   template cudaError_t launch_taylor_adjoint3<T>(const Geom&, const T*, const T*, const int*, const double*,   \
-                                                 T*, const T*, T, T, T*, T*, int, int*, void*, cudaStream_t);  \
+                                                 T*, const T*, T, T, T*, T*, int, int*, void*, cudaStream_t,   \
+                                                 int, T*);                                                     \
   template void launch_metric3<T>(const Geom&, const T*, const double*, double, int, double, double*, double*,  \
                                   double*, cudaStream_t);
 STC_ADV3_INST(float)

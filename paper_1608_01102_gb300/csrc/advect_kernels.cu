@@ -439,7 +439,7 @@ template <class T>
 __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                       const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
-                      T* out, T* powers, int kmax) {
+                      T* out, T* powers, int kmax, int s_end, T* mu_m1) {
   __shared__ T dtk[kTaylorKmaxLimit + 1];
   fill_dt_over_k(g, kmax, dtk);
   cg::cluster_group cl = cg::this_cluster();
@@ -473,7 +473,7 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
     clj[q] = e / nx;
     cii[q] = e - clj[q] * nx;
   }
-  for (int st = g.N - 1; st >= 1; --st) {
+  for (int st = g.N - 1; st >= s_end; --st) {
     // every CTA has finished the previous step (halo reads of the term
     // buffers, reads of the global powers) before they are overwritten
     cl.sync();
@@ -571,10 +571,14 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       if (e < nown) m[q] = cur[2 * nx + e] - T(mterm[cbase + e]);
     }
   }
+  // mu_0, or with s_end = 0 the adjoint density of step 0 (T_0^T mu_0 - m_0)
+  T* mu_out = s_end == 0 ? mu_m1 : mu;
+  if (mu_out) {
 #pragma unroll
-  for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
-    const int e = threadIdx.x + q * blockDim.x;
-    if (e < nown) mu[(size_t)s.r0 * nx + e] = m[q];
+    for (int q = 0; q < kAdvMaxCellsPerThread; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      if (e < nown) mu_out[(size_t)s.r0 * nx + e] = m[q];
+    }
   }
   cl.sync();
 }
@@ -736,7 +740,7 @@ template <class T>
 __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                       const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
-                      T* out, T* powers, int kmax);
+                      T* out, T* powers, int kmax, int s_end, T* mu_m1);
 
 // A 16-CTA cluster halves each CTA's rows (the per-term latency of the sweeps
 // scales with them); it needs 16 SMs of one GPC free at once.  The device is
@@ -803,11 +807,13 @@ cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, d
 template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int s_end, T* mu_m1) {
   if (kmax < 1 || kmax > kTaylorKmaxLimit) return cudaErrorInvalidValue;   // size of the dt/k table
+  if (s_end != 0 && s_end != 1) return cudaErrorInvalidValue;
   Geom gg = g;
-  void* args[] = {&gg,          (void*)&vel,  (void*)&rho,   (void*)&K,   (void*)&mterm,  (void*)&mu,
-                  (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax};
+  void* args[] = {&gg,          (void*)&vel,   (void*)&rho,  (void*)&K,   (void*)&mterm,  (void*)&mu,
+                  (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax,
+                  (void*)&s_end, (void*)&mu_m1};
   return cluster_launch(taylor_adjoint_kernel<T>, adv_layout<T>(g, true, advect_cluster_ctas()).total, st, args);
 }
 
@@ -911,7 +917,7 @@ namespace stc {
   template cudaError_t launch_taylor_forward<T>(const Geom&, const T*, T*, int*, double, int, int*,           \
                                                 cudaStream_t);                                                \
   template cudaError_t launch_taylor_adjoint<T>(const Geom&, const T*, const T*, const int*, const double*, T*, \
-                                                const T*, T, T, T*, T*, int, cudaStream_t);                    \
+                                                const T*, T, T, T*, T*, int, cudaStream_t, int, T*);           \
   template void launch_metric<T>(const Geom&, const T*, const double*, double, int, double, double*, double*,   \
                                  double*, cudaStream_t);
 STC_ADV_INST(float)

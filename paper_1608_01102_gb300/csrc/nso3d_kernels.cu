@@ -757,6 +757,283 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
 }
 
 // ---------------------------------------------------------------------------
+// SCGS on the 3D grid, one thread per cell: the same local system (u blocks
+// eliminated in closed form, N symmetric saddle v blocks coupled by
+// O_t = -P U_{t+1} / dt) solved by block Thomas elimination along time, the
+// O(N) solve of Sec. 4.3.  A level with many cells per colour has parallelism
+// enough across cells, and this form does about half the arithmetic of the
+// cyclic reduction with no shared memory.  Each thread streams its pivots'
+// solutions (Z_t = A_t^{-1} [O_t; 0] and z_t = A_t^{-1} r_t, 49 values per
+// block) to a scratch laid out cell-fastest, so the accesses of a warp are
+// coalesced.  Passes: (1) ascending elimination, (2) descending
+// substitution x_t = z_t - Z_t x_{t+1} in place, (3) ascending recovery of
+// the u blocks and x += omega delta.  U_t is recomputed in pass 3 from the
+// not yet updated v_{t+1} (the cell's own faces of slab t+1 are written only
+// after it; the stencil's other faces belong to cells of other colours).
+// ---------------------------------------------------------------------------
+constexpr int kThomasRec = NF * NF + NF + NB;   // X (6x6), multipliers (6), z (7)
+
+template <class T, class S>
+struct ThomasCell {
+  const Geom& g;
+  int fidx[NF], cc;
+  S act[NF];
+  Cell3 cl;
+  __device__ ThomasCell(const Geom& g_, int colour, int q) : g(g_) {
+    cl = colour_cell(g, colour, q);
+    fidx[0] = xf(g, cl.k, cl.j, cl.i);
+    fidx[1] = xf(g, cl.k, cl.j, cl.i + 1);
+    fidx[2] = yf(g, cl.k, cl.j, cl.i);
+    fidx[3] = yf(g, cl.k, cl.j + 1, cl.i);
+    fidx[4] = zf(g, cl.k, cl.j, cl.i);
+    fidx[5] = zf(g, cl.k + 1, cl.j, cl.i);
+    act[0] = S(cl.i > 0);
+    act[1] = S(cl.i < g.nx - 1);
+    act[2] = S(cl.j > 0);
+    act[3] = S(cl.j < g.ny - 1);
+    act[4] = S(cl.k > 0);
+    act[5] = S(cl.k < g.nz - 1);
+    cc = cid(g, cl.k, cl.j, cl.i);
+  }
+  // U_t = (I/dt + dAdv_loc(v_{t+1})) on the active face pairs
+  __device__ void coupling(const T* v_t1, S idt, S U[NF][NF]) const {
+    local_adv_jac3<T, S>(g, v_t1, cl.k, cl.j, cl.i, act, U);
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+#pragma unroll
+      for (int b = 0; b < NF; ++b) U[a][b] = ((a == b ? idt : S(0)) + S(g.self_adv) * U[a][b]) * act[a] * act[b];
+  }
+  // y_t = D_u^{-1} b_u(t), b_u = -(f - res) at the cell's u faces and p_{t+1}
+  __device__ void u_solve(const CState<T>& r, int t, const CellG3<S>& cg, S y[NB]) const {
+    S bf[NF], pb[NF];
+    const T* ru = r.u + (size_t)t * g.F;
+#pragma unroll
+    for (int a = 0; a < NF; ++a) bf[a] = S(-ld(ru + fidx[a])) * act[a];
+    const S bp = S(-ld(r.p + (size_t)t * g.C + cc));
+    cg.proj(bf, pb);
+    S gb = S(0);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) gb += cg.gh[a] * bf[a];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) y[a] = -pb[a] + cg.gh[a] * bp;
+    y[NF] = gb + bp * cg.ig2;
+  }
+};
+
+template <class T, class S>
+__global__ void __launch_bounds__(64)
+scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, const double* __restrict__ lm_dev,
+                     S* __restrict__ zbuf) {
+  pdl_wait();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ncell) return;
+  const int N = g.N;
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
+  const S idt = pick<S>(g.idt, g.idtf);
+  const ThomasCell<T, S> tc(g, colour, q);
+  CellG3<S> cg;
+  cg.init(g, tc.cl.i, tc.cl.j, tc.cl.k);
+  auto rec = [&](int t, int e) -> S& { return zbuf[((size_t)t * kThomasRec + e) * ncell + q]; };
+
+  // ---- pass 1: ascending elimination ----------------------------------------
+  // carried from block t-1: M = O_{t-1}^T X_{t-1} (faces), m = O_{t-1}^T z_{t-1};
+  // from U_t (computed at block t-1): Sn = U_t^T P U_t, Rn = -U_t^T y_t
+  S M[NF][NF], m[NF], Sn[NF][NF], Rn[NF];
+  {
+    S U[NF][NF], y[NB];
+    tc.coupling(x.v + (size_t)g.F, idt, U);
+    tc.u_solve(r, 0, cg, y);
+#pragma unroll
+    for (int b = 0; b < NF; ++b) {
+      S w[NF], pw[NF];
+#pragma unroll
+      for (int a = 0; a < NF; ++a) w[a] = U[a][b];
+      cg.proj(w, pw);
+#pragma unroll
+      for (int a = 0; a < NF; ++a) Sn[a][b] = pw[a];   // P U column b (temporarily)
+    }
+    S PU[NF][NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+#pragma unroll
+      for (int b = 0; b < NF; ++b) PU[a][b] = Sn[a][b];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+#pragma unroll
+      for (int b = 0; b < NF; ++b) {
+        S s = S(0);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) s += U[c][a] * PU[c][b];
+        Sn[a][b] = s;
+      }
+      S s = S(0);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) s += U[c][a] * y[c];
+      Rn[a] = -s;
+      m[a] = S(0);
+#pragma unroll
+      for (int b = 0; b < NF; ++b) M[a][b] = S(0);
+    }
+  }
+  for (int t = 0; t < N; ++t) {
+    const int tv = t + 1;
+    // pivot block of v_tv
+    S A[NF][NF], B[NF][NB], qv[NB];
+    const T* rv = r.v + (size_t)tv * g.F;
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+#pragma unroll
+      for (int b = 0; b < NF; ++b) {
+        S v = Sn[a][b] - M[a][b];
+        if (tv < N) v += ((a == b ? cg.act[a] : S(0)) - cg.gh[a] * cg.g[b]) * idt * idt;
+        if (a == b) v += cg.act[a] > S(0) ? ((tv < N ? pick<S>(g.a, g.af) : S(0)) + lm) : S(1);
+        A[a][b] = v;
+      }
+      B[a][NF] = S(-ld(rv + tc.fidx[a])) * tc.act[a] + Rn[a] - m[a];
+    }
+    qv[NF] = S(-ld(r.pbar + (size_t)tv * g.C + tc.cc));
+    // coupling to v_{tv+1}: O = -P U_tv / dt, and the next block's Sn, Rn
+    if (tv < N) {
+      S U[NF][NF], y[NB];
+      tc.coupling(x.v + (size_t)(tv + 1) * g.F, idt, U);
+      tc.u_solve(r, tv, cg, y);
+#pragma unroll
+      for (int a = 0; a < NF; ++a) B[a][NF] += idt * cg.act[a] * y[a];
+      S PU[NF][NF];
+#pragma unroll
+      for (int b = 0; b < NF; ++b) {
+        S w[NF], pw[NF];
+#pragma unroll
+        for (int a = 0; a < NF; ++a) w[a] = U[a][b];
+        cg.proj(w, pw);
+#pragma unroll
+        for (int a = 0; a < NF; ++a) {
+          PU[a][b] = pw[a];
+          B[a][b] = -idt * pw[a];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < NF; ++a) {
+#pragma unroll
+        for (int b = 0; b < NF; ++b) {
+          S s = S(0);
+#pragma unroll
+          for (int c = 0; c < NF; ++c) s += U[c][a] * PU[c][b];
+          Sn[a][b] = s;
+        }
+        S s = S(0);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) s += U[c][a] * y[c];
+        Rn[a] = -s;
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < NF; ++a)
+#pragma unroll
+        for (int b = 0; b < NF; ++b) B[a][b] = S(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NF; ++c) qv[c] = S(0);
+    const S gam = shift_sym6(A, cg);
+    S Y[NB];
+    S O[NF][NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+#pragma unroll
+      for (int b = 0; b < NF; ++b) O[a][b] = B[a][b];
+    saddle_solve6<S, NB>(A, cg.g, B, qv, Y);
+    Y[NF] += gam * qv[NF];
+    // record Z_t = (X, multipliers) and z_t
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+#pragma unroll
+      for (int b = 0; b < NF; ++b) rec(t, a * NF + b) = B[a][b];
+      rec(t, NF * NF + a) = Y[a];
+      rec(t, NF * NF + NF + a) = B[a][NF];
+    }
+    rec(t, NF * NF + 2 * NF) = Y[NF];
+    // carried into the next pivot: M = O^T X, m = O^T z (faces)
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+#pragma unroll
+      for (int b = 0; b < NF; ++b) {
+        S s = S(0);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) s += O[c][a] * B[c][b];
+        M[a][b] = s;
+      }
+      S s = S(0);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) s += O[c][a] * B[c][NF];
+      m[a] = s;
+    }
+  }
+
+  // ---- pass 2: descending substitution, x_t overwrites z_t -------------------
+  {
+    S xn[NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) xn[a] = rec(N - 1, NF * NF + NF + a);
+    for (int t = N - 2; t >= 0; --t) {
+      S xt[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        S v = rec(t, NF * NF + NF + a);
+#pragma unroll
+        for (int b = 0; b < NF; ++b) v -= (a < NF ? rec(t, a * NF + b) : rec(t, NF * NF + b)) * xn[b];
+        xt[a] = v;
+      }
+#pragma unroll
+      for (int a = 0; a < NB; ++a) rec(t, NF * NF + NF + a) = xt[a];
+#pragma unroll
+      for (int a = 0; a < NF; ++a) xn[a] = xt[a];
+    }
+  }
+
+  // ---- pass 3: u blocks from the v solution, x += omega delta ---------------
+  const T om = pick<T>(g.omega, g.omegaf);
+  S xv0[NF];
+#pragma unroll
+  for (int a = 0; a < NF; ++a) xv0[a] = S(0);
+  for (int t = 0; t < N; ++t) {
+    S U[NF][NF], y[NB], xv1[NB];
+    tc.coupling(x.v + (size_t)(t + 1) * g.F, idt, U);
+    tc.u_solve(r, t, cg, y);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) xv1[a] = rec(t, NF * NF + NF + a);
+    S w[NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+      S v = S(0);
+#pragma unroll
+      for (int b = 0; b < NF; ++b) v -= U[a][b] * xv1[b];
+      if (t >= 1) v += idt * cg.act[a] * xv0[a];
+      w[a] = v;
+    }
+    S pw[NF];
+    cg.proj(w, pw);
+    S gw = S(0);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) gw += cg.gh[a] * w[a];
+    T* fu = x.u + (size_t)t * g.F;
+    T* fv = x.v + (size_t)(t + 1) * g.F;
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+      if (tc.act[a] > S(0)) {
+        const int f = tc.fidx[a];
+        fu[f] = fu[f] + om * T(y[a] - pw[a]);
+        fv[f] = fv[f] + om * T(xv1[a]);
+      }
+    T* fp = x.p + (size_t)t * g.C + tc.cc;
+    T* fpb = x.pbar + (size_t)(t + 1) * g.C + tc.cc;
+    *fp = *fp + om * T(y[NF] + gw);
+    *fpb = *fpb + om * T(xv1[NF]);
+#pragma unroll
+    for (int a = 0; a < NF; ++a) xv0[a] = xv1[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // transfers (Sec. 4.3 with a third axis): R = mean of the 8 children (cells) /
 // the 4 coincident fine faces (faces); P = trilinear, faces linear along the
 // normal and (3/4, 1/4) across, clamped at walls.  Time modes as the 2D
@@ -1044,9 +1321,35 @@ static void launch_scgs3_ts(const Geom& g, State<T> x, CState<T> r, int colour, 
               ncell, cpb, lm_dev);
 }
 
+// Colours with at least kThomasMinCells cells run the thread-per-cell block
+// Thomas kernel (given its scratch); smaller ones the cyclic reduction, whose
+// critical path is log N rather than N block steps.
+constexpr int kThomasMinCells = 16384;
+
+size_t scgs3_thomas_scratch_bytes(const Geom& g, size_t ssize) {
+  const size_t ncell = (size_t)((g.nx + 1) / 2) * ((g.ny + 1) / 2) * ((g.nz + 1) / 2);
+  return (size_t)kThomasRec * g.N * ncell * ssize;
+}
+
+template <class T, class S>
+static void launch_scgs3t(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev, void* scratch,
+                          cudaStream_t st) {
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+  const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
+  launch_pdl3(scgs3t_colour_kernel<T, S>, dim3((ncell + 63) / 64), dim3(64), 0, st, g, x, r, colour, ncell, lm_dev,
+              static_cast<S*>(scratch));
+}
+
 template <class T>
 void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
-                         const double* lm_dev) {
+                         const double* lm_dev, void* scratch) {
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
+  const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
+  if (scratch && ncell >= kThomasMinCells) {
+    if (solve_fp32) launch_scgs3t<T, float>(g, x, r, colour, lm_dev, scratch, st);
+    else launch_scgs3t<T, T>(g, x, r, colour, lm_dev, scratch, st);
+    return;
+  }
   if (solve_fp32) launch_scgs3_ts<T, float>(g, x, r, colour, lm_dev, st);
   else launch_scgs3_ts<T, T>(g, x, r, colour, lm_dev, st);
 }
@@ -1101,7 +1404,7 @@ void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, 
   template void launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,    \
                                                cudaStream_t, const double*);                                  \
   template void launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \
-                                       const double*);                                                        \
+                                       const double*, void*);                                                 \
   template void launch_kkt_force_rhs3<T>(const Geom&, const T*, T*, cudaStream_t);                            \
   template void launch_kkt_grad_rhs3<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);
 STC3_INST_T(float)

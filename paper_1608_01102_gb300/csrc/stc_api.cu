@@ -94,6 +94,11 @@ struct stc_problem {
   size_t star_bytes = 0;
   void* pscratch = nullptr;       // projection level arrays when they do not fit on chip
   void* adv3 = nullptr;           // 3D sweeps: term buffers and grid-barrier words
+  void* sc3 = nullptr;            // 3D SCGS: per-cell block Thomas records (finest level's size)
+  // forward simulation and its adjoint (allocated at their first use)
+  void *sim_gu = nullptr, *sim_a0 = nullptr, *sim_l0 = nullptr, *sim_aN = nullptr, *sim_w1 = nullptr,
+       *sim_w2 = nullptr, *sim_w3 = nullptr;
+  double* sim_grho = nullptr;     // dL/d rho_i, i = 0..N (fp64)
   std::vector<int> key_steps;
   std::vector<double> key_c;
   double* dscal = nullptr;  // device fp64 scalars
@@ -225,7 +230,7 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
-        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm);
+        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm, P->sc3);
       });
       if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
       count(P, 1);
@@ -467,17 +472,18 @@ void forward(stc_problem* P, const void* vel, void* rho, int* K, cudaStream_t st
 }
 
 void adjoint(stc_problem* P, const void* vel, const void* rho, const int* K, const void* base, double alpha,
-             double beta, void* out, cudaStream_t st) {
+             double beta, void* out, cudaStream_t st, int s_end = 1, void* mu_m1 = nullptr) {
   const Geom& g = P->lv[0].g;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     if (g.dim == 3)
       ck(launch_taylor_adjoint3<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
-                                   T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, P->derr, P->adv3, st),
+                                   T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, P->derr, P->adv3, st, s_end,
+                                   (T*)mu_m1),
          "taylor adjoint");
     else
       ck(launch_taylor_adjoint<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
-                                  T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st),
+                                  T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st, s_end, (T*)mu_m1),
          "taylor adjoint");
   });
   count(P, 1);
@@ -697,6 +703,83 @@ struct FieldRef {
   bool dbl = false;
 };
 
+// buffers of the forward simulation and its adjoint, allocated at first use
+// (a control problem that never simulates does not hold them)
+void sim_alloc(stc_problem* P) {
+  if (P->sim_gu) return;
+  const Geom& g = P->lv[0].g;
+  const size_t ts = P->ts, N = g.N;
+  P->sim_gu = dalloc(P, N * g.F * ts);
+  P->sim_a0 = dalloc(P, g.F * ts);
+  P->sim_l0 = dalloc(P, g.C * ts);
+  P->sim_aN = dalloc(P, g.F * ts);
+  P->sim_w1 = dalloc(P, g.F * ts);
+  P->sim_w2 = dalloc(P, g.F * ts);
+  P->sim_w3 = dalloc(P, g.F * ts);
+  P->sim_grho = (double*)dalloc(P, (N + 1) * g.C * sizeof(double));
+}
+
+// max |a - b| over the interior of a face slab into dscal[slot], b = a; and
+// max |b| into dscal[slot + 1]; returns the pair after a synchronising read
+std::pair<double, double> step_change(stc_problem* P, const void* a, void* b, cudaStream_t st, int slot) {
+  const Geom& g = P->lv[0].g;
+  ck(cudaMemsetAsync(P->dscal + slot, 0, 2 * sizeof(double), st), "memset");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_absdiff_max_copy<T>((const T*)a, (T*)b, (size_t)g.F, P->dscal + slot, st);
+    launch_absmax<T>((const T*)b, (size_t)g.F, P->dscal + slot + 1, P->derr, st);
+  });
+  count(P, 2);
+  const double d = read_scalar(P, slot);
+  return {d, P->hscal[slot + 1]};
+}
+
+// v_{t+1} from v_t and u_t: Picard v <- Q[v_t + dt (u_t - Adv(v))] until the
+// change is at most tol * max|v|; returns the iterations used
+int picard_step(stc_problem* P, int t, double tol, int max_iter) {
+  const Geom& g = P->lv[0].g;
+  const size_t fb = (size_t)g.F * P->ts;
+  char* v = (char*)P->lv[0].x.v;
+  const char* u = (const char*)P->lv[0].x.u;
+  ck(cudaMemcpyAsync(v + (t + 1) * fb, v + t * fb, fb, cudaMemcpyDeviceToDevice, P->st), "copy");
+  for (int it = 1; it <= max_iter; ++it) {
+    dispatch(P->dbl, [&](auto tag) {
+      using T = decltype(tag);
+      launch_picard_rhs<T>(g, (const T*)(v + t * fb), (const T*)(u + t * fb), (const T*)(v + (t + 1) * fb), g.dt,
+                           (T*)P->sim_w1, P->st);
+    });
+    count(P, 1);
+    project(P, P->sim_w1, 1, P->st);
+    const auto dm = step_change(P, P->sim_w1, v + (t + 1) * fb, P->st, 6);
+    if (!(dm.first == dm.first)) fail(STC_ERR_DIVERGED, "non-finite velocity in the implicit step");
+    if (dm.first <= tol * std::max(dm.second, 1e-300)) return it;
+  }
+  fail(STC_ERR_NOT_CONVERGED, "implicit Navier-Stokes step: Picard iteration did not converge");
+  return max_iter;
+}
+
+// z = Q[a - dt dAdv(v_{t+1})^T z] (the transposed step), z into sim_w2
+int picard_adjoint_step(stc_problem* P, int t, const void* a, double tol, int max_iter) {
+  const Geom& g = P->lv[0].g;
+  const size_t fb = (size_t)g.F * P->ts;
+  const char* v = (const char*)P->lv[0].x.v;
+  ck(cudaMemsetAsync(P->sim_w2, 0, fb, P->st), "memset");
+  for (int it = 1; it <= max_iter; ++it) {
+    dispatch(P->dbl, [&](auto tag) {
+      using T = decltype(tag);
+      launch_picard_adj_rhs<T>(g, (const T*)(v + (t + 1) * fb), (const T*)a, (const T*)P->sim_w2, g.dt,
+                               (T*)P->sim_w3, P->st);
+    });
+    count(P, 1);
+    project(P, P->sim_w3, 1, P->st);
+    const auto dm = step_change(P, P->sim_w3, P->sim_w2, P->st, 6);
+    if (!(dm.first == dm.first)) fail(STC_ERR_DIVERGED, "non-finite value in the transposed implicit step");
+    if (dm.first <= tol * std::max(dm.second, 1e-300)) return it;
+  }
+  fail(STC_ERR_NOT_CONVERGED, "transposed implicit step: iteration did not converge");
+  return max_iter;
+}
+
 FieldRef field_ref(stc_problem* P, int field, int level) {
   const int nl = (int)P->lv.size();
   if (level < 0 || level >= nl) fail(STC_ERR_INVALID_ARG, "level out of range");
@@ -747,6 +830,11 @@ FieldRef field_ref(stc_problem* P, int field, int level) {
     case STC_FIELD_KKT_U: r.ptr = P->uk; r.count = N * g.F; break;
     case STC_FIELD_KKT_G: r.ptr = P->gk; r.count = (N + 1) * g.F; break;
     case STC_FIELD_MTERM: r.ptr = P->mterm; r.count = (N + 1) * g.C; r.kind = 1; break;
+    case STC_FIELD_SIM_GRAD_RHO: sim_alloc(P); r.ptr = P->sim_grho; r.count = (N + 1) * g.C; r.kind = 1; break;
+    case STC_FIELD_SIM_GRAD_U: sim_alloc(P); r.ptr = P->sim_gu; r.count = N * g.F; break;
+    case STC_FIELD_SIM_ADJ_V0: sim_alloc(P); r.ptr = P->sim_a0; r.count = g.F; break;
+    case STC_FIELD_SIM_ADJ_RHO0: sim_alloc(P); r.ptr = P->sim_l0; r.count = g.C; break;
+    case STC_FIELD_SIM_ADJ_VN: sim_alloc(P); r.ptr = P->sim_aN; r.count = g.F; break;
     default: fail(STC_ERR_INVALID_ARG, "unknown field id");
   }
   return r;
@@ -850,7 +938,8 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
   Geom g0 = make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt);
   if (g0.dim == 3) {
-    total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts);
+    total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts) +
+             b(scgs3_thomas_scratch_bytes(g0, ts));
   } else if (project_needs_scratch(g0, ts)) {
     total += b((N + 1) * project_smem(g0, ts));
   }
@@ -1014,6 +1103,7 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     if (d3) {
       P->pscratch = dalloc(P, project3_scratch_elems(g0, N + 1) * ts);
       P->adv3 = dalloc(P, advect3_scratch_bytes(g0, ts));
+      P->sc3 = dalloc(P, scgs3_thomas_scratch_bytes(g0, P->dbl ? 8 : 4));
     } else if (project_needs_scratch(g0, ts)) {
       P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
     }
@@ -1293,6 +1383,84 @@ stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int
   if (ny) *ny = g.ny;
   if (nz) *nz = g.dim == 3 ? g.nz : 0;
   return STC_OK;
+}
+
+stc_status stc_simulate(stc_problem* p, double picard_tol, int max_iter, int* iters) {
+  if (!p || !(picard_tol > 0) || max_iter < 1) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    sim_alloc(p);
+    const Geom& g = p->lv[0].g;
+    int total = 0;
+    for (int t = 0; t < g.N; ++t) total += picard_step(p, t, picard_tol, max_iter);
+    forward(p, p->lv[0].x.v, p->rho, p->K, p->st);
+    p->rho_at_vstar = false;
+    (void)read_scalar(p, 0);   // surfaces the sweep's device error flags
+    if (iters) *iters = total;
+  });
+}
+
+stc_status stc_simulate_adjoint(stc_problem* p, double picard_tol, int max_iter, int with_step0, int* iters) {
+  if (!p || !(picard_tol > 0) || max_iter < 1 || with_step0 < 0 || with_step0 > 1) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    sim_alloc(p);
+    const Geom& g = p->lv[0].g;
+    const size_t N = g.N, fb = (size_t)g.F * p->ts;
+    // density adjoint: the sweep's metric terms are -dL/drho
+    launch_sim_copy<double, double>((N + 1) * g.C, p->sim_grho, -1.0, p->mterm, p->st);
+    ck(cudaMemsetAsync(p->dens, 0, (N + 1) * fb, p->st), "memset");
+    if (with_step0) ck(cudaMemsetAsync(p->sim_l0, 0, (size_t)g.C * p->ts, p->st), "memset");
+    adjoint(p, p->lv[0].x.v, p->rho, p->K, nullptr, 0.0, 1.0, p->dens, p->st, with_step0 ? 0 : 1,
+            with_step0 ? p->sim_l0 : nullptr);
+    if (!with_step0) ck(cudaMemsetAsync(p->sim_l0, 0, (size_t)g.C * p->ts, p->st), "memset");   // not formed
+    // velocity adjoint, i = N-1 .. 0: xi = Pi_i^T a = dt z, a <- dens_i + z
+    ck(cudaMemcpyAsync(p->sim_a0, p->sim_aN, fb, cudaMemcpyDeviceToDevice, p->st), "copy");
+    int total = 0;
+    for (int i = (int)N - 1; i >= 0; --i) {
+      total += picard_adjoint_step(p, i, p->sim_a0, picard_tol, max_iter);
+      dispatch(p->dbl, [&](auto tag) {
+        using T = decltype(tag);
+        launch_sim_axpby<T>((size_t)g.F, g.dt, (const T*)p->sim_w2, 0.0, nullptr,
+                            (T*)((char*)p->sim_gu + i * fb), p->st);
+        launch_sim_axpby<T>((size_t)g.F, 1.0, (const T*)((char*)p->dens + i * fb), 1.0, (const T*)p->sim_w2,
+                            (T*)p->sim_a0, p->st);
+      });
+      count(p, 2);
+    }
+    (void)read_scalar(p, 0);
+    if (iters) *iters = total;
+  });
+}
+
+stc_status stc_copy_field_device(stc_problem* p, int field, int level, void* buffer, size_t len, int buffer_is_double,
+                                 int to_field, double scale) {
+  if (!p || !buffer || buffer_is_double < 0 || buffer_is_double > 1 || to_field < 0 || to_field > 1) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() {
+    FieldRef r = field_ref(p, field, level);
+    if (len != r.count) fail(STC_ERR_INVALID_ARG, "length does not match the field size");
+    const bool fdbl = r.kind == 1 || r.dbl;
+    auto go = [&](auto ftag, auto btag) {
+      using Tf = decltype(ftag);
+      using Tb = decltype(btag);
+      if (to_field) launch_sim_copy<Tb, Tf>(len, (const Tb*)buffer, scale, (Tf*)r.ptr, p->st);
+      else launch_sim_copy<Tf, Tb>(len, (const Tf*)r.ptr, scale, (Tb*)buffer, p->st);
+    };
+    if (fdbl && buffer_is_double) go(double(), double());
+    else if (fdbl) go(double(), float());
+    else if (buffer_is_double) go(float(), double());
+    else go(float(), float());
+    count(p, 1);
+    check_launch("copy");
+    if (to_field && (field == STC_FIELD_VSTAR || field == STC_FIELD_RHO)) p->rho_at_vstar = false;
+  });
 }
 
 stc_status stc_level_steps(const stc_problem* p, int level, int* num_steps, double* dt) {

@@ -20,10 +20,12 @@ void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, 
 template <class T>
 void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
                                 cudaStream_t st, const double* only_if_undone = nullptr);
-// lm_dev (optional): device fp64 Levenberg-Marquardt shift of the v blocks, else g.lm
+// lm_dev (optional): device fp64 Levenberg-Marquardt shift of the v blocks, else g.lm;
+// scratch3 (3D, optional): scgs3_thomas_scratch_bytes of the finest level, which
+// lets large colours run the thread-per-cell block Thomas kernel
 template <class T>
 void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
-                        const double* lm_dev = nullptr);
+                        const double* lm_dev = nullptr, void* scratch3 = nullptr);
 size_t scgs_smem_bytes(int N, size_t tsize);
 int colour_extent(int n, int parity);
 template <class Tf, class Tc>
@@ -59,10 +61,13 @@ cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, d
                                   cudaStream_t st);
 // Backward adjoint sweep (Eq. KKTPO): mu_{s-1} = T_s^T mu_s - m_s, mu_{N-1} = -m_N;
 // out_s = alpha * base_s + beta * (dA[rho_s, v_s]/dv)^T mu_s for s = 1..N-1.
+// s_end = 1: steps N-1..1 (the AO sweep; v_0 is data).  s_end = 0 also runs step
+// 0: out_0 and, into mu_m1 (C entries, may be null), T_0^T mu_0 - m_0 (the
+// adjoint density of rho_0, for chaining simulation segments); mu_0 stays mu_0.
 template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int s_end = 1, T* mu_m1 = nullptr);
 // m_s = c * sum_l G_l^T G_l (rho_s - rho*_s) (fp64) into mterm slab s.
 template <class T>
 void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
@@ -119,8 +124,9 @@ void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<
                                  cudaStream_t st, const double* only_if_undone);
 template <class T>
 void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
-                         const double* lm_dev);
+                         const double* lm_dev, void* scratch);
 size_t scgs3_smem_bytes(int N, size_t tsize);   // shared memory of one cell's SCGS solve
+size_t scgs3_thomas_scratch_bytes(const Geom& g, size_t ssize);
 template <class Tf, class Tc>
 void launch_restrict3(const Geom& gf, const Geom& gc, CState<Tf> s, State<Tc> d, State<Tc> d2, cudaStream_t st);
 template <class Tf, class Tc>
@@ -141,7 +147,7 @@ cudaError_t launch_taylor_forward3(const Geom& g, const T* vel, T* rho, int* K, 
 template <class T>
 cudaError_t launch_taylor_adjoint3(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                    T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax, int* err,
-                                   void* scratch, cudaStream_t st);
+                                   void* scratch, cudaStream_t st, int s_end = 1, T* mu_m1 = nullptr);
 template <class T>
 void launch_metric3(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
                     double* out, double* tmp0, double* tmp1, cudaStream_t st);
@@ -151,5 +157,19 @@ bool project3_supported(const Geom& g);
 template <class T>
 cudaError_t launch_project3(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch);
 int project3_launches(const Geom& g, int vcycles);
+
+// --- forward simulation and its adjoint (sim_kernels.cu) --------------------
+// out = v_prev + dt (u - Adv(v)) (interior faces; walls 0)
+template <class T>
+void launch_picard_rhs(const Geom& g, const T* v_prev, const T* u, const T* v, double dt, T* out, cudaStream_t st);
+// out = y - dt dAdv(v)^T z (interior faces; walls 0)
+template <class T>
+void launch_picard_adj_rhs(const Geom& g, const T* v, const T* y, const T* z, double dt, T* out, cudaStream_t st);
+// out = a x + b y (y may be null)
+template <class T>
+void launch_sim_axpby(size_t n, double a, const T* x, double b, const T* y, T* out, cudaStream_t st);
+// d = scale * s with conversion
+template <class Ts, class Td>
+void launch_sim_copy(size_t n, const Ts* s, double scale, Td* d, cudaStream_t st);
 
 }  // namespace stc

@@ -18,7 +18,8 @@ P_int = ctypes.POINTER(ctypes.c_int)
 
 FIELDS = dict(V=0, PBAR=1, U=2, P=3, RES_V=4, RES_PBAR=5, RES_U=6, RES_P=7, Z=8, VSTAR=9, LAMBDA=10,
               RHO=11, MU=12, W=13, Y=14, KKT_U=15, KKT_G=16, MTERM=17, RES_IN_V=18, RES_IN_PBAR=19,
-              RES_IN_U=20, RES_IN_P=21, XOLD_V=22, XOLD_PBAR=23, XOLD_U=24, XOLD_P=25)
+              RES_IN_U=20, RES_IN_P=21, XOLD_V=22, XOLD_PBAR=23, XOLD_U=24, XOLD_P=25,
+              SIM_GRAD_RHO=26, SIM_GRAD_U=27, SIM_ADJ_V0=28, SIM_ADJ_RHO0=29, SIM_ADJ_VN=30)
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
           6: "UNSUPPORTED", 7: "BUSY"}
@@ -88,6 +89,9 @@ SIGNATURES = {
     "stc_level_info": (c_int, [c_void_p, P_int, c_int, P_int, P_int]),
     "stc_level_steps": (c_int, [c_void_p, c_int, P_int, P_double]),
     "stc_level_dims": (c_int, [c_void_p, c_int, P_int, P_int, P_int]),
+    "stc_simulate": (c_int, [c_void_p, c_double, c_int, P_int]),
+    "stc_simulate_adjoint": (c_int, [c_void_p, c_double, c_int, c_int, P_int]),
+    "stc_copy_field_device": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, c_int, c_int, c_double]),
     "stc_advect": (c_int, [c_void_p, c_int]),
     "stc_get_taylor_orders": (c_int, [c_void_p, P_int, c_size_t]),
     "stc_metric_terms": (c_int, [c_void_p]),
@@ -214,9 +218,13 @@ class Problem:
         F, C = grid_sizes(*self.level_shape(level))
         N = self.level_steps(level)[0] if level > 0 else self.N
         face_np1 = ("V", "RES_V", "RES_IN_V", "XOLD_V", "KKT_G")
-        cell_np1 = ("PBAR", "RES_PBAR", "RES_IN_PBAR", "XOLD_PBAR", "RHO", "MTERM")
-        face_n = ("U", "RES_U", "RES_IN_U", "XOLD_U", "Z", "VSTAR", "LAMBDA", "W", "Y", "KKT_U")
+        cell_np1 = ("PBAR", "RES_PBAR", "RES_IN_PBAR", "XOLD_PBAR", "RHO", "MTERM", "SIM_GRAD_RHO")
+        face_n = ("U", "RES_U", "RES_IN_U", "XOLD_U", "Z", "VSTAR", "LAMBDA", "W", "Y", "KKT_U", "SIM_GRAD_U")
         cell_n = ("P", "RES_P", "RES_IN_P", "XOLD_P", "MU")
+        if name in ("SIM_ADJ_V0", "SIM_ADJ_VN"):
+            return (1, F)
+        if name == "SIM_ADJ_RHO0":
+            return (1, C)
         if name in face_np1:
             return (N + 1, F)
         if name in cell_np1:
@@ -335,6 +343,24 @@ class Problem:
 
     def forces(self):
         return self.get("U")
+
+    # forward simulation and its adjoint ------------------------------------
+    def simulate(self, tol=1e-6, max_iter=100):
+        """stc_simulate: v_1..v_N and rho_1..rho_N from v_0, rho_0 and U;
+        returns the Picard iterations used."""
+        it = c_int()
+        _check(self.lib.stc_simulate(self.h, tol, max_iter, ctypes.byref(it)))
+        return it.value
+
+    def simulate_adjoint(self, tol=1e-6, max_iter=100, with_step0=False):
+        it = c_int()
+        _check(self.lib.stc_simulate_adjoint(self.h, tol, max_iter, 1 if with_step0 else 0, ctypes.byref(it)))
+        return it.value
+
+    def copy_device(self, name, ptr, count, is_double, to_field, scale=1.0, level=0):
+        """Device-to-device copy between a field and the buffer at device address ptr."""
+        _check(self.lib.stc_copy_field_device(self.h, FIELDS[name], level, c_void_p(int(ptr)), count,
+                                              1 if is_double else 0, 1 if to_field else 0, float(scale)))
 
     def launch_count(self):
         n = ctypes.c_longlong()

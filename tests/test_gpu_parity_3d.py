@@ -201,6 +201,28 @@ def test_scgs_sweep_3d(prec, shape, N):
             assert err <= tol * np.linalg.norm(d) + floor, (l, k, err / max(np.linalg.norm(d), 1e-300))
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_scgs_sweep_3d_thread_per_cell(prec):
+    """A colour of >= 16384 cells runs the thread-per-cell block Thomas kernel
+    (64 x 64 x 32: 16384 cells per colour on the finest level).  From the zero
+    state towards a smooth target: the first sweep builds a velocity, the
+    second runs with the Adv coupling of that velocity.  (A random state with
+    O(1) pressures at h = 1/64 is amplified ~1e16-fold by the colour sweeps --
+    no test of anything.)"""
+    nx, ny, nz, N = 64, 64, 32, 2
+    P, G = make_pair3(nx, ny, nz, N, precision=prec)
+    z = velocity3(nx, ny, nz, N, amp=0.5, seed=45)[1:]
+    G.set("Z", z)
+    x = kkt.zero_state(P)
+    res = kkt.zero_state(P, P.grid)
+    for s in range(2):
+        G.smooth(level=0, sweeps=1)
+        scgs.sweep(P, P.grid, x, z, res)
+        got = G.get_state()
+        for k in x:
+            assert rel(got[k], x[k]) < (1e-9 if prec == 1 else 2e-4), (s, k, rel(got[k], x[k]))
+
+
 # ---------------------------------------------------------------------------
 # a9: restriction and prolongation-correction
 # ---------------------------------------------------------------------------
