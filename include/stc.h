@@ -221,7 +221,9 @@ stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int
  * stc_simulate solves each implicit step of Eq. NSA/NSB,
  *   (v_{i+1} - v_i)/dt + Adv(v_{i+1}) - u_i + grad p = 0,  div v_{i+1} = 0,
  * by the Picard iteration v <- Q[v_i + dt (u_i - Adv(v))] until the change is
- * at most picard_tol * max|v| (STC_ERR_NOT_CONVERGED after max_iter), writes
+ * at most picard_tol * max|v|, or has stopped halving after 8 iterations within
+ * 100 picard_tol * max|v| (the rounding floor of fp32), STC_ERR_NOT_CONVERGED
+ * after max_iter; writes
  * v_1..v_N, then advects rho_1..rho_N with v_0..v_{N-1} (Eq. Conv; Taylor
  * orders as stc_advect).  iters (may be NULL): Picard iterations in total.
  * The buffers of both calls are allocated at the first call (not counted by

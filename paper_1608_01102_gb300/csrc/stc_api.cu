@@ -734,6 +734,17 @@ std::pair<double, double> step_change(stc_problem* P, const void* a, void* b, cu
   return {d, P->hscal[slot + 1]};
 }
 
+// Convergence of the (transposed) Picard iteration: the change d at most tol *
+// max|x|, or -- the rounding floor of the state type -- d no longer halving
+// after 8 iterations while within 100 tol * max|x| (the iteration map is a
+// fixed linear-plus-Adv map whose change cannot fall below its rounding).
+bool picard_done(double d, double xmax, double tol, int it, double* prev) {
+  const double ref = tol * std::max(xmax, 1e-300);
+  const bool done = d <= ref || (it >= 8 && d >= 0.5 * *prev && d <= 100.0 * ref);
+  *prev = d;
+  return done;
+}
+
 // v_{t+1} from v_t and u_t: Picard v <- Q[v_t + dt (u_t - Adv(v))] until the
 // change is at most tol * max|v|; returns the iterations used
 int picard_step(stc_problem* P, int t, double tol, int max_iter) {
@@ -742,6 +753,7 @@ int picard_step(stc_problem* P, int t, double tol, int max_iter) {
   char* v = (char*)P->lv[0].x.v;
   const char* u = (const char*)P->lv[0].x.u;
   ck(cudaMemcpyAsync(v + (t + 1) * fb, v + t * fb, fb, cudaMemcpyDeviceToDevice, P->st), "copy");
+  double prev = std::numeric_limits<double>::infinity();
   for (int it = 1; it <= max_iter; ++it) {
     dispatch(P->dbl, [&](auto tag) {
       using T = decltype(tag);
@@ -752,9 +764,10 @@ int picard_step(stc_problem* P, int t, double tol, int max_iter) {
     project(P, P->sim_w1, 1, P->st);
     const auto dm = step_change(P, P->sim_w1, v + (t + 1) * fb, P->st, 6);
     if (!(dm.first == dm.first)) fail(STC_ERR_DIVERGED, "non-finite velocity in the implicit step");
-    if (dm.first <= tol * std::max(dm.second, 1e-300)) return it;
+    if (picard_done(dm.first, dm.second, tol, it, &prev)) return it;
   }
-  fail(STC_ERR_NOT_CONVERGED, "implicit Navier-Stokes step: Picard iteration did not converge");
+  fail(STC_ERR_NOT_CONVERGED, "implicit Navier-Stokes step: Picard iteration did not converge (change " +
+                                  std::to_string(prev) + ")");
   return max_iter;
 }
 
@@ -764,6 +777,7 @@ int picard_adjoint_step(stc_problem* P, int t, const void* a, double tol, int ma
   const size_t fb = (size_t)g.F * P->ts;
   const char* v = (const char*)P->lv[0].x.v;
   ck(cudaMemsetAsync(P->sim_w2, 0, fb, P->st), "memset");
+  double prev = std::numeric_limits<double>::infinity();
   for (int it = 1; it <= max_iter; ++it) {
     dispatch(P->dbl, [&](auto tag) {
       using T = decltype(tag);
@@ -774,9 +788,10 @@ int picard_adjoint_step(stc_problem* P, int t, const void* a, double tol, int ma
     project(P, P->sim_w3, 1, P->st);
     const auto dm = step_change(P, P->sim_w3, P->sim_w2, P->st, 6);
     if (!(dm.first == dm.first)) fail(STC_ERR_DIVERGED, "non-finite value in the transposed implicit step");
-    if (dm.first <= tol * std::max(dm.second, 1e-300)) return it;
+    if (picard_done(dm.first, dm.second, tol, it, &prev)) return it;
   }
-  fail(STC_ERR_NOT_CONVERGED, "transposed implicit step: iteration did not converge");
+  fail(STC_ERR_NOT_CONVERGED, "transposed implicit step: iteration did not converge (change " +
+                                  std::to_string(prev) + ")");
   return max_iter;
 }
 
