@@ -42,10 +42,13 @@ class Problem:
     self_advection: bool = True      # False drops Adv (linear saddle problem; pins only)
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
     nz: int = 0                      # 0: the 2D grid nx x ny; > 0: the 3D grid nx x ny x nz
+    periodic: bool = False           # 3D only: every axis wraps (the paper's periodic benchmarks)
 
     def __post_init__(self):
         self.h = 1.0 / self.nx
-        self.grid = (mac.Grid3(self.nx, self.ny, self.nz, self.h) if self.nz
+        if self.periodic and not self.nz:
+            raise ValueError("periodic boundaries are built for the 3D grid")
+        self.grid = (mac.Grid3(self.nx, self.ny, self.nz, self.h, self.periodic) if self.nz
                      else mac.Grid(self.nx, self.ny, self.h))
         self.rho0 = np.asarray(self.rho0, float).ravel()
         if self.v0 is None:
@@ -61,7 +64,7 @@ class Problem:
             return np.zeros(self.grid.C)
         star, c = self.keyframes[i]
         return metric.apply_metric(self.nx, self.ny, rho_i - star, self.metric_levels,
-                                   self.metric_sigma0, c, self.nz)
+                                   self.metric_sigma0, c, self.nz, self.periodic)
 
     def misfit(self, rhos):
         e = 0.0

@@ -83,12 +83,17 @@ class Grid:
 
 
 class Grid3:
-    """Index bookkeeping for one nx-by-ny-by-nz MAC grid with cell size h."""
+    """Index bookkeeping for one nx-by-ny-by-nz MAC grid with cell size h.
+
+    periodic=True: every axis wraps (no walls).  The face layout keeps n + 1
+    slots per axis; slot n is not a face (it stays zero) and face 0 lies
+    between cells n-1 and 0.  Edges and neighbour indices wrap likewise."""
 
     dim = 3
 
-    def __init__(self, nx, ny, nz, h):
+    def __init__(self, nx, ny, nz, h, periodic=False):
         self.nx, self.ny, self.nz, self.h = int(nx), int(ny), int(nz), float(h)
+        self.periodic = bool(periodic)
         self.C = self.nx * self.ny * self.nz
         self.Fx = self.nz * self.ny * (self.nx + 1)
         self.Fy = self.nz * (self.ny + 1) * self.nx
@@ -125,12 +130,13 @@ class Grid3:
                 (self.nz + 1, self.ny, self.nx))
 
     def interior_faces(self):
+        lo = 0 if self.periodic else 1
         mx = np.zeros(self.face_shapes()[0])
-        mx[:, :, 1:self.nx] = 1.0
+        mx[:, :, lo:self.nx] = 1.0
         my = np.zeros(self.face_shapes()[1])
-        my[:, 1:self.ny, :] = 1.0
+        my[:, lo:self.ny, :] = 1.0
         mz = np.zeros(self.face_shapes()[2])
-        mz[1:self.nz] = 1.0
+        mz[lo:self.nz] = 1.0
         return self.join(mx, my, mz)
 
     def split(self, v):
@@ -144,10 +150,10 @@ class Grid3:
                                np.asarray(vz).ravel()])
 
     def coarse(self):
-        return Grid3(self.nx // 2, self.ny // 2, self.nz // 2, 2.0 * self.h)
+        return Grid3(self.nx // 2, self.ny // 2, self.nz // 2, 2.0 * self.h, self.periodic)
 
     def key(self):
-        return (self.nx, self.ny, self.nz, self.h)
+        return (self.nx, self.ny, self.nz, self.h, self.periodic)
 
     def cell_shape(self):
         return (self.nz, self.ny, self.nx)
@@ -293,7 +299,68 @@ def _ops3(nx, ny, nz, h):
                 terms=terms, terms_T=[(a.T.tocsr(), b.T.tocsr()) for a, b in terms])
 
 
+@lru_cache(maxsize=16)
+def _ops3p(nx, ny, nz, h):
+    """The operators of _ops3 on the triply periodic grid: the same stencils
+    with every neighbour index taken modulo the axis length; all faces with
+    normal index < n are faces, all edges interior."""
+    g = Grid3(nx, ny, nz, h, periodic=True)
+    ih = 1.0 / h
+    ar = np.arange
+
+    def mesh(kr, jr, ir):
+        return np.meshgrid(kr, jr, ir, indexing="ij")
+
+    wx, wy, wz = (lambda a: a % nx), (lambda a: a % ny), (lambda a: a % nz)
+    K, J, I = mesh(ar(nz), ar(ny), ar(nx))
+    c = g.cell(K, J, I)
+    D = _sparse([(c, g.xf(K, J, wx(I + 1)), ih), (c, g.xf(K, J, I), -ih),
+                 (c, g.yf(K, wy(J + 1), I), ih), (c, g.yf(K, J, I), -ih),
+                 (c, g.zf(wz(K + 1), J, I), ih), (c, g.zf(K, J, I), -ih)], (g.C, g.F))
+    fx, fy, fz = g.xf(K, J, I), g.yf(K, J, I), g.zf(K, J, I)     # every face, indexed by (k, j, i)
+    G = _sparse([(fx, g.cell(K, J, I), ih), (fx, g.cell(K, J, wx(I - 1)), -ih),
+                 (fy, g.cell(K, J, I), ih), (fy, g.cell(K, wy(J - 1), I), -ih),
+                 (fz, g.cell(K, J, I), ih), (fz, g.cell(wz(K - 1), J, I), -ih)], (g.F, g.C))
+    ex, ey, ez = g.xe(K, J, I), g.ye(K, J, I), g.ze(K, J, I)      # every edge, indexed by (k, j, i)
+    Wx = _sparse([(ex, g.zf(K, J, I), ih), (ex, g.zf(K, wy(J - 1), I), -ih),
+                  (ex, g.yf(K, J, I), -ih), (ex, g.yf(wz(K - 1), J, I), ih)], (g.Ex, g.F))
+    Wy = _sparse([(ey, g.xf(K, J, I), ih), (ey, g.xf(wz(K - 1), J, I), -ih),
+                  (ey, g.zf(K, J, I), -ih), (ey, g.zf(K, J, wx(I - 1)), ih)], (g.Ey, g.F))
+    Wz = _sparse([(ez, g.yf(K, J, I), ih), (ez, g.yf(K, J, wx(I - 1)), -ih),
+                  (ez, g.xf(K, J, I), -ih), (ez, g.xf(K, wy(J - 1), I), ih)], (g.Ez, g.F))
+    Oy_x = _sparse([(fx, g.ye(K, J, I), .5), (fx, g.ye(wz(K + 1), J, I), .5)], (g.F, g.Ey))
+    Oz_x = _sparse([(fx, g.ze(K, J, I), .5), (fx, g.ze(K, wy(J + 1), I), .5)], (g.F, g.Ez))
+    Oz_y = _sparse([(fy, g.ze(K, J, I), .5), (fy, g.ze(K, J, wx(I + 1)), .5)], (g.F, g.Ez))
+    Ox_y = _sparse([(fy, g.xe(K, J, I), .5), (fy, g.xe(wz(K + 1), J, I), .5)], (g.F, g.Ex))
+    Ox_z = _sparse([(fz, g.xe(K, J, I), .5), (fz, g.xe(K, wy(J + 1), I), .5)], (g.F, g.Ex))
+    Oy_z = _sparse([(fz, g.ye(K, J, I), .5), (fz, g.ye(K, J, wx(I + 1)), .5)], (g.F, g.Ey))
+    q = 0.25
+    im, jm, km = wx(I - 1), wy(J - 1), wz(K - 1)
+    ip, jp, kp = wx(I + 1), wy(J + 1), wz(K + 1)
+    Tz_x = _sparse([(fx, g.zf(K, J, im), q), (fx, g.zf(K, J, I), q),
+                    (fx, g.zf(kp, J, im), q), (fx, g.zf(kp, J, I), q)], (g.F, g.F))
+    Ty_x = _sparse([(fx, g.yf(K, J, im), q), (fx, g.yf(K, J, I), q),
+                    (fx, g.yf(K, jp, im), q), (fx, g.yf(K, jp, I), q)], (g.F, g.F))
+    Tx_y = _sparse([(fy, g.xf(K, jm, I), q), (fy, g.xf(K, jm, ip), q),
+                    (fy, g.xf(K, J, I), q), (fy, g.xf(K, J, ip), q)], (g.F, g.F))
+    Tz_y = _sparse([(fy, g.zf(K, jm, I), q), (fy, g.zf(K, J, I), q),
+                    (fy, g.zf(kp, jm, I), q), (fy, g.zf(kp, J, I), q)], (g.F, g.F))
+    Ty_z = _sparse([(fz, g.yf(km, J, I), q), (fz, g.yf(km, jp, I), q),
+                    (fz, g.yf(K, J, I), q), (fz, g.yf(K, jp, I), q)], (g.F, g.F))
+    Tx_z = _sparse([(fz, g.xf(km, J, I), q), (fz, g.xf(km, J, ip), q),
+                    (fz, g.xf(K, J, I), q), (fz, g.xf(K, J, ip), q)], (g.F, g.F))
+    M1 = (Oy_x @ Wy + Oz_y @ Wz + Ox_z @ Wx).tocsr()
+    T1 = (Tz_x + Tx_y + Ty_z).tocsr()
+    M2 = (-(Oz_x @ Wz + Ox_y @ Wx + Oy_z @ Wy)).tocsr()
+    T2 = (Ty_x + Tz_y + Tx_z).tocsr()
+    terms = [(M1, T1), (M2, T2)]
+    return dict(grid=g, D=D, G=G, Wx=Wx, Wy=Wy, Wz=Wz, mask=g.interior_faces(), D_T=D.T.tocsr(),
+                terms=terms, terms_T=[(a.T.tocsr(), b.T.tocsr()) for a, b in terms])
+
+
 def ops(grid):
+    if grid.dim == 3 and getattr(grid, "periodic", False):
+        return _ops3p(grid.nx, grid.ny, grid.nz, grid.h)
     if grid.dim == 3:
         return _ops3(grid.nx, grid.ny, grid.nz, grid.h)
     return _ops(grid.nx, grid.ny, grid.h)
@@ -400,7 +467,32 @@ def _quick_weights(vn):
     return wpos, 1.0 - wpos
 
 
+def _quick_face_matrix3p(g, v):
+    """QUICK face values on the periodic grid: faces 0..n-1 of every axis,
+    lower cell p-1 and the far cells taken modulo n."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    vx, vy, vz = g.split(v)
+    K, J, I = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    entries = []
+    for axis, (vn, n) in enumerate(((vx[:, :, :nx], nx), (vy[:, :ny, :], ny), (vz[:nz], nz))):
+        wp, wn = _quick_weights(vn)
+        crd = [I, J, K][axis]
+
+        def cell(p):
+            c = [K, J, I]
+            c[2 - axis] = p % n
+            return g.cell(*c)
+
+        f = [g.xf, g.yf, g.zf][axis](K, J, I)
+        L, R, LL, RR = cell(crd - 1), cell(crd), cell(crd - 2), cell(crd + 1)
+        entries += [(f, L, wp * 6 / 8), (f, R, wp * 3 / 8), (f, LL, -wp / 8),
+                    (f, R, wn * 6 / 8), (f, L, wn * 3 / 8), (f, RR, -wn / 8)]
+    return _sparse(entries, (g.F, g.C))
+
+
 def _quick_face_matrix3(g, v):
+    if g.periodic:
+        return _quick_face_matrix3p(g, v)
     nx, ny, nz = g.nx, g.ny, g.nz
     vx, vy, vz = g.split(v)
     ar = np.arange

@@ -24,21 +24,22 @@ def gaussian_taps(sigma):
     return w / w.sum()
 
 
-def blur_matrix_1d(n, sigma):
-    """n x n matrix of one normalised, truncated, clamp-to-edge Gaussian blur."""
+def blur_matrix_1d(n, sigma, periodic=False):
+    """n x n matrix of one normalised, truncated Gaussian blur, clamp-to-edge
+    (or wrapping around on a periodic axis)."""
     w = gaussian_taps(sigma)
     R = (len(w) - 1) // 2
     M = np.zeros((n, n))
     for a in range(n):
         for t in range(-R, R + 1):
-            b = min(max(a + t, 0), n - 1)
+            b = (a + t) % n if periodic else min(max(a + t, 0), n - 1)
             M[a, b] += w[t + R]
     return M
 
 
-def apply_metric(nx, ny, x, levels, sigma0=1.0, c=1.0, nz=0):
+def apply_metric(nx, ny, x, levels, sigma0=1.0, c=1.0, nz=0, periodic=False):
     """C x = c sum_l G_l^T G_l x for a centre field x (flattened, i fastest);
-    nz > 0 makes it a 3D field of shape (nz, ny, nx)."""
+    nz > 0 makes it a 3D field of shape (nz, ny, nx); periodic: the filters wrap."""
     shape = (nz, ny, nx) if nz else (ny, nx)
     X = x.reshape(shape)
     if levels == 0:
@@ -46,7 +47,7 @@ def apply_metric(nx, ny, x, levels, sigma0=1.0, c=1.0, nz=0):
     out = np.zeros_like(X)
     for l in range(levels):
         s = sigma0 * 2.0 ** l
-        mats = [blur_matrix_1d(n, s) for n in shape]     # one per axis
+        mats = [blur_matrix_1d(n, s, periodic) for n in shape]     # one per axis
         GX = X
         for ax, M in enumerate(mats):                    # G_l x
             GX = np.moveaxis(np.tensordot(M, GX, axes=([1], [ax])), 0, ax)

@@ -41,6 +41,11 @@ def cell_faces(grid, idx):
     index arrays idx = (J, I) or (K, J, I), and their activity (1 = not a wall)."""
     if grid.dim == 3:
         K, J, I = idx
+        if getattr(grid, "periodic", False):
+            faces = np.stack([grid.xf(K, J, I), grid.xf(K, J, (I + 1) % grid.nx), grid.yf(K, J, I),
+                              grid.yf(K, (J + 1) % grid.ny, I), grid.zf(K, J, I),
+                              grid.zf((K + 1) % grid.nz, J, I)], -1)
+            return faces, np.ones(faces.shape)
         faces = np.stack([grid.xf(K, J, I), grid.xf(K, J, I + 1), grid.yf(K, J, I),
                           grid.yf(K, J + 1, I), grid.zf(K, J, I), grid.zf(K + 1, J, I)], -1)
         active = np.stack([I > 0, I < grid.nx - 1, J > 0, J < grid.ny - 1,

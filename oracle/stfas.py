@@ -98,14 +98,32 @@ def _interp_weights_cell(nf, nc):
     return a, b
 
 
-def _interp_cells_axis(Xc, axis, nf):
-    """(3/4, 1/4) interpolation of cell-centred data to nf fine cells along ``axis``."""
-    a, b = _interp_weights_cell(nf, Xc.shape[axis])
+def _interp_cells_axis(Xc, axis, nf, periodic=False):
+    """(3/4, 1/4) interpolation of cell-centred data to nf fine cells along ``axis``
+    (the far neighbour clamped at a wall, wrapped on a periodic axis)."""
+    if periodic:
+        k = np.arange(nf)
+        a = k // 2
+        b = np.where(k % 2 == 0, a - 1, a + 1) % Xc.shape[axis]
+    else:
+        a, b = _interp_weights_cell(nf, Xc.shape[axis])
     return 0.75 * np.take(Xc, a, axis=axis) + 0.25 * np.take(Xc, b, axis=axis)
 
 
-def _interp_normal_axis(Xc, axis, nf_faces):
-    """Linear interpolation of face data along the face normal (weights 1 or 1/2, 1/2)."""
+def _interp_normal_axis(Xc, axis, nf_faces, periodic=False):
+    """Linear interpolation of face data along the face normal (weights 1 or 1/2, 1/2);
+    on a periodic axis the coarse face after the last is face 0."""
+    if periodic:
+        nc = Xc.shape[axis] - 1              # coarse faces 0..nc-1 (slot nc unused)
+        k = np.arange(nf_faces)
+        a = np.minimum(k // 2, nc - 1)
+        b = (k // 2 + 1) % nc
+        wb = np.where(k % 2 == 1, 0.5, 0.0)
+        wa = np.where(k == nf_faces - 1, 0.0, 1.0 - wb)   # the unused fine slot stays zero
+        wb = np.where(k == nf_faces - 1, 0.0, wb)
+        shape = [1] * Xc.ndim
+        shape[axis] = -1
+        return np.take(Xc, a, axis=axis) * wa.reshape(shape) + np.take(Xc, b, axis=axis) * wb.reshape(shape)
     a, b, wa, wb = _interp_weights_normal(nf_faces, Xc.shape[axis])
     shape = [1] * Xc.ndim
     shape[axis] = -1
@@ -116,7 +134,7 @@ def prolong_cells(fine, coarse, xc):
     if fine.dim == 3:
         X = xc.reshape(coarse.cell_shape())
         for axis, nf in enumerate(fine.cell_shape()):
-            X = _interp_cells_axis(X, axis, nf)
+            X = _interp_cells_axis(X, axis, nf, fine.periodic)
         return X.ravel()
     Xc = xc.reshape(coarse.ny, coarse.nx)
     ay, by = _interp_weights_cell(fine.ny, coarse.ny)
@@ -141,9 +159,9 @@ def prolong_faces(fine, coarse, vc):
             nfs = fine.face_shapes()[2 - normal]
             for axis in range(3):
                 if axis == normal:
-                    X = _interp_normal_axis(X, axis, nfs[axis])
+                    X = _interp_normal_axis(X, axis, nfs[axis], fine.periodic)
                 else:
-                    X = _interp_cells_axis(X, axis, nfs[axis])
+                    X = _interp_cells_axis(X, axis, nfs[axis], fine.periodic)
             out.append(X.ravel())
         return np.concatenate(out)
     cx, cy = coarse.split(vc)

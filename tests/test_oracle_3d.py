@@ -419,3 +419,161 @@ def test_admm_decreases_the_objective_3d():
     assert J < 0.9 * J0, (J, J0)
     assert max(np.max(np.abs(mac.div(P.grid, a))) for a in x["v"]) < 1e-6
     assert hist[-1]["kkt_rel"] < hist[0]["kkt_rel"]
+
+
+# ---------------------------------------------------------------------------
+# periodic boundaries (every axis wraps; the paper's periodic benchmarks are 3D)
+# ---------------------------------------------------------------------------
+def _roll(g, v, axis, sh):
+    """Periodic shift of a face field by sh cells along axis (0 = x, 1 = y, 2 = z)."""
+    comps = [a.copy() for a in g.split(v)]
+    arr_axis = 2 - axis
+    for c, a in enumerate(comps):
+        if c == axis:          # the normal component: slots 0..n-1 are the faces
+            sl = [slice(None)] * 3
+            sl[arr_axis] = slice(0, a.shape[arr_axis] - 1)
+            a[tuple(sl)] = np.roll(a[tuple(sl)], sh, axis=arr_axis)
+        else:
+            comps[c] = np.roll(a, sh, axis=arr_axis)
+    return g.join(*comps)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_periodic_operators_commute_with_periodic_shifts(axis):
+    rng = np.random.default_rng(61)
+    g = mac.Grid3(6, 4, 8, 1.0 / 6, periodic=True)
+    v = rng.standard_normal(g.F) * g.interior_faces()
+    u = rng.standard_normal(g.F) * g.interior_faces()
+    rho = rng.random(g.C)
+    sh = 2 if axis != 1 else 1
+    rv = _roll(g, v, axis, sh)
+    np.testing.assert_allclose(mac.adv(g, rv), _roll(g, mac.adv(g, v), axis, sh), atol=1e-12)
+    np.testing.assert_allclose(mac.adv_jacobian_T_apply(g, rv, _roll(g, u, axis, sh)),
+                               _roll(g, mac.adv_jacobian_T_apply(g, v, u), axis, sh), atol=1e-12)
+    R = np.roll(rho.reshape(g.cell_shape()), sh, axis=2 - axis).ravel()
+    AR = (mac.advection_matrix(g, rv) @ R).reshape(g.cell_shape())
+    np.testing.assert_allclose(AR, np.roll((mac.advection_matrix(g, v) @ rho).reshape(g.cell_shape()), sh,
+                                           axis=2 - axis), atol=1e-12)
+
+
+def test_periodic_operators_equal_the_closed_ones_away_from_the_boundary():
+    """Fields vanishing within three cells of every boundary plane: the wrap never
+    reaches them, so div, grad, Adv, its transpose and QUICK agree with the
+    closed-box operators."""
+    rng = np.random.default_rng(62)
+    n = 10
+    gp = mac.Grid3(n, n, n, 1.0 / n, periodic=True)
+    gc = mac.Grid3(n, n, n, 1.0 / n)
+    sup = []
+    for shape in gc.face_shapes():
+        a = np.zeros(shape)
+        a[3:-3, 3:-3, 3:-3] = 1.0
+        sup.append(a)
+    m = gc.join(*sup)
+    v = rng.standard_normal(gc.F) * m
+    u = rng.standard_normal(gc.F) * m
+    rho = np.zeros(gc.cell_shape())
+    rho[3:-3, 3:-3, 3:-3] = rng.random((n - 6,) * 3)
+    rho = rho.ravel()
+    np.testing.assert_allclose(mac.div(gp, v), mac.div(gc, v), atol=1e-12)
+    np.testing.assert_allclose(mac.adv(gp, v), mac.adv(gc, v), atol=1e-12)
+    np.testing.assert_allclose(mac.adv_jacobian_T_apply(gp, v, u), mac.adv_jacobian_T_apply(gc, v, u), atol=1e-12)
+    np.testing.assert_allclose(mac.advection_matrix(gp, v) @ rho, mac.advection_matrix(gc, v) @ rho, atol=1e-12)
+    p = rng.random(gc.C)
+    interior = gc.interior_faces()
+    np.testing.assert_allclose(mac.grad(gp, p) * interior, mac.grad(gc, p), atol=1e-12)
+
+
+def test_periodic_projection_matches_the_fft_closed_form():
+    rng = np.random.default_rng(63)
+    g = mac.Grid3(8, 6, 4, 1.0 / 8, periodic=True)
+    b = rng.standard_normal(g.C)
+    b -= b.mean()
+    B = np.fft.fftn(b.reshape(g.cell_shape()))
+    lam = 0.0
+    for axis, n in enumerate(g.cell_shape()):
+        k = np.arange(n)
+        shape = [1, 1, 1]
+        shape[axis] = n
+        lam = lam - (4 / g.h ** 2) * (np.sin(np.pi * k / n) ** 2).reshape(shape)
+    lam = np.broadcast_to(lam, B.shape).copy()
+    lam[0, 0, 0] = 1.0
+    Pp = B / lam
+    Pp[0, 0, 0] = 0.0
+    np.testing.assert_allclose(projection.poisson_neumann(g, b), np.real(np.fft.ifftn(Pp)).ravel(), atol=1e-12)
+    a = rng.standard_normal(g.F) * g.interior_faces()
+    Qa = projection.project(g, a)
+    assert np.max(np.abs(mac.div(g, Qa))) < 1e-10
+    # a constant (harmonic) field is left alone: no walls remove it
+    const = g.interior_faces() * 0.0
+    cx, cy, cz = g.split(const)
+    cx[:, :, :g.nx] = 1.0
+    c = g.join(cx, cy, cz)
+    np.testing.assert_allclose(projection.project(g, c), c, atol=1e-12)
+
+
+def _problem3p(n=4, nz=4, N=3, **kw):
+    rho0 = workloads.gaussian_ball3(n, n, nz, (0.5, 0.35, 0.5 * nz / n), 0.2)
+    star = workloads.gaussian_ball3(n, n, nz, (0.5, 0.65, 0.45 * nz / n), 0.2)
+    args = dict(r=1e-2, K=1.0, keyframes={N: (star, 1.0)}, metric_levels=1, nz=nz, periodic=True)
+    args.update(kw)
+    return kkt.Problem(n, n, N, 1.0 / N, rho0, **args)
+
+
+def test_periodic_reduced_gradient_and_scgs_blocks():
+    rng = np.random.default_rng(64)
+    P = _problem3p()
+    v = _solenoidal(P, rng, 0.4)
+    _, Ks = kkt.forward_density(P, v)
+    g = kkt.reduced_gradient(P, v)
+    d = _solenoidal(P, rng, 1.0)
+    eps = 1e-6
+    fd = (kkt.objective(P, v + eps * d, Ks) - kkt.objective(P, v - eps * d, Ks)) / (2 * eps)
+    an = float(np.sum(g * d))
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12), (fd, an)
+    # the local blocks of the corner cell (its faces wrap) are FD columns of f
+    P = _problem3p(lm_shift=0.0)
+    x = _random_state(P, rng)
+    x["u"][:] = 0.0
+    gr = P.grid
+    idx = (np.array([0]), np.array([0]), np.array([gr.nx - 1]))
+    faces, active = scgs.cell_faces(gr, idx)
+    assert np.all(active == 1.0)
+    cell = gr.cell(*idx)[0]
+    Dg, Lo, Up = scgs.assemble(P, gr, x, faces, active)
+    A = scgs.dense_from_blocks(Dg[0], Lo[0], Up[0])
+    z = np.zeros((P.N, gr.F))
+    unk = []
+    for i in range(P.N):
+        unk += [("u", i, f) for f in faces[0]] + [("p", i, cell)]
+        unk += [("v", i + 1, f) for f in faces[0]] + [("pbar", i + 1, cell)]
+    f0 = kkt.nso_residual(P, gr, x, z)
+    for col, (k, i, ix) in enumerate(unk):
+        xp = kkt.copy_state(x)
+        xp[k][i][ix] += eps
+        fp = kkt.nso_residual(P, gr, xp, z)
+        fdc = np.array([(fp[kk][ii][jx] - f0[kk][ii][jx]) / eps for kk, ii, jx in unk])
+        np.testing.assert_allclose(A[:, col], fdc, atol=2e-4 * max(1.0, np.max(np.abs(fdc))))
+
+
+def test_periodic_vcycles_converge_to_direct_solution():
+    rng = np.random.default_rng(65)
+    nx, nz, N = 8, 4, 2
+    rho0 = workloads.gaussian_ball3(nx, nx, nz, (0.5, 0.35, 0.3), 0.2)
+    P = kkt.Problem(nx, nx, N, 1.0 / N, rho0, r=1e-2, K=1.0, nz=nz, coarsest_n=2, periodic=True,
+                    self_advection=False, keyframes={N: (rho0, 1.0)})
+    assert [(g.nx, g.ny, g.nz) for g in stfas.hierarchy(P)] == [(8, 8, 4), (4, 4, 2)]
+    z = np.array([projection.project(P.grid, w) for w in
+                  rng.standard_normal((N, P.grid.F)) * P.grid.interior_faces()])
+    ref = _linear_solution(P, z)
+    x = kkt.zero_state(P)
+    hist = [stfas.stfas_cycle(P, x, z) for _ in range(25)]
+    for k in ("v", "u"):
+        scale = max(np.max(np.abs(ref[k])), 1e-3 * np.max(np.abs(ref["u"])))
+        np.testing.assert_allclose(x[k], ref[k], atol=1e-7 * scale)
+    # pressures are defined up to a constant per step
+    for k in ("pbar", "p"):
+        d = x[k] - ref[k]
+        d -= d.mean(axis=1, keepdims=True)
+        assert np.max(np.abs(d)) < 1e-6 * max(1.0, np.max(np.abs(ref[k])))
+    assert hist[-1] < 1e-8 * hist[0]
