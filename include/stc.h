@@ -103,6 +103,12 @@ typedef struct {
                            [nz][ny+1][nx], then z-faces [nz+1][ny][nx]; the hierarchy
                            halves all three axes; SCGS blocks are 7x7 (6 faces + pressure)
                            with 8 parity colours.  1 is invalid. */
+  int boundary;         /* 0 (default): the closed box (wall faces are not unknowns).
+                           1: periodic in every axis (3D only; nx, ny, nz even, so the
+                           parity colours of SCGS stay independent across the wrap).
+                           Face layouts keep n + 1 slots per axis; slot n is not a face
+                           and reads as zero; neighbour indices, QUICK stencils, the
+                           metric filters and the transfers wrap. */
 } stc_params;
 
 typedef struct {

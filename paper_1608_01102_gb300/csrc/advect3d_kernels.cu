@@ -86,14 +86,21 @@ __device__ __forceinline__ int face_at(const Geom& g, int a, int k, int j, int i
   return a == 0 ? xf(g, k, j, i) : (a == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
 }
 
-// QUICK face value of cell field t at the interior face p (1..n-1) along axis
-// a of the line through cell c0 (the line's first cell), normal velocity vf
+// position p +- d of an axis line: clamped to the wall cells, or wrapped
+__device__ __forceinline__ int line_pos(const Geom& g, int p, int n) {
+  if (g.periodic) return p < 0 ? p + n : (p >= n ? p - n : p);
+  return p < 0 ? 0 : (p > n - 1 ? n - 1 : p);
+}
+
+// QUICK face value of cell field t at the face p along axis a of the line
+// through cell c0 (the line's first cell), normal velocity vf: lower cell p-1,
+// upper cell p, far cells p-2 and p+1 (clamped at walls, wrapped if periodic)
 template <class T>
-__device__ __forceinline__ T quick_face(const T* t, int c0, Axis ax, int p, T vf) {
+__device__ __forceinline__ T quick_face(const Geom& g, const T* t, int c0, Axis ax, int p, T vf) {
   T c[4];
   quick_coef3(vf, c);
-  const int lo = p - 1, hi = p;
-  const int llo = lo - 1 < 0 ? 0 : lo - 1, hhi = hi + 1 > ax.n - 1 ? ax.n - 1 : hi + 1;
+  const int lo = line_pos(g, p - 1, ax.n), hi = line_pos(g, p, ax.n);
+  const int llo = line_pos(g, p - 2, ax.n), hhi = line_pos(g, p + 1, ax.n);
   return c[0] * ldcg(t + c0 + lo * ax.stride) + c[1] * ldcg(t + c0 + hi * ax.stride) +
          c[2] * ldcg(t + c0 + llo * ax.stride) + c[3] * ldcg(t + c0 + hhi * ax.stride);
 }
@@ -111,13 +118,13 @@ __device__ T apply_A(const Geom& g, const T* v, const T* t, int k, int j, int i)
     const int fm = a == 0 ? face_at(g, 0, k, j, i) : (a == 1 ? face_at(g, 1, k, j, i) : face_at(g, 2, k, j, i));
     const int fp = a == 0 ? face_at(g, 0, k, j, i + 1) : (a == 1 ? face_at(g, 1, k, j + 1, i) : face_at(g, 2, k + 1, j, i));
     T Fp = T(0), Fm = T(0);
-    if (p + 1 <= ax.n - 1) {
+    if (g.periodic || p + 1 <= ax.n - 1) {
       const T vf = ld(v + fp);
-      Fp = vf * quick_face(t, c0, ax, p + 1, vf);
+      Fp = vf * quick_face(g, t, c0, ax, p + 1, vf);
     }
-    if (p >= 1) {
+    if (g.periodic || p >= 1) {
       const T vf = ld(v + fm);
-      Fm = vf * quick_face(t, c0, ax, p, vf);
+      Fm = vf * quick_face(g, t, c0, ax, p, vf);
     }
     acc += Fp - Fm;
   }
@@ -126,7 +133,8 @@ __device__ T apply_A(const Geom& g, const T* v, const T* t, int k, int j, int i)
 
 // (A(v)^T w)_c: sum over the faces f of each axis line whose QUICK stencil
 // holds c of coef(f, c) E_f, E_f = v_f (w_hi - w_lo) / h (clamped stencils
-// included: face 1 also reaches cell 0 through lo-1, face n-1 cell n-1 through hi+1)
+// included: face 1 also reaches cell 0 through lo-1, face n-1 cell n-1 through
+// hi+1; on a periodic axis the faces p-1 .. p+2 wrap)
 template <class T>
 __device__ T apply_AT(const Geom& g, const T* v, const T* w, int k, int j, int i) {
   const int crd[3] = {i, j, k};
@@ -139,14 +147,15 @@ __device__ T apply_AT(const Geom& g, const T* v, const T* w, int k, int j, int i
     const int c0 = cid(g, k, j, i) - p * ax.stride;
 #pragma unroll
     for (int d = -1; d <= 2; ++d) {
-      const int f = p + d;     // face position along the axis
-      if (f < 1 || f > ax.n - 1) continue;
+      int f = p + d;     // face position along the axis
+      if (g.periodic) f = f < 0 ? f + ax.n : (f >= ax.n ? f - ax.n : f);
+      else if (f < 1 || f > ax.n - 1) continue;
       const int fk = a == 2 ? f : k, fj = a == 1 ? f : j, fi = a == 0 ? f : i;
       const T vf = ld(v + face_at(g, a, fk, fj, fi));
       T c[4];
       quick_coef3(vf, c);
-      const int lo = f - 1, hi = f;
-      const int llo = lo - 1 < 0 ? 0 : lo - 1, hhi = hi + 1 > ax.n - 1 ? ax.n - 1 : hi + 1;
+      const int lo = line_pos(g, f - 1, ax.n), hi = f;
+      const int llo = line_pos(g, f - 2, ax.n), hhi = line_pos(g, f + 1, ax.n);
       const T E = vf * (ldcg(w + c0 + hi * ax.stride) - ldcg(w + c0 + lo * ax.stride)) * ih;
       T cf = T(0);
       if (lo == p) cf += c[0];
@@ -318,13 +327,13 @@ taylor_adjoint3_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ 
       for (int f = tid; f < F; f += nth) {
         int fk, fj, fi;
         const int a = face_coords(g, f, fk, fj, fi);
-        if (!interior(g, a, fk, fj, fi)) continue;
+        if (!is_face(g, a, fk, fj, fi)) continue;
         const Axis ax = axis_of(g, a);
         const int p = a == 0 ? fi : (a == 1 ? fj : fk);
         const int c0 = cid(g, a == 2 ? 0 : fk, a == 1 ? 0 : fj, a == 0 ? 0 : fi);
         const T vf = ld(vs + f);
-        const T q = quick_face(P, c0, ax, p, vf);
-        const T d = (ldcg(cur + c0 + p * ax.stride) - ldcg(cur + c0 + (p - 1) * ax.stride)) * ih;
+        const T q = quick_face(g, P, c0, ax, p, vf);
+        const T d = (ldcg(cur + c0 + p * ax.stride) - ldcg(cur + c0 + line_pos(g, p - 1, ax.n) * ax.stride)) * ih;
         os[f] += beta * q * d;
       }
       const T fac = mm == 0 ? T(1) : dtk[mm];
@@ -352,7 +361,7 @@ taylor_adjoint3_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ 
 // ---------------------------------------------------------------------------
 template <class Tc, class To>
 __global__ void blur3_kernel(int nx, int ny, int nz, int axis, int transpose, double sigma, const Tc* __restrict__ in,
-                             To* out, double scale, int accumulate) {
+                             To* out, double scale, int accumulate, int periodic) {
   extern __shared__ double wsm3[];
   const int R = (int)ceil(3.0 * sigma);
   const int nt = 2 * R + 1;
@@ -383,7 +392,14 @@ __global__ void blur3_kernel(int nx, int ny, int nz, int axis, int transpose, do
     auto at = [&](int b) { return in[base + b * stride]; };
     const int a = crd;
     Tc acc = Tc(0);
-    if (!transpose) {
+    if (periodic) {
+      // circulant: G^T is the same filter with the taps reversed
+      for (int t = -R; t <= R; ++t) {
+        int b = (a + (transpose ? -t : t)) % n;
+        b = b < 0 ? b + n : b;
+        acc += w[t + R] * at(b);
+      }
+    } else if (!transpose) {
       for (int t = -R; t <= R; ++t) {
         int b = a + t;
         b = b < 0 ? 0 : (b > n - 1 ? n - 1 : b);
@@ -523,12 +539,13 @@ void launch_metric3(const Geom& g, const T* rho_s, const double* star, double c,
     const double sig = sigma0 * (double)(1 << l);
     const int R = (int)ceil(3.0 * sig);
     const size_t sm = sizeof(double) * 3 * (2 * R + 1);
-    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 0, 0, sig, d0, d1, 1.0, 0);       // G_x
-    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 1, 0, sig, d1, d2, 1.0, 0);       // G_y
-    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 2, 0, sig, d2, d1, 1.0, 0);       // G_z
-    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 2, 1, sig, d1, d2, 1.0, 0);       // G_z^T
-    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 1, 1, sig, d2, d1, 1.0, 0);       // G_y^T
-    blur3_kernel<T, double><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 0, 1, sig, d1, out, c, 1);   // += c G_x^T
+    const int pr = g.periodic;
+    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 0, 0, sig, d0, d1, 1.0, 0, pr);       // G_x
+    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 1, 0, sig, d1, d2, 1.0, 0, pr);       // G_y
+    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 2, 0, sig, d2, d1, 1.0, 0, pr);       // G_z
+    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 2, 1, sig, d1, d2, 1.0, 0, pr);       // G_z^T
+    blur3_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 1, 1, sig, d2, d1, 1.0, 0, pr);       // G_y^T
+    blur3_kernel<T, double><<<nb, tpb, sm, st>>>(g.nx, g.ny, g.nz, 0, 1, sig, d1, out, c, 1, pr);   // += c G_x^T
   }
 }
 

@@ -13,6 +13,13 @@
 //        v_{a+2} faces around it; O2, V2 likewise with a+2 and a+1
 // (axes cyclic: x -> y -> z -> x).  On a field that does not vary along one
 // axis and has no velocity along it, this is the 2D operator of the other two.
+//
+// Periodic grids (Geom::periodic): every neighbour index wraps modulo the axis
+// length, so there are no walls; the layout keeps n + 1 face slots per axis
+// and slot n is not a face (held at zero).  Index helpers take the cell or
+// face coordinate with offsets of at most +-2 and wrap them; `interior`
+// answers for neighbours (always true when periodic), `is_face` for
+// coordinates decoded from a slot (false only for the unused slot n).
 #pragma once
 
 #include "stc_internal.cuh"
@@ -20,26 +27,34 @@
 namespace stc {
 namespace g3 {
 
+// wrap a coordinate with |offset| <= n into [0, n) on a periodic grid
+__host__ __device__ __forceinline__ int wr(const Geom& g, int a, int n) {
+  return g.periodic ? (a < 0 ? a + n : (a >= n ? a - n : a)) : a;
+}
+
 __host__ __device__ __forceinline__ int xf(const Geom& g, int k, int j, int i) {
-  return (k * g.ny + j) * (g.nx + 1) + i;
+  return (wr(g, k, g.nz) * g.ny + wr(g, j, g.ny)) * (g.nx + 1) + wr(g, i, g.nx);
 }
 __host__ __device__ __forceinline__ int yf(const Geom& g, int k, int j, int i) {
-  return g.Fx + (k * (g.ny + 1) + j) * g.nx + i;
+  return g.Fx + (wr(g, k, g.nz) * (g.ny + 1) + wr(g, j, g.ny)) * g.nx + wr(g, i, g.nx);
 }
 __host__ __device__ __forceinline__ int zf(const Geom& g, int k, int j, int i) {
-  return g.Fxy + (k * g.ny + j) * g.nx + i;
+  return g.Fxy + (wr(g, k, g.nz) * g.ny + wr(g, j, g.ny)) * g.nx + wr(g, i, g.nx);
 }
-__host__ __device__ __forceinline__ int cid(const Geom& g, int k, int j, int i) { return (k * g.ny + j) * g.nx + i; }
+__host__ __device__ __forceinline__ int cid(const Geom& g, int k, int j, int i) {
+  return (wr(g, k, g.nz) * g.ny + wr(g, j, g.ny)) * g.nx + wr(g, i, g.nx);
+}
 
-// interior (non-wall) faces, with the index range check folded in
+// interior (non-wall) faces, with the index range check folded in; on a
+// periodic grid every neighbour is a face
 __device__ __forceinline__ bool xin(const Geom& g, int k, int j, int i) {
-  return i >= 1 && i <= g.nx - 1 && j >= 0 && j < g.ny && k >= 0 && k < g.nz;
+  return g.periodic || (i >= 1 && i <= g.nx - 1 && j >= 0 && j < g.ny && k >= 0 && k < g.nz);
 }
 __device__ __forceinline__ bool yin(const Geom& g, int k, int j, int i) {
-  return j >= 1 && j <= g.ny - 1 && i >= 0 && i < g.nx && k >= 0 && k < g.nz;
+  return g.periodic || (j >= 1 && j <= g.ny - 1 && i >= 0 && i < g.nx && k >= 0 && k < g.nz);
 }
 __device__ __forceinline__ bool zin(const Geom& g, int k, int j, int i) {
-  return k >= 1 && k <= g.nz - 1 && i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+  return g.periodic || (k >= 1 && k <= g.nz - 1 && i >= 0 && i < g.nx && j >= 0 && j < g.ny);
 }
 
 // decode a face index into (axis, k, j, i)
@@ -75,21 +90,21 @@ __device__ __forceinline__ R ldv(const T* v, int f) {
 // curl components on edges (zero on edges lying in a wall)
 template <class T, class R = T>
 __device__ __forceinline__ R wx(const Geom& g, const T* v, int k, int j, int i) {
-  if (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz) return R(0);
+  if (!g.periodic && (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz)) return R(0);
   const R a = ldv<T, R>(v, zf(g, k, j, i)) - ldv<T, R>(v, zf(g, k, j - 1, i));
   const R b = ldv<T, R>(v, yf(g, k, j, i)) - ldv<T, R>(v, yf(g, k - 1, j, i));
   return (a - b) * pick<R>(g.ih, g.ihf);
 }
 template <class T, class R = T>
 __device__ __forceinline__ R wy(const Geom& g, const T* v, int k, int j, int i) {
-  if (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz) return R(0);
+  if (!g.periodic && (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz)) return R(0);
   const R a = ldv<T, R>(v, xf(g, k, j, i)) - ldv<T, R>(v, xf(g, k - 1, j, i));
   const R b = ldv<T, R>(v, zf(g, k, j, i)) - ldv<T, R>(v, zf(g, k, j, i - 1));
   return (a - b) * pick<R>(g.ih, g.ihf);
 }
 template <class T, class R = T>
 __device__ __forceinline__ R wz(const Geom& g, const T* v, int k, int j, int i) {
-  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return R(0);
+  if (!g.periodic && (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny)) return R(0);
   const R a = ldv<T, R>(v, yf(g, k, j, i)) - ldv<T, R>(v, yf(g, k, j, i - 1));
   const R b = ldv<T, R>(v, xf(g, k, j, i)) - ldv<T, R>(v, xf(g, k, j - 1, i));
   return (a - b) * pick<R>(g.ih, g.ihf);
@@ -145,6 +160,13 @@ __device__ __forceinline__ bool interior(const Geom& g, int axis, int k, int j, 
   return axis == 0 ? xin(g, k, j, i) : (axis == 1 ? yin(g, k, j, i) : zin(g, k, j, i));
 }
 
+// a face unknown at coordinates decoded from a slot (wall faces and, when
+// periodic, the unused slot n are not)
+__device__ __forceinline__ bool is_face(const Geom& g, int axis, int k, int j, int i) {
+  if (g.periodic) return axis == 0 ? i < g.nx : (axis == 1 ? j < g.ny : k < g.nz);
+  return interior(g, axis, k, j, i);
+}
+
 template <class T>
 __device__ __forceinline__ T adv(const Geom& g, const T* v, int axis, int k, int j, int i) {
   if (!interior(g, axis, k, j, i)) return T(0);
@@ -190,21 +212,21 @@ __device__ __forceinline__ T beta2(const Geom& g, const T* v, const T* u, int ax
 // x-edge: omega_x is O2 of y-faces (k,j,i), (k-1,j,i) and O1 of z-faces (k,j,i), (k,j-1,i)
 template <class T>
 __device__ __forceinline__ T qx(const Geom& g, const T* v, const T* u, int k, int j, int i) {
-  if (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz) return T(0);
+  if (!g.periodic && (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz)) return T(0);
   return T(0.5) * (alpha2(g, v, u, 1, k, j, i) + alpha2(g, v, u, 1, k - 1, j, i) + alpha1(g, v, u, 2, k, j, i) +
                    alpha1(g, v, u, 2, k, j - 1, i));
 }
 // y-edge: omega_y is O1 of x-faces (k,j,i), (k-1,j,i) and O2 of z-faces (k,j,i), (k,j,i-1)
 template <class T>
 __device__ __forceinline__ T qy(const Geom& g, const T* v, const T* u, int k, int j, int i) {
-  if (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz) return T(0);
+  if (!g.periodic && (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz)) return T(0);
   return T(0.5) * (alpha1(g, v, u, 0, k, j, i) + alpha1(g, v, u, 0, k - 1, j, i) + alpha2(g, v, u, 2, k, j, i) +
                    alpha2(g, v, u, 2, k, j, i - 1));
 }
 // z-edge: omega_z is O2 of x-faces (k,j,i), (k,j-1,i) and O1 of y-faces (k,j,i), (k,j,i-1)
 template <class T>
 __device__ __forceinline__ T qz(const Geom& g, const T* v, const T* u, int k, int j, int i) {
-  if (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny) return T(0);
+  if (!g.periodic && (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny)) return T(0);
   return T(0.5) * (alpha2(g, v, u, 0, k, j, i) + alpha2(g, v, u, 0, k, j - 1, i) + alpha1(g, v, u, 1, k, j, i) +
                    alpha1(g, v, u, 1, k, j, i - 1));
 }
@@ -245,8 +267,8 @@ template <class T>
 __device__ __forceinline__ T grad(const Geom& g, const T* p, int axis, int k, int j, int i) {
   if (!interior(g, axis, k, j, i)) return T(0);
   const int c = cid(g, k, j, i);
-  const int o = axis == 0 ? 1 : (axis == 1 ? g.nx : g.nx * g.ny);
-  return (ld(p + c) - ld(p + c - o)) * pick<T>(g.ih, g.ihf);
+  const int cm = axis == 0 ? cid(g, k, j, i - 1) : (axis == 1 ? cid(g, k, j - 1, i) : cid(g, k - 1, j, i));
+  return (ld(p + c) - ld(p + cm)) * pick<T>(g.ih, g.ihf);
 }
 
 template <class T>

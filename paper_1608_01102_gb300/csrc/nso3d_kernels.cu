@@ -67,7 +67,7 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
   if (e < g.F) {
     int k, j, i;
     const int axis = face_coords(g, e, k, j, i);
-    const bool in = interior(g, axis, k, j, i);
+    const bool in = is_face(g, axis, k, j, i);
     if (t >= 1) {
       T val = T(0);
       if (in) {
@@ -145,8 +145,10 @@ __global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __rest
       j = py + 2 * (r % ncy);
       k = r / ncy;
     }
+    // (the unused slot n of a periodic axis aliases face 0: its rows stay untouched)
+    if (g.periodic && !is_face(g, axis, k, j, i)) return;
     const int f = axis == 0 ? xf(g, k, j, i) : (axis == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
-    const bool in = interior(g, axis, k, j, i);
+    const bool in = is_face(g, axis, k, j, i);
     if (t >= 1) {
       T val = T(0);
       if (in) {
@@ -209,12 +211,13 @@ template <class S>
 struct CellG3 {
   S act[NF], g[NF], gh[NF], ig2;
   __device__ void init(const Geom& geo, int i, int j, int k) {
-    act[0] = S(i > 0);
-    act[1] = S(i < geo.nx - 1);
-    act[2] = S(j > 0);
-    act[3] = S(j < geo.ny - 1);
-    act[4] = S(k > 0);
-    act[5] = S(k < geo.nz - 1);
+    const bool pr = geo.periodic != 0;   // no walls: every face of every cell is an unknown
+    act[0] = S(pr || i > 0);
+    act[1] = S(pr || i < geo.nx - 1);
+    act[2] = S(pr || j > 0);
+    act[3] = S(pr || j < geo.ny - 1);
+    act[4] = S(pr || k > 0);
+    act[5] = S(pr || k < geo.nz - 1);
     S g2 = S(0);
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
@@ -422,7 +425,9 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
     const Cell3 cl = colour_cell(g, colour, q);
     const int fidx[NF] = {xf(g, cl.k, cl.j, cl.i), xf(g, cl.k, cl.j, cl.i + 1), yf(g, cl.k, cl.j, cl.i),
                           yf(g, cl.k, cl.j + 1, cl.i), zf(g, cl.k, cl.j, cl.i), zf(g, cl.k + 1, cl.j, cl.i)};
-    S act[NF] = {S(cl.i > 0), S(cl.i < g.nx - 1), S(cl.j > 0), S(cl.j < g.ny - 1), S(cl.k > 0), S(cl.k < g.nz - 1)};
+    const bool pr = g.periodic != 0;
+    S act[NF] = {S(pr || cl.i > 0), S(pr || cl.i < g.nx - 1), S(pr || cl.j > 0), S(pr || cl.j < g.ny - 1),
+                 S(pr || cl.k > 0), S(pr || cl.k < g.nz - 1)};
     const int cc = cid(g, cl.k, cl.j, cl.i);
     S Jl[NF][NF];
     local_adv_jac3<T, S>(g, x.v + (size_t)(t + 1) * g.F, cl.k, cl.j, cl.i, act, Jl);
@@ -708,7 +713,9 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
     const Cell3 cl = colour_cell(g, colour, q);
     const int fidx[NF] = {xf(g, cl.k, cl.j, cl.i), xf(g, cl.k, cl.j, cl.i + 1), yf(g, cl.k, cl.j, cl.i),
                           yf(g, cl.k, cl.j + 1, cl.i), zf(g, cl.k, cl.j, cl.i), zf(g, cl.k + 1, cl.j, cl.i)};
-    const bool actb[NF] = {cl.i > 0, cl.i < g.nx - 1, cl.j > 0, cl.j < g.ny - 1, cl.k > 0, cl.k < g.nz - 1};
+    const bool pr = g.periodic != 0;
+    const bool actb[NF] = {pr || cl.i > 0, pr || cl.i < g.nx - 1, pr || cl.j > 0, pr || cl.j < g.ny - 1,
+                           pr || cl.k > 0, pr || cl.k < g.nz - 1};
     const int cc = cid(g, cl.k, cl.j, cl.i);
     T* fu = x.u + (size_t)t * g.F;
     T* fv = x.v + (size_t)(t + 1) * g.F;
@@ -787,12 +794,13 @@ struct ThomasCell {
     fidx[3] = yf(g, cl.k, cl.j + 1, cl.i);
     fidx[4] = zf(g, cl.k, cl.j, cl.i);
     fidx[5] = zf(g, cl.k + 1, cl.j, cl.i);
-    act[0] = S(cl.i > 0);
-    act[1] = S(cl.i < g.nx - 1);
-    act[2] = S(cl.j > 0);
-    act[3] = S(cl.j < g.ny - 1);
-    act[4] = S(cl.k > 0);
-    act[5] = S(cl.k < g.nz - 1);
+    const bool pr = g.periodic != 0;
+    act[0] = S(pr || cl.i > 0);
+    act[1] = S(pr || cl.i < g.nx - 1);
+    act[2] = S(pr || cl.j > 0);
+    act[3] = S(pr || cl.j < g.ny - 1);
+    act[4] = S(pr || cl.k > 0);
+    act[5] = S(pr || cl.k < g.nz - 1);
     cc = cid(g, cl.k, cl.j, cl.i);
   }
   // U_t = (I/dt + dAdv_loc(v_{t+1})) on the active face pairs
@@ -1065,7 +1073,9 @@ __global__ void restrict3_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, con
     const int f = (int)(e - (size_t)t * gc.F);
     int K, J, I;
     const int axis = face_coords(gc, f, K, J, I);
+    const bool slot = !gc.periodic || is_face(gc, axis, K, J, I);   // the unused periodic slot stays 0
     auto rs = [&](int tf) -> Tc {
+      if (!slot) return Tc(0);
       const Tf* s = sf + (size_t)tf * gf.F;
       Tc acc = Tc(0);
 #pragma unroll
@@ -1105,10 +1115,13 @@ __global__ void restrict3_kernel(Geom gf, Geom gc, int nt_face, int nt_cell, con
   }
 }
 
-__device__ __forceinline__ void cell_interp3(int k, int nc, int& a, int& b) {
+// (3/4, 1/4) neighbours of fine cell k among nc coarse cells: clamped at a
+// wall, wrapped on a periodic axis
+__device__ __forceinline__ void cell_interp3(int k, int nc, int& a, int& b, bool periodic = false) {
   a = k >> 1;
   b = (k & 1) ? a + 1 : a - 1;
-  b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
+  if (periodic) b = b < 0 ? b + nc : (b > nc - 1 ? b - nc : b);
+  else b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
 }
 
 template <class Tf, class Tc>
@@ -1137,6 +1150,7 @@ __global__ void prolong3_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_ce
     const int f = (int)(e - (size_t)(t - t0_face) * gf.F);
     int k, j, i;
     const int axis = face_coords(gf, f, k, j, i);
+    if (gf.periodic && !is_face(gf, axis, k, j, i)) return;
     // per axis (k, j, i): two coarse indices and weights
     int ca[3], cb[3];
     W wa[3], wb[3];
@@ -1151,7 +1165,7 @@ __global__ void prolong3_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_ce
         wb[d] = (fine[d] & 1) ? W(0.5) : W(0);
         wa[d] = W(1) - wb[d];
       } else {
-        cell_interp3(fine[d], nce[d], ca[d], cb[d]);
+        cell_interp3(fine[d], nce[d], ca[d], cb[d], gf.periodic != 0);
         wa[d] = W(0.75);
         wb[d] = W(0.25);
       }
@@ -1181,9 +1195,9 @@ __global__ void prolong3_correct_kernel(Geom gf, Geom gc, int nt_face, int nt_ce
     const int c = (int)(ec - (size_t)(t - t0_cell) * gf.C);
     const int i = c % gf.nx, r = c / gf.nx, j = r % gf.ny, k = r / gf.ny;
     int ka, kb, ja, jb, ia, ib;
-    cell_interp3(k, gc.nz, ka, kb);
-    cell_interp3(j, gc.ny, ja, jb);
-    cell_interp3(i, gc.nx, ia, ib);
+    cell_interp3(k, gc.nz, ka, kb, gf.periodic != 0);
+    cell_interp3(j, gc.ny, ja, jb, gf.periodic != 0);
+    cell_interp3(i, gc.nx, ia, ib, gf.periodic != 0);
     auto ps = [&](int tc) -> W {
       const Tc* n = cnc + (size_t)tc * gc.C;
       const Tc* o = coc + (size_t)tc * gc.C;
@@ -1215,7 +1229,7 @@ __global__ void kkt_force_rhs3_kernel(Geom g, const T* __restrict__ v, T* out) {
   int k, j, i;
   const int axis = face_coords(g, e, k, j, i);
   T val = T(0);
-  if (interior(g, axis, k, j, i))
+  if (is_face(g, axis, k, j, i))
     val = (vn[e] - vt[e]) * pick<T>(g.idt, g.idtf) + T(g.self_adv) * adv(g, vn, axis, k, j, i);
   out[(size_t)t * g.F + e] = val;
 }
@@ -1232,7 +1246,7 @@ __global__ void kkt_grad_rhs3_kernel(Geom g, const T* __restrict__ v, const T* _
   int k, j, i;
   const int axis = face_coords(g, e, k, j, i);
   T val = T(0);
-  if (interior(g, axis, k, j, i)) {
+  if (is_face(g, axis, k, j, i)) {
     T s = um[e] * pick<T>(g.idt, g.idtf);
     if (g.self_adv) s += jtu(g, vt, um, axis, k, j, i);
     if (t < g.N) s -= u[(size_t)t * g.F + e] * pick<T>(g.idt, g.idtf);

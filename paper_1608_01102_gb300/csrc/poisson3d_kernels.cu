@@ -49,7 +49,34 @@ P3Levels p3_levels(const Geom& g, int count) {
 
 struct Lv {
   int nx, ny, nz, C;
+  int periodic;   // neighbours wrap (no walls: 6 neighbours everywhere)
 };
+
+// neighbour sum and count of cell (k, j, i) on a level
+template <class Acc>
+__device__ __forceinline__ int p3_neighbours(const Lv& L, int k, int j, int i, Acc acc) {
+  if (L.periodic) {
+    const int im = i > 0 ? i - 1 : L.nx - 1, ip = i < L.nx - 1 ? i + 1 : 0;
+    const int jm = j > 0 ? j - 1 : L.ny - 1, jp = j < L.ny - 1 ? j + 1 : 0;
+    const int km = k > 0 ? k - 1 : L.nz - 1, kp = k < L.nz - 1 ? k + 1 : 0;
+    acc((k * L.ny + j) * L.nx + im);
+    acc((k * L.ny + j) * L.nx + ip);
+    acc((k * L.ny + jm) * L.nx + i);
+    acc((k * L.ny + jp) * L.nx + i);
+    acc((km * L.ny + j) * L.nx + i);
+    acc((kp * L.ny + j) * L.nx + i);
+    return 6;
+  }
+  const int c = (k * L.ny + j) * L.nx + i;
+  int nn = 0;
+  if (i > 0) { acc(c - 1); ++nn; }
+  if (i < L.nx - 1) { acc(c + 1); ++nn; }
+  if (j > 0) { acc(c - L.nx); ++nn; }
+  if (j < L.ny - 1) { acc(c + L.nx); ++nn; }
+  if (k > 0) { acc(c - L.nx * L.ny); ++nn; }
+  if (k < L.nz - 1) { acc(c + L.nx * L.ny); ++nn; }
+  return nn;
+}
 
 template <class T>
 __global__ void p3_div_kernel(Geom g, const T* __restrict__ fields, int count, T* phi, T* b) {
@@ -79,13 +106,7 @@ __global__ void p3_rb_kernel(Lv L, int count, T* phi, const T* __restrict__ b, T
     T* p = phi + (size_t)f * L.C;
     const int c = (k * L.ny + j) * L.nx + i;
     T s = T(0);
-    int nn = 0;
-    if (i > 0) { s += p[c - 1]; ++nn; }
-    if (i < L.nx - 1) { s += p[c + 1]; ++nn; }
-    if (j > 0) { s += p[c - L.nx]; ++nn; }
-    if (j < L.ny - 1) { s += p[c + L.nx]; ++nn; }
-    if (k > 0) { s += p[c - L.nx * L.ny]; ++nn; }
-    if (k < L.nz - 1) { s += p[c + L.nx * L.ny]; ++nn; }
+    const int nn = p3_neighbours(L, k, j, i, [&](int q) { s += p[q]; });
     p[c] = (s - h2 * b[(size_t)f * L.C + c]) / T(nn);
   }
 }
@@ -94,13 +115,7 @@ template <class T>
 __device__ __forceinline__ T p3_lap(const T* p, Lv L, int k, int j, int i, T ih2) {
   const int c = (k * L.ny + j) * L.nx + i;
   T s = T(0);
-  int nn = 0;
-  if (i > 0) { s += p[c - 1]; ++nn; }
-  if (i < L.nx - 1) { s += p[c + 1]; ++nn; }
-  if (j > 0) { s += p[c - L.nx]; ++nn; }
-  if (j < L.ny - 1) { s += p[c + L.nx]; ++nn; }
-  if (k > 0) { s += p[c - L.nx * L.ny]; ++nn; }
-  if (k < L.nz - 1) { s += p[c + L.nx * L.ny]; ++nn; }
+  const int nn = p3_neighbours(L, k, j, i, [&](int q) { s += p[q]; });
   return (s - T(nn) * p[c]) * ih2;
 }
 
@@ -129,10 +144,11 @@ __global__ void p3_restrict_kernel(Lv F, Lv Cc, int count, const T* __restrict__
   }
 }
 
-__device__ __forceinline__ void p3_interp(int k, int nc, int& a, int& b) {
+__device__ __forceinline__ void p3_interp(int k, int nc, int& a, int& b, bool periodic) {
   a = k >> 1;
   b = (k & 1) ? a + 1 : a - 1;
-  b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
+  if (periodic) b = b < 0 ? b + nc : (b > nc - 1 ? b - nc : b);
+  else b = b < 0 ? 0 : (b > nc - 1 ? nc - 1 : b);
 }
 
 // phi_l += P phi_{l+1} (trilinear, (3/4, 1/4) per axis, clamped)
@@ -143,9 +159,9 @@ __global__ void p3_prolong_kernel(Lv F, Lv Cc, int count, T* phi, const T* __res
     const int f = (int)(e / F.C), c = (int)(e - (size_t)f * F.C);
     const int i = c % F.nx, r = c / F.nx, j = r % F.ny, k = r / F.ny;
     int ka, kb, ja, jb, ia, ib;
-    p3_interp(k, Cc.nz, ka, kb);
-    p3_interp(j, Cc.ny, ja, jb);
-    p3_interp(i, Cc.nx, ia, ib);
+    p3_interp(k, Cc.nz, ka, kb, F.periodic != 0);
+    p3_interp(j, Cc.ny, ja, jb, F.periodic != 0);
+    p3_interp(i, Cc.nx, ia, ib, F.periodic != 0);
     const T* pc = phic + (size_t)f * Cc.C;
     T acc = T(0);
 #pragma unroll
@@ -187,13 +203,7 @@ __global__ void p3_coarsest_kernel(Lv L, T* phi, const T* __restrict__ b, double
         const int i = e % L.nx, r = e / L.nx, j = r % L.ny, k = r / L.ny;
         if (((i + j + k) & 1) != colour) continue;
         double s = 0.0;
-        int nn = 0;
-        if (i > 0) { s += cp[e - 1]; ++nn; }
-        if (i < L.nx - 1) { s += cp[e + 1]; ++nn; }
-        if (j > 0) { s += cp[e - L.nx]; ++nn; }
-        if (j < L.ny - 1) { s += cp[e + L.nx]; ++nn; }
-        if (k > 0) { s += cp[e - L.nx * L.ny]; ++nn; }
-        if (k < L.nz - 1) { s += cp[e + L.nx * L.ny]; ++nn; }
+        const int nn = p3_neighbours(L, k, j, i, [&](int q) { s += cp[q]; });
         cp[e] = nn > 0 ? (s - h2 * cb[e]) / nn : 0.0;
       }
       __syncthreads();
@@ -210,7 +220,7 @@ __global__ void p3_grad_sub_kernel(Geom g, T* fields, int count, const T* __rest
     int k, j, i;
     const int axis = face_coords(g, f, k, j, i);
     T* v = fields + (size_t)fi * g.F;
-    if (interior(g, axis, k, j, i)) v[f] -= grad(g, phi + (size_t)fi * g.C, axis, k, j, i);
+    if (is_face(g, axis, k, j, i)) v[f] -= grad(g, phi + (size_t)fi * g.C, axis, k, j, i);
     else v[f] = T(0);
   }
 }
@@ -243,6 +253,7 @@ cudaError_t launch_project3(const Geom& g, T* fields, int count, int vcycles, cu
     L.ny = P.ny[l];
     L.nz = P.nz[l];
     L.C = L.nx * L.ny * L.nz;
+    L.periodic = g.periodic;
     return L;
   };
   auto phi_of = [&](int l) { return scratch + P.off[l]; };

@@ -23,7 +23,7 @@ __global__ void picard_rhs_kernel(Geom g, const T* __restrict__ v_prev, const T*
   if (g.dim == 3) {
     int k, j, i;
     const int axis = g3::face_coords(g, e, k, j, i);
-    in = g3::interior(g, axis, k, j, i);
+    in = g3::is_face(g, axis, k, j, i);
     if (in && g.self_adv) a = g3::adv(g, v, axis, k, j, i);
   } else if (e < g.Fx) {
     const int j = e / (g.nx + 1), i = e - j * (g.nx + 1);
@@ -49,7 +49,7 @@ __global__ void picard_adj_rhs_kernel(Geom g, const T* __restrict__ v, const T* 
   if (g.dim == 3) {
     int k, j, i;
     const int axis = g3::face_coords(g, e, k, j, i);
-    in = g3::interior(g, axis, k, j, i);
+    in = g3::is_face(g, axis, k, j, i);
     if (in && g.self_adv) jt = g3::jtu(g, v, z, axis, k, j, i);
   } else if (e < g.Fx) {
     const int j = e / (g.nx + 1), i = e - j * (g.nx + 1);

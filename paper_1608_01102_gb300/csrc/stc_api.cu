@@ -164,6 +164,7 @@ Geom make_geom(const stc_params& prm, int nx, int ny, int nz, double h, int N, d
     g.Fxy = g.F;
     g.C = nx * ny;
   }
+  g.periodic = (nz > 0 && prm.boundary == 1) ? 1 : 0;
   g.h = h;
   g.ih = 1.0 / h;
   g.dt = dt;
@@ -909,7 +910,8 @@ bool params_valid(const stc_params& prm) {
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
       prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1 || prm.nz < 0 ||
-      prm.nz == 1);
+      prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 ||
+      (prm.boundary == 1 && (prm.nz == 0 || prm.nx % 2 || prm.ny % 2 || prm.nz % 2)));
 }
 
 // Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
@@ -1013,6 +1015,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->al_threshold = -1.0;
   p->time_coarsen = 0;
   p->nz = 0;
+  p->boundary = 0;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -1166,7 +1169,7 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
           }
           const int p = axis == 0 ? i : (axis == 1 ? j : k);
           const int n = axis == 0 ? g0.nx : (axis == 1 ? g0.ny : g0.nz);
-          if (p == 0 || p == n) vv[f] = 0.0;
+          if (p == n || (!g0.periodic && p == 0)) vv[f] = 0.0;   // walls / the unused periodic slot
         }
       } else {
         for (int j = 0; j < g0.ny; ++j) {

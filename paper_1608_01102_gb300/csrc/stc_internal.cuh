@@ -23,6 +23,7 @@ struct Geom {
   int Fx, F, C;      // x-face count, face count, cell count
   int dim, nz;       // 2 or 3; cells along z (1 in 2D)
   int Fy, Fxy;       // y-face count; x- plus y-face count
+  int periodic;      // 3D only: 1 = every axis wraps (face slot n of an axis is unused)
   double h, ih;      // cell size and 1/h
   double dt, idt;    // timestep and 1/dt
   double a;          // K / r   (Eq. KKTAO row 1)

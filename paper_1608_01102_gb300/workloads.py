@@ -144,19 +144,22 @@ def face_count3(nx, ny, nz):
     return nz * ny * (nx + 1) + nz * (ny + 1) * nx + (nz + 1) * ny * nx
 
 
-def interior_face_mask3(nx, ny, nz):
+def interior_face_mask3(nx, ny, nz, periodic=False):
+    """1 on the face unknowns: interior faces of the closed box, or every face
+    slot but the unused slot n of each axis on the periodic grid."""
+    lo = 0 if periodic else 1
     mx = np.zeros((nz, ny, nx + 1))
-    mx[:, :, 1:nx] = 1.0
+    mx[:, :, lo:nx] = 1.0
     my = np.zeros((nz, ny + 1, nx))
-    my[:, 1:ny, :] = 1.0
+    my[:, lo:ny, :] = 1.0
     mz = np.zeros((nz + 1, ny, nx))
-    mz[1:nz] = 1.0
+    mz[lo:nz] = 1.0
     return np.concatenate([mx.ravel(), my.ravel(), mz.ravel()])
 
 
-def random_faces3(rng, nx, ny, nz, count, scale=1.0):
-    """Random 3D face fields, zero on wall faces: (count, F)."""
-    m = interior_face_mask3(nx, ny, nz)
+def random_faces3(rng, nx, ny, nz, count, scale=1.0, periodic=False):
+    """Random 3D face fields, zero on wall faces (on the unused slots if periodic): (count, F)."""
+    m = interior_face_mask3(nx, ny, nz, periodic)
     return rng.standard_normal((count, face_count3(nx, ny, nz))) * m * scale
 
 

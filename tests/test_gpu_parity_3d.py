@@ -19,14 +19,16 @@ PREC = [1, 0]
 
 
 def make_pair3(nx, ny, nz, N, precision=1, levels=1, r=1e-2, K=1.0, keyframes="end", sigma=0.15, dt=None,
-               **over):
+               periodic=False, **over):
     rho0 = workloads.gaussian_ball3(nx, ny, nz, (0.5, 0.35 * ny / nx, 0.5 * nz / nx), sigma)
     star = workloads.gaussian_ball3(nx, ny, nz, (0.5, 0.65 * ny / nx, 0.45 * nz / nx), sigma)
     kf = {N: (star, 1.0)} if keyframes == "end" else (keyframes or {})
     dt = 1.0 / N if dt is None else dt
     o_over = {k: v for k, v in over.items() if k not in ("poisson_vcycles", "scgs_omega")}
-    P = kkt.Problem(nx, ny, N, dt, rho0, r=r, K=K, keyframes=kf, metric_levels=levels, nz=nz, **o_over)
-    prm = stc.default_params(nx, ny, N, precision=precision, r=r, K=K, metric_levels=levels, dt=dt, nz=nz)
+    P = kkt.Problem(nx, ny, N, dt, rho0, r=r, K=K, keyframes=kf, metric_levels=levels, nz=nz, periodic=periodic,
+                    **o_over)
+    prm = stc.default_params(nx, ny, N, precision=precision, r=r, K=K, metric_levels=levels, dt=dt, nz=nz,
+                             boundary=1 if periodic else 0)
     for k, v in over.items():
         setattr(prm, k, int(v) if isinstance(v, bool) else v)
     G = stc.Problem(prm, rho0)
@@ -35,9 +37,9 @@ def make_pair3(nx, ny, nz, N, precision=1, levels=1, r=1e-2, K=1.0, keyframes="e
     return P, G
 
 
-def velocity3(nx, ny, nz, N, amp=0.6, seed=0, noise=0.05):
+def velocity3(nx, ny, nz, N, amp=0.6, seed=0, noise=0.05, periodic=False):
     rng = np.random.default_rng(seed)
-    m = workloads.interior_face_mask3(nx, ny, nz)
+    m = workloads.interior_face_mask3(nx, ny, nz, periodic)
     v = np.zeros((N + 1, workloads.face_count3(nx, ny, nz)))
     for i in range(1, N + 1):
         c = (0.5 + 0.1 * np.sin(i), 0.5 * ny / nx + 0.05 * np.cos(i), 0.5 * nz / nx)
@@ -201,8 +203,9 @@ def test_scgs_sweep_3d(prec, shape, N):
             assert err <= tol * np.linalg.norm(d) + floor, (l, k, err / max(np.linalg.norm(d), 1e-300))
 
 
+@pytest.mark.parametrize("periodic", [False, True])
 @pytest.mark.parametrize("prec", PREC)
-def test_scgs_sweep_3d_thread_per_cell(prec):
+def test_scgs_sweep_3d_thread_per_cell(prec, periodic):
     """A colour of >= 16384 cells runs the thread-per-cell block Thomas kernel
     (64 x 64 x 32: 16384 cells per colour on the finest level).  From the zero
     state towards a smooth target: the first sweep builds a velocity, the
@@ -210,8 +213,8 @@ def test_scgs_sweep_3d_thread_per_cell(prec):
     O(1) pressures at h = 1/64 is amplified ~1e16-fold by the colour sweeps --
     no test of anything.)"""
     nx, ny, nz, N = 64, 64, 32, 2
-    P, G = make_pair3(nx, ny, nz, N, precision=prec)
-    z = velocity3(nx, ny, nz, N, amp=0.5, seed=45)[1:]
+    P, G = make_pair3(nx, ny, nz, N, precision=prec, periodic=periodic)
+    z = velocity3(nx, ny, nz, N, amp=0.5, seed=45, periodic=periodic)[1:]
     G.set("Z", z)
     x = kkt.zero_state(P)
     res = kkt.zero_state(P, P.grid)
@@ -335,3 +338,138 @@ def test_admm_iterations_3d(prec):
     div_gpu = max(np.max(np.abs(mac.div(P.grid, a))) for a in v)
     div_ref = max(np.max(np.abs(mac.div(P.grid, a))) for a in x["v"])
     assert div_gpu <= 2 * div_ref + (1e-10 if prec == 1 else 1e-4), (div_gpu, div_ref)
+
+
+# ---------------------------------------------------------------------------
+# periodic boundaries (every axis wraps), the same steps against the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", PREC)
+def test_periodic_residual_transfers_and_sweep(prec):
+    nx, ny, nz, N = 8, 8, 8, 3
+    P, G = make_pair3(nx, ny, nz, N, precision=prec, periodic=True, dt=1.0 / 16)
+    grids = stfas.hierarchy(P)
+    for l, g in enumerate(grids):
+        x = random_state3(P, 110 + l, grid=g, scale=0.3)
+        x["u"] *= 0.3
+        z = np.random.default_rng(120 + l).standard_normal((N, g.F)) * g.interior_faces() * 0.3
+        G.set_state(x, level=l)
+        G.set("Z", z, level=l)
+        G.nso_residual(level=l)
+        f = kkt.nso_residual(P, g, x, z)
+        got = G.get_state(level=l, prefix="RES_")
+        dbl = prec == 1 or (l == len(grids) - 1 and l > 0)
+        for k in f:
+            assert rel(got[k], f[k]) < (1e-12 if dbl else 2e-6), (l, k, rel(got[k], f[k]))
+        res = kkt.zero_state(P, g)
+        G.smooth(level=l, sweeps=1)
+        ref = kkt.copy_state(x)
+        scgs.sweep(P, g, ref, z, res)
+        got = G.get_state(level=l)
+        for k in ref:
+            d = ref[k] - x[k]
+            err = np.linalg.norm(got[k] - ref[k])
+            tol = TOL[1]["smooth"] if prec == 1 else TOL[0]["smooth"]
+            floor = 0.0 if prec == 1 else 2e-7 * np.linalg.norm(x[k])
+            assert err <= tol * np.linalg.norm(d) + floor, (l, k, err / max(np.linalg.norm(d), 1e-300))
+    x0 = random_state3(P, 130)
+    G.set_state(x0, 0)
+    G.restrict(0)
+    xc = stfas.restrict_state(grids[0], x0)
+    got = G.get_state(1)
+    tol = 1e-14 if prec == 1 else 1e-6
+    for k in xc:
+        assert rel(got[k], xc[k]) < tol, k
+    xn = random_state3(P, 131, grid=grids[1])
+    G.set_state(xn, 1)
+    G.prolong_correct(0)
+    corr = stfas.prolong_state(grids[0], grids[1], kkt.state_sub(xn, xc))
+    corr["v"][0] = 0.0
+    corr["pbar"][0] = 0.0
+    got = G.get_state(0)
+    for k in x0:
+        assert rel(got[k], x0[k] + corr[k]) < tol * 10, k
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_periodic_advection_adjoint_and_projection(prec):
+    nx, ny, nz, N = 8, 8, 8, 4
+    mid = workloads.gaussian_ball3(nx, ny, nz, (0.1, 0.5, 0.5), 0.12)     # straddles the wrap
+    end = workloads.gaussian_ball3(nx, ny, nz, (0.9, 0.6, 0.4), 0.12)
+    kf = {N // 2: (mid, 0.5), N: (end, 1.0)}
+    P, G = make_pair3(nx, ny, nz, N, precision=prec, levels=2, keyframes=kf, K=2.0, periodic=True)
+    rng = np.random.default_rng(140)
+    v = np.zeros((N + 1, P.grid.F))
+    v[1:] = rng.standard_normal((N, P.grid.F)) * P.grid.interior_faces() * 0.4
+    v[:, :P.grid.Fx] += 0.6 * P.grid.interior_faces()[:P.grid.Fx]   # a mean flow across the wrap
+    w = rng.standard_normal((N, P.grid.F)) * P.grid.interior_faces() * 0.2
+    G.set("VSTAR", v[:N])
+    G.set("W", w)
+    G.advect("VSTAR")
+    G.metric_terms()
+    G.adjoint("VSTAR", 1.0, 1.0 / P.K)
+    rhos, Ks = kkt.forward_density(P, v[:N])
+    np.testing.assert_array_equal(G.taylor_orders(), Ks)
+    rho = G.get("RHO")
+    for i in range(N + 1):
+        assert rel(rho[i], rhos[i]) < (1e-12 if prec == 1 else 1e-5), i
+    mt = G.get("MTERM")
+    for s in kf:
+        assert rel(mt[s], P.misfit_grad(s, rhos[s])) < (1e-11 if prec == 1 else 2e-5), s
+    mu_ref = kkt.adjoint_density(P, v[:N], rhos, Ks)
+    mu = G.get("MU")
+    for s in range(N):
+        assert rel(mu[s], mu_ref[s]) < (1e-11 if prec == 1 else 2e-5), s
+    dens = kkt.density_gradient(P, v[:N], rhos, Ks, mu_ref)
+    y = G.get("Y")
+    for s in range(1, N):
+        assert rel(y[s], w[s] - dens[s] / P.K) < (1e-11 if prec == 1 else 2e-5), s
+    # projection of 3 fields (the constant x-flow is harmonic and survives)
+    G.set("W", w)
+    G.project("W", 0, 3)
+    out = G.get("W")
+    for i in range(3):
+        ref = projection.project(P.grid, w[i])
+        assert rel(out[i], ref) < TOL[prec]["project"] * 5, (i, rel(out[i], ref))
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_periodic_vcycle_kkt_and_admm(prec):
+    nx, ny, nz, N = 8, 8, 8, 4
+    P, G = make_pair3(nx, ny, nz, N, precision=prec, r=1e-3, periodic=True)
+    v = velocity3(nx, ny, nz, N, amp=0.5, seed=150, periodic=True)
+    lam = workloads.random_faces3(np.random.default_rng(151), nx, ny, nz, N, 0.05, periodic=True)
+    lam[0] = 0.0
+    G.set("VSTAR", v[:N])
+    G.set("LAMBDA", lam)
+    G.prepare_targets()
+    z = v[:N] - lam / P.K
+    x = kkt.zero_state(P)
+    for c in range(2):
+        f_gpu = G.vcycle(1)
+        f_ref = stfas.stfas_cycle(P, x, z)
+        got = G.get_state(0)
+        for k in x:
+            assert rel(got[k], x[k]) < TOL[prec]["vcycle"], (c, k, rel(got[k], x[k]))
+        assert abs(f_gpu - f_ref) <= 1e-3 * f_ref + TOL[prec]["vcycle"] * 1e3
+    vs = np.array([projection.project(P.grid, a) for a in v])
+    G.set("V", vs)
+    norm = G.kkt_residual()
+    g_ref = kkt.reduced_gradient(P, vs)
+    tol = 2e-7 if prec == 1 else 2e-4
+    assert rel(G.get("KKT_G")[1:], g_ref[1:]) < tol
+    assert abs(norm - np.linalg.norm(g_ref)) <= tol * np.linalg.norm(g_ref)
+    P2, G2 = make_pair3(nx, ny, nz, N, precision=prec, r=1e-3, periodic=True)
+    rep = G2.solve(tol=1e-12, max_admm=2)
+    xs, _, _, hist = admm.solve(P2, tol=1e-12, max_admm=2, eps_admm=P2.rho_scale / 100)
+    tol = 1e-5 if prec == 1 else 2e-3
+    assert rep["admm_iters"] == len(hist)
+    assert abs(rep["kkt_rel"] - hist[-1]["kkt_rel"]) <= tol * hist[-1]["kkt_rel"]
+    assert rel(G2.get("V"), xs["v"]) < tol
+
+
+def test_periodic_parameters_are_validated():
+    with pytest.raises(stc.StcError):
+        make_pair3(8, 8, 6 + 1, 2, periodic=True)          # odd nz breaks the parity colours
+    prm = stc.default_params(16, 16, 4, boundary=1)       # 2D: periodic is a 3D option
+    with pytest.raises(stc.StcError):
+        stc.Problem(prm, np.ones(256))
