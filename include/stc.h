@@ -109,6 +109,13 @@ typedef struct {
                            Face layouts keep n + 1 slots per axis; slot n is not a face
                            and reads as zero; neighbour indices, QUICK stencils, the
                            metric filters and the transfers wrap. */
+  int scgs_cta_cells;   /* 2D smoother kernel choice, results unchanged: a colour of at
+                           most this many cells runs one CTA per cell (each block step of
+                           the cyclic reduction split over the CTA's threads; short
+                           dependency chains for the coarse levels), a larger one a warp
+                           per cell.  0: always a warp per cell.  -1 (default): 256 for
+                           fp32 solves, every colour for fp64 solves (the faster choice
+                           measured on GB300 for each solve type). */
 } stc_params;
 
 typedef struct {

@@ -424,23 +424,14 @@ __device__ __forceinline__ S shift_sym(S A[4][4], const CellG<S>& cg) {
   return gam;
 }
 
-template <class T, class S>
-__global__ void __launch_bounds__(256)
-scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb,
-                   const double* __restrict__ lm_dev) {
-  pdl_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Phases A and A2 of one colour's SCGS for the cells q0 .. q0 + cpb - 1 (see
+// above): U_t, y_t and the v-block records (STRIDE values per block) in
+// shared memory; ends with a CTA barrier.
+template <class T, class S, int STRIDE>
+__device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, const CState<T>& r, int colour,
+                                              int ncx, int ncell, int cpb, int q0, S lm, S* Us, S* Bu, S* Vb) {
   const int N = g.N;
-  // Levenberg-Marquardt shift of the v blocks: a device scalar when the solve
-  // adapts it between V-cycles (the captured graph stays valid), else g.lm
-  const S lm = S(lm_dev ? *lm_dev : g.lm);
-  const int ncell = ncx * ncy;
-  const int q0 = blockIdx.x * cpb;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
-  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u -> y_t [N][5][cpb]
-  S* Vb = Bu + (size_t)N * 5 * cpb;                   // v blocks   [cpb][N][kCrStride]
   const S idt = pick<S>(g.idt, g.idtf);
-
   // ---- phase A: couplings and right-hand sides ----------------------------
   for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
     const int c = item % cpb, t = item / cpb;
@@ -461,7 +452,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
         U[(a2 * 4 + b2) * cpb] =
             ((a2 == b2 ? pick<S>(g.idt, g.idtf) : S(0)) + S(g.self_adv) * Jl[a2][b2]) * S(act[a2] * act[b2]);
     S* Ru = Bu + (size_t)t * 5 * cpb + c;
-    S* Rv = Vb + ((size_t)c * N + t) * kCrStride + CR_R;
+    S* Rv = Vb + ((size_t)c * N + t) * STRIDE + CR_R;
     const T* ru = r.u + (size_t)t * g.F;
     const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
@@ -504,7 +495,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     CellG<S> cg_;
     cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
     const int tv = t + 1;
-    S* V = Vb + ((size_t)c * N + t) * kCrStride;
+    S* V = Vb + ((size_t)c * N + t) * STRIDE;
     const S* U = Us + (size_t)t * 16 * cpb + c;     // U_{tv-1}
     S Um[4][4];
 #pragma unroll
@@ -566,6 +557,93 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     }
   }
   __syncthreads();
+
+}
+
+// Phase C: the u blocks from the solved v blocks, x += omega delta.
+template <class T, class S, int STRIDE>
+__device__ __forceinline__ void scgs_update(const Geom& g, const State<T>& x, int colour, int ncx, int ncell,
+                                            int cpb, int q0, const S* Us, const S* Bu, const S* Vb) {
+  const int N = g.N;
+  const S idt = pick<S>(g.idt, g.idtf);
+  // ---- phase C: u blocks from the v solution, x += omega * delta -----------
+  // The old values of the 10 unknowns are all loaded before any store: the
+  // state arrays may alias as far as the compiler knows, so interleaved
+  // read-modify-writes would serialise ten global-memory latencies.
+  const T om = pick<T>(g.omega, g.omegaf);
+  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
+    const int c = item % cpb, t = item / cpb;
+    const int q = q0 + c;
+    if (q >= ncell) continue;
+    const int i = 2 * (q % ncx) + (colour & 1);
+    const int j = 2 * (q / ncx) + (colour >> 1);
+    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
+    const bool actb[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
+    const int cc = cidx(g, j, i);
+    T* fu = x.u + (size_t)t * g.F;
+    T* fv = x.v + (size_t)(t + 1) * g.F;
+    T* fp = x.p + (size_t)t * g.C + cc;
+    T* fpb = x.pbar + (size_t)(t + 1) * g.C + cc;
+    T old_u[4], old_v[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      old_u[a2] = actb[a2] ? fu[fidx[a2]] : T(0);
+      old_v[a2] = actb[a2] ? fv[fidx[a2]] : T(0);
+    }
+    const T old_p = *fp, old_pb = *fpb;
+    CellG<S> cg_;
+    cg_.init(g, i, j);
+    // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
+    const S* U = Us + (size_t)t * 16 * cpb + c;
+    const S* xv1 = Vb + ((size_t)c * N + t) * STRIDE + CR_Z;          // v_{t+1}
+    const S* xv0 = Vb + ((size_t)c * N + (t > 0 ? t - 1 : 0)) * STRIDE + CR_Z;   // v_t
+    S w[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      S v = S(0);
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) v -= U[(a2 * 4 + b2) * cpb] * xv1[b2];
+      if (t >= 1) v += idt * cg_.act[a2] * xv0[a2];
+      w[a2] = v;
+    }
+    S pw[4];
+    cg_.proj(w, pw);
+    S gw = S(0);
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) gw += cg_.gh[a2] * w[a2];
+    const S* y = Bu + (size_t)t * 5 * cpb + c;
+    S du[5];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
+    du[4] = y[4 * cpb] + gw;
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2)
+      if (actb[a2]) {
+        fu[fidx[a2]] = old_u[a2] + om * T(du[a2]);
+        fv[fidx[a2]] = old_v[a2] + om * T(xv1[a2]);
+      }
+    *fp = old_p + om * T(du[4]);
+    *fpb = old_pb + om * T(xv1[4]);
+  }
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(256)
+scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb,
+                   const double* __restrict__ lm_dev) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = g.N;
+  // Levenberg-Marquardt shift of the v blocks: a device scalar when the solve
+  // adapts it between V-cycles (the captured graph stays valid), else g.lm
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
+  const int ncell = ncx * ncy;
+  const int q0 = blockIdx.x * cpb;
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
+  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u -> y_t [N][5][cpb]
+  S* Vb = Bu + (size_t)N * 5 * cpb;                   // v blocks   [cpb][N][kCrStride]
+
+  scgs_assemble<T, S, kCrStride>(g, x, r, colour, ncx, ncell, cpb, q0, lm, Us, Bu, Vb);
 
   // ---- phase B: cyclic reduction over the v blocks, one warp per cell -------
   {
@@ -732,65 +810,182 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   }
   __syncthreads();
 
-  // ---- phase C: u blocks from the v solution, x += omega * delta -----------
-  // The old values of the 10 unknowns are all loaded before any store: the
-  // state arrays may alias as far as the compiler knows, so interleaved
-  // read-modify-writes would serialise ten global-memory latencies.
-  const T om = pick<T>(g.omega, g.omegaf);
-  for (int item = threadIdx.x; item < cpb * N; item += blockDim.x) {
-    const int c = item % cpb, t = item / cpb;
-    const int q = q0 + c;
-    if (q >= ncell) continue;
-    const int i = 2 * (q % ncx) + (colour & 1);
-    const int j = 2 * (q / ncx) + (colour >> 1);
-    const int fidx[4] = {xf(g, j, i), xf(g, j, i + 1), yf(g, j, i), yf(g, j + 1, i)};
-    const bool actb[4] = {i > 0, i < g.nx - 1, j > 0, j < g.ny - 1};
-    const int cc = cidx(g, j, i);
-    T* fu = x.u + (size_t)t * g.F;
-    T* fv = x.v + (size_t)(t + 1) * g.F;
-    T* fp = x.p + (size_t)t * g.C + cc;
-    T* fpb = x.pbar + (size_t)(t + 1) * g.C + cc;
-    T old_u[4], old_v[4];
+  scgs_update<T, S, kCrStride>(g, x, colour, ncx, ncell, cpb, q0, Us, Bu, Vb);
+}
+
+// The same colour step with one CTA per cell, for colours of few cells (the
+// coarse levels), where the warp-per-cell reduction leaves the GPU idle and
+// its time is the length of one cell's dependency chain.  Every block step of
+// the cyclic reduction is split over the CTA's threads: an odd block's
+// elimination by right-hand-side column (each thread a saddle solve with one
+// column: the same factorisation and the same arithmetic per column as the
+// nine-column solve), an even block's update by output entry (the 10 entries
+// of the symmetric face block, 4 of the right-hand side, 16 of the new
+// coupling), the unwinding by unknown.  The couplings are double-buffered
+// (CR_C at even levels, CR_C2 at odd ones) because an even block's update
+// reads its old coupling while writing the new one.
+constexpr int kCrStride2 = 93;
+enum : int { CR_C2 = 77 };
+constexpr int kCellCtaThreads = 128;
+
+__host__ __device__ inline size_t scgs_cell_floats2(int N) { return (size_t)(16 + 5 + kCrStride2) * N; }
+
+template <class T, class S>
+__global__ void __launch_bounds__(kCellCtaThreads)
+scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
+                        const double* __restrict__ lm_dev) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = g.N;
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
+  const int ncell = ncx * ncy;
+  const int q = blockIdx.x;
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16]
+  S* Bu = Us + (size_t)N * 16;                        // b_u -> y_t [N][5]
+  S* V = Bu + (size_t)N * 5;                          // v blocks   [N][kCrStride2]
+  scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V);
+
+  CellG<S> cg_;
+  cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+  int top = 0, lev = 0;
+  for (int s2 = 1; s2 < N; s2 <<= 1, ++lev) {
+    top = s2;
+    const int cur = (lev & 1) ? CR_C2 : CR_C, nxt = (lev & 1) ? CR_C : CR_C2;
+    const int nk = (N + s2 - 1) / s2;      // blocks k s2 < N; odd k are eliminated
+    const int nodd = nk / 2, neven = (nk + 1) / 2;
+    // eliminate the odd blocks o = s2 (2m + 1), one right-hand-side column per thread
+    for (int task = threadIdx.x; task < nodd * 9; task += blockDim.x) {
+      const int m = task / 9, col = task - 9 * m;
+      const int o = s2 * (2 * m + 1);
+      const bool hasb = o + s2 < N;
+      S* Vo = V + (size_t)o * kCrStride2;
+      const S* Va = V + (size_t)(o - s2) * kCrStride2;
+      S A[4][4];
+      load_sym(Vo + CR_A, A);
+      S B[4][1];
 #pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2) {
-      old_u[a2] = actb[a2] ? fu[fidx[a2]] : T(0);
-      old_v[a2] = actb[a2] ? fv[fidx[a2]] : T(0);
-    }
-    const T old_p = *fp, old_pb = *fpb;
-    CellG<S> cg_;
-    cg_.init(g, i, j);
-    // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
-    const S* U = Us + (size_t)t * 16 * cpb + c;
-    const S* xv1 = Vb + ((size_t)c * N + t) * kCrStride + CR_Z;          // v_{t+1}
-    const S* xv0 = Vb + ((size_t)c * N + (t > 0 ? t - 1 : 0)) * kCrStride + CR_Z;   // v_t
-    S w[4];
+      for (int r2 = 0; r2 < 4; ++r2)
+        B[r2][0] = col < 4 ? Va[cur + col * 4 + r2]                                  // (coupling a -> o)^T
+                 : col < 8 ? (hasb ? Vo[cur + r2 * 4 + (col - 4)] : S(0))           // coupling o -> b
+                           : Vo[CR_R + r2];
+      S qv[1] = {col == 8 ? Vo[CR_R + 4] : S(0)};
+      const S gam = shift_sym(A, cg_);
+      S Y[1];
+      saddle_solve<S, 1>(A, cg_.g, B, qv, Y);
+      if (col < 8) {
+        S* Z = Vo + (col < 4 ? CR_ZL : CR_ZR);
+        const int c2 = col & 3;
 #pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2) {
-      S v = S(0);
+        for (int r2 = 0; r2 < 4; ++r2) Z[r2 * 4 + c2] = B[r2][0];
+        Z[16 + c2] = Y[0];
+      } else {
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) v -= U[(a2 * 4 + b2) * cpb] * xv1[b2];
-      if (t >= 1) v += idt * cg_.act[a2] * xv0[a2];
-      w[a2] = v;
-    }
-    S pw[4];
-    cg_.proj(w, pw);
-    S gw = S(0);
-#pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2) gw += cg_.gh[a2] * w[a2];
-    const S* y = Bu + (size_t)t * 5 * cpb + c;
-    S du[5];
-#pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
-    du[4] = y[4 * cpb] + gw;
-#pragma unroll
-    for (int a2 = 0; a2 < 4; ++a2)
-      if (actb[a2]) {
-        fu[fidx[a2]] = old_u[a2] + om * T(du[a2]);
-        fv[fidx[a2]] = old_v[a2] + om * T(xv1[a2]);
+        for (int r2 = 0; r2 < 4; ++r2) Vo[CR_Z + r2] = B[r2][0];
+        Vo[CR_Z + 4] = Y[0] + gam * qv[0];
       }
-    *fp = old_p + om * T(du[4]);
-    *fpb = old_pb + om * T(xv1[4]);
+    }
+    __syncthreads();
+    // update the even blocks e = 2 s2 m from both eliminated neighbours, one entry per thread
+    for (int task = threadIdx.x; task < neven * 30; task += blockDim.x) {
+      const int m = task / 30, k = task - 30 * m;
+      const int e = 2 * s2 * m;
+      S* Ve = V + (size_t)e * kCrStride2;
+      const int o2 = e + s2, o1 = e - s2;
+      const S* V2 = o2 < N ? V + (size_t)o2 * kCrStride2 : nullptr;
+      const S* V1 = o1 >= 0 ? V + (size_t)o1 * kCrStride2 : nullptr;
+      if (k < 10) {
+        // A[a][b] and A[b][a] as the warp kernel forms them, then symmetrised
+        // row a, column b of the k-th stored entry (rows of the upper triangle)
+        const int a = k < 4 ? 0 : k < 7 ? 1 : k < 9 ? 2 : 3;
+        const int b = k < 4 ? k : k < 7 ? k - 3 : k < 9 ? k - 5 : 3;
+        S ab = Ve[CR_A + k], ba = ab;
+        if (V2) {
+          S aL = S(0), bL = S(0);
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) {
+            aL += Ve[cur + a * 4 + k2] * V2[CR_ZL + k2 * 4 + b];
+            bL += Ve[cur + b * 4 + k2] * V2[CR_ZL + k2 * 4 + a];
+          }
+          ab -= aL;
+          ba -= bL;
+        }
+        if (V1) {
+          S aR = S(0), bR = S(0);
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) {
+            aR += V1[cur + k2 * 4 + a] * V1[CR_ZR + k2 * 4 + b];
+            bR += V1[cur + k2 * 4 + b] * V1[CR_ZR + k2 * 4 + a];
+          }
+          ab -= aR;
+          ba -= bR;
+        }
+        Ve[CR_A + k] = S(0.5) * (ab + ba);
+      } else if (k < 14) {
+        const int r2 = k - 10;
+        S rf = Ve[CR_R + r2];
+        if (V2) {
+          S az = S(0);
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) az += Ve[cur + r2 * 4 + k2] * V2[CR_Z + k2];
+          rf -= az;
+        }
+        if (V1) {
+          S az = S(0);
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) az += V1[cur + k2 * 4 + r2] * V1[CR_Z + k2];
+          rf -= az;
+        }
+        Ve[CR_R + r2] = rf;
+      } else {
+        const int r2 = (k - 14) >> 2, c2 = (k - 14) & 3;
+        S cn = S(0);
+        if (V2 && o2 + s2 < N) {
+          S aR = S(0);
+#pragma unroll
+          for (int k2 = 0; k2 < 4; ++k2) aR += Ve[cur + r2 * 4 + k2] * V2[CR_ZR + k2 * 4 + c2];
+          cn = -aR;
+        }
+        Ve[nxt + r2 * 4 + c2] = cn;
+      }
+    }
+    __syncthreads();
   }
+  // the last remaining block
+  if (threadIdx.x == 0) {
+    S A[4][4];
+    load_sym(V + CR_A, A);
+    S B[4][1];
+    S qv[1] = {V[CR_R + 4]};
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) B[r2][0] = V[CR_R + r2];
+    const S gam = shift_sym(A, cg_);
+    S Y[1];
+    saddle_solve<S, 1>(A, cg_.g, B, qv, Y);
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) V[CR_Z + r2] = B[r2][0];
+    V[CR_Z + 4] = Y[0] + gam * qv[0];
+  }
+  __syncthreads();
+  // unwind: x_o = z_o - ZL_o x_a - ZR_o x_b, one unknown per thread
+  for (int s2 = top; s2 >= 1; s2 >>= 1) {
+    const int nodd = ((N + s2 - 1) / s2) / 2;
+    for (int task = threadIdx.x; task < nodd * 5; task += blockDim.x) {
+      const int m = task / 5, r2 = task - 5 * m;
+      const int o = s2 * (2 * m + 1);
+      S* Vo = V + (size_t)o * kCrStride2;
+      const S* Va = V + (size_t)(o - s2) * kCrStride2;
+      const bool hasb = o + s2 < N;
+      S v = Vo[CR_Z + r2];
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) {
+        const S xb = hasb ? V[(size_t)(o + s2) * kCrStride2 + CR_Z + k2] : S(0);
+        v -= Vo[CR_ZL + r2 * 4 + k2] * Va[CR_Z + k2] + Vo[CR_ZR + r2 * 4 + k2] * xb;
+      }
+      Vo[CR_Z + r2] = v;
+    }
+    __syncthreads();
+  }
+  scgs_update<T, S, kCrStride2>(g, x, colour, ncx, ncell, 1, q, Us, Bu, V);
 }
 
 // ---------------------------------------------------------------------------
@@ -1079,6 +1274,27 @@ int scgs_cells_per_cta(int N) {
   return c < 1 ? 1 : c;
 }
 
+// the CTA-per-cell kernel; false (nothing launched) when one cell's records
+// do not fit in shared memory
+template <class T, class S>
+static bool launch_scgs_cell_ts(const Geom& g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
+                                const double* lm_dev, cudaStream_t st) {
+  static std::once_flag attr_once;
+  static int max_smem = 0;
+  std::call_once(attr_once, [] {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, (const void*)scgs_colour_cell_kernel<T, S>);
+    max_smem = 227 * 1024 - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute((const void*)scgs_colour_cell_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         max_smem);
+  });
+  const size_t sm = scgs_cell_floats2(g.N) * sizeof(S);
+  if (sm > (size_t)max_smem) return false;
+  launch_pdl(scgs_colour_cell_kernel<T, S>, dim3(ncx * ncy), dim3(kCellCtaThreads), sm, st, g, x, r, colour, ncx,
+             ncy, lm_dev);
+  return true;
+}
+
 template <class T, class S>
 static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev,
                            cudaStream_t st) {
@@ -1086,6 +1302,11 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
   const int ncy = colour_extent(g.ny, colour >> 1);
   const int ncell = ncx * ncy;
   if (ncell <= 0) return;
+  // measured on the 128^2 x 40 hierarchy: fp32 solves are faster with a warp
+  // per cell above ~256 cells per colour, fp64 solves with a CTA per cell at
+  // every level
+  const int cta_cells = g.cta_cells >= 0 ? g.cta_cells : (sizeof(S) == 4 ? 256 : 1 << 30);
+  if (ncell <= cta_cells && launch_scgs_cell_ts<T, S>(g, x, r, colour, ncx, ncy, lm_dev, st)) return;
   const int cpb = scgs_cells_per_cta<S>(g.N);
   const size_t sm = (size_t)cpb * scgs_cell_floats(g.N) * sizeof(S);
   static std::once_flag attr_once;

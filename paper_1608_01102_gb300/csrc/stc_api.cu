@@ -173,6 +173,7 @@ Geom make_geom(const stc_params& prm, int nx, int ny, int nz, double h, int N, d
   g.lm = prm.lm_shift < 0 ? 1.0 / (prm.dt * prm.dt) : prm.lm_shift;
   g.omega = prm.scgs_omega;
   g.self_adv = prm.self_advection ? 1 : 0;
+  g.cta_cells = prm.scgs_cta_cells;
   set_fp32_copies(g);
   return g;
 }
@@ -910,7 +911,7 @@ bool params_valid(const stc_params& prm) {
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
       prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1 || prm.nz < 0 ||
-      prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 ||
+      prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 || prm.scgs_cta_cells < -1 ||
       (prm.boundary == 1 && (prm.nz == 0 || prm.nx % 2 || prm.ny % 2 || prm.nz % 2)));
 }
 
@@ -1016,6 +1017,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->time_coarsen = 0;
   p->nz = 0;
   p->boundary = 0;
+  p->scgs_cta_cells = -1;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }

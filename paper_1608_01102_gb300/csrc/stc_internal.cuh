@@ -30,6 +30,7 @@ struct Geom {
   double lm;         // Levenberg-Marquardt shift of the smoother's v blocks
   double omega;      // SCGS under-relaxation
   int self_adv;      // 1: Adv on (0 only for linear saddle tests)
+  int cta_cells;     // 2D SCGS: colours of at most this many cells take the CTA-per-cell kernel (-1: by solve type)
   // the same scalars rounded to fp32 on the host (set_fp32_copies): fp32
   // kernels read these instead of converting fp64 scalars in every thread
   // (conversions from fp64 run at the much lower fp64 rate)
