@@ -116,6 +116,11 @@ typedef struct {
                            per cell.  0: always a warp per cell.  -1 (default): 256 for
                            fp32 solves, every colour for fp64 solves (the faster choice
                            measured on GB300 for each solve type). */
+  int ao_trials;        /* AO blend (Sec. 5), 2D: blend factors 2^-h tried at once, each
+                           on its own stream with its own trajectory buffers (1..8; 1 =
+                           one at a time; 3D always one at a time).  The accepted factor
+                           is the first that does not raise the objective, exactly as
+                           in the one-at-a-time search.  Default 4. */
 } stc_params;
 
 typedef struct {

@@ -830,23 +830,19 @@ constexpr int kCellCtaThreads = 128;
 
 __host__ __device__ inline size_t scgs_cell_floats2(int N) { return (size_t)(16 + 5 + kCrStride2) * N; }
 
-template <class T, class S>
-__global__ void __launch_bounds__(kCellCtaThreads)
-scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
-                        const double* __restrict__ lm_dev) {
-  pdl_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = g.N;
-  const S lm = S(lm_dev ? *lm_dev : g.lm);
-  const int ncell = ncx * ncy;
-  const int q = blockIdx.x;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16]
-  S* Bu = Us + (size_t)N * 16;                        // b_u -> y_t [N][5]
-  S* V = Bu + (size_t)N * 5;                          // v blocks   [N][kCrStride2]
-  scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V);
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+  if (WARP) __syncwarp();
+  else __syncthreads();
+}
 
-  CellG<S> cg_;
-  cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+// The split cyclic reduction of one cell's v blocks V (records of kCrStride2)
+// by a group of nl threads (rank lane): a warp (WARP) or the whole CTA.  (A
+// warp per cell with this split measured slower than the nine-column solve
+// per lane at every level: the split repeats the factorisation per column and
+// its task kinds diverge within the warp; only a CTA per cell gains.)
+template <class S, bool WARP>
+__device__ __forceinline__ void cr_split(S* V, int N, const CellG<S>& cg_, int lane, int nl) {
   int top = 0, lev = 0;
   for (int s2 = 1; s2 < N; s2 <<= 1, ++lev) {
     top = s2;
@@ -854,7 +850,7 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
     const int nk = (N + s2 - 1) / s2;      // blocks k s2 < N; odd k are eliminated
     const int nodd = nk / 2, neven = (nk + 1) / 2;
     // eliminate the odd blocks o = s2 (2m + 1), one right-hand-side column per thread
-    for (int task = threadIdx.x; task < nodd * 9; task += blockDim.x) {
+    for (int task = lane; task < nodd * 9; task += nl) {
       const int m = task / 9, col = task - 9 * m;
       const int o = s2 * (2 * m + 1);
       const bool hasb = o + s2 < N;
@@ -884,9 +880,9 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
         Vo[CR_Z + 4] = Y[0] + gam * qv[0];
       }
     }
-    __syncthreads();
+    group_sync<WARP>();
     // update the even blocks e = 2 s2 m from both eliminated neighbours, one entry per thread
-    for (int task = threadIdx.x; task < neven * 30; task += blockDim.x) {
+    for (int task = lane; task < neven * 30; task += nl) {
       const int m = task / 30, k = task - 30 * m;
       const int e = 2 * s2 * m;
       S* Ve = V + (size_t)e * kCrStride2;
@@ -948,10 +944,10 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
         Ve[nxt + r2 * 4 + c2] = cn;
       }
     }
-    __syncthreads();
+    group_sync<WARP>();
   }
   // the last remaining block
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     S A[4][4];
     load_sym(V + CR_A, A);
     S B[4][1];
@@ -965,11 +961,11 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
     for (int r2 = 0; r2 < 4; ++r2) V[CR_Z + r2] = B[r2][0];
     V[CR_Z + 4] = Y[0] + gam * qv[0];
   }
-  __syncthreads();
+  group_sync<WARP>();
   // unwind: x_o = z_o - ZL_o x_a - ZR_o x_b, one unknown per thread
   for (int s2 = top; s2 >= 1; s2 >>= 1) {
     const int nodd = ((N + s2 - 1) / s2) / 2;
-    for (int task = threadIdx.x; task < nodd * 5; task += blockDim.x) {
+    for (int task = lane; task < nodd * 5; task += nl) {
       const int m = task / 5, r2 = task - 5 * m;
       const int o = s2 * (2 * m + 1);
       S* Vo = V + (size_t)o * kCrStride2;
@@ -983,8 +979,28 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
       }
       Vo[CR_Z + r2] = v;
     }
-    __syncthreads();
+    group_sync<WARP>();
   }
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(kCellCtaThreads)
+scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
+                        const double* __restrict__ lm_dev) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = g.N;
+  const S lm = S(lm_dev ? *lm_dev : g.lm);
+  const int ncell = ncx * ncy;
+  const int q = blockIdx.x;
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16]
+  S* Bu = Us + (size_t)N * 16;                        // b_u -> y_t [N][5]
+  S* V = Bu + (size_t)N * 5;                          // v blocks   [N][kCrStride2]
+  scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V);
+
+  CellG<S> cg_;
+  cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
+  cr_split<S, false>(V, N, cg_, threadIdx.x, blockDim.x);
   scgs_update<T, S, kCrStride2>(g, x, colour, ncx, ncell, 1, q, Us, Bu, V);
 }
 

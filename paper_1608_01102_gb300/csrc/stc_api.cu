@@ -70,6 +70,8 @@ void ck(cudaError_t e, const char* what) {
 
 void stc::set_last_error(const char* msg) { g_last_error = msg; }
 
+constexpr int kMaxTrials = 8;   // most AO blend factors tried at once
+
 struct stc_problem {
   stc_params prm;
   cudaStream_t st = nullptr;      // user stream (may be the legacy default)
@@ -83,6 +85,22 @@ struct stc_problem {
        *v0 = nullptr;
   void *vcand = nullptr, *rho_c = nullptr;   // AO blend trial: v*, its densities and Taylor orders
   int *K = nullptr, *Kk = nullptr, *K_c = nullptr;
+  // concurrent AO blend trials (2D): trial j's v*, densities, orders, metric
+  // terms, metric temporaries, error flags and objective; trial 0 is
+  // vcand / rho_c / K_c (and mtmp0 / mtmp1)
+  int ntrials = 1;
+  void* tv[kMaxTrials] = {};
+  void* trho[kMaxTrials] = {};
+  int* tK[kMaxTrials] = {};
+  double* tmterm[kMaxTrials] = {};
+  double* ttmp0[kMaxTrials] = {};
+  double* ttmp1[kMaxTrials] = {};
+  int* terr = nullptr;
+  double* dtrial = nullptr;
+  void* htrial = nullptr;         // pinned: kMaxTrials doubles, then kMaxTrials ints
+  cudaStream_t tst[kMaxTrials] = {};
+  cudaEvent_t tfork = nullptr;
+  cudaEvent_t tdone[kMaxTrials] = {};
   bool rho_at_vstar = false;      // rho / K hold the forward sweep of the current v*
   std::vector<int> ao_trace;      // halvings per pass of the last AO
   double* dguard = nullptr;       // per level {before, after} ||res - f||_2^2 of the guarded correction
@@ -351,6 +369,13 @@ void enqueue_top_vcycle(stc_problem* P, cudaStream_t st) {
   residual_norm(P, 0, 0, st);
 }
 
+// device error flags -> the call's error (no flag: nothing)
+void raise_device_errors(int flags) {
+  if (flags & DEV_BARRIER_TIMEOUT) fail(STC_ERR_CUDA, "a grid-wide barrier of a 3D sweep timed out");
+  if (flags & DEV_TAYLOR_KMAX) fail(STC_ERR_DIVERGED, "Taylor series exceeded taylor_kmax");
+  if (flags & DEV_NONFINITE) fail(STC_ERR_DIVERGED, "non-finite value in a residual norm");
+}
+
 // Reads a device fp64 scalar (synchronising the stream) and surfaces device
 // error flags.  With kmax_rejects (an AO blend trial) a Taylor-order overflow,
 // with nonfinite_rejects (an NSO V-cycle under the LM safeguard) a non-finite
@@ -366,9 +391,7 @@ double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool non
     ck(cudaStreamSynchronize(P->st), "sync");
     return std::numeric_limits<double>::infinity();
   }
-  if (*P->herr & DEV_BARRIER_TIMEOUT) fail(STC_ERR_CUDA, "a grid-wide barrier of a 3D sweep timed out");
-  if (*P->herr & DEV_TAYLOR_KMAX) fail(STC_ERR_DIVERGED, "Taylor series exceeded taylor_kmax");
-  if (*P->herr & DEV_NONFINITE) fail(STC_ERR_DIVERGED, "non-finite value in a residual norm");
+  raise_device_errors(*P->herr);
   return P->hscal[slot];
 }
 
@@ -443,31 +466,38 @@ void nso_begin(stc_problem* P) {
 // ---------------------------------------------------------------------------
 // AO / KKT building blocks (finest level)
 // ---------------------------------------------------------------------------
-void metric_terms(stc_problem* P, const void* rho, cudaStream_t st) {
+void metric_terms(stc_problem* P, const void* rho, cudaStream_t st, double* mterm = nullptr, double* tmp0 = nullptr,
+                  double* tmp1 = nullptr) {
   const Geom& g = P->lv[0].g;
-  ck(cudaMemsetAsync(P->mterm, 0, sizeof(double) * (size_t)(g.N + 1) * g.C, st), "memset");
+  if (!mterm) {
+    mterm = P->mterm;
+    tmp0 = P->mtmp0;
+    tmp1 = P->mtmp1;
+  }
+  ck(cudaMemsetAsync(mterm, 0, sizeof(double) * (size_t)(g.N + 1) * g.C, st), "memset");
   for (size_t k = 0; k < P->key_steps.size(); ++k) {
     const int s = P->key_steps[k];
     dispatch(P->dbl, [&](auto tag) {
       using T = decltype(tag);
       launch_metric<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, P->key_c[k], P->prm.metric_levels,
-                       P->prm.metric_sigma0, P->mterm + (size_t)s * g.C, P->mtmp0, P->mtmp1, st);
+                       P->prm.metric_sigma0, mterm + (size_t)s * g.C, tmp0, tmp1, st);
     });
   }
   count(P, (long long)P->key_steps.size() * (P->prm.metric_levels > 0 ? 1 + 4 * P->prm.metric_levels : 2));
   check_launch("metric");
 }
 
-void forward(stc_problem* P, const void* vel, void* rho, int* K, cudaStream_t st) {
+void forward(stc_problem* P, const void* vel, void* rho, int* K, cudaStream_t st, int* err = nullptr) {
   const Geom& g = P->lv[0].g;
+  if (!err) err = P->derr;
   const double thresh = P->prm.taylor_tol * P->rho_scale;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     if (g.dim == 3)
-      ck(launch_taylor_forward3<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, P->adv3, st),
+      ck(launch_taylor_forward3<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, err, P->adv3, st),
          "taylor forward");
     else
-      ck(launch_taylor_forward<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, P->derr, st),
+      ck(launch_taylor_forward<T>(g, (const T*)vel, (T*)rho, K, thresh, P->prm.taylor_kmax, err, st),
          "taylor forward");
   });
   count(P, 1);
@@ -525,22 +555,82 @@ void prepare_targets(stc_problem* P, cudaStream_t st) {
 
 // AO objective of Eq. PO at v* = vel with densities rho (metric terms current):
 // 0.5 sum_keys (rho_s - rho*_s)^T C_s (rho_s - rho*_s) + K/2 sum_{i=1}^{N-1} ||w_i - v*_i||^2
-double ao_objective(stc_problem* P, const void* vel, const void* rho, cudaStream_t st, bool trial = false) {
+// (enqueues the sum into *out, which it zeroes first; mterm: the metric terms of rho)
+void enqueue_ao_objective(stc_problem* P, const void* vel, const void* rho, const double* mterm, double* out,
+                          cudaStream_t st) {
   const Geom& g = P->lv[0].g;
-  ck(cudaMemsetAsync(P->dscal + 4, 0, sizeof(double), st), "memset");
+  ck(cudaMemsetAsync(out, 0, sizeof(double), st), "memset");
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     for (size_t k = 0; k < P->key_steps.size(); ++k) {
       const int s = P->key_steps[k];
-      launch_misfit_dot<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, P->mterm + (size_t)s * g.C,
-                           P->dscal + 4, st);
+      launch_misfit_dot<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, mterm + (size_t)s * g.C, out, st);
     }
-    launch_diff_sumsq<T>((const T*)P->w + g.F, (const T*)vel + g.F, (size_t)(g.N - 1) * g.F, 0.5 * P->prm.K,
-                         P->dscal + 4, st);
+    launch_diff_sumsq<T>((const T*)P->w + g.F, (const T*)vel + g.F, (size_t)(g.N - 1) * g.F, 0.5 * P->prm.K, out, st);
   });
   count(P, (long long)P->key_steps.size() + (g.N > 1 ? 1 : 0));
   check_launch("ao objective");
+}
+
+double ao_objective(stc_problem* P, const void* vel, const void* rho, cudaStream_t st, bool trial = false) {
+  enqueue_ao_objective(P, vel, rho, P->mterm, P->dscal + 4, st);
   return read_scalar(P, 4, trial);
+}
+
+// Sec. 5 blend with P->ntrials factors at once (2D): in a round, trial j
+// tries a = 2^-(h0 + j) on its own stream and buffers (blend, forward sweep,
+// metric terms, objective); the first trial of the round whose objective
+// does not exceed J is taken, so the result is the one-at-a-time search's.
+// Returns the halvings taken (-1: none) and updates J.
+int blend_concurrent(stc_problem* P, double& J, cudaStream_t st) {
+  const Geom& g = P->lv[0].g;
+  const size_t fb = (size_t)g.F * P->ts;
+  double* hval = (double*)P->htrial;
+  int* herrs = (int*)(hval + kMaxTrials);
+  for (int h0 = 0; h0 <= P->prm.ao_halvings; h0 += P->ntrials) {
+    const int nb = std::min(P->ntrials, P->prm.ao_halvings + 1 - h0);
+    ck(cudaEventRecord(P->tfork, st), "event");
+    for (int j = 0; j < nb; ++j) {
+      cudaStream_t s = P->tst[j];
+      ck(cudaStreamWaitEvent(s, P->tfork, 0), "wait");
+      ck(cudaMemcpyAsync(P->tv[j], P->vstar, fb, cudaMemcpyDeviceToDevice, s), "copy v*_0");
+      const double a = std::ldexp(1.0, -(h0 + j));
+      dispatch(P->dbl, [&](auto tag) {
+        using T = decltype(tag);
+        launch_blend_faces<T>(g, g.N - 1, (const T*)P->vstar + g.F, (const T*)P->y + g.F, a, (T*)P->tv[j] + g.F, s);
+      });
+      count(P, g.N > 1 ? 1 : 0);
+      forward(P, P->tv[j], P->trho[j], P->tK[j], s, P->terr + j);
+      metric_terms(P, P->trho[j], s, P->tmterm[j], P->ttmp0[j], P->ttmp1[j]);
+      enqueue_ao_objective(P, P->tv[j], P->trho[j], P->tmterm[j], P->dtrial + j, s);
+      ck(cudaEventRecord(P->tdone[j], s), "event");
+      ck(cudaStreamWaitEvent(st, P->tdone[j], 0), "wait");
+    }
+    ck(cudaMemcpyAsync(hval, P->dtrial, nb * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaMemcpyAsync(herrs, P->terr, nb * sizeof(int), cudaMemcpyDeviceToHost, st), "d2h");
+    ck(cudaMemsetAsync(P->terr, 0, nb * sizeof(int), st), "memset");
+    ck(cudaStreamSynchronize(st), "sync");
+    // a trial's Taylor-order overflow rejects it (as in read_scalar); any
+    // other device error fails the call
+    int other = 0;
+    for (int j = 0; j < nb; ++j) other |= herrs[j] & ~DEV_TAYLOR_KMAX;
+    raise_device_errors(other);
+    for (int j = 0; j < nb; ++j) {
+      const double Jc = (herrs[j] & DEV_TAYLOR_KMAX) ? std::numeric_limits<double>::infinity() : hval[j];
+      if (Jc <= J) {
+        std::swap(P->vstar, P->tv[j]);
+        std::swap(P->rho, P->trho[j]);
+        std::swap(P->K, P->tK[j]);
+        std::swap(P->mterm, P->tmterm[j]);
+        P->vcand = P->tv[0];
+        P->rho_c = P->trho[0];
+        P->K_c = P->tK[0];
+        J = Jc;
+        return h0 + j;
+      }
+    }
+  }
+  return -1;
 }
 
 void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
@@ -578,8 +668,14 @@ void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
       continue;
     }
     // Sec. 5 blend: first a = 2^-h whose forward sweep does not raise the objective
-    ck(cudaMemcpyAsync(P->vcand, P->vstar, fb, cudaMemcpyDeviceToDevice, st), "copy v*_0");
     int taken = -1;
+    if (P->ntrials > 1) {
+      taken = blend_concurrent(P, J, st);
+      P->ao_trace.push_back(taken);
+      if (taken < 0) break;   // the metric terms of the kept v* are untouched
+      continue;
+    }
+    ck(cudaMemcpyAsync(P->vcand, P->vstar, fb, cudaMemcpyDeviceToDevice, st), "copy v*_0");
     double a = 1.0;
     for (int h = 0; h <= P->prm.ao_halvings; ++h, a *= 0.5) {
       dispatch(P->dbl, [&](auto tag) {
@@ -911,13 +1007,19 @@ bool params_valid(const stc_params& prm) {
       !(prm.scgs_omega > 0) || prm.poisson_vcycles < 1 || prm.ao_halvings < -1 || prm.ao_halvings > 60 ||
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
       prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1 || prm.nz < 0 ||
-      prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 || prm.scgs_cta_cells < -1 ||
+      prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 || prm.scgs_cta_cells < -1 || prm.ao_trials < 1 || prm.ao_trials > kMaxTrials ||
       (prm.boundary == 1 && (prm.nz == 0 || prm.nx % 2 || prm.ny % 2 || prm.nz % 2)));
 }
 
 // Device bytes that stc_create_problem plus stc_set_keyframes(nkeys) allocate:
 // the same list of buffers as the allocations below, without allocating
 // (the serving admission test).  Must be kept in step with them.
+// blend trials run at once: 2D with the blend on; 3D sweeps share one scratch
+int ao_trial_count(const stc_params& prm) {
+  return (prm.nz == 0 && prm.ao_halvings >= 0) ? std::min(prm.ao_trials, std::min(kMaxTrials, prm.ao_halvings + 1))
+                                               : 1;
+}
+
 size_t plan_bytes(const stc_params& prm, int nkeys) {
   auto b = [](size_t n) { return n == 0 ? (size_t)16 : n; };
   const bool dbl = prm.precision == 1;
@@ -954,6 +1056,10 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
            b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
+  const int nt = ao_trial_count(prm);
+  if (nt > 1)
+    total += (size_t)(nt - 1) * (b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) + b(C * 8) + b(2 * C * 8)) +
+             (size_t)nt * b((N + 1) * C * 8) + b(kMaxTrials * 4) + b(kMaxTrials * 8);
   Geom g0 = make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt);
   if (g0.dim == 3) {
     total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts) +
@@ -973,6 +1079,12 @@ void free_problem(stc_problem* P) {
   if (P->hscal) cudaFreeHost(P->hscal);
   if (P->herr) cudaFreeHost(P->herr);
   if (P->cap) cudaStreamDestroy(P->cap);
+  for (int j = 0; j < kMaxTrials; ++j) {
+    if (P->tst[j]) cudaStreamDestroy(P->tst[j]);
+    if (P->tdone[j]) cudaEventDestroy(P->tdone[j]);
+  }
+  if (P->tfork) cudaEventDestroy(P->tfork);
+  if (P->htrial) cudaFreeHost(P->htrial);
   delete P;
 }
 
@@ -1018,6 +1130,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->nz = 0;
   p->boundary = 0;
   p->scgs_cta_cells = -1;
+  p->ao_trials = 4;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -1119,6 +1232,30 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->mtmp1 = (double*)dalloc(P, 2 * C * sizeof(double));
     P->dscal = (double*)dalloc(P, 16 * sizeof(double));
     P->derr = (int*)dalloc(P, sizeof(int));
+    P->ntrials = ao_trial_count(prm);
+    if (P->ntrials > 1) {
+      P->tv[0] = P->vcand;
+      P->trho[0] = P->rho_c;
+      P->tK[0] = P->K_c;
+      P->ttmp0[0] = P->mtmp0;
+      P->ttmp1[0] = P->mtmp1;
+      for (int j = 0; j < P->ntrials; ++j) {
+        if (j > 0) {
+          P->tv[j] = dalloc(P, N * F * ts);
+          P->trho[j] = dalloc(P, (N + 1) * C * ts);
+          P->tK[j] = (int*)dalloc(P, N * sizeof(int));
+          P->ttmp0[j] = (double*)dalloc(P, C * sizeof(double));
+          P->ttmp1[j] = (double*)dalloc(P, 2 * C * sizeof(double));
+        }
+        P->tmterm[j] = (double*)dalloc(P, (N + 1) * C * sizeof(double));
+        ck(cudaStreamCreateWithFlags(&P->tst[j], cudaStreamNonBlocking), "stream");
+        ck(cudaEventCreateWithFlags(&P->tdone[j], cudaEventDisableTiming), "event");
+      }
+      P->terr = (int*)dalloc(P, kMaxTrials * sizeof(int));
+      P->dtrial = (double*)dalloc(P, kMaxTrials * sizeof(double));
+      ck(cudaEventCreateWithFlags(&P->tfork, cudaEventDisableTiming), "event");
+      ck(cudaMallocHost(&P->htrial, kMaxTrials * (sizeof(double) + sizeof(int))), "pinned");
+    }
     // projections run on at most N + 1 fields at once (stc_project on V or KKT_G)
     if (d3) {
       P->pscratch = dalloc(P, project3_scratch_elems(g0, N + 1) * ts);
@@ -1145,6 +1282,10 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     copy_in(P, r, rho0);
     r.ptr = P->rho_c;
     copy_in(P, r, rho0);
+    for (int j = 1; j < P->ntrials; ++j) {
+      r.ptr = P->trho[j];
+      copy_in(P, r, rho0);
+    }
     if (v0) {
       std::vector<double> vv(v0, v0 + F);
       // wall faces are not unknowns: keep them zero

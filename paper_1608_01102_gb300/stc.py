@@ -34,7 +34,8 @@ class StcParams(ctypes.Structure):
                 ("metric_sigma0", c_double), ("scgs_omega", c_double), ("lm_shift", c_double),
                 ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
                 ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double), ("time_coarsen", c_int),
-                ("nz", c_int), ("boundary", c_int), ("scgs_cta_cells", c_int)]
+                ("nz", c_int), ("boundary", c_int), ("scgs_cta_cells", c_int),
+                ("ao_trials", c_int)]
 
 
 class StcReport(ctypes.Structure):

@@ -32,7 +32,8 @@ def make_pair(nx=16, ny=None, N=6, precision=1, levels=2, r=1e-2, K=1.0, keyfram
         kf = {}
     else:
         kf = keyframes
-    o_over = {k: v for k, v in over.items() if k not in ("poisson_vcycles", "scgs_omega")}
+    gpu_only = ("poisson_vcycles", "scgs_omega", "ao_trials", "scgs_cta_cells")   # kernel / schedule choices
+    o_over = {k: v for k, v in over.items() if k not in gpu_only}
     if "scgs_omega" in over:
         o_over["omega"] = over["scgs_omega"]
     dt = 1.0 / N if dt is None else dt

@@ -366,6 +366,32 @@ def test_ao_blend_halvings(prec):
         assert rel(rho[s], rhos_ref[s]) < TOL[prec]["ao"]
 
 
+@pytest.mark.parametrize("trials", [1, 2, 3, 8])
+def test_ao_blend_trials_at_once_match_one_at_a_time(trials):
+    """The blend factors tried at once (in rounds of `trials`, each on its own
+    stream and buffers) take the same factor as the oracle's one-at-a-time
+    search, and the state is bit-identical to the library's own one-at-a-time
+    search (stc_params.ao_trials = 1), rejected Taylor overflows included."""
+    nx, ny, N = 16, 16, 6
+    v = velocity_trajectory(nx, ny, N, amp=0.4, seed=7)
+    lam = workloads.random_faces(np.random.default_rng(8), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    out = {}
+    for t in (1, trials):
+        P, G = make_pair(nx, ny, N=N, precision=0, levels=2, K=0.2, ao_trials=t)
+        G.set("V", v)
+        G.set("LAMBDA", lam)
+        G.ao(4)
+        out[t] = (G.ao_trace(), G.get("VSTAR"), G.get("RHO"), G.get("MTERM"), list(G.taylor_orders()))
+        G.close()
+    trace_ref = []
+    admm.ao(P, v, lam, iters=4, trace=trace_ref)
+    assert max(trace_ref) >= 2
+    assert out[trials][0] == out[1][0] == trace_ref
+    for a, b in zip(out[trials][1:], out[1][1:]):
+        np.testing.assert_array_equal(a, b)
+
+
 @pytest.mark.parametrize("prec", PREC)
 def test_ao_plain(prec):
     """ao_halvings = -1: the plain Alg. 1 (v* = y every pass)."""
