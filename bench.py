@@ -54,7 +54,7 @@ ORACLE_STEPS = 2  # timesteps of the bounded oracle sample (same grid, same per-
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level SCGS colour launch
 # of this workload (ncu --set full, profiles/scgs_colour_finest_letters_128x40.md);
 # to be re-measured whenever scgs_colour_kernel changes
-SCGS_FINEST_DRAM_BYTES = 23256320 + 768
+SCGS_FINEST_DRAM_BYTES = 23255552 + 512
 
 
 def _peaks():
@@ -341,8 +341,11 @@ def solve_leg(stc, cfg, n, nz, N, levels, max_admm):
             "stopped_by": "kkt" if rep["kkt_rel"] <= 1e-4 else "iteration cap"}
 
 
-def serve_leg(stc, workloads, count, max_admm, budget=64 << 30, workers=8):
-    """Replay the first `count` requests of the seeded stream in real time."""
+def serve_leg(stc, workloads, count, max_admm, budget=64 << 30, workers=8, ao_trials=1):
+    """Replay the first `count` requests of the seeded stream in real time.
+    The requests try AO blend factors one at a time (ao_trials = 1): the
+    concurrent solves already share the GPU, and speculative trials would
+    compete with them."""
     reqs = workloads.config_serving(count)
     with stc.Server(budget, workers=workers) as S:
         t0 = time.perf_counter()
@@ -353,7 +356,7 @@ def serve_leg(stc, workloads, count, max_admm, budget=64 << 30, workers=8):
                 time.sleep(delay)
             n, N = r["nx"], r["N"]
             prm = stc.default_params(n, n, N, precision=0, r=r["r"], K=1.0,
-                                     metric_levels=max(0, int(np.floor(np.log2(n / 2)))))
+                                     metric_levels=max(0, int(np.floor(np.log2(n / 2)))), ao_trials=ao_trials)
             tickets.append(S.submit(prm, r["rho0"], r["keyframes"], tol=1e-4, max_admm=max_admm))
         infos = [S.wait(t) for t in tickets]
         peak = S.stats()["peak_bytes"]

@@ -345,11 +345,13 @@ stc_status stc_admm_update(stc_problem* p, double* drho);
  * graph replay counts each kernel node it runs). */
 stc_status stc_launch_count(const stc_problem* p, long long* launches);
 
-/* enable != 0: the V-cycle graph is rebuilt with a CUDA event pair around every
- * finest-level SCGS colour launch (the dominant kernel), recorded on the
- * stream that runs it; stc_kernel_timing then returns the summed device time
+/* enable != 0: the first V-cycle of every stc_vcycle call runs a second
+ * V-cycle graph with a CUDA event pair around every finest-level SCGS colour
+ * launch (the dominant kernel), recorded on the stream
+ * that runs it (the other cycles run the plain graph, so the events perturb
+ * one cycle per call); stc_kernel_timing then returns the summed device time
  * (ms) and the number of timed launches since the last enable.  enable = 0
- * rebuilds the graph without events. */
+ * drops the timed graph. */
 stc_status stc_set_kernel_timing(stc_problem* p, int enable);
 stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* launches);
 

@@ -99,6 +99,8 @@ struct stc_problem {
   double* dtrial = nullptr;
   void* htrial = nullptr;         // pinned: kMaxTrials doubles, then kMaxTrials ints
   cudaStream_t tst[kMaxTrials] = {};
+  cudaStream_t aux = nullptr;     // second stream of the KKT evaluation (force branch)
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   cudaEvent_t tfork = nullptr;
   cudaEvent_t tdone[kMaxTrials] = {};
   bool rho_at_vstar = false;      // rho / K hold the forward sweep of the current v*
@@ -126,6 +128,8 @@ struct stc_problem {
   double rho_scale = 0.0;
   double fscale = -1.0;
   cudaGraphExec_t vgraph = nullptr;
+  cudaGraphExec_t vgraph_t = nullptr;   // the same V-cycle with events around the finest SCGS launches
+  bool capture_timed = false;           // capturing vgraph_t
   bool broken = false;
   // instrumentation
   long long launches = 0;       // kernels enqueued (graph replays add graph_launches)
@@ -306,7 +310,7 @@ void vcycle_level(stc_problem* P, int l, cudaStream_t st) {
   }
   Level& L = P->lv[l];
   Level& Cc = P->lv[l + 1];
-  const bool timed = P->timing && l == 0 && P->counter == &P->graph_launches;
+  const bool timed = P->capture_timed && l == 0 && P->counter == &P->graph_launches;
   // guard: norms[0] = ||r^h||_2^2 before the correction, norms[1] after it
   double* norms = P->prm.cgc_guard ? P->dguard + 2 * l : nullptr;
   smooth(P, l, P->prm.pre, st, timed);
@@ -395,31 +399,38 @@ double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool non
   return P->hscal[slot];
 }
 
-double run_vcycle(stc_problem* P, bool nonfinite_rejects = false) {
-  if (!P->vgraph) {
+// (timed_cycle: with kernel timing on, this cycle runs the graph with events;
+// the others run the plain one, so the events perturb one cycle per call)
+double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cycle = false) {
+  const bool tg = P->timing && timed_cycle;
+  cudaGraphExec_t& ge = tg ? P->vgraph_t : P->vgraph;
+  if (!ge) {
     cudaGraph_t graph = nullptr;
     P->graph_launches = 0;
-    P->ev_used = 0;
+    if (tg) P->ev_used = 0;
+    P->capture_timed = tg;
     P->counter = &P->graph_launches;
     ck(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed), "begin capture");
     try {
       enqueue_top_vcycle(P, P->cap);
     } catch (...) {
       P->counter = nullptr;
+      P->capture_timed = false;
       cudaStreamEndCapture(P->cap, &graph);
       if (graph) cudaGraphDestroy(graph);
       throw;
     }
     P->counter = nullptr;
+    P->capture_timed = false;
     ck(cudaStreamEndCapture(P->cap, &graph), "end capture");
-    cudaError_t e = cudaGraphInstantiate(&P->vgraph, graph, 0);
+    cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
     cudaGraphDestroy(graph);
     ck(e, "graph instantiate");
   }
-  ck(cudaGraphLaunch(P->vgraph, P->st), "graph launch");
+  ck(cudaGraphLaunch(ge, P->st), "graph launch");
   P->launches += P->graph_launches;
   const double f = read_scalar(P, 0, false, nonfinite_rejects);
-  for (int k = 0; k < P->ev_used; ++k) {
+  for (int k = 0; tg && k < P->ev_used; ++k) {
     float ms = 0.f;
     ck(cudaEventElapsedTime(&ms, P->ev_start[k], P->ev_stop[k]), "event time");
     P->timed_ms += ms;
@@ -709,14 +720,21 @@ void ao(stc_problem* P, int iters, bool warm, cudaStream_t st) {
 void kkt(stc_problem* P, cudaStream_t st) {
   Level& L0 = P->lv[0];
   const Geom& g = L0.g;
+  // the force branch (u(v) = Q[...], its own buffers and the projection's
+  // scratch) runs beside the density branch (forward sweep, metric terms,
+  // adjoint sweep: one cluster each) on a second stream
+  ck(cudaEventRecord(P->aux_fork, st), "event");
+  ck(cudaStreamWaitEvent(P->aux, P->aux_fork, 0), "wait");
+  dispatch(P->dbl, [&](auto tag) {
+    using T = decltype(tag);
+    launch_kkt_force_rhs<T>(g, (const T*)L0.x.v, (T*)P->uk, P->aux);
+  });
+  project(P, P->uk, g.N, P->aux);
+  ck(cudaEventRecord(P->aux_join, P->aux), "event");
   forward(P, L0.x.v, P->rho_k, P->Kk, st);
   metric_terms(P, P->rho_k, st);
   adjoint(P, L0.x.v, P->rho_k, P->Kk, nullptr, 0.0, -1.0, P->dens, st);
-  dispatch(P->dbl, [&](auto tag) {
-    using T = decltype(tag);
-    launch_kkt_force_rhs<T>(g, (const T*)L0.x.v, (T*)P->uk, st);
-  });
-  project(P, P->uk, g.N, st);
+  ck(cudaStreamWaitEvent(st, P->aux_join, 0), "wait");
   // objective of Eq. opt at v: misfit of rho(v) (dscal[5]) and ||u(v)||^2 (dscal[6])
   ck(cudaMemsetAsync(P->dscal + 5, 0, 2 * sizeof(double), st), "memset");
   dispatch(P->dbl, [&](auto tag) {
@@ -1073,6 +1091,7 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
 void free_problem(stc_problem* P) {
   if (!P) return;
   if (P->vgraph) cudaGraphExecDestroy(P->vgraph);
+  if (P->vgraph_t) cudaGraphExecDestroy(P->vgraph_t);
   for (cudaEvent_t e : P->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : P->ev_stop) cudaEventDestroy(e);
   for (void* p : P->allocs) cudaFree(p);
@@ -1084,6 +1103,9 @@ void free_problem(stc_problem* P) {
     if (P->tdone[j]) cudaEventDestroy(P->tdone[j]);
   }
   if (P->tfork) cudaEventDestroy(P->tfork);
+  if (P->aux) cudaStreamDestroy(P->aux);
+  if (P->aux_fork) cudaEventDestroy(P->aux_fork);
+  if (P->aux_join) cudaEventDestroy(P->aux_join);
   if (P->htrial) cudaFreeHost(P->htrial);
   delete P;
 }
@@ -1188,6 +1210,9 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
                 (!project_needs_scratch(g0, P->ts) && (int)project_smem(g0, P->ts) > smem_optin)))
       fail(STC_ERR_UNSUPPORTED, "shared memory of this device too small for the grid");
     ck(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking), "stream");
+    ck(cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking), "stream");
+    ck(cudaEventCreateWithFlags(&P->aux_fork, cudaEventDisableTiming), "event");
+    ck(cudaEventCreateWithFlags(&P->aux_join, cudaEventDisableTiming), "event");
     const int N = prm.num_steps;
     for (size_t l = 0; l < geoms.size(); ++l) {
       Level L;
@@ -1390,7 +1415,7 @@ stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf) {
   }
   return guarded(p, [&]() {
     double f = 0.0;
-    for (int c = 0; c < ncycles; ++c) f = run_vcycle(p);
+    for (int c = 0; c < ncycles; ++c) f = run_vcycle(p, false, c == 0);
     if (ncycles == 0) {
       residual_norm(p, 0, 0, p->st);
       f = read_scalar(p, 0);
@@ -1852,10 +1877,11 @@ stc_status stc_set_kernel_timing(stc_problem* p, int enable) {
     return STC_ERR_INVALID_ARG;
   }
   return guarded(p, [&]() {
-    if (p->vgraph) {
-      ck(cudaGraphExecDestroy(p->vgraph), "graph destroy");
-      p->vgraph = nullptr;
-    }
+    for (cudaGraphExec_t* ge : {&p->vgraph, &p->vgraph_t})
+      if (*ge) {
+        ck(cudaGraphExecDestroy(*ge), "graph destroy");
+        *ge = nullptr;
+      }
     p->timing = enable != 0;
     p->timed_ms = 0.0;
     p->timed_launches = 0;
