@@ -77,7 +77,10 @@ typedef struct {
   double metric_sigma0; /* std-dev of the first filter in cells (1)                */
   double scgs_omega;    /* SCGS under-relaxation (0.8)                             */
   double lm_shift;      /* Levenberg-Marquardt shift of the smoother's v blocks; <0: 1/dt^2 */
-  int poisson_vcycles;  /* multigrid cycles per projection Q (8)                   */
+  int poisson_vcycles;  /* multigrid cycles per projection Q (8) where Q runs as a
+                           multigrid: 3D, and 2D fields too large for one CTA's
+                           shared memory.  Other 2D fields are projected exactly
+                           (DCT-II diagonalisation of the Neumann Laplacian). */
   int self_advection;   /* 1 (default); 0 drops Adv (linear saddle problem, tests only) */
   int ao_halvings;      /* Sec. 5 safeguard of Alg. 1: v* moves to v* + a (y - v*) with
                            a = 1, 1/2, ... (at most this many halvings) until the AO
@@ -287,7 +290,9 @@ stc_status stc_metric_terms(stc_problem* p);
 stc_status stc_adjoint(stc_problem* p, int source_field, double alpha, double beta);
 
 /* Solenoidal projection Q (Eq. KKTPO) in place on slabs [first, first+count)
- * of a face field of the finest level (V, U, VSTAR, Y, W, KKT_U, KKT_G, Z). */
+ * of a face field of the finest level (V, U, VSTAR, Y, W, KKT_U, KKT_G, Z):
+ * Q v = v - G phi, (D G) phi = D v.  Exact (DCT) for 2D fields that fit on
+ * chip, else poisson_vcycles multigrid cycles (Sec. 4.1's solver). */
 stc_status stc_project(stc_problem* p, int field, int first, int count);
 
 /* One AO solve (Alg. 1): w = v + lambda/K; v* = w (warm_start = 0) or the

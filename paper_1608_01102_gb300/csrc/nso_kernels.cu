@@ -826,7 +826,9 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
 // reads its old coupling while writing the new one.
 constexpr int kCrStride2 = 93;
 enum : int { CR_C2 = 77 };
-constexpr int kCellCtaThreads = 128;
+// threads of the CTA-per-cell kernel: 256 on colours of at most 256 cells
+// (shorter rounds of the split block steps), 128 on larger ones (occupancy)
+constexpr int kCellCtaThreadsSmall = 256, kCellCtaThreadsLarge = 128, kCellCtaSmallCells = 256;
 
 __host__ __device__ inline size_t scgs_cell_floats2(int N) { return (size_t)(16 + 5 + kCrStride2) * N; }
 
@@ -983,8 +985,8 @@ __device__ __forceinline__ void cr_split(S* V, int N, const CellG<S>& cg_, int l
   }
 }
 
-template <class T, class S>
-__global__ void __launch_bounds__(kCellCtaThreads)
+template <class T, class S, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
                         const double* __restrict__ lm_dev) {
   pdl_wait();
@@ -1290,25 +1292,34 @@ int scgs_cells_per_cta(int N) {
   return c < 1 ? 1 : c;
 }
 
+// the CTA-per-cell kernel with THREADS threads (false: the records do not fit)
+template <class T, class S, int THREADS>
+static bool launch_scgs_cell_tts(const Geom& g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
+                                 const double* lm_dev, cudaStream_t st) {
+  static std::once_flag attr_once;
+  static int max_smem = 0;
+  std::call_once(attr_once, [] {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, (const void*)scgs_colour_cell_kernel<T, S, THREADS>);
+    max_smem = 227 * 1024 - (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute((const void*)scgs_colour_cell_kernel<T, S, THREADS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  });
+  const size_t sm = scgs_cell_floats2(g.N) * sizeof(S);
+  if (sm > (size_t)max_smem) return false;
+  launch_pdl(scgs_colour_cell_kernel<T, S, THREADS>, dim3(ncx * ncy), dim3(THREADS), sm, st, g, x, r, colour, ncx,
+             ncy, lm_dev);
+  return true;
+}
+
 // the CTA-per-cell kernel; false (nothing launched) when one cell's records
 // do not fit in shared memory
 template <class T, class S>
 static bool launch_scgs_cell_ts(const Geom& g, State<T> x, CState<T> r, int colour, int ncx, int ncy,
                                 const double* lm_dev, cudaStream_t st) {
-  static std::once_flag attr_once;
-  static int max_smem = 0;
-  std::call_once(attr_once, [] {
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, (const void*)scgs_colour_cell_kernel<T, S>);
-    max_smem = 227 * 1024 - (int)fa.sharedSizeBytes;
-    cudaFuncSetAttribute((const void*)scgs_colour_cell_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         max_smem);
-  });
-  const size_t sm = scgs_cell_floats2(g.N) * sizeof(S);
-  if (sm > (size_t)max_smem) return false;
-  launch_pdl(scgs_colour_cell_kernel<T, S>, dim3(ncx * ncy), dim3(kCellCtaThreads), sm, st, g, x, r, colour, ncx,
-             ncy, lm_dev);
-  return true;
+  if (ncx * ncy <= kCellCtaSmallCells)
+    return launch_scgs_cell_tts<T, S, kCellCtaThreadsSmall>(g, x, r, colour, ncx, ncy, lm_dev, st);
+  return launch_scgs_cell_tts<T, S, kCellCtaThreadsLarge>(g, x, r, colour, ncx, ncy, lm_dev, st);
 }
 
 template <class T, class S>

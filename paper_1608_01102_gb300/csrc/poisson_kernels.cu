@@ -9,6 +9,7 @@
 // average restriction and bilinear prolongation, the coarsest level (<= 64
 // cells) by 30 parallel red-black Gauss-Seidel sweeps in fp64, then v - G phi
 // written back.
+#include <cmath>
 #include <mutex>
 #include "stc_internal.cuh"
 #include "stc_kernels.h"
@@ -263,10 +264,174 @@ bool project_supported(const Geom& g, size_t) {
 
 bool project_needs_scratch(const Geom& g, size_t tsize) { return project_smem(g, tsize) > kProjectSmemLimit; }
 
+// ---------------------------------------------------------------------------
+// Exact Q on the closed 2D box.  The cell-centred Neumann Laplacian D G of the
+// uniform grid is diagonalised by the orthonormal DCT-II in each axis:
+// D G = (C_y (x) C_x)^T diag(lam) (C_y (x) C_x), C[k][i] = s_k cos(pi k (2i+1) / 2n),
+// lam = -(4/h^2) (sin^2(pi kx / 2nx) + sin^2(pi ky / 2ny)).  So
+// phi = C_y^T [(C_y b C_x^T) / lam] C_x, with 1/lam_00 = 0 dropping the
+// constant (the null space, which G removes anyway): four dense products per
+// field.  One CTA per field, b and the intermediates in shared memory, 4x4
+// outputs per thread.  This is Q itself to rounding, where the multigrid gives
+// Q to its truncation after `vcycles` cycles.
+// ---------------------------------------------------------------------------
+size_t project_dct_elems(const Geom& g) {
+  return 2 * (size_t)g.nx * g.nx + 2 * (size_t)g.ny * g.ny + (size_t)g.nx * g.ny;
+}
+
+bool project_dct_fits(const Geom& g, size_t tsize) {
+  return g.dim == 2 && 2 * (size_t)g.nx * g.ny * tsize <= kProjectSmemLimit;
+}
+
+// C_x, C_x^T, C_y, C_y^T, 1/lam (row ky, column kx), in fp64
+void project_dct_tables(const Geom& g, double* out) {
+  const double pi = 3.14159265358979323846;
+  auto basis = [&](int n, double* C, double* CT) {
+    for (int k = 0; k < n; ++k) {
+      const double sk = std::sqrt((k == 0 ? 1.0 : 2.0) / n);
+      for (int i = 0; i < n; ++i) {
+        const double c = sk * std::cos(pi * k * (2.0 * i + 1.0) / (2.0 * n));
+        C[(size_t)k * n + i] = c;
+        CT[(size_t)i * n + k] = c;
+      }
+    }
+  };
+  double* Cx = out;
+  double* CxT = Cx + (size_t)g.nx * g.nx;
+  double* Cy = CxT + (size_t)g.nx * g.nx;
+  double* CyT = Cy + (size_t)g.ny * g.ny;
+  double* il = CyT + (size_t)g.ny * g.ny;
+  basis(g.nx, Cx, CxT);
+  basis(g.ny, Cy, CyT);
+  const double ih2 = 1.0 / (g.h * g.h);
+  for (int ky = 0; ky < g.ny; ++ky)
+    for (int kx = 0; kx < g.nx; ++kx) {
+      const double sx = std::sin(pi * kx / (2.0 * g.nx)), sy = std::sin(pi * ky / (2.0 * g.ny));
+      const double lam = -4.0 * ih2 * (sx * sx + sy * sy);
+      il[(size_t)ky * g.nx + kx] = (kx == 0 && ky == 0) ? 0.0 : 1.0 / lam;
+    }
+}
+
+// out[r][c] = (sum_k A[r][k] B[k][c]) * (scale ? scale[r][c] : 1), all row-major
+// (leading dimensions lda, ldb, Cc); k in order, so the result is deterministic
 template <class T>
-cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch) {
+__device__ __forceinline__ void dct_gemm(T* out, const T* A, int lda, const T* B, int ldb, int R, int Cc, int K,
+                                         const T* __restrict__ scale) {
+  const int ntr = (R + 3) >> 2, ntc = (Cc + 3) >> 2;
+  const bool vec = (Cc & 3) == 0 && (ldb & 3) == 0;
+  for (int t = threadIdx.x; t < ntr * ntc; t += blockDim.x) {
+    const int r0 = (t / ntc) * 4, c0 = (t - (t / ntc) * ntc) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int k = 0; k < K; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = r0 + i < R ? A[(size_t)(r0 + i) * lda + k] : T(0);
+      const T* bk = B + (size_t)k * ldb + c0;
+      if (vec) {
+        if constexpr (sizeof(T) == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(bk);
+          b[0] = q.x;
+          b[1] = q.y;
+          b[2] = q.z;
+          b[3] = q.w;
+        } else {
+          const double2 q0 = reinterpret_cast<const double2*>(bk)[0], q1 = reinterpret_cast<const double2*>(bk)[1];
+          b[0] = q0.x;
+          b[1] = q0.y;
+          b[2] = q1.x;
+          b[3] = q1.y;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = c0 + j < Cc ? bk[j] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (r0 + i < R && c0 + j < Cc) {
+          const size_t e = (size_t)(r0 + i) * Cc + c0 + j;
+          out[e] = scale ? acc[i][j] * scale[e] : acc[i][j];
+        }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPoissonThreads, 1)
+project_dct_kernel(Geom g, T* fields, const T* __restrict__ tab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = g.nx, ny = g.ny;
+  T* S1 = reinterpret_cast<T*>(smem_raw);             // [ny][nx]
+  T* S2 = S1 + (size_t)nx * ny;                       // [ny][nx]
+  const T* Cx = tab;
+  const T* CxT = Cx + (size_t)nx * nx;
+  const T* Cy = CxT + (size_t)nx * nx;
+  const T* CyT = Cy + (size_t)ny * ny;
+  const T* il = CyT + (size_t)ny * ny;
+  T* v = fields + (size_t)blockIdx.x * g.F;
+  {
+    RowWalk w(nx);
+    for (int e = threadIdx.x; e < nx * ny; e += blockDim.x, w.next()) S1[e] = divergence(g, v, w.q, w.r);
+  }
+  __syncthreads();
+  dct_gemm(S2, Cy, ny, S1, nx, ny, nx, ny, (const T*)nullptr);   // C_y b
+  __syncthreads();
+  dct_gemm(S1, S2, nx, CxT, nx, ny, nx, nx, il);                 // (C_y b C_x^T) / lam
+  __syncthreads();
+  dct_gemm(S2, CyT, ny, S1, nx, ny, nx, ny, (const T*)nullptr);  // C_y^T (.)
+  __syncthreads();
+  dct_gemm(S1, S2, nx, Cx, nx, ny, nx, nx, (const T*)nullptr);   // (.) C_x = phi
+  __syncthreads();
+  const T ih = pick<T>(g.ih, g.ihf);
+  for (int e = threadIdx.x; e < g.F; e += blockDim.x) {
+    if (e < g.Fx) {
+      const int j = e / (nx + 1), i = e - j * (nx + 1);
+      if (i >= 1 && i <= nx - 1) v[e] -= (S1[j * nx + i] - S1[j * nx + i - 1]) * ih;
+      else v[e] = T(0);
+    } else {
+      const int q = e - g.Fx;
+      const int j = q / nx, i = q - j * nx;
+      if (j >= 1 && j <= ny - 1) v[e] -= (S1[j * nx + i] - S1[(j - 1) * nx + i]) * ih;
+      else v[e] = T(0);
+    }
+  }
+}
+
+template <class T>
+static cudaError_t launch_project_dct(const Geom& g, T* fields, int count, cudaStream_t st, const T* tab) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    attr_err = cudaGetDevice(&dev);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (attr_err == cudaSuccess) attr_err = cudaFuncGetAttributes(&fa, (const void*)project_dct_kernel<T>);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute((const void*)project_dct_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin - (int)fa.sharedSizeBytes);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  project_dct_kernel<T><<<count, kPoissonThreads, 2 * (size_t)g.nx * g.ny * sizeof(T), st>>>(g, fields, tab);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st, T* scratch,
+                           const T* dct) {
   if (g.dim == 3) return launch_project3<T>(g, fields, count, vcycles, st, scratch);
   if (count <= 0) return cudaSuccess;
+  if (dct && project_dct_fits(g, sizeof(T))) return launch_project_dct<T>(g, fields, count, st, dct);
   const size_t layout = project_smem(g, sizeof(T));
   if (project_needs_scratch(g, sizeof(T)) && !scratch) return cudaErrorInvalidValue;
   const size_t sm = scratch ? 0 : layout;
@@ -473,7 +638,7 @@ void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* o
 }
 
 #define STC_POI_INST(T)                                                                                        \
-  template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t, T*);                        \
+  template cudaError_t launch_project<T>(const Geom&, T*, int, int, cudaStream_t, T*, const T*);              \
   template void launch_ao_init<T>(const Geom&, const T*, const T*, double, T*, T*, int, cudaStream_t);             \
   template void launch_axpby_faces<T>(const Geom&, int, const T*, double, const T*, double, T*, cudaStream_t); \
   template void launch_kkt_force_rhs<T>(const Geom&, const T*, T*, cudaStream_t);                             \

@@ -113,6 +113,7 @@ struct stc_problem {
   double *mterm = nullptr, *mtmp0 = nullptr, *mtmp1 = nullptr, *star = nullptr;
   size_t star_bytes = 0;
   void* pscratch = nullptr;       // projection level arrays when they do not fit on chip
+  void* dct = nullptr;            // 2D: DCT tables of the exact projection (project_dct_tables, state type)
   void* adv3 = nullptr;           // 3D sweeps: term buffers and grid-barrier words
   void* sc3 = nullptr;            // 3D SCGS: per-cell block Thomas records (finest level's size)
   // forward simulation and its adjoint (allocated at their first use)
@@ -536,7 +537,8 @@ void project(stc_problem* P, void* fields, int count, cudaStream_t st) {
   const Geom& g = P->lv[0].g;
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st, (T*)P->pscratch), "project");
+    ck(launch_project<T>(g, (T*)fields, count, P->prm.poisson_vcycles, st, (T*)P->pscratch, (const T*)P->dct),
+       "project");
   });
   if (count > 0) ::count(P, g.dim == 3 ? project3_launches(g, P->prm.poisson_vcycles) : 1);
 }
@@ -1079,6 +1081,7 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
     total += (size_t)(nt - 1) * (b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) + b(C * 8) + b(2 * C * 8)) +
              (size_t)nt * b((N + 1) * C * 8) + b(kMaxTrials * 4) + b(kMaxTrials * 8);
   Geom g0 = make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt);
+  if (project_dct_fits(g0, ts)) total += b(project_dct_elems(g0) * ts);
   if (g0.dim == 3) {
     total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts) +
              b(scgs3_thomas_scratch_bytes(g0, ts));
@@ -1288,6 +1291,18 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       P->sc3 = dalloc(P, scgs3_thomas_scratch_bytes(g0, P->dbl ? 8 : 4));
     } else if (project_needs_scratch(g0, ts)) {
       P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
+    }
+    if (project_dct_fits(g0, ts)) {
+      const size_t ne = project_dct_elems(g0);
+      std::vector<double> tab(ne);
+      project_dct_tables(g0, tab.data());
+      P->dct = dalloc(P, ne * ts);
+      if (P->dbl) {
+        ck(cudaMemcpy(P->dct, tab.data(), ne * ts, cudaMemcpyHostToDevice), "h2d");
+      } else {
+        std::vector<float> tf(tab.begin(), tab.end());
+        ck(cudaMemcpy(P->dct, tf.data(), ne * ts, cudaMemcpyHostToDevice), "h2d");
+      }
     }
     ck(cudaMallocHost(&P->hscal, 16 * sizeof(double)), "pinned");
     ck(cudaMallocHost(&P->herr, sizeof(int)), "pinned");

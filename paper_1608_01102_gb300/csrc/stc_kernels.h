@@ -78,12 +78,17 @@ bool advect_supported(const Geom& g);
 
 // --- projection and elementwise helpers (poisson_kernels.cu) ---------------
 // In-place solenoidal projection of `count` face fields (stride F): Q v = v - G phi
-// with (D G) phi = D v solved by an on-chip multigrid V(2,2) cycle.
-// scratch: (count x project_smem / tsize) elements of global memory, required
+// with (D G) phi = D v.  dct (2D, project_dct_fits): the tables of
+// project_dct_tables in T, and phi exactly by the DCT diagonalisation; else an
+// on-chip multigrid V(2,2) cycle (vcycles of them).  scratch: (count x
+// project_smem / tsize) elements of global memory, required for the multigrid
 // when project_needs_scratch (the level arrays then live there, not on chip)
 template <class T>
 cudaError_t launch_project(const Geom& g, T* fields, int count, int vcycles, cudaStream_t st,
-                           T* scratch = nullptr);
+                           T* scratch = nullptr, const T* dct = nullptr);
+size_t project_dct_elems(const Geom& g);
+bool project_dct_fits(const Geom& g, size_t tsize);
+void project_dct_tables(const Geom& g, double* out);
 size_t project_smem(const Geom& g, size_t tsize);
 bool project_supported(const Geom& g, size_t tsize);
 constexpr size_t kProjectSmemLimit = 200 * 1024;   // on-chip layout limit (opt-in 227 KB less static use)

@@ -39,6 +39,34 @@ def test_projection(prec, shape):
         assert np.max(np.abs(d)) < TOL[prec]["project"] * np.max(np.abs(mac.div(P.grid, w[i]))) * 10
 
 
+@pytest.mark.parametrize("prec", PREC)
+@pytest.mark.parametrize("shape", [(16, 16), (24, 12), (10, 6), (48, 48), (128, 96)])
+def test_projection_is_exact_where_the_dct_applies(prec, shape):
+    """2D fields that fit on chip are projected through the DCT-II
+    diagonalisation of the Neumann Laplacian: Q itself to rounding, against the
+    oracle's sparse direct solve (10 x 6: the scalar path of the products;
+    128 x 96: a non-square bench-sized grid).  Q is idempotent and leaves
+    divergence at the rounding level."""
+    nx, ny = shape
+    P, G = make_pair(nx, ny, N=3, precision=prec, levels=0)
+    rng = np.random.default_rng(3)
+    w = workloads.random_faces(rng, nx, ny, 3)
+    w[1] += workloads.swirl_velocity(nx, ny, 3.0)
+    G.set("W", w)
+    G.project("W", 0, 3)
+    out = G.get("W")
+    tol = 1e-12 if prec == 1 else 5e-6
+    for i in range(3):
+        ref = projection.project(P.grid, w[i])
+        assert rel(out[i], ref) < tol, (i, rel(out[i], ref))
+        assert np.max(np.abs(mac.div(P.grid, out[i]))) < tol * np.max(np.abs(mac.div(P.grid, w[i]))) * 100
+    G.set("W", out)
+    G.project("W", 0, 3)
+    again = G.get("W")
+    for i in range(3):
+        assert rel(again[i], out[i]) < tol, i
+
+
 def test_projection_with_global_scratch_fp64_128():
     """128^2 in fp64 does not fit the on-chip multigrid layout: the level
     arrays move to a per-field global scratch (same arithmetic)."""
