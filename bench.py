@@ -54,7 +54,7 @@ ORACLE_STEPS = 2  # timesteps of the bounded oracle sample (same grid, same per-
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level SCGS colour launch
 # of this workload (ncu --set full, profiles/scgs_colour_finest_letters_128x40.md);
 # to be re-measured whenever scgs_colour_kernel changes
-SCGS_FINEST_DRAM_BYTES = 23255552 + 512
+SCGS_FINEST_DRAM_BYTES = 23257856 + 768
 
 
 def _peaks():

@@ -1,6 +1,7 @@
 // NSO subproblem kernels: residual f of Eq. KKTAO, the temporally augmented
 // SCGS smoother of Sec. 4.3 / Eq. HESS, the STFAS transfer operators R and P
 // (Sec. 4.3, Alg. 2) and reductions.
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include "stc_internal.cuh"
@@ -355,7 +356,6 @@ __device__ __forceinline__ void saddle_solve(T A[4][4], const T gv[4], T B[4][NC
 constexpr int kCrStride = 77;   // per-block record, odd so a warp's lanes hit distinct banks
 enum : int { CR_A = 0, CR_R = 10, CR_C = 15, CR_ZL = 31, CR_ZR = 51, CR_Z = 71 };
 
-__host__ __device__ inline size_t scgs_cell_floats(int N) { return (size_t)(16 + 5 + kCrStride) * N; }
 
 // per-cell constants: active-face flags, g = d(grad p)/dp_c, P = I - g g^T/|g|^2
 template <class S>
@@ -424,12 +424,28 @@ __device__ __forceinline__ S shift_sym(S A[4][4], const CellG<S>& cg) {
   return gam;
 }
 
+// Shared-memory layout of the smoother: the U_t row of time t starts at t us,
+// the b_u row at t bs (the entries of a row cpb apart, cells fastest), cell c's
+// block records at c cs, block k of a cell at k STRIDE (+ k / 32 with shift).
+// The warp kernel skews them so that a warp's lanes hit distinct banks: us and
+// bs are = cpb (mod 32), so the lanes of a (cell, time) sweep read consecutive
+// banks; cs is searched on the host; the one-word shift per 32 blocks parts the
+// blocks 32 apart that lanes m and m + 16 of the reduction touch.
+struct ScgsLay {
+  int us, bs, cs, shift;
+};
+
+__host__ __device__ inline int blk_off(const ScgsLay& L, int k, int stride) {
+  return k * stride + (L.shift ? k >> 5 : 0);
+}
+
 // Phases A and A2 of one colour's SCGS for the cells q0 .. q0 + cpb - 1 (see
 // above): U_t, y_t and the v-block records (STRIDE values per block) in
 // shared memory; ends with a CTA barrier.
 template <class T, class S, int STRIDE>
 __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, const CState<T>& r, int colour,
-                                              int ncx, int ncell, int cpb, int q0, S lm, S* Us, S* Bu, S* Vb) {
+                                              int ncx, int ncell, int cpb, int q0, S lm, S* Us, S* Bu, S* Vb,
+                                              const ScgsLay& L) {
   const int N = g.N;
   const S idt = pick<S>(g.idt, g.idtf);
   // ---- phase A: couplings and right-hand sides ----------------------------
@@ -444,15 +460,15 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
     const int cc = cidx(g, j, i);
     S Jl[4][4];   // in the solve type: the blocks are stored as S
     local_adv_jac<T, S>(g, x.v + (size_t)(t + 1) * g.F, j, i, Jl);
-    S* U = Us + (size_t)t * 16 * cpb + c;
+    S* U = Us + (size_t)t * L.us + c;
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
 #pragma unroll
       for (int b2 = 0; b2 < 4; ++b2)
         U[(a2 * 4 + b2) * cpb] =
             ((a2 == b2 ? pick<S>(g.idt, g.idtf) : S(0)) + S(g.self_adv) * Jl[a2][b2]) * S(act[a2] * act[b2]);
-    S* Ru = Bu + (size_t)t * 5 * cpb + c;
-    S* Rv = Vb + ((size_t)c * N + t) * STRIDE + CR_R;
+    S* Ru = Bu + (size_t)t * L.bs + c;
+    S* Rv = Vb + (size_t)c * L.cs + blk_off(L, t, STRIDE) + CR_R;
     const T* ru = r.u + (size_t)t * g.F;
     const T* rv = r.v + (size_t)(t + 1) * g.F;
 #pragma unroll
@@ -473,7 +489,7 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
     if (q >= ncell) continue;
     CellG<S> cg_;
     cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
-    S* Ru = Bu + (size_t)t * 5 * cpb + c;
+    S* Ru = Bu + (size_t)t * L.bs + c;
     S bf[4], pb[4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) bf[a2] = Ru[a2 * cpb];
@@ -495,8 +511,8 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
     CellG<S> cg_;
     cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
     const int tv = t + 1;
-    S* V = Vb + ((size_t)c * N + t) * STRIDE;
-    const S* U = Us + (size_t)t * 16 * cpb + c;     // U_{tv-1}
+    S* V = Vb + (size_t)c * L.cs + blk_off(L, t, STRIDE);
+    const S* U = Us + (size_t)t * L.us + c;     // U_{tv-1}
     S Um[4][4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2)
@@ -527,7 +543,7 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
         ++e;
       }
     // R = b_v + [tv<N] y_tv / dt - U_{tv-1}^T y_{tv-1}
-    const S* y0 = Bu + (size_t)t * 5 * cpb + c;
+    const S* y0 = Bu + (size_t)t * L.bs + c;
     S yv[4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) yv[a2] = y0[a2 * cpb];
@@ -536,12 +552,12 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
       S v = V[CR_R + a2];
 #pragma unroll
       for (int c2 = 0; c2 < 4; ++c2) v -= Um[c2][a2] * yv[c2];
-      if (tv < N) v += idt * cg_.act[a2] * Bu[((size_t)tv * 5 + a2) * cpb + c];
+      if (tv < N) v += idt * cg_.act[a2] * Bu[(size_t)tv * L.bs + a2 * cpb + c];
       V[CR_R + a2] = v;
     }
     // coupling to v_{tv+1}: O_tv = -P U_tv / dt
     if (tv < N) {
-      const S* U1 = Us + (size_t)tv * 16 * cpb + c;
+      const S* U1 = Us + (size_t)tv * L.us + c;
 #pragma unroll
       for (int b2 = 0; b2 < 4; ++b2) {
         S w[4], pw[4];
@@ -563,7 +579,8 @@ __device__ __forceinline__ void scgs_assemble(const Geom& g, const State<T>& x, 
 // Phase C: the u blocks from the solved v blocks, x += omega delta.
 template <class T, class S, int STRIDE>
 __device__ __forceinline__ void scgs_update(const Geom& g, const State<T>& x, int colour, int ncx, int ncell,
-                                            int cpb, int q0, const S* Us, const S* Bu, const S* Vb) {
+                                            int cpb, int q0, const S* Us, const S* Bu, const S* Vb,
+                                            const ScgsLay& L) {
   const int N = g.N;
   const S idt = pick<S>(g.idt, g.idtf);
   // ---- phase C: u blocks from the v solution, x += omega * delta -----------
@@ -594,9 +611,9 @@ __device__ __forceinline__ void scgs_update(const Geom& g, const State<T>& x, in
     CellG<S> cg_;
     cg_.init(g, i, j);
     // w = [t>=1] x_v(t)/dt - U_t x_v(t+1);  x_u = y_t + [-P w; gh^T w]
-    const S* U = Us + (size_t)t * 16 * cpb + c;
-    const S* xv1 = Vb + ((size_t)c * N + t) * STRIDE + CR_Z;          // v_{t+1}
-    const S* xv0 = Vb + ((size_t)c * N + (t > 0 ? t - 1 : 0)) * STRIDE + CR_Z;   // v_t
+    const S* U = Us + (size_t)t * L.us + c;
+    const S* xv1 = Vb + (size_t)c * L.cs + blk_off(L, t, STRIDE) + CR_Z;          // v_{t+1}
+    const S* xv0 = Vb + (size_t)c * L.cs + blk_off(L, t > 0 ? t - 1 : 0, STRIDE) + CR_Z;   // v_t
     S w[4];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) {
@@ -611,7 +628,7 @@ __device__ __forceinline__ void scgs_update(const Geom& g, const State<T>& x, in
     S gw = S(0);
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) gw += cg_.gh[a2] * w[a2];
-    const S* y = Bu + (size_t)t * 5 * cpb + c;
+    const S* y = Bu + (size_t)t * L.bs + c;
     S du[5];
 #pragma unroll
     for (int a2 = 0; a2 < 4; ++a2) du[a2] = y[a2 * cpb] - pw[a2];
@@ -630,7 +647,7 @@ __device__ __forceinline__ void scgs_update(const Geom& g, const State<T>& x, in
 template <class T, class S>
 __global__ void __launch_bounds__(256)
 scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy, int cpb,
-                   const double* __restrict__ lm_dev) {
+                   const double* __restrict__ lm_dev, ScgsLay L) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
@@ -639,11 +656,11 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   const S lm = S(lm_dev ? *lm_dev : g.lm);
   const int ncell = ncx * ncy;
   const int q0 = blockIdx.x * cpb;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb]
-  S* Bu = Us + (size_t)N * 16 * cpb;                  // b_u -> y_t [N][5][cpb]
-  S* Vb = Bu + (size_t)N * 5 * cpb;                   // v blocks   [cpb][N][kCrStride]
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16][cpb], rows L.us apart
+  S* Bu = Us + (size_t)N * L.us;                      // b_u -> y_t [N][5][cpb], rows L.bs apart
+  S* Vb = Bu + (size_t)N * L.bs;                      // v blocks   [cpb][N][kCrStride], cells L.cs apart
 
-  scgs_assemble<T, S, kCrStride>(g, x, r, colour, ncx, ncell, cpb, q0, lm, Us, Bu, Vb);
+  scgs_assemble<T, S, kCrStride>(g, x, r, colour, ncx, ncell, cpb, q0, lm, Us, Bu, Vb, L);
 
   // ---- phase B: cyclic reduction over the v blocks, one warp per cell -------
   {
@@ -652,7 +669,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
     if (warp < cpb && q < ncell) {
       CellG<S> cg_;
       cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
-      S* V = Vb + (size_t)warp * N * kCrStride;
+      S* V = Vb + (size_t)warp * L.cs;
       int top = 0;
       for (int s2 = 1; s2 < N; s2 <<= 1) {
         top = s2;
@@ -661,8 +678,8 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
           const int o = s2 * (2 * m + 1);
           if (o >= N) break;
           const bool hasb = o + s2 < N;
-          S* Vo = V + (size_t)o * kCrStride;
-          const S* Va = V + (size_t)(o - s2) * kCrStride;
+          S* Vo = V + blk_off(L, o, kCrStride);
+          const S* Va = V + blk_off(L, o - s2, kCrStride);
           S A[4][4];
           load_sym(Vo + CR_A, A);
           S B[4][9];
@@ -702,7 +719,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
         for (int m = lane;; m += 32) {
           const int e = 2 * s2 * m;
           if (e >= N) break;
-          S* Ve = V + (size_t)e * kCrStride;
+          S* Ve = V + blk_off(L, e, kCrStride);
           S A[4][4];
           load_sym(Ve + CR_A, A);
           S rf[4], Ce[4][4], Cn[4][4];
@@ -717,7 +734,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
           }
           const int o2 = e + s2;
           if (o2 < N) {
-            const S* V2 = V + (size_t)o2 * kCrStride;
+            const S* V2 = V + blk_off(L, o2, kCrStride);
             const bool hasb2 = o2 + s2 < N;
 #pragma unroll
             for (int r2 = 0; r2 < 4; ++r2) {
@@ -740,7 +757,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
           }
           const int o1 = e - s2;
           if (o1 >= 0) {
-            const S* V1 = V + (size_t)o1 * kCrStride;
+            const S* V1 = V + blk_off(L, o1, kCrStride);
 #pragma unroll
             for (int r2 = 0; r2 < 4; ++r2) {
 #pragma unroll
@@ -787,14 +804,14 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
         for (int m = lane;; m += 32) {
           const int o = s2 * (2 * m + 1);
           if (o >= N) break;
-          S* Vo = V + (size_t)o * kCrStride;
-          const S* Va = V + (size_t)(o - s2) * kCrStride;
+          S* Vo = V + blk_off(L, o, kCrStride);
+          const S* Va = V + blk_off(L, o - s2, kCrStride);
           const bool hasb = o + s2 < N;
           S xa[4], xb[4];
 #pragma unroll
           for (int k2 = 0; k2 < 4; ++k2) {
             xa[k2] = Va[CR_Z + k2];
-            xb[k2] = hasb ? V[(size_t)(o + s2) * kCrStride + CR_Z + k2] : S(0);
+            xb[k2] = hasb ? V[blk_off(L, o + s2, kCrStride) + CR_Z + k2] : S(0);
           }
 #pragma unroll
           for (int r2 = 0; r2 < 5; ++r2) {
@@ -810,7 +827,7 @@ scgs_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, int ncy
   }
   __syncthreads();
 
-  scgs_update<T, S, kCrStride>(g, x, colour, ncx, ncell, cpb, q0, Us, Bu, Vb);
+  scgs_update<T, S, kCrStride>(g, x, colour, ncx, ncell, cpb, q0, Us, Bu, Vb, L);
 }
 
 // The same colour step with one CTA per cell, for colours of few cells (the
@@ -998,12 +1015,13 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
   S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16]
   S* Bu = Us + (size_t)N * 16;                        // b_u -> y_t [N][5]
   S* V = Bu + (size_t)N * 5;                          // v blocks   [N][kCrStride2]
-  scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V);
+  const ScgsLay L{16, 5, N * kCrStride2, 0};
+  scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V, L);
 
   CellG<S> cg_;
   cg_.init(g, 2 * (q % ncx) + (colour & 1), 2 * (q / ncx) + (colour >> 1));
   cr_split<S, false>(V, N, cg_, threadIdx.x, blockDim.x);
-  scgs_update<T, S, kCrStride2>(g, x, colour, ncx, ncell, 1, q, Us, Bu, V);
+  scgs_update<T, S, kCrStride2>(g, x, colour, ncx, ncell, 1, q, Us, Bu, V, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -1283,13 +1301,44 @@ void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T
   launch_pdl(nso_residual_colour_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, px, py, only_if_undone);
 }
 
+// the warp kernel's skewed layout for N blocks and cpb cells per CTA; cs is the
+// first stride from the dense size whose (cell, time) sweep has the fewest
+// lanes per bank (a constant offset rotates the banks, so one offset suffices)
+ScgsLay scgs_warp_layout(int N, int cpb) {
+  auto skew = [](int x, int m) { return x + (((m - x) % 32) + 32) % 32; };
+  ScgsLay L;
+  L.us = skew(16 * cpb, cpb);
+  L.bs = skew(5 * cpb, cpb);
+  L.shift = 1;
+  const int base = N * kCrStride + ((N - 1) >> 5) + 1;
+  L.cs = base;
+  int best = 1 << 30;
+  for (int cs = base; cs < base + 32; ++cs) {
+    int cnt[32] = {0}, worst = 0;
+    for (int l = 0; l < 32 && l / cpb < N; ++l) {
+      const int bank = (int)(((long long)(l % cpb) * cs + blk_off(L, l / cpb, kCrStride)) % 32);
+      worst = std::max(worst, ++cnt[bank]);
+    }
+    if (worst < best) {
+      best = worst;
+      L.cs = cs;
+    }
+  }
+  return L;
+}
+
+static size_t scgs_warp_bytes(int N, int cpb, size_t tsize) {
+  const ScgsLay L = scgs_warp_layout(N, cpb);
+  return ((size_t)N * (L.us + L.bs) + (size_t)cpb * L.cs) * tsize;
+}
+
+// one warp per cell, at most 8 per CTA, two CTAs per SM (228 KB of shared
+// memory per SM, 1 KB of it reserved per CTA)
 template <class S>
 int scgs_cells_per_cta(int N) {
-  // one warp per cell, at most 8 per CTA; ~110 KB of shared memory per CTA
-  const size_t per = scgs_cell_floats(N) * sizeof(S);
-  int c = (int)((110 * 1024) / per);
-  if (c > 8) c = 8;
-  return c < 1 ? 1 : c;
+  for (int c = 8; c > 1; --c)
+    if (scgs_warp_bytes(N, c, sizeof(S)) <= 115712) return c;
+  return 1;
 }
 
 // the CTA-per-cell kernel with THREADS threads (false: the records do not fit)
@@ -1335,7 +1384,8 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
   const int cta_cells = g.cta_cells >= 0 ? g.cta_cells : (sizeof(S) == 4 ? 256 : 1 << 30);
   if (ncell <= cta_cells && launch_scgs_cell_ts<T, S>(g, x, r, colour, ncx, ncy, lm_dev, st)) return;
   const int cpb = scgs_cells_per_cta<S>(g.N);
-  const size_t sm = (size_t)cpb * scgs_cell_floats(g.N) * sizeof(S);
+  const ScgsLay lay = scgs_warp_layout(g.N, cpb);
+  const size_t sm = ((size_t)g.N * (lay.us + lay.bs) + (size_t)cpb * lay.cs) * sizeof(S);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncAttributes fa{};
@@ -1344,7 +1394,7 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
                          227 * 1024 - (int)fa.sharedSizeBytes);
   });
   launch_pdl(scgs_colour_kernel<T, S>, dim3(blocks_for(ncell, cpb)), dim3(32 * cpb), sm, st, g, x, r, colour, ncx, ncy,
-             cpb, lm_dev);
+             cpb, lm_dev, lay);
 }
 
 template <class T>
@@ -1356,8 +1406,8 @@ void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
-  return tsize == 4 ? (size_t)scgs_cells_per_cta<float>(N) * scgs_cell_floats(N) * 4
-                    : (size_t)scgs_cells_per_cta<double>(N) * scgs_cell_floats(N) * 8;
+  return tsize == 4 ? scgs_warp_bytes(N, scgs_cells_per_cta<float>(N), 4)
+                    : scgs_warp_bytes(N, scgs_cells_per_cta<double>(N), 8);
 }
 
 template <class Tf, class Tc>
