@@ -592,10 +592,15 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
 // fp32 policy: the metric term feeds the fp32 adjoint sweep); the weights are
 // formed in fp64 and the result is accumulated into the fp64 metric slab.
 // ---------------------------------------------------------------------------
+// One separable pass for every level at once: level l = blockIdx.y filters
+// in + l in_stride into out + l out_stride with sigma_l = sigma0 2^l.
 template <class Tc, class To>
-__global__ void blur_kernel(int nx, int ny, int axis, int transpose, double sigma, const Tc* __restrict__ in,
-                            To* out, double scale, int accumulate) {
+__global__ void blur_kernel(int nx, int ny, int axis, int transpose, double sigma0, const Tc* __restrict__ in,
+                            size_t in_stride, To* out, size_t out_stride, double scale) {
   extern __shared__ double wsm[];
+  const double sigma = sigma0 * (double)(1 << blockIdx.y);
+  in += (size_t)blockIdx.y * in_stride;
+  out += (size_t)blockIdx.y * out_stride;
   const int R = (int)ceil(3.0 * sigma);
   const int nt = 2 * R + 1;
   double* wd = wsm;              // raw weights, then their prefix sums (fp64)
@@ -652,9 +657,17 @@ __global__ void blur_kernel(int nx, int ny, int axis, int transpose, double sigm
         for (int b = lo; b <= hi; ++b) acc += w[a - b + R] * at(b);
       }
     }
-    const Tc val = acc * Tc(scale);
-    if (accumulate) out[e] += To(val);
-    else out[e] = To(val);
+    out[e] = To(acc * Tc(scale));
+  }
+}
+
+// out = sum over the levels, in level order from zero, of the per-level terms
+template <class Tc>
+__global__ void level_sum_kernel(const Tc* __restrict__ v, int levels, int C, double* out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C; e += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < levels; ++l) acc += (double)v[(size_t)l * C + e];
+    out[e] = acc;
   }
 }
 
@@ -669,7 +682,12 @@ __global__ void scale_kernel(const Tc* __restrict__ in, double* out, double c, i
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) out[e] = c * (double)in[e];
 }
 
-// tmp0: C doubles, tmp1: 2C doubles (used as arrays of the state type)
+size_t metric_tmp1_doubles(size_t C, int levels) { return 2 * C * (size_t)(levels > 1 ? levels : 1); }
+
+// tmp0: C doubles, tmp1: metric_tmp1_doubles (used as arrays of the state
+// type: per level, G_x d and G_y^T G_y G_x d, then c G_x^T of that).  Each
+// pass runs every level in one launch; the levels are summed in level order
+// at the end, as the per-level accumulation did.
 template <class T>
 void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
                    double* out, double* tmp0, double* tmp1, cudaStream_t st) {
@@ -678,23 +696,22 @@ void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, 
   const int tpb = 256;
   const unsigned nb = (unsigned)((C + tpb - 1) / tpb);
   T* d0 = reinterpret_cast<T*>(tmp0);
-  T* d1 = reinterpret_cast<T*>(tmp1);
-  T* d2 = d1 + C;
+  T* d1 = reinterpret_cast<T*>(tmp1);            // [levels][C]
+  T* d2 = d1 + (size_t)levels * C;               // [levels][C]
   metric_diff_kernel<T, T><<<nb, tpb, 0, st>>>(rho_s, star, d0, C);
   if (levels <= 0) {
     scale_kernel<T><<<nb, tpb, 0, st>>>(d0, out, c, C);   // C_i = c_i I
     return;
   }
-  cudaMemsetAsync(out, 0, sizeof(double) * C, st);
-  for (int l = 0; l < levels; ++l) {
-    const double sig = sigma0 * (double)(1 << l);
-    const int R = (int)ceil(3.0 * sig);
-    const size_t sm = sizeof(double) * 3 * (2 * R + 1);
-    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 0, sig, d0, d1, 1.0, 0);          // G_x
-    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 0, sig, d1, d2, 1.0, 0);          // G_y
-    blur_kernel<T, T><<<nb, tpb, sm, st>>>(g.nx, g.ny, 1, 1, sig, d2, d1, 1.0, 0);          // G_y^T
-    blur_kernel<T, double><<<nb, tpb, sm, st>>>(g.nx, g.ny, 0, 1, sig, d1, out, c, 1);      // += c G_x^T
-  }
+  const int R = (int)ceil(3.0 * sigma0 * (double)(1 << (levels - 1)));   // the widest level's taps
+  const size_t sm = sizeof(double) * 3 * (2 * R + 1);
+  const dim3 grid(nb, levels);
+  const size_t Cs = (size_t)C;
+  blur_kernel<T, T><<<grid, tpb, sm, st>>>(g.nx, g.ny, 0, 0, sigma0, d0, 0, d1, Cs, 1.0);   // G_x
+  blur_kernel<T, T><<<grid, tpb, sm, st>>>(g.nx, g.ny, 1, 0, sigma0, d1, Cs, d2, Cs, 1.0);  // G_y
+  blur_kernel<T, T><<<grid, tpb, sm, st>>>(g.nx, g.ny, 1, 1, sigma0, d2, Cs, d1, Cs, 1.0);  // G_y^T
+  blur_kernel<T, T><<<grid, tpb, sm, st>>>(g.nx, g.ny, 0, 1, sigma0, d1, Cs, d2, Cs, c);    // c G_x^T
+  level_sum_kernel<T><<<nb, tpb, 0, st>>>(d2, levels, C, out);
 }
 
 // ---------------------------------------------------------------------------

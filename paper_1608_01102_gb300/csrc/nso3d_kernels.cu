@@ -42,22 +42,10 @@ __device__ __forceinline__ T row3(const Geom& g, const CState<T>& x, int t, int 
   return val;
 }
 
-__device__ __forceinline__ void block_sumsq(double w, double* sq) {
-  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-  __shared__ double part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    w = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    if (threadIdx.x == 0) atomicAdd(sq, w);
-  }
-}
-
 // out = sf * f(x) + sr * res; thread x: face e (< F) and cell e (< C); blockIdx.y: t
 template <class T>
 __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res, State<T> out,
-                                     T sf, T sr, double* sq, const double* only_if_undone) {
+                                     T sf, T sr, double* sq, RedScratch rs, const double* only_if_undone) {
   pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
@@ -106,7 +94,7 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
       acc += val * val;
     }
   }
-  if (sq) block_sumsq((double)acc, sq);
+  if (sq) block_sum_ordered((double)acc, sq, rs);
 }
 
 // f - res at what one colour's SCGS reads: the faces of its cells (x-faces of
@@ -1279,10 +1267,15 @@ inline unsigned blocks3(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / t
 // ---------------------------------------------------------------------------
 template <class T>
 void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                          cudaStream_t st, double* sq, const double* only_if_undone) {
+                          cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs) {
   const int n = g.F > g.C ? g.F : g.C;
   launch_pdl3(nso_residual3_kernel<T>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out, sf, sr,
-              sq, only_if_undone);
+              sq, rs, only_if_undone);
+}
+
+size_t nso_residual3_blocks(const Geom& g) {
+  const int n = g.F > g.C ? g.F : g.C;
+  return (size_t)blocks3(n, 128) * (g.N + 1);
 }
 
 template <class T>
@@ -1414,7 +1407,7 @@ void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, 
 
 #define STC3_INST_T(T)                                                                                         \
   template void launch_nso_residual3<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
-                                        cudaStream_t, double*, const double*);                                \
+                                        cudaStream_t, double*, const double*, RedScratch);                                \
   template void launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,    \
                                                cudaStream_t, const double*);                                  \
   template void launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \

@@ -52,7 +52,7 @@ __device__ __forceinline__ T nso_row3(const Geom& g, const CState<T>& x, int t, 
 
 template <class T>
 __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z,
-                                   CState<T> res, State<T> out, T sf, T sr, double* sq,
+                                   CState<T> res, State<T> out, T sf, T sr, double* sq, RedScratch rs,
                                    const double* only_if_undone) {
   pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,18 +117,7 @@ __global__ void nso_residual_kernel(Geom g, CState<T> x, const T* __restrict__ z
       acc += val * val;
     }
   }
-  if (sq) {
-    double w = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    __shared__ double part[32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      w = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-      if (threadIdx.x == 0) atomicAdd(sq, w);
-    }
-  }
+  if (sq) block_sum_ordered((double)acc, sq, rs);
 }
 
 // ---------------------------------------------------------------------------
@@ -847,7 +836,8 @@ enum : int { CR_C2 = 77 };
 // (shorter rounds of the split block steps), 128 on larger ones (occupancy)
 constexpr int kCellCtaThreadsSmall = 256, kCellCtaThreadsLarge = 128, kCellCtaSmallCells = 256;
 
-__host__ __device__ inline size_t scgs_cell_floats2(int N) { return (size_t)(16 + 5 + kCrStride2) * N; }
+// (U rows 17 apart: odd, so the time-indexed lanes of a one-cell CTA hit distinct banks)
+__host__ __device__ inline size_t scgs_cell_floats2(int N) { return (size_t)(17 + 5 + kCrStride2) * N; }
 
 template <bool WARP>
 __device__ __forceinline__ void group_sync() {
@@ -1012,10 +1002,10 @@ scgs_colour_cell_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncx, in
   const S lm = S(lm_dev ? *lm_dev : g.lm);
   const int ncell = ncx * ncy;
   const int q = blockIdx.x;
-  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][16]
-  S* Bu = Us + (size_t)N * 16;                        // b_u -> y_t [N][5]
+  S* Us = reinterpret_cast<S*>(smem_raw);            // U_t        [N][17] (16 used)
+  S* Bu = Us + (size_t)N * 17;                        // b_u -> y_t [N][5]
   S* V = Bu + (size_t)N * 5;                          // v blocks   [N][kCrStride2]
-  const ScgsLay L{16, 5, N * kCrStride2, 0};
+  const ScgsLay L{17, 5, N * kCrStride2, 0};
   scgs_assemble<T, S, kCrStride2>(g, x, r, colour, ncx, ncell, 1, q, lm, Us, Bu, V, L);
 
   CellG<S> cg_;
@@ -1206,22 +1196,14 @@ __global__ void absmax_kernel(const T* __restrict__ a, size_t n, double* out, in
 }
 
 template <class T>
-__global__ void sumsq_kernel(const T* __restrict__ a, size_t n, double* out) {
+__global__ void sumsq_kernel(const T* __restrict__ a, size_t n, double* out, RedScratch rs) {
   pdl_wait();
   double s = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     double v = (double)a[e];
     s += v * v;
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double sm[32];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x + 31) / 32) ? sm[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) atomicAdd(out, s);
-  }
+  block_sum_ordered(s, out, rs);
 }
 
 // subtract the mean of each of `count` slabs of length C (one block per slab)
@@ -1279,12 +1261,18 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st, double* sq, const double* only_if_undone) {
-  if (g.dim == 3) return launch_nso_residual3<T>(g, x, z, res, out, sf, sr, st, sq, only_if_undone);
+                         cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs) {
+  if (g.dim == 3) return launch_nso_residual3<T>(g, x, z, res, out, sf, sr, st, sq, only_if_undone, rs);
   const int tpb = 128;
   const int n = g.F > g.C ? g.F : g.C;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
-  launch_pdl(nso_residual_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, sf, sr, sq, only_if_undone);
+  launch_pdl(nso_residual_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, sf, sr, sq, rs, only_if_undone);
+}
+
+size_t nso_residual_blocks(const Geom& g) {
+  if (g.dim == 3) return nso_residual3_blocks(g);
+  const int n = g.F > g.C ? g.F : g.C;
+  return (size_t)blocks_for(n, 128) * (g.N + 1);
 }
 
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
@@ -1463,12 +1451,12 @@ void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st)
 }
 
 template <class T>
-void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st) {
+void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st, RedScratch rs) {
   const int tpb = 256;
   unsigned nb = blocks_for(n, tpb);
-  if (nb > 1216) nb = 1216;
+  if (nb > kReduceMaxBlocks) nb = kReduceMaxBlocks;
   if (nb == 0) nb = 1;
-  launch_pdl(sumsq_kernel<T>, dim3(nb), dim3(tpb), 0, st, a, n, out);
+  launch_pdl(sumsq_kernel<T>, dim3(nb), dim3(tpb), 0, st, a, n, out, rs);
 }
 
 template <class T>
@@ -1488,13 +1476,13 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 
 #define STC_INST_T(T)                                                                                     \
   template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
-                                       cudaStream_t, double*, const double*);                              \
+                                       cudaStream_t, double*, const double*, RedScratch);                  \
   template void launch_nso_residual_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,     \
                                               cudaStream_t, const double*);                                \
   template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
                                       const double*, void*);                                               \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
-  template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t);                                 \
+  template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t, RedScratch);                     \
   template void launch_remove_mean<T>(T*, int, int, cudaStream_t);
 STC_INST_T(float)
 STC_INST_T(double)

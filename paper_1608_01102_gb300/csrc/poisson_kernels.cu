@@ -552,37 +552,26 @@ __global__ void blend_kernel(size_t n, const T* __restrict__ x, const T* __restr
     out[e] = x[e] + T(a) * (y[e] - x[e]);
 }
 
-__device__ __forceinline__ void block_add(double s, double* out) {
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x + 31) / 32 ? part[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) atomicAdd(out, s);
-  }
-}
 
 // keyframe misfit of Eq. opt in the C_i metric: 0.5 (rho - rho*)^T m with m = C (rho - rho*)
 template <class T>
 __global__ void misfit_dot_kernel(int C, const T* __restrict__ rho, const double* __restrict__ star,
-                                  const double* __restrict__ m, double* out) {
+                                  const double* __restrict__ m, double* out, RedScratch rs) {
   double s = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C; e += gridDim.x * blockDim.x)
     s += ((double)rho[e] - star[e]) * m[e];
-  block_add(0.5 * s, out);
+  block_sum_ordered(0.5 * s, out, rs);
 }
 
 template <class T>
 __global__ void diff_sumsq_kernel(size_t n, const T* __restrict__ a, const T* __restrict__ b, double scale,
-                                  double* out) {
+                                  double* out, RedScratch rs) {
   double s = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double d = (double)a[e] - (double)b[e];
     s += d * d;
   }
-  block_add(scale * s, out);
+  block_sum_ordered(scale * s, out, rs);
 }
 
 static inline unsigned nblk(size_t n, int tpb, unsigned cap = 4096) {
@@ -628,13 +617,14 @@ void launch_blend_faces(const Geom& g, int count, const T* x, const T* y, double
 }
 template <class T>
 void launch_misfit_dot(const Geom& g, const T* rho, const double* star, const double* m, double* out,
-                       cudaStream_t st) {
-  misfit_dot_kernel<T><<<nblk(g.C, 256, 304), 256, 0, st>>>(g.C, rho, star, m, out);
+                       cudaStream_t st, RedScratch rs) {
+  misfit_dot_kernel<T><<<nblk(g.C, 256, 304), 256, 0, st>>>(g.C, rho, star, m, out, rs);
 }
 template <class T>
-void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st) {
+void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st,
+                       RedScratch rs) {
   if (n == 0) return;
-  diff_sumsq_kernel<T><<<nblk(n, 256, 1216), 256, 0, st>>>(n, a, b, scale, out);
+  diff_sumsq_kernel<T><<<nblk(n, 256, kReduceMaxBlocks), 256, 0, st>>>(n, a, b, scale, out, rs);
 }
 
 #define STC_POI_INST(T)                                                                                        \
@@ -646,8 +636,8 @@ void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* o
   template void launch_absdiff_max_copy<T>(const T*, T*, size_t, double*, cudaStream_t);                   \
   template void launch_blend_faces<T>(const Geom&, int, const T*, const T*, double, T*, cudaStream_t);        \
   template void launch_misfit_dot<T>(const Geom&, const T*, const double*, const double*, double*,            \
-                                     cudaStream_t);                                                           \
-  template void launch_diff_sumsq<T>(const T*, const T*, size_t, double, double*, cudaStream_t);
+                                     cudaStream_t, RedScratch);                                               \
+  template void launch_diff_sumsq<T>(const T*, const T*, size_t, double, double*, cudaStream_t, RedScratch);
 STC_POI_INST(float)
 STC_POI_INST(double)
 

@@ -126,6 +126,8 @@ struct stc_problem {
   double* hscal = nullptr;  // pinned host mirror
   int* derr = nullptr;
   int* herr = nullptr;
+  RedScratch red{};               // deterministic sums on the problem's stream
+  RedScratch tred[kMaxTrials] = {};   // ... on the blend trials' streams
   double rho_scale = 0.0;
   double fscale = -1.0;
   cudaGraphExec_t vgraph = nullptr;
@@ -161,6 +163,22 @@ void* dalloc(stc_problem* P, size_t bytes) {
   P->allocs.push_back(p);
   ck(cudaMemsetAsync(p, 0, bytes, P->st), "memset");
   return p;
+}
+
+// scratch of the deterministic sums: partials for cap blocks and a ticket
+RedScratch alloc_red(stc_problem* P, size_t cap) {
+  RedScratch r;
+  r.part = (double*)dalloc(P, cap * sizeof(double));
+  r.ticket = (unsigned*)dalloc(P, sizeof(unsigned));
+  r.cap = (unsigned)cap;
+  return r;
+}
+
+// the most blocks of a reduction on the problem's stream: the finest level's
+// residual with its fused norm, or the generic sums
+size_t red_capacity(const Geom& g0) {
+  const size_t b = nso_residual_blocks(g0);
+  return b > kReduceMaxBlocks ? b : kReduceMaxBlocks;
 }
 
 // (N, dt: the level's; the smoother's LM shift stays the finest level's;
@@ -230,7 +248,7 @@ void nso_residual(stc_problem* P, int l, double sf, double sr, const FieldSet& r
   dispatch(L.dbl, [&](auto tag) {
     using T = decltype(tag);
     launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st,
-                           sq, only_if_undone);
+                           sq, only_if_undone, P->red);
   });
   count(P, 1);
 }
@@ -495,7 +513,10 @@ void metric_terms(stc_problem* P, const void* rho, cudaStream_t st, double* mter
                        P->prm.metric_sigma0, mterm + (size_t)s * g.C, tmp0, tmp1, st);
     });
   }
-  count(P, (long long)P->key_steps.size() * (P->prm.metric_levels > 0 ? 1 + 4 * P->prm.metric_levels : 2));
+  // per keyframe: the difference, then 2D four all-level passes and the level
+  // sum, 3D six passes per level; without levels the difference and a scaling
+  const int L = P->prm.metric_levels;
+  count(P, (long long)P->key_steps.size() * (L > 0 ? (g.dim == 3 ? 1 + 6 * L : 6) : 2));
   check_launch("metric");
 }
 
@@ -570,23 +591,25 @@ void prepare_targets(stc_problem* P, cudaStream_t st) {
 // 0.5 sum_keys (rho_s - rho*_s)^T C_s (rho_s - rho*_s) + K/2 sum_{i=1}^{N-1} ||w_i - v*_i||^2
 // (enqueues the sum into *out, which it zeroes first; mterm: the metric terms of rho)
 void enqueue_ao_objective(stc_problem* P, const void* vel, const void* rho, const double* mterm, double* out,
-                          cudaStream_t st) {
+                          cudaStream_t st, const RedScratch& rs) {
   const Geom& g = P->lv[0].g;
   ck(cudaMemsetAsync(out, 0, sizeof(double), st), "memset");
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
     for (size_t k = 0; k < P->key_steps.size(); ++k) {
       const int s = P->key_steps[k];
-      launch_misfit_dot<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, mterm + (size_t)s * g.C, out, st);
+      launch_misfit_dot<T>(g, (const T*)rho + (size_t)s * g.C, P->star + k * g.C, mterm + (size_t)s * g.C, out, st,
+                           rs);
     }
-    launch_diff_sumsq<T>((const T*)P->w + g.F, (const T*)vel + g.F, (size_t)(g.N - 1) * g.F, 0.5 * P->prm.K, out, st);
+    launch_diff_sumsq<T>((const T*)P->w + g.F, (const T*)vel + g.F, (size_t)(g.N - 1) * g.F, 0.5 * P->prm.K, out, st,
+                         rs);
   });
   count(P, (long long)P->key_steps.size() + (g.N > 1 ? 1 : 0));
   check_launch("ao objective");
 }
 
 double ao_objective(stc_problem* P, const void* vel, const void* rho, cudaStream_t st, bool trial = false) {
-  enqueue_ao_objective(P, vel, rho, P->mterm, P->dscal + 4, st);
+  enqueue_ao_objective(P, vel, rho, P->mterm, P->dscal + 4, st, P->red);
   return read_scalar(P, 4, trial);
 }
 
@@ -615,7 +638,7 @@ int blend_concurrent(stc_problem* P, double& J, cudaStream_t st) {
       count(P, g.N > 1 ? 1 : 0);
       forward(P, P->tv[j], P->trho[j], P->tK[j], s, P->terr + j);
       metric_terms(P, P->trho[j], s, P->tmterm[j], P->ttmp0[j], P->ttmp1[j]);
-      enqueue_ao_objective(P, P->tv[j], P->trho[j], P->tmterm[j], P->dtrial + j, s);
+      enqueue_ao_objective(P, P->tv[j], P->trho[j], P->tmterm[j], P->dtrial + j, s, P->tred[j]);
       ck(cudaEventRecord(P->tdone[j], s), "event");
       ck(cudaStreamWaitEvent(st, P->tdone[j], 0), "wait");
     }
@@ -744,9 +767,9 @@ void kkt(stc_problem* P, cudaStream_t st) {
     for (size_t k = 0; k < P->key_steps.size(); ++k) {
       const int s = P->key_steps[k];
       launch_misfit_dot<T>(g, (const T*)P->rho_k + (size_t)s * g.C, P->star + k * g.C, P->mterm + (size_t)s * g.C,
-                           P->dscal + 5, st);
+                           P->dscal + 5, st, P->red);
     }
-    launch_sumsq<T>((const T*)P->uk, (size_t)g.N * g.F, P->dscal + 6, st);
+    launch_sumsq<T>((const T*)P->uk, (size_t)g.N * g.F, P->dscal + 6, st, P->red);
   });
   count(P, (long long)P->key_steps.size() + 1);
   dispatch(P->dbl, [&](auto tag) {
@@ -757,7 +780,7 @@ void kkt(stc_problem* P, cudaStream_t st) {
   ck(cudaMemsetAsync(P->dscal + 1, 0, sizeof(double), st), "memset");
   dispatch(P->dbl, [&](auto tag) {
     using T = decltype(tag);
-    launch_sumsq<T>((const T*)P->gk, (size_t)(g.N + 1) * g.F, P->dscal + 1, st);
+    launch_sumsq<T>((const T*)P->gk, (size_t)(g.N + 1) * g.F, P->dscal + 1, st, P->red);
   });
   count(P, 3);
   check_launch("kkt");
@@ -1074,11 +1097,14 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   total += 3 * b((N + 1) * C * ts) + b(N * C * ts) + 2 * b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) +
            b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts, N) : 0) + 4 * b(N * F * ts) +
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
-           b((N + 1) * C * 8) + b(C * 8) + b(2 * C * 8) + b(16 * 8) + b(4);
+           b((N + 1) * C * 8) + b(C * 8) + b(metric_tmp1_doubles(C, prm.metric_levels) * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
+  total += b(red_capacity(make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt)) * 8) + b(4);
   const int nt = ao_trial_count(prm);
+  if (nt > 1) total += (size_t)nt * (b(kReduceMaxBlocks * 8) + b(4));
   if (nt > 1)
-    total += (size_t)(nt - 1) * (b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) + b(C * 8) + b(2 * C * 8)) +
+    total += (size_t)(nt - 1) * (b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) + b(C * 8) +
+                                 b(metric_tmp1_doubles(C, prm.metric_levels) * 8)) +
              (size_t)nt * b((N + 1) * C * 8) + b(kMaxTrials * 4) + b(kMaxTrials * 8);
   Geom g0 = make_geom(prm, prm.nx, prm.ny, prm.nz, 1.0 / prm.nx, prm.num_steps, prm.dt);
   if (project_dct_fits(g0, ts)) total += b(project_dct_elems(g0) * ts);
@@ -1257,9 +1283,10 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->Kk = (int*)dalloc(P, N * sizeof(int));
     P->mterm = (double*)dalloc(P, (N + 1) * C * sizeof(double));
     P->mtmp0 = (double*)dalloc(P, C * sizeof(double));
-    P->mtmp1 = (double*)dalloc(P, 2 * C * sizeof(double));
+    P->mtmp1 = (double*)dalloc(P, metric_tmp1_doubles(C, prm.metric_levels) * sizeof(double));
     P->dscal = (double*)dalloc(P, 16 * sizeof(double));
     P->derr = (int*)dalloc(P, sizeof(int));
+    P->red = alloc_red(P, red_capacity(g0));
     P->ntrials = ao_trial_count(prm);
     if (P->ntrials > 1) {
       P->tv[0] = P->vcand;
@@ -1273,9 +1300,10 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
           P->trho[j] = dalloc(P, (N + 1) * C * ts);
           P->tK[j] = (int*)dalloc(P, N * sizeof(int));
           P->ttmp0[j] = (double*)dalloc(P, C * sizeof(double));
-          P->ttmp1[j] = (double*)dalloc(P, 2 * C * sizeof(double));
+          P->ttmp1[j] = (double*)dalloc(P, metric_tmp1_doubles(C, prm.metric_levels) * sizeof(double));
         }
         P->tmterm[j] = (double*)dalloc(P, (N + 1) * C * sizeof(double));
+        P->tred[j] = alloc_red(P, kReduceMaxBlocks);
         ck(cudaStreamCreateWithFlags(&P->tst[j], cudaStreamNonBlocking), "stream");
         ck(cudaEventCreateWithFlags(&P->tdone[j], cudaEventDisableTiming), "event");
       }
@@ -1297,12 +1325,13 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       std::vector<double> tab(ne);
       project_dct_tables(g0, tab.data());
       P->dct = dalloc(P, ne * ts);
-      if (P->dbl) {
-        ck(cudaMemcpy(P->dct, tab.data(), ne * ts, cudaMemcpyHostToDevice), "h2d");
-      } else {
-        std::vector<float> tf(tab.begin(), tab.end());
-        ck(cudaMemcpy(P->dct, tf.data(), ne * ts, cudaMemcpyHostToDevice), "h2d");
-      }
+      // on the problem's stream, after dalloc's zeroing (a copy on another
+      // stream could land before that memset)
+      std::vector<float> tf(P->dbl ? 0 : ne);
+      for (size_t e = 0; e < tf.size(); ++e) tf[e] = (float)tab[e];
+      const void* src = P->dbl ? (const void*)tab.data() : (const void*)tf.data();
+      ck(cudaMemcpyAsync(P->dct, src, ne * ts, cudaMemcpyHostToDevice, P->st), "h2d");
+      ck(cudaStreamSynchronize(P->st), "sync");
     }
     ck(cudaMallocHost(&P->hscal, 16 * sizeof(double)), "pinned");
     ck(cudaMallocHost(&P->herr, sizeof(int)), "pinned");

@@ -81,6 +81,51 @@ __host__ __device__ inline int cidx(const Geom& g, int j, int i) { return j * g.
 template <class T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// Deterministic fp64 sums.  Every block leaves its total in part[block]; the
+// last block to take a ticket adds the partials in block order and adds the
+// result to *out, then resets the ticket.  A sum therefore does not depend on
+// the order in which the blocks ran (cross-block atomics did: a tie in a
+// guard's comparison could then go either way between two runs).  cap: the
+// entries of part (a launch must not have more blocks).
+struct RedScratch {
+  double* part;
+  unsigned* ticket;
+  unsigned cap;
+};
+
+// called by every thread of every block of the launch; v: this thread's share
+__device__ inline void block_sum_ordered(double v, double* out, const RedScratch& rs) {
+  __shared__ double wpart[32];
+  __shared__ int last_s;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const int nw = (int)((blockDim.x + 31) >> 5);
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += wpart[k];
+    rs.part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    __threadfence();
+    last_s = atomicAdd(rs.ticket, 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (!last_s) return;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) t += __ldcg(rs.part + b);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wpart[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += wpart[k];
+    *out += s;
+    *rs.ticket = 0;
+  }
+}
+
 // Programmatic dependent launch: a kernel of the V-cycle chain may be launched
 // while its predecessor is still finishing; it waits here, before touching any
 // data, until the predecessor has completed and its writes are visible.  A

@@ -14,7 +14,13 @@ void set_last_error(const char* msg);
 // guarded coarse-grid correction was undone (after > before or NaN).
 template <class T>
 void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr);
+                         cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr,
+                         RedScratch rs = RedScratch{});
+// blocks of a launch_nso_residual launch (the RedScratch capacity its sq needs)
+size_t nso_residual_blocks(const Geom& g);
+size_t nso_residual3_blocks(const Geom& g);
+// most blocks of the other reductions (sumsq, diff_sumsq; misfit_dot uses fewer)
+constexpr unsigned kReduceMaxBlocks = 1216;
 // out = f - res at the faces and cells one SCGS colour reads (other entries untouched);
 // only_if_undone as in launch_nso_residual
 template <class T>
@@ -40,7 +46,7 @@ void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<
 template <class T>
 void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st);
 template <class T>
-void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st);
+void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st, RedScratch rs);
 template <class T>
 void launch_remove_mean(T* a, int count, int C, cudaStream_t st);
 template <class Ts, class Td>
@@ -68,6 +74,8 @@ template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
                                   cudaStream_t st, int s_end = 1, T* mu_m1 = nullptr);
+// doubles of launch_metric's tmp1 for C cells and the given levels
+size_t metric_tmp1_doubles(size_t C, int levels);
 // m_s = c * sum_l G_l^T G_l (rho_s - rho*_s) (fp64) into mterm slab s.
 template <class T>
 void launch_metric(const Geom& g, const T* rho_s, const double* star, double c, int levels, double sigma0,
@@ -113,17 +121,18 @@ void launch_blend_faces(const Geom& g, int count, const T* x, const T* y, double
 // out += 0.5 * sum_c (rho_c - star_c) * m_c over one cell slab (fp64)
 template <class T>
 void launch_misfit_dot(const Geom& g, const T* rho, const double* star, const double* m, double* out,
-                       cudaStream_t st);
+                       cudaStream_t st, RedScratch rs);
 // out += scale * sum_e (a_e - b_e)^2 over n entries (fp64)
 template <class T>
-void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st);
+void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* out, cudaStream_t st,
+                       RedScratch rs);
 
 // --- 3D grid (nso3d_kernels.cu, advect3d_kernels.cu, poisson3d_kernels.cu) ---
 // Same contracts as the 2D launchers above; the generic launchers forward to
 // these when g.dim == 3.
 template <class T>
 void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                          cudaStream_t st, double* sq, const double* only_if_undone);
+                          cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs);
 template <class T>
 void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
                                  cudaStream_t st, const double* only_if_undone);

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import admm, kkt, mac, projection, scgs, stfas
-from paper_1608_01102_gb300 import workloads
+from paper_1608_01102_gb300 import stc, workloads
 
 from gpu_common import TOL, make_pair, random_state, rel, velocity_trajectory
 
@@ -65,6 +65,29 @@ def test_projection_is_exact_where_the_dct_applies(prec, shape):
     again = G.get("W")
     for i in range(3):
         assert rel(again[i], out[i]) < tol, i
+
+
+def test_problem_created_on_a_busy_stream_projects_exactly():
+    """Everything a problem uploads at creation is ordered after the zeroing
+    of its buffers on the problem's own stream: created on a non-blocking
+    stream that is still busy, the projection tables must hold (a copy issued
+    on another stream would land before the queued memset and be erased)."""
+    torch = pytest.importorskip("torch")
+    nx = ny = 32
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        torch.cuda._sleep(200_000_000)            # ~0.1 s of GPU time ahead of the problem's setup
+    P, _ = make_pair(nx, ny, N=2, precision=1, levels=0)
+    prm = stc.default_params(nx, ny, 2, precision=1, r=1e-2, K=1.0, metric_levels=0)
+    G = stc.Problem(prm, P.rho0, stream=s.cuda_stream)
+    w = workloads.random_faces(np.random.default_rng(5), nx, ny, 2)
+    w[1] += workloads.swirl_velocity(nx, ny, 3.0)
+    G.set("W", w)
+    G.project("W", 0, 2)
+    out = G.get("W")
+    for i in range(2):
+        assert rel(out[i], projection.project(P.grid, w[i])) < 1e-12, i
+    G.close()
 
 
 def test_projection_with_global_scratch_fp64_128():

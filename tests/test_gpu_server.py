@@ -39,10 +39,12 @@ def test_each_result_is_the_same_alone_and_in_the_mix(prec):
         tickets = [S.submit(*_problem(*c, prec), tol=1e-6, max_admm=6) for c in CASES]
         infos = [S.wait(t) for t in tickets]
         assert S.stats()["peak_bytes"] <= budget
+        seen = [(i["report"]["admm_iters"], i["report"]["vcycles"]) for i in infos]
+        ref = [(r["admm_iters"], r["vcycles"]) for r, _ in alone]
         for t, info, (rep, u) in zip(tickets, infos, alone):
             assert info["state"] == "done", info
-            assert info["report"]["admm_iters"] == rep["admm_iters"]
-            assert info["report"]["vcycles"] == rep["vcycles"]
+            assert info["report"]["admm_iters"] == rep["admm_iters"], (seen, ref)
+            assert info["report"]["vcycles"] == rep["vcycles"], (seen, ref)
             got = S.forces(t)
             assert _rel(got, u) <= (1e-9 if prec == 1 else 1e-5), _rel(got, u)
             assert abs(info["report"]["kkt_rel"] - rep["kkt_rel"]) <= 1e-6 * rep["kkt_rel"] + 1e-12
