@@ -229,6 +229,43 @@ def test_scgs_sweep(prec, shape, N):
             assert err <= tol * np.linalg.norm(d) + floor, (l, k, err / max(np.linalg.norm(d), 1e-300))
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_warp_and_cta_per_cell_smoothers_agree(prec):
+    """The two 2D smoother kernels solve the same local systems: one warp per
+    cell (the nine-column saddle solve per lane) and one CTA per cell (the
+    block steps split over its threads, one column per thread).  Per level
+    and through whole V-cycles on 32^2 x 8 they agree to rounding (the split
+    repeats the same arithmetic per column, so in practice bit for bit)."""
+    nx, ny, N = 32, 32, 8
+    v = velocity_trajectory(nx, ny, N, amp=0.5, seed=61)
+    lam = workloads.random_faces(np.random.default_rng(62), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    out = {}
+    for name, over in (("cta", dict()), ("warp", dict(scgs_cta_cells=0))):
+        P, G = make_pair(nx, ny, N=N, precision=prec, dt=1.0 / 16, **over)
+        G.set("VSTAR", v[:N])
+        G.set("LAMBDA", lam)
+        G.prepare_targets()
+        states = []
+        for l in range(G.num_levels()):
+            g = stfas.hierarchy(P)[l]
+            G.set_state(random_state(P, 70 + l, grid=g, scale=0.3), level=l)
+            G.smooth(level=l, sweeps=2)
+            states.append(G.get_state(level=l))
+        G.set_state(kkt.zero_state(P))
+        f = [G.vcycle(1) for _ in range(3)]
+        out[name] = (states, f, G.get_state())
+        G.close()
+    (sa, fa, xa), (sb, fb, xb) = out["cta"], out["warp"]
+    for l, (a, b) in enumerate(zip(sa, sb)):
+        for k in a:
+            assert rel(a[k], b[k]) <= TOL[prec]["smooth"], (l, k, rel(a[k], b[k]))
+    for a, b in zip(fa, fb):
+        assert abs(a - b) <= TOL[prec]["vcycle"] * abs(b), (fa, fb)
+    for k in xa:
+        assert rel(xa[k], xb[k]) <= TOL[prec]["vcycle"], (k, rel(xa[k], xb[k]))
+
+
 # ---------------------------------------------------------------------------
 # a9: restriction and prolongation-correction
 # ---------------------------------------------------------------------------
