@@ -248,8 +248,9 @@ stc_status stc_level_dims(const stc_problem* p, int level, int* nx, int* ny, int
  * v_1..v_N, then advects rho_1..rho_N with v_0..v_{N-1} (Eq. Conv; Taylor
  * orders as stc_advect).  iters (may be NULL): Picard iterations in total.
  * The buffers of both calls are allocated at the first call (not counted by
- * stc_problem_bytes).  The multigrid projection makes Q exact to its
- * truncation (~1e-7 relative in fp32, ~1e-9 in fp64 after 8 cycles). */
+ * stc_problem_bytes).  Q is exact to rounding where the 2D DCT projection
+ * applies; the multigrid projection (3D, large 2D fields) makes it exact to
+ * its truncation (~1e-7 relative in fp32, ~1e-9 in fp64 after 8 cycles). */
 stc_status stc_simulate(stc_problem* p, double picard_tol, int max_iter, int* iters);
 /* Adjoint of stc_simulate's map (u, v_0, rho_0) -> (rho_0..rho_N, v_N) at its last
  * trajectory: given dL/d rho_i in STC_FIELD_SIM_GRAD_RHO and dL/d v_N in
@@ -368,6 +369,15 @@ stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes);
  * admission size).  STC_ERR_INVALID_ARG for parameters stc_create_problem
  * rejects. */
 stc_status stc_problem_bytes(const stc_params* params, int nkeys, size_t* bytes);
+/* The tables of the exact 2D projection (host arithmetic, no device): for the
+ * closed nx x ny box with h = 1/nx, out receives, in order, the orthonormal
+ * DCT-II matrices C_x (nx x nx, C[k][i] = s_k cos(pi k (2i+1) / 2n), s_0 =
+ * sqrt(1/n), s_k = sqrt(2/n)), C_x^T, C_y (ny x ny), C_y^T, then 1/lam
+ * (ny x nx, row ky, column kx; lam = -(4/h^2)(sin^2(pi kx/2nx) +
+ * sin^2(pi ky/2ny)), 1/lam_00 = 0), row-major fp64: 2 nx^2 + 2 ny^2 + nx ny
+ * values.  The library rounds them to the state type.  STC_ERR_INVALID_ARG
+ * for nx or ny < 1, a null out, or len smaller than that count. */
+stc_status stc_dct_tables(int nx, int ny, double* out, size_t len);
 
 /* ---- allocation-free entry point ------------------------------------------- */
 

@@ -1950,6 +1950,25 @@ stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* 
   return STC_OK;
 }
 
+stc_status stc_dct_tables(int nx, int ny, double* out, size_t len) {
+  if (nx < 1 || ny < 1 || !out) {
+    stc::set_last_error("invalid argument");
+    return STC_ERR_INVALID_ARG;
+  }
+  Geom g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.dim = 2;
+  g.nz = 1;
+  g.h = 1.0 / nx;
+  if (len < project_dct_elems(g)) {
+    stc::set_last_error("output shorter than 2 nx^2 + 2 ny^2 + nx ny");
+    return STC_ERR_INVALID_ARG;
+  }
+  project_dct_tables(g, out);
+  return STC_OK;
+}
+
 stc_status stc_problem_bytes(const stc_params* params, int nkeys, size_t* bytes) {
   if (!params || !bytes || nkeys < 0 || !params_valid(*params)) {
     stc::set_last_error("invalid parameters");

@@ -104,6 +104,7 @@ SIGNATURES = {
     "stc_nso_residual": (c_int, [c_void_p, c_int, P_double]),
     "stc_smooth": (c_int, [c_void_p, c_int, c_int]),
     "stc_problem_bytes": (c_int, [ctypes.POINTER(StcParams), c_int, ctypes.POINTER(c_size_t)]),
+    "stc_dct_tables": (c_int, [c_int, c_int, P_double, c_size_t]),
     "stc_server_default_params": (None, [ctypes.POINTER(ServerParams), c_size_t]),
     "stc_server_create": (c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(c_void_p)]),
     "stc_server_submit": (c_int, [P_server, ctypes.POINTER(Request), P_ll]),
@@ -422,6 +423,21 @@ def problem_bytes(params, nkeys=1):
     b = c_size_t()
     _check(load().stc_problem_bytes(ctypes.byref(params), nkeys, ctypes.byref(b)))
     return b.value
+
+
+def dct_tables(nx, ny):
+    """The exact 2D projection's tables (stc_dct_tables: host arithmetic, no
+    device needed): dict with Cx, CxT, Cy, CyT (square) and inv_lam (ny x nx)."""
+    n = 2 * nx * nx + 2 * ny * ny + nx * ny
+    out = np.zeros(n)
+    _check(load().stc_dct_tables(nx, ny, out.ctypes.data_as(P_double), n))
+    sizes = [("Cx", (nx, nx)), ("CxT", (nx, nx)), ("Cy", (ny, ny)), ("CyT", (ny, ny)), ("inv_lam", (ny, nx))]
+    res, o = {}, 0
+    for name, shp in sizes:
+        k = shp[0] * shp[1]
+        res[name] = out[o:o + k].reshape(shp)
+        o += k
+    return res
 
 
 TICKET_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
