@@ -9,7 +9,8 @@ namespace stc {
 void set_last_error(const char* msg);
 
 // --- NSO (nso_kernels.cu) ---------------------------------------------------
-// out = sf * f(x) + sr * res.  sq (optional): += sum of squares of out (fp64).
+// out = sf * f(x) + sr * res.  sq (optional): += sum of squares of out (fp64,
+// summed in block order through rs, which needs nso_residual_blocks(g) partials).
 // only_if_undone (optional, a guard's {before, after} norms): skip unless the
 // guarded coarse-grid correction was undone (after > before or NaN).
 template <class T>
@@ -45,6 +46,7 @@ void launch_prolong_correct(const Geom& gf, const Geom& gc, State<Tf> f, CState<
                             cudaStream_t st, const double* undo_if_rose = nullptr);
 template <class T>
 void launch_absmax(const T* a, size_t n, double* out, int* err, cudaStream_t st);
+// *out += sum of a_e^2 (fp64, block order through rs; at most kReduceMaxBlocks blocks)
 template <class T>
 void launch_sumsq(const T* a, size_t n, double* out, cudaStream_t st, RedScratch rs);
 template <class T>
