@@ -1315,18 +1315,30 @@ ScgsLay scgs_warp_layout(int N, int cpb) {
   return L;
 }
 
-static size_t scgs_warp_bytes(int N, int cpb, size_t tsize) {
-  const ScgsLay L = scgs_warp_layout(N, cpb);
+struct WarpPlan {
+  int cpb;
+  ScgsLay lay;
+  size_t bytes;
+};
+
+static size_t scgs_warp_bytes(int N, int cpb, const ScgsLay& L, size_t tsize) {
   return ((size_t)N * (L.us + L.bs) + (size_t)cpb * L.cs) * tsize;
 }
 
 // one warp per cell, at most 8 per CTA, two CTAs per SM (228 KB of shared
-// memory per SM, 1 KB of it reserved per CTA)
+// memory per SM, 1 KB of it reserved per CTA), in the skewed layout; when not
+// even one cell fits that way (long horizons: the skew pads a one-cell row of
+// b_u from 5 to 33 values), one cell per CTA in the dense layout (U rows 17
+// apart, b_u rows 5: odd, so the time-indexed lanes still hit distinct banks)
 template <class S>
-int scgs_cells_per_cta(int N) {
-  for (int c = 8; c > 1; --c)
-    if (scgs_warp_bytes(N, c, sizeof(S)) <= 115712) return c;
-  return 1;
+WarpPlan scgs_warp_plan(int N) {
+  for (int c = 8; c >= 1; --c) {
+    const ScgsLay L = scgs_warp_layout(N, c);
+    const size_t b = scgs_warp_bytes(N, c, L, sizeof(S));
+    if (b <= 115712) return {c, L, b};
+  }
+  const ScgsLay L{17, 5, N * kCrStride + ((N - 1) >> 5) + 1, 1};
+  return {1, L, scgs_warp_bytes(N, 1, L, sizeof(S))};
 }
 
 // the CTA-per-cell kernel with THREADS threads (false: the records do not fit)
@@ -1371,9 +1383,10 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
   // every level
   const int cta_cells = g.cta_cells >= 0 ? g.cta_cells : (sizeof(S) == 4 ? 256 : 1 << 30);
   if (ncell <= cta_cells && launch_scgs_cell_ts<T, S>(g, x, r, colour, ncx, ncy, lm_dev, st)) return;
-  const int cpb = scgs_cells_per_cta<S>(g.N);
-  const ScgsLay lay = scgs_warp_layout(g.N, cpb);
-  const size_t sm = ((size_t)g.N * (lay.us + lay.bs) + (size_t)cpb * lay.cs) * sizeof(S);
+  const WarpPlan plan = scgs_warp_plan<S>(g.N);
+  const int cpb = plan.cpb;
+  const ScgsLay lay = plan.lay;
+  const size_t sm = plan.bytes;
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncAttributes fa{};
@@ -1394,8 +1407,7 @@ void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
-  return tsize == 4 ? scgs_warp_bytes(N, scgs_cells_per_cta<float>(N), 4)
-                    : scgs_warp_bytes(N, scgs_cells_per_cta<double>(N), 8);
+  return tsize == 4 ? scgs_warp_plan<float>(N).bytes : scgs_warp_plan<double>(N).bytes;
 }
 
 template <class Tf, class Tc>
