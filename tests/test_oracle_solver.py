@@ -60,6 +60,34 @@ def test_reduced_gradient_matches_central_differences_8x8x4():
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12), (fd, an)
 
 
+def _brute_objective_frozen(P, u, Ks):
+    """J(u) of the full-resimulation chain with the Taylor orders held fixed."""
+    rhos, _ = kkt.forward_density(P, brute.simulate(P, u), Ks)
+    return 0.5 * P.r * float(np.sum(u * u)) + P.misfit(rhos)
+
+
+def _check_brute_gradient(P, rng, ndirs):
+    """dJ/du of brute.objective_and_gradient (the adjoint chain through the
+    implicit Navier-Stokes steps, ns_step_adjoint, and the density sweep)
+    against central differences of J(u) along random directions of the
+    interior faces (Appendix A: u is the control of the full problem)."""
+    m = mac.ops(P.grid)["mask"]
+    u = rng.standard_normal((P.N, P.grid.F)) * m * 0.3
+    J, g = brute.objective_and_gradient(P, u)
+    _, Ks = kkt.forward_density(P, brute.simulate(P, u))
+    assert abs(J - _brute_objective_frozen(P, u, Ks)) <= 1e-12 * abs(J)
+    for _ in range(ndirs):
+        d = rng.standard_normal(u.shape) * m
+        eps = 1e-5
+        fd = (_brute_objective_frozen(P, u + eps * d, Ks) - _brute_objective_frozen(P, u - eps * d, Ks)) / (2 * eps)
+        an = float(np.sum(g * d))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12), (fd, an)
+
+
+def test_full_resimulation_gradient_matches_central_differences_8x8x4():
+    _check_brute_gradient(_problem(levels=2, r=0.05), np.random.default_rng(23), 3)
+
+
 def test_zero_control_gives_zero_gradient_and_zero_residual():
     """Keyframe = the uncontrolled outcome from a nonzero v_0: J has its global
     minimum 0 at the Navier-Stokes trajectory, so g = 0 and f = 0 there."""
