@@ -392,6 +392,36 @@ def test_vcycle(prec, shape, N):
         assert abs(f_gpu - f_ref) <= 1e-3 * f_ref + TOL[prec]["vcycle"] * 1e3
 
 
+@pytest.mark.parametrize("prec", PREC)
+def test_vcycle_plain_alg2(prec):
+    """Alg. 2 exactly as printed: no coarse-correction guard, no damping
+    (omega = 1) and the Eq. HESS local blocks without a Levenberg-Marquardt
+    shift (lm_shift = 0, no adaptation) -- none of the safeguards that the
+    library and the oracle turn on by default.  Three cycles from zero."""
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, r=1e-3, cgc_guard=False, scgs_omega=1.0, lm_shift=0.0,
+                     lm_adapt=False)
+    assert P.lm_shift == 0.0 and P.omega == 1.0 and not P.cgc_guard
+    v = velocity_trajectory(nx, ny, N, amp=1.0, seed=5)
+    lam = workloads.random_faces(np.random.default_rng(6), nx, ny, N, 0.05)
+    lam[0] = 0.0
+    G.set("VSTAR", v[:N])
+    G.set("LAMBDA", lam)
+    G.prepare_targets()
+    z = v[:N] - lam / P.K
+    x = kkt.zero_state(P)
+    f_prev = np.inf
+    for c in range(3):
+        f_gpu = G.vcycle(1)
+        f_ref = stfas.stfas_cycle(P, x, z)
+        assert f_ref < 0.2 * f_prev       # the plain cycle contracts on this problem
+        f_prev = f_ref
+        got = G.get_state(0)
+        for k in x:
+            assert rel(got[k], x[k]) < TOL[prec]["vcycle"], (c, k, rel(got[k], x[k]))
+        assert abs(f_gpu - f_ref) <= 1e-3 * f_ref + TOL[prec]["vcycle"] * 1e3
+
+
 # ---------------------------------------------------------------------------
 # Alg. 1: AO fixed point (forward, adjoint, projection) and targets
 # ---------------------------------------------------------------------------
@@ -557,6 +587,23 @@ def test_admm_al_fallback(prec):
     assert abs(rep["objective"] - hist[-1]["objective"]) <= tol * hist[-1]["objective"]
     assert rel(G.get("V"), x["v"]) < tol
     assert rel(G.get("LAMBDA")[1:], lam[1:]) < (tol if prec == 1 else 1e-2) or np.all(lam == 0)
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_admm_adaptive_penalty(prec):
+    """k_adapt: the same penalty decisions (K = 4, 4, 2, 1, 0.5, 0.25 on this
+    case; every r_p / r_d ratio at least a factor 1.7 from the switching
+    thresholds) and the same iterate as the oracle after 6 ADMM iterations."""
+    nx, ny, N = 16, 16, 6
+    P, G = make_pair(nx, ny, N=N, precision=prec, levels=2, r=1e-3, sigma=0.12, K=4.0, k_adapt=True)
+    rep = G.solve(tol=1e-12, max_admm=6)
+    x, vs, lam, hist = admm.solve(P, tol=1e-12, max_admm=6, eps_admm=P.rho_scale / 100)
+    assert [h["K"] for h in hist] == [4.0, 4.0, 2.0, 1.0, 0.5, 0.25]
+    assert rep["admm_iters"] == len(hist) and rep["K_final"] == hist[-1]["K"]
+    tol = 1e-5 if prec == 1 else 1e-3
+    assert abs(rep["kkt_rel"] - hist[-1]["kkt_rel"]) <= tol * hist[-1]["kkt_rel"]
+    assert rel(G.get("V"), x["v"]) < tol
+    assert rel(G.get("U"), x["u"]) < (tol if prec == 1 else 1e-3)
 
 
 # ---------------------------------------------------------------------------
