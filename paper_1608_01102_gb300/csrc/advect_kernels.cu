@@ -439,7 +439,7 @@ template <class T>
 __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                       const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
-                      T* out, T* powers, int kmax, int s_end, T* mu_m1) {
+                      T* out, T* powers, int kmax, int s_end, T* mu_m1, int* err) {
   __shared__ T dtk[kTaylorKmaxLimit + 1];
   fill_dt_over_k(g, kmax, dtk);
   cg::cluster_group cl = cg::this_cluster();
@@ -484,8 +484,12 @@ taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ r
       if (e < nown) mu[cbase + e] = m[q];
     }
     int K = Ks[st];
-    if (K < 1) K = 1;
-    if (K > kmax) K = kmax;
+    if (K < 1 || K > kmax) {
+      // an order the powers buffer cannot hold: flagged, and the sweep
+      // continues with the clamped order (its output is then not the adjoint)
+      if (err && rank == 0 && threadIdx.x == 0) atomicOr(err, DEV_TAYLOR_KMAX);
+      K = K < 1 ? 1 : kmax;
+    }
     const T* rs = rho + (size_t)st * g.C;
     load_velocity(g, s, vel + (size_t)st * g.F, vx, vy);
     // powers P_1 .. P_{K-1}
@@ -757,7 +761,7 @@ template <class T>
 __global__ void __launch_bounds__(kAdvThreads, 1)
 taylor_adjoint_kernel(Geom g, const T* __restrict__ vel, const T* __restrict__ rho, const int* __restrict__ Ks,
                       const double* __restrict__ mterm, T* mu, const T* __restrict__ base, T alpha, T beta,
-                      T* out, T* powers, int kmax, int s_end, T* mu_m1);
+                      T* out, T* powers, int kmax, int s_end, T* mu_m1, int* err);
 
 // A 16-CTA cluster halves each CTA's rows (the per-term latency of the sweeps
 // scales with them); it needs 16 SMs of one GPC free at once.  The device is
@@ -824,13 +828,13 @@ cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, d
 template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
-                                  cudaStream_t st, int s_end, T* mu_m1) {
+                                  int* err, cudaStream_t st, int s_end, T* mu_m1) {
   if (kmax < 1 || kmax > kTaylorKmaxLimit) return cudaErrorInvalidValue;   // size of the dt/k table
   if (s_end != 0 && s_end != 1) return cudaErrorInvalidValue;
   Geom gg = g;
   void* args[] = {&gg,          (void*)&vel,   (void*)&rho,  (void*)&K,   (void*)&mterm,  (void*)&mu,
                   (void*)&base, (void*)&alpha, (void*)&beta, (void*)&out, (void*)&powers, (void*)&kmax,
-                  (void*)&s_end, (void*)&mu_m1};
+                  (void*)&s_end, (void*)&mu_m1, (void*)&err};
   return cluster_launch(taylor_adjoint_kernel<T>, adv_layout<T>(g, true, advect_cluster_ctas()).total, st, args);
 }
 
@@ -845,11 +849,14 @@ cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, con
 // cell fields -- lives in this file-scope device array instead of a buffer the
 // problem allocates.  It is modest (4 MiB) and, being a module global, it is
 // held on every GPU that loads the library until the process exits.  All
-// calls share it, so calls that overlap on the GPU race; nothing in it needs
-// to start at zero (each power is written before it is read).
+// calls share it, so calls that overlap on the GPU race; the powers need not
+// start at zero (each is written before it is read).  A tail of 64 words after
+// the powers holds the sweep's error word, cleared by each call before its
+// launch.
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocPowersFloats = (size_t)1 << 20;
-static __device__ __align__(256) float g_noalloc_powers[kNoAllocPowersFloats];
+constexpr size_t kNoAllocTailWords = 64;
+static __device__ __align__(256) float g_noalloc_powers[kNoAllocPowersFloats + kNoAllocTailWords];
 
 namespace {
 std::mutex g_noalloc_mutex;
@@ -892,7 +899,7 @@ extern "C" stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, d
     set_last_error("stc_adjoint_sweep_noalloc: taylor_kmax * nx * ny exceeds the fixed scratch of 1048576 floats");
     return STC_ERR_INVALID_ARG;
   }
-  Geom g;
+  Geom g{};
   g.nx = nx;
   g.ny = ny;
   g.N = num_steps;
@@ -917,13 +924,25 @@ extern "C" stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, d
     return STC_ERR_UNSUPPORTED;
   }
   float* scratch = nullptr;
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
   cudaError_t e = noalloc_powers(&scratch);
+  int* err = scratch ? reinterpret_cast<int*>(scratch + kNoAllocPowersFloats) : nullptr;
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e == cudaSuccess)
     e = launch_taylor_adjoint<float>(g, vel, rho, K, mterm, mu, base, float(alpha), float(beta), out, scratch,
-                                     taylor_kmax, (cudaStream_t)cuda_stream);
+                                     taylor_kmax, err, st);
+  // the error word comes back on the caller's stream (pageable host memory:
+  // no allocation), so the call returns once the sweep has finished
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));
     return STC_ERR_CUDA;
+  }
+  if (herr & DEV_TAYLOR_KMAX) {
+    set_last_error("stc_adjoint_sweep_noalloc: a Taylor order in K lies outside 1..taylor_kmax");
+    return STC_ERR_DIVERGED;
   }
   return STC_OK;
 }
@@ -934,7 +953,7 @@ namespace stc {
   template cudaError_t launch_taylor_forward<T>(const Geom&, const T*, T*, int*, double, int, int*,           \
                                                 cudaStream_t);                                                \
   template cudaError_t launch_taylor_adjoint<T>(const Geom&, const T*, const T*, const int*, const double*, T*, \
-                                                const T*, T, T, T*, T*, int, cudaStream_t, int, T*);           \
+                                                const T*, T, T, T*, T*, int, int*, cudaStream_t, int, T*);     \
   template void launch_metric<T>(const Geom&, const T*, const double*, double, int, double, double*, double*,   \
                                  double*, cudaStream_t);
 STC_ADV_INST(float)

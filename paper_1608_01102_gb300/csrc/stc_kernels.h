@@ -72,10 +72,11 @@ cudaError_t launch_taylor_forward(const Geom& g, const T* vel, T* rho, int* K, d
 // s_end = 1: steps N-1..1 (the AO sweep; v_0 is data).  s_end = 0 also runs step
 // 0: out_0 and, into mu_m1 (C entries, may be null), T_0^T mu_0 - m_0 (the
 // adjoint density of rho_0, for chaining simulation segments); mu_0 stays mu_0.
+// A Taylor order outside 1..kmax sets DEV_TAYLOR_KMAX in *err (may be null).
 template <class T>
 cudaError_t launch_taylor_adjoint(const Geom& g, const T* vel, const T* rho, const int* K, const double* mterm,
                                   T* mu, const T* base, T alpha, T beta, T* out, T* powers, int kmax,
-                                  cudaStream_t st, int s_end = 1, T* mu_m1 = nullptr);
+                                  int* err, cudaStream_t st, int s_end = 1, T* mu_m1 = nullptr);
 // doubles of launch_metric's tmp1 for C cells and the given levels
 size_t metric_tmp1_doubles(size_t C, int levels);
 // m_s = c * sum_l G_l^T G_l (rho_s - rho*_s) (fp64) into mterm slab s.

@@ -62,3 +62,30 @@ def test_noalloc_rejects_scratch_beyond_the_fixed_size():
     with pytest.raises(stc.StcError) as e:
         stc.adjoint_sweep_noalloc(128, 128, 4, 0.25, 65, p, p, p, p, p, None, 1.0, 1.0, p)
     assert "1048576" in str(e.value)
+
+
+def test_noalloc_reports_an_order_above_taylor_kmax():
+    """Orders from a forward sweep run with a larger taylor_kmax than the one
+    passed are reported (STC_ERR_DIVERGED), not silently truncated; the next
+    call with valid orders succeeds (each call clears the error word)."""
+    torch = pytest.importorskip("torch")
+    nx, ny, N, kmax = 16, 16, 3, 8
+    dev = torch.device("cuda")
+    f32 = dict(dtype=torch.float32, device=dev)
+    F = workloads.face_count(nx, ny)
+    vel = torch.zeros((N, F), **f32)
+    rho = torch.ones((N + 1, nx * ny), **f32)
+    mterm = torch.zeros((N + 1, nx * ny), dtype=torch.float64, device=dev)
+    mu = torch.zeros((N, nx * ny), **f32)
+    out = torch.zeros((N, F), **f32)
+    stream = torch.cuda.current_stream().cuda_stream
+    bad = torch.tensor([1, kmax + 1, 1], dtype=torch.int32, device=dev)
+    with pytest.raises(stc.StcError) as e:
+        stc.adjoint_sweep_noalloc(nx, ny, N, 1.0 / N, kmax, vel.data_ptr(), rho.data_ptr(), bad.data_ptr(),
+                                  mterm.data_ptr(), mu.data_ptr(), None, 0.0, 1.0, out.data_ptr(), stream)
+    assert e.value.code == 5 and "taylor_kmax" in str(e.value)
+    good = torch.tensor([1, kmax, 1], dtype=torch.int32, device=dev)
+    stc.adjoint_sweep_noalloc(nx, ny, N, 1.0 / N, kmax, vel.data_ptr(), rho.data_ptr(), good.data_ptr(),
+                              mterm.data_ptr(), mu.data_ptr(), None, 0.0, 1.0, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.all(mu == 0) and torch.all(out[1:] == 0)
