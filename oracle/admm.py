@@ -35,6 +35,14 @@ Readings:
 * NSO target z_i = v*_i - lambda_i / K (scaled ADMM form of Eq. optAdmm).
 * stopping: the relative KKT residual R(v) = ||g(v)|| / ||g(v_start)|| <= tol,
   or Alg. 3's max_i ||rho_i^last - rho_i||_inf < eps_admm.
+* residual balancing of the penalty (``P.k_adapt``, off by default: Alg. 3
+  keeps Table 2's constant K; an extension, not the paper's): after each
+  multiplier update, with the primal residual r_p = ||v - v*|| and the dual
+  residual r_d = K ||v - v_prev|| over steps 1..N-1 (v_prev: v at the
+  previous update), K doubles when r_p > 10 r_d and halves when r_d > 10 r_p,
+  within 2^+-10 of its starting value.  The fixed point of the iteration does
+  not depend on K (Sec. 4: K sets the rate); the target z and the AO centre w
+  use the new K through the unscaled multiplier.
 * Sec. 5's augmented-Lagrangian fallback (``P.al_threshold`` >= 0; default -1
   = the plain Alg. 3): the multiplier update is applied only once the
   objective J(v) of Eq. opt stops decreasing by more than al_threshold * |J|
@@ -46,6 +54,7 @@ import numpy as np
 from . import advection, kkt, projection, stfas
 
 LM_MAX_RATIO = 4.0 ** 6   # largest LM shift relative to its default
+ADAPT_MU, ADAPT_TAU, ADAPT_RANGE = 10.0, 2.0, 1024.0   # residual balancing of K (P.k_adapt)
 
 
 def ao(P, v, lam, iters=None, start=None, trace=None):
@@ -170,6 +179,8 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
     fscale = None
     vstar = None
     lm = dict(gamma=P.lm_shift, gamma0=P.lm_shift, rejected=0)
+    K0 = P.K
+    v_prev = None
     for it in range(max_admm):
         vstar, rhos, _ = ao(P, x["v"], lam, start=vstar)
         z = vstar - lam / P.K
@@ -182,7 +193,7 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
         apply = P.al_threshold < 0 or (J_prev - J) <= P.al_threshold * abs(J_prev)
         hist.append(dict(it=it, kkt_rel=R, f_inf=fres, vcycles=cycles, drho=dr,
                          objective=J, rejected=lm["rejected"], lm_shift=lm["gamma"],
-                         lambda_updates=updates + (1 if apply else 0)))
+                         lambda_updates=updates + (1 if apply else 0), K=P.K))
         J_prev = J
         if callback:
             callback(hist[-1])
@@ -192,5 +203,18 @@ def solve(P, tol=1e-6, max_admm=50, eps_admm=None, eps_stfas=1e-5, max_vcycles=2
         if apply:
             lam[1:N] += P.K * P.beta * (x["v"][1:N] - vstar[1:N])
             updates += 1
+            if P.k_adapt:
+                if v_prev is not None and N > 1:
+                    rp = float(np.linalg.norm(x["v"][1:N] - vstar[1:N]))
+                    rd = P.K * float(np.linalg.norm(x["v"][1:N] - v_prev[1:N]))
+                    hist[-1]["r_primal"], hist[-1]["r_dual"] = rp, rd
+                    Kn = P.K
+                    if rp > ADAPT_MU * rd:
+                        Kn = P.K * ADAPT_TAU
+                    elif rd > ADAPT_MU * rp:
+                        Kn = P.K / ADAPT_TAU
+                    P.K = min(max(Kn, K0 / ADAPT_RANGE), K0 * ADAPT_RANGE)
+                v_prev = x["v"].copy()
     P.lm_shift = lm["gamma0"]
+    P.K = K0
     return x, vstar, lam, hist

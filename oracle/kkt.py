@@ -43,6 +43,7 @@ class Problem:
     lm_shift: float = None           # LM shift of the smoother's v blocks, default 1/dt^2
     nz: int = 0                      # 0: the 2D grid nx x ny; > 0: the 3D grid nx x ny x nz
     periodic: bool = False           # 3D only: every axis wraps (the paper's periodic benchmarks)
+    k_adapt: bool = False            # residual balancing of the ADMM penalty K in solve() (not in the paper)
 
     def __post_init__(self):
         self.h = 1.0 / self.nx
