@@ -124,6 +124,13 @@ typedef struct {
                            one at a time; 3D always one at a time).  The accepted factor
                            is the first that does not raise the objective, exactly as
                            in the one-at-a-time search.  Default 4. */
+  int k_adapt;          /* 0 (default): the ADMM penalty K stays fixed (Alg. 3 with Table 2's
+                           constant K).  1: stc_solve balances it (residual balancing, not in
+                           the paper): after each multiplier update, with r_p = ||v - v*|| and
+                           r_d = K ||v - v_prev|| over steps 1..N-1, K doubles when r_p > 10 r_d
+                           and halves when r_d > 10 r_p, within 2^+-10 of its value at the
+                           start of the solve.  The fixed point does not depend on K; the
+                           adapted K stays in the problem after the solve (report.K_final). */
 } stc_params;
 
 typedef struct {
@@ -144,6 +151,11 @@ typedef struct {
   double objective;     /* J(v) of Eq. opt at exit (misfit + r/2 ||u||^2)        */
   int lambda_updates;   /* multiplier updates applied (fewer than admm_iters under
                            the AL fallback)                                       */
+  double seconds_to_1e2; /* times at which kkt_rel first reached 1e-2, 1e-3, 1e-6 */
+  double seconds_to_1e3; /* (<0: never)                                           */
+  double seconds_to_1e6;
+  double K_final;       /* the ADMM penalty at exit (differs from params.K when it
+                           adapts, stc_params.k_adapt)                            */
 } stc_report;
 
 /* Field identifiers for stc_get_field / stc_set_field (level 0 = finest grid). */
@@ -215,6 +227,14 @@ stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf);
  * density-change test, or after max_admm iterations (then
  * STC_ERR_NOT_CONVERGED, with the state kept).  report may be NULL. */
 stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_report* report);
+
+/* Per-iteration record of the last stc_solve on this problem: for ADMM
+ * iteration k (0-based), out[3k] = kkt_rel after it, out[3k+1] = seconds since
+ * the solve started, out[3k+2] = the penalty K it used.  Writes min(len,
+ * 3 count) values; *count (may be NULL) = iterations recorded (0 before any
+ * solve).  Host data only; no device work.  STC_ERR_INVALID_ARG for a null
+ * problem, or a null out with len > 0. */
+stc_status stc_solve_history(const stc_problem* p, double* out, size_t len, int* count);
 
 /* Results.  len must equal the field size: u N x faces, rho (N+1) x cells,
  * v (N+1) x faces. */
@@ -345,6 +365,15 @@ stc_status stc_kkt_residual(stc_problem* p, double* norm);
  * then rho^last = rho. */
 stc_status stc_admm_update(stc_problem* p, double* drho);
 
+/* Sets the ADMM penalty K (Eq. optAdmm) and the multiplier step beta (Alg. 3)
+ * of an existing problem, for the iterations that follow (K > 0, beta > 0,
+ * else STC_ERR_INVALID_ARG and nothing changes).  The multiplier lambda is kept
+ * unscaled, so the scaled target z = v* - lambda/K and the AO centre
+ * w = v + lambda/K follow the new K; the NSO's K/r of every level changes and
+ * the V-cycle graph is captured again at the next V-cycle.  K changes the path
+ * of the iteration, not its fixed point (Sec. 4).  Synchronises the stream. */
+stc_status stc_set_penalty(stc_problem* p, double K, double beta);
+
 /* ---- instrumentation ------------------------------------------------------ */
 
 /* Number of kernel launches this problem has enqueued since creation (a V-cycle
@@ -353,13 +382,25 @@ stc_status stc_launch_count(const stc_problem* p, long long* launches);
 
 /* enable != 0: the first V-cycle of every stc_vcycle call runs a second
  * V-cycle graph with a CUDA event pair around every finest-level SCGS colour
- * launch (the dominant kernel), recorded on the stream
- * that runs it (the other cycles run the plain graph, so the events perturb
- * one cycle per call); stc_kernel_timing then returns the summed device time
- * (ms) and the number of timed launches since the last enable.  enable = 0
- * drops the timed graph. */
+ * launch and every finest-level colour residual launch (the two largest
+ * kernels), recorded on the stream that runs them (the other cycles run the
+ * plain graph, so the events perturb one cycle per call).
+ * stc_kernel_timing_of(kind) then returns the summed device time (ms) and the
+ * number of timed launches of kind 0 (SCGS colour) or 1 (colour residual)
+ * since the last enable; stc_kernel_timing is kind 0.  Another kind is
+ * STC_ERR_INVALID_ARG.  enable = 0 drops the timed graph. */
 stc_status stc_set_kernel_timing(stc_problem* p, int enable);
 stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* launches);
+stc_status stc_kernel_timing_of(const stc_problem* p, int kind, double* total_ms, long long* launches);
+
+/* FP32 fused multiply-add throughput of the current device, measured: four
+ * timed launches of a kernel that keeps every SM busy with independent FMA
+ * chains (four waves of the resident CTAs), the best of the last three, in
+ * GFLOP/s (2 flops per FMA) into *gflops.  The ALU-side roofline denominator
+ * of the SCGS smoother (its dense block arithmetic, Eq. HESS).  Runs on
+ * cuda_stream (NULL = legacy default stream) and synchronises it;
+ * STC_ERR_INVALID_ARG for a null gflops, STC_ERR_CUDA on a CUDA error. */
+stc_status stc_measure_fp32_peak(void* cuda_stream, double* gflops);
 
 /* Device memory held by the problem, in bytes. */
 stc_status stc_memory_bytes(const stc_problem* p, size_t* bytes);
@@ -394,17 +435,27 @@ stc_status stc_dct_tables(int nx, int ny, double* out, size_t len);
  * C_i (rho_i - rho*_i) (N+1 cell slabs, fp64), mu = output adjoint (N cell
  * slabs), base = N face slabs or NULL, out = output face slabs: slab i =
  * alpha base_i + beta (dA[rho_i, vel_i]/dvel_i)^T mu_i for i = 1..N-1 (slab 0
- * is not written).  Enqueued on cuda_stream (NULL = legacy default stream).
+ * is not written).  Enqueued on cuda_stream (NULL = legacy default stream);
+ * the call then reads the sweep's error word back on that stream and returns
+ * once the sweep has finished: a Taylor order in K outside 1..taylor_kmax
+ * (orders from a forward sweep run with a larger taylor_kmax) returns
+ * STC_ERR_DIVERGED, and mu / out are then not the adjoint.
  *
  * Scratch: the sweep's Taylor powers live in one library-wide device array of
- * 1,048,576 floats (4 MiB) that every GPU loading the library holds until the
- * process exits.  taylor_kmax * nx * ny above that returns STC_ERR_INVALID_ARG
- * with a message.  Every call shares the array and it keeps the last call's
- * contents (nothing needs to start at zero), so calls that overlap on the GPU
- * race: serialise them.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or
- * allocating library routine is called. */
+ * 1,048,576 floats (4 MiB, plus 64 words holding the error word) that every
+ * GPU loading the library holds until the process exits.  taylor_kmax * nx *
+ * ny above that returns STC_ERR_INVALID_ARG with a message.  Every call
+ * shares the array and it keeps the last call's contents (the powers need not
+ * start at zero; each call clears the error word), so calls that overlap on
+ * the GPU race: serialise them.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current and
+ * caches it for the process; that lookup may load the library's device code
+ * (CUDA loads modules lazily), which is when the 4 MiB array is placed on the
+ * device, so make the first call -- or any earlier use of the library on that
+ * device -- before reserving the rest of the device memory in a pool, and
+ * before any stream capture.  The cached address does not survive
+ * cudaDeviceReset: do not use this entry point on a device after resetting
+ * it.  No cudaMalloc, cudaFree or allocating library routine is called. */
 stc_status stc_adjoint_sweep_noalloc(int nx, int ny, int num_steps, double dt, int taylor_kmax,
                                      const float* vel, const float* rho, const int* K, const double* mterm,
                                      float* mu, const float* base, double alpha, double beta, float* out,

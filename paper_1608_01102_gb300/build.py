@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstc.so")
 SOURCES = ["stc_api.cu", "nso_kernels.cu", "advect_kernels.cu", "poisson_kernels.cu", "stc_server.cu",
-           "nso3d_kernels.cu", "advect3d_kernels.cu", "poisson3d_kernels.cu", "sim_kernels.cu"]
+           "nso3d_kernels.cu", "advect3d_kernels.cu", "poisson3d_kernels.cu", "sim_kernels.cu",
+           "peak_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]

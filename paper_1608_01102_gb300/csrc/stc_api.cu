@@ -84,6 +84,7 @@ struct stc_problem {
        *w = nullptr, *y = nullptr, *uk = nullptr, *gk = nullptr, *dens = nullptr, *powers = nullptr,
        *v0 = nullptr;
   void *vcand = nullptr, *rho_c = nullptr;   // AO blend trial: v*, its densities and Taylor orders
+  void* vprev = nullptr;          // k_adapt: v of the previous ADMM iteration
   int *K = nullptr, *Kk = nullptr, *K_c = nullptr;
   // concurrent AO blend trials (2D): trial j's v*, densities, orders, metric
   // terms, metric temporaries, error flags and objective; trial 0 is
@@ -105,6 +106,7 @@ struct stc_problem {
   cudaEvent_t tdone[kMaxTrials] = {};
   bool rho_at_vstar = false;      // rho / K hold the forward sweep of the current v*
   std::vector<int> ao_trace;      // halvings per pass of the last AO
+  std::vector<double> solve_hist; // last stc_solve: per ADMM iteration (kkt_rel, seconds, K)
   double* dguard = nullptr;       // per level {before, after} ||res - f||_2^2 of the guarded correction
   double* dlm = nullptr;          // device copy of the smoother's LM shift gamma (read by every SCGS launch)
   double lm0 = 0.0, lm = 0.0;     // default and current gamma
@@ -139,10 +141,11 @@ struct stc_problem {
   long long graph_launches = 0; // kernel nodes of the V-cycle graph
   long long* counter = nullptr; // where enqueue sites count: &launches, or &graph_launches while capturing
   bool timing = false;
-  std::vector<cudaEvent_t> ev_start, ev_stop;
-  int ev_used = 0;              // event pairs recorded by the current graph
-  double timed_ms = 0.0;
-  long long timed_launches = 0;
+  // kind 0: the finest level's SCGS colour launches, kind 1: its colour residuals
+  std::vector<cudaEvent_t> ev_start[2], ev_stop[2];
+  int ev_used[2] = {};          // event pairs recorded by the current graph
+  double timed_ms[2] = {};
+  long long timed_launches[2] = {};
   size_t bytes = 0;
 };
 
@@ -262,20 +265,23 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < ncol; ++c) {
       // f - res where this colour's cells read it, all from the pre-colour state
+      const bool evr = timed && P->ev_used[1] < (int)P->ev_start[1].size();
+      if (evr) ck(cudaEventRecordWithFlags(P->ev_start[1][P->ev_used[1]], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         launch_nso_residual_colour<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(L.res), st_of<T>(L.tmp), c, st,
                                       s == 0 && c == 0 ? first_only_if_undone : nullptr);
       });
+      if (evr) ck(cudaEventRecordWithFlags(P->ev_stop[1][P->ev_used[1]++], st, cudaEventRecordExternal), "event");
       count(P, 1);
-      const bool ev = timed && P->ev_used < (int)P->ev_start.size();
-      if (ev) ck(cudaEventRecordWithFlags(P->ev_start[P->ev_used], st, cudaEventRecordExternal), "event");
+      const bool ev = timed && P->ev_used[0] < (int)P->ev_start[0].size();
+      if (ev) ck(cudaEventRecordWithFlags(P->ev_start[0][P->ev_used[0]], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
         launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm, P->sc3);
       });
-      if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[P->ev_used++], st, cudaEventRecordExternal), "event");
+      if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[0][P->ev_used[0]++], st, cudaEventRecordExternal), "event");
       count(P, 1);
     }
 }
@@ -426,7 +432,7 @@ double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cyc
   if (!ge) {
     cudaGraph_t graph = nullptr;
     P->graph_launches = 0;
-    if (tg) P->ev_used = 0;
+    if (tg) P->ev_used[0] = P->ev_used[1] = 0;
     P->capture_timed = tg;
     P->counter = &P->graph_launches;
     ck(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed), "begin capture");
@@ -449,12 +455,13 @@ double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cyc
   ck(cudaGraphLaunch(ge, P->st), "graph launch");
   P->launches += P->graph_launches;
   const double f = read_scalar(P, 0, false, nonfinite_rejects);
-  for (int k = 0; tg && k < P->ev_used; ++k) {
-    float ms = 0.f;
-    ck(cudaEventElapsedTime(&ms, P->ev_start[k], P->ev_stop[k]), "event time");
-    P->timed_ms += ms;
-    P->timed_launches += 1;
-  }
+  for (int kind = 0; tg && kind < 2; ++kind)
+    for (int k = 0; k < P->ev_used[kind]; ++k) {
+      float ms = 0.f;
+      ck(cudaEventElapsedTime(&ms, P->ev_start[kind][k], P->ev_stop[kind][k]), "event time");
+      P->timed_ms[kind] += ms;
+      P->timed_launches[kind] += 1;
+    }
   return f;
 }
 
@@ -548,7 +555,8 @@ void adjoint(stc_problem* P, const void* vel, const void* rho, const int* K, con
          "taylor adjoint");
     else
       ck(launch_taylor_adjoint<T>(g, (const T*)vel, (const T*)rho, K, P->mterm, (T*)P->mu, (const T*)base, T(alpha),
-                                  T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, st, s_end, (T*)mu_m1),
+                                  T(beta), (T*)out, (T*)P->powers, P->prm.taylor_kmax, P->derr, st, s_end,
+                                  (T*)mu_m1),
          "taylor adjoint");
   });
   count(P, 1);
@@ -1051,6 +1059,7 @@ bool params_valid(const stc_params& prm) {
       prm.cgc_guard < 0 || prm.cgc_guard > 1 || prm.lm_adapt < 0 || prm.lm_adapt > 1 ||
       prm.al_threshold != prm.al_threshold || prm.time_coarsen < 0 || prm.time_coarsen > 1 || prm.nz < 0 ||
       prm.nz == 1 || prm.boundary < 0 || prm.boundary > 1 || prm.scgs_cta_cells < -1 || prm.ao_trials < 1 || prm.ao_trials > kMaxTrials ||
+      prm.k_adapt < 0 || prm.k_adapt > 1 ||
       (prm.boundary == 1 && (prm.nz == 0 || prm.nx % 2 || prm.ny % 2 || prm.nz % 2)));
 }
 
@@ -1095,7 +1104,8 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   }
   const size_t F = faces(prm.nx, prm.ny, prm.nz), C = cells(prm.nx, prm.ny, prm.nz);
   total += 3 * b((N + 1) * C * ts) + b(N * C * ts) + 2 * b(N * F * ts) + b((N + 1) * C * ts) + b(N * 4) +
-           b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts, N) : 0) + 4 * b(N * F * ts) +
+           b(2 * dims.size() * 8) + b(8) + (prm.lm_adapt ? fieldset(F, C, ts, N) : 0) +
+           (prm.k_adapt ? b((N + 1) * F * ts) : 0) + 4 * b(N * F * ts) +
            2 * b((N + 1) * F * ts) + b((size_t)prm.taylor_kmax * C * ts) + b(F * ts) + 2 * b(N * 4) +
            b((N + 1) * C * 8) + b(C * 8) + b(metric_tmp1_doubles(C, prm.metric_levels) * 8) + b(16 * 8) + b(4);
   if (nkeys > 0) total += b((size_t)nkeys * C * 8);
@@ -1121,8 +1131,10 @@ void free_problem(stc_problem* P) {
   if (!P) return;
   if (P->vgraph) cudaGraphExecDestroy(P->vgraph);
   if (P->vgraph_t) cudaGraphExecDestroy(P->vgraph_t);
-  for (cudaEvent_t e : P->ev_start) cudaEventDestroy(e);
-  for (cudaEvent_t e : P->ev_stop) cudaEventDestroy(e);
+  for (int kind = 0; kind < 2; ++kind) {
+    for (cudaEvent_t e : P->ev_start[kind]) cudaEventDestroy(e);
+    for (cudaEvent_t e : P->ev_stop[kind]) cudaEventDestroy(e);
+  }
   for (void* p : P->allocs) cudaFree(p);
   if (P->hscal) cudaFreeHost(P->hscal);
   if (P->herr) cudaFreeHost(P->herr);
@@ -1144,6 +1156,57 @@ void free_problem(stc_problem* P) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// the ADMM penalty of every level and the multiplier step; the V-cycle graphs
+// carry K/r in their kernel arguments and are captured again at the next cycle
+void set_penalty_impl(stc_problem* p, double K, double beta) {
+  ck(cudaStreamSynchronize(p->st), "sync");
+  p->prm.K = K;
+  p->prm.beta = beta;
+  for (Level& L : p->lv) {
+    L.g.a = K / p->prm.r;
+    set_fp32_copies(L.g);
+  }
+  for (cudaGraphExec_t* ge : {&p->vgraph, &p->vgraph_t})
+    if (*ge) {
+      ck(cudaGraphExecDestroy(*ge), "graph destroy");
+      *ge = nullptr;
+    }
+}
+
+// Residual balancing of the ADMM penalty (stc_params.k_adapt; the paper keeps
+// K fixed): with the primal residual r_p = ||v - v*|| and the dual residual
+// r_d = K ||v - v_prev|| over steps 1..N-1 (v_prev: the previous iteration's
+// v), K doubles when r_p > 10 r_d and halves when r_d > 10 r_p, within 2^+-10
+// of its value at the start of the solve.  first: only v_prev is recorded.
+constexpr double kAdaptMu = 10.0, kAdaptTau = 2.0, kAdaptRange = 1024.0;
+
+void adapt_penalty(stc_problem* P, bool first, double K0) {
+  const Geom& g = P->lv[0].g;
+  const size_t fb = (size_t)(g.N + 1) * g.F * P->ts;
+  if (!first && g.N > 1) {
+    ck(cudaMemsetAsync(P->dscal + 10, 0, 2 * sizeof(double), P->st), "memset");
+    dispatch(P->dbl, [&](auto tag) {
+      using T = decltype(tag);
+      const size_t n = (size_t)(g.N - 1) * g.F;
+      launch_diff_sumsq<T>((const T*)P->lv[0].x.v + g.F, (const T*)P->vstar + g.F, n, 1.0, P->dscal + 10, P->st,
+                           P->red);
+      launch_diff_sumsq<T>((const T*)P->lv[0].x.v + g.F, (const T*)P->vprev + g.F, n, 1.0, P->dscal + 11, P->st,
+                           P->red);
+    });
+    count(P, 2);
+    ck(cudaMemcpyAsync(P->hscal + 10, P->dscal + 10, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->st), "d2h");
+    ck(cudaStreamSynchronize(P->st), "sync");
+    const double K = P->prm.K;
+    const double rp = std::sqrt(P->hscal[10]), rd = K * std::sqrt(P->hscal[11]);
+    double Kn = K;
+    if (rp > kAdaptMu * rd) Kn = K * kAdaptTau;
+    else if (rd > kAdaptMu * rp) Kn = K / kAdaptTau;
+    Kn = std::min(std::max(Kn, K0 / kAdaptRange), K0 * kAdaptRange);
+    if (Kn != K) set_penalty_impl(P, Kn, P->prm.beta);
+  }
+  ck(cudaMemcpyAsync(P->vprev, P->lv[0].x.v, fb, cudaMemcpyDeviceToDevice, P->st), "copy");
+}
+
 extern "C" {
 
 void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
@@ -1182,6 +1245,7 @@ void stc_default_params(stc_params* p, int nx, int ny, int num_steps) {
   p->boundary = 0;
   p->scgs_cta_cells = -1;
   p->ao_trials = 4;
+  p->k_adapt = 0;
 }
 
 const char* stc_last_error(void) { return g_last_error.c_str(); }
@@ -1271,6 +1335,7 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
     P->dguard = (double*)dalloc(P, 2 * P->lv.size() * sizeof(double));
     P->dlm = (double*)dalloc(P, sizeof(double));
     if (prm.lm_adapt) alloc_fieldset(P, P->xb, g0, P->dbl);
+    if (prm.k_adapt) P->vprev = dalloc(P, (N + 1) * F * ts);
     P->lam = dalloc(P, N * F * ts);
     P->w = dalloc(P, N * F * ts);
     P->y = dalloc(P, N * F * ts);
@@ -1476,11 +1541,16 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
   stc_report rep;
   std::memset(&rep, 0, sizeof(rep));
   rep.seconds_to_1e4 = -1.0;
+  rep.seconds_to_1e2 = rep.seconds_to_1e3 = rep.seconds_to_1e6 = -1.0;
   rep.seconds_to_density_stop = -1.0;
+  rep.K_final = p->prm.K;
   bool converged = false;
   stc_status s = guarded(p, [&]() {
     auto t0 = std::chrono::steady_clock::now();
     const stc_params& prm = p->prm;
+    const double K0 = prm.K;
+    bool have_prev = false;   // k_adapt: v_prev holds a previous iteration's v
+    p->solve_hist.clear();
     reset_state(p);
     const Geom& g = p->lv[0].g;
     const double eps_admm = prm.eps_admm < 0 ? p->rho_scale / 100.0 : prm.eps_admm;
@@ -1515,6 +1585,11 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       J_prev = J;
       admm_update(p, p->st, update);   // drho test + lambda update (lambda unused if we stop)
       const double drho = read_scalar(p, 2);
+      const double K_used = prm.K;
+      if (prm.k_adapt && update) {
+        adapt_penalty(p, !have_prev, K0);
+        have_prev = true;
+      }
       rep.objective = J;
       if (update) ++rep.lambda_updates;
       rep.admm_iters = it + 1;
@@ -1526,7 +1601,12 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
       rep.f_inf = f;
       rep.drho = drho;
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      p->solve_hist.insert(p->solve_hist.end(), {rep.kkt_rel, el, K_used});
+      if (rep.kkt_rel <= 1e-2 && rep.seconds_to_1e2 < 0) rep.seconds_to_1e2 = el;
+      if (rep.kkt_rel <= 1e-3 && rep.seconds_to_1e3 < 0) rep.seconds_to_1e3 = el;
       if (rep.kkt_rel <= 1e-4 && rep.seconds_to_1e4 < 0) rep.seconds_to_1e4 = el;
+      if (rep.kkt_rel <= 1e-6 && rep.seconds_to_1e6 < 0) rep.seconds_to_1e6 = el;
+      rep.K_final = K_used;
       if (drho < p->rho_scale / 100.0 && rep.density_stop_iter == 0) {
         rep.density_stop_iter = it + 1;
         rep.seconds_to_density_stop = el;
@@ -1545,6 +1625,17 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
     g_last_error = "ADMM iteration cap reached";
     return STC_ERR_NOT_CONVERGED;
   }
+  return STC_OK;
+}
+
+stc_status stc_solve_history(const stc_problem* p, double* out, size_t len, int* count) {
+  if (!p || (!out && len > 0)) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  const size_t n = p->solve_hist.size() / 3;
+  for (size_t k = 0; k < 3 * n && k < len; ++k) out[k] = p->solve_hist[k];
+  if (count) *count = (int)n;
   return STC_OK;
 }
 
@@ -1906,6 +1997,14 @@ stc_status stc_admm_update(stc_problem* p, double* drho) {
   });
 }
 
+stc_status stc_set_penalty(stc_problem* p, double K, double beta) {
+  if (!p || !(K > 0) || !(beta > 0) || !std::isfinite(K) || !std::isfinite(beta)) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() { set_penalty_impl(p, K, beta); });
+}
+
 stc_status stc_launch_count(const stc_problem* p, long long* launches) {
   if (!p || !launches) {
     g_last_error = "null argument";
@@ -1927,26 +2026,34 @@ stc_status stc_set_kernel_timing(stc_problem* p, int enable) {
         *ge = nullptr;
       }
     p->timing = enable != 0;
-    p->timed_ms = 0.0;
-    p->timed_launches = 0;
-    const size_t need = p->lv.size() > 1 ? (size_t)4 * (p->prm.pre + p->prm.post) : (size_t)4 * p->prm.coarse_sweeps;
-    while (p->timing && p->ev_start.size() < need) {
-      cudaEvent_t a, b;
-      ck(cudaEventCreate(&a), "event");
-      ck(cudaEventCreate(&b), "event");
-      p->ev_start.push_back(a);
-      p->ev_stop.push_back(b);
+    // one event pair per finest-level colour launch of a cycle (the finest
+    // level is smoothed with events only when it is not the coarsest)
+    const size_t need = p->lv.size() > 1 ? (size_t)(1 << p->lv[0].g.dim) * (p->prm.pre + p->prm.post) : 0;
+    for (int kind = 0; kind < 2; ++kind) {
+      p->timed_ms[kind] = 0.0;
+      p->timed_launches[kind] = 0;
+      while (p->timing && p->ev_start[kind].size() < need) {
+        cudaEvent_t a, b;
+        ck(cudaEventCreate(&a), "event");
+        ck(cudaEventCreate(&b), "event");
+        p->ev_start[kind].push_back(a);
+        p->ev_stop[kind].push_back(b);
+      }
     }
   });
 }
 
 stc_status stc_kernel_timing(const stc_problem* p, double* total_ms, long long* launches) {
-  if (!p) {
-    g_last_error = "null argument";
+  return stc_kernel_timing_of(p, 0, total_ms, launches);
+}
+
+stc_status stc_kernel_timing_of(const stc_problem* p, int kind, double* total_ms, long long* launches) {
+  if (!p || kind < 0 || kind > 1) {
+    g_last_error = "invalid argument";
     return STC_ERR_INVALID_ARG;
   }
-  if (total_ms) *total_ms = p->timed_ms;
-  if (launches) *launches = p->timed_launches;
+  if (total_ms) *total_ms = p->timed_ms[kind];
+  if (launches) *launches = p->timed_launches[kind];
   return STC_OK;
 }
 

@@ -35,7 +35,7 @@ class StcParams(ctypes.Structure):
                 ("poisson_vcycles", c_int), ("self_advection", c_int), ("ao_halvings", c_int),
                 ("cgc_guard", c_int), ("lm_adapt", c_int), ("al_threshold", c_double), ("time_coarsen", c_int),
                 ("nz", c_int), ("boundary", c_int), ("scgs_cta_cells", c_int),
-                ("ao_trials", c_int)]
+                ("ao_trials", c_int), ("k_adapt", c_int)]
 
 
 class StcReport(ctypes.Structure):
@@ -43,7 +43,8 @@ class StcReport(ctypes.Structure):
                 ("f_inf", c_double), ("drho", c_double), ("seconds", c_double),
                 ("seconds_to_1e4", c_double), ("rejected_vcycles", c_int), ("lm_shift", c_double),
                 ("density_stop_iter", c_int), ("seconds_to_density_stop", c_double), ("objective", c_double),
-                ("lambda_updates", c_int)]
+                ("lambda_updates", c_int), ("seconds_to_1e2", c_double), ("seconds_to_1e3", c_double),
+                ("seconds_to_1e6", c_double), ("K_final", c_double)]
 
 
 class ServerParams(ctypes.Structure):
@@ -121,9 +122,13 @@ SIGNATURES = {
     "stc_prolong_correct": (c_int, [c_void_p, c_int]),
     "stc_kkt_residual": (c_int, [c_void_p, P_double]),
     "stc_admm_update": (c_int, [c_void_p, P_double]),
+    "stc_set_penalty": (c_int, [c_void_p, c_double, c_double]),
+    "stc_solve_history": (c_int, [c_void_p, P_double, c_size_t, P_int]),
     "stc_launch_count": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "stc_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "stc_kernel_timing": (c_int, [c_void_p, P_double, ctypes.POINTER(ctypes.c_longlong)]),
+    "stc_kernel_timing_of": (c_int, [c_void_p, c_int, P_double, ctypes.POINTER(ctypes.c_longlong)]),
+    "stc_measure_fp32_peak": (c_int, [c_void_p, P_double]),
     "stc_memory_bytes": (c_int, [c_void_p, ctypes.POINTER(c_size_t)]),
     "stc_adjoint_sweep_noalloc": (c_int, [c_int, c_int, c_int, c_double, c_int, c_void_p, c_void_p, c_void_p,
                                           c_void_p, c_void_p, c_void_p, c_double, c_double, c_void_p,
@@ -279,6 +284,15 @@ class Problem:
             _check(code)
         return {k: getattr(rep, k) for k, _ in StcReport._fields_}
 
+    def solve_history(self):
+        """[(kkt_rel, seconds, K)] per ADMM iteration of the last solve."""
+        n = c_int()
+        _check(self.lib.stc_solve_history(self.h, None, 0, ctypes.byref(n)))
+        buf = np.zeros(3 * n.value)
+        if n.value:
+            _check(self.lib.stc_solve_history(self.h, _dptr(buf), buf.size, ctypes.byref(n)))
+        return [tuple(buf[3 * k:3 * k + 3]) for k in range(n.value)]
+
     def advect(self, source="VSTAR"):
         _check(self.lib.stc_advect(self.h, FIELDS[source]))
 
@@ -343,6 +357,9 @@ class Problem:
         _check(self.lib.stc_admm_update(self.h, ctypes.byref(f)))
         return f.value
 
+    def set_penalty(self, K, beta=1.0):
+        _check(self.lib.stc_set_penalty(self.h, K, beta))
+
     def forces(self):
         return self.get("U")
 
@@ -372,9 +389,11 @@ class Problem:
     def set_kernel_timing(self, on=True):
         _check(self.lib.stc_set_kernel_timing(self.h, 1 if on else 0))
 
-    def kernel_timing(self):
+    def kernel_timing(self, kind=0):
+        """(summed ms, launches) of the timed finest-level launches: kind 0 =
+        SCGS colour, 1 = colour residual."""
         ms, n = c_double(), ctypes.c_longlong()
-        _check(self.lib.stc_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        _check(self.lib.stc_kernel_timing_of(self.h, kind, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
     def taylor_kmax(self):
@@ -415,6 +434,13 @@ def adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vel, rho, K, mterm, mu, ba
     vp = lambda p: c_void_p(int(p)) if p else None
     _check(lib.stc_adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vp(vel), vp(rho), vp(K), vp(mterm), vp(mu),
                                          vp(base), alpha, beta, vp(out), vp(stream)))
+
+
+def measure_fp32_peak(stream=None):
+    """stc_measure_fp32_peak: the device's FP32 FMA throughput in GFLOP/s."""
+    g = c_double()
+    _check(load().stc_measure_fp32_peak(c_void_p(int(stream)) if stream else None, ctypes.byref(g)))
+    return g.value
 
 
 def problem_bytes(params, nkeys=1):
