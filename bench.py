@@ -474,7 +474,8 @@ def seconds_to(hist, R):
     return None
 
 
-def serve_leg(stc, workloads, count, max_admm, fp64_count, budget=64 << 30, workers=8, ao_trials=1):
+def serve_leg(stc, workloads, count, max_admm, fp64_count, budget=64 << 30, workers=8, ao_trials=1, mode=1,
+              max_resident=16):
     """Replay the first `count` requests of the seeded stream in real time
     (fp32); then solve the first `fp64_count` of them one after another with
     the plain fp64 per-problem solve, the baseline of the serving form.  The
@@ -488,16 +489,36 @@ def serve_leg(stc, workloads, count, max_admm, fp64_count, budget=64 << 30, work
                                   metric_levels=max(0, int(np.floor(np.log2(n / 2)))), ao_trials=ao_trials,
                                   k_adapt=1)
 
-    with stc.Server(budget, workers=workers) as S:
-        t0 = time.perf_counter()
-        tickets = []
-        for r in reqs:
-            delay = r["arrival"] - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(S.submit(params(r, 0), r["rho0"], r["keyframes"], tol=1e-4, max_admm=max_admm))
-        infos = [S.wait(t) for t in tickets]
-        peak = S.stats()["peak_bytes"]
+    if mode == 1:
+        # stepped serving: this thread submits arrivals and drives the batched steps
+        import torch
+        stream = torch.cuda.Stream()
+        with stc.Server(budget, mode=1, stream=stream.cuda_stream, max_resident=max_resident) as S:
+            t0 = time.perf_counter()
+            tickets, nxt, active, steps = [], 0, 0, 0
+            while nxt < len(reqs) or active > 0:
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+                    r = reqs[nxt]
+                    tickets.append(S.submit(params(r, 0), r["rho0"], r["keyframes"], tol=1e-4, max_admm=max_admm))
+                    nxt += 1
+                active = S.step()
+                steps += 1
+                if active == 0 and nxt < len(reqs):
+                    time.sleep(max(0.0, reqs[nxt]["arrival"] - (time.perf_counter() - t0)))
+            infos = [S.poll(t) for t in tickets]
+            peak = S.stats()["peak_bytes"]
+    else:
+        with stc.Server(budget, workers=workers) as S:
+            t0 = time.perf_counter()
+            tickets = []
+            for r in reqs:
+                delay = r["arrival"] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(S.submit(params(r, 0), r["rho0"], r["keyframes"], tol=1e-4, max_admm=max_admm))
+            infos = [S.wait(t) for t in tickets]
+            peak = S.stats()["peak_bytes"]
     lat = [i["t_done"] - i["t_submit"] for i in infos if i["state"] == "done"]
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
     kk = [i["report"]["kkt_rel"] for i in infos if i["state"] == "done"]
@@ -507,7 +528,11 @@ def serve_leg(stc, workloads, count, max_admm, fp64_count, budget=64 << 30, work
            "problems_per_hour": 3600.0 * len(lat) / span if span > 0 else None,
            "reached_kkt_1e-4": sum(k <= 1e-4 for k in kk), "kkt_rel_median": float(np.median(kk)) if kk else None,
            "admm_iters_median": float(np.median([i["report"]["admm_iters"] for i in infos])),
-           "budget_bytes": budget, "peak_bytes": peak, "workers": workers, "max_admm": max_admm,
+           "budget_bytes": budget, "peak_bytes": peak, "max_admm": max_admm,
+           "mode": ("stepped: each stc_server_step runs the next NSO V-cycle of every resident problem as one "
+                    "batched CUDA graph launch, admission and retirement between steps, max %d resident"
+                    % max_resident) if mode == 1 else
+                   "worker threads: %d concurrent stc_solve calls, one stream each" % workers,
            "stream": "workloads.config_serving(seed 4004): Poisson 4/s, n in {32,48,64,96,128}, N in [16,48], "
                      "1-3 disc/bar keyframes, fp32 policy, stop at KKT 1e-4 or Alg. 3's density test"}
     if fp64_count > 0:
@@ -601,7 +626,8 @@ def run_native(args, rank, world, local_rank):
         legs["3d_fp32"], _ = solve_leg(stc, workloads, "3d", 0, 1e-4, args.solve3d_max_admm, k_adapt=1)
         line["time_to_solution"] = legs
     if solo and args.serve > 0:
-        line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, args.serve_fp64)
+        line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, args.serve_fp64, mode=1)
+        line["served_threads"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, 0, mode=0)
     print(json.dumps(line), flush=True)
 
 

@@ -228,6 +228,43 @@ stc_status stc_vcycle(stc_problem* p, int ncycles, double* nso_res_inf);
  * STC_ERR_NOT_CONVERGED, with the state kept).  report may be NULL. */
 stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_report* report);
 
+/* ---- the ADMM loop as resumable phases, and batched NSO V-cycles ---------- */
+
+/* stc_solve (Alg. 3) split into the phases a serving loop interleaves across
+ * problems.  stc_solve_begin resets the state and evaluates the KKT
+ * denominator at v = 0 (as stc_solve does).  Then, per ADMM iteration:
+ * phase 0 -- stc_solve_head runs Alg. 1 and starts the NSO solve; phase 1 --
+ * NSO V-cycles under the LM safeguard of Sec. 5 (stc_batch_nso_cycle; one per
+ * call) while *wants_cycle of stc_solve_phase is 1, i.e. until ||f||_inf <=
+ * eps_stfas times the first NSO's norm, max_vcycles, or a cycle undone at the
+ * largest shift (at least one cycle per iteration); then stc_solve_tail
+ * (KKT metric, multiplier update, penalty balancing, stopping tests) leads to
+ * phase 0 again or to phase 2 (finished).  stc_solve_report gives the report
+ * so far and whether a stopping test held.  A phase call out of turn returns
+ * STC_ERR_INVALID_ARG.  Running the phases in this order is stc_solve. */
+stc_status stc_solve_begin(stc_problem* p, double kkt_rel_tol, int max_admm);
+stc_status stc_solve_phase(const stc_problem* p, int* phase, int* wants_cycle);
+stc_status stc_solve_head(stc_problem* p);
+stc_status stc_solve_tail(stc_problem* p);
+stc_status stc_solve_report(const stc_problem* p, stc_report* report, int* converged);
+
+/* A batch runs the NSO V-cycles of many problems as ONE CUDA graph launch on
+ * its stream: each problem's captured V-cycle graph (Alg. 2) is a child node,
+ * the children independent, so their kernels overlap on the device.  The
+ * instantiated batch graph is kept and reused while the set of problems (and
+ * their captured graphs) stays the same.  stc_batch_nso_cycle: every problem
+ * of probs[0..n) whose solve is in phase 1 and wants a cycle gets one V-cycle
+ * in the launch; afterwards each reads its ||f||_inf and takes the LM
+ * decision (Sec. 5).  *cycled (may be NULL) = problems cycled; status (n
+ * entries, may be NULL) receives each problem's outcome (a failing problem
+ * does not stop the others).  The problems' streams are synchronised before
+ * the launch and the batch stream after it.  All problems must live on the
+ * current device. */
+typedef struct stc_batch stc_batch;
+stc_status stc_batch_create(void* cuda_stream, stc_batch** out);
+stc_status stc_batch_nso_cycle(stc_batch* b, stc_problem* const* probs, int n, int* cycled, stc_status* status);
+stc_status stc_batch_destroy(stc_batch* b);
+
 /* Per-iteration record of the last stc_solve on this problem: for ADMM
  * iteration k (0-based), out[3k] = kkt_rel after it, out[3k+1] = seconds since
  * the solve started, out[3k+2] = the penalty K it used.  Writes min(len,

@@ -14,8 +14,21 @@
  * device bytes of the problem), the analogue for this library of the memory
  * bound M ~ 8 n^d (1 + d) N of Sec. 5.
  *
- * Threading: every stc_server_* call is safe from any host thread.  Results
- * are copied to host memory owned by the server until stc_server_release.
+ * Two modes.  Mode 0 (worker threads): each admitted problem runs stc_solve
+ * on its own stream and the launches of all resident problems interleave.
+ * Mode 1 (stepped): no threads; each stc_server_step admits what fits, runs
+ * the AO head of every problem whose ADMM iteration begins, then ONE batched
+ * CUDA graph launch holding the next NSO V-cycle of every resident problem
+ * (stc_batch_nso_cycle: the problems' captured V-cycle graphs as concurrent
+ * child nodes; the instantiated graph is reused while the resident set stays
+ * the same), then the KKT/update tail of problems whose NSO solve ended, and
+ * retires finished problems, returning their memory at once -- continuous
+ * batching at V-cycle granularity.  All stepped work runs on one stream
+ * (stc_server_params.stream).
+ *
+ * Threading: every stc_server_* call is safe from any host thread (stepped
+ * steps are serialised).  Results are copied to host memory owned by the
+ * server until stc_server_release.
  *
  * Errors: as in stc.h; stc_last_error() describes the last failing call of
  * the calling thread.  A request whose solve fails ends in state
@@ -41,6 +54,13 @@ typedef struct {
                           for testing the scheduler without a GPU)                      */
   int device;          /* CUDA device of the GPU backend                                */
   int max_bypass;      /* times a queued request may be passed over by later ones (8)  */
+  int mode;            /* 0 (default): worker threads; 1: stepped (stc_server_step)    */
+  void* stream;        /* mode 1: CUDA stream of every problem and of the batched
+                          launches (NULL = legacy default stream)                     */
+  int max_resident;    /* mode 1: problems solving at once (16)                         */
+  double kkt_rel_tol;  /* mode 1: stopping tolerance of problems submitted with
+                          stc_server_submit_problem (1e-4)                            */
+  int max_admm;        /* mode 1: their ADMM iteration cap (50)                         */
 } stc_server_params;
 
 typedef struct {
@@ -84,9 +104,22 @@ stc_status stc_server_create(const stc_server_params* sp, stc_server** out);
 /* Queues a request.  STC_ERR_INVALID_ARG for malformed requests and
  * STC_ERR_OOM when the request alone exceeds the budget (never admissible). */
 stc_status stc_server_submit(stc_server* s, const stc_request* rq, long long* ticket);
+/* Mode 1: queues a problem the caller created (on the server's stream, with
+ * its keyframes set), solved with the server's kkt_rel_tol and max_admm.  Its
+ * admission size is stc_memory_bytes(problem) (already allocated: the budget
+ * bounds how many problems solve at once).  The server does not destroy it;
+ * the caller must not use it until the ticket is finished.  STC_ERR_INVALID_ARG
+ * in mode 0, STC_ERR_OOM when it alone exceeds the budget. */
+stc_status stc_server_submit_problem(stc_server* s, stc_problem* problem, long long* ticket);
+/* Mode 1: one serving step (see above); *active (may be NULL) = problems
+ * resident or queued after it.  Failures of single problems end their
+ * tickets (FAILED) and the step carries on.  STC_ERR_INVALID_ARG in mode 0. */
+stc_status stc_server_step(stc_server* s, int* active);
 stc_status stc_server_poll(stc_server* s, long long ticket, stc_ticket_info* info);
 /* Blocks until the ticket is DONE, FAILED or CANCELLED, or timeout_s elapses
- * (timeout_s < 0: no limit); info receives the state either way. */
+ * (timeout_s < 0: no limit); info receives the state either way.  In mode 1
+ * the waiting thread runs stc_server_step itself until then (or until no
+ * problem is left). */
 stc_status stc_server_wait(stc_server* s, long long ticket, double timeout_s, stc_ticket_info* info);
 /* Cancels a queued request; a running one is not interrupted (STC_ERR_BUSY). */
 stc_status stc_server_cancel(stc_server* s, long long ticket);

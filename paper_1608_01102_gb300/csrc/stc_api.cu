@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <limits>
@@ -72,6 +73,21 @@ void stc::set_last_error(const char* msg) { g_last_error = msg; }
 
 constexpr int kMaxTrials = 8;   // most AO blend factors tried at once
 
+// The ADMM loop of one stc_solve (Alg. 3) as resumable phases, so that a
+// serving step can run the V-cycles of many problems in one graph launch.
+struct SolveRun {
+  int phase = 2;                  // 0: an iteration begins (AO due); 1: NSO V-cycles due; 2: finished
+  double tol = 1e-4;
+  int max_admm = 0;
+  std::chrono::steady_clock::time_point t0;
+  double K0 = 0.0, g0 = 0.0, J_prev = 0.0, eps_admm = 0.0, f = 0.0;
+  bool have_prev = false;         // k_adapt: v_prev holds a previous iteration's v
+  bool give_up = false;           // the NSO solve ends (a cycle undone at the largest LM shift)
+  bool converged = false;
+  int it = 0, cycles = 0;
+  stc_report rep{};
+};
+
 struct stc_problem {
   stc_params prm;
   cudaStream_t st = nullptr;      // user stream (may be the legacy default)
@@ -107,6 +123,9 @@ struct stc_problem {
   bool rho_at_vstar = false;      // rho / K hold the forward sweep of the current v*
   std::vector<int> ao_trace;      // halvings per pass of the last AO
   std::vector<double> solve_hist; // last stc_solve: per ADMM iteration (kkt_rel, seconds, K)
+  SolveRun run;                   // the solve in progress (or the last one)
+  cudaGraph_t vgraph_src = nullptr;   // the captured plain V-cycle (child node of batched launches)
+  long long vgraph_version = 0;   // bumped at every capture of vgraph
   double* dguard = nullptr;       // per level {before, after} ||res - f||_2^2 of the guarded correction
   double* dlm = nullptr;          // device copy of the smoother's LM shift gamma (read by every SCGS launch)
   double lm0 = 0.0, lm = 0.0;     // default and current gamma
@@ -426,8 +445,9 @@ double read_scalar(stc_problem* P, int slot, bool kmax_rejects = false, bool non
 
 // (timed_cycle: with kernel timing on, this cycle runs the graph with events;
 // the others run the plain one, so the events perturb one cycle per call)
-double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cycle = false) {
-  const bool tg = P->timing && timed_cycle;
+// captures the V-cycle graph (timed: with the event pairs) if it is not there;
+// the plain graph's source is kept for batched launches (a child node)
+void ensure_vgraph(stc_problem* P, bool tg) {
   cudaGraphExec_t& ge = tg ? P->vgraph_t : P->vgraph;
   if (!ge) {
     cudaGraph_t graph = nullptr;
@@ -449,9 +469,21 @@ double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cyc
     P->capture_timed = false;
     ck(cudaStreamEndCapture(P->cap, &graph), "end capture");
     cudaError_t e = cudaGraphInstantiate(&ge, graph, 0);
-    cudaGraphDestroy(graph);
+    if (!tg && e == cudaSuccess) {
+      if (P->vgraph_src) cudaGraphDestroy(P->vgraph_src);
+      P->vgraph_src = graph;
+      ++P->vgraph_version;
+    } else {
+      cudaGraphDestroy(graph);
+    }
     ck(e, "graph instantiate");
   }
+}
+
+double run_vcycle(stc_problem* P, bool nonfinite_rejects = false, bool timed_cycle = false) {
+  const bool tg = P->timing && timed_cycle;
+  ensure_vgraph(P, tg);
+  cudaGraphExec_t& ge = tg ? P->vgraph_t : P->vgraph;
   ck(cudaGraphLaunch(ge, P->st), "graph launch");
   P->launches += P->graph_launches;
   const double f = read_scalar(P, 0, false, nonfinite_rejects);
@@ -483,16 +515,26 @@ constexpr double kLmMaxRatio = 4096.0;   // largest LM shift relative to its def
 
 // *give_up is set when a cycle was undone at the largest shift: the NSO solve
 // ends there (unbounded growth left every later cycle undone).
-double nso_cycle(stc_problem* P, double f_old, bool* give_up) {
+// after one V-cycle that left ||f||_inf = f_new: the LM safeguard's decision
+// (Sec. 5) -- a cycle that raised the norm is undone and the shift quadrupled
+void lm_decide(stc_problem* P, double f_old, double f_new, double* f, bool* give_up) {
   *give_up = false;
-  if (!P->prm.lm_adapt) return run_vcycle(P);
-  const double f = run_vcycle(P, true);
-  if (f <= f_old) return f;
+  if (!P->prm.lm_adapt || f_new <= f_old) {
+    *f = f_new;
+    return;
+  }
   copy_state(P, P->xb, P->lv[0].x, P->st);
   ++P->rejected;
   if (P->lm >= kLmMaxRatio * P->lm0) *give_up = true;
   else set_lm(P, std::min(4.0 * P->lm, kLmMaxRatio * P->lm0));
-  return f_old;
+  *f = f_old;
+}
+
+double nso_cycle(stc_problem* P, double f_old, bool* give_up) {
+  const double f_new = run_vcycle(P, P->prm.lm_adapt != 0);
+  double f = f_old;
+  lm_decide(P, f_old, f_new, &f, give_up);
+  return f;
 }
 
 // start of an NSO solve: the LM shift halves back toward its default
@@ -1131,6 +1173,7 @@ void free_problem(stc_problem* P) {
   if (!P) return;
   if (P->vgraph) cudaGraphExecDestroy(P->vgraph);
   if (P->vgraph_t) cudaGraphExecDestroy(P->vgraph_t);
+  if (P->vgraph_src) cudaGraphDestroy(P->vgraph_src);
   for (int kind = 0; kind < 2; ++kind) {
     for (cudaEvent_t e : P->ev_start[kind]) cudaEventDestroy(e);
     for (cudaEvent_t e : P->ev_stop[kind]) cudaEventDestroy(e);
@@ -1156,6 +1199,19 @@ void free_problem(stc_problem* P) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// the V-cycle graphs (captured again at the next cycle)
+void drop_vgraphs(stc_problem* p) {
+  for (cudaGraphExec_t* ge : {&p->vgraph, &p->vgraph_t})
+    if (*ge) {
+      ck(cudaGraphExecDestroy(*ge), "graph destroy");
+      *ge = nullptr;
+    }
+  if (p->vgraph_src) {
+    cudaGraphDestroy(p->vgraph_src);
+    p->vgraph_src = nullptr;
+  }
+}
+
 // the ADMM penalty of every level and the multiplier step; the V-cycle graphs
 // carry K/r in their kernel arguments and are captured again at the next cycle
 void set_penalty_impl(stc_problem* p, double K, double beta) {
@@ -1166,11 +1222,7 @@ void set_penalty_impl(stc_problem* p, double K, double beta) {
     L.g.a = K / p->prm.r;
     set_fp32_copies(L.g);
   }
-  for (cudaGraphExec_t* ge : {&p->vgraph, &p->vgraph_t})
-    if (*ge) {
-      ck(cudaGraphExecDestroy(*ge), "graph destroy");
-      *ge = nullptr;
-    }
+  drop_vgraphs(p);
 }
 
 // Residual balancing of the ADMM penalty (stc_params.k_adapt; the paper keeps
@@ -1205,6 +1257,118 @@ void adapt_penalty(stc_problem* P, bool first, double K0) {
     if (Kn != K) set_penalty_impl(P, Kn, P->prm.beta);
   }
   ck(cudaMemcpyAsync(P->vprev, P->lv[0].x.v, fb, cudaMemcpyDeviceToDevice, P->st), "copy");
+}
+
+// ---------------------------------------------------------------------------
+// stc_solve as resumable phases (Alg. 3): begin; then per ADMM iteration the
+// head (Alg. 1 and the NSO residual), NSO V-cycles until the tolerance (one per
+// call of solve_cycle_done after a V-cycle ran), and the tail (KKT metric,
+// multiplier update, stopping tests).  stc_solve runs them in a loop; a
+// serving step runs the V-cycles of many problems in one graph launch.
+// ---------------------------------------------------------------------------
+void solve_begin(stc_problem* p, double tol, int max_admm) {
+  SolveRun& S = p->run;
+  S = SolveRun{};
+  std::memset(&S.rep, 0, sizeof(S.rep));
+  S.rep.seconds_to_1e4 = -1.0;
+  S.rep.seconds_to_1e2 = S.rep.seconds_to_1e3 = S.rep.seconds_to_1e6 = -1.0;
+  S.rep.seconds_to_density_stop = -1.0;
+  S.rep.K_final = p->prm.K;
+  S.tol = tol;
+  S.max_admm = max_admm;
+  S.t0 = std::chrono::steady_clock::now();
+  S.K0 = p->prm.K;
+  p->solve_hist.clear();
+  reset_state(p);
+  const Geom& g = p->lv[0].g;
+  S.eps_admm = p->prm.eps_admm < 0 ? p->rho_scale / 100.0 : p->prm.eps_admm;
+  // rho^last = uncontrolled densities; KKT denominator at the start
+  kkt(p, p->st);
+  S.g0 = std::sqrt(read_scalar(p, 1));
+  S.J_prev = p->hscal[5] + 0.5 * p->prm.r * p->hscal[6];   // objective at v_start
+  ck(cudaMemcpyAsync(p->rho_last, p->rho_k, (size_t)(g.N + 1) * g.C * p->ts, cudaMemcpyDeviceToDevice, p->st),
+     "copy");
+  p->fscale = -1.0;
+  S.phase = max_admm > 0 ? 0 : 2;
+}
+
+// Alg. 1 (warm-started after the first iteration), the NSO residual, the start of the NSO solve
+void solve_head(stc_problem* p) {
+  SolveRun& S = p->run;
+  ao(p, p->prm.ao_iters, S.it > 0, p->st);
+  residual_norm(p, 0, 0, p->st);
+  S.f = read_scalar(p, 0);
+  if (p->fscale < 0) p->fscale = S.f;
+  S.cycles = 0;
+  S.give_up = false;
+  nso_begin(p);
+  S.phase = 1;
+}
+
+// at least one V-cycle per ADMM iteration, then until the NSO tolerance or the cap
+bool solve_wants_cycle(const stc_problem* p) {
+  const SolveRun& S = p->run;
+  return S.phase == 1 && (S.cycles < 1 || S.f > p->prm.eps_stfas * p->fscale) && S.cycles < p->prm.max_vcycles &&
+         !S.give_up;
+}
+
+void solve_cycle_done(stc_problem* p, double f_new) {
+  SolveRun& S = p->run;
+  lm_decide(p, S.f, f_new, &S.f, &S.give_up);
+  ++S.cycles;
+}
+
+// KKT metric, AL-fallback decision, multiplier update, penalty balancing, stopping tests
+void solve_tail(stc_problem* p) {
+  SolveRun& S = p->run;
+  stc_report& rep = S.rep;
+  const stc_params& prm = p->prm;
+  kkt(p, p->st);
+  const double gn = std::sqrt(read_scalar(p, 1));
+  const double J = p->hscal[5] + 0.5 * prm.r * p->hscal[6];
+  // Sec. 5 AL fallback: hold lambda while the objective still falls by more
+  // than al_threshold * |J| per iteration (al_threshold < 0: plain Alg. 3)
+  const bool update = prm.al_threshold < 0 || (S.J_prev - J) <= prm.al_threshold * std::fabs(S.J_prev);
+  S.J_prev = J;
+  admm_update(p, p->st, update);   // drho test + lambda update (lambda unused if we stop)
+  const double drho = read_scalar(p, 2);
+  const double K_used = prm.K;
+  if (prm.k_adapt && update) {
+    adapt_penalty(p, !S.have_prev, S.K0);
+    S.have_prev = true;
+  }
+  rep.objective = J;
+  if (update) ++rep.lambda_updates;
+  rep.admm_iters = S.it + 1;
+  rep.vcycles += S.cycles;
+  rep.rejected_vcycles = p->rejected;
+  rep.lm_shift = p->lm;
+  rep.kkt_abs = gn;
+  rep.kkt_rel = S.g0 > 0 ? gn / S.g0 : 0.0;
+  rep.f_inf = S.f;
+  rep.drho = drho;
+  const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+  p->solve_hist.insert(p->solve_hist.end(), {rep.kkt_rel, el, K_used});
+  if (rep.kkt_rel <= 1e-2 && rep.seconds_to_1e2 < 0) rep.seconds_to_1e2 = el;
+  if (rep.kkt_rel <= 1e-3 && rep.seconds_to_1e3 < 0) rep.seconds_to_1e3 = el;
+  if (rep.kkt_rel <= 1e-4 && rep.seconds_to_1e4 < 0) rep.seconds_to_1e4 = el;
+  if (rep.kkt_rel <= 1e-6 && rep.seconds_to_1e6 < 0) rep.seconds_to_1e6 = el;
+  rep.K_final = K_used;
+  if (drho < p->rho_scale / 100.0 && rep.density_stop_iter == 0) {
+    rep.density_stop_iter = S.it + 1;
+    rep.seconds_to_density_stop = el;
+  }
+  ++S.it;
+  if (rep.kkt_rel <= S.tol || drho < S.eps_admm) {
+    S.converged = true;
+    S.phase = 2;
+  } else {
+    S.phase = S.it < S.max_admm ? 0 : 2;
+  }
+  if (S.phase == 2) {
+    ck(cudaStreamSynchronize(p->st), "sync");
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+  }
 }
 
 extern "C" {
@@ -1538,92 +1702,162 @@ stc_status stc_solve(stc_problem* p, double kkt_rel_tol, int max_admm, stc_repor
     g_last_error = "invalid argument";
     return STC_ERR_INVALID_ARG;
   }
-  stc_report rep;
-  std::memset(&rep, 0, sizeof(rep));
-  rep.seconds_to_1e4 = -1.0;
-  rep.seconds_to_1e2 = rep.seconds_to_1e3 = rep.seconds_to_1e6 = -1.0;
-  rep.seconds_to_density_stop = -1.0;
-  rep.K_final = p->prm.K;
-  bool converged = false;
+  p->run = SolveRun{};
+  p->run.rep.K_final = p->prm.K;
   stc_status s = guarded(p, [&]() {
-    auto t0 = std::chrono::steady_clock::now();
-    const stc_params& prm = p->prm;
-    const double K0 = prm.K;
-    bool have_prev = false;   // k_adapt: v_prev holds a previous iteration's v
-    p->solve_hist.clear();
-    reset_state(p);
-    const Geom& g = p->lv[0].g;
-    const double eps_admm = prm.eps_admm < 0 ? p->rho_scale / 100.0 : prm.eps_admm;
-    // rho^last = uncontrolled densities; KKT denominator at the start
-    kkt(p, p->st);
-    const double g0 = std::sqrt(read_scalar(p, 1));
-    double J_prev = p->hscal[5] + 0.5 * prm.r * p->hscal[6];   // objective at v_start
-    ck(cudaMemcpyAsync(p->rho_last, p->rho_k, (size_t)(g.N + 1) * g.C * p->ts, cudaMemcpyDeviceToDevice, p->st),
-       "copy");
-    p->fscale = -1.0;
-    for (int it = 0; it < max_admm; ++it) {
-      // Alg. 1 initialises v* = v + lambda/K on the first ADMM iteration and
-      // continues from the previous v* afterwards (warm start)
-      ao(p, prm.ao_iters, it > 0, p->st);
-      residual_norm(p, 0, 0, p->st);
-      double f = read_scalar(p, 0);
-      if (p->fscale < 0) p->fscale = f;
-      int cycles = 0;
-      nso_begin(p);
-      // at least one V-cycle per ADMM iteration, then until the NSO tolerance
-      bool give_up = false;
-      while ((cycles < 1 || f > prm.eps_stfas * p->fscale) && cycles < prm.max_vcycles && !give_up) {
-        f = nso_cycle(p, f, &give_up);
-        ++cycles;
-      }
-      kkt(p, p->st);
-      const double gn = std::sqrt(read_scalar(p, 1));
-      const double J = p->hscal[5] + 0.5 * prm.r * p->hscal[6];
-      // Sec. 5 AL fallback: hold lambda while the objective still falls by more
-      // than al_threshold * |J| per iteration (al_threshold < 0: plain Alg. 3)
-      const bool update = prm.al_threshold < 0 || (J_prev - J) <= prm.al_threshold * std::fabs(J_prev);
-      J_prev = J;
-      admm_update(p, p->st, update);   // drho test + lambda update (lambda unused if we stop)
-      const double drho = read_scalar(p, 2);
-      const double K_used = prm.K;
-      if (prm.k_adapt && update) {
-        adapt_penalty(p, !have_prev, K0);
-        have_prev = true;
-      }
-      rep.objective = J;
-      if (update) ++rep.lambda_updates;
-      rep.admm_iters = it + 1;
-      rep.vcycles += cycles;
-      rep.rejected_vcycles = p->rejected;
-      rep.lm_shift = p->lm;
-      rep.kkt_abs = gn;
-      rep.kkt_rel = g0 > 0 ? gn / g0 : 0.0;
-      rep.f_inf = f;
-      rep.drho = drho;
-      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      p->solve_hist.insert(p->solve_hist.end(), {rep.kkt_rel, el, K_used});
-      if (rep.kkt_rel <= 1e-2 && rep.seconds_to_1e2 < 0) rep.seconds_to_1e2 = el;
-      if (rep.kkt_rel <= 1e-3 && rep.seconds_to_1e3 < 0) rep.seconds_to_1e3 = el;
-      if (rep.kkt_rel <= 1e-4 && rep.seconds_to_1e4 < 0) rep.seconds_to_1e4 = el;
-      if (rep.kkt_rel <= 1e-6 && rep.seconds_to_1e6 < 0) rep.seconds_to_1e6 = el;
-      rep.K_final = K_used;
-      if (drho < p->rho_scale / 100.0 && rep.density_stop_iter == 0) {
-        rep.density_stop_iter = it + 1;
-        rep.seconds_to_density_stop = el;
-      }
-      if (rep.kkt_rel <= kkt_rel_tol || drho < eps_admm) {
-        converged = rep.kkt_rel <= kkt_rel_tol || drho < eps_admm;
-        break;
-      }
+    solve_begin(p, kkt_rel_tol, max_admm);
+    while (p->run.phase != 2) {
+      solve_head(p);
+      while (solve_wants_cycle(p)) solve_cycle_done(p, run_vcycle(p, p->prm.lm_adapt != 0));
+      solve_tail(p);
     }
-    ck(cudaStreamSynchronize(p->st), "sync");
-    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });
-  if (report) *report = rep;
+  if (report) *report = p->run.rep;
   if (s != STC_OK) return s;
-  if (!converged) {
+  if (!p->run.converged) {
     g_last_error = "ADMM iteration cap reached";
     return STC_ERR_NOT_CONVERGED;
+  }
+  return STC_OK;
+}
+
+// ---- resumable solve and batched NSO cycles --------------------------------
+
+stc_status stc_solve_begin(stc_problem* p, double kkt_rel_tol, int max_admm) {
+  if (!p || max_admm < 0) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  p->run = SolveRun{};
+  return guarded(p, [&]() { solve_begin(p, kkt_rel_tol, max_admm); });
+}
+
+stc_status stc_solve_phase(const stc_problem* p, int* phase, int* wants_cycle) {
+  if (!p || !phase) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  *phase = p->run.phase;
+  if (wants_cycle) *wants_cycle = solve_wants_cycle(p) ? 1 : 0;
+  return STC_OK;
+}
+
+stc_status stc_solve_head(stc_problem* p) {
+  if (!p || p->run.phase != 0) {
+    g_last_error = "stc_solve_head: no ADMM iteration is due";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() { solve_head(p); });
+}
+
+stc_status stc_solve_tail(stc_problem* p) {
+  if (!p || p->run.phase != 1 || solve_wants_cycle(p)) {
+    g_last_error = "stc_solve_tail: the NSO solve of this iteration is not finished";
+    return STC_ERR_INVALID_ARG;
+  }
+  return guarded(p, [&]() { solve_tail(p); });
+}
+
+stc_status stc_solve_report(const stc_problem* p, stc_report* report, int* converged) {
+  if (!p) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  if (report) *report = p->run.rep;
+  if (converged) *converged = p->run.converged ? 1 : 0;
+  return STC_OK;
+}
+
+}  // extern "C"
+
+struct stc_batch {
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<const stc_problem*, long long>> key;   // composition of exec
+  long long launches = 0;
+};
+
+extern "C" {
+
+stc_status stc_batch_create(void* cuda_stream, stc_batch** out) {
+  if (!out) {
+    g_last_error = "null argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  *out = new (std::nothrow) stc_batch();
+  if (!*out) {
+    g_last_error = "host allocation failed";
+    return STC_ERR_OOM;
+  }
+  (*out)->st = (cudaStream_t)cuda_stream;
+  return STC_OK;
+}
+
+stc_status stc_batch_destroy(stc_batch* b) {
+  if (!b) return STC_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+  return STC_OK;
+}
+
+stc_status stc_batch_nso_cycle(stc_batch* b, stc_problem* const* probs, int n, int* cycled, stc_status* status) {
+  if (!b || n < 0 || (n > 0 && !probs)) {
+    g_last_error = "invalid argument";
+    return STC_ERR_INVALID_ARG;
+  }
+  std::vector<stc_problem*> go;
+  for (int k = 0; k < n; ++k) {
+    if (status) status[k] = STC_OK;
+    stc_problem* p = probs[k];
+    if (!p || p->broken || !solve_wants_cycle(p)) continue;
+    const stc_status sk = guarded(p, [&]() {
+      ensure_vgraph(p, false);
+      ck(cudaStreamSynchronize(p->st), "sync");   // the problem's own work before the batched launch
+    });
+    if (sk != STC_OK) {
+      if (status) status[k] = sk;
+      continue;
+    }
+    go.push_back(p);
+  }
+  if (cycled) *cycled = (int)go.size();
+  if (go.empty()) return STC_OK;
+  std::vector<std::pair<const stc_problem*, long long>> key;
+  for (stc_problem* p : go) key.emplace_back(p, p->vgraph_version);
+  try {
+    if (!b->exec || key != b->key) {
+      if (b->exec) {
+        ck(cudaGraphExecDestroy(b->exec), "graph destroy");
+        b->exec = nullptr;
+      }
+      cudaGraph_t root = nullptr;
+      ck(cudaGraphCreate(&root, 0), "graph create");
+      cudaError_t e = cudaSuccess;
+      for (stc_problem* p : go) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddChildGraphNode(&node, root, nullptr, 0, p->vgraph_src);
+        if (e != cudaSuccess) break;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, root, 0);
+      cudaGraphDestroy(root);
+      ck(e, "batched graph");
+      b->key = key;
+    }
+    ck(cudaGraphLaunch(b->exec, b->st), "batched graph launch");
+    ck(cudaStreamSynchronize(b->st), "sync");
+  } catch (const StcError& e) {
+    g_last_error = e.msg;
+    return e.code;
+  }
+  // each problem's norm, then its LM decision (Sec. 5)
+  for (int k = 0; k < n; ++k) {
+    stc_problem* p = probs[k];
+    if (std::find(go.begin(), go.end(), p) == go.end()) continue;
+    const stc_status sk = guarded(p, [&]() {
+      p->launches += p->graph_launches;
+      solve_cycle_done(p, read_scalar(p, 0, false, p->prm.lm_adapt != 0));
+    });
+    if (status) status[k] = sk;
   }
   return STC_OK;
 }
@@ -2020,11 +2254,7 @@ stc_status stc_set_kernel_timing(stc_problem* p, int enable) {
     return STC_ERR_INVALID_ARG;
   }
   return guarded(p, [&]() {
-    for (cudaGraphExec_t* ge : {&p->vgraph, &p->vgraph_t})
-      if (*ge) {
-        ck(cudaGraphExecDestroy(*ge), "graph destroy");
-        *ge = nullptr;
-      }
+    drop_vgraphs(p);
     p->timing = enable != 0;
     // one event pair per finest-level colour launch of a cycle (the finest
     // level is smoothed with events only when it is not the coarsest)

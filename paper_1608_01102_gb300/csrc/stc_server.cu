@@ -1,6 +1,8 @@
 // Serving runtime: admission of control problems against a device-memory
-// budget and concurrent solves on per-problem CUDA streams (host code; the
-// device work is the library's own kernels through stc_solve).
+// budget, and either concurrent solves on per-problem CUDA streams (worker
+// threads, mode 0) or steps in which the NSO V-cycles of every resident
+// problem run as one batched CUDA graph launch (mode 1).  Host code; the
+// device work is the library's own kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +38,8 @@ struct Request {
   int bypassed = 0;
   stc_ticket_info info{};
   std::vector<double> forces;
+  stc_problem* p = nullptr;   // stepped mode: the resident problem
+  bool owned = true;          // false: submitted by the caller (stc_server_submit_problem)
 };
 
 }  // namespace
@@ -53,6 +57,10 @@ struct stc_server {
   bool stopping = false;
   Clock::time_point t0 = Clock::now();
   std::vector<std::thread> workers;
+  // stepped mode (sp.mode == 1)
+  std::mutex step_mu;                 // one step at a time
+  std::vector<Request*> resident;     // admitted, solving (touched by the stepping thread only)
+  stc_batch* batch = nullptr;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -159,6 +167,129 @@ Request* find(stc_server* s, long long ticket) {
   return it == s->all.end() ? nullptr : it->second.get();
 }
 
+// stepped mode: a resident request ends (its memory returns to the budget)
+void finish_stepped(stc_server* s, Request* r, stc_status status) {
+  r->info.status = status;
+  if (status != STC_OK && status != STC_ERR_NOT_CONVERGED) set_error(r, stc_last_error());
+  if (r->p) {
+    stc_solve_report(r->p, &r->info.report, nullptr);
+    if (r->owned) stc_destroy_problem(r->p);
+    r->p = nullptr;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->in_use -= r->bytes;
+  s->running--;
+  r->info.t_done = s->now();
+  r->info.state = (status == STC_OK || status == STC_ERR_NOT_CONVERGED) ? STC_TICKET_DONE : STC_TICKET_FAILED;
+  s->cv_done.notify_all();
+}
+
+size_t face_count(const stc_params& prm) {
+  if (prm.nz > 0)
+    return (size_t)prm.nz * prm.ny * (prm.nx + 1) + (size_t)prm.nz * (prm.ny + 1) * prm.nx +
+           (size_t)(prm.nz + 1) * prm.ny * prm.nx;
+  return (size_t)prm.ny * (prm.nx + 1) + (size_t)(prm.ny + 1) * prm.nx;
+}
+
+// One serving step: admission, the heads (Alg. 1) of problems whose ADMM
+// iteration begins, one batched launch of every resident problem's next NSO
+// V-cycle, the tails (KKT metric, multiplier update, stopping tests) of
+// problems whose NSO solve ended, and retirement of finished problems.
+stc_status step_stepped(stc_server* s, int* active) {
+  std::lock_guard<std::mutex> step_lock(s->step_mu);
+  std::vector<Request*> admitted;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    while ((int)(s->resident.size() + admitted.size()) < s->sp.max_resident) {
+      Request* r = pick(s);
+      if (!r) break;
+      s->in_use += r->bytes;
+      s->peak = std::max(s->peak, s->in_use);
+      s->running++;
+      r->info.state = STC_TICKET_RUNNING;
+      r->info.t_admit = s->now();
+      admitted.push_back(r);
+    }
+    if (!admitted.empty()) s->cv_done.notify_all();
+  }
+  for (Request* r : admitted) {
+    stc_status st = STC_OK;
+    if (!r->p) {
+      st = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), s->sp.stream, &r->p);
+      if (st == STC_OK && !r->steps.empty())
+        st = stc_set_keyframes(r->p, (int)r->steps.size(), r->steps.data(), r->stars.data(), r->cs.data());
+    }
+    if (st == STC_OK) st = stc_solve_begin(r->p, r->tol, r->max_admm);
+    if (st != STC_OK) finish_stepped(s, r, st);
+    else s->resident.push_back(r);
+  }
+  std::vector<std::pair<Request*, stc_status>> failed;
+  auto failed_status = [&](Request* r) {
+    for (auto& f : failed)
+      if (f.first == r) return f.second;
+    return STC_OK;
+  };
+  auto phase = [](Request* r, int* wants) {
+    int ph = 2;
+    stc_solve_phase(r->p, &ph, wants);
+    return ph;
+  };
+  for (Request* r : s->resident) {
+    int w = 0;
+    if (phase(r, &w) == 0) {
+      const stc_status st = stc_solve_head(r->p);
+      if (st != STC_OK) failed.emplace_back(r, st);
+    }
+  }
+  std::vector<stc_problem*> probs;
+  std::vector<Request*> owners;
+  for (Request* r : s->resident) {
+    int w = 0;
+    if (failed_status(r) == STC_OK && phase(r, &w) == 1 && w) {
+      probs.push_back(r->p);
+      owners.push_back(r);
+    }
+  }
+  if (!probs.empty()) {
+    std::vector<stc_status> sts(probs.size(), STC_OK);
+    const stc_status b = stc_batch_nso_cycle(s->batch, probs.data(), (int)probs.size(), nullptr, sts.data());
+    for (size_t k = 0; k < probs.size(); ++k)
+      if (b != STC_OK || sts[k] != STC_OK) failed.emplace_back(owners[k], b != STC_OK ? b : sts[k]);
+  }
+  std::vector<Request*> keep;
+  for (Request* r : s->resident) {
+    if (failed_status(r) != STC_OK) {
+      finish_stepped(s, r, failed_status(r));
+      continue;
+    }
+    int w = 0;
+    if (phase(r, &w) == 1 && !w) {
+      const stc_status st = stc_solve_tail(r->p);
+      if (st != STC_OK) {
+        finish_stepped(s, r, st);
+        continue;
+      }
+    }
+    if (phase(r, &w) == 2) {
+      int conv = 0;
+      stc_solve_report(r->p, &r->info.report, &conv);
+      stc_status st = conv ? STC_OK : STC_ERR_NOT_CONVERGED;
+      r->forces.resize((size_t)r->prm.num_steps * face_count(r->prm));
+      const stc_status g = stc_get_forces(r->p, r->forces.data(), r->forces.size());
+      if (g != STC_OK) st = g;
+      finish_stepped(s, r, st);
+      continue;
+    }
+    keep.push_back(r);
+  }
+  s->resident.swap(keep);
+  if (active) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    *active = (int)(s->resident.size() + s->queue.size());
+  }
+  return STC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -171,16 +302,31 @@ void stc_server_default_params(stc_server_params* sp, size_t budget_bytes) {
   sp->backend = 0;
   sp->device = 0;
   sp->max_bypass = 8;
+  sp->mode = 0;
+  sp->stream = nullptr;
+  sp->max_resident = 16;
+  sp->kkt_rel_tol = 1e-4;
+  sp->max_admm = 50;
 }
 
 stc_status stc_server_create(const stc_server_params* sp, stc_server** out) {
   if (!sp || !out || sp->workers < 1 || sp->workers > 256 || sp->budget_bytes == 0 || sp->backend < 0 ||
-      sp->backend > 1 || sp->max_bypass < 0)
+      sp->backend > 1 || sp->max_bypass < 0 || sp->mode < 0 || sp->mode > 1 ||
+      (sp->mode == 1 && (sp->backend != 0 || sp->max_resident < 1 || sp->max_admm < 0)))
     return fail_arg("invalid server parameters");
   *out = nullptr;
   stc_server* s = new (std::nothrow) stc_server();
   if (!s) return fail_arg("host allocation failed", STC_ERR_OOM);
   s->sp = *sp;
+  if (sp->mode == 1) {   // stepped: no worker threads; the caller's steps do the work
+    if (cudaSetDevice(sp->device) != cudaSuccess || stc_batch_create(sp->stream, &s->batch) != STC_OK) {
+      cudaGetLastError();
+      delete s;
+      return fail_arg("could not set up the batched stepping", STC_ERR_CUDA);
+    }
+    *out = s;
+    return STC_OK;
+  }
   try {
     for (int k = 0; k < sp->workers; ++k) s->workers.emplace_back(worker, s);
   } catch (...) {
@@ -243,6 +389,47 @@ stc_status stc_server_submit(stc_server* s, const stc_request* rq, long long* ti
   return STC_OK;
 }
 
+stc_status stc_server_submit_problem(stc_server* s, stc_problem* p, long long* ticket) {
+  if (!s || !p || !ticket) return fail_arg("null argument");
+  if (s->sp.mode != 1) return fail_arg("problem submits need a stepped server (mode 1)");
+  size_t bytes = 0;
+  if (stc_memory_bytes(p, &bytes) != STC_OK) return fail_arg("invalid problem");
+  if (bytes > s->sp.budget_bytes) return fail_arg("problem exceeds the server's memory budget", STC_ERR_OOM);
+  auto r = std::make_unique<Request>();
+  r->p = p;
+  r->owned = false;
+  r->tol = s->sp.kkt_rel_tol;
+  r->max_admm = s->sp.max_admm;
+  int nx = 0, ny = 0, nz = 0, N = 0;
+  double dt = 0.0;
+  stc_level_dims(p, 0, &nx, &ny, &nz);
+  stc_level_steps(p, 0, &N, &dt);
+  r->prm.nx = nx;
+  r->prm.ny = ny;
+  r->prm.nz = nz > 1 ? nz : 0;
+  r->prm.num_steps = N;
+  r->bytes = bytes;
+  r->info.state = STC_TICKET_QUEUED;
+  r->info.bytes = bytes;
+  r->info.t_admit = r->info.t_done = -1.0;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stopping) return fail_arg("server is shutting down", STC_ERR_BUSY);
+    r->ticket = s->next_ticket++;
+    r->info.t_submit = s->now();
+    *ticket = r->ticket;
+    s->queue.push_back(r.get());
+    s->all[r->ticket] = std::move(r);
+  }
+  return STC_OK;
+}
+
+stc_status stc_server_step(stc_server* s, int* active) {
+  if (!s) return fail_arg("null argument");
+  if (s->sp.mode != 1) return fail_arg("stc_server_step needs a stepped server (mode 1)");
+  return step_stepped(s, active);
+}
+
 stc_status stc_server_poll(stc_server* s, long long ticket, stc_ticket_info* info) {
   if (!s || !info) return fail_arg("null argument");
   std::lock_guard<std::mutex> lock(s->mu);
@@ -258,6 +445,18 @@ stc_status stc_server_wait(stc_server* s, long long ticket, double timeout_s, st
   Request* r = find(s, ticket);
   if (!r) return fail_arg("unknown ticket");
   auto done = [&] { return finished(r->info.state); };
+  if (s->sp.mode == 1) {   // stepped: the waiting thread drives the steps
+    const double until = timeout_s < 0 ? -1.0 : s->now() + timeout_s;
+    while (!done() && (until < 0 || s->now() < until)) {
+      lock.unlock();
+      int active = 0;
+      const stc_status st = step_stepped(s, &active);
+      lock.lock();
+      if (st != STC_OK || active == 0) break;
+    }
+    if (info) *info = r->info;
+    return STC_OK;
+  }
   if (timeout_s < 0)
     s->cv_done.wait(lock, done);
   else
@@ -334,6 +533,16 @@ stc_status stc_server_destroy(stc_server* s) {
   s->cv_work.notify_all();
   s->cv_done.notify_all();
   for (auto& t : s->workers) t.join();
+  {
+    std::lock_guard<std::mutex> step_lock(s->step_mu);
+    for (Request* r : s->resident) {   // stepped mode: solves still in flight end here
+      if (r->p && r->owned) stc_destroy_problem(r->p);
+      r->p = nullptr;
+      r->info.state = STC_TICKET_CANCELLED;
+    }
+    s->resident.clear();
+    if (s->batch) stc_batch_destroy(s->batch);
+  }
   delete s;
   return STC_OK;
 }

@@ -49,7 +49,8 @@ class StcReport(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("budget_bytes", c_size_t), ("workers", c_int), ("backend", c_int), ("device", c_int),
-                ("max_bypass", c_int)]
+                ("max_bypass", c_int), ("mode", c_int), ("stream", c_void_p), ("max_resident", c_int),
+                ("kkt_rel_tol", c_double), ("max_admm", c_int)]
 
 
 class Request(ctypes.Structure):
@@ -109,6 +110,8 @@ SIGNATURES = {
     "stc_server_default_params": (None, [ctypes.POINTER(ServerParams), c_size_t]),
     "stc_server_create": (c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(c_void_p)]),
     "stc_server_submit": (c_int, [P_server, ctypes.POINTER(Request), P_ll]),
+    "stc_server_submit_problem": (c_int, [P_server, c_void_p, P_ll]),
+    "stc_server_step": (c_int, [P_server, P_int]),
     "stc_server_poll": (c_int, [P_server, ctypes.c_longlong, ctypes.POINTER(TicketInfo)]),
     "stc_server_wait": (c_int, [P_server, ctypes.c_longlong, c_double, ctypes.POINTER(TicketInfo)]),
     "stc_server_cancel": (c_int, [P_server, ctypes.c_longlong]),
@@ -124,6 +127,14 @@ SIGNATURES = {
     "stc_admm_update": (c_int, [c_void_p, P_double]),
     "stc_set_penalty": (c_int, [c_void_p, c_double, c_double]),
     "stc_solve_history": (c_int, [c_void_p, P_double, c_size_t, P_int]),
+    "stc_solve_begin": (c_int, [c_void_p, c_double, c_int]),
+    "stc_solve_phase": (c_int, [c_void_p, P_int, P_int]),
+    "stc_solve_head": (c_int, [c_void_p]),
+    "stc_solve_tail": (c_int, [c_void_p]),
+    "stc_solve_report": (c_int, [c_void_p, ctypes.POINTER(StcReport), P_int]),
+    "stc_batch_create": (c_int, [c_void_p, ctypes.POINTER(c_void_p)]),
+    "stc_batch_nso_cycle": (c_int, [c_void_p, ctypes.POINTER(c_void_p), c_int, P_int, P_int]),
+    "stc_batch_destroy": (c_int, [c_void_p]),
     "stc_launch_count": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "stc_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "stc_kernel_timing": (c_int, [c_void_p, P_double, ctypes.POINTER(ctypes.c_longlong)]),
@@ -293,6 +304,29 @@ class Problem:
             _check(self.lib.stc_solve_history(self.h, _dptr(buf), buf.size, ctypes.byref(n)))
         return [tuple(buf[3 * k:3 * k + 3]) for k in range(n.value)]
 
+    # the ADMM loop as resumable phases (stc_solve_begin / _head / _tail) ---------
+    def solve_begin(self, tol=1e-4, max_admm=50):
+        _check(self.lib.stc_solve_begin(self.h, tol, max_admm))
+
+    def solve_phase(self):
+        """(phase, wants_cycle): phase 0 = AO due, 1 = NSO cycles, 2 = finished."""
+        ph, w = c_int(), c_int()
+        _check(self.lib.stc_solve_phase(self.h, ctypes.byref(ph), ctypes.byref(w)))
+        return ph.value, bool(w.value)
+
+    def solve_head(self):
+        _check(self.lib.stc_solve_head(self.h))
+
+    def solve_tail(self):
+        _check(self.lib.stc_solve_tail(self.h))
+
+    def solve_report(self):
+        rep, conv = StcReport(), c_int()
+        _check(self.lib.stc_solve_report(self.h, ctypes.byref(rep), ctypes.byref(conv)))
+        out = {k: getattr(rep, k) for k, _ in StcReport._fields_}
+        out["converged"] = bool(conv.value)
+        return out
+
     def advect(self, source="VSTAR"):
         _check(self.lib.stc_advect(self.h, FIELDS[source]))
 
@@ -436,6 +470,42 @@ def adjoint_sweep_noalloc(nx, ny, N, dt, taylor_kmax, vel, rho, K, mterm, mu, ba
                                          vp(base), alpha, beta, vp(out), vp(stream)))
 
 
+class Batch:
+    """stc_batch: NSO V-cycles of many problems in one CUDA graph launch."""
+
+    def __init__(self, stream=None):
+        self.lib = load()
+        h = c_void_p()
+        _check(self.lib.stc_batch_create(c_void_p(int(stream)) if stream else None, ctypes.byref(h)))
+        self.h = h
+
+    def nso_cycle(self, problems):
+        """One V-cycle for every problem that wants one; returns (cycled, statuses)."""
+        n = len(problems)
+        arr = (c_void_p * max(n, 1))(*[p.h for p in problems])
+        st = (c_int * max(n, 1))()
+        c = c_int()
+        _check(self.lib.stc_batch_nso_cycle(self.h, arr, n, ctypes.byref(c), st))
+        return c.value, [int(st[k]) for k in range(n)]
+
+    def close(self):
+        if self.h:
+            self.lib.stc_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def measure_fp32_peak(stream=None):
     """stc_measure_fp32_peak: the device's FP32 FMA throughput in GFLOP/s."""
     g = c_double()
@@ -480,11 +550,15 @@ def _info_dict(info):
 class Server:
     """Serving many control problems on one device (include/stc_server.h)."""
 
-    def __init__(self, budget_bytes, workers=8, backend=0, device=0, max_bypass=8):
+    def __init__(self, budget_bytes, workers=8, backend=0, device=0, max_bypass=8, mode=0, stream=None,
+                 max_resident=16, tol=1e-4, max_admm=50):
+        """mode 0: worker threads; mode 1: stepped (step() runs one batched step)."""
         self.lib = load()
         sp = ServerParams()
         self.lib.stc_server_default_params(ctypes.byref(sp), int(budget_bytes))
         sp.workers, sp.backend, sp.device, sp.max_bypass = workers, backend, device, max_bypass
+        sp.mode, sp.max_resident, sp.kkt_rel_tol, sp.max_admm = mode, max_resident, tol, max_admm
+        sp.stream = c_void_p(int(stream)) if stream else None
         h = c_void_p()
         _check(self.lib.stc_server_create(ctypes.byref(sp), ctypes.byref(h)))
         self.h = h
@@ -515,6 +589,19 @@ class Server:
         F = grid_sizes(params.nx, params.ny, params.nz)[0]
         self._sizes[t.value] = (params.num_steps, F)
         return t.value
+
+    def submit_problem(self, problem):
+        """Mode 1: queue a Problem created on the server's stream (not destroyed by the server)."""
+        t = ctypes.c_longlong()
+        _check(self.lib.stc_server_submit_problem(self.h, problem.h, ctypes.byref(t)))
+        self._sizes[t.value] = (problem.N, problem.field_shape("U")[1])
+        return t.value
+
+    def step(self):
+        """Mode 1: one serving step; returns the problems resident or queued after it."""
+        a = c_int()
+        _check(self.lib.stc_server_step(self.h, ctypes.byref(a)))
+        return a.value
 
     def poll(self, ticket):
         info = TicketInfo()
