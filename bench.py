@@ -579,7 +579,7 @@ def run_native(args, rank, world, local_rank):
         cpu2 = {"value": v, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": sample_text("letters"),
                 "seconds": s}
 
-    m = measure_step(stc, workloads, head, args, dev, world)
+    m = measure_step(stc, workloads, head, args, dev, world, with_e2e=not args.no_e2e)
     if rank != 0:
         return
     line = {"metric": "STFAS spacetime cells/s", "value": m["value"], "unit": "cells/s", "n_gpus": world,
@@ -588,7 +588,7 @@ def run_native(args, rank, world, local_rank):
             "config": {"workload": m["workload"], "vcycles_per_step": VCYCLES,
                        "l2": "256 MiB buffer written between timed steps (outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": m["roofline"], "e2e": m["e2e"], "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
+            "roofline": m["roofline"], "e2e": m.get("e2e"), "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
             "vcycle_only": m["vcycle_only"], "kernels": m["kernels"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -602,9 +602,9 @@ def run_native(args, rank, world, local_rank):
                          "peak_gflops": fp32, "frac": fl[0] / (sc["avg_launch_us"] * 1e-6) / 1e9 / fp32,
                          "flops_rule": "2 x FFMA + FADD + FMUL thread instructions of one launch (ncu count)"}
     if solo and not args.no_secondary:
-        m2 = measure_step(stc, workloads, other, args, dev, world)
-        sec = {k: m2[k] for k in ("value", "ms_per_step", "roofline", "kernels", "vcycle_only", "e2e", "clocks",
-                                  "gpu_launches", "workload")}
+        m2 = measure_step(stc, workloads, other, args, dev, world, with_e2e=not args.no_e2e)
+        sec = {k: m2.get(k) for k in ("value", "ms_per_step", "roofline", "kernels", "vcycle_only", "e2e", "clocks",
+                                      "gpu_launches", "workload")}
         if cpu2 is not None:
             sec["cpu_baseline"] = cpu2
         line["letters" if other == "letters" else "3d"] = sec
@@ -642,6 +642,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workload's step line")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (short profiling runs)")
     ap.add_argument("--small-max-admm", type=int, default=1500)
     ap.add_argument("--solve-max-admm", type=int, default=500)
     ap.add_argument("--fp64-max-admm", type=int, default=40)

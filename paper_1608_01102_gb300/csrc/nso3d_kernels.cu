@@ -42,10 +42,158 @@ __device__ __forceinline__ T row3(const Geom& g, const CState<T>& x, int t, int 
   return val;
 }
 
-// out = sf * f(x) + sr * res; thread x: face e (< F) and cell e (< C); blockIdx.y: t
+// ---------------------------------------------------------------------------
+// Two-pass form of rows 1 and 3 on large levels.  The Jacobian-transpose term
+// (dAdv(v_t)/dv)^T u_{t-1} of row 1 gathers, per face, the products
+// alpha1 = V1 u, alpha2 = -V2 u, beta1 = O1 u, beta2 = -O2 u of ~24 faces
+// around it, and each product needs the Lamb-vector terms (O1, V1, O2, V2) of
+// its own face: evaluated inline per output face, that is ~150 dependent
+// loads and thousands of instructions per face, and the kernel was bound by
+// instruction fetch.  Pass A (lamb3_terms_kernel, one launch per face axis)
+// evaluates the terms of v_t once per face and stores the four products with
+// u_{t-1} and Adv(v_t) = O1 V1 - O2 V2; pass B (the residual kernels with
+// AB = true) gathers them.  Same sums in the same order as the inline form.
+// ---------------------------------------------------------------------------
+// the four products as planes (alpha1, alpha2, beta1, beta2), each (N+1) x F:
+// a gather reads one product of a face, so separate planes keep a warp's
+// loads to the sectors it uses
 template <class T>
+struct AB4 {
+  T* p[4];
+  size_t plane;   // (N + 1) F
+};
+
+// pass A: faces of one axis at times t = 0..N (blockIdx.y); AB4 of v_t with
+// u_{t-1} for t >= 1, Adv(v_t); zero on slots that are not interior faces
+template <class T, int AXIS>
+__global__ void __launch_bounds__(128) lamb3_terms_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ u,
+                                                          AB4<T> ab, T* __restrict__ advb) {
+  pdl_wait();
+  const int t = blockIdx.y;
+  const int n0 = AXIS == 0 ? g.nx + 1 : g.nx, n1 = AXIS == 1 ? g.ny + 1 : g.ny;
+  const int nf = n0 * n1 * (AXIS == 2 ? g.nz + 1 : g.nz);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nf || t > g.N) return;
+  const int i = e % n0, r = e / n0, j = r % n1, k = r / n1;
+  const int f = (AXIS == 0 ? 0 : (AXIS == 1 ? g.Fx : g.Fxy)) + e;
+  const size_t at = (size_t)t * g.F + f;
+  T o[4] = {T(0), T(0), T(0), T(0)};
+  T a = T(0);
+  if (interior(g, AXIS, k, j, i)) {
+    const Terms<T> tm = terms<T, T>(g, v + (size_t)t * g.F, AXIS, k, j, i);
+    a = tm.o1 * tm.v1 - tm.o2 * tm.v2;
+    if (t >= 1) {
+      const T uf = ld(u + (size_t)(t - 1) * g.F + f);
+      o[0] = tm.v1 * uf;
+      o[1] = -tm.v2 * uf;
+      o[2] = tm.o1 * uf;
+      o[3] = -tm.o2 * uf;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) ab.p[c][at] = o[c];
+  advb[at] = a;
+}
+
+// one product of the face (axis, k, j, i) of slice t, zero off the interior faces
+// the planes of one time slice
+template <class T>
+struct ABt {
+  const T* p[4];
+};
+
+template <class T, int C>
+__device__ __forceinline__ T abv(const Geom& g, const ABt<T>& abt, int axis, int k, int j, int i) {
+  if (!interior(g, axis, k, j, i)) return T(0);
+  const int f = axis == 0 ? xf(g, k, j, i) : (axis == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
+  return ld(abt.p[C] + f);
+}
+
+// the edge sums Q from stored products (the same sums as qx, qy, qz)
+template <class T>
+__device__ __forceinline__ T qx_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+  if (!g.periodic && (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz)) return T(0);
+  return T(0.5) * (abv<T, 1>(g, a, 1, k, j, i) + abv<T, 1>(g, a, 1, k - 1, j, i) + abv<T, 0>(g, a, 2, k, j, i) +
+                   abv<T, 0>(g, a, 2, k, j - 1, i));
+}
+template <class T>
+__device__ __forceinline__ T qy_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+  if (!g.periodic && (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz)) return T(0);
+  return T(0.5) * (abv<T, 0>(g, a, 0, k, j, i) + abv<T, 0>(g, a, 0, k - 1, j, i) + abv<T, 1>(g, a, 2, k, j, i) +
+                   abv<T, 1>(g, a, 2, k, j, i - 1));
+}
+template <class T>
+__device__ __forceinline__ T qz_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+  if (!g.periodic && (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny)) return T(0);
+  return T(0.5) * (abv<T, 1>(g, a, 0, k, j, i) + abv<T, 1>(g, a, 0, k, j - 1, i) + abv<T, 0>(g, a, 1, k, j, i) +
+                   abv<T, 0>(g, a, 1, k, j, i - 1));
+}
+
+// (dAdv/dv)^T u at an interior face from stored products (the order of jtu)
+template <class T>
+__device__ T jtu_ab(const Geom& g, const ABt<T>& a, int axis, int k, int j, int i) {
+  const T ih = pick<T>(g.ih, g.ihf);
+  if (axis == 0) {
+    const T r = (qy_ab(g, a, k, j, i) - qy_ab(g, a, k + 1, j, i) - qz_ab(g, a, k, j, i) + qz_ab(g, a, k, j + 1, i)) *
+                ih;
+    const T s = abv<T, 2>(g, a, 1, k, j, i - 1) + abv<T, 2>(g, a, 1, k, j, i) + abv<T, 2>(g, a, 1, k, j + 1, i - 1) +
+                abv<T, 2>(g, a, 1, k, j + 1, i) + abv<T, 3>(g, a, 2, k, j, i - 1) + abv<T, 3>(g, a, 2, k, j, i) +
+                abv<T, 3>(g, a, 2, k + 1, j, i - 1) + abv<T, 3>(g, a, 2, k + 1, j, i);
+    return r + T(0.25) * s;
+  }
+  if (axis == 1) {
+    const T r = (qz_ab(g, a, k, j, i) - qz_ab(g, a, k, j, i + 1) - qx_ab(g, a, k, j, i) + qx_ab(g, a, k + 1, j, i)) *
+                ih;
+    const T s = abv<T, 3>(g, a, 0, k, j, i) + abv<T, 3>(g, a, 0, k, j, i + 1) + abv<T, 3>(g, a, 0, k, j - 1, i) +
+                abv<T, 3>(g, a, 0, k, j - 1, i + 1) + abv<T, 2>(g, a, 2, k, j, i) + abv<T, 2>(g, a, 2, k, j - 1, i) +
+                abv<T, 2>(g, a, 2, k + 1, j, i) + abv<T, 2>(g, a, 2, k + 1, j - 1, i);
+    return r + T(0.25) * s;
+  }
+  const T r = (qx_ab(g, a, k, j, i) - qx_ab(g, a, k, j + 1, i) - qy_ab(g, a, k, j, i) + qy_ab(g, a, k, j, i + 1)) * ih;
+  const T s = abv<T, 2>(g, a, 0, k, j, i) + abv<T, 2>(g, a, 0, k, j, i + 1) + abv<T, 2>(g, a, 0, k - 1, j, i) +
+              abv<T, 2>(g, a, 0, k - 1, j, i + 1) + abv<T, 3>(g, a, 1, k, j, i) + abv<T, 3>(g, a, 1, k, j + 1, i) +
+              abv<T, 3>(g, a, 1, k - 1, j, i) + abv<T, 3>(g, a, 1, k - 1, j + 1, i);
+  return r + T(0.25) * s;
+}
+
+// rows 1 and 3 from the stored products (AB) or inline
+template <class T, bool AB>
+__device__ __forceinline__ T row1x(const Geom& g, const CState<T>& x, const T* __restrict__ z, const AB4<T>& ab,
+                                   int t, int e, int axis, int k, int j, int i) {
+  if (!AB) return row1(g, x, z, t, e, axis, k, j, i);
+  const T* vt = x.v + (size_t)t * g.F;
+  const T* pb = x.pbar + (size_t)t * g.C;
+  T val = ld(x.u + (size_t)(t - 1) * g.F + e) * pick<T>(g.idt, g.idtf);
+  if (g.self_adv) {
+    const size_t o = (size_t)t * g.F;
+    const ABt<T> a{{ab.p[0] + o, ab.p[1] + o, ab.p[2] + o, ab.p[3] + o}};
+    val += jtu_ab(g, a, axis, k, j, i);
+  }
+  val += grad(g, pb, axis, k, j, i);
+  if (t < g.N) {
+    const T* ut = x.u + (size_t)t * g.F;
+    val += pick<T>(g.a, g.af) * (ld(vt + e) - ld(z + (size_t)t * g.F + e)) - ld(ut + e) * pick<T>(g.idt, g.idtf);
+  }
+  return val;
+}
+
+template <class T, bool AB>
+__device__ __forceinline__ T row3x(const Geom& g, const CState<T>& x, const T* advb, int t, int e, int axis, int k,
+                                   int j, int i) {
+  if (!AB) return row3(g, x, t, e, axis, k, j, i);
+  const T* vn = x.v + (size_t)(t + 1) * g.F;
+  const T* vt = x.v + (size_t)t * g.F;
+  T val = (ld(vn + e) - ld(vt + e)) * pick<T>(g.idt, g.idtf) - ld(x.u + (size_t)t * g.F + e);
+  if (g.self_adv) val += ld(advb + (size_t)(t + 1) * g.F + e);
+  val += grad(g, x.p + (size_t)t * g.C, axis, k, j, i);
+  return val;
+}
+
+// out = sf * f(x) + sr * res; thread x: face e (< F) and cell e (< C); blockIdx.y: t
+template <class T, bool AB>
 __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res, State<T> out,
-                                     T sf, T sr, double* sq, RedScratch rs, const double* only_if_undone) {
+                                     T sf, T sr, double* sq, RedScratch rs, const double* only_if_undone,
+                                     AB4<T> ab, const T* __restrict__ advb) {
   pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
@@ -59,7 +207,7 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
     if (t >= 1) {
       T val = T(0);
       if (in) {
-        val = row1(g, x, z, t, e, axis, k, j, i) * sf;
+        val = row1x<T, AB>(g, x, z, ab, t, e, axis, k, j, i) * sf;
         if (res.v) val += sr * ld(res.v + (size_t)t * g.F + e);
       }
       out.v[(size_t)t * g.F + e] = val;
@@ -70,7 +218,7 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
     if (t < g.N) {
       T val = T(0);
       if (in) {
-        val = row3(g, x, t, e, axis, k, j, i) * sf;
+        val = row3x<T, AB>(g, x, advb, t, e, axis, k, j, i) * sf;
         if (res.u) val += sr * ld(res.u + (size_t)t * g.F + e);
       }
       out.u[(size_t)t * g.F + e] = val;
@@ -100,9 +248,10 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
 // f - res at what one colour's SCGS reads: the faces of its cells (x-faces of
 // rows j = py, k = pz (mod 2); y-faces of i = px, k = pz; z-faces of i = px,
 // j = py) and its cells.  Thread x: index over those; blockIdx.y: t.
-template <class T>
+template <class T, bool AB>
 __global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res,
-                                            State<T> out, int px, int py, int pz, const double* only_if_undone) {
+                                            State<T> out, int px, int py, int pz, const double* only_if_undone,
+                                            AB4<T> ab, const T* __restrict__ advb) {
   pdl_wait();
   const int t = blockIdx.y;
   if (t > g.N) return;
@@ -140,7 +289,7 @@ __global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __rest
     if (t >= 1) {
       T val = T(0);
       if (in) {
-        val = row1(g, x, z, t, f, axis, k, j, i);
+        val = row1x<T, AB>(g, x, z, ab, t, f, axis, k, j, i);
         if (res.v) val -= ld(res.v + (size_t)t * g.F + f);
       }
       out.v[(size_t)t * g.F + f] = val;
@@ -148,7 +297,7 @@ __global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __rest
     if (t < g.N) {
       T val = T(0);
       if (in) {
-        val = row3(g, x, t, f, axis, k, j, i);
+        val = row3x<T, AB>(g, x, advb, t, f, axis, k, j, i);
         if (res.u) val -= ld(res.u + (size_t)t * g.F + f);
       }
       out.u[(size_t)t * g.F + f] = val;
@@ -1265,12 +1414,46 @@ inline unsigned blocks3(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / t
 // ---------------------------------------------------------------------------
 // launchers (called by the dimension-generic launchers when g.dim == 3)
 // ---------------------------------------------------------------------------
+// pass A of the two-pass rows on levels of at least this many faces (smaller
+// levels keep the inline form: there the extra launches cost more than the
+// gathers they save)
+constexpr int kLambMinFaces = 50000;
+
+size_t lamb3_scratch_bytes(const Geom& g, size_t tsize) {
+  return g.F < kLambMinFaces ? 0 : (size_t)(g.N + 1) * g.F * 5 * tsize;
+}
+
+// pass A into the scratch (AB4 slices then the Adv slices); false: inline form
 template <class T>
-void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                          cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs) {
+bool lamb3_pass_a(const Geom& g, CState<T> x, void* scratch, size_t bytes, cudaStream_t st, AB4<T>* ab,
+                  T** advb) {
+  if (!scratch || g.F < kLambMinFaces || bytes < lamb3_scratch_bytes(g, sizeof(T))) return false;
+  ab->plane = (size_t)(g.N + 1) * g.F;
+  T* base = reinterpret_cast<T*>(scratch);
+  for (int c = 0; c < 4; ++c) ab->p[c] = base + c * ab->plane;
+  *advb = base + 4 * ab->plane;
+  const int nfx = (g.nx + 1) * g.ny * g.nz, nfy = g.nx * (g.ny + 1) * g.nz, nfz = g.nx * g.ny * (g.nz + 1);
+  launch_pdl3(lamb3_terms_kernel<T, 0>, dim3(blocks3(nfx, 128), g.N + 1), dim3(128), 0, st, g, x.v, x.u, *ab, *advb);
+  launch_pdl3(lamb3_terms_kernel<T, 1>, dim3(blocks3(nfy, 128), g.N + 1), dim3(128), 0, st, g, x.v, x.u, *ab, *advb);
+  launch_pdl3(lamb3_terms_kernel<T, 2>, dim3(blocks3(nfz, 128), g.N + 1), dim3(128), 0, st, g, x.v, x.u, *ab, *advb);
+  return true;
+}
+
+template <class T>
+int launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                         cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs, void* lamb,
+                         size_t lamb_bytes) {
   const int n = g.F > g.C ? g.F : g.C;
-  launch_pdl3(nso_residual3_kernel<T>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out, sf, sr,
-              sq, rs, only_if_undone);
+  AB4<T> ab{};
+  T* advb = nullptr;
+  if (lamb3_pass_a(g, x, lamb, lamb_bytes, st, &ab, &advb)) {
+    launch_pdl3(nso_residual3_kernel<T, true>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
+                sf, sr, sq, rs, only_if_undone, ab, (const T*)advb);
+    return 4;
+  }
+  launch_pdl3(nso_residual3_kernel<T, false>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
+              sf, sr, sq, rs, only_if_undone, AB4<T>{}, (const T*)nullptr);
+  return 1;
 }
 
 size_t nso_residual3_blocks(const Geom& g) {
@@ -1279,13 +1462,21 @@ size_t nso_residual3_blocks(const Geom& g) {
 }
 
 template <class T>
-void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
-                                 cudaStream_t st, const double* only_if_undone) {
+int launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                cudaStream_t st, const double* only_if_undone, void* lamb, size_t lamb_bytes) {
   const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
   const int ncx = (g.nx - px + 1) / 2, ncy = (g.ny - py + 1) / 2, ncz = (g.nz - pz + 1) / 2;
   const int n = ncz * ncy * (g.nx + 1) + ncz * (g.ny + 1) * ncx + (g.nz + 1) * ncy * ncx + ncx * ncy * ncz;
-  launch_pdl3(nso_residual3_colour_kernel<T>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
-              px, py, pz, only_if_undone);
+  AB4<T> ab{};
+  T* advb = nullptr;
+  if (lamb3_pass_a(g, x, lamb, lamb_bytes, st, &ab, &advb)) {
+    launch_pdl3(nso_residual3_colour_kernel<T, true>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res,
+                out, px, py, pz, only_if_undone, ab, (const T*)advb);
+    return 4;
+  }
+  launch_pdl3(nso_residual3_colour_kernel<T, false>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res,
+              out, px, py, pz, only_if_undone, AB4<T>{}, (const T*)nullptr);
+  return 1;
 }
 
 size_t scgs3_smem_bytes(int N, size_t tsize) { return scgs3_cell_floats(N) * tsize; }
@@ -1406,10 +1597,10 @@ void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, 
 }
 
 #define STC3_INST_T(T)                                                                                         \
-  template void launch_nso_residual3<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
-                                        cudaStream_t, double*, const double*, RedScratch);                                \
-  template void launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,    \
-                                               cudaStream_t, const double*);                                  \
+  template int launch_nso_residual3<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,           \
+                                       cudaStream_t, double*, const double*, RedScratch, void*, size_t);       \
+  template int launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,     \
+                                              cudaStream_t, const double*, void*, size_t);                    \
   template void launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \
                                        const double*, void*);                                                 \
   template void launch_kkt_force_rhs3<T>(const Geom&, const T*, T*, cudaStream_t);                            \

@@ -1260,13 +1260,16 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 }
 
 template <class T>
-void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs) {
-  if (g.dim == 3) return launch_nso_residual3<T>(g, x, z, res, out, sf, sr, st, sq, only_if_undone, rs);
+int launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                        cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs, void* lamb,
+                        size_t lamb_bytes) {
+  if (g.dim == 3)
+    return launch_nso_residual3<T>(g, x, z, res, out, sf, sr, st, sq, only_if_undone, rs, lamb, lamb_bytes);
   const int tpb = 128;
   const int n = g.F > g.C ? g.F : g.C;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
   launch_pdl(nso_residual_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, sf, sr, sq, rs, only_if_undone);
+  return 1;
 }
 
 size_t nso_residual_blocks(const Geom& g) {
@@ -1278,15 +1281,16 @@ size_t nso_residual_blocks(const Geom& g) {
 int colour_extent(int n, int parity) { return (n - parity + 1) / 2; }
 
 template <class T>
-void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
-                                cudaStream_t st, const double* only_if_undone) {
-  if (g.dim == 3) return launch_nso_residual3_colour<T>(g, x, z, res, out, colour, st, only_if_undone);
+int launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                               cudaStream_t st, const double* only_if_undone, void* lamb, size_t lamb_bytes) {
+  if (g.dim == 3) return launch_nso_residual3_colour<T>(g, x, z, res, out, colour, st, only_if_undone, lamb, lamb_bytes);
   const int px = colour & 1, py = colour >> 1;
   const int nrx = colour_extent(g.ny, py), ncy = colour_extent(g.nx, px);
   const int n = nrx * (g.nx + 1) + (g.ny + 1) * ncy + colour_extent(g.nx, px) * nrx;
   const int tpb = 128;
   dim3 grid(blocks_for(n, tpb), g.N + 1);
   launch_pdl(nso_residual_colour_kernel<T>, grid, dim3(tpb), 0, st, g, x, z, res, out, px, py, only_if_undone);
+  return 1;
 }
 
 // the warp kernel's skewed layout for N blocks and cpb cells per CTA; cs is the
@@ -1487,10 +1491,10 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
 }
 
 #define STC_INST_T(T)                                                                                     \
-  template void launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,          \
-                                       cudaStream_t, double*, const double*, RedScratch);                  \
-  template void launch_nso_residual_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,     \
-                                              cudaStream_t, const double*);                                \
+  template int launch_nso_residual<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, T, T,           \
+                                      cudaStream_t, double*, const double*, RedScratch, void*, size_t);    \
+  template int launch_nso_residual_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,      \
+                                             cudaStream_t, const double*, void*, size_t);                 \
   template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
                                       const double*, void*);                                               \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \

@@ -137,6 +137,8 @@ struct stc_problem {
   void* dct = nullptr;            // 2D: DCT tables of the exact projection (project_dct_tables, state type)
   void* adv3 = nullptr;           // 3D sweeps: term buffers and grid-barrier words
   void* sc3 = nullptr;            // 3D SCGS: per-cell block Thomas records (finest level's size)
+  void* lamb3 = nullptr;          // 3D: two-pass residual scratch (finest level's size; large levels only)
+  size_t lamb3_bytes = 0;
   // forward simulation and its adjoint (allocated at their first use)
   void *sim_gu = nullptr, *sim_a0 = nullptr, *sim_l0 = nullptr, *sim_aN = nullptr, *sim_w1 = nullptr,
        *sim_w2 = nullptr, *sim_w3 = nullptr;
@@ -267,12 +269,13 @@ void check_launch(const char* what) { ck(cudaGetLastError(), what); }
 void nso_residual(stc_problem* P, int l, double sf, double sr, const FieldSet& res, const FieldSet& out,
                   cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr) {
   Level& L = P->lv[l];
+  int k = 0;
   dispatch(L.dbl, [&](auto tag) {
     using T = decltype(tag);
-    launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st,
-                           sq, only_if_undone, P->red);
+    k = launch_nso_residual<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(res), st_of<T>(out), T(sf), T(sr), st,
+                               sq, only_if_undone, P->red, P->lamb3, P->lamb3_bytes);
   });
-  count(P, 1);
+  count(P, k);
 }
 
 // `first_only_if_undone`: the residual in L.tmp is already current unless the
@@ -286,13 +289,15 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
       // f - res where this colour's cells read it, all from the pre-colour state
       const bool evr = timed && P->ev_used[1] < (int)P->ev_start[1].size();
       if (evr) ck(cudaEventRecordWithFlags(P->ev_start[1][P->ev_used[1]], st, cudaEventRecordExternal), "event");
+      int k = 0;
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
-        launch_nso_residual_colour<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(L.res), st_of<T>(L.tmp), c, st,
-                                      s == 0 && c == 0 ? first_only_if_undone : nullptr);
+        k = launch_nso_residual_colour<T>(L.g, cst_of<T>(L.x), (const T*)L.z, cst_of<T>(L.res), st_of<T>(L.tmp), c,
+                                          st, s == 0 && c == 0 ? first_only_if_undone : nullptr, P->lamb3,
+                                          P->lamb3_bytes);
       });
       if (evr) ck(cudaEventRecordWithFlags(P->ev_stop[1][P->ev_used[1]++], st, cudaEventRecordExternal), "event");
-      count(P, 1);
+      count(P, k);
       const bool ev = timed && P->ev_used[0] < (int)P->ev_start[0].size();
       if (ev) ck(cudaEventRecordWithFlags(P->ev_start[0][P->ev_used[0]], st, cudaEventRecordExternal), "event");
       dispatch(L.dbl, [&](auto tag) {
@@ -1163,6 +1168,7 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   if (g0.dim == 3) {
     total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts) +
              b(scgs3_thomas_scratch_bytes(g0, ts));
+    if (lamb3_scratch_bytes(g0, ts) > 0) total += b(lamb3_scratch_bytes(g0, ts));
   } else if (project_needs_scratch(g0, ts)) {
     total += b((N + 1) * project_smem(g0, ts));
   }
@@ -1546,6 +1552,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       P->pscratch = dalloc(P, project3_scratch_elems(g0, N + 1) * ts);
       P->adv3 = dalloc(P, advect3_scratch_bytes(g0, ts));
       P->sc3 = dalloc(P, scgs3_thomas_scratch_bytes(g0, P->dbl ? 8 : 4));
+      P->lamb3_bytes = lamb3_scratch_bytes(g0, ts);   // the finest level is the largest user
+      if (P->lamb3_bytes > 0) P->lamb3 = dalloc(P, P->lamb3_bytes);
     } else if (project_needs_scratch(g0, ts)) {
       P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));
     }

@@ -14,9 +14,9 @@ void set_last_error(const char* msg);
 // only_if_undone (optional, a guard's {before, after} norms): skip unless the
 // guarded coarse-grid correction was undone (after > before or NaN).
 template <class T>
-void launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                         cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr,
-                         RedScratch rs = RedScratch{});
+int launch_nso_residual(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                        cudaStream_t st, double* sq = nullptr, const double* only_if_undone = nullptr,
+                        RedScratch rs = RedScratch{}, void* lamb = nullptr, size_t lamb_bytes = 0);
 // blocks of a launch_nso_residual launch (the RedScratch capacity its sq needs)
 size_t nso_residual_blocks(const Geom& g);
 size_t nso_residual3_blocks(const Geom& g);
@@ -25,8 +25,9 @@ constexpr unsigned kReduceMaxBlocks = 1216;
 // out = f - res at the faces and cells one SCGS colour reads (other entries untouched);
 // only_if_undone as in launch_nso_residual
 template <class T>
-void launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
-                                cudaStream_t st, const double* only_if_undone = nullptr);
+int launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                               cudaStream_t st, const double* only_if_undone = nullptr, void* lamb = nullptr,
+                               size_t lamb_bytes = 0);
 // lm_dev (optional): device fp64 Levenberg-Marquardt shift of the v blocks, else g.lm;
 // scratch3 (3D, optional): scgs3_thomas_scratch_bytes of the finest level, which
 // lets large colours run the thread-per-cell block Thomas kernel
@@ -133,12 +134,17 @@ void launch_diff_sumsq(const T* a, const T* b, size_t n, double scale, double* o
 // --- 3D grid (nso3d_kernels.cu, advect3d_kernels.cu, poisson3d_kernels.cu) ---
 // Same contracts as the 2D launchers above; the generic launchers forward to
 // these when g.dim == 3.
+// lamb / lamb_bytes: scratch of the two-pass rows (lamb3_scratch_bytes; NULL:
+// the inline form).  Return the kernels launched.
 template <class T>
-void launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
-                          cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs);
+int launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, T sf, T sr,
+                         cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs, void* lamb,
+                         size_t lamb_bytes);
 template <class T>
-void launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
-                                 cudaStream_t st, const double* only_if_undone);
+int launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T> res, State<T> out, int colour,
+                                cudaStream_t st, const double* only_if_undone, void* lamb, size_t lamb_bytes);
+// bytes of the two-pass residual scratch of a 3D level (0: the level keeps the inline form)
+size_t lamb3_scratch_bytes(const Geom& g, size_t tsize);
 template <class T>
 void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                          const double* lm_dev, void* scratch);

@@ -183,6 +183,56 @@ def swirl_velocity3(nx, ny, nz, amplitude, centre=(0.5, 0.5, 0.5), width=0.25):
     return np.concatenate(out) * interior_face_mask3(nx, ny, nz)
 
 
+def _fftn(a):
+    try:
+        import scipy.fft
+        return scipy.fft.fftn(a, workers=-1)
+    except ImportError:
+        return np.fft.fftn(a)
+
+
+def _ifftn(a):
+    try:
+        import scipy.fft
+        return scipy.fft.ifftn(a, workers=-1)
+    except ImportError:
+        return np.fft.ifftn(a)
+
+
+def gaussian_random_faces3(nx, ny, nz, count, seed, corr_cells=8.0, amplitude=0.1):
+    """Seeded smooth random 3D face fields (count, F): per slab and face axis,
+    white noise filtered by a Gaussian of standard deviation corr_cells cells
+    (FFT, periodic), the whole set scaled to max |u| = amplitude, zero on wall
+    faces.  (Gradient parts are left in: every implicit step projects them
+    out.)"""
+    rng = np.random.default_rng(seed)
+    shapes = [(nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)]
+    out = np.zeros((count, face_count3(nx, ny, nz)))
+    for c in range(count):
+        parts = []
+        for shp in shapes:
+            w = rng.standard_normal(shp)
+            k = [np.fft.fftfreq(n) for n in shp]
+            K2 = sum(np.meshgrid(*[q * q for q in k], indexing="ij"))
+            filt = np.exp(-2.0 * (np.pi * corr_cells) ** 2 * K2)
+            parts.append(np.real(_ifftn(_fftn(w) * filt)).ravel())
+        out[c] = np.concatenate(parts)
+    out *= interior_face_mask3(nx, ny, nz)[None]
+    return out * (amplitude / np.max(np.abs(out)))
+
+
+def config_autograd(n=128, N=48, seed=5005):
+    """The differentiable-simulation workload: n^3 cells, N steps, dt = 1/N;
+    initial density a Gaussian ball (sigma 0.1) at (0.5, 0.35, 0.5); forces a
+    seeded smooth random field (correlation length 8 cells, max |u| = 0.1);
+    target rho* a seeded union of ellipsoids blurred by one cell, mass-matched."""
+    rho0 = gaussian_ball3(n, n, n, (0.5, 0.35, 0.5), 0.1)
+    rng = np.random.default_rng(seed)
+    star = ellipsoid_union(n, n, n, int(rng.integers(0, 2**31 - 1)), rho0.sum(), 1.0)
+    u = gaussian_random_faces3(n, n, n, N, int(rng.integers(0, 2**31 - 1)), 8.0, 0.1)
+    return dict(nx=n, ny=n, nz=n, N=N, dt=1.0 / N, rho0=rho0, star=star, u=u)
+
+
 def config_small(n=32, N=16):
     """2D, n^2 cells, N steps, dt = 1/N: ball (sigma 0.08) at (0.5, 0.3) to the
     same ball at (0.5, 0.7) at t = T, zero initial velocity, r = 1e-3."""

@@ -97,3 +97,45 @@ def test_checkpointed_segments_give_the_same_gradient(nz):
     np.testing.assert_allclose(r2, r1, rtol=0, atol=1e-12 * np.max(np.abs(r1)))
     assert np.linalg.norm(g2 - g1) <= 1e-9 * np.linalg.norm(g1)
     simc.close()
+
+
+def test_full_size_gradient_against_central_differences_128cubed():
+    """The differentiable-simulation workload at size: 128^3 cells, 48 steps,
+    fp32, checkpoint-and-recompute every 8 steps, smooth seeded random forces
+    (correlation length 8 cells, max |u| = 0.1), loss 1/2 ||rho_N - rho*||^2 to
+    a blurred ellipsoid union.  The gradient from the adjoint backward pass
+    against central differences of the same map on 16 seeded random
+    directions (each a smooth random field like u times seeded per-step
+    weights, so that the differences stay where the map is smooth); the
+    checkpointed forward pass keeps 6 segment starts instead of 48 steps."""
+    from paper_1608_01102_gb300 import autograd
+    cfg = workloads.config_autograd(128, 48)
+    n, N = 128, 48
+    sim = autograd.Simulation(n, n, N, cfg["rho0"], nz=n, precision=0, checkpoint_every=8)
+    assert len(sim.segments) == 6
+    u = cfg["u"]
+    loss, g, rho = _loss_and_grad(sim, u, cfg["star"])
+    assert np.isfinite(loss) and np.all(np.isfinite(g))
+    assert np.max(np.abs(rho[-1] - cfg["rho0"])) > 1e-3       # the forces move the density
+    errs = []
+    for k in range(16):
+        f = workloads.gaussian_random_faces3(n, n, n, 1, 7000 + k, 8.0, 0.1)[0]
+        d = np.random.default_rng(7100 + k).standard_normal(N)[:, None] * f[None]
+        eps = 0.05
+        lp = _loss_and_grad_value(sim, u + eps * d, cfg["star"])
+        lm = _loss_and_grad_value(sim, u - eps * d, cfg["star"])
+        fd = (lp - lm) / (2 * eps)
+        an = float(np.sum(g * d))
+        errs.append(abs(fd - an) / max(abs(an), 1e-30))
+    errs = np.array(errs)
+    assert np.median(errs) < 1e-2 and np.max(errs) < 5e-2, errs
+    sim.close()
+
+
+def _loss_and_grad_value(sim, u, star):
+    from paper_1608_01102_gb300 import autograd
+    with torch.no_grad():
+        ut = torch.tensor(u, dtype=sim.dtype, device="cuda")
+        rho = autograd.simulate(ut, sim)
+        st = torch.tensor(star, dtype=sim.dtype, device="cuda")
+        return float(0.5 * ((rho[-1] - st) ** 2).sum())

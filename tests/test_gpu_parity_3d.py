@@ -149,8 +149,10 @@ def test_adjoint_sweep_3d(prec, shape, N, levels):
 # a4: NSO residual f on every level
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", PREC)
-@pytest.mark.parametrize("shape,N", [((8, 8, 8), 3), ((12, 8, 8), 2)])
+@pytest.mark.parametrize("shape,N", [((8, 8, 8), 3), ((12, 8, 8), 2), ((32, 32, 32), 2), ((40, 32, 24), 2)])
 def test_nso_residual_3d_all_levels(prec, shape, N):
+    """Levels of at least 50000 faces (32^3, 40 x 32 x 24) take the two-pass
+    form (the Lamb-vector products stored per face, then gathered)."""
     nx, ny, nz = shape
     P, G = make_pair3(nx, ny, nz, N, precision=prec)
     grids = stfas.hierarchy(P)
