@@ -394,6 +394,8 @@ def measure_step(stc, workloads, name, args, dev, world, with_e2e=True):
     out["vcycle_only"] = {"ms": statistics.median(vt), "value": n * n * (nz or 1) * N / (statistics.median(vt) * 1e-3),
                           "unit": "cells/s"}
 
+    out["sweeps"] = sweep_rooflines(G, stream, flush, n, nz, N, dim, peak, peak_kind)
+
     if with_e2e:
         # end to end through the public API with host buffers: keyframes up, forces down
         h2d = sum(a.nbytes for a, _ in keys.values())
@@ -409,6 +411,42 @@ def measure_step(stc, workloads, name, args, dev, world, with_e2e=True):
         out["e2e"] = {"value": world * cells / (sum(e2e_times) / len(e2e_times)), "unit": "cells/s",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     G.close()
+    return out
+
+
+def sweep_rooflines(G, stream, flush, n, nz, N, dim, peak, peak_kind):
+    """Achieved HBM bandwidth of the AO sweeps at the problem's current v*: the
+    Taylor forward sweep (Eq. Adv; per step read rho_i and v_i, write rho_{i+1}:
+    (2 + d) C floats), the backward adjoint sweep (Eq. KKTPO; per step read
+    rho_i, mu_i, v_i, the fp64 metric term, w_i, write mu_{i-1} and y_i: (4 + 3d)
+    C floats) and the projection Q of the N - 1 fields y_1..y_{N-1} (read and
+    write each field, 2F floats; the Poisson solve inside is not counted).
+    CUDA events on the problem's stream, L2 flushed before each, median of 3."""
+    import torch
+    C = n * n * (nz or 1)
+    F = G.field_shape("V")[1]
+    legs = {"taylor_forward": (lambda: G.advect("VSTAR"), 4.0 * N * C * (2 + dim)),
+            "adjoint": (lambda: G.adjoint("VSTAR", 1.0, 1.0), 4.0 * N * C * (4 + 3 * dim)),
+            "projection": (lambda: G.project("Y", 1, N - 1), 4.0 * (N - 1) * 2 * F)}
+    G.advect("VSTAR")
+    G.metric_terms()
+    out = {}
+    for name, (fn, nbytes) in legs.items():
+        ts = []
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "peak_kind": peak_kind}
     return out
 
 
@@ -589,7 +627,7 @@ def run_native(args, rank, world, local_rank):
                        "l2": "256 MiB buffer written between timed steps (outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": m["roofline"], "e2e": m.get("e2e"), "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
-            "vcycle_only": m["vcycle_only"], "kernels": m["kernels"]}
+            "vcycle_only": m["vcycle_only"], "kernels": m["kernels"], "sweeps": m["sweeps"]}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if solo:
@@ -604,7 +642,7 @@ def run_native(args, rank, world, local_rank):
     if solo and not args.no_secondary:
         m2 = measure_step(stc, workloads, other, args, dev, world, with_e2e=not args.no_e2e)
         sec = {k: m2.get(k) for k in ("value", "ms_per_step", "roofline", "kernels", "vcycle_only", "e2e", "clocks",
-                                      "gpu_launches", "workload")}
+                                      "gpu_launches", "workload", "sweeps")}
         if cpu2 is not None:
             sec["cpu_baseline"] = cpu2
         line["letters" if other == "letters" else "3d"] = sec

@@ -23,8 +23,10 @@
  * child nodes; the instantiated graph is reused while the resident set stays
  * the same), then the KKT/update tail of problems whose NSO solve ended, and
  * retires finished problems, returning their memory at once -- continuous
- * batching at V-cycle granularity.  All stepped work runs on one stream
- * (stc_server_params.stream).
+ * batching at V-cycle granularity.  A server-created problem has its own
+ * stream, and the heads and tails of different problems run concurrently
+ * (one host thread each), so their sweeps overlap on the device; the batched
+ * launches run on stc_server_params.stream.
  *
  * Threading: every stc_server_* call is safe from any host thread (stepped
  * steps are serialised).  Results are copied to host memory owned by the
@@ -55,8 +57,8 @@ typedef struct {
   int device;          /* CUDA device of the GPU backend                                */
   int max_bypass;      /* times a queued request may be passed over by later ones (8)  */
   int mode;            /* 0 (default): worker threads; 1: stepped (stc_server_step)    */
-  void* stream;        /* mode 1: CUDA stream of every problem and of the batched
-                          launches (NULL = legacy default stream)                     */
+  void* stream;        /* mode 1: CUDA stream of the batched launches (NULL = legacy
+                          default stream)                                             */
   int max_resident;    /* mode 1: problems solving at once (16)                         */
   double kkt_rel_tol;  /* mode 1: stopping tolerance of problems submitted with
                           stc_server_submit_problem (1e-4)                            */
@@ -104,8 +106,9 @@ stc_status stc_server_create(const stc_server_params* sp, stc_server** out);
 /* Queues a request.  STC_ERR_INVALID_ARG for malformed requests and
  * STC_ERR_OOM when the request alone exceeds the budget (never admissible). */
 stc_status stc_server_submit(stc_server* s, const stc_request* rq, long long* ticket);
-/* Mode 1: queues a problem the caller created (on the server's stream, with
- * its keyframes set), solved with the server's kkt_rel_tol and max_admm.  Its
+/* Mode 1: queues a problem the caller created (on any stream of the server's
+ * device, with its keyframes set), solved with the server's kkt_rel_tol and
+ * max_admm.  Its
  * admission size is stc_memory_bytes(problem) (already allocated: the budget
  * bounds how many problems solve at once).  The server does not destroy it;
  * the caller must not use it until the ticket is finished.  STC_ERR_INVALID_ARG

@@ -54,20 +54,90 @@ __device__ __forceinline__ T row3(const Geom& g, const CState<T>& x, int t, int 
 // u_{t-1} and Adv(v_t) = O1 V1 - O2 V2; pass B (the residual kernels with
 // AB = true) gathers them.  Same sums in the same order as the inline form.
 // ---------------------------------------------------------------------------
-// the four products as planes (alpha1, alpha2, beta1, beta2), each (N+1) x F:
-// a gather reads one product of a face, so separate planes keep a warp's
-// loads to the sectors it uses
+// the four products of a face in one 16- (fp32) or 32-byte (fp64) record:
+// the gathers of row 1 often take two products of the same face (measured:
+// records beat four separate planes, 1.25 against 1.33 ms per colour residual)
 template <class T>
-struct AB4 {
-  T* p[4];
-  size_t plane;   // (N + 1) F
+struct alignas(4 * sizeof(T)) AB4 {
+  T a1, a2, b1, b2;
 };
+
+// Terms (O1, V1, O2, V2) of an interior face of the closed box from its base
+// indices and fixed strides: the same loads, differences and sums in the same
+// order as terms_x / terms_y / terms_z of grid3d.cuh, without re-deriving every
+// neighbour's index (pass A was bound by that integer arithmetic).  Axes are
+// cyclic: for an a-face, b = a+1 and c = a+2; O1 is the mean of the two
+// omega_b edges at offsets 0 and +1 along c, V1 the mean of the four c-faces
+// at offsets (0, -1 along a) x (0, +1 along c); O2, V2 the same with b, c
+// swapped.  lo_c / hi_c: the edge at offset 0 / +1 along c lies in a wall.
+__device__ __forceinline__ void box_strides(const Geom& g, int st[3][3]) {
+  st[0][0] = 1; st[0][1] = g.nx + 1; st[0][2] = (g.nx + 1) * g.ny;
+  st[1][0] = 1; st[1][1] = g.nx;     st[1][2] = g.nx * (g.ny + 1);
+  st[2][0] = 1; st[2][1] = g.nx;     st[2][2] = g.nx * g.ny;
+}
+
+// omega_b on the edge between faces f_a (axis a) and f_c (axis c) at base
+// indices fa, fc, as in wx/wy/wz: (v_a(+0) - v_a(-1 along c)) - (v_c(+0) - v_c(-1 along a)),
+// with the sign convention of the component b = a+1
+template <class T, int A>
+__device__ __forceinline__ T edge_b(const T* v, int fa, int fc, int sa_c, int sc_a, T ih) {
+  // A = 0: omega_y = (x(k) - x(k-1)) - (z(i) - z(i-1));  A = 1: omega_z = (y(i) - y(i-1)) - (x(j) - x(j-1));
+  // A = 2: omega_x = (z(j) - z(j-1)) - (y(k) - y(k-1))
+  const T a = ld(v + fa) - ld(v + fa - sa_c);
+  const T b = ld(v + fc) - ld(v + fc - sc_a);
+  return (a - b) * ih;
+}
+
+// omega_c on the edge between faces f_b and f_a, as in wx/wy/wz:
+// (v_b(+0) - v_b(-1 along a)) - (v_a(+0) - v_a(-1 along b))
+template <class T>
+__device__ __forceinline__ T edge_c(const T* v, int fb, int fa, int sb_a, int sa_b, T ih) {
+  const T a = ld(v + fb) - ld(v + fb - sb_a);
+  const T b = ld(v + fa) - ld(v + fa - sa_b);
+  return (a - b) * ih;
+}
+
+// mean of the four faces f + {-sa, 0} x {0, +sp} in the summation order of
+// grid3d.cuh: FIRST_A lists both offsets along a at the first +sp offset
+// before the second (terms_x), otherwise both +sp offsets at -sa first
+template <class T, bool FIRST_A>
+__device__ __forceinline__ T mean4(const T* v, int f, int sa, int sp) {
+  if (FIRST_A) return T(0.25) * (ld(v + f - sa) + ld(v + f) + ld(v + f + sp - sa) + ld(v + f + sp));
+  return T(0.25) * (ld(v + f - sa) + ld(v + f - sa + sp) + ld(v + f) + ld(v + f + sp));
+}
+
+template <class T, int A>
+__device__ __forceinline__ Terms<T> terms_box(const Geom& g, const T* v, int k, int j, int i) {
+  constexpr int B = (A + 1) % 3, C = (A + 2) % 3;
+  int st[3][3];
+  box_strides(g, st);
+  const int c3[3] = {i, j, k};
+  const int n3[3] = {g.nx, g.ny, g.nz};
+  const int fa = A == 0 ? xf(g, k, j, i) : (A == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
+  const int fb = B == 0 ? xf(g, k, j, i) : (B == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
+  const int fc = C == 0 ? xf(g, k, j, i) : (C == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
+  const T ih = pick<T>(g.ih, g.ihf);
+  Terms<T> t;
+  // O1: omega_b edges at offsets 0 and +1 along c (a wall edge when the c coordinate is 0 or n_c)
+  const T w0 = c3[C] > 0 ? edge_b<T, A>(v, fa, fc, st[A][C], st[C][A], ih) : T(0);
+  const T w1 = c3[C] + 1 < n3[C] ? edge_b<T, A>(v, fa + st[A][C], fc + st[C][C], st[A][C], st[C][A], ih) : T(0);
+  t.o1 = T(0.5) * (w0 + w1);
+  // V1: c-faces at (a: -1, 0) x (c: 0, +1)
+  t.v1 = mean4<T, A == 0>(v, fc, st[C][A], st[C][C]);
+  // O2: omega_c edges at offsets 0 and +1 along b
+  const T q0 = c3[B] > 0 ? edge_c<T>(v, fb, fa, st[B][A], st[A][B], ih) : T(0);
+  const T q1 = c3[B] + 1 < n3[B] ? edge_c<T>(v, fb + st[B][B], fa + st[A][B], st[B][A], st[A][B], ih) : T(0);
+  t.o2 = T(0.5) * (q0 + q1);
+  // V2: b-faces at (a: -1, 0) x (b: 0, +1)
+  t.v2 = mean4<T, A != 2>(v, fb, st[B][A], st[B][B]);
+  return t;
+}
 
 // pass A: faces of one axis at times t = 0..N (blockIdx.y); AB4 of v_t with
 // u_{t-1} for t >= 1, Adv(v_t); zero on slots that are not interior faces
 template <class T, int AXIS>
 __global__ void __launch_bounds__(128) lamb3_terms_kernel(Geom g, const T* __restrict__ v, const T* __restrict__ u,
-                                                          AB4<T> ab, T* __restrict__ advb) {
+                                                          AB4<T>* __restrict__ ab, T* __restrict__ advb) {
   pdl_wait();
   const int t = blockIdx.y;
   const int n0 = AXIS == 0 ? g.nx + 1 : g.nx, n1 = AXIS == 1 ? g.ny + 1 : g.ny;
@@ -77,53 +147,52 @@ __global__ void __launch_bounds__(128) lamb3_terms_kernel(Geom g, const T* __res
   const int i = e % n0, r = e / n0, j = r % n1, k = r / n1;
   const int f = (AXIS == 0 ? 0 : (AXIS == 1 ? g.Fx : g.Fxy)) + e;
   const size_t at = (size_t)t * g.F + f;
-  T o[4] = {T(0), T(0), T(0), T(0)};
+  AB4<T> o{T(0), T(0), T(0), T(0)};
   T a = T(0);
   if (interior(g, AXIS, k, j, i)) {
-    const Terms<T> tm = terms<T, T>(g, v + (size_t)t * g.F, AXIS, k, j, i);
+    const Terms<T> tm = g.periodic ? terms<T, T>(g, v + (size_t)t * g.F, AXIS, k, j, i)
+                                   : terms_box<T, AXIS>(g, v + (size_t)t * g.F, k, j, i);
     a = tm.o1 * tm.v1 - tm.o2 * tm.v2;
     if (t >= 1) {
       const T uf = ld(u + (size_t)(t - 1) * g.F + f);
-      o[0] = tm.v1 * uf;
-      o[1] = -tm.v2 * uf;
-      o[2] = tm.o1 * uf;
-      o[3] = -tm.o2 * uf;
+      o.a1 = tm.v1 * uf;
+      o.a2 = -tm.v2 * uf;
+      o.b1 = tm.o1 * uf;
+      o.b2 = -tm.o2 * uf;
     }
   }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) ab.p[c][at] = o[c];
+  ab[at] = o;
   advb[at] = a;
 }
 
 // one product of the face (axis, k, j, i) of slice t, zero off the interior faces
-// the planes of one time slice
+// the records of one time slice
 template <class T>
-struct ABt {
-  const T* p[4];
-};
+using ABt = const AB4<T>*;
 
 template <class T, int C>
-__device__ __forceinline__ T abv(const Geom& g, const ABt<T>& abt, int axis, int k, int j, int i) {
+__device__ __forceinline__ T abv(const Geom& g, ABt<T> abt, int axis, int k, int j, int i) {
   if (!interior(g, axis, k, j, i)) return T(0);
   const int f = axis == 0 ? xf(g, k, j, i) : (axis == 1 ? yf(g, k, j, i) : zf(g, k, j, i));
-  return ld(abt.p[C] + f);
+  const AB4<T> q = abt[f];
+  return C == 0 ? q.a1 : (C == 1 ? q.a2 : (C == 2 ? q.b1 : q.b2));
 }
 
 // the edge sums Q from stored products (the same sums as qx, qy, qz)
 template <class T>
-__device__ __forceinline__ T qx_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+__device__ __forceinline__ T qx_ab(const Geom& g, ABt<T> a, int k, int j, int i) {
   if (!g.periodic && (j <= 0 || j >= g.ny || k <= 0 || k >= g.nz)) return T(0);
   return T(0.5) * (abv<T, 1>(g, a, 1, k, j, i) + abv<T, 1>(g, a, 1, k - 1, j, i) + abv<T, 0>(g, a, 2, k, j, i) +
                    abv<T, 0>(g, a, 2, k, j - 1, i));
 }
 template <class T>
-__device__ __forceinline__ T qy_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+__device__ __forceinline__ T qy_ab(const Geom& g, ABt<T> a, int k, int j, int i) {
   if (!g.periodic && (i <= 0 || i >= g.nx || k <= 0 || k >= g.nz)) return T(0);
   return T(0.5) * (abv<T, 0>(g, a, 0, k, j, i) + abv<T, 0>(g, a, 0, k - 1, j, i) + abv<T, 1>(g, a, 2, k, j, i) +
                    abv<T, 1>(g, a, 2, k, j, i - 1));
 }
 template <class T>
-__device__ __forceinline__ T qz_ab(const Geom& g, const ABt<T>& a, int k, int j, int i) {
+__device__ __forceinline__ T qz_ab(const Geom& g, ABt<T> a, int k, int j, int i) {
   if (!g.periodic && (i <= 0 || i >= g.nx || j <= 0 || j >= g.ny)) return T(0);
   return T(0.5) * (abv<T, 1>(g, a, 0, k, j, i) + abv<T, 1>(g, a, 0, k, j - 1, i) + abv<T, 0>(g, a, 1, k, j, i) +
                    abv<T, 0>(g, a, 1, k, j, i - 1));
@@ -131,7 +200,7 @@ __device__ __forceinline__ T qz_ab(const Geom& g, const ABt<T>& a, int k, int j,
 
 // (dAdv/dv)^T u at an interior face from stored products (the order of jtu)
 template <class T>
-__device__ T jtu_ab(const Geom& g, const ABt<T>& a, int axis, int k, int j, int i) {
+__device__ T jtu_ab(const Geom& g, ABt<T> a, int axis, int k, int j, int i) {
   const T ih = pick<T>(g.ih, g.ihf);
   if (axis == 0) {
     const T r = (qy_ab(g, a, k, j, i) - qy_ab(g, a, k + 1, j, i) - qz_ab(g, a, k, j, i) + qz_ab(g, a, k, j + 1, i)) *
@@ -158,17 +227,13 @@ __device__ T jtu_ab(const Geom& g, const ABt<T>& a, int axis, int k, int j, int 
 
 // rows 1 and 3 from the stored products (AB) or inline
 template <class T, bool AB>
-__device__ __forceinline__ T row1x(const Geom& g, const CState<T>& x, const T* __restrict__ z, const AB4<T>& ab,
+__device__ __forceinline__ T row1x(const Geom& g, const CState<T>& x, const T* __restrict__ z, ABt<T> ab,
                                    int t, int e, int axis, int k, int j, int i) {
   if (!AB) return row1(g, x, z, t, e, axis, k, j, i);
   const T* vt = x.v + (size_t)t * g.F;
   const T* pb = x.pbar + (size_t)t * g.C;
   T val = ld(x.u + (size_t)(t - 1) * g.F + e) * pick<T>(g.idt, g.idtf);
-  if (g.self_adv) {
-    const size_t o = (size_t)t * g.F;
-    const ABt<T> a{{ab.p[0] + o, ab.p[1] + o, ab.p[2] + o, ab.p[3] + o}};
-    val += jtu_ab(g, a, axis, k, j, i);
-  }
+  if (g.self_adv) val += jtu_ab(g, ab + (size_t)t * g.F, axis, k, j, i);
   val += grad(g, pb, axis, k, j, i);
   if (t < g.N) {
     const T* ut = x.u + (size_t)t * g.F;
@@ -193,7 +258,7 @@ __device__ __forceinline__ T row3x(const Geom& g, const CState<T>& x, const T* a
 template <class T, bool AB>
 __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res, State<T> out,
                                      T sf, T sr, double* sq, RedScratch rs, const double* only_if_undone,
-                                     AB4<T> ab, const T* __restrict__ advb) {
+                                     const AB4<T>* __restrict__ ab, const T* __restrict__ advb) {
   pdl_wait();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
@@ -251,7 +316,7 @@ __global__ void nso_residual3_kernel(Geom g, CState<T> x, const T* __restrict__ 
 template <class T, bool AB>
 __global__ void nso_residual3_colour_kernel(Geom g, CState<T> x, const T* __restrict__ z, CState<T> res,
                                             State<T> out, int px, int py, int pz, const double* only_if_undone,
-                                            AB4<T> ab, const T* __restrict__ advb) {
+                                            const AB4<T>* __restrict__ ab, const T* __restrict__ advb) {
   pdl_wait();
   const int t = blockIdx.y;
   if (t > g.N) return;
@@ -1425,13 +1490,11 @@ size_t lamb3_scratch_bytes(const Geom& g, size_t tsize) {
 
 // pass A into the scratch (AB4 slices then the Adv slices); false: inline form
 template <class T>
-bool lamb3_pass_a(const Geom& g, CState<T> x, void* scratch, size_t bytes, cudaStream_t st, AB4<T>* ab,
+bool lamb3_pass_a(const Geom& g, CState<T> x, void* scratch, size_t bytes, cudaStream_t st, AB4<T>** ab,
                   T** advb) {
   if (!scratch || g.F < kLambMinFaces || bytes < lamb3_scratch_bytes(g, sizeof(T))) return false;
-  ab->plane = (size_t)(g.N + 1) * g.F;
-  T* base = reinterpret_cast<T*>(scratch);
-  for (int c = 0; c < 4; ++c) ab->p[c] = base + c * ab->plane;
-  *advb = base + 4 * ab->plane;
+  *ab = reinterpret_cast<AB4<T>*>(scratch);
+  *advb = reinterpret_cast<T*>(*ab + (size_t)(g.N + 1) * g.F);
   const int nfx = (g.nx + 1) * g.ny * g.nz, nfy = g.nx * (g.ny + 1) * g.nz, nfz = g.nx * g.ny * (g.nz + 1);
   launch_pdl3(lamb3_terms_kernel<T, 0>, dim3(blocks3(nfx, 128), g.N + 1), dim3(128), 0, st, g, x.v, x.u, *ab, *advb);
   launch_pdl3(lamb3_terms_kernel<T, 1>, dim3(blocks3(nfy, 128), g.N + 1), dim3(128), 0, st, g, x.v, x.u, *ab, *advb);
@@ -1444,15 +1507,15 @@ int launch_nso_residual3(const Geom& g, CState<T> x, const T* z, CState<T> res, 
                          cudaStream_t st, double* sq, const double* only_if_undone, RedScratch rs, void* lamb,
                          size_t lamb_bytes) {
   const int n = g.F > g.C ? g.F : g.C;
-  AB4<T> ab{};
+  AB4<T>* ab = nullptr;
   T* advb = nullptr;
   if (lamb3_pass_a(g, x, lamb, lamb_bytes, st, &ab, &advb)) {
     launch_pdl3(nso_residual3_kernel<T, true>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
-                sf, sr, sq, rs, only_if_undone, ab, (const T*)advb);
+                sf, sr, sq, rs, only_if_undone, (const AB4<T>*)ab, (const T*)advb);
     return 4;
   }
   launch_pdl3(nso_residual3_kernel<T, false>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res, out,
-              sf, sr, sq, rs, only_if_undone, AB4<T>{}, (const T*)nullptr);
+              sf, sr, sq, rs, only_if_undone, (const AB4<T>*)nullptr, (const T*)nullptr);
   return 1;
 }
 
@@ -1467,15 +1530,15 @@ int launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T
   const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
   const int ncx = (g.nx - px + 1) / 2, ncy = (g.ny - py + 1) / 2, ncz = (g.nz - pz + 1) / 2;
   const int n = ncz * ncy * (g.nx + 1) + ncz * (g.ny + 1) * ncx + (g.nz + 1) * ncy * ncx + ncx * ncy * ncz;
-  AB4<T> ab{};
+  AB4<T>* ab = nullptr;
   T* advb = nullptr;
   if (lamb3_pass_a(g, x, lamb, lamb_bytes, st, &ab, &advb)) {
     launch_pdl3(nso_residual3_colour_kernel<T, true>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res,
-                out, px, py, pz, only_if_undone, ab, (const T*)advb);
+                out, px, py, pz, only_if_undone, (const AB4<T>*)ab, (const T*)advb);
     return 4;
   }
   launch_pdl3(nso_residual3_colour_kernel<T, false>, dim3(blocks3(n, 128), g.N + 1), dim3(128), 0, st, g, x, z, res,
-              out, px, py, pz, only_if_undone, AB4<T>{}, (const T*)nullptr);
+              out, px, py, pz, only_if_undone, (const AB4<T>*)nullptr, (const T*)nullptr);
   return 1;
 }
 

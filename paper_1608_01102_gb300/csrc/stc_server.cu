@@ -10,6 +10,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <future>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -40,6 +41,7 @@ struct Request {
   std::vector<double> forces;
   stc_problem* p = nullptr;   // stepped mode: the resident problem
   bool owned = true;          // false: submitted by the caller (stc_server_submit_problem)
+  cudaStream_t st = nullptr;  // stepped mode: the stream of a server-created problem
 };
 
 }  // namespace
@@ -176,6 +178,10 @@ void finish_stepped(stc_server* s, Request* r, stc_status status) {
     if (r->owned) stc_destroy_problem(r->p);
     r->p = nullptr;
   }
+  if (r->st) {
+    cudaStreamDestroy(r->st);
+    r->st = nullptr;
+  }
   std::lock_guard<std::mutex> lock(s->mu);
   s->in_use -= r->bytes;
   s->running--;
@@ -189,6 +195,24 @@ size_t face_count(const stc_params& prm) {
     return (size_t)prm.nz * prm.ny * (prm.nx + 1) + (size_t)prm.nz * (prm.ny + 1) * prm.nx +
            (size_t)(prm.nz + 1) * prm.ny * prm.nx;
   return (size_t)prm.ny * (prm.nx + 1) + (size_t)(prm.ny + 1) * prm.nx;
+}
+
+// f(r) for every resident request, one host thread each (a problem is used by
+// one thread at a time; different problems may be driven concurrently); the
+// failures are appended to `failed`
+template <class F>
+void run_parallel(stc_server* s, F&& f, std::vector<std::pair<Request*, stc_status>>& failed) {
+  std::vector<std::pair<Request*, std::future<stc_status>>> jobs;
+  for (Request* r : s->resident) {
+    bool done = false;
+    for (auto& fl : failed) done = done || fl.first == r;
+    if (!done) jobs.emplace_back(r, std::async(std::launch::async, [&f, r] { return f(r); }));
+  }
+  std::vector<stc_status> st(jobs.size());
+  for (size_t k = 0; k < jobs.size(); ++k) st[k] = jobs[k].second.get();
+  // (the jobs read `failed`: it grows only once all of them have finished)
+  for (size_t k = 0; k < jobs.size(); ++k)
+    if (st[k] != STC_OK) failed.emplace_back(jobs[k].first, st[k]);
 }
 
 // One serving step: admission, the heads (Alg. 1) of problems whose ADMM
@@ -215,7 +239,16 @@ stc_status step_stepped(stc_server* s, int* active) {
   for (Request* r : admitted) {
     stc_status st = STC_OK;
     if (!r->p) {
-      st = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), s->sp.stream, &r->p);
+      // each server-created problem has its own stream, so that the heads and
+      // tails of different problems overlap on the device
+      if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        r->st = nullptr;
+        stc::set_last_error("could not create a stream for the request");
+        finish_stepped(s, r, STC_ERR_CUDA);
+        continue;
+      }
+      st = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), r->st, &r->p);
       if (st == STC_OK && !r->steps.empty())
         st = stc_set_keyframes(r->p, (int)r->steps.size(), r->steps.data(), r->stars.data(), r->cs.data());
     }
@@ -234,13 +267,11 @@ stc_status step_stepped(stc_server* s, int* active) {
     stc_solve_phase(r->p, &ph, wants);
     return ph;
   };
-  for (Request* r : s->resident) {
+  // heads (Alg. 1) of the problems whose ADMM iteration begins, concurrently
+  run_parallel(s, [&](Request* r) {
     int w = 0;
-    if (phase(r, &w) == 0) {
-      const stc_status st = stc_solve_head(r->p);
-      if (st != STC_OK) failed.emplace_back(r, st);
-    }
-  }
+    return phase(r, &w) == 0 ? stc_solve_head(r->p) : STC_OK;
+  }, failed);
   std::vector<stc_problem*> probs;
   std::vector<Request*> owners;
   for (Request* r : s->resident) {
@@ -256,6 +287,11 @@ stc_status step_stepped(stc_server* s, int* active) {
     for (size_t k = 0; k < probs.size(); ++k)
       if (b != STC_OK || sts[k] != STC_OK) failed.emplace_back(owners[k], b != STC_OK ? b : sts[k]);
   }
+  // tails (KKT metric, multiplier update, stopping tests) of finished NSO solves, concurrently
+  run_parallel(s, [&](Request* r) {
+    int w = 0;
+    return failed_status(r) == STC_OK && phase(r, &w) == 1 && !w ? stc_solve_tail(r->p) : STC_OK;
+  }, failed);
   std::vector<Request*> keep;
   for (Request* r : s->resident) {
     if (failed_status(r) != STC_OK) {
@@ -263,13 +299,6 @@ stc_status step_stepped(stc_server* s, int* active) {
       continue;
     }
     int w = 0;
-    if (phase(r, &w) == 1 && !w) {
-      const stc_status st = stc_solve_tail(r->p);
-      if (st != STC_OK) {
-        finish_stepped(s, r, st);
-        continue;
-      }
-    }
     if (phase(r, &w) == 2) {
       int conv = 0;
       stc_solve_report(r->p, &r->info.report, &conv);

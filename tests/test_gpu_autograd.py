@@ -139,3 +139,35 @@ def _loss_and_grad_value(sim, u, star):
         rho = autograd.simulate(ut, sim)
         st = torch.tensor(star, dtype=sim.dtype, device="cuda")
         return float(0.5 * ((rho[-1] - st) ** 2).sum())
+
+
+GOLDEN32 = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                      "golden", "autograd_32cubed.npz")
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_gradient_matches_the_oracle_at_32cubed(precision):
+    """The autograd map at 32^3 (the differentiable-simulation recipe, 2 steps
+    of dt = 1/48) against the fp64 oracle's Newton-solved chain and adjoint
+    (tests/golden/make_autograd_32.py): the loss, ||g|| and g's projections
+    on 32 seeded random directions.  For an error e of g, a projection on a
+    direction of independent unit normals is distributed as N(0, ||e||^2), so
+    each projection must agree within 4 tol ||g||."""
+    import os
+    from paper_1608_01102_gb300 import autograd
+    if not os.path.exists(GOLDEN32):
+        pytest.skip("tests/golden/autograd_32cubed.npz has not been written")
+    ref = np.load(GOLDEN32)
+    n, N = 32, 2
+    cfg = workloads.config_autograd(n, N)
+    sim = autograd.Simulation(n, n, N, cfg["rho0"], nz=n, dt=1.0 / 48, precision=precision)
+    m = workloads.interior_face_mask3(n, n, n)
+    loss, g, _ = _loss_and_grad(sim, cfg["u"] * m, cfg["star"])
+    tol = 1e-5 if precision == 1 else 2e-3
+    gn = float(ref["gnorm"])
+    assert abs(loss - float(ref["loss"])) <= tol * float(ref["loss"])
+    assert abs(np.linalg.norm(g * m) - gn) <= tol * gn
+    for k in range(len(ref["proj"])):
+        d = np.random.default_rng(9000 + k).standard_normal(g.shape) * m
+        assert abs(float(np.sum(g * d)) - float(ref["proj"][k])) <= 4 * tol * gn, k
+    sim.close()
