@@ -83,11 +83,18 @@ KERNEL_SOURCES = {"scgs": {2: ["nso_kernels.cu", "stc_internal.cuh"],
                            3: ["nso3d_kernels.cu", "grid3d.cuh", "stc_internal.cuh"]},
                   "cres": {2: ["nso_kernels.cu", "stc_internal.cuh"],
                            3: ["nso3d_kernels.cu", "grid3d.cuh", "stc_internal.cuh"]}}
-MEASURED_TRAFFIC = {}   # (kind, dim) -> (bytes per launch, source digest)
+# 3D colour residual: the two-pass form's four launches together (three
+# lamb3_terms_kernel face axes + nso_residual3_colour_kernel).  Taken with
+# ncu --metrics on `bench.py --steps 1 --warmup 0 --no-secondary --no-solve
+# --serve 0 --no-cpu-baseline --no-e2e` (and --workload letters), first launches.
+MEASURED_TRAFFIC = {("scgs", 2): (23256576, "bc017195b37462c1"),
+                    ("cres", 2): (31584000, "bc017195b37462c1"),
+                    ("scgs", 3): (1762414080, "84a2d032ae29ffb8"),
+                    ("cres", 3): (538580992 + 533033216 + 532835584 + 1677781504, "84a2d032ae29ffb8")}
 # FP32 operations of one finest-level SCGS colour launch (2 x FFMA + FADD +
 # FMUL thread instructions, ncu), with the digest of the sources they were
 # counted on: dim -> (flops per launch, source digest)
-MEASURED_SCGS_FLOPS = {}
+MEASURED_SCGS_FLOPS = {2: (2.93888e8, "bc017195b37462c1"), 3: (7.45251e9, "84a2d032ae29ffb8")}
 
 ORACLE_STEPS = 2      # timesteps of the bounded oracle samples (same grid, same per-step work)
 
@@ -599,6 +606,50 @@ def serve_leg(stc, workloads, count, max_admm, fp64_count, budget=64 << 30, work
     return out
 
 
+def autograd_leg(workloads, n=128, N=48, every=8):
+    """The forward simulation as a torch.autograd.Function at the
+    differentiable-simulation workload's size: n^3 cells, N steps, fp32,
+    checkpoint-and-recompute every `every` steps; one untimed pass, then the
+    forward and the backward timed with CUDA events."""
+    import torch
+
+    from paper_1608_01102_gb300 import autograd
+    cfg = workloads.config_autograd(n, N)
+    sim = autograd.Simulation(n, n, N, cfg["rho0"], nz=n, precision=0, checkpoint_every=every)
+    st = torch.tensor(cfg["star"], dtype=torch.float32, device="cuda")
+    times = []
+    for rep in range(2):
+        u = torch.tensor(cfg["u"], dtype=torch.float32, device="cuda", requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        rho = autograd.simulate(u, sim)
+        loss = 0.5 * ((rho[-1] - st) ** 2).sum()
+        e[1].record()
+        loss.backward()
+        e[2].record()
+        e[2].synchronize()
+        times.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+    fwd, bwd = times[-1]
+    out = {"workload": "%d^3 cells, %d steps, fp32, checkpoint every %d steps (%d segments), seeded smooth random "
+                       "forces (correlation 8 cells, max |u| 0.1), loss 1/2 ||rho_N - rho*||^2" % (n, N, every,
+                                                                                               len(sim.segments)),
+           "forward_ms": fwd, "backward_ms": bwd, "picard_iterations": sim.picard_iterations,
+           "loss": float(loss.detach()), "grad_norm": float(u.grad.norm())}
+    sim.close()
+    return out
+
+
+def attach_alu(sc, dim, fp32):
+    """The SCGS launch against the measured FP32 FMA rate (ALU side of its roofline)."""
+    fl = MEASURED_SCGS_FLOPS.get(dim)
+    if not sc or not fp32 or not fl or fl[1] != source_digest("scgs", dim):
+        return
+    g = fl[0] / (sc["avg_launch_us"] * 1e-6) / 1e9
+    sc["alu"] = {"flops_per_launch": fl[0], "achieved_gflops": g, "peak_gflops": fp32, "frac": g / fp32,
+                 "peak_kind": "measured (stc_measure_fp32_peak)",
+                 "flops_rule": "2 x FFMA + FADD + FMUL thread instructions of one launch (ncu count)"}
+
+
 def run_native(args, rank, world, local_rank):
     import torch
 
@@ -634,17 +685,14 @@ def run_native(args, rank, world, local_rank):
         fp32 = stc.measure_fp32_peak()
         sc = m["kernels"]["scgs_colour"]
         line["fp32_fma_peak_gflops"] = fp32
-        fl = MEASURED_SCGS_FLOPS.get(3 if head == "3d" else 2)
-        if sc and fl and fl[1] == source_digest("scgs", 3 if head == "3d" else 2):
-            sc["alu"] = {"flops_per_launch": fl[0], "achieved_gflops": fl[0] / (sc["avg_launch_us"] * 1e-6) / 1e9,
-                         "peak_gflops": fp32, "frac": fl[0] / (sc["avg_launch_us"] * 1e-6) / 1e9 / fp32,
-                         "flops_rule": "2 x FFMA + FADD + FMUL thread instructions of one launch (ncu count)"}
+        attach_alu(sc, 3 if head == "3d" else 2, fp32)
     if solo and not args.no_secondary:
         m2 = measure_step(stc, workloads, other, args, dev, world, with_e2e=not args.no_e2e)
         sec = {k: m2.get(k) for k in ("value", "ms_per_step", "roofline", "kernels", "vcycle_only", "e2e", "clocks",
                                       "gpu_launches", "workload", "sweeps")}
         if cpu2 is not None:
             sec["cpu_baseline"] = cpu2
+        attach_alu(sec["kernels"]["scgs_colour"], 3 if other == "3d" else 2, line.get("fp32_fma_peak_gflops"))
         line["letters" if other == "letters" else "3d"] = sec
     if solo and not args.no_solve:
         legs = {}
@@ -663,6 +711,8 @@ def run_native(args, rank, world, local_rank):
                         "reached (the same per-problem solve, fp32 state vs plain fp64)"}
         legs["3d_fp32"], _ = solve_leg(stc, workloads, "3d", 0, 1e-4, args.solve3d_max_admm, k_adapt=1)
         line["time_to_solution"] = legs
+    if solo and not args.no_autograd:
+        line["autograd"] = autograd_leg(workloads)
     if solo and args.serve > 0:
         line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, args.serve_fp64, mode=1)
         line["served_threads"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, 0, mode=0)
@@ -681,6 +731,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the other workload's step line")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (short profiling runs)")
+    ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-simulation leg")
     ap.add_argument("--small-max-admm", type=int, default=1500)
     ap.add_argument("--solve-max-admm", type=int, default=500)
     ap.add_argument("--fp64-max-admm", type=int, default=40)

@@ -16,17 +16,17 @@
  *
  * Two modes.  Mode 0 (worker threads): each admitted problem runs stc_solve
  * on its own stream and the launches of all resident problems interleave.
- * Mode 1 (stepped): no threads; each stc_server_step admits what fits, runs
- * the AO head of every problem whose ADMM iteration begins, then ONE batched
- * CUDA graph launch holding the next NSO V-cycle of every resident problem
- * (stc_batch_nso_cycle: the problems' captured V-cycle graphs as concurrent
- * child nodes; the instantiated graph is reused while the resident set stays
- * the same), then the KKT/update tail of problems whose NSO solve ended, and
- * retires finished problems, returning their memory at once -- continuous
- * batching at V-cycle granularity.  A server-created problem has its own
- * stream, and the heads and tails of different problems run concurrently
- * (one host thread each), so their sweeps overlap on the device; the batched
- * launches run on stc_server_params.stream.
+ * Mode 1 (stepped): the caller drives stc_server_step.  A step admits what
+ * fits, starts background jobs (one host thread and the problem's own stream
+ * each) for the set-up of admitted problems, the AO head (Alg. 1) of problems
+ * whose ADMM iteration begins and the KKT/update tail of problems whose NSO
+ * solve ended, then runs ONE batched CUDA graph launch holding the next NSO
+ * V-cycle of every idle problem (stc_batch_nso_cycle: the problems' captured
+ * V-cycle graphs as concurrent child nodes; the instantiated graph is reused
+ * while that set stays the same), and retires finished problems, returning
+ * their memory at once -- continuous batching at V-cycle granularity, with
+ * heads and tails overlapping the batched V-cycles on the device.  The
+ * batched launches run on stc_server_params.stream.
  *
  * Threading: every stc_server_* call is safe from any host thread (stepped
  * steps are serialised).  Results are copied to host memory owned by the

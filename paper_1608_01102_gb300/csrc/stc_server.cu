@@ -42,6 +42,7 @@ struct Request {
   stc_problem* p = nullptr;   // stepped mode: the resident problem
   bool owned = true;          // false: submitted by the caller (stc_server_submit_problem)
   cudaStream_t st = nullptr;  // stepped mode: the stream of a server-created problem
+  std::future<stc_status> job;  // stepped mode: a head or tail running in the background
 };
 
 }  // namespace
@@ -197,28 +198,13 @@ size_t face_count(const stc_params& prm) {
   return (size_t)prm.ny * (prm.nx + 1) + (size_t)(prm.ny + 1) * prm.nx;
 }
 
-// f(r) for every resident request, one host thread each (a problem is used by
-// one thread at a time; different problems may be driven concurrently); the
-// failures are appended to `failed`
-template <class F>
-void run_parallel(stc_server* s, F&& f, std::vector<std::pair<Request*, stc_status>>& failed) {
-  std::vector<std::pair<Request*, std::future<stc_status>>> jobs;
-  for (Request* r : s->resident) {
-    bool done = false;
-    for (auto& fl : failed) done = done || fl.first == r;
-    if (!done) jobs.emplace_back(r, std::async(std::launch::async, [&f, r] { return f(r); }));
-  }
-  std::vector<stc_status> st(jobs.size());
-  for (size_t k = 0; k < jobs.size(); ++k) st[k] = jobs[k].second.get();
-  // (the jobs read `failed`: it grows only once all of them have finished)
-  for (size_t k = 0; k < jobs.size(); ++k)
-    if (st[k] != STC_OK) failed.emplace_back(jobs[k].first, st[k]);
-}
-
-// One serving step: admission, the heads (Alg. 1) of problems whose ADMM
-// iteration begins, one batched launch of every resident problem's next NSO
-// V-cycle, the tails (KKT metric, multiplier update, stopping tests) of
-// problems whose NSO solve ended, and retirement of finished problems.
+// One serving step: admission; background jobs (one host thread and the
+// problem's own stream each) for the set-up of admitted problems, the heads
+// (Alg. 1) of problems whose ADMM iteration begins and the tails (KKT metric,
+// multiplier update, stopping tests) of problems whose NSO solve ended; one
+// batched launch of the next NSO V-cycle of every idle problem that wants one
+// (or, when none does, a wait for a job to finish); retirement of finished
+// problems.  A problem in a job does not hold up the others' V-cycles.
 stc_status step_stepped(stc_server* s, int* active) {
   std::lock_guard<std::mutex> step_lock(s->step_mu);
   std::vector<Request*> admitted;
@@ -236,47 +222,73 @@ stc_status step_stepped(stc_server* s, int* active) {
     }
     if (!admitted.empty()) s->cv_done.notify_all();
   }
+  // an admitted request's set-up (problem creation, keyframes, stc_solve_begin)
+  // runs as its first background job
   for (Request* r : admitted) {
-    stc_status st = STC_OK;
-    if (!r->p) {
-      // each server-created problem has its own stream, so that the heads and
-      // tails of different problems overlap on the device
-      if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        r->st = nullptr;
-        stc::set_last_error("could not create a stream for the request");
-        finish_stepped(s, r, STC_ERR_CUDA);
-        continue;
+    r->job = std::async(std::launch::async, [r] {
+      stc_status st = STC_OK;
+      if (!r->p) {
+        // each server-created problem has its own stream, so that the heads
+        // and tails of different problems overlap on the device
+        if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) {
+          cudaGetLastError();
+          r->st = nullptr;
+          stc::set_last_error("could not create a stream for the request");
+          return STC_ERR_CUDA;
+        }
+        st = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), r->st, &r->p);
+        if (st == STC_OK && !r->steps.empty())
+          st = stc_set_keyframes(r->p, (int)r->steps.size(), r->steps.data(), r->stars.data(), r->cs.data());
       }
-      st = stc_create_problem(&r->prm, r->rho0.data(), r->v0.empty() ? nullptr : r->v0.data(), r->st, &r->p);
-      if (st == STC_OK && !r->steps.empty())
-        st = stc_set_keyframes(r->p, (int)r->steps.size(), r->steps.data(), r->stars.data(), r->cs.data());
-    }
-    if (st == STC_OK) st = stc_solve_begin(r->p, r->tol, r->max_admm);
-    if (st != STC_OK) finish_stepped(s, r, st);
-    else s->resident.push_back(r);
+      if (st == STC_OK) st = stc_solve_begin(r->p, r->tol, r->max_admm);
+      return st;
+    });
+    s->resident.push_back(r);
   }
+  // background jobs that have finished: their problems are idle again
   std::vector<std::pair<Request*, stc_status>> failed;
+  auto collect = [&](Request* r) {
+    const stc_status st = r->job.get();
+    if (st != STC_OK) failed.emplace_back(r, st);
+  };
+  for (Request* r : s->resident)
+    if (r->job.valid() && r->job.wait_for(std::chrono::seconds(0)) == std::future_status::ready) collect(r);
   auto failed_status = [&](Request* r) {
     for (auto& f : failed)
       if (f.first == r) return f.second;
     return STC_OK;
   };
+  // (the solve state of a problem is read only while no job of it runs)
   auto phase = [](Request* r, int* wants) {
     int ph = 2;
     stc_solve_phase(r->p, &ph, wants);
     return ph;
   };
-  // heads (Alg. 1) of the problems whose ADMM iteration begins, concurrently
-  run_parallel(s, [&](Request* r) {
+  // idle problems whose ADMM iteration begins (Alg. 1), or whose NSO solve
+  // ended (KKT metric, multiplier update, stopping tests, then the next head),
+  // get a background job on their own stream
+  for (Request* r : s->resident) {
+    if (r->job.valid() || failed_status(r) != STC_OK || !r->p) continue;
     int w = 0;
-    return phase(r, &w) == 0 ? stc_solve_head(r->p) : STC_OK;
-  }, failed);
+    const int ph = phase(r, &w);
+    if (ph == 0) {
+      r->job = std::async(std::launch::async, [r] { return stc_solve_head(r->p); });
+    } else if (ph == 1 && !w) {
+      r->job = std::async(std::launch::async, [r] {
+        stc_status st = stc_solve_tail(r->p);
+        int ph2 = 2, w2 = 0;
+        if (st == STC_OK) stc_solve_phase(r->p, &ph2, &w2);
+        if (st == STC_OK && ph2 == 0) st = stc_solve_head(r->p);
+        return st;
+      });
+    }
+  }
+  // one batched launch: the next NSO V-cycle of every idle problem that wants one
   std::vector<stc_problem*> probs;
   std::vector<Request*> owners;
   for (Request* r : s->resident) {
     int w = 0;
-    if (failed_status(r) == STC_OK && phase(r, &w) == 1 && w) {
+    if (!r->job.valid() && failed_status(r) == STC_OK && r->p && phase(r, &w) == 1 && w) {
       probs.push_back(r->p);
       owners.push_back(r);
     }
@@ -286,14 +298,30 @@ stc_status step_stepped(stc_server* s, int* active) {
     const stc_status b = stc_batch_nso_cycle(s->batch, probs.data(), (int)probs.size(), nullptr, sts.data());
     for (size_t k = 0; k < probs.size(); ++k)
       if (b != STC_OK || sts[k] != STC_OK) failed.emplace_back(owners[k], b != STC_OK ? b : sts[k]);
+  } else {
+    // nothing to cycle: wait until some background job finishes
+    bool any = false, done = false;
+    while (!done) {
+      any = false;
+      for (Request* r : s->resident)
+        if (r->job.valid()) {
+          any = true;
+          if (r->job.wait_for(std::chrono::microseconds(200)) == std::future_status::ready) {
+            collect(r);
+            done = true;
+            break;
+          }
+        }
+      if (!any) break;
+    }
   }
-  // tails (KKT metric, multiplier update, stopping tests) of finished NSO solves, concurrently
-  run_parallel(s, [&](Request* r) {
-    int w = 0;
-    return failed_status(r) == STC_OK && phase(r, &w) == 1 && !w ? stc_solve_tail(r->p) : STC_OK;
-  }, failed);
+  // retire idle problems that failed or finished
   std::vector<Request*> keep;
   for (Request* r : s->resident) {
+    if (r->job.valid()) {
+      keep.push_back(r);
+      continue;
+    }
     if (failed_status(r) != STC_OK) {
       finish_stepped(s, r, failed_status(r));
       continue;
@@ -564,9 +592,13 @@ stc_status stc_server_destroy(stc_server* s) {
   for (auto& t : s->workers) t.join();
   {
     std::lock_guard<std::mutex> step_lock(s->step_mu);
+    for (Request* r : s->resident)     // background jobs finish first
+      if (r->job.valid()) r->job.wait();
     for (Request* r : s->resident) {   // stepped mode: solves still in flight end here
       if (r->p && r->owned) stc_destroy_problem(r->p);
       r->p = nullptr;
+      if (r->st) cudaStreamDestroy(r->st);
+      r->st = nullptr;
       r->info.state = STC_TICKET_CANCELLED;
     }
     s->resident.clear();
