@@ -1,5 +1,5 @@
-"""GPU: the forward simulation as a torch.autograd.Function (spec pattern
-3) against the fp64 oracle.
+"""GPU: the forward simulation as a torch.autograd.Function (the differentiable
+simulation) against the fp64 oracle.
 
 The oracle solves each implicit Navier-Stokes step exactly (Newton, sparse
 direct solves; oracle.brute) and differentiates the whole chain by its own

@@ -3,7 +3,7 @@
 The reference is tests/golden/admm_solved_8x8x4.npz, written by
 tests/golden/make_admm_solved.py (the oracle's Alg. 3 with residual balancing
 of K, solved to a relative KKT residual of 1e-7).  The library solves the same
-problem from v = 0 with the same rule; the benchmark spec's tolerances apply to the
+problem from v = 0 with the same rule; the precision policy's tolerances apply to the
 result: force field relative L2 <= 1e-3 and objective relative <= 1e-4.
 """
 import os

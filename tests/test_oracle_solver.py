@@ -386,7 +386,7 @@ def test_al_fallback_holds_lambda_while_the_objective_falls():
 
 @pytest.mark.slow
 def test_admm_reaches_the_full_resimulation_objective_on_a_tiny_problem():
-    """North-star check: STFAS + ADMM and a full-resimulation quasi-Newton solve
+    """STFAS + ADMM and a full-resimulation quasi-Newton solve
     (Sec. 5's comparison system) reach the same objective on a tiny problem."""
     P = _problem(8, 4, sigma=0.15, levels=0, r=1e-2)
     x, vstar, lam, hist = admm.solve(P, tol=1e-7, max_admm=300, eps_admm=0.0)
