@@ -26,9 +26,11 @@ Beside the step figures (rank 0, N = 1; skip with the --no-* flags):
   fp64; 64^3 x 60 for a few iterations), with the seconds at which 1e-2, 1e-3
   and 1e-4 were first reached;
 * served: the first --serve requests of the seeded Poisson serving stream
-  replayed in real time into stc_server (fp32, 64 GB budget), p50/p99 time
-  to solution and problems/hour, beside the plain fp64 per-problem solve of
-  the first few of the same requests one after another.
+  replayed in real time into stc_server (fp32, 64 GB budget, worker-thread
+  mode), p50/p99 time to solution and problems/hour, beside the plain fp64
+  per-problem solve of the first few of the same requests one after another;
+  served_batched replays the same into the stepped mode (batched V-cycle
+  launches, continuous admission).
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference];
 N > 1 under torchrun runs one independent replica per GPU (the method has no
@@ -714,8 +716,8 @@ def run_native(args, rank, world, local_rank):
     if solo and not args.no_autograd:
         line["autograd"] = autograd_leg(workloads)
     if solo and args.serve > 0:
-        line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, args.serve_fp64, mode=1)
-        line["served_threads"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, 0, mode=0)
+        line["served"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, args.serve_fp64, mode=0)
+        line["served_batched"] = serve_leg(stc, workloads, args.serve, args.serve_max_admm, 0, mode=1)
     print(json.dumps(line), flush=True)
 
 

@@ -1479,13 +1479,21 @@ inline unsigned blocks3(size_t n, int tpb) { return (unsigned)((n + tpb - 1) / t
 // ---------------------------------------------------------------------------
 // launchers (called by the dimension-generic launchers when g.dim == 3)
 // ---------------------------------------------------------------------------
-// pass A of the two-pass rows on levels of at least this many faces (smaller
-// levels keep the inline form: there the extra launches cost more than the
-// gathers they save)
-constexpr int kLambMinFaces = 50000;
+// pass A of the two-pass rows on levels of at least this many faces.  Every
+// level qualifies: on the small levels, and on the fp64 coarsest level at
+// GB300's low fp64 rate, the inline gathers cost more than the three extra
+// launches (measured inline: ~60-100 us per colour residual on 16^3 .. 4^3).
+constexpr int kLambMinFaces = 0;
 
 size_t lamb3_scratch_bytes(const Geom& g, size_t tsize) {
   return g.F < kLambMinFaces ? 0 : (size_t)(g.N + 1) * g.F * 5 * tsize;
+}
+
+// the scratch of a whole hierarchy: the largest level's need (the finest in
+// its type, or the fp64 coarsest level of an fp32 hierarchy)
+size_t lamb3_scratch_bytes_max(const Geom& finest, size_t tsize, const Geom& coarsest, size_t csize) {
+  const size_t a = lamb3_scratch_bytes(finest, tsize), b = lamb3_scratch_bytes(coarsest, csize);
+  return a > b ? a : b;
 }
 
 // pass A into the scratch (AB4 slices then the Adv slices); false: inline form

@@ -1168,7 +1168,10 @@ size_t plan_bytes(const stc_params& prm, int nkeys) {
   if (g0.dim == 3) {
     total += b(advect3_scratch_bytes(g0, ts)) + b(project3_scratch_elems(g0, (int)N + 1) * ts) +
              b(scgs3_thomas_scratch_bytes(g0, ts));
-    if (lamb3_scratch_bytes(g0, ts) > 0) total += b(lamb3_scratch_bytes(g0, ts));
+    const Dim& dc = dims.back();
+    const Geom gc = make_geom(prm, dc.nx, dc.ny, dc.nz, 1.0 / dc.nx, dc.N, prm.dt);
+    const size_t lb = lamb3_scratch_bytes_max(g0, ts, gc, dims.size() > 1 ? 8 : ts);
+    if (lb > 0) total += b(lb);
   } else if (project_needs_scratch(g0, ts)) {
     total += b((N + 1) * project_smem(g0, ts));
   }
@@ -1552,7 +1555,8 @@ stc_status stc_create_problem(const stc_params* params, const double* rho0, cons
       P->pscratch = dalloc(P, project3_scratch_elems(g0, N + 1) * ts);
       P->adv3 = dalloc(P, advect3_scratch_bytes(g0, ts));
       P->sc3 = dalloc(P, scgs3_thomas_scratch_bytes(g0, P->dbl ? 8 : 4));
-      P->lamb3_bytes = lamb3_scratch_bytes(g0, ts);   // the finest level is the largest user
+      const Level& Lc = P->lv.back();
+      P->lamb3_bytes = lamb3_scratch_bytes_max(g0, ts, Lc.g, esz(Lc.dbl));
       if (P->lamb3_bytes > 0) P->lamb3 = dalloc(P, P->lamb3_bytes);
     } else if (project_needs_scratch(g0, ts)) {
       P->pscratch = dalloc(P, (N + 1) * project_smem(g0, ts));

@@ -145,6 +145,7 @@ int launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T
                                 cudaStream_t st, const double* only_if_undone, void* lamb, size_t lamb_bytes);
 // bytes of the two-pass residual scratch of a 3D level (0: the level keeps the inline form)
 size_t lamb3_scratch_bytes(const Geom& g, size_t tsize);
+size_t lamb3_scratch_bytes_max(const Geom& finest, size_t tsize, const Geom& coarsest, size_t csize);
 template <class T>
 void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                          const double* lm_dev, void* scratch);
