@@ -981,6 +981,7 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
 // after it; the stencil's other faces belong to cells of other colours).
 // ---------------------------------------------------------------------------
 constexpr int kThomasRec = NF * NF + NF + NB;   // X (6x6), multipliers (6), z (7)
+constexpr int kThomasCpl = NF * NF;             // U_t of one cell and step (6x6)
 
 template <class T, class S>
 struct ThomasCell {
@@ -1030,6 +1031,32 @@ struct ThomasCell {
   }
 };
 
+// The couplings U_t = I/dt + dAdv_loc(v_{t+1}) of every cell of the colour
+// and every step, precomputed: each needs ~144 scattered loads of v around the
+// cell, independent of the Thomas recurrence, which the thread-per-cell
+// kernel otherwise issues twice per step inside its dependency chain.  Stored
+// cell-fastest after the records (coalesced streaming loads in the solve).
+// The colour's own faces of v_{t+1} are updated only after the solve's last
+// use of U_t, and the stencil's other faces belong to other colours, so the
+// values equal the ones the solve computed in place.  (Precomputing the
+// residual-row loads as well -- y_t and the v-block right-hand side, 14
+// loads per step -- measured no faster: the extra scratch traffic offset them.)
+template <class T, class S>
+__global__ void __launch_bounds__(128)
+scgs3t_coupling_kernel(Geom g, const T* __restrict__ v, int colour, int ncell, S* __restrict__ ubuf) {
+  pdl_wait();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (q >= ncell || t >= g.N) return;
+  const ThomasCell<T, S> tc(g, colour, q);
+  S U[NF][NF];
+  tc.coupling(v + (size_t)(t + 1) * g.F, pick<S>(g.idt, g.idtf), U);
+#pragma unroll
+  for (int a = 0; a < NF; ++a)
+#pragma unroll
+    for (int b = 0; b < NF; ++b) ubuf[((size_t)t * kThomasCpl + a * NF + b) * ncell + q] = U[a][b];
+}
+
 template <class T, class S>
 __global__ void __launch_bounds__(64)
 scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, const double* __restrict__ lm_dev,
@@ -1044,6 +1071,13 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   CellG3<S> cg;
   cg.init(g, tc.cl.i, tc.cl.j, tc.cl.k);
   auto rec = [&](int t, int e) -> S& { return zbuf[((size_t)t * kThomasRec + e) * ncell + q]; };
+  const S* ubuf = zbuf + (size_t)kThomasRec * N * ncell;
+  auto load_u = [&](int t, S U[NF][NF]) {
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+#pragma unroll
+      for (int b = 0; b < NF; ++b) U[a][b] = ubuf[((size_t)t * kThomasCpl + a * NF + b) * ncell + q];
+  };
 
   // ---- pass 1: ascending elimination ----------------------------------------
   // carried from block t-1: M = O_{t-1}^T X_{t-1} (faces), m = O_{t-1}^T z_{t-1};
@@ -1051,7 +1085,7 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   S M[NF][NF], m[NF], Sn[NF][NF], Rn[NF];
   {
     S U[NF][NF], y[NB];
-    tc.coupling(x.v + (size_t)g.F, idt, U);
+    load_u(0, U);
     tc.u_solve(r, 0, cg, y);
 #pragma unroll
     for (int b = 0; b < NF; ++b) {
@@ -1105,7 +1139,7 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
     // coupling to v_{tv+1}: O = -P U_tv / dt, and the next block's Sn, Rn
     if (tv < N) {
       S U[NF][NF], y[NB];
-      tc.coupling(x.v + (size_t)(tv + 1) * g.F, idt, U);
+      load_u(tv, U);
       tc.u_solve(r, tv, cg, y);
 #pragma unroll
       for (int a = 0; a < NF; ++a) B[a][NF] += idt * cg.act[a] * y[a];
@@ -1207,7 +1241,7 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   for (int a = 0; a < NF; ++a) xv0[a] = S(0);
   for (int t = 0; t < N; ++t) {
     S U[NF][NF], y[NB], xv1[NB];
-    tc.coupling(x.v + (size_t)(t + 1) * g.F, idt, U);
+    load_u(t, U);
     tc.u_solve(r, t, cg, y);
 #pragma unroll
     for (int a = 0; a < NB; ++a) xv1[a] = rec(t, NF * NF + NF + a);
@@ -1597,7 +1631,7 @@ constexpr int kThomasMinCells = 16384;
 
 size_t scgs3_thomas_scratch_bytes(const Geom& g, size_t ssize) {
   const size_t ncell = (size_t)((g.nx + 1) / 2) * ((g.ny + 1) / 2) * ((g.nz + 1) / 2);
-  return (size_t)kThomasRec * g.N * ncell * ssize;
+  return (size_t)(kThomasRec + kThomasCpl) * g.N * ncell * ssize;   // records, then couplings
 }
 
 template <class T, class S>
@@ -1605,22 +1639,26 @@ static void launch_scgs3t(const Geom& g, State<T> x, CState<T> r, int colour, co
                           cudaStream_t st) {
   const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
   const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
+  S* zbuf = static_cast<S*>(scratch);
+  launch_pdl3(scgs3t_coupling_kernel<T, S>, dim3((ncell + 127) / 128, g.N), dim3(128), 0, st, g, (const T*)x.v,
+              colour, ncell, zbuf + (size_t)kThomasRec * g.N * ncell);
   launch_pdl3(scgs3t_colour_kernel<T, S>, dim3((ncell + 63) / 64), dim3(64), 0, st, g, x, r, colour, ncell, lm_dev,
-              static_cast<S*>(scratch));
+              zbuf);
 }
 
 template <class T>
-void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+int launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                          const double* lm_dev, void* scratch) {
   const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
   const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
   if (scratch && ncell >= kThomasMinCells) {
     if (solve_fp32) launch_scgs3t<T, float>(g, x, r, colour, lm_dev, scratch, st);
     else launch_scgs3t<T, T>(g, x, r, colour, lm_dev, scratch, st);
-    return;
+    return 2;   // the couplings, then the Thomas solve
   }
   if (solve_fp32) launch_scgs3_ts<T, float>(g, x, r, colour, lm_dev, st);
   else launch_scgs3_ts<T, T>(g, x, r, colour, lm_dev, st);
+  return 1;
 }
 
 template <class Tf, class Tc>
@@ -1672,7 +1710,7 @@ void launch_kkt_grad_rhs3(const Geom& g, const T* v, const T* u, const T* dens, 
                                        cudaStream_t, double*, const double*, RedScratch, void*, size_t);       \
   template int launch_nso_residual3_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,     \
                                               cudaStream_t, const double*, void*, size_t);                    \
-  template void launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \
+  template int launch_scgs3_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,             \
                                        const double*, void*);                                                 \
   template void launch_kkt_force_rhs3<T>(const Geom&, const T*, T*, cudaStream_t);                            \
   template void launch_kkt_grad_rhs3<T>(const Geom&, const T*, const T*, const T*, double, T*, cudaStream_t);

@@ -1403,11 +1403,12 @@ static void launch_scgs_ts(const Geom& g, State<T> x, CState<T> r, int colour, c
 }
 
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
-                        const double* lm_dev, void* scratch3) {
+int launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+                       const double* lm_dev, void* scratch3) {
   if (g.dim == 3) return launch_scgs3_colour<T>(g, x, r, colour, solve_fp32, st, lm_dev, scratch3);
   if (solve_fp32) launch_scgs_ts<T, float>(g, x, r, colour, lm_dev, st);
   else launch_scgs_ts<T, T>(g, x, r, colour, lm_dev, st);
+  return 1;
 }
 
 size_t scgs_smem_bytes(int N, size_t tsize) {
@@ -1495,7 +1496,7 @@ void launch_convert(const Ts* s, Td* d, size_t n, cudaStream_t st) {
                                       cudaStream_t, double*, const double*, RedScratch, void*, size_t);    \
   template int launch_nso_residual_colour<T>(const Geom&, CState<T>, const T*, CState<T>, State<T>, int,      \
                                              cudaStream_t, const double*, void*, size_t);                 \
-  template void launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
+  template int launch_scgs_colour<T>(const Geom&, State<T>, CState<T>, int, bool, cudaStream_t,           \
                                       const double*, void*);                                               \
   template void launch_absmax<T>(const T*, size_t, double*, int*, cudaStream_t);                          \
   template void launch_sumsq<T>(const T*, size_t, double*, cudaStream_t, RedScratch);                     \

@@ -300,13 +300,14 @@ void smooth(stc_problem* P, int l, int sweeps, cudaStream_t st, bool timed = fal
       count(P, k);
       const bool ev = timed && P->ev_used[0] < (int)P->ev_start[0].size();
       if (ev) ck(cudaEventRecordWithFlags(P->ev_start[0][P->ev_used[0]], st, cudaEventRecordExternal), "event");
+      int ks = 0;
       dispatch(L.dbl, [&](auto tag) {
         using T = decltype(tag);
         // fp32 mode: fp64 coarsest state and residuals, fp32 per-cell correction solve
-        launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm, P->sc3);
+        ks = launch_scgs_colour<T>(L.g, st_of<T>(L.x), cst_of<T>(L.tmp), c, !P->dbl, st, P->dlm, P->sc3);
       });
       if (ev) ck(cudaEventRecordWithFlags(P->ev_stop[0][P->ev_used[0]++], st, cudaEventRecordExternal), "event");
-      count(P, 1);
+      count(P, ks);
     }
 }
 

@@ -32,7 +32,7 @@ int launch_nso_residual_colour(const Geom& g, CState<T> x, const T* z, CState<T>
 // scratch3 (3D, optional): scgs3_thomas_scratch_bytes of the finest level, which
 // lets large colours run the thread-per-cell block Thomas kernel
 template <class T>
-void launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+int launch_scgs_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                         const double* lm_dev = nullptr, void* scratch3 = nullptr);
 size_t scgs_smem_bytes(int N, size_t tsize);
 int colour_extent(int n, int parity);
@@ -147,7 +147,7 @@ int launch_nso_residual3_colour(const Geom& g, CState<T> x, const T* z, CState<T
 size_t lamb3_scratch_bytes(const Geom& g, size_t tsize);
 size_t lamb3_scratch_bytes_max(const Geom& finest, size_t tsize, const Geom& coarsest, size_t csize);
 template <class T>
-void launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
+int launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool solve_fp32, cudaStream_t st,
                          const double* lm_dev, void* scratch);
 size_t scgs3_smem_bytes(int N, size_t tsize);   // shared memory of one cell's SCGS solve
 size_t scgs3_thomas_scratch_bytes(const Geom& g, size_t ssize);
