@@ -86,17 +86,20 @@ KERNEL_SOURCES = {"scgs": {2: ["nso_kernels.cu", "stc_internal.cuh"],
                   "cres": {2: ["nso_kernels.cu", "stc_internal.cuh"],
                            3: ["nso3d_kernels.cu", "grid3d.cuh", "stc_internal.cuh"]}}
 # 3D colour residual: the two-pass form's four launches together (three
-# lamb3_terms_kernel face axes + nso_residual3_colour_kernel).  Taken with
+# lamb3_terms_kernel face axes + nso_residual3_colour_kernel); 3D SCGS: the
+# coupling kernel and the Thomas kernel together.  Taken with
 # ncu --metrics on `bench.py --steps 1 --warmup 0 --no-secondary --no-solve
-# --serve 0 --no-cpu-baseline --no-e2e` (and --workload letters), first launches.
-MEASURED_TRAFFIC = {("scgs", 2): (23256576, "bc017195b37462c1"),
-                    ("cres", 2): (31584000, "bc017195b37462c1"),
-                    ("scgs", 3): (1762414080, "84a2d032ae29ffb8"),
-                    ("cres", 3): (538580992 + 533033216 + 532835584 + 1677781504, "84a2d032ae29ffb8")}
+# --serve 0 --no-cpu-baseline --no-e2e --no-autograd` (and --workload
+# letters), the first launches of each kernel.
+MEASURED_TRAFFIC = {("scgs", 2): (23258624, "4602f9532e8dcd2a"),
+                    ("cres", 2): (31350528 + 261120, "4602f9532e8dcd2a"),
+                    ("scgs", 3): (180978688 + 226662912 + 1459975936 + 596761088, "9a05fc05e288db44"),
+                    ("cres", 3): (538740736 + 533024000 + 533236992 + 1677952768,
+                                  "9a05fc05e288db44")}
 # FP32 operations of one finest-level SCGS colour launch (2 x FFMA + FADD +
 # FMUL thread instructions, ncu), with the digest of the sources they were
 # counted on: dim -> (flops per launch, source digest)
-MEASURED_SCGS_FLOPS = {2: (2.93888e8, "bc017195b37462c1"), 3: (7.45251e9, "84a2d032ae29ffb8")}
+MEASURED_SCGS_FLOPS = {2: (2.93888e8, "4602f9532e8dcd2a"), 3: (6.51190e9, "9a05fc05e288db44")}
 
 ORACLE_STEPS = 2      # timesteps of the bounded oracle samples (same grid, same per-step work)
 
@@ -305,7 +308,8 @@ def kernel_roofline(G, kind, dim, n, nz, N, peak, peak_kind):
     F = G.field_shape("V")[1]
     if kind == 0:
         per_launch = SCGS_BYTES_PER_CELL_SWEEP[dim] * C * N / 2 ** dim
-        name = "scgs3 colour kernel (finest level)" if dim == 3 else "scgs_colour_kernel<float> (finest level)"
+        name = ("scgs3t_coupling_kernel + scgs3t_colour_kernel<float> (finest level)" if dim == 3
+                else "scgs_colour_kernel<float> (finest level)")
         key = "scgs"
     else:
         a, b = CRES_FLOATS[dim]

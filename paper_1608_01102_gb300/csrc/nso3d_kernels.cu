@@ -608,7 +608,8 @@ __device__ __forceinline__ Cell3 colour_cell(const Geom& g, int colour, int q) {
 
 template <class T, class S>
 __global__ void __launch_bounds__(256)
-scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int cpb, const double* __restrict__ lm_dev) {
+scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int cpb, const double* __restrict__ lm_dev,
+                    const S* __restrict__ ubuf) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = g.N;
@@ -631,14 +632,19 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
     S act[NF] = {S(pr || cl.i > 0), S(pr || cl.i < g.nx - 1), S(pr || cl.j > 0), S(pr || cl.j < g.ny - 1),
                  S(pr || cl.k > 0), S(pr || cl.k < g.nz - 1)};
     const int cc = cid(g, cl.k, cl.j, cl.i);
-    S Jl[NF][NF];
-    local_adv_jac3<T, S>(g, x.v + (size_t)(t + 1) * g.F, cl.k, cl.j, cl.i, act, Jl);
     S* U = Us + (size_t)t * NF * NF * cpb + c;
+    if (ubuf) {   // the couplings precomputed for the colour ([t][36][ncell], scgs3t_coupling_kernel)
 #pragma unroll
-    for (int a2 = 0; a2 < NF; ++a2)
+      for (int e = 0; e < NF * NF; ++e) U[e * cpb] = ubuf[((size_t)t * NF * NF + e) * ncell + q];
+    } else {
+      S Jl[NF][NF];
+      local_adv_jac3<T, S>(g, x.v + (size_t)(t + 1) * g.F, cl.k, cl.j, cl.i, act, Jl);
 #pragma unroll
-      for (int b2 = 0; b2 < NF; ++b2)
-        U[(a2 * NF + b2) * cpb] = ((a2 == b2 ? idt : S(0)) + S(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2];
+      for (int a2 = 0; a2 < NF; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < NF; ++b2)
+          U[(a2 * NF + b2) * cpb] = ((a2 == b2 ? idt : S(0)) + S(g.self_adv) * Jl[a2][b2]) * act[a2] * act[b2];
+    }
     S* Ru = Bu + (size_t)t * NB * cpb + c;
     S* Rv = Vb + ((size_t)c * N + t) * kCr3Stride + C3_R;
     const T* ru = r.u + (size_t)t * g.F;
@@ -1601,8 +1607,8 @@ static int scgs3_cells_per_block(int N, size_t ssize) {
 }
 
 template <class T, class S>
-static void launch_scgs3_ts(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev,
-                            cudaStream_t st) {
+static int launch_scgs3_ts(const Geom& g, State<T> x, CState<T> r, int colour, const double* lm_dev,
+                           cudaStream_t st, void* scratch) {
   static std::once_flag once;
   std::call_once(once, [] {
     int dev = 0, optin = 0;
@@ -1615,13 +1621,18 @@ static void launch_scgs3_ts(const Geom& g, State<T> x, CState<T> r, int colour, 
   });
   const int px = colour & 1, py = (colour >> 1) & 1, pz = colour >> 2;
   const int ncell = ((g.nx - px + 1) / 2) * ((g.ny - py + 1) / 2) * ((g.nz - pz + 1) / 2);
-  if (ncell == 0) return;
+  if (ncell == 0) return 0;
   const int cpb = scgs3_cells_per_block(g.N, sizeof(S));
-  if (cpb < 1) return;   // refused at problem creation (scgs_smem_bytes)
+  if (cpb < 1) return 0;   // refused at problem creation (scgs_smem_bytes)
   const size_t smem = (size_t)cpb * scgs3_smem_bytes(g.N, sizeof(S));
   const int threads = 32 * cpb < 64 ? 64 : 32 * cpb;
+  S* ubuf = static_cast<S*>(scratch);
+  if (ubuf)   // (a coarser level's colour fits the finest level's scratch)
+    launch_pdl3(scgs3t_coupling_kernel<T, S>, dim3((ncell + 127) / 128, g.N), dim3(128), 0, st, g, (const T*)x.v,
+                colour, ncell, ubuf);
   launch_pdl3(scgs3_colour_kernel<T, S>, dim3((ncell + cpb - 1) / cpb), dim3(threads), smem, st, g, x, r, colour,
-              ncell, cpb, lm_dev);
+              ncell, cpb, lm_dev, (const S*)ubuf);
+  return ubuf ? 2 : 1;
 }
 
 // Colours with at least kThomasMinCells cells run the thread-per-cell block
@@ -1656,9 +1667,8 @@ int launch_scgs3_colour(const Geom& g, State<T> x, CState<T> r, int colour, bool
     else launch_scgs3t<T, T>(g, x, r, colour, lm_dev, scratch, st);
     return 2;   // the couplings, then the Thomas solve
   }
-  if (solve_fp32) launch_scgs3_ts<T, float>(g, x, r, colour, lm_dev, st);
-  else launch_scgs3_ts<T, T>(g, x, r, colour, lm_dev, st);
-  return 1;
+  if (solve_fp32) return launch_scgs3_ts<T, float>(g, x, r, colour, lm_dev, st, scratch);
+  return launch_scgs3_ts<T, T>(g, x, r, colour, lm_dev, st, scratch);
 }
 
 template <class Tf, class Tc>
