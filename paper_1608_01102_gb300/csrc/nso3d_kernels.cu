@@ -982,9 +982,9 @@ scgs3_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, int 
 // block) to a scratch laid out cell-fastest, so the accesses of a warp are
 // coalesced.  Passes: (1) ascending elimination, (2) descending
 // substitution x_t = z_t - Z_t x_{t+1} in place, (3) ascending recovery of
-// the u blocks and x += omega delta.  U_t is recomputed in pass 3 from the
-// not yet updated v_{t+1} (the cell's own faces of slab t+1 are written only
-// after it; the stencil's other faces belong to cells of other colours).
+// the u blocks and x += omega delta.  The couplings U_t come precomputed
+// (scgs3t_coupling_kernel) and every global value a step reads is copied
+// into shared memory one step ahead, so the recurrence waits on no load.
 // ---------------------------------------------------------------------------
 constexpr int kThomasRec = NF * NF + NF + NB;   // X (6x6), multipliers (6), z (7)
 constexpr int kThomasCpl = NF * NF;             // U_t of one cell and step (6x6)
@@ -1020,13 +1020,13 @@ struct ThomasCell {
 #pragma unroll
       for (int b = 0; b < NF; ++b) U[a][b] = ((a == b ? idt : S(0)) + S(g.self_adv) * U[a][b]) * act[a] * act[b];
   }
-  // y_t = D_u^{-1} b_u(t), b_u = -(f - res) at the cell's u faces and p_{t+1}
-  __device__ void u_solve(const CState<T>& r, int t, const CellG3<S>& cg, S y[NB]) const {
+  // y_t = D_u^{-1} b_u(t), b_u = -(f - res) at the cell's u faces and p_{t+1},
+  // from the rows (f - res) of u at slab t (ruv, the cell's faces) and of p (rpv)
+  __device__ void u_solve_v(const T ruv[NF], T rpv, const CellG3<S>& cg, S y[NB]) const {
     S bf[NF], pb[NF];
-    const T* ru = r.u + (size_t)t * g.F;
 #pragma unroll
-    for (int a = 0; a < NF; ++a) bf[a] = S(-ld(ru + fidx[a])) * act[a];
-    const S bp = S(-ld(r.p + (size_t)t * g.C + cc));
+    for (int a = 0; a < NF; ++a) bf[a] = S(-ruv[a]) * act[a];
+    const S bp = S(-rpv);
     cg.proj(bf, pb);
     S gb = S(0);
 #pragma unroll
@@ -1063,11 +1063,40 @@ scgs3t_coupling_kernel(Geom g, const T* __restrict__ v, int colour, int ncell, S
     for (int b = 0; b < NF; ++b) ubuf[((size_t)t * kThomasCpl + a * NF + b) * ncell + q] = U[a][b];
 }
 
+// Per-thread asynchronous copies (cp.async, sm_80+) that stage the global data
+// one step of the Thomas kernel reads -- couplings, residual rows, records,
+// state -- into the thread's own column of a two-stage shared-memory buffer one
+// step ahead, so that no global load sits on the recurrence's dependency chain.
+// Every thread copies and reads only its own column: the per-thread
+// wait_group is the only synchronisation the buffer needs.
+template <class E>
+__device__ __forceinline__ void cpa(E* smem, const E* gmem) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "cp.async of 4 or 8 bytes");
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if constexpr (sizeof(E) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all groups but the most recent one complete
+__device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+constexpr int kThomasThreads = 64;   // threads (cells) per CTA
+constexpr int kStageS = kThomasRec;  // S values staged per step, at most (pass 2: a record)
+constexpr int kStageT = 3 * NF + 3;  // T values staged per step, at most (pass 3: r.u, r.p, u, v, p, pbar)
+
 template <class T, class S>
-__global__ void __launch_bounds__(64)
+constexpr size_t scgs3t_smem_bytes() {
+  return (size_t)2 * kThomasThreads * (kStageS * sizeof(S) + kStageT * sizeof(T));
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(kThomasThreads)
 scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, const double* __restrict__ lm_dev,
                      S* __restrict__ zbuf) {
   pdl_wait();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ncell) return;
   const int N = g.N;
@@ -1078,21 +1107,64 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   cg.init(g, tc.cl.i, tc.cl.j, tc.cl.k);
   auto rec = [&](int t, int e) -> S& { return zbuf[((size_t)t * kThomasRec + e) * ncell + q]; };
   const S* ubuf = zbuf + (size_t)kThomasRec * N * ncell;
-  auto load_u = [&](int t, S U[NF][NF]) {
+  auto ucp = [&](int t, int e) -> const S* { return ubuf + ((size_t)t * kThomasCpl + e) * ncell + q; };
+  // the thread's column of the staging buffers: [stage][element][thread]
+  S* const stS = reinterpret_cast<S*>(smem_raw) + threadIdx.x;
+  T* const stT = reinterpret_cast<T*>(smem_raw + (size_t)2 * kThomasThreads * kStageS * sizeof(S)) + threadIdx.x;
+  auto sS = [&](int stage, int e) -> S& { return stS[(stage * kStageS + e) * kThomasThreads]; };
+  auto sT = [&](int stage, int e) -> T& { return stT[(stage * kStageT + e) * kThomasThreads]; };
+  auto stage_u = [&](int t, int stage) {
 #pragma unroll
-    for (int a = 0; a < NF; ++a)
+    for (int e = 0; e < kThomasCpl; ++e) cpa(&sS(stage, e), ucp(t, e));
+  };
+  auto stage_rup = [&](int t, int stage, int e0) {   // rows of u at the cell's faces and of p, slab t
+    const T* ru = r.u + (size_t)t * g.F;
 #pragma unroll
-      for (int b = 0; b < NF; ++b) U[a][b] = ubuf[((size_t)t * kThomasCpl + a * NF + b) * ncell + q];
+    for (int a = 0; a < NF; ++a) cpa(&sT(stage, e0 + a), ru + tc.fidx[a]);
+    cpa(&sT(stage, e0 + NF), r.p + (size_t)t * g.C + tc.cc);
   };
 
   // ---- pass 1: ascending elimination ----------------------------------------
+  // Slab s stages U_s, the rows of u and p at s (s < N) in S 0..35 / T 0..6,
+  // and the rows of v and pbar at s (s >= 1) in T 7..13; the set-up consumes
+  // slab 0, elimination step t slab t + 1.
+  auto stage1 = [&](int s, int stage) {
+    if (s < N) {
+      stage_u(s, stage);
+      stage_rup(s, stage, 0);
+    }
+    if (s >= 1) {
+      const T* rv = r.v + (size_t)s * g.F;
+#pragma unroll
+      for (int a = 0; a < NF; ++a) cpa(&sT(stage, NB + a), rv + tc.fidx[a]);
+      cpa(&sT(stage, NB + NF), r.pbar + (size_t)s * g.C + tc.cc);
+    }
+  };
+  auto staged_y = [&](int stage, S y[NB]) {
+    T ruv[NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) ruv[a] = sT(stage, a);
+    tc.u_solve_v(ruv, sT(stage, NF), cg, y);
+  };
+  auto staged_u = [&](int stage, S U[NF][NF]) {
+#pragma unroll
+    for (int a = 0; a < NF; ++a)
+#pragma unroll
+      for (int b = 0; b < NF; ++b) U[a][b] = sS(stage, a * NF + b);
+  };
+
   // carried from block t-1: M = O_{t-1}^T X_{t-1} (faces), m = O_{t-1}^T z_{t-1};
   // from U_t (computed at block t-1): Sn = U_t^T P U_t, Rn = -U_t^T y_t
   S M[NF][NF], m[NF], Sn[NF][NF], Rn[NF];
+  stage1(0, 0);
+  cpa_commit();
+  stage1(1, 1);
+  cpa_commit();
+  cpa_wait_prev();
   {
     S U[NF][NF], y[NB];
-    load_u(0, U);
-    tc.u_solve(r, 0, cg, y);
+    staged_u(0, U);
+    staged_y(0, y);
 #pragma unroll
     for (int b = 0; b < NF; ++b) {
       S w[NF], pw[NF];
@@ -1127,9 +1199,12 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   }
   for (int t = 0; t < N; ++t) {
     const int tv = t + 1;
+    const int cur = tv & 1;
+    if (tv + 1 <= N) stage1(tv + 1, (tv + 1) & 1);   // the stage slab t - 1 used
+    cpa_commit();
+    cpa_wait_prev();                                   // slab tv has landed
     // pivot block of v_tv
     S A[NF][NF], B[NF][NB], qv[NB];
-    const T* rv = r.v + (size_t)tv * g.F;
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
 #pragma unroll
@@ -1139,14 +1214,14 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
         if (a == b) v += cg.act[a] > S(0) ? ((tv < N ? pick<S>(g.a, g.af) : S(0)) + lm) : S(1);
         A[a][b] = v;
       }
-      B[a][NF] = S(-ld(rv + tc.fidx[a])) * tc.act[a] + Rn[a] - m[a];
+      B[a][NF] = S(-sT(cur, NB + a)) * tc.act[a] + Rn[a] - m[a];
     }
-    qv[NF] = S(-ld(r.pbar + (size_t)tv * g.C + tc.cc));
+    qv[NF] = S(-sT(cur, NB + NF));
     // coupling to v_{tv+1}: O = -P U_tv / dt, and the next block's Sn, Rn
     if (tv < N) {
       S U[NF][NF], y[NB];
-      load_u(tv, U);
-      tc.u_solve(r, tv, cg, y);
+      staged_u(cur, U);
+      staged_y(cur, y);
 #pragma unroll
       for (int a = 0; a < NF; ++a) B[a][NF] += idt * cg.act[a] * y[a];
       S PU[NF][NF];
@@ -1220,17 +1295,33 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   }
 
   // ---- pass 2: descending substitution, x_t overwrites z_t -------------------
+  // Step i stages the record of block t = N - 1 - i (written in pass 1 by this
+  // thread; the fence orders those stores before the copies that read them).
+  __threadfence_block();
+  auto stage2 = [&](int t, int stage) {
+#pragma unroll
+    for (int e = 0; e < kThomasRec; ++e) cpa(&sS(stage, e), &rec(t, e));
+  };
   {
     S xn[NF];
+    stage2(N - 1, 0);
+    cpa_commit();
+    if (N >= 2) stage2(N - 2, 1);
+    cpa_commit();
+    cpa_wait_prev();
 #pragma unroll
-    for (int a = 0; a < NF; ++a) xn[a] = rec(N - 1, NF * NF + NF + a);
+    for (int a = 0; a < NF; ++a) xn[a] = sS(0, NF * NF + NF + a);
     for (int t = N - 2; t >= 0; --t) {
+      const int i = N - 1 - t, cur = i & 1;
+      if (t >= 1) stage2(t - 1, (i + 1) & 1);
+      cpa_commit();
+      cpa_wait_prev();
       S xt[NB];
 #pragma unroll
       for (int a = 0; a < NB; ++a) {
-        S v = rec(t, NF * NF + NF + a);
+        S v = sS(cur, NF * NF + NF + a);
 #pragma unroll
-        for (int b = 0; b < NF; ++b) v -= (a < NF ? rec(t, a * NF + b) : rec(t, NF * NF + b)) * xn[b];
+        for (int b = 0; b < NF; ++b) v -= (a < NF ? sS(cur, a * NF + b) : sS(cur, NF * NF + b)) * xn[b];
         xt[a] = v;
       }
 #pragma unroll
@@ -1241,16 +1332,42 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
   }
 
   // ---- pass 3: u blocks from the v solution, x += omega delta ---------------
+  // Step t stages U_t (S 0..35), the v-block solution x_t (S 36..42), the rows
+  // of u and p at t (T 0..6) and the state it updates: u_t and v_{t+1} at the
+  // cell's faces (T 7..18), p_t and pbar_{t+1} at the cell (T 19, 20).  Only
+  // this thread writes those entries, each after its own copy has landed.
+  __threadfence_block();
+  auto stage3 = [&](int t, int stage) {
+    stage_u(t, stage);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) cpa(&sS(stage, kThomasCpl + a), &rec(t, NF * NF + NF + a));
+    stage_rup(t, stage, 0);
+    const T* fu = x.u + (size_t)t * g.F;
+    const T* fv = x.v + (size_t)(t + 1) * g.F;
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+      cpa(&sT(stage, NB + a), fu + tc.fidx[a]);
+      cpa(&sT(stage, NB + NF + a), fv + tc.fidx[a]);
+    }
+    cpa(&sT(stage, NB + 2 * NF), x.p + (size_t)t * g.C + tc.cc);
+    cpa(&sT(stage, NB + 2 * NF + 1), x.pbar + (size_t)(t + 1) * g.C + tc.cc);
+  };
   const T om = pick<T>(g.omega, g.omegaf);
   S xv0[NF];
 #pragma unroll
   for (int a = 0; a < NF; ++a) xv0[a] = S(0);
+  stage3(0, 0);
+  cpa_commit();
   for (int t = 0; t < N; ++t) {
+    const int cur = t & 1;
+    if (t + 1 < N) stage3(t + 1, (t + 1) & 1);
+    cpa_commit();
+    cpa_wait_prev();
     S U[NF][NF], y[NB], xv1[NB];
-    load_u(t, U);
-    tc.u_solve(r, t, cg, y);
+    staged_u(cur, U);
+    staged_y(cur, y);
 #pragma unroll
-    for (int a = 0; a < NB; ++a) xv1[a] = rec(t, NF * NF + NF + a);
+    for (int a = 0; a < NB; ++a) xv1[a] = sS(cur, kThomasCpl + a);
     S w[NF];
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
@@ -1271,13 +1388,11 @@ scgs3t_colour_kernel(Geom g, State<T> x, CState<T> r, int colour, int ncell, con
     for (int a = 0; a < NF; ++a)
       if (tc.act[a] > S(0)) {
         const int f = tc.fidx[a];
-        fu[f] = fu[f] + om * T(y[a] - pw[a]);
-        fv[f] = fv[f] + om * T(xv1[a]);
+        fu[f] = sT(cur, NB + a) + om * T(y[a] - pw[a]);
+        fv[f] = sT(cur, NB + NF + a) + om * T(xv1[a]);
       }
-    T* fp = x.p + (size_t)t * g.C + tc.cc;
-    T* fpb = x.pbar + (size_t)(t + 1) * g.C + tc.cc;
-    *fp = *fp + om * T(y[NF] + gw);
-    *fpb = *fpb + om * T(xv1[NF]);
+    x.p[(size_t)t * g.C + tc.cc] = sT(cur, NB + 2 * NF) + om * T(y[NF] + gw);
+    x.pbar[(size_t)(t + 1) * g.C + tc.cc] = sT(cur, NB + 2 * NF + 1) + om * T(xv1[NF]);
 #pragma unroll
     for (int a = 0; a < NF; ++a) xv0[a] = xv1[a];
   }
@@ -1653,8 +1768,15 @@ static void launch_scgs3t(const Geom& g, State<T> x, CState<T> r, int colour, co
   S* zbuf = static_cast<S*>(scratch);
   launch_pdl3(scgs3t_coupling_kernel<T, S>, dim3((ncell + 127) / 128, g.N), dim3(128), 0, st, g, (const T*)x.v,
               colour, ncell, zbuf + (size_t)kThomasRec * g.N * ncell);
-  launch_pdl3(scgs3t_colour_kernel<T, S>, dim3((ncell + 63) / 64), dim3(64), 0, st, g, x, r, colour, ncell, lm_dev,
-              zbuf);
+  constexpr size_t smem = scgs3t_smem_bytes<T, S>();
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute((const void*)scgs3t_colour_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  });
+  launch_pdl3(scgs3t_colour_kernel<T, S>, dim3((ncell + kThomasThreads - 1) / kThomasThreads), dim3(kThomasThreads),
+              smem, st, g, x, r, colour, ncell, lm_dev, zbuf);
 }
 
 template <class T>
