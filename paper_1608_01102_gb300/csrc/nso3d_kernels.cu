@@ -225,6 +225,52 @@ __device__ T jtu_ab(const Geom& g, ABt<T> a, int axis, int k, int j, int i) {
   return r + T(0.25) * s;
 }
 
+// The same gather at a face of a closed box at least one cell from the walls
+// along every axis (1 <= i, j, k <= n - 2): there every edge sum and every
+// product jtu_ab reads is interior, so the wall tests drop out and the records
+// sit at fixed offsets from the face's three base indices.  Same sums in the
+// same order as jtu_ab.
+template <class T>
+__device__ __forceinline__ bool jtu_fast_ok(const Geom& g, int k, int j, int i) {
+  return !g.periodic && i >= 1 && i <= g.nx - 2 && j >= 1 && j <= g.ny - 2 && k >= 1 && k <= g.nz - 2;
+}
+
+template <class T>
+__device__ T jtu_ab_far(const Geom& g, ABt<T> a, int axis, int k, int j, int i) {
+  const T ih = pick<T>(g.ih, g.ihf);
+  const int sxy = g.nx + 1, sxz = (g.nx + 1) * g.ny;   // x-face strides along j, k
+  const int syy = g.nx, syz = g.nx * (g.ny + 1);       // y-faces
+  const int szy = g.nx, szz = g.nx * g.ny;             // z-faces
+  const AB4<T>* X = a + (k * g.ny + j) * sxy + i;
+  const AB4<T>* Y = a + g.Fx + (k * (g.ny + 1) + j) * syy + i;
+  const AB4<T>* Z = a + g.Fxy + (k * g.ny + j) * szy + i;
+  if (axis == 0) {
+    const T qy0 = T(0.5) * (X[0].a1 + X[-sxz].a1 + Z[0].a2 + Z[-1].a2);
+    const T qy1 = T(0.5) * (X[sxz].a1 + X[0].a1 + Z[szz].a2 + Z[szz - 1].a2);
+    const T qz0 = T(0.5) * (X[0].a2 + X[-sxy].a2 + Y[0].a1 + Y[-1].a1);
+    const T qz1 = T(0.5) * (X[sxy].a2 + X[0].a2 + Y[syy].a1 + Y[syy - 1].a1);
+    const T r = (qy0 - qy1 - qz0 + qz1) * ih;
+    const T s = Y[-1].b1 + Y[0].b1 + Y[syy - 1].b1 + Y[syy].b1 + Z[-1].b2 + Z[0].b2 + Z[szz - 1].b2 + Z[szz].b2;
+    return r + T(0.25) * s;
+  }
+  if (axis == 1) {
+    const T qz0 = T(0.5) * (X[0].a2 + X[-sxy].a2 + Y[0].a1 + Y[-1].a1);
+    const T qz1 = T(0.5) * (X[1].a2 + X[1 - sxy].a2 + Y[1].a1 + Y[0].a1);
+    const T qx0 = T(0.5) * (Y[0].a2 + Y[-syz].a2 + Z[0].a1 + Z[-szy].a1);
+    const T qx1 = T(0.5) * (Y[syz].a2 + Y[0].a2 + Z[szz].a1 + Z[szz - szy].a1);
+    const T r = (qz0 - qz1 - qx0 + qx1) * ih;
+    const T s = X[0].b2 + X[1].b2 + X[-sxy].b2 + X[1 - sxy].b2 + Z[0].b1 + Z[-szy].b1 + Z[szz].b1 + Z[szz - szy].b1;
+    return r + T(0.25) * s;
+  }
+  const T qx0 = T(0.5) * (Y[0].a2 + Y[-syz].a2 + Z[0].a1 + Z[-szy].a1);
+  const T qx1 = T(0.5) * (Y[syy].a2 + Y[syy - syz].a2 + Z[szy].a1 + Z[0].a1);
+  const T qy0 = T(0.5) * (X[0].a1 + X[-sxz].a1 + Z[0].a2 + Z[-1].a2);
+  const T qy1 = T(0.5) * (X[1].a1 + X[1 - sxz].a1 + Z[1].a2 + Z[0].a2);
+  const T r = (qx0 - qx1 - qy0 + qy1) * ih;
+  const T s = X[0].b1 + X[1].b1 + X[-sxz].b1 + X[1 - sxz].b1 + Y[0].b2 + Y[syy].b2 + Y[-syz].b2 + Y[syy - syz].b2;
+  return r + T(0.25) * s;
+}
+
 // rows 1 and 3 from the stored products (AB) or inline
 template <class T, bool AB>
 __device__ __forceinline__ T row1x(const Geom& g, const CState<T>& x, const T* __restrict__ z, ABt<T> ab,
@@ -233,7 +279,9 @@ __device__ __forceinline__ T row1x(const Geom& g, const CState<T>& x, const T* _
   const T* vt = x.v + (size_t)t * g.F;
   const T* pb = x.pbar + (size_t)t * g.C;
   T val = ld(x.u + (size_t)(t - 1) * g.F + e) * pick<T>(g.idt, g.idtf);
-  if (g.self_adv) val += jtu_ab(g, ab + (size_t)t * g.F, axis, k, j, i);
+  if (g.self_adv)
+    val += jtu_fast_ok<T>(g, k, j, i) ? jtu_ab_far(g, ab + (size_t)t * g.F, axis, k, j, i)
+                                      : jtu_ab(g, ab + (size_t)t * g.F, axis, k, j, i);
   val += grad(g, pb, axis, k, j, i);
   if (t < g.N) {
     const T* ut = x.u + (size_t)t * g.F;
