@@ -508,7 +508,16 @@ __device__ void local_adv_jac3(const Geom& g, const T* v, int k, int j, int i, c
     const int A = f >> 1, s = f & 1;
     const int fk = k + (A == 2 ? s : 0), fj = j + (A == 1 ? s : 0), fi = i + (A == 0 ? s : 0);
     if (!interior(g, A, fk, fj, fi)) continue;
-    const Terms<R> tm = terms<T, R>(g, v, A, fk, fj, fi);
+    Terms<R> tm;
+    if constexpr (std::is_same<T, R>::value) {   // closed box: the strength-reduced form of pass A
+      if (!g.periodic)
+        tm = A == 0 ? terms_box<T, 0>(g, v, fk, fj, fi)
+                    : (A == 1 ? terms_box<T, 1>(g, v, fk, fj, fi) : terms_box<T, 2>(g, v, fk, fj, fi));
+      else
+        tm = terms<T, R>(g, v, A, fk, fj, fi);
+    } else {
+      tm = terms<T, R>(g, v, A, fk, fj, fi);
+    }
 #pragma unroll
     for (int term = 0; term < 2; ++term) {
       const int C = term == 0 ? (A + 1) % 3 : (A + 2) % 3;
